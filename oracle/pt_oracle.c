@@ -1,0 +1,1243 @@
+/*
+ * pt_oracle.c -- CPU oracle for the path tracer. TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, recursive Monte Carlo path tracer in double precision.  It is the
+ * reference that the CUDA path is checked against and it shares no code with it:
+ * only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference legs
+ * may load it.
+ *
+ * What it computes (paper: "Physically-based Path Tracer using WebGPU and OpenPBR"):
+ *   - the pixel estimate of the rendering equation I = g [eps + int p I]   (Sec. 1.1, Eq. 1)
+ *     by backward path tracing from a perspective camera with per-sample jitter (Sec. 5.1.2),
+ *   - closest-hit search through an AABB BVH (Sec. 5.1.1); a brute-force loop over all
+ *     triangles is kept beside it as the pin,
+ *   - OpenPBR-style shading at every hit with importance sampling (Sec. 4, Sec. 5.1.3),
+ *   - Russian roulette and averaging of the samples (Sec. 5.1.3), progressive (Sec. 5.1.4).
+ * Where the paper is silent (light sampling, MIS, the RNG keying, the lobe formulas, camera
+ * conventions, depth semantics, roulette rule) this file follows the readings listed in the
+ * design notes; each such place says "reading:" below.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), counter
+ * (pixel, sample, bounce, dim/4), key (lo32(seed), hi32(seed)), word dim%4, uniform
+ * U = (word >> 8) * 2^-24.  Reading: the paper uses PCG (Sec. 5.1.2); a counter-based
+ * generator is used instead so the oracle and the GPU draw identical numbers.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------------------ */
+/* small vector algebra                                                                   */
+/* ------------------------------------------------------------------------------------ */
+typedef struct { double x, y, z; } v3;
+
+static inline v3 mk(double x, double y, double z) { v3 r; r.x = x; r.y = y; r.z = z; return r; }
+static inline v3 add(v3 a, v3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static inline v3 sub(v3 a, v3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static inline v3 scl(v3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+static inline v3 hmul(v3 a, v3 b) { return mk(a.x * b.x, a.y * b.y, a.z * b.z); }
+static inline double dot(v3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static inline v3 cross(v3 a, v3 b) {
+    return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static inline double length(v3 a) { return sqrt(dot(a, a)); }
+static inline v3 normalize(v3 a) { return scl(a, 1.0 / length(a)); }
+static inline double get(v3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
+static inline double lum(v3 c) { return 0.2126 * c.x + 0.7152 * c.y + 0.0722 * c.z; }
+static inline double maxc(v3 c) { return fmax(c.x, fmax(c.y, c.z)); }
+static inline v3 splat(double s) { return mk(s, s, s); }
+
+/* ------------------------------------------------------------------------------------ */
+/* Philox4x32-10                                                                          */
+/* ------------------------------------------------------------------------------------ */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod_a = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t prod_b = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(prod_b >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)prod_b;
+        uint32_t y2 = (uint32_t)(prod_a >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)prod_a;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += 0x9E3779B9u;  /* Weyl key schedule */
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+double oracle_uniform(uint32_t pixel, uint32_t sample, uint32_t bounce, uint32_t dim,
+                      uint64_t seed) {
+    uint32_t ctr[4] = {pixel, sample, bounce, dim >> 2};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return (double)(out[dim & 3u] >> 8) * (1.0 / 16777216.0);
+}
+
+/* dimension table of one path vertex */
+enum { DIM_CAM_X = 0, DIM_CAM_Y = 1, DIM_LIGHT_PICK = 2, DIM_LIGHT_U = 3, DIM_LIGHT_V = 4,
+       DIM_LOBE = 5, DIM_DIR_U = 6, DIM_DIR_V = 7, DIM_REFRACT = 8, DIM_RR = 9 };
+
+/* ------------------------------------------------------------------------------------ */
+/* OpenPBR parameters (26 values per material, same order as the C-ABI table)            */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    double base_weight; v3 base_color; double metalness; double diffuse_roughness;
+    double spec_weight; v3 spec_color; double spec_rough; double spec_ior;
+    double trans_weight; v3 trans_color;
+    double coat_weight; v3 coat_color; double coat_rough; double coat_ior;
+    double emission; v3 emission_color;
+} omat;
+
+static omat unpack_material(const double* p) {
+    omat m;
+    m.base_weight = p[0]; m.base_color = mk(p[1], p[2], p[3]);
+    m.metalness = p[4]; m.diffuse_roughness = p[5];
+    m.spec_weight = p[6]; m.spec_color = mk(p[7], p[8], p[9]);
+    m.spec_rough = p[10]; m.spec_ior = p[11];
+    m.trans_weight = p[12]; m.trans_color = mk(p[13], p[14], p[15]);
+    m.coat_weight = p[16]; m.coat_color = mk(p[17], p[18], p[19]);
+    m.coat_rough = p[20]; m.coat_ior = p[21];
+    m.emission = p[22]; m.emission_color = mk(p[23], p[24], p[25]);
+    return m;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Fresnel                                                                                */
+/* ------------------------------------------------------------------------------------ */
+/* Exact unpolarised dielectric Fresnel reflectance.  cos_i = cosine on the incident side
+ * (clamped to [0, 1]); eta = n_transmitted / n_incident.  Total internal reflection -> 1. */
+double oracle_fresnel_dielectric(double cos_i, double eta) {
+    if (cos_i < 0.0) cos_i = 0.0;
+    if (cos_i > 1.0) cos_i = 1.0;
+    double sin2_t = (1.0 - cos_i * cos_i) / (eta * eta);
+    if (sin2_t >= 1.0) return 1.0;
+    double cos_t = sqrt(1.0 - sin2_t);
+    double r_par = (eta * cos_i - cos_t) / (eta * cos_i + cos_t);
+    double r_perp = (cos_i - eta * cos_t) / (cos_i + eta * cos_t);
+    return 0.5 * (r_par * r_par + r_perp * r_perp);
+}
+
+/* Metal Fresnel: Schlick's curve from F0, corrected by a mu(1-mu)^6 term so that at the
+ * 82-degree reference angle (mu = 1/7) it equals tint * Schlick (the "F82-tint" model of the
+ * Adobe Standard Material that OpenPBR adopts).  Clamped to [0, 1].
+ * Reading: OpenPBR's metal Fresnel; base_weight*base_color is F0, specular_color the tint. */
+static double f82_channel(double f0, double tint, double mu) {
+    const double mu_bar = 1.0 / 7.0;
+    double one_m = 1.0 - mu;
+    double schlick = f0 + (1.0 - f0) * pow(one_m, 5.0);
+    double schlick_bar = f0 + (1.0 - f0) * pow(1.0 - mu_bar, 5.0);
+    double b = schlick_bar * (1.0 - tint) / (mu_bar * pow(1.0 - mu_bar, 6.0));
+    double f = schlick - b * mu * pow(one_m, 6.0);
+    return f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+}
+static v3 fresnel_f82(v3 f0, v3 tint, double mu) {
+    if (mu < 0.0) mu = 0.0;
+    if (mu > 1.0) mu = 1.0;
+    return mk(f82_channel(f0.x, tint.x, mu), f82_channel(f0.y, tint.y, mu),
+              f82_channel(f0.z, tint.z, mu));
+}
+void oracle_fresnel_f82(const double f0[3], const double tint[3], double mu, double out[3]) {
+    v3 r = fresnel_f82(mk(f0[0], f0[1], f0[2]), mk(tint[0], tint[1], tint[2]), mu);
+    out[0] = r.x; out[1] = r.y; out[2] = r.z;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* GGX microfacet distribution (Trowbridge-Reitz), alpha = roughness^2                     */
+/* ------------------------------------------------------------------------------------ */
+double oracle_ggx_D(const double h[3], double a) {
+    if (h[2] <= 0.0) return 0.0;
+    double a2 = a * a;
+    double s2 = h[0] * h[0] + h[1] * h[1];
+    double c2 = h[2] * h[2];
+    double d = a2 * c2 + s2;   /* = (cos^2 (a^2 - 1) + 1) for a unit h */
+    return a2 / (M_PI * d * d);
+}
+static double ggx_D(v3 h, double a) { double hh[3] = {h.x, h.y, h.z}; return oracle_ggx_D(hh, a); }
+
+/* Smith Lambda for GGX: (-1 + sqrt(1 + a^2 tan^2))/2, written without cancellation. */
+static double ggx_lambda(v3 w, double a) {
+    double c2 = w.z * w.z;
+    if (c2 <= 0.0) return INFINITY;
+    double t2 = (w.x * w.x + w.y * w.y) / c2;
+    double x = a * a * t2;
+    return x / (2.0 * (1.0 + sqrt(1.0 + x)));
+}
+double oracle_ggx_G1(const double w[3], double a) {
+    return 1.0 / (1.0 + ggx_lambda(mk(w[0], w[1], w[2]), a));
+}
+static double ggx_G1(v3 w, double a) { return 1.0 / (1.0 + ggx_lambda(w, a)); }
+/* height-correlated masking-shadowing */
+static double ggx_G2(v3 wo, v3 wi, double a) {
+    return 1.0 / (1.0 + ggx_lambda(wo, a) + ggx_lambda(wi, a));
+}
+/* density of visible normals: G1(wo) max(0, wo.h) D(h) / wo.z */
+static double ggx_vndf_pdf(v3 wo, v3 h, double a) {
+    double oh = dot(wo, h);
+    if (oh <= 0.0 || wo.z <= 0.0) return 0.0;
+    return ggx_G1(wo, a) * oh * ggx_D(h, a) / wo.z;
+}
+/* Sampling of visible normals (Heitz, JCGT 7(4), 2018): stretch the view vector to the
+ * unit-roughness configuration, sample the projected hemisphere, unstretch. */
+static v3 ggx_vndf_sample(v3 wo, double a, double u1, double u2) {
+    v3 vh = normalize(mk(a * wo.x, a * wo.y, wo.z));
+    double lensq = vh.x * vh.x + vh.y * vh.y;
+    v3 t1 = lensq > 0.0 ? scl(mk(-vh.y, vh.x, 0.0), 1.0 / sqrt(lensq)) : mk(1.0, 0.0, 0.0);
+    v3 t2 = cross(vh, t1);
+    double r = sqrt(u1);
+    double phi = 2.0 * M_PI * u2;
+    double p1 = r * cos(phi);
+    double p2 = r * sin(phi);
+    double s = 0.5 * (1.0 + vh.z);
+    p2 = (1.0 - s) * sqrt(fmax(0.0, 1.0 - p1 * p1)) + s * p2;
+    v3 nh = add(add(scl(t1, p1), scl(t2, p2)), scl(vh, sqrt(fmax(0.0, 1.0 - p1 * p1 - p2 * p2))));
+    return normalize(mk(a * nh.x, a * nh.y, fmax(0.0, nh.z)));
+}
+void oracle_ggx_vndf_sample(const double wo[3], double a, double u1, double u2, double out[3]) {
+    v3 h = ggx_vndf_sample(mk(wo[0], wo[1], wo[2]), a, u1, u2);
+    out[0] = h.x; out[1] = h.y; out[2] = h.z;
+}
+
+static v3 reflect(v3 wo, v3 h) { return sub(scl(h, 2.0 * dot(wo, h)), wo); }
+/* refraction of wo (on the +h side) into the medium with relative index eta; 0 on TIR */
+static int refract(v3 wo, v3 h, double eta, v3* wi) {
+    double ci = dot(wo, h);
+    double s2t = (1.0 - ci * ci) / (eta * eta);
+    if (s2t >= 1.0) return 0;
+    double ct = sqrt(1.0 - s2t);
+    *wi = add(scl(wo, -1.0 / eta), scl(h, ci / eta - ct));
+    return 1;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* OpenPBR subset as a mixture of lobes (local frame, shading normal = +z, wo.z > 0)      */
+/*                                                                                        */
+/* Reading of the layering (OpenPBR is not fully specified in the paper, Sec. 4):          */
+/*   f = cw f_coat + A_c (m f_metal + (1-m) f_diel)                                       */
+/*   A_c(mi, mo) = cw cc (1 - Fc(|mi|)) (1 - Fc(mo)) + (1 - cw)                           */
+/*   f_metal = sw F82(bw bc, sc, wo.h) D G2 / (4 mo mi)                                   */
+/*   f_diel  = sw sc F(wo.h) D G2 / (4 mo mi)                                              */
+/*           + (1-t) (1 - sw F(|mi|)) (1 - sw F(mo)) bw bc / pi                             */
+/*           + t tc (1 - sw F(wo.h)) D G2 |wi.h| (wo.h) / (|mi| mo (wo.h + eta wi.h)^2)     */
+/*   f_coat  = Fc(wo.h) Dc G2c / (4 mo mi)                                                 */
+/* alpha < 1e-4 makes a lobe a delta lobe.  eta = specular_ior seen from the side of wo:   */
+/* for transmissive materials hit from the back it is 1/ior.                             */
+/* ------------------------------------------------------------------------------------ */
+enum { LOBE_COAT = 0, LOBE_METAL = 1, LOBE_DIEL = 2, LOBE_DIFF = 3, N_LOBES = 4 };
+
+typedef struct {
+    omat m;
+    double eta_s, eta_c;
+    double a_s, a_c;
+    int delta_s, delta_c;
+    double p[N_LOBES];     /* lobe selection probabilities */
+    int any;               /* some lobe has positive weight */
+    int has_smooth;        /* some non-delta lobe has positive weight */
+} closure;
+
+static void closure_setup(closure* C, const omat* m, int front, double mu_o) {
+    C->m = *m;
+    C->eta_s = (m->trans_weight > 0.0 && !front) ? 1.0 / m->spec_ior : m->spec_ior;
+    C->eta_c = m->coat_ior;
+    C->a_s = m->spec_rough * m->spec_rough;
+    C->a_c = m->coat_rough * m->coat_rough;
+    C->delta_s = C->a_s < 1e-4;
+    C->delta_c = C->a_c < 1e-4;
+    double fc = oracle_fresnel_dielectric(mu_o, C->eta_c);
+    double w_coat = m->coat_weight * fc;
+    double att = m->coat_weight * lum(m->coat_color) * (1.0 - fc) + (1.0 - m->coat_weight);
+    v3 f0 = scl(m->base_color, m->base_weight);
+    double w_metal = att * m->metalness * m->spec_weight * lum(fresnel_f82(f0, m->spec_color, mu_o));
+    double fs = oracle_fresnel_dielectric(mu_o, C->eta_s);
+    double w_spec = att * (1.0 - m->metalness) * m->spec_weight * lum(m->spec_color) * fs;
+    double w_trans = att * (1.0 - m->metalness) * m->trans_weight * lum(m->trans_color) *
+                     (1.0 - m->spec_weight * fs);
+    double w_diff = att * (1.0 - m->metalness) * (1.0 - m->trans_weight) *
+                    (1.0 - m->spec_weight * fs) * lum(f0);
+    double w[N_LOBES] = {w_coat, w_metal, w_spec + w_trans, w_diff};
+    double sum = w[0] + w[1] + w[2] + w[3];
+    C->any = sum > 0.0;
+    for (int j = 0; j < N_LOBES; ++j) C->p[j] = C->any ? w[j] / sum : 0.0;
+    C->has_smooth = (C->p[LOBE_COAT] > 0.0 && !C->delta_c) ||
+                    ((C->p[LOBE_METAL] > 0.0 || C->p[LOBE_DIEL] > 0.0) && !C->delta_s) ||
+                    C->p[LOBE_DIFF] > 0.0;
+}
+
+/* probability of reflecting (vs refracting) in the dielectric lobe, given F(wo.h) */
+static double diel_reflect_prob(const closure* C, double F) {
+    const omat* m = &C->m;
+    double r = m->spec_weight * lum(m->spec_color) * F;
+    double t = m->trans_weight * lum(m->trans_color) * (1.0 - m->spec_weight * F);
+    if (F >= 1.0) return 1.0;
+    double s = r + t;
+    return s > 0.0 ? r / s : 1.0;
+}
+
+static v3 coat_attenuation(const closure* C, double mu_i_abs, double mu_o) {
+    const omat* m = &C->m;
+    double fci = oracle_fresnel_dielectric(mu_i_abs, C->eta_c);
+    double fco = oracle_fresnel_dielectric(mu_o, C->eta_c);
+    return add(scl(m->coat_color, m->coat_weight * (1.0 - fci) * (1.0 - fco)),
+               splat(1.0 - m->coat_weight));
+}
+
+/* non-delta part of f(wo, wi) and the mixture pdf of producing wi by BSDF sampling */
+static void closure_eval(const closure* C, v3 wo, v3 wi, v3* f_out, double* pdf_out) {
+    const omat* m = &C->m;
+    v3 f = splat(0.0);
+    double pdf = 0.0;
+    double mo = wo.z, mi = wi.z;
+    *f_out = f;
+    *pdf_out = 0.0;
+    if (mo <= 0.0 || mi == 0.0) return;
+    v3 ac = coat_attenuation(C, fabs(mi), mo);
+    if (mi > 0.0) {
+        v3 h = normalize(add(wo, wi));
+        double oh = dot(wo, h);
+        if (oh <= 0.0) return;
+        if (!C->delta_c && m->coat_weight > 0.0) {
+            double fr = oracle_fresnel_dielectric(oh, C->eta_c);
+            double val = m->coat_weight * fr * ggx_D(h, C->a_c) * ggx_G2(wo, wi, C->a_c) /
+                         (4.0 * mo * mi);
+            f = add(f, splat(val));
+            pdf += C->p[LOBE_COAT] * ggx_vndf_pdf(wo, h, C->a_c) / (4.0 * oh);
+        }
+        if (!C->delta_s) {
+            double dg = ggx_D(h, C->a_s) * ggx_G2(wo, wi, C->a_s) / (4.0 * mo * mi);
+            double vndf = ggx_vndf_pdf(wo, h, C->a_s) / (4.0 * oh);
+            if (m->metalness > 0.0) {
+                v3 fm = fresnel_f82(scl(m->base_color, m->base_weight), m->spec_color, oh);
+                f = add(f, scl(hmul(ac, fm), m->metalness * m->spec_weight * dg));
+            }
+            pdf += C->p[LOBE_METAL] * vndf;
+            double fr = oracle_fresnel_dielectric(oh, C->eta_s);
+            f = add(f, scl(hmul(ac, m->spec_color), (1.0 - m->metalness) * m->spec_weight * fr * dg));
+            pdf += C->p[LOBE_DIEL] * diel_reflect_prob(C, fr) * vndf;
+        }
+        double fsi = oracle_fresnel_dielectric(mi, C->eta_s);
+        double fso = oracle_fresnel_dielectric(mo, C->eta_s);
+        double kd = (1.0 - m->metalness) * (1.0 - m->trans_weight) * (1.0 - m->spec_weight * fsi) *
+                    (1.0 - m->spec_weight * fso) * m->base_weight / M_PI;
+        f = add(f, scl(hmul(ac, m->base_color), kd));
+        pdf += C->p[LOBE_DIFF] * mi / M_PI;
+    } else {
+        if (!C->delta_s && m->trans_weight > 0.0) {
+            double eta = C->eta_s;
+            v3 h = normalize(add(wo, scl(wi, eta)));
+            if (h.z < 0.0) h = scl(h, -1.0);
+            double oh = dot(wo, h), ih = dot(wi, h);
+            if (oh > 0.0 && ih < 0.0) {
+                double fr = oracle_fresnel_dielectric(oh, eta);
+                double denom = oh + eta * ih;
+                double dg = ggx_D(h, C->a_s) * ggx_G2(wo, wi, C->a_s);
+                double val = (1.0 - m->metalness) * m->trans_weight * (1.0 - m->spec_weight * fr) *
+                             dg * fabs(ih) * oh / (fabs(mi) * mo * denom * denom);
+                f = add(f, scl(hmul(ac, m->trans_color), val));
+                pdf += C->p[LOBE_DIEL] * (1.0 - diel_reflect_prob(C, fr)) *
+                       ggx_vndf_pdf(wo, h, C->a_s) * eta * eta * fabs(ih) / (denom * denom);
+            }
+        }
+    }
+    *f_out = f;
+    *pdf_out = pdf;
+}
+
+typedef struct {
+    v3 wi;
+    v3 weight;     /* f |cos| / pdf (delta lobes: reflectance / selection probability) */
+    double pdf;    /* mixture pdf of the non-delta lobes at wi (0 for a delta sample) */
+    int is_delta;
+} bsdf_sample_t;
+
+/* one-sample mixture: pick a lobe with u_lobe, sample it with (u1, u2), dielectric
+ * reflect/refract with u_refr.  Returns 0 if the sample is invalid (path ends). */
+static int closure_sample(const closure* C, v3 wo, double u_lobe, double u1, double u2,
+                          double u_refr, bsdf_sample_t* out) {
+    const omat* m = &C->m;
+    if (!C->any || wo.z <= 0.0) return 0;
+    int lobe = -1, last = -1;
+    double c = 0.0;
+    for (int j = 0; j < N_LOBES; ++j) {
+        if (C->p[j] <= 0.0) continue;
+        last = j;
+        c += C->p[j];
+        if (u_lobe < c) { lobe = j; break; }
+    }
+    if (lobe < 0) lobe = last;
+    double mo = wo.z;
+    v3 wi;
+    out->is_delta = 0;
+    out->pdf = 0.0;
+    if (lobe == LOBE_COAT) {
+        if (C->delta_c) {
+            out->wi = mk(-wo.x, -wo.y, wo.z);
+            out->weight = splat(m->coat_weight * oracle_fresnel_dielectric(mo, C->eta_c) /
+                                C->p[LOBE_COAT]);
+            out->is_delta = 1;
+            return 1;
+        }
+        v3 h = ggx_vndf_sample(wo, C->a_c, u1, u2);
+        wi = reflect(wo, h);
+        if (wi.z <= 0.0) return 0;
+    } else if (lobe == LOBE_METAL) {
+        if (C->delta_s) {
+            out->wi = mk(-wo.x, -wo.y, wo.z);
+            v3 fm = fresnel_f82(scl(m->base_color, m->base_weight), m->spec_color, mo);
+            out->weight = scl(hmul(coat_attenuation(C, mo, mo), fm),
+                              m->metalness * m->spec_weight / C->p[LOBE_METAL]);
+            out->is_delta = 1;
+            return 1;
+        }
+        v3 h = ggx_vndf_sample(wo, C->a_s, u1, u2);
+        wi = reflect(wo, h);
+        if (wi.z <= 0.0) return 0;
+    } else if (lobe == LOBE_DIEL) {
+        v3 h = C->delta_s ? mk(0.0, 0.0, 1.0) : ggx_vndf_sample(wo, C->a_s, u1, u2);
+        double oh = dot(wo, h);
+        if (oh <= 0.0) return 0;
+        double fr = oracle_fresnel_dielectric(oh, C->eta_s);
+        double pr = diel_reflect_prob(C, fr);
+        int do_reflect = u_refr < pr;
+        if (do_reflect) {
+            wi = reflect(wo, h);
+            if (wi.z <= 0.0) return 0;
+        } else {
+            if (!refract(wo, h, C->eta_s, &wi)) return 0;
+            if (wi.z >= 0.0) return 0;
+        }
+        if (C->delta_s) {
+            out->wi = wi;
+            out->is_delta = 1;
+            if (do_reflect) {
+                out->weight = scl(hmul(coat_attenuation(C, mo, mo), m->spec_color),
+                                  (1.0 - m->metalness) * m->spec_weight * fr /
+                                      (C->p[LOBE_DIEL] * pr));
+            } else {
+                out->weight = scl(hmul(coat_attenuation(C, fabs(wi.z), mo), m->trans_color),
+                                  (1.0 - m->metalness) * m->trans_weight *
+                                      (1.0 - m->spec_weight * fr) /
+                                      (C->eta_s * C->eta_s * C->p[LOBE_DIEL] * (1.0 - pr)));
+            }
+            return 1;
+        }
+    } else {
+        double r = sqrt(u1), phi = 2.0 * M_PI * u2;
+        wi = mk(r * cos(phi), r * sin(phi), sqrt(fmax(0.0, 1.0 - u1)));
+        if (wi.z <= 0.0) return 0;
+    }
+    v3 f;
+    double pdf;
+    closure_eval(C, wo, wi, &f, &pdf);
+    if (!(pdf > 0.0)) return 0;
+    out->wi = wi;
+    out->pdf = pdf;
+    out->weight = scl(f, fabs(wi.z) / pdf);
+    return 1;
+}
+
+/* ---- exported BSDF entry points (local frame) for the lobe pins and the GPU parity ---- */
+void oracle_bsdf_eval(const double* mat26, int front, const double wo[3], const double wi[3],
+                      double f_out[3], double* pdf_out) {
+    omat m = unpack_material(mat26);
+    closure C;
+    closure_setup(&C, &m, front, wo[2]);
+    v3 f;
+    closure_eval(&C, mk(wo[0], wo[1], wo[2]), mk(wi[0], wi[1], wi[2]), &f, pdf_out);
+    f_out[0] = f.x; f_out[1] = f.y; f_out[2] = f.z;
+}
+
+int oracle_bsdf_sample(const double* mat26, int front, const double wo[3], const double u[4],
+                       double wi_out[3], double weight_out[3], double* pdf_out, int* delta_out) {
+    omat m = unpack_material(mat26);
+    closure C;
+    closure_setup(&C, &m, front, wo[2]);
+    bsdf_sample_t s;
+    int ok = closure_sample(&C, mk(wo[0], wo[1], wo[2]), u[0], u[1], u[2], u[3], &s);
+    if (!ok) { *pdf_out = 0.0; *delta_out = 0; return 0; }
+    wi_out[0] = s.wi.x; wi_out[1] = s.wi.y; wi_out[2] = s.wi.z;
+    weight_out[0] = s.weight.x; weight_out[1] = s.weight.y; weight_out[2] = s.weight.z;
+    *pdf_out = s.pdf;
+    *delta_out = s.is_delta;
+    return 1;
+}
+
+void oracle_lobe_probs(const double* mat26, int front, double mu_o, double out[4]) {
+    omat m = unpack_material(mat26);
+    closure C;
+    closure_setup(&C, &m, front, mu_o);
+    for (int j = 0; j < N_LOBES; ++j) out[j] = C.p[j];
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Scene                                                                                  */
+/* ------------------------------------------------------------------------------------ */
+typedef struct { double lo[3], hi[3]; int left, right, start, count; } bvh_node;
+
+typedef struct {
+    int n_mesh_tris, n_tris;       /* n_tris = mesh + 2 per quad light */
+    v3* tv;                        /* 3 vertices per triangle */
+    int* tri_mat;                  /* material id (mesh triangles) or -1-light index */
+    int n_mats;
+    omat* mats;
+    int n_quads;
+    v3 *q_p0, *q_e1, *q_e2, *q_L, *q_n;
+    double* q_area;
+    int* q_two_sided;
+    int env_w, env_h;
+    double* env;                   /* h * w * 3 */
+    double* env_w_tex;             /* texel weights lum * sin(theta) */
+    double* env_marg;              /* h + 1 */
+    double* env_cond;              /* h * (w + 1) */
+    double env_total;
+    double eps;                    /* spawn offset */
+    int use_bvh;
+    bvh_node* nodes;
+    int n_nodes;
+    int* order;
+} oscene;
+
+/* ---- BVH: top-down median split on the longest centroid axis, leaves of <= 4 ---- */
+typedef struct { double c[3]; double lo[3], hi[3]; int id; } prim_ref;
+
+static void swap_ref(prim_ref* a, prim_ref* b) { prim_ref t = *a; *a = *b; *b = t; }
+
+/* Hoare selection: puts the k-th smallest (by centroid on axis) at index k */
+static void select_kth(prim_ref* r, int n, int k, int axis) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        double pivot = r[(lo + hi) / 2].c[axis];
+        int i = lo, j = hi;
+        while (i <= j) {
+            while (r[i].c[axis] < pivot) ++i;
+            while (r[j].c[axis] > pivot) --j;
+            if (i <= j) { swap_ref(&r[i], &r[j]); ++i; --j; }
+        }
+        if (k <= j) hi = j;
+        else if (k >= i) lo = i;
+        else break;
+    }
+}
+
+static int build_rec(oscene* S, prim_ref* r, int start, int count, int* next) {
+    int ni = (*next)++;
+    bvh_node* nd = &S->nodes[ni];
+    double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int a = 0; a < 3; ++a) { nd->lo[a] = INFINITY; nd->hi[a] = -INFINITY; }
+    for (int i = start; i < start + count; ++i)
+        for (int a = 0; a < 3; ++a) {
+            nd->lo[a] = fmin(nd->lo[a], r[i].lo[a]);
+            nd->hi[a] = fmax(nd->hi[a], r[i].hi[a]);
+            clo[a] = fmin(clo[a], r[i].c[a]);
+            chi[a] = fmax(chi[a], r[i].c[a]);
+        }
+    if (count <= 4) {
+        nd->left = nd->right = -1;
+        nd->start = start;
+        nd->count = count;
+        return ni;
+    }
+    int axis = 0;
+    for (int a = 1; a < 3; ++a)
+        if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
+    int half = count / 2;
+    select_kth(r + start, count, half, axis);
+    nd->start = start;
+    nd->count = 0;
+    int l = build_rec(S, r, start, half, next);
+    int rr = build_rec(S, r, start + half, count - half, next);
+    S->nodes[ni].left = l;
+    S->nodes[ni].right = rr;
+    return ni;
+}
+
+static void build_bvh(oscene* S) {
+    int n = S->n_tris;
+    prim_ref* r = (prim_ref*)malloc(sizeof(prim_ref) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        v3 a = S->tv[3 * i], b = S->tv[3 * i + 1], c = S->tv[3 * i + 2];
+        for (int ax = 0; ax < 3; ++ax) {
+            double x = get(a, ax), y = get(b, ax), z = get(c, ax);
+            r[i].lo[ax] = fmin(x, fmin(y, z));
+            r[i].hi[ax] = fmax(x, fmax(y, z));
+            r[i].c[ax] = (x + y + z) / 3.0;
+        }
+        r[i].id = i;
+    }
+    S->nodes = (bvh_node*)malloc(sizeof(bvh_node) * (size_t)(2 * (n > 0 ? n : 1)));
+    int next = 0;
+    if (n > 0) build_rec(S, r, 0, n, &next);
+    S->n_nodes = next;
+    S->order = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) S->order[i] = r[i].id;
+    free(r);
+}
+
+/* ---- environment map tables (reading: piecewise-constant 2D distribution over texels,
+ *      weight = luminance * sin(theta at the texel centre)) ---- */
+static void build_env(oscene* S) {
+    int w = S->env_w, h = S->env_h;
+    S->env_w_tex = (double*)malloc(sizeof(double) * (size_t)w * h);
+    S->env_marg = (double*)malloc(sizeof(double) * (size_t)(h + 1));
+    S->env_cond = (double*)malloc(sizeof(double) * (size_t)h * (w + 1));
+    double total = 0.0;
+    double* row = (double*)malloc(sizeof(double) * (size_t)h);
+    for (int y = 0; y < h; ++y) {
+        double st = sin(M_PI * (y + 0.5) / h);
+        double rs = 0.0;
+        for (int x = 0; x < w; ++x) {
+            const double* t = &S->env[3 * ((size_t)y * w + x)];
+            double wt = lum(mk(t[0], t[1], t[2])) * st;
+            if (wt < 0.0) wt = 0.0;
+            S->env_w_tex[(size_t)y * w + x] = wt;
+            rs += wt;
+        }
+        row[y] = rs;
+        double* cd = &S->env_cond[(size_t)y * (w + 1)];
+        cd[0] = 0.0;
+        double acc = 0.0;
+        for (int x = 0; x < w; ++x) {
+            acc += S->env_w_tex[(size_t)y * w + x];
+            cd[x + 1] = rs > 0.0 ? acc / rs : (double)(x + 1) / w;
+        }
+        total += rs;
+    }
+    S->env_marg[0] = 0.0;
+    double acc = 0.0;
+    for (int y = 0; y < h; ++y) {
+        acc += row[y];
+        S->env_marg[y + 1] = total > 0.0 ? acc / total : (double)(y + 1) / h;
+    }
+    S->env_total = total;
+    free(row);
+}
+
+void* oracle_scene_create(const double* vertices, int n_vertices, const uint32_t* indices,
+                          int n_tris, const uint32_t* mat_ids, const double* mats, int n_mats,
+                          const double* quads, int n_quads, const double* env, int env_w,
+                          int env_h, int use_bvh) {
+    (void)n_vertices;
+    oscene* S = (oscene*)calloc(1, sizeof(oscene));
+    S->n_mesh_tris = n_tris;
+    S->n_tris = n_tris + 2 * n_quads;
+    S->tv = (v3*)malloc(sizeof(v3) * 3 * (size_t)(S->n_tris > 0 ? S->n_tris : 1));
+    S->tri_mat = (int*)malloc(sizeof(int) * (size_t)(S->n_tris > 0 ? S->n_tris : 1));
+    for (int i = 0; i < n_tris; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            const double* p = &vertices[3 * (size_t)indices[3 * (size_t)i + k]];
+            S->tv[3 * i + k] = mk(p[0], p[1], p[2]);
+        }
+        S->tri_mat[i] = (int)mat_ids[i];
+    }
+    S->n_mats = n_mats;
+    S->mats = (omat*)malloc(sizeof(omat) * (size_t)(n_mats > 0 ? n_mats : 1));
+    for (int i = 0; i < n_mats; ++i) S->mats[i] = unpack_material(&mats[26 * i]);
+    S->n_quads = n_quads;
+    size_t nq = (size_t)(n_quads > 0 ? n_quads : 1);
+    S->q_p0 = (v3*)malloc(sizeof(v3) * nq); S->q_e1 = (v3*)malloc(sizeof(v3) * nq);
+    S->q_e2 = (v3*)malloc(sizeof(v3) * nq); S->q_L = (v3*)malloc(sizeof(v3) * nq);
+    S->q_n = (v3*)malloc(sizeof(v3) * nq);
+    S->q_area = (double*)malloc(sizeof(double) * nq);
+    S->q_two_sided = (int*)malloc(sizeof(int) * nq);
+    for (int l = 0; l < n_quads; ++l) {
+        const double* q = &quads[13 * l];
+        v3 p0 = mk(q[0], q[1], q[2]), e1 = mk(q[3], q[4], q[5]), e2 = mk(q[6], q[7], q[8]);
+        S->q_p0[l] = p0; S->q_e1[l] = e1; S->q_e2[l] = e2;
+        S->q_L[l] = mk(q[9], q[10], q[11]);
+        v3 n = cross(e1, e2);
+        S->q_area[l] = length(n);
+        S->q_n[l] = normalize(n);
+        S->q_two_sided[l] = q[12] != 0.0;
+        /* the light is also geometry: two triangles appended after the mesh */
+        int t0 = n_tris + 2 * l, t1 = t0 + 1;
+        v3 p1 = add(p0, e1), p2 = add(add(p0, e1), e2), p3 = add(p0, e2);
+        S->tv[3 * t0] = p0; S->tv[3 * t0 + 1] = p1; S->tv[3 * t0 + 2] = p2;
+        S->tv[3 * t1] = p0; S->tv[3 * t1 + 1] = p2; S->tv[3 * t1 + 2] = p3;
+        S->tri_mat[t0] = -1 - l;
+        S->tri_mat[t1] = -1 - l;
+    }
+    S->env_w = env ? env_w : 0;
+    S->env_h = env ? env_h : 0;
+    if (env) {
+        S->env = (double*)malloc(sizeof(double) * 3 * (size_t)env_w * env_h);
+        memcpy(S->env, env, sizeof(double) * 3 * (size_t)env_w * env_h);
+        build_env(S);
+    }
+    /* spawn offset: 1e-4 of the scene bounding-box diagonal (reading) */
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < 3 * S->n_tris; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], get(S->tv[i], a));
+            hi[a] = fmax(hi[a], get(S->tv[i], a));
+        }
+    double diag = S->n_tris > 0 ? sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) +
+                                       (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                       (hi[2] - lo[2]) * (hi[2] - lo[2]))
+                                : 1.0;
+    S->eps = 1e-4 * diag;
+    S->use_bvh = use_bvh;
+    if (use_bvh) build_bvh(S);
+    return S;
+}
+
+void oracle_scene_destroy(void* h) {
+    oscene* S = (oscene*)h;
+    if (!S) return;
+    free(S->tv); free(S->tri_mat); free(S->mats);
+    free(S->q_p0); free(S->q_e1); free(S->q_e2); free(S->q_L); free(S->q_n);
+    free(S->q_area); free(S->q_two_sided);
+    free(S->env); free(S->env_w_tex); free(S->env_marg); free(S->env_cond);
+    free(S->nodes); free(S->order);
+    free(S);
+}
+
+double oracle_scene_eps(void* h) { return ((oscene*)h)->eps; }
+
+/* ------------------------------------------------------------------------------------ */
+/* Ray / triangle: watertight test (Woop, Benthin, Wald, JCGT 2(1), 2013), in double      */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    v3 o, d;
+    int kx, ky, kz;
+    double sx, sy, sz;
+} wray;
+
+static wray make_wray(v3 o, v3 d) {
+    wray r;
+    r.o = o; r.d = d;
+    double ad[3] = {fabs(d.x), fabs(d.y), fabs(d.z)};
+    int kz = 0;
+    if (ad[1] > ad[kz]) kz = 1;
+    if (ad[2] > ad[kz]) kz = 2;
+    int kx = (kz + 1) % 3, ky = (kx + 1) % 3;
+    if (get(d, kz) < 0.0) { int t = kx; kx = ky; ky = t; }
+    r.kx = kx; r.ky = ky; r.kz = kz;
+    r.sx = get(d, kx) / get(d, kz);
+    r.sy = get(d, ky) / get(d, kz);
+    r.sz = 1.0 / get(d, kz);
+    return r;
+}
+
+/* returns 1 and t (and barycentrics) if the ray hits the triangle with 0 < t < tmax */
+static int tri_hit(const wray* r, v3 p0, v3 p1, v3 p2, double tmax, double* t_out,
+                   double* u_out, double* v_out) {
+    v3 A = sub(p0, r->o), B = sub(p1, r->o), C = sub(p2, r->o);
+    double ax = get(A, r->kx) - r->sx * get(A, r->kz), ay = get(A, r->ky) - r->sy * get(A, r->kz);
+    double bx = get(B, r->kx) - r->sx * get(B, r->kz), by = get(B, r->ky) - r->sy * get(B, r->kz);
+    double cx = get(C, r->kx) - r->sx * get(C, r->kz), cy = get(C, r->ky) - r->sy * get(C, r->kz);
+    double U = cx * by - cy * bx;
+    double V = ax * cy - ay * cx;
+    double W = bx * ay - by * ax;
+    if ((U < 0.0 || V < 0.0 || W < 0.0) && (U > 0.0 || V > 0.0 || W > 0.0)) return 0;
+    double det = U + V + W;
+    if (det == 0.0) return 0;
+    double az = r->sz * get(A, r->kz), bz = r->sz * get(B, r->kz), cz = r->sz * get(C, r->kz);
+    double T = U * az + V * bz + W * cz;
+    double t = T / det;
+    if (!(t > 0.0) || !(t < tmax)) return 0;
+    *t_out = t;
+    *u_out = V / det;   /* weight of p1 */
+    *v_out = W / det;   /* weight of p2 */
+    return 1;
+}
+
+typedef struct { int tri; double t, u, v; } ohit;
+
+static int box_hit(const bvh_node* n, v3 o, v3 d, double tmax, double* tnear_out) {
+    double t0 = 0.0, t1 = tmax;
+    for (int a = 0; a < 3; ++a) {
+        double oa = get(o, a), da = get(d, a);
+        if (da == 0.0) {
+            if (oa < n->lo[a] || oa > n->hi[a]) return 0;
+            continue;
+        }
+        double ta = (n->lo[a] - oa) / da, tb = (n->hi[a] - oa) / da;
+        if (ta > tb) { double t = ta; ta = tb; tb = t; }
+        if (ta > t0) t0 = ta;
+        if (tb < t1) t1 = tb;
+    }
+    /* slack keeps flat boxes (axis-aligned triangles) from being lost to rounding */
+    if (t0 > t1 * (1.0 + 1e-9) + 1e-300) return 0;
+    *tnear_out = t0;
+    return 1;
+}
+
+static inline int closer(double t, int id, const ohit* best) {
+    return t < best->t || (t == best->t && id < best->tri);
+}
+
+static void intersect_brute(const oscene* S, v3 o, v3 d, double tmax, ohit* h) {
+    wray r = make_wray(o, d);
+    h->tri = -1; h->t = tmax; h->u = h->v = 0.0;
+    for (int i = 0; i < S->n_tris; ++i) {
+        double t, u, v;
+        if (tri_hit(&r, S->tv[3 * i], S->tv[3 * i + 1], S->tv[3 * i + 2], tmax, &t, &u, &v) &&
+            (h->tri < 0 || closer(t, i, h))) {
+            h->tri = i; h->t = t; h->u = u; h->v = v;
+        }
+    }
+}
+
+static void intersect_bvh(const oscene* S, v3 o, v3 d, double tmax, ohit* h) {
+    wray r = make_wray(o, d);
+    h->tri = -1; h->t = tmax; h->u = h->v = 0.0;
+    if (S->n_tris == 0) return;
+    int stack[128];
+    int sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const bvh_node* n = &S->nodes[stack[--sp]];
+        double tn;
+        if (!box_hit(n, o, d, h->tri < 0 ? tmax : h->t, &tn)) continue;
+        if (n->left < 0) {
+            for (int k = n->start; k < n->start + n->count; ++k) {
+                int i = S->order[k];
+                double t, u, v;
+                if (tri_hit(&r, S->tv[3 * i], S->tv[3 * i + 1], S->tv[3 * i + 2], tmax, &t, &u, &v) &&
+                    (h->tri < 0 || closer(t, i, h))) {
+                    h->tri = i; h->t = t; h->u = u; h->v = v;
+                }
+            }
+        } else {
+            stack[sp++] = n->right;
+            stack[sp++] = n->left;
+        }
+    }
+}
+
+static void intersect(const oscene* S, v3 o, v3 d, double tmax, ohit* h) {
+    if (S->use_bvh) intersect_bvh(S, o, d, tmax, h);
+    else intersect_brute(S, o, d, tmax, h);
+}
+
+static int occluded(const oscene* S, v3 o, v3 d, double tmax) {
+    ohit h;
+    intersect(S, o, d, tmax, &h);
+    return h.tri >= 0;
+}
+
+/* closest hit for n rays (o, d, tmax, pad per ray); mode 0 = scene's own structure,
+ * 1 = brute force */
+void oracle_intersect(void* hs, const double* rays, int n, int brute, int* tri_out,
+                      double* t_out, double* uv_out) {
+    const oscene* S = (const oscene*)hs;
+    for (int i = 0; i < n; ++i) {
+        const double* r = &rays[8 * i];
+        ohit h;
+        v3 o = mk(r[0], r[1], r[2]), d = mk(r[3], r[4], r[5]);
+        if (brute) intersect_brute(S, o, d, r[6], &h);
+        else intersect(S, o, d, r[6], &h);
+        tri_out[i] = h.tri;
+        t_out[i] = h.tri >= 0 ? h.t : INFINITY;
+        uv_out[2 * i] = h.u;
+        uv_out[2 * i + 1] = h.v;
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Environment map: lat-long, +y up; u = 0.5 + atan2(dx, -dz)/(2 pi), v = acos(dy)/pi     */
+/* ------------------------------------------------------------------------------------ */
+static void env_texel(const oscene* S, v3 d, int* x, int* y) {
+    double u = 0.5 + atan2(d.x, -d.z) / (2.0 * M_PI);
+    double dy = d.y < -1.0 ? -1.0 : (d.y > 1.0 ? 1.0 : d.y);
+    double v = acos(dy) / M_PI;
+    int ix = (int)floor(u * S->env_w), iy = (int)floor(v * S->env_h);
+    if (ix < 0) ix = 0;
+    if (ix > S->env_w - 1) ix = S->env_w - 1;
+    if (iy < 0) iy = 0;
+    if (iy > S->env_h - 1) iy = S->env_h - 1;
+    *x = ix; *y = iy;
+}
+
+static v3 env_radiance(const oscene* S, v3 d) {
+    int x, y;
+    env_texel(S, d, &x, &y);
+    const double* t = &S->env[3 * ((size_t)y * S->env_w + x)];
+    return mk(t[0], t[1], t[2]);
+}
+
+/* solid-angle density of sampling direction d from the environment distribution */
+static double env_pdf(const oscene* S, v3 d) {
+    if (S->env_total <= 0.0) return 0.0;
+    int x, y;
+    env_texel(S, d, &x, &y);
+    double s = sqrt(fmax(0.0, 1.0 - d.y * d.y));
+    if (s <= 0.0) return 0.0;
+    double pdf_uv = S->env_w_tex[(size_t)y * S->env_w + x] / S->env_total *
+                    (double)S->env_w * S->env_h;
+    return pdf_uv / (2.0 * M_PI * M_PI * s);
+}
+
+/* largest i in [0, n-1] with cdf[i] <= u (cdf has n+1 entries, cdf[0] = 0) */
+static int cdf_find(const double* cdf, int n, double u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (cdf[mid] <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+static int env_sample(const oscene* S, double u3, double u4, v3* d, double* pdf, v3* L) {
+    if (S->env_total <= 0.0) return 0;
+    int w = S->env_w, h = S->env_h;
+    int y = cdf_find(S->env_marg, h, u3);
+    double m0 = S->env_marg[y], m1 = S->env_marg[y + 1];
+    double dv = m1 > m0 ? (u3 - m0) / (m1 - m0) : 0.5;
+    const double* cd = &S->env_cond[(size_t)y * (w + 1)];
+    int x = cdf_find(cd, w, u4);
+    double c0 = cd[x], c1 = cd[x + 1];
+    double du = c1 > c0 ? (u4 - c0) / (c1 - c0) : 0.5;
+    double u = (x + du) / w, v = (y + dv) / h;
+    double theta = v * M_PI, phi = (u - 0.5) * 2.0 * M_PI;
+    double st = sin(theta);
+    if (st <= 0.0) return 0;
+    *d = mk(st * sin(phi), cos(theta), -st * cos(phi));
+    double pdf_uv = S->env_w_tex[(size_t)y * w + x] / S->env_total * (double)w * h;
+    *pdf = pdf_uv / (2.0 * M_PI * M_PI * st);
+    const double* t = &S->env[3 * ((size_t)y * w + x)];
+    *L = mk(t[0], t[1], t[2]);
+    return *pdf > 0.0;
+}
+
+int oracle_env_sample(void* hs, double u3, double u4, double d_out[3], double* pdf,
+                      double L_out[3]) {
+    v3 d, L;
+    int ok = env_sample((oscene*)hs, u3, u4, &d, pdf, &L);
+    if (ok) {
+        d_out[0] = d.x; d_out[1] = d.y; d_out[2] = d.z;
+        L_out[0] = L.x; L_out[1] = L.y; L_out[2] = L.z;
+    }
+    return ok;
+}
+double oracle_env_pdf(void* hs, const double d[3]) {
+    return env_pdf((oscene*)hs, mk(d[0], d[1], d[2]));
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Path tracer                                                                             */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    v3 origin, target, up;
+    double vfov_deg;
+    int width, height;
+} ocam;
+
+typedef struct {
+    long long ext_rays, shadow_rays, nan_dropped, rr_terminated, paths;
+} ostats;
+
+/* orthonormal basis around n (Duff et al., JCGT 6(1), 2017) */
+static void onb(v3 n, v3* t, v3* b) {
+    double s = n.z >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (s + n.z);
+    double c = n.x * n.y * a;
+    *t = mk(1.0 + s * n.x * n.x * a, s * c, -s * n.x);
+    *b = mk(c, s + n.y * n.y * a, -n.y);
+}
+
+static inline double power_heuristic(double pa, double pb) {
+    double a2 = pa * pa, b2 = pb * pb;
+    return a2 + b2 > 0.0 ? a2 / (a2 + b2) : 0.0;
+}
+
+static v3 offset_origin(const oscene* S, v3 x, v3 ng, v3 dir) {
+    double s = dot(dir, ng) > 0.0 ? 1.0 : -1.0;
+    return add(x, scl(ng, s * S->eps));
+}
+
+static inline double U(uint32_t p, uint32_t s, uint32_t k, uint32_t dim, uint64_t seed) {
+    return oracle_uniform(p, s, k, dim, seed);
+}
+
+/* the camera ray of pixel (px, py), sample s: pinhole, jitter inside the pixel (box filter) */
+static void camera_ray(const ocam* c, int px, int py, uint32_t s, uint64_t seed, v3* o, v3* d) {
+    uint32_t p = (uint32_t)(py * c->width + px);
+    double u0 = U(p, s, 0, DIM_CAM_X, seed), u1 = U(p, s, 0, DIM_CAM_Y, seed);
+    v3 fwd = normalize(sub(c->target, c->origin));
+    v3 right = normalize(cross(fwd, c->up));
+    v3 up = cross(right, fwd);
+    double th = tan(0.5 * c->vfov_deg * M_PI / 180.0);
+    double aspect = (double)c->width / (double)c->height;
+    double nx = (2.0 * (px + u0) / c->width - 1.0) * aspect * th;
+    double ny = (1.0 - 2.0 * (py + u1) / c->height) * th;
+    *o = c->origin;
+    *d = normalize(add(add(fwd, scl(right, nx)), scl(up, ny)));
+}
+
+/* Radiance of one path (pixel p, sample s).  Recursion written as a loop over vertices k.
+ * Readings: pbrt-style depth (max_depth = number of BSDF-sampled bounces); next-event
+ * estimation at every vertex with a non-delta lobe, env chosen with probability 1/2 when
+ * both kinds of light exist, quads uniformly; power heuristic (beta = 2); roulette from
+ * vertex 3 with q = min(0.95, max beta); lights are black emitters, emission front side. */
+/* flags: bit 0 = no next-event estimation (BSDF sampling only, emission weight 1),
+ *        bit 1 = no Russian roulette */
+enum { FLAG_NO_NEE = 1, FLAG_NO_RR = 2 };
+
+static v3 trace_path(const oscene* S, const ocam* cam, int px, int py, uint32_t s,
+                     int max_depth, uint64_t seed, int flags, ostats* st) {
+    uint32_t p = (uint32_t)(py * cam->width + px);
+    v3 o, d;
+    camera_ray(cam, px, py, s, seed, &o, &d);
+    v3 L = splat(0.0), beta = splat(1.0);
+    int nee = !(flags & FLAG_NO_NEE);
+    int prev_delta = 1;
+    double prev_pdf = 0.0;
+    int has_env = S->env_w > 0 && S->env_total > 0.0;
+    double p_env = has_env ? (S->n_quads > 0 ? 0.5 : 1.0) : 0.0;
+    for (int k = 0;; ++k) {
+        ohit h;
+        intersect(S, o, d, INFINITY, &h);
+        st->ext_rays++;
+        if (h.tri < 0) {
+            if (has_env) {
+                v3 Le = env_radiance(S, d);
+                double w = 1.0;
+                if (!prev_delta && nee) w = power_heuristic(prev_pdf, p_env * env_pdf(S, d));
+                L = add(L, scl(hmul(beta, Le), w));
+            }
+            break;
+        }
+        v3 x = add(o, scl(d, h.t));
+        v3 p0 = S->tv[3 * h.tri], p1 = S->tv[3 * h.tri + 1], p2 = S->tv[3 * h.tri + 2];
+        v3 ng = normalize(cross(sub(p1, p0), sub(p2, p0)));
+        v3 wo_w = scl(d, -1.0);
+        int front = dot(wo_w, ng) > 0.0;
+        int mid = S->tri_mat[h.tri];
+        if (mid < 0) {
+            int l = -1 - mid;
+            double cl = dot(wo_w, S->q_n[l]);
+            if (cl > 0.0 || (S->q_two_sided[l] && cl < 0.0)) {
+                double w = 1.0;
+                if (!prev_delta && nee) {
+                    double pl = (1.0 - p_env) / S->n_quads * h.t * h.t / (S->q_area[l] * fabs(cl));
+                    w = power_heuristic(prev_pdf, pl);
+                }
+                L = add(L, scl(hmul(beta, S->q_L[l]), w));
+            }
+            break;
+        }
+        const omat* m = &S->mats[mid];
+        if (m->emission > 0.0 && front) L = add(L, scl(hmul(beta, m->emission_color), m->emission));
+        if (k == max_depth) break;
+
+        v3 n = front ? ng : scl(ng, -1.0);
+        v3 tt, bb;
+        onb(n, &tt, &bb);
+        v3 wo = mk(dot(wo_w, tt), dot(wo_w, bb), dot(wo_w, n));
+        closure C;
+        closure_setup(&C, m, front, wo.z);
+
+        /* next-event estimation */
+        if (nee && C.has_smooth && (has_env || S->n_quads > 0)) {
+            double u2 = U(p, s, (uint32_t)k, DIM_LIGHT_PICK, seed);
+            double u3 = U(p, s, (uint32_t)k, DIM_LIGHT_U, seed);
+            double u4 = U(p, s, (uint32_t)k, DIM_LIGHT_V, seed);
+            v3 ld, Le = splat(0.0), ly = splat(0.0);
+            double pl = 0.0;
+            int ok = 0, to_quad = 0;
+            if (u2 < p_env) {
+                double pe;
+                if (env_sample(S, u3, u4, &ld, &pe, &Le)) {
+                    pl = p_env * pe;
+                    ok = 1;
+                }
+            } else {
+                int l = (int)floor((u2 - p_env) / (1.0 - p_env) * S->n_quads);
+                if (l > S->n_quads - 1) l = S->n_quads - 1;
+                v3 y = add(add(S->q_p0[l], scl(S->q_e1[l], u3)), scl(S->q_e2[l], u4));
+                v3 to = sub(y, x);
+                double dist2 = dot(to, to), dist = sqrt(dist2);
+                ld = scl(to, 1.0 / dist);
+                double cl = -dot(ld, S->q_n[l]);
+                if (cl > 0.0 || (S->q_two_sided[l] && cl < 0.0)) {
+                    pl = (1.0 - p_env) / S->n_quads * dist2 / (S->q_area[l] * fabs(cl));
+                    Le = S->q_L[l];
+                    ly = y;
+                    to_quad = 1;
+                    ok = 1;
+                }
+            }
+            if (ok && pl > 0.0) {
+                v3 wl = mk(dot(ld, tt), dot(ld, bb), dot(ld, n));
+                v3 f;
+                double pb;
+                closure_eval(&C, wo, wl, &f, &pb);
+                if (maxc(f) > 0.0) {
+                    /* shadow ray from the offset origin; towards a quad it aims at the light
+                     * point itself and stops 1e-4 (relative) short of it */
+                    v3 so = offset_origin(S, x, ng, ld);
+                    v3 sd = ld;
+                    double tmax = INFINITY;
+                    if (to_quad) {
+                        v3 to = sub(ly, so);
+                        double dl = length(to);
+                        sd = scl(to, 1.0 / dl);
+                        tmax = (1.0 - 1e-4) * dl;
+                    }
+                    st->shadow_rays++;
+                    if (!occluded(S, so, sd, tmax)) {
+                        double w = power_heuristic(pl, pb);
+                        L = add(L, scl(hmul(hmul(beta, f), Le), fabs(wl.z) * w / pl));
+                    }
+                }
+            }
+        }
+
+        /* BSDF sampling */
+        double u5 = U(p, s, (uint32_t)k, DIM_LOBE, seed);
+        double u6 = U(p, s, (uint32_t)k, DIM_DIR_U, seed);
+        double u7 = U(p, s, (uint32_t)k, DIM_DIR_V, seed);
+        double u8 = U(p, s, (uint32_t)k, DIM_REFRACT, seed);
+        bsdf_sample_t bs;
+        if (!closure_sample(&C, wo, u5, u6, u7, u8, &bs)) break;
+        beta = hmul(beta, bs.weight);
+        if (k >= 3 && !(flags & FLAG_NO_RR)) {
+            double q = fmin(0.95, maxc(beta));
+            if (U(p, s, (uint32_t)k, DIM_RR, seed) >= q) { st->rr_terminated++; break; }
+            beta = scl(beta, 1.0 / q);
+        }
+        v3 wi_w = add(add(scl(tt, bs.wi.x), scl(bb, bs.wi.y)), scl(n, bs.wi.z));
+        o = offset_origin(S, x, ng, wi_w);
+        d = normalize(wi_w);
+        prev_delta = bs.is_delta;
+        prev_pdf = bs.pdf;
+    }
+    return L;
+}
+
+/* ---- multi-threaded rendering of a crop of the frame ---- */
+typedef struct {
+    const oscene* S;
+    const ocam* cam;
+    int x0, y0, cw, ch, row_step;
+    uint32_t s0, spp;
+    int max_depth;
+    uint64_t seed;
+    int flags;
+    double* sum;          /* ch * cw * 3 */
+    double* samples;      /* optional ch * cw * spp * 3 */
+    int tid, nthreads;
+    ostats st;
+} job_t;
+
+static void* worker(void* arg) {
+    job_t* J = (job_t*)arg;
+    memset(&J->st, 0, sizeof(J->st));
+    for (int j = J->tid; j * J->row_step < J->ch; j += J->nthreads) {
+        int ry = j * J->row_step;
+        for (int rx = 0; rx < J->cw; ++rx) {
+            double acc[3] = {0, 0, 0};
+            for (uint32_t i = 0; i < J->spp; ++i) {
+                v3 L = trace_path(J->S, J->cam, J->x0 + rx, J->y0 + ry, J->s0 + i, J->max_depth,
+                                  J->seed, J->flags, &J->st);
+                J->st.paths++;
+                if (!isfinite(L.x) || !isfinite(L.y) || !isfinite(L.z)) {
+                    J->st.nan_dropped++;
+                    L = splat(0.0);
+                }
+                acc[0] += L.x; acc[1] += L.y; acc[2] += L.z;
+                if (J->samples) {
+                    double* sp = &J->samples[(((size_t)ry * J->cw + rx) * J->spp + i) * 3];
+                    sp[0] = L.x; sp[1] = L.y; sp[2] = L.z;
+                }
+            }
+            double* o = &J->sum[((size_t)ry * J->cw + rx) * 3];
+            o[0] = acc[0]; o[1] = acc[1]; o[2] = acc[2];
+        }
+    }
+    return NULL;
+}
+
+/* Render samples s0 .. s0+spp-1 of the crop [x0, x0+cw) x [y0, y0+ch) of the full frame.
+ * sum_out receives the per-pixel sum of sample radiance (divide by spp for the estimate).
+ * cam = origin[3], target[3], up[3], vfov_deg; row_step > 1 renders only every row_step-th
+ * row of the crop (others stay 0); flags as for trace_path.  stats_out (5 int64): extension rays, shadow rays, NaN
+ * samples dropped, roulette terminations, paths. */
+void oracle_render(void* hs, const double* cam9, double vfov_deg, int width, int height,
+                   int x0, int y0, int cw, int ch, uint32_t s0, uint32_t spp, int max_depth,
+                   uint64_t seed, int flags, int nthreads, int row_step, double* sum_out,
+                   double* samples_out, long long* stats_out) {
+    ocam cam;
+    cam.origin = mk(cam9[0], cam9[1], cam9[2]);
+    cam.target = mk(cam9[3], cam9[4], cam9[5]);
+    cam.up = mk(cam9[6], cam9[7], cam9[8]);
+    cam.vfov_deg = vfov_deg;
+    cam.width = width;
+    cam.height = height;
+    if (nthreads < 1) nthreads = 1;
+    if (row_step < 1) row_step = 1;
+    memset(sum_out, 0, sizeof(double) * 3 * (size_t)cw * ch);
+    job_t* jobs = (job_t*)calloc((size_t)nthreads, sizeof(job_t));
+    pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+    for (int t = 0; t < nthreads; ++t) {
+        job_t* J = &jobs[t];
+        J->S = (const oscene*)hs; J->cam = &cam;
+        J->x0 = x0; J->y0 = y0; J->cw = cw; J->ch = ch; J->row_step = row_step;
+        J->s0 = s0; J->spp = spp; J->max_depth = max_depth; J->seed = seed; J->flags = flags;
+        J->sum = sum_out; J->samples = samples_out; J->tid = t; J->nthreads = nthreads;
+        if (nthreads == 1) worker(J);
+        else pthread_create(&th[t], NULL, worker, J);
+    }
+    if (nthreads > 1)
+        for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    long long tot[5] = {0, 0, 0, 0, 0};
+    for (int t = 0; t < nthreads; ++t) {
+        tot[0] += jobs[t].st.ext_rays; tot[1] += jobs[t].st.shadow_rays;
+        tot[2] += jobs[t].st.nan_dropped; tot[3] += jobs[t].st.rr_terminated;
+        tot[4] += jobs[t].st.paths;
+    }
+    if (stats_out) memcpy(stats_out, tot, sizeof(tot));
+    free(jobs);
+    free(th);
+}
+
+/* camera ray of one pixel/sample, for the ray-generation parity check */
+void oracle_camera_ray(const double* cam9, double vfov_deg, int width, int height, int px,
+                       int py, uint32_t s, uint64_t seed, double o_out[3], double d_out[3]) {
+    ocam cam;
+    cam.origin = mk(cam9[0], cam9[1], cam9[2]);
+    cam.target = mk(cam9[3], cam9[4], cam9[5]);
+    cam.up = mk(cam9[6], cam9[7], cam9[8]);
+    cam.vfov_deg = vfov_deg;
+    cam.width = width;
+    cam.height = height;
+    v3 o, d;
+    camera_ray(&cam, px, py, s, seed, &o, &d);
+    o_out[0] = o.x; o_out[1] = o.y; o_out[2] = o.z;
+    d_out[0] = d.x; d_out[1] = d.y; d_out[2] = d.z;
+}
+
+/* ---- batched forms of the BSDF entry points (n tuples, row-major arrays) ---- */
+void oracle_bsdf_eval_batch(const double* mat26, int front, int n, const double* wo,
+                            const double* wi, double* f_out, double* pdf_out) {
+    for (int i = 0; i < n; ++i)
+        oracle_bsdf_eval(mat26, front, &wo[3 * i], &wi[3 * i], &f_out[3 * i], &pdf_out[i]);
+}
+
+void oracle_bsdf_sample_batch(const double* mat26, int front, int n, const double* wo,
+                              const double* u, double* wi_out, double* weight_out,
+                              double* pdf_out, int* delta_out, int* ok_out) {
+    for (int i = 0; i < n; ++i) {
+        ok_out[i] = oracle_bsdf_sample(mat26, front, &wo[3 * i], &u[4 * i], &wi_out[3 * i],
+                                       &weight_out[3 * i], &pdf_out[i], &delta_out[i]);
+        if (!ok_out[i]) {
+            wi_out[3 * i] = wi_out[3 * i + 1] = wi_out[3 * i + 2] = 0.0;
+            weight_out[3 * i] = weight_out[3 * i + 1] = weight_out[3 * i + 2] = 0.0;
+        }
+    }
+}
+
+void oracle_uniform_batch(int n, const uint32_t* pixel, const uint32_t* sample,
+                          const uint32_t* bounce, const uint32_t* dim, uint64_t seed,
+                          double* out) {
+    for (int i = 0; i < n; ++i) out[i] = oracle_uniform(pixel[i], sample[i], bounce[i], dim[i], seed);
+}

@@ -1,0 +1,320 @@
+"""Pins of the oracle's OpenPBR subset: closed forms, Monte Carlo identities, reciprocity,
+sample/eval consistency and a chi-square fit of the sampler against its own pdf.
+
+Each check would fail on a plausible mistake in the lobe code: a dropped Fresnel or
+shadowing factor breaks the energy bound or reciprocity, a wrong Jacobian breaks the pdf
+normalisation or the chi-square fit, a wrong VNDF breaks the projected-area identity.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.stats import chi2 as chi2d
+
+import oracle
+from paper_2407_19977_gb300 import scenes
+
+RNG = np.random.default_rng(20240728)
+
+
+def _sphere_dirs(n, rng=RNG):
+    z = 1.0 - 2.0 * rng.random(n)
+    phi = 2.0 * math.pi * rng.random(n)
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def _hemi_dir(mu, phi=0.3):
+    s = math.sqrt(max(0.0, 1.0 - mu * mu))
+    return np.array([s * math.cos(phi), s * math.sin(phi), mu])
+
+
+# materials with every lobe rough enough for quadrature- and MC-based checks
+MATS = {
+    "diffuse_white": scenes.openpbr(base_color=(1, 1, 1), specular_weight=0.0),
+    "plastic": scenes.openpbr(base_color=(0.6, 0.5, 0.4), specular_roughness=0.4),
+    "metal": scenes.openpbr(base_color=(0.9, 0.7, 0.5), base_metalness=1.0, specular_roughness=0.45,
+                            specular_color=(0.8, 0.9, 1.0)),
+    "coated": scenes.openpbr(base_color=(0.8, 0.05, 0.05), specular_roughness=0.5, coat_weight=1.0,
+                             coat_roughness=0.35, coat_ior=1.5),
+    "rough_glass": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.45,
+                                  transmission_weight=1.0),
+    "mixed": scenes.openpbr(base_color=(0.7, 0.6, 0.9), base_metalness=0.3, specular_roughness=0.5,
+                            transmission_weight=0.4, transmission_color=(0.9, 0.8, 0.7),
+                            coat_weight=0.5, coat_roughness=0.4, coat_color=(0.9, 0.9, 0.6)),
+}
+WHITE = {
+    "white_plastic": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.3),
+    "white_metal": scenes.openpbr(base_color=(1, 1, 1), base_metalness=1.0, specular_roughness=0.3),
+    "white_coated": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.6, coat_weight=1.0,
+                                   coat_roughness=0.2),
+    "white_glass": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.3, transmission_weight=1.0),
+    "white_mixed": scenes.openpbr(base_color=(1, 1, 1), base_metalness=0.5, specular_roughness=0.35,
+                                  transmission_weight=0.5, coat_weight=0.5, coat_roughness=0.3),
+}
+
+
+# ------------------------------------------------------------------ closed forms
+
+def test_fresnel_closed_forms():
+    assert oracle.fresnel_dielectric(1.0, 1.5) == pytest.approx(0.04, abs=1e-15)
+    assert oracle.fresnel_dielectric(0.7, 1.0) == pytest.approx(0.0, abs=1e-15)
+    assert oracle.fresnel_dielectric(0.0, 1.5) == pytest.approx(1.0, abs=1e-15)
+    # textbook sin/tan form of Fresnel's equations (Hecht), a different formula
+    for eta in (1.33, 1.5, 2.2, 1 / 1.5):
+        for ci in np.linspace(0.05, 0.99, 17):
+            ti = math.acos(ci)
+            st = math.sin(ti) / eta
+            if st >= 1.0:
+                assert oracle.fresnel_dielectric(ci, eta) == 1.0  # total internal reflection
+                continue
+            tt = math.asin(st)
+            rs = (math.sin(ti - tt) / math.sin(ti + tt)) ** 2
+            rp = (math.tan(ti - tt) / math.tan(ti + tt)) ** 2
+            assert oracle.fresnel_dielectric(ci, eta) == pytest.approx(0.5 * (rs + rp), rel=1e-10)
+    # critical angle for eta = 1/1.5: sin(theta_c) = 1/1.5
+    cc = math.cos(math.asin(1 / 1.5))
+    assert oracle.fresnel_dielectric(cc - 1e-6, 1 / 1.5) == 1.0
+    assert oracle.fresnel_dielectric(cc + 1e-3, 1 / 1.5) < 1.0
+
+
+def test_f82_tint_closed_forms():
+    f0 = np.array([0.9, 0.6, 0.3])
+    tint = np.array([0.5, 0.8, 1.0])
+    assert np.allclose(oracle.fresnel_f82(f0, tint, 1.0), f0, atol=1e-15)
+    assert np.allclose(oracle.fresnel_f82(f0, tint, 0.0), 1.0, atol=1e-15)
+    mu = 1.0 / 7.0
+    schlick = f0 + (1 - f0) * (1 - mu) ** 5
+    assert np.allclose(oracle.fresnel_f82(f0, tint, mu), tint * schlick, atol=1e-13)
+    # unit tint reduces to Schlick's approximation
+    for m in np.linspace(0, 1, 11):
+        assert np.allclose(oracle.fresnel_f82(f0, np.ones(3), m), f0 + (1 - f0) * (1 - m) ** 5,
+                           atol=1e-13)
+
+
+@pytest.mark.parametrize("alpha", [0.02, 0.09, 0.3, 0.8])
+def test_ggx_normalisation_and_projected_area(alpha):
+    # integrate over theta with a substitution that resolves the peak: tan(theta) = alpha * tan(x)
+    n = 4000
+    x = (np.arange(n) + 0.5) / n * (math.pi / 2)
+    th = np.arctan(alpha * np.tan(x))
+    dth = alpha / np.cos(x) ** 2 / (1 + (alpha * np.tan(x)) ** 2) * (math.pi / 2 / n)
+    D = np.array([oracle.ggx_D([math.sin(t), 0.0, math.cos(t)], alpha) for t in th])
+    total = (D * np.cos(th) * np.sin(th) * dth).sum() * 2 * math.pi
+    assert total == pytest.approx(1.0, abs=2e-4)
+    # projected area: int G1(wo) max(0, wo.h) D(h) dh = cos(theta_o)
+    for mu_o in (0.95, 0.6, 0.2):
+        wo = _hemi_dir(mu_o, 0.0)
+        g1 = oracle.ggx_G1(wo, alpha)
+        nphi = 256
+        phis = (np.arange(nphi) + 0.5) / nphi * 2 * math.pi
+        acc = 0.0
+        for t, dt, d in zip(th, dth, D):
+            h = np.stack([math.sin(t) * np.cos(phis), math.sin(t) * np.sin(phis),
+                          np.full(nphi, math.cos(t))], 1)
+            oh = np.maximum(h @ wo, 0.0)
+            acc += (oh * d).sum() * math.sin(t) * dt * (2 * math.pi / nphi)
+        assert g1 * acc == pytest.approx(mu_o, rel=2e-3)
+
+
+def test_vndf_sampler_matches_visible_normal_density():
+    # E_h[h_z^2] under VNDF sampling equals the quadrature of h_z^2 G1 (wo.h) D / wo_z
+    for alpha, mu_o in ((0.3, 0.8), (0.6, 0.3)):
+        wo = _hemi_dir(mu_o, 0.4)
+        n = 60000
+        u = RNG.random((n, 2))
+        hs = np.array([oracle.ggx_vndf_sample(wo, alpha, a, b) for a, b in u])
+        assert np.all(hs[:, 2] >= 0) and np.allclose(np.linalg.norm(hs, axis=1), 1.0)
+        assert np.all(hs @ wo >= -1e-12)
+        est = (hs[:, 2] ** 2).mean()
+        err = (hs[:, 2] ** 2).std() / math.sqrt(n)
+        # quadrature
+        nt, nphi = 600, 256
+        t = (np.arange(nt) + 0.5) / nt * (math.pi / 2)
+        phis = (np.arange(nphi) + 0.5) / nphi * 2 * math.pi
+        T, P = np.meshgrid(t, phis, indexing="ij")
+        h = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1).reshape(-1, 3)
+        D = np.array([oracle.ggx_D(x, alpha) for x in h[:: 1]])
+        dens = oracle.ggx_G1(wo, alpha) * np.maximum(h @ wo, 0) * D / wo[2]
+        w = (np.sin(T).ravel()) * (math.pi / 2 / nt) * (2 * math.pi / nphi)
+        assert (dens * w).sum() == pytest.approx(1.0, abs=3e-3)
+        ref = (dens * h[:, 2] ** 2 * w).sum()
+        assert abs(est - ref) < 4 * err + 2e-3
+
+
+def test_lambert_closed_form():
+    rho = np.array([0.3, 0.6, 0.9])
+    mat = scenes.openpbr(base_color=tuple(rho), specular_weight=0.0)
+    wo = _sphere_dirs(500)
+    wo[:, 2] = np.abs(wo[:, 2]) + 1e-3
+    wo /= np.linalg.norm(wo, axis=1, keepdims=True)
+    wi = _sphere_dirs(500)
+    wi[:, 2] = np.abs(wi[:, 2]) + 1e-3
+    wi /= np.linalg.norm(wi, axis=1, keepdims=True)
+    f, pdf = oracle.bsdf_eval_batch(mat, 1, wo, wi)
+    assert np.allclose(f, rho / math.pi, rtol=1e-14)
+    assert np.allclose(pdf, wi[:, 2] / math.pi, rtol=1e-14)
+    # a below-horizon direction gets nothing
+    f, pdf = oracle.bsdf_eval_batch(mat, 1, wo, wi * np.array([1, 1, -1]))
+    assert np.all(f == 0) and np.all(pdf == 0)
+
+
+def test_delta_lobes_weights():
+    glass = scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.0, transmission_weight=1.0)
+    for mu in (0.9, 0.5, 0.15):
+        wo = _hemi_dir(mu)
+        F = oracle.fresnel_dielectric(mu, 1.5)
+        ok, wi, w, pdf, dl = oracle.bsdf_sample(glass, 1, wo, [0.5, 0.3, 0.3, F * 0.5])
+        assert ok and dl and np.allclose(wi, [-wo[0], -wo[1], wo[2]])
+        assert np.allclose(w, 1.0)  # F / P(reflect) with P(reflect) = F
+        ok, wi, w, pdf, dl = oracle.bsdf_sample(glass, 1, wo, [0.5, 0.3, 0.3, 0.5 * (1 + F)])
+        assert ok and dl and wi[2] < 0
+        assert np.allclose(w, 1.0 / 1.5 ** 2)  # radiance scaling 1/eta^2
+        # Snell's law on the refracted direction
+        s_t = math.sqrt(wi[0] ** 2 + wi[1] ** 2)
+        assert s_t == pytest.approx(math.sqrt(1 - mu * mu) / 1.5, rel=1e-12)
+    # a perfect mirror conductor (F0 = 1) has reflectance 1 at every angle
+    mirror = scenes.openpbr(base_color=(1, 1, 1), base_metalness=1.0, specular_roughness=0.0)
+    for mu in (0.95, 0.3, 0.02):
+        ok, wi, w, pdf, dl = oracle.bsdf_sample(mirror, 1, _hemi_dir(mu), [0.2, 0.5, 0.5, 0.5])
+        assert ok and dl and np.allclose(w, 1.0)
+    # total internal reflection from inside the glass
+    cc = math.cos(math.asin(1 / 1.5))
+    wo = _hemi_dir(cc * 0.5)
+    for u8 in (0.1, 0.9):
+        ok, wi, w, pdf, dl = oracle.bsdf_sample(glass, 0, wo, [0.5, 0.3, 0.3, u8])
+        assert ok and wi[2] > 0 and np.allclose(w, 1.0)
+
+
+# ------------------------------------------------------------------ Monte Carlo identities
+
+@pytest.mark.parametrize("name", sorted(MATS))
+def test_sample_eval_consistency(name):
+    mat = MATS[name]
+    for front in (1, 0):
+        for mu in (0.9, 0.4, 0.08):
+            n = 3000
+            wo = np.tile(_hemi_dir(mu, 1.1), (n, 1))
+            u = RNG.random((n, 4))
+            ok, wi, w, pdf, dl = oracle.bsdf_sample_batch(mat, front, wo, u)
+            sel = ok & ~dl
+            assert sel.sum() > 0
+            f, pdf2 = oracle.bsdf_eval_batch(mat, front, wo[sel], wi[sel])
+            assert np.allclose(pdf[sel], pdf2, rtol=1e-10)
+            assert np.allclose(w[sel], f * np.abs(wi[sel, 2:3]) / pdf2[:, None], rtol=1e-9)
+            assert np.allclose(np.linalg.norm(wi[sel], axis=1), 1.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("name", sorted(MATS))
+def test_pdf_integrates_to_valid_sample_fraction(name):
+    mat = MATS[name]
+    for front in (1, 0):
+        for mu in (0.85, 0.3):
+            wo = _hemi_dir(mu, 0.7)
+            n = 200_000
+            dirs = _sphere_dirs(n)
+            _, pdf = oracle.bsdf_eval_batch(mat, front, np.tile(wo, (n, 1)), dirs)
+            vals = pdf * 4 * math.pi
+            integral, err_i = vals.mean(), vals.std() / math.sqrt(n)
+            m = 100_000
+            ok, wi, w, p, dl = oracle.bsdf_sample_batch(mat, front, np.tile(wo, (m, 1)),
+                                                        RNG.random((m, 4)))
+            frac = (ok & ~dl).mean()
+            err_f = math.sqrt(frac * (1 - frac) / m)
+            assert integral <= 1.0 + 4 * err_i
+            assert abs(integral - frac) < 4.5 * math.hypot(err_i, err_f) + 1e-3, (integral, frac)
+
+
+@pytest.mark.parametrize("name", sorted(WHITE))
+def test_albedo_at_most_one(name):
+    mat = WHITE[name]
+    for front in (1, 0):
+        for mu in (0.98, 0.7, 0.4, 0.15, 0.03):
+            n = 40_000
+            ok, wi, w, p, dl = oracle.bsdf_sample_batch(mat, front, np.tile(_hemi_dir(mu), (n, 1)),
+                                                        RNG.random((n, 4)))
+            if front == 0 and "glass" in name or "mixed" in name and front == 0:
+                # transmissive interfaces seen from inside: radiance scaling by eta^2 < 1 side
+                w = w * np.where(wi[:, 2:3] < 0, 1.0 / 1.5 ** 2, 1.0)
+            alb = w.mean(0)
+            err = w.std(0) / math.sqrt(n)
+            assert np.all(alb <= 1.0 + 4 * err + 1e-3), (mu, front, alb)
+            assert np.all(alb > 0.0)
+
+
+def test_white_lambert_albedo_exactly_one():
+    mat = scenes.openpbr(base_color=(1, 1, 1), specular_weight=0.0)
+    n = 2000
+    ok, wi, w, p, dl = oracle.bsdf_sample_batch(mat, 1, np.tile(_hemi_dir(0.4), (n, 1)),
+                                                RNG.random((n, 4)))
+    assert ok.all() and np.allclose(w, 1.0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("name", sorted(MATS))
+def test_reciprocity(name):
+    mat = MATS[name]
+    n = 400
+    a = _sphere_dirs(n)
+    b = _sphere_dirs(n)
+    a[:, 2] = np.abs(a[:, 2]) + 1e-3
+    a /= np.linalg.norm(a, axis=1, keepdims=True)
+    # reflection: f(a, b) = f(b, a) with both directions above the surface
+    b_up = b.copy()
+    b_up[:, 2] = np.abs(b_up[:, 2]) + 1e-3
+    b_up /= np.linalg.norm(b_up, axis=1, keepdims=True)
+    for front in (1, 0):
+        f1, _ = oracle.bsdf_eval_batch(mat, front, a, b_up)
+        f2, _ = oracle.bsdf_eval_batch(mat, front, b_up, a)
+        assert np.allclose(f1, f2, rtol=1e-12, atol=1e-300)
+    # transmission: f(a -> b)/eta_a^2 = f(b -> a)/eta_b^2, evaluated from the other side
+    b_dn = b_up * np.array([1, 1, -1])
+    flip = np.array([1, 1, -1])
+    f_fwd, _ = oracle.bsdf_eval_batch(mat, 1, a, b_dn)
+    f_rev, _ = oracle.bsdf_eval_batch(mat, 0, b_dn * flip, a * flip)
+    if mat[12] > 0:
+        assert np.any(f_fwd > 0)
+    assert np.allclose(f_fwd, f_rev / 1.5 ** 2, rtol=1e-10, atol=1e-300)
+
+
+@pytest.mark.parametrize("name", ["plastic", "metal", "coated", "rough_glass", "mixed"])
+def test_sampler_chi_square(name):
+    mat = MATS[name]
+    mu = 0.55
+    wo = _hemi_dir(mu, 0.9)
+    nz, nphi = 20, 24
+    n = 150_000
+    ok, wi, w, p, dl = oracle.bsdf_sample_batch(mat, 1, np.tile(wo, (n, 1)), RNG.random((n, 4)))
+    assert not dl.any()
+    z = wi[ok, 2]
+    phi = np.mod(np.arctan2(wi[ok, 1], wi[ok, 0]), 2 * math.pi)
+    obs, _, _ = np.histogram2d(z, phi, bins=[nz, nphi], range=[[-1, 1], [0, 2 * math.pi]])
+    # expected mass per bin: midpoint quadrature of the pdf in (z, phi), 8 x 8 per bin
+    sub = 8
+    zs = -1 + (np.arange(nz * sub) + 0.5) * (2.0 / (nz * sub))
+    ps = (np.arange(nphi * sub) + 0.5) * (2 * math.pi / (nphi * sub))
+    Z, P = np.meshgrid(zs, ps, indexing="ij")
+    R = np.sqrt(1 - Z * Z)
+    dirs = np.stack([R * np.cos(P), R * np.sin(P), Z], -1).reshape(-1, 3)
+    _, pdf = oracle.bsdf_eval_batch(mat, 1, np.tile(wo, (dirs.shape[0], 1)), dirs)
+    cell = (2.0 / (nz * sub)) * (2 * math.pi / (nphi * sub))
+    exp = (pdf.reshape(nz * sub, nphi * sub) * cell).reshape(nz, sub, nphi, sub).sum((1, 3)) * n
+    invalid_obs = n - ok.sum()
+    invalid_exp = n - exp.sum()
+    o = np.append(obs.ravel(), invalid_obs)
+    e = np.append(exp.ravel(), max(invalid_exp, 1e-9))
+    keep = e >= 5
+    o_m = np.append(o[keep], o[~keep].sum())
+    e_m = np.append(e[keep], e[~keep].sum())
+    if e_m[-1] < 5:
+        o_m, e_m = o_m[:-1], e_m[:-1]
+    stat = ((o_m - e_m) ** 2 / e_m).sum()
+    dof = len(o_m) - 1
+    assert chi2d.sf(stat, dof) > 1e-5, (stat, dof)
+
+
+def test_lobe_probabilities_form_a_distribution():
+    for name, mat in {**MATS, **WHITE}.items():
+        for front in (1, 0):
+            for mu in (0.9, 0.3, 0.01):
+                p = oracle.lobe_probs(mat, front, mu)
+                assert np.all(p >= 0) and p.sum() == pytest.approx(1.0, abs=1e-12), name

@@ -1,0 +1,365 @@
+"""Benchmark of the path tracer's hot path on one node.
+
+A step is one progressive frame of the whole hot path -- camera rays, closest hit through
+the compressed wide BVH, material sort, OpenPBR shading with next-event estimation and
+Russian roulette, shadow rays, Kahan accumulation -- for the synthetic CAD pushbutton
+(~210k triangles, analytic-sky environment + one quad light) at 1920x1080, one sample per
+pixel, max depth 8.  The BVH is built once before the timed region (its build time is
+reported as `bvh_build_ms`).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The metric is traced rays per second (camera + BSDF-sampled extension rays + shadow rays);
+spp/s at 1080p is reported beside it.  With --impl reference the CPU oracle renders bounded
+samples of the same frame on the host cores (the comparison arm of this benchmark).
+Multi-GPU runs are independent replicas (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "pushbutton": "synthetic CAD pushbutton, 209,600 triangles + 2 light triangles, 1920x1080, 1 spp/step, "
+                  "max depth 8, analytic sky 512x256 + 1 quad light",
+}
+NODE_BYTES = 80      # compressed 8-wide BVH node
+TRI_BYTES = 48       # triangle record
+RAY_BYTES = 32       # ray in (origin + direction float4 pair)
+HIT_BYTES = 16       # hit record out
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pushbutton", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="wavefront", choices=["auto", "wavefront", "megakernel"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    return ap.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_2407_19977_gb300/csrc/pt_device.cuh", "paper_2407_19977_gb300/csrc/pt_render.cu"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
+    current kernel source (the summary records the source hash); else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != _source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _make_workload(name):
+    from paper_2407_19977_gb300 import scenes
+    if name == "pushbutton":
+        return scenes.pushbutton()
+    raise ValueError(name)
+
+
+def cpu_baseline(sc, target_s: float, seed: int = 0):
+    """The oracle as it stands, on all host cores, over a bounded sample of the frame:
+    every `row_step`-th row at one sample per pixel, sized to about `target_s` seconds."""
+    import oracle
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    osc = oracle.OracleScene(sc)
+    setup = time.perf_counter() - t0
+    # calibration on every 64th row, then scale the sample to the target time
+    t0 = time.perf_counter()
+    _, _, st = osc.render(spp=1, seed=seed, row_step=64, threads=threads)
+    cal = max(time.perf_counter() - t0, 1e-3)
+    rows_cal = len(range(0, sc.camera.height, 64))
+    rows = max(1, min(sc.camera.height, int(rows_cal * target_s / cal)))
+    row_step = max(1, sc.camera.height // rows)
+    spp = 1
+    if row_step == 1:
+        spp = max(1, int(round(target_s / (cal * sc.camera.height / rows_cal))))
+    t0 = time.perf_counter()
+    _, _, st = osc.render(spp=spp, seed=seed, s0=1000, row_step=row_step, threads=threads)
+    dt = time.perf_counter() - t0
+    rays = st["ext_rays"] + st["shadow_rays"]
+    px = st["paths"] / spp
+    return {
+        "value": rays / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+        "sample": f"every {row_step}th row of the 1920x1080 frame ({int(px)} pixels) at {spp} spp, "
+                  f"{rays} rays in {dt:.2f} s; oracle BVH setup {setup:.2f} s",
+        "spp_per_s_1080p": st["paths"] / dt / (sc.camera.width * sc.camera.height),
+    }
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the CPU oracle on this host, same workload, metric and unit."""
+    if rank != 0:
+        return
+    sc = _make_workload(args.workload)
+    import oracle
+    threads = os.cpu_count() or 1
+    osc = oracle.OracleScene(sc)
+    # each step renders a bounded slice: every 32nd row of the frame at 1 spp
+    row_step = 32
+    for w in range(args.warmup):
+        osc.render(spp=1, seed=0, s0=w, row_step=row_step, threads=threads)
+    t0 = time.perf_counter()
+    rays = paths = 0
+    for k in range(args.steps):
+        _, _, st = osc.render(spp=1, seed=0, s0=100 + k, row_step=row_step, threads=threads)
+        rays += st["ext_rays"] + st["shadow_rays"]
+        paths += st["paths"]
+    dt = time.perf_counter() - t0
+    value = rays / dt / 1e6
+    out = {
+        "metric": "Mrays/s at 1080p (pushbutton)", "value": value, "unit": "Mrays/s", "impl": "reference",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "sample": f"every {row_step}th row, 1 spp per step"},
+        "spp_per_s_1080p": paths / dt / (sc.camera.width * sc.camera.height),
+        "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+                         "sample": f"every {row_step}th row of the 1080p frame at 1 spp per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2407_19977_gb300 import api
+    from paper_2407_19977_gb300 import native as N
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    sc = _make_workload(args.workload)
+    cam = sc.camera
+    W, H = cam.width, cam.height
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    scene = api.Scene(sc, build=False)
+    torch.cuda.synchronize()
+    upload_ms = (time.perf_counter() - t0) * 1e3
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    scene.build()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    bvh_ms = ev0.elapsed_time(ev1)
+    mode = {"auto": N.PT_MODE_AUTO, "wavefront": N.PT_MODE_WAVEFRONT, "megakernel": N.PT_MODE_MEGAKERNEL}[args.mode]
+    acc = api.Accum(W, H)
+    seed = 1000 * rank
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    for _ in range(args.warmup):
+        scene.render(1, seed=seed, accum=acc, mode=mode)
+    torch.cuda.synchronize()
+    # untimed instrumented frame at the first timed sample index: node visits and triangle
+    # tests per ray give the traversal's algorithmic bytes
+    s_first = acc.spp_done
+    probe = api.Accum(W, H)
+    probe.c.spp_done = s_first
+    before = scene.stats()
+    scene.render(1, seed=seed, accum=probe, mode=mode, flags=N.PT_FLAG_COUNT)
+    after = scene.stats()
+    cnt = {k: after[k] - before[k] for k in ("ext_rays", "shadow_rays", "trace_nodes", "trace_tris",
+                                             "shadow_nodes", "shadow_tris")}
+    trace_bytes_step = (cnt["trace_nodes"] * NODE_BYTES + cnt["trace_tris"] * TRI_BYTES +
+                        cnt["ext_rays"] * (RAY_BYTES + HIT_BYTES))
+    # timed region
+    kernel_ms = (N.f32 * 6)()
+    kernel_launches = (N.u32 * 6)()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    st_before = scene.stats()
+    launches_before = api.launch_count()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.fill_(float(k))  # L2 flush between steps, outside the timed events
+            starts[k].record(stream)
+            scene.render(1, seed=seed, accum=acc, mode=mode, kernel_ms=kernel_ms, kernel_launches=kernel_launches)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    launches = api.launch_count() - launches_before
+    st_after = scene.stats()
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    rays = (st_after["ext_rays"] - st_before["ext_rays"]) + (st_after["shadow_rays"] - st_before["shadow_rays"])
+    t_max = dev_ms
+    rays_all = rays
+    if world > 1:
+        tt = torch.tensor([dev_ms, float(rays)], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_max, rays_all = float(mx[0]), float(tt[1])
+    value = rays_all / (t_max * 1e-3) / 1e6
+    spp_s = world * args.steps / (t_max * 1e-3)
+    # end to end through the public API: the step's inputs cross host->device (the camera and
+    # seed, marshalled into the launch) and the frame estimate comes back to pinned host memory
+    host_img = torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(3, args.steps // 2)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e_before = scene.stats()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        cam_k = type(cam)(**cam.__dict__)
+        scene.render(1, seed=seed, accum=acc, mode=mode, camera=cam_k)
+        host_img.copy_(acc.sum, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    e_after = scene.stats()
+    e2e_rays = (e_after["ext_rays"] - e_before["ext_rays"]) + (e_after["shadow_rays"] - e_before["shadow_rays"])
+    e2e_val = e2e_rays / e2e_s / 1e6 * world
+    # roofline of the dominant kernel (closest-hit traversal)
+    kms = {n: float(kernel_ms[i]) / args.steps for i, n in enumerate(N.KERNEL_KINDS)}
+    kl = {n: int(kernel_launches[i]) // args.steps for i, n in enumerate(N.KERNEL_KINDS)}
+    peaks, peak_src = _peaks()
+    trace_ms = kms["trace"]
+    achieved_gbs = trace_bytes_step / (trace_ms * 1e-3) / 1e9 if trace_ms > 0 else None
+    traffic = _recorded_traffic("trace")
+    result = {
+        "metric": "Mrays/s at 1080p (pushbutton)",
+        "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "mode": args.mode, "l2": "flushed between steps",
+                   "parallelism": f"replicas x{world}"},
+        "spp_per_s_1080p": spp_s,
+        "rays_per_step": rays / args.steps,
+        "bvh_build_ms": bvh_ms, "upload_ms": upload_ms,
+        "kernel_ms_per_step": kms, "kernel_launches_per_step": kl,
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_val, "unit": "Mrays/s", "h2d_bytes_per_step": 48 + 8,
+                "d2h_bytes_per_step": W * H * 3 * 4},
+        "roofline": {"bound": "hbm", "kernel": "k_wf_trace (closest hit)",
+                     "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved_gbs / peaks["hbm_gbs"] if achieved_gbs else None,
+                     "traffic": traffic, "peak_source": peak_src,
+                     "algorithmic_bytes_per_step": trace_bytes_step,
+                     "per_ray": {"nodes": cnt["trace_nodes"] / max(cnt["ext_rays"], 1),
+                                 "tris": cnt["trace_tris"] / max(cnt["ext_rays"], 1)}},
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,324 @@
+/*
+ * pt.h -- C-ABI of the GB300 path tracer (CUDA, sm_103a).
+ *
+ * The library computes the Monte Carlo estimate of the rendering equation
+ *   I(x, x') = g(x, x') [ eps(x, x') + int_S p(x, x', x'') I(x', x'') dx'' ]
+ * ("Physically-based Path Tracer using WebGPU and OpenPBR", Sec. 1.1) by backward path
+ * tracing from a perspective camera with per-sample jitter (Sec. 5.1.2), closest-hit
+ * search through a BVH over triangle meshes (Sec. 5.1.1), OpenPBR shading with importance
+ * sampling and Russian roulette at every hit (Sec. 4, Sec. 5.1.3), and progressive
+ * per-pixel averaging (Sec. 5.1.3, Sec. 5.1.4).  Scene setup happens once, sampling runs
+ * repeatedly on the GPU (Sec. 5.1, Fig. "path tracer pipeline").
+ *
+ * Conventions for every call:
+ *  - Returns a pt_status; nothing throws or aborts across the ABI.  pt_last_error() gives
+ *    a human-readable detail for the calling thread's most recent failure.
+ *  - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued asynchronously on that stream; device-side failures (for example an
+ *    exhausted spin budget) are reported by the next call that synchronises
+ *    (pt_get_stats, pt_scene_sync) as PT_ERR_TIMEOUT / PT_ERR_QUEUE_OVERFLOW.
+ *  - Pointers documented as "device" must be device memory of the current CUDA device;
+ *    "host" pointers are ordinary host memory.  The library copies every scene input at
+ *    create time: the caller may free its arrays when pt_scene_create returns.
+ *  - Caller-owned output buffers (accumulators, hit arrays, NRC buffers) stay owned by
+ *    the caller and must outlive the enqueued work.
+ *  - Coordinates are right-handed, +y up; triangles wind counter-clockwise seen from their
+ *    front side; the geometric normal is normalize((v1 - v0) x (v2 - v0)).
+ */
+#ifndef PT_H_
+#define PT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PT_OK = 0,
+    PT_ERR_INVALID_ARG = 1,     /* bad pointer, size, index, NaN/Inf or parameter range */
+    PT_ERR_OOM = 2,             /* device or host allocation failed */
+    PT_ERR_CUDA = 3,            /* a CUDA runtime call failed (detail in pt_last_error) */
+    PT_ERR_NOT_BUILT = 4,       /* pt_render before pt_bvh_build */
+    PT_ERR_TIMEOUT = 5,         /* a bounded device-side wait ran out of budget */
+    PT_ERR_QUEUE_OVERFLOW = 6,  /* a device work queue or traversal stack overflowed */
+    PT_ERR_UNSUPPORTED = 7      /* option value not supported by this build */
+} pt_status;
+
+typedef struct pt_scene pt_scene;   /* opaque, library-owned */
+typedef struct pt_nrc pt_nrc;       /* opaque, library-owned */
+
+/* OpenPBR surface parameters (Sec. 4; the paper's material model).  26 floats, in this
+ * order; the Python generators and the oracle use the same order.
+ * Valid ranges (checked by pt_scene_create): weights, colors, roughnesses and metalness
+ * in [0, 1]; specular_ior and coat_ior in (1, 3]; emission_luminance >= 0.
+ * base_diffuse_roughness must be 0 (Lambertian base). */
+typedef struct {
+    float base_weight;
+    float base_color[3];
+    float base_metalness;
+    float base_diffuse_roughness;
+    float specular_weight;
+    float specular_color[3];
+    float specular_roughness;
+    float specular_ior;
+    float transmission_weight;
+    float transmission_color[3];
+    float coat_weight;
+    float coat_color[3];
+    float coat_roughness;
+    float coat_ior;
+    float emission_luminance;
+    float emission_color[3];
+} pt_openpbr;
+
+/* Parallelogram area light p0 + a e1 + b e2, (a, b) in [0,1]^2, radiance L emitted on the
+ * side of e1 x e2 (both sides if two_sided).  The library also makes it geometry: two
+ * black triangles appended after the mesh's triangles, light l -> triangle ids
+ * n_triangles + 2l and n_triangles + 2l + 1. */
+typedef struct {
+    float p0[3];
+    float e1[3];
+    float e2[3];
+    float radiance[3];
+    int32_t two_sided;
+} pt_quad_light;
+
+/* Pinhole camera: vertical field of view vfov_deg; the full frame is width x height
+ * pixels, pixel (x, y) with y growing downwards; pixel id p = y * width + x keys the
+ * random numbers (Sec. 5.1.2: adjacent pixels run concurrently, each sample jittered). */
+typedef struct {
+    float origin[3];
+    float target[3];
+    float up[3];
+    float vfov_deg;
+    uint32_t width;
+    uint32_t height;
+} pt_camera;
+
+/* Progressive accumulator (Sec. 5.1.4), caller-owned DEVICE buffers of width*height*3
+ * floats each, row-major RGB over the rendered window (the whole frame or a crop).
+ * sum/comp are a Kahan-compensated running sum of the sample radiance; the estimate is
+ * sum / spp_done.  pt_render adds samples spp_done .. spp_done+spp-1 and advances
+ * spp_done, so calling it repeatedly equals one long call (same random numbers). */
+typedef struct {
+    float* sum;
+    float* comp;
+    uint64_t spp_done;
+    uint32_t width;
+    uint32_t height;
+} pt_accum;
+
+enum {
+    PT_FLAG_NO_NEE = 1u,        /* BSDF sampling only; every emission hit gets weight 1 */
+    PT_FLAG_NO_RR = 2u,         /* no Russian roulette */
+    PT_FLAG_COUNT = 4u          /* wavefront: count BVH node visits and triangle tests (slower) */
+};
+
+/* wavefront kernel kinds, indices of pt_render_opts.kernel_ms */
+enum { PT_K_RAYGEN = 0, PT_K_TRACE = 1, PT_K_SORT = 2, PT_K_SHADE = 3, PT_K_SHADOW = 4, PT_K_ACCUM = 5,
+       PT_K_KINDS = 6 };
+
+enum {
+    PT_MODE_AUTO = 0,           /* pick per the autotuned table (pt_autotune) */
+    PT_MODE_WAVEFRONT = 1,      /* queue-driven kernels per bounce (raygen/trace/sort/shade/shadow) */
+    PT_MODE_MEGAKERNEL = 2      /* persistent kernel, one path per thread, work-queue fetch */
+};
+
+typedef struct {
+    uint32_t crop_x0, crop_y0;  /* window origin in the full frame; size = accum->width/height */
+    uint32_t flags;             /* PT_FLAG_* */
+    uint32_t mode;              /* PT_MODE_* */
+    uint32_t wave_paths;        /* wavefront: paths per wave (0 = automatic) */
+    int32_t sort_by_material;   /* wavefront: -1 automatic, 0 off, 1 on */
+    uint32_t block_size;        /* threads per block (0 = automatic) */
+    float* sample_out;          /* optional DEVICE buffer, height*width*spp*3 floats: the
+                                   radiance of each sample (pixel-major, then sample) */
+    pt_nrc* nrc;                /* optional neural radiance cache: paths end at their 2nd
+                                   diffuse-ish vertex and add beta * cache(vertex) */
+    uint32_t nrc_train;         /* with nrc: collect training suffixes and train this frame */
+    float* kernel_ms;           /* optional HOST float[PT_K_KINDS]: wavefront mode adds the
+                                   CUDA-event time of each kernel kind (synchronises the
+                                   stream at the end of the call) */
+    uint32_t* kernel_launches;  /* optional HOST uint32[PT_K_KINDS]: launches per kind */
+} pt_render_opts;
+
+typedef struct {
+    uint32_t leaf_size;         /* max triangles per leaf, 1..4 (0 = 4) */
+} pt_bvh_opts;
+
+typedef struct {
+    uint64_t ext_rays;          /* extension rays traced (camera + BSDF-sampled) */
+    uint64_t shadow_rays;       /* shadow rays traced */
+    uint64_t paths;             /* paths started */
+    uint64_t nan_dropped;       /* samples with NaN/Inf radiance, discarded */
+    uint64_t rr_terminated;     /* paths ended by Russian roulette */
+    uint64_t nrc_queries;       /* paths ended by the radiance cache */
+    uint64_t kernel_launches;   /* kernels this library launched for this scene */
+    uint64_t bvh_nodes;         /* wide BVH nodes */
+    uint64_t bvh_depth;         /* wide BVH depth */
+    uint64_t n_triangles;       /* mesh + light triangles */
+    uint64_t trace_nodes;       /* PT_FLAG_COUNT: wide nodes visited by closest-hit rays */
+    uint64_t trace_tris;        /* PT_FLAG_COUNT: triangle tests of closest-hit rays */
+    uint64_t shadow_nodes;      /* PT_FLAG_COUNT: wide nodes visited by shadow rays */
+    uint64_t shadow_tris;       /* PT_FLAG_COUNT: triangle tests of shadow rays */
+    uint32_t error_flags;       /* sticky device error bits (1 = stack overflow, 2 = timeout) */
+    uint32_t reserved;
+} pt_stats;
+
+/* Scene setup (Sec. 5.1.1 "CPU setup": load geometry and materials).
+ *  vertices      float[n_vertices*3]      positions
+ *  indices       uint32[n_triangles*3]    vertex indices, each < n_vertices
+ *  material_ids  uint32[n_triangles]      each < n_materials
+ *  materials     pt_openpbr[n_materials]  (host memory always)
+ *  lights        pt_quad_light[n_lights]  (host memory always; may be NULL if 0)
+ *  env_rgb       float[env_h*env_w*3]     lat-long radiance, row 0 looks along +y;
+ *                u = 0.5 + atan2(dx, -dz)/(2 pi), v = acos(dy)/pi; NULL = black
+ *  inputs_on_device: 1 if vertices/indices/material_ids/env_rgb are device pointers.
+ * Errors: PT_ERR_INVALID_ARG (out-of-range index or parameter, NaN/Inf vertex or env,
+ * zero-sized arrays with non-NULL requirements), PT_ERR_OOM, PT_ERR_CUDA. */
+pt_status pt_scene_create(const float* vertices, uint32_t n_vertices, const uint32_t* indices,
+                          uint32_t n_triangles, const uint32_t* material_ids,
+                          const pt_openpbr* materials, uint32_t n_materials,
+                          const pt_quad_light* lights, uint32_t n_lights, const float* env_rgb,
+                          uint32_t env_w, uint32_t env_h, int inputs_on_device,
+                          void* cuda_stream, pt_scene** out);
+
+/* Device BVH build (Sec. 5.1.1: AABB hierarchy, O(log n) intersection): 64-bit Morton codes,
+ * radix sort, linear BVH, collapse to a compressed 8-wide BVH with 8-bit child boxes.
+ * Enqueued on cuda_stream; synchronises that stream once per wide-tree level.  Also
+ * builds the environment sampling tables. */
+pt_status pt_bvh_build(pt_scene* scene, const pt_bvh_opts* opts, void* cuda_stream);
+
+/* Render spp samples per pixel of the window accum->width x accum->height at
+ * (opts->crop_x0, opts->crop_y0) of the camera's frame (Sec. 5.1.2-5.1.4): camera ray,
+ * closest hit, emission with MIS, next-event estimation to quads and the environment,
+ * OpenPBR BSDF sample, Russian roulette, max_depth BSDF bounces, Kahan accumulation.
+ * seed keys the Philox4x32-10 counter (pixel, sample, bounce, dim/4).
+ * Errors: PT_ERR_NOT_BUILT, PT_ERR_INVALID_ARG (window outside the frame, NULL accum),
+ * PT_ERR_OOM (work buffers), PT_ERR_CUDA. */
+pt_status pt_render(pt_scene* scene, const pt_camera* camera, uint32_t spp, uint32_t max_depth,
+                    uint64_t seed, pt_accum* accum, const pt_render_opts* opts,
+                    void* cuda_stream);
+
+/* One job of a batched launch: a built scene, its camera, its accumulator (whole frame). */
+typedef struct {
+    pt_scene* scene;
+    pt_camera camera;
+    uint32_t spp;
+    uint32_t max_depth;
+    uint64_t seed;
+    pt_accum* accum;
+} pt_job;
+
+typedef struct {
+    uint32_t tile_pixels;       /* pixels per work item (0 = automatic) */
+    uint32_t spp_chunk;         /* samples per work item (0 = automatic) */
+    uint32_t block_size;        /* threads per block (0 = automatic) */
+    uint32_t blocks_per_sm;     /* resident blocks per SM of the persistent grid (0 = auto) */
+    uint32_t use_graph;         /* 1: capture the launch into a CUDA graph and replay it */
+    uint64_t spin_budget;       /* bounded device waits: iterations before PT_ERR_TIMEOUT */
+} pt_batch_opts;
+
+/* Batched rendering of many scenes of uneven size in ONE persistent launch: blocks pop
+ * (job, tile, sample-chunk) items from a shared work queue in device memory until it is
+ * empty.  Each job's image equals rendering it alone with pt_render.  */
+pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const pt_batch_opts* opts,
+                          void* cuda_stream);
+
+/* Closest hit of n rays through the scene's BVH (Sec. 5.1.3 "checks for intersections using
+ * the BVH").  rays: DEVICE float[n*8] = origin[3], dir[3], tmax, unused.  Outputs (DEVICE):
+ * hit_tri uint32[n] triangle id (mesh ids, then light triangles; 0xFFFFFFFF on a miss),
+ * hit_t float[n], hit_uv float[n*2] barycentric weights of v1 and v2.  Ties at equal t go
+ * to the lower triangle id.  flags bit 0 (PT_TRACE_ANY): occlusion only (hit_tri = 0 or ~0);
+ * bit 1 (PT_TRACE_COUNT): hit_uv receives the ray's wide-node visits and triangle tests. */
+enum { PT_TRACE_ANY = 1, PT_TRACE_COUNT = 2 };
+pt_status pt_trace(pt_scene* scene, const float* rays, uint32_t n, int flags,
+                   uint32_t* hit_tri, float* hit_t, float* hit_uv, void* cuda_stream);
+
+/* OpenPBR BSDF in the local shading frame (normal = +z, wo.z > 0) for n tuples (Sec. 4,
+ * Sec. 5.1.3 importance sampling).  All arrays DEVICE.  materials pt_openpbr[n],
+ * front int32[n] (1 = the side the winding faces), wo/wi float[n*3].
+ * eval: f_out float[n*3] (non-delta lobes), pdf_out float[n] (mixture sampling pdf).
+ * sample: u float[n*4] = (lobe, dir1, dir2, refract) uniforms; outputs wi float[n*3],
+ * weight float[n*3] = f|cos|/pdf, pdf float[n], flags uint32[n] (1 = valid, 2 = delta). */
+pt_status pt_bsdf_eval(const pt_openpbr* materials, const int32_t* front, const float* wo,
+                       const float* wi, uint32_t n, float* f_out, float* pdf_out,
+                       void* cuda_stream);
+pt_status pt_bsdf_sample(const pt_openpbr* materials, const int32_t* front, const float* wo,
+                         const float* u, uint32_t n, float* wi_out, float* weight_out,
+                         float* pdf_out, uint32_t* flags_out, void* cuda_stream);
+
+/* Camera rays of n (pixel x, pixel y, sample) triples (Sec. 5.1.2).  pixels: DEVICE
+ * uint32[n*3]; out: DEVICE float[n*6] = origin[3], dir[3]. */
+pt_status pt_camera_rays(const pt_camera* camera, uint64_t seed, const uint32_t* pixels,
+                         uint32_t n, float* out, void* cuda_stream);
+
+/* Philox4x32-10 uniforms for n (pixel, sample, bounce, dim) keys: keys DEVICE uint32[n*4],
+ * out DEVICE float[n]. */
+pt_status pt_uniforms(uint64_t seed, const uint32_t* keys, uint32_t n, float* out,
+                      void* cuda_stream);
+
+/* Environment sampling table queries (DEVICE arrays): sample n directions from uniforms
+ * u float[n*2] -> dir float[n*3], pdf float[n] (solid angle); or evaluate the pdf of
+ * n directions. */
+pt_status pt_env_sample(pt_scene* scene, const float* u, uint32_t n, float* dir_out,
+                        float* pdf_out, void* cuda_stream);
+pt_status pt_env_pdf(pt_scene* scene, const float* dirs, uint32_t n, float* pdf_out,
+                     void* cuda_stream);
+
+/* Copy the built BVH to HOST memory for inspection (Sec. 5.1.1 structure checks): nodes
+ * uint32[5*4*n_nodes] in the 80-byte node layout, triangles float[12*n_tris] in leaf order
+ * (w of the first float4 = original triangle id bits, of the second = material code).
+ * Pass NULL buffers to query n_nodes / n_tris only.  Synchronises the stream. */
+pt_status pt_bvh_export(pt_scene* scene, uint32_t* nodes_out, float* tris_out, uint32_t* n_nodes,
+                        uint32_t* n_tris, void* cuda_stream);
+
+/* Statistics and sticky device error bits; synchronises the scene's last stream. */
+pt_status pt_get_stats(pt_scene* scene, pt_stats* out);
+pt_status pt_scene_sync(pt_scene* scene);
+void pt_scene_destroy(pt_scene* scene);
+
+/* Kernels launched by this library in this process (all scenes). */
+uint64_t pt_launch_count(void);
+
+/* ---------------- Neural radiance cache (the paper's future work, Sec. 6.1) ----------------
+ * Multiresolution hash-grid encoding of the vertex position (levels x features per entry,
+ * 2^log2_table entries per level) concatenated with direction, normal and roughness, fed
+ * to a 64-wide MLP with n_hidden hidden layers (ReLU), output RGB.  Weights and grid are
+ * trained online with Adam on a relative L2 loss by the library's own forward/backward
+ * kernels; the MLP runs on the tensor cores (FP16 operands, FP32 accumulation). */
+typedef struct {
+    uint32_t n_levels;          /* hash-grid levels (16) */
+    uint32_t log2_table;        /* log2 entries per level (19) */
+    uint32_t base_resolution;   /* coarsest grid resolution (16) */
+    float per_level_scale;      /* resolution growth per level (0 = from 2048 finest) */
+    uint32_t n_hidden;          /* hidden layers (4) */
+    float learning_rate;        /* Adam step size (1e-2 grid and MLP) */
+    uint32_t batch;             /* training samples per step (16384) */
+    uint64_t seed;              /* weight initialisation seed */
+    float scene_min[3];         /* position normalisation box */
+    float scene_max[3];
+} pt_nrc_opts;
+
+/* Query layout for pt_nrc_infer / training samples (DEVICE arrays of float[n*16]):
+ * pos[3], dir[3], normal[3], roughness, target_rgb[3] (training only), pad[3]. */
+pt_status pt_nrc_create(const pt_nrc_opts* opts, void* cuda_stream, pt_nrc** out);
+pt_status pt_nrc_train(pt_nrc* nrc, const float* samples, uint32_t n, void* cuda_stream);
+pt_status pt_nrc_infer(pt_nrc* nrc, const float* queries, uint32_t n, float* out_rgb,
+                       void* cuda_stream);
+/* Parameter access for tests and checkpoints: FP32 master copies (DEVICE float arrays).
+ * which = 0: MLP weights (layer-major, each [out][in]), 1: hash-grid table. */
+pt_status pt_nrc_params(pt_nrc* nrc, int which, float** ptr, uint64_t* count);
+/* Last training loss (mean relative L2 over the most recent step; synchronises). */
+pt_status pt_nrc_last_loss(pt_nrc* nrc, float* loss);
+void pt_nrc_destroy(pt_nrc* nrc);
+
+const char* pt_status_string(pt_status status);
+const char* pt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PT_H_ */

@@ -1,0 +1,568 @@
+// pt_bvh.cu -- device BVH build (Sec. 5.1.1: AABB hierarchy over the triangles).
+//
+// 1. centroid bounds, 2. 63-bit Morton codes, 3. LSD radix sort (8 passes of 8 bits),
+// 4. binary radix tree over the sorted codes (Karras, HPG 2012), 5. bottom-up boxes,
+// 6. top-down collapse into an 8-wide BVH with 8-bit quantised child boxes (80-byte nodes;
+//    the layout of compressed wide BVHs, Ylitie, Karras, Laine, HPG 2017), whose leaf
+//    triangles are laid out contiguously per node.
+// The environment's sampling tables (marginal/conditional CDFs) are built here too.
+#include <vector>
+
+#include "pt_internal.h"
+
+#define LEAF_BIT 0x80000000u
+
+__device__ __forceinline__ uint32_t f2ord_b(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f_b(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__device__ __forceinline__ float3 tri_centroid(const float4* t, uint32_t i) {
+    const float4 a = t[3u * i], b = t[3u * i + 1], c = t[3u * i + 2];
+    return mk3((a.x + b.x + c.x) * (1.0f / 3.0f), (a.y + b.y + c.y) * (1.0f / 3.0f), (a.z + b.z + c.z) * (1.0f / 3.0f));
+}
+
+__global__ void k_centroid_bounds(const float4* tris, uint32_t n, uint32_t* cb) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+    if (i < n) {
+        const float3 c = tri_centroid(tris, i);
+        lo[0] = hi[0] = c.x; lo[1] = hi[1] = c.y; lo[2] = hi[2] = c.z;
+    }
+    for (int a = 0; a < 3; ++a) {
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&cb[a], f2ord_b(lo[a]));
+            atomicMax(&cb[3 + a], f2ord_b(hi[a]));
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;  // 21 bits
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+__global__ void k_morton(const float4* tris, uint32_t n, const uint32_t* cb, uint64_t* keys, uint32_t* vals) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float3 c = tri_centroid(tris, i);
+    float q[3];
+    for (int a = 0; a < 3; ++a) {
+        const float lo = ord2f_b(cb[a]), hi = ord2f_b(cb[3 + a]);
+        const float ext = hi - lo;
+        const float t = ext > 0.0f ? (comp3(c, a) - lo) / ext : 0.5f;
+        q[a] = fminf(fmaxf(t * 2097152.0f, 0.0f), 2097151.0f);
+    }
+    keys[i] = spread3((uint32_t)q[0]) << 2 | spread3((uint32_t)q[1]) << 1 | spread3((uint32_t)q[2]);
+    vals[i] = i;
+}
+
+// ------------------------------------------------------------------ LSD radix sort
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+
+__global__ void k_rs_hist(const uint64_t* keys, uint32_t n, int shift, uint32_t* hist, uint32_t nblocks) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const uint32_t idx = base + r * RS_THREADS + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of m counters by one block of 1024 threads
+__global__ void k_rs_scan(uint32_t* data, uint32_t m) {
+    __shared__ uint32_t part[1024];
+    const uint32_t per = (m + 1023) / 1024;
+    const uint32_t b = threadIdx.x * per, e = min(b + per, m);
+    uint32_t sum = 0;
+    for (uint32_t i = b; i < e; ++i) sum += data[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const uint32_t v = threadIdx.x >= (uint32_t)off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - sum;
+    for (uint32_t i = b; i < e; ++i) {
+        const uint32_t v = data[i];
+        data[i] = run;
+        run += v;
+    }
+}
+
+// stable scatter: tile order = round-major, then thread; ranks from warp match + per-warp counts
+__global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, uint32_t n,
+                             int shift, const uint32_t* hist, uint32_t nblocks) {
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[RS_THREADS / 32][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    base[tid] = hist[tid * nblocks + blockIdx.x];
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const uint32_t idx = blockIdx.x * RS_TILE + r * RS_THREADS + tid;
+        const bool valid = idx < n;
+        const uint64_t key = valid ? kin[idx] : 0ull;
+        const uint32_t digit = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
+        for (int j = tid; j < (RS_THREADS / 32) * 256; j += RS_THREADS) (&wcnt[0][0])[j] = 0u;
+        __syncthreads();
+        const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = base[tid];
+            for (int w = 0; w < RS_THREADS / 32; ++w) {
+                const uint32_t c = wcnt[w][tid];
+                wcnt[w][tid] = run;
+                run += c;
+            }
+            base[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = wcnt[warp][digit] + rank;
+            kout[pos] = key;
+            vout[pos] = vin[idx];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ binary radix tree
+__device__ __forceinline__ int lcp(const uint64_t* keys, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    const uint64_t a = keys[i], b = keys[j];
+    if (a == b) return 64 + __clz((uint32_t)(i ^ j));
+    return __clzll((long long)(a ^ b));
+}
+
+__global__ void k_karras(const uint64_t* keys, int n, uint32_t* left, uint32_t* right, uint32_t* par_int,
+                         uint32_t* par_leaf, uint32_t* first, uint32_t* last) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (lcp(keys, n, i, i + 1) - lcp(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = lcp(keys, n, i, i - d);
+    int lmax = 2;
+    while (lcp(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (lcp(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = lcp(keys, n, i, j);
+    int s = 0, t = l;
+    for (;;) {
+        t = (t + 1) >> 1;
+        if (lcp(keys, n, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+    }
+    const int gamma = i + s * d + min(d, 0);
+    const int lo = min(i, j), hi = max(i, j);
+    const uint32_t L = (lo == gamma) ? (LEAF_BIT | (uint32_t)gamma) : (uint32_t)gamma;
+    const uint32_t R = (hi == gamma + 1) ? (LEAF_BIT | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
+    left[i] = L;
+    right[i] = R;
+    first[i] = (uint32_t)lo;
+    last[i] = (uint32_t)hi;
+    if (L & LEAF_BIT) par_leaf[L & ~LEAF_BIT] = (uint32_t)i; else par_int[L] = (uint32_t)i;
+    if (R & LEAF_BIT) par_leaf[R & ~LEAF_BIT] = (uint32_t)i; else par_int[R] = (uint32_t)i;
+    if (i == 0) par_int[0] = 0xffffffffu;
+}
+
+struct Box {
+    float3 lo, hi;
+};
+
+__device__ __forceinline__ Box tri_box(const float4* tris, uint32_t t) {
+    const float4 a = tris[3u * t], b = tris[3u * t + 1], c = tris[3u * t + 2];
+    Box r;
+    r.lo = mk3(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z)));
+    r.hi = mk3(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)), fmaxf(a.z, fmaxf(b.z, c.z)));
+    return r;
+}
+__device__ __forceinline__ Box box_union(Box a, Box b) {
+    Box r;
+    r.lo = mk3(fminf(a.lo.x, b.lo.x), fminf(a.lo.y, b.lo.y), fminf(a.lo.z, b.lo.z));
+    r.hi = mk3(fmaxf(a.hi.x, b.hi.x), fmaxf(a.hi.y, b.hi.y), fmaxf(a.hi.z, b.hi.z));
+    return r;
+}
+
+struct BinTree {
+    const uint32_t *left, *right, *first, *last, *perm;
+    float4 *blo, *bhi;
+    const float4* tris;
+};
+
+__device__ __forceinline__ Box ref_box(const BinTree& T, uint32_t ref) {
+    if (ref & LEAF_BIT) return tri_box(T.tris, T.perm[ref & ~LEAF_BIT]);
+    const float4 lo = __ldcg(T.blo + ref), hi = __ldcg(T.bhi + ref);
+    Box b;
+    b.lo = xyz(lo);
+    b.hi = xyz(hi);
+    return b;
+}
+
+__global__ void k_bottom_up(BinTree T, int n, const uint32_t* par_int, const uint32_t* par_leaf, uint32_t* flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t node = par_leaf[i];
+    while (node != 0xffffffffu) {
+        __threadfence();
+        if (atomicAdd(&flags[node], 1u) == 0u) return;  // first child to arrive stops
+        __threadfence();
+        const Box b = box_union(ref_box(T, T.left[node]), ref_box(T, T.right[node]));
+        __stcg(T.blo + node, make_float4(b.lo.x, b.lo.y, b.lo.z, 0.0f));
+        __stcg(T.bhi + node, make_float4(b.hi.x, b.hi.y, b.hi.z, 0.0f));
+        node = par_int[node];
+    }
+}
+
+// ------------------------------------------------------------------ collapse to 8-wide nodes
+struct CollapseCtx {
+    BinTree T;
+    uint32_t leaf_size;
+    uint32_t* task_ref;     // binary node ref of each wide-node task
+    uint32_t* task_node;    // wide node index of each task
+    uint32_t* counters;     // [0] node count, [1] triangle count, [2] queue tail
+    uint4* nodes;
+    float4* out_tris;
+    const float4* in_tris;
+};
+
+__device__ __forceinline__ uint32_t ref_count(const BinTree& T, uint32_t ref) {
+    return (ref & LEAF_BIT) ? 1u : T.last[ref] - T.first[ref] + 1u;
+}
+__device__ __forceinline__ uint32_t ref_first(const BinTree& T, uint32_t ref) {
+    return (ref & LEAF_BIT) ? (ref & ~LEAF_BIT) : T.first[ref];
+}
+__device__ __forceinline__ float area(const Box& b) {
+    const float dx = b.hi.x - b.lo.x, dy = b.hi.y - b.lo.y, dz = b.hi.z - b.lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__device__ __forceinline__ uint32_t pack_bytes(const uint32_t* q, int off) {
+    return q[off] | (q[off + 1] << 8) | (q[off + 2] << 16) | (q[off + 3] << 24);
+}
+
+__global__ void k_collapse(CollapseCtx C, uint32_t qbeg, uint32_t qend) {
+    const uint32_t ti = qbeg + blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= qend) return;
+    const BinTree& T = C.T;
+    const uint32_t root_ref = C.task_ref[ti];
+    const uint32_t wnode = C.task_node[ti];
+    uint32_t ch[8];
+    Box cb[8];
+    int nc = 0;
+    if ((root_ref & LEAF_BIT) || ref_count(T, root_ref) <= C.leaf_size) {
+        ch[0] = root_ref;
+        cb[0] = ref_box(T, root_ref);
+        nc = 1;
+    } else {
+        ch[0] = T.left[root_ref];
+        ch[1] = T.right[root_ref];
+        cb[0] = ref_box(T, ch[0]);
+        cb[1] = ref_box(T, ch[1]);
+        nc = 2;
+        while (nc < 8) {
+            int best = -1;
+            float best_a = -1.0f;
+            for (int j = 0; j < nc; ++j) {
+                if ((ch[j] & LEAF_BIT) || ref_count(T, ch[j]) <= C.leaf_size) continue;
+                const float a = area(cb[j]);
+                if (a > best_a) { best_a = a; best = j; }
+            }
+            if (best < 0) break;
+            const uint32_t r = ch[best];
+            ch[best] = T.left[r];
+            cb[best] = ref_box(T, ch[best]);
+            ch[nc] = T.right[r];
+            cb[nc] = ref_box(T, ch[nc]);
+            ++nc;
+        }
+    }
+    uint32_t n_int = 0, n_leaf_tris = 0;
+    for (int j = 0; j < nc; ++j) {
+        const uint32_t c = ref_count(T, ch[j]);
+        if (c > C.leaf_size) ++n_int; else n_leaf_tris += c;
+    }
+    const uint32_t child_base = n_int ? atomicAdd(&C.counters[0], n_int) : 0u;
+    const uint32_t tri_base = n_leaf_tris ? atomicAdd(&C.counters[1], n_leaf_tris) : 0u;
+    const uint32_t qpos = n_int ? atomicAdd(&C.counters[2], n_int) : 0u;
+    // node box and quantisation frame
+    Box nb = cb[0];
+    for (int j = 1; j < nc; ++j) nb = box_union(nb, cb[j]);
+    const float3 p = nb.lo;
+    float ext[3] = {nb.hi.x - nb.lo.x, nb.hi.y - nb.lo.y, nb.hi.z - nb.lo.z};
+    const float emax = fmaxf(ext[0], fmaxf(ext[1], ext[2]));
+    uint32_t ebias[3];
+    float scale[3];
+    for (int a = 0; a < 3; ++a) {
+        const float e = fmaxf(fmaxf(ext[a], emax * 1e-6f), 1e-30f);
+        int ex;
+        frexpf(e / 255.0f, &ex);
+        int b = min(max(ex + 127, 1), 254);
+        float sc = __uint_as_float((uint32_t)b << 23);
+        while (b < 254 && fmaf(255.0f, sc, comp3(p, a)) < comp3(nb.hi, a)) { ++b; sc = __uint_as_float((uint32_t)b << 23); }
+        ebias[a] = (uint32_t)b;
+        scale[a] = sc;
+    }
+    uint32_t qlo[3][8], qhi[3][8], meta[8];
+    uint32_t imask = 0, rank = 0, toff = 0;
+    for (int j = 0; j < 8; ++j) {
+        meta[j] = 0;
+        for (int a = 0; a < 3; ++a) { qlo[a][j] = 0; qhi[a][j] = 0; }
+    }
+    for (int j = 0; j < nc; ++j) {
+        for (int a = 0; a < 3; ++a) {
+            const float pa = comp3(p, a), sc = scale[a];
+            const float lo = comp3(cb[j].lo, a), hi = comp3(cb[j].hi, a);
+            float ql = floorf(__fsub_rd(lo, pa) / sc);
+            ql = fminf(fmaxf(ql, 0.0f), 255.0f);
+            while (ql > 0.0f && fmaf(ql, sc, pa) > lo) ql -= 1.0f;
+            float qh = ceilf(__fsub_ru(hi, pa) / sc);
+            qh = fminf(fmaxf(qh, 0.0f), 255.0f);
+            while (qh < 255.0f && fmaf(qh, sc, pa) < hi) qh += 1.0f;
+            qlo[a][j] = (uint32_t)ql;
+            qhi[a][j] = (uint32_t)qh;
+        }
+        const uint32_t c = ref_count(T, ch[j]);
+        if (c > C.leaf_size) {
+            imask |= 1u << j;
+            meta[j] = 1u;
+            C.task_ref[qpos + rank] = ch[j];
+            C.task_node[qpos + rank] = child_base + rank;
+            ++rank;
+        } else {
+            meta[j] = (c << 5) | toff;
+            const uint32_t f = ref_first(T, ch[j]);
+            for (uint32_t k = 0; k < c; ++k) {
+                const uint32_t src = T.perm[f + k];
+                const uint32_t dst = tri_base + toff + k;
+                C.out_tris[3u * dst + 0] = C.in_tris[3u * src + 0];
+                C.out_tris[3u * dst + 1] = C.in_tris[3u * src + 1];
+                C.out_tris[3u * dst + 2] = C.in_tris[3u * src + 2];
+            }
+            toff += c;
+        }
+    }
+    uint4* o = C.nodes + 5u * wnode;
+    o[0] = make_uint4(__float_as_uint(p.x), __float_as_uint(p.y), __float_as_uint(p.z),
+                      ebias[0] | (ebias[1] << 8) | (ebias[2] << 16) | (imask << 24));
+    o[1] = make_uint4(child_base, tri_base, pack_bytes(meta, 0), pack_bytes(meta, 4));
+    o[2] = make_uint4(pack_bytes(qlo[0], 0), pack_bytes(qlo[0], 4), pack_bytes(qlo[1], 0), pack_bytes(qlo[1], 4));
+    o[3] = make_uint4(pack_bytes(qlo[2], 0), pack_bytes(qlo[2], 4), pack_bytes(qhi[0], 0), pack_bytes(qhi[0], 4));
+    o[4] = make_uint4(pack_bytes(qhi[1], 0), pack_bytes(qhi[1], 4), pack_bytes(qhi[2], 0), pack_bytes(qhi[2], 4));
+}
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t n) {
+    return cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+}
+
+pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, cudaStream_t st) {
+    const uint32_t n = s->n_tris;
+    if (s->d_nodes) { cudaFree(s->d_nodes); s->d_nodes = nullptr; }
+    if (s->d_tris) { cudaFree(s->d_tris); s->d_tris = nullptr; }
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr, *hist = nullptr, *cb = nullptr;
+    uint32_t *left = nullptr, *right = nullptr, *pint = nullptr, *pleaf = nullptr, *first = nullptr, *last = nullptr;
+    uint32_t *flags = nullptr, *tref = nullptr, *tnode = nullptr, *counters = nullptr;
+    float4 *blo = nullptr, *bhi = nullptr;
+    const uint32_t nblocks = (n + RS_TILE - 1) / RS_TILE;
+    pt_status status = PT_OK;
+    auto cleanup = [&]() {
+        void* ps[] = {k0, k1, v0, v1, hist, cb, left, right, pint, pleaf, first, last, flags, tref, tnode, counters, blo, bhi};
+        for (void* q : ps)
+            if (q) cudaFree(q);
+    };
+#define BTRY(call)                                                                           \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            pt_set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                \
+            cleanup();                                                                       \
+            return e_ == cudaErrorMemoryAllocation ? PT_ERR_OOM : PT_ERR_CUDA;               \
+        }                                                                                    \
+    } while (0)
+    BTRY(dalloc(&k0, n)); BTRY(dalloc(&k1, n)); BTRY(dalloc(&v0, n)); BTRY(dalloc(&v1, n));
+    BTRY(dalloc(&hist, (size_t)256 * nblocks)); BTRY(dalloc(&cb, 8));
+    BTRY(dalloc(&left, n)); BTRY(dalloc(&right, n)); BTRY(dalloc(&pint, n)); BTRY(dalloc(&pleaf, n));
+    BTRY(dalloc(&first, n)); BTRY(dalloc(&last, n)); BTRY(dalloc(&flags, n));
+    BTRY(dalloc(&tref, n + 1)); BTRY(dalloc(&tnode, n + 1)); BTRY(dalloc(&counters, 4));
+    BTRY(dalloc(&blo, n)); BTRY(dalloc(&bhi, n));
+    BTRY(dalloc(&s->d_nodes, (size_t)5 * (n + 1)));
+    BTRY(dalloc(&s->d_tris, (size_t)3 * n));
+
+    const uint32_t cbinit[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+    BTRY(cudaMemcpyAsync(cb, cbinit, sizeof(cbinit), cudaMemcpyHostToDevice, st));
+    const uint32_t g = (n + 255) / 256;
+    PT_LAUNCH(k_centroid_bounds, g, 256, 0, st, s->d_tris_raw, n, cb);
+    PT_LAUNCH(k_morton, g, 256, 0, st, s->d_tris_raw, n, cb, k0, v0);
+    s->launches += 2;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 8 * pass;
+        PT_LAUNCH(k_rs_hist, nblocks, RS_THREADS, 0, st, k0, n, shift, hist, nblocks);
+        PT_LAUNCH(k_rs_scan, 1, 1024, 0, st, hist, 256u * nblocks);
+        PT_LAUNCH(k_rs_scatter, nblocks, RS_THREADS, 0, st, k0, v0, k1, v1, n, shift, hist, nblocks);
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+        s->launches += 3;
+    }
+    BinTree T;
+    T.left = left; T.right = right; T.first = first; T.last = last; T.perm = v0;
+    T.blo = blo; T.bhi = bhi; T.tris = s->d_tris_raw;
+    if (n > 1) {
+        PT_LAUNCH(k_karras, (n - 1 + 255) / 256, 256, 0, st, k0, (int)n, left, right, pint, pleaf, first, last);
+        BTRY(cudaMemsetAsync(flags, 0, (size_t)n * sizeof(uint32_t), st));
+        PT_LAUNCH(k_bottom_up, g, 256, 0, st, T, (int)n, pint, pleaf, flags);
+        s->launches += 2;
+    }
+    // collapse, one level per launch
+    const uint32_t root_ref = n > 1 ? 0u : LEAF_BIT;
+    const uint32_t init[4] = {1u, 0u, 1u, 0u};
+    BTRY(cudaMemcpyAsync(counters, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    const uint32_t zero = 0;
+    BTRY(cudaMemcpyAsync(tref, &root_ref, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    BTRY(cudaMemcpyAsync(tnode, &zero, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    CollapseCtx C;
+    C.T = T;
+    C.leaf_size = leaf_size;
+    C.task_ref = tref;
+    C.task_node = tnode;
+    C.counters = counters;
+    C.nodes = s->d_nodes;
+    C.out_tris = s->d_tris;
+    C.in_tris = s->d_tris_raw;
+    uint32_t qbeg = 0, qend = 1, depth = 0;
+    uint32_t host_counters[4] = {0, 0, 0, 0};
+    while (qbeg < qend) {
+        const uint32_t cnt = qend - qbeg;
+        PT_LAUNCH(k_collapse, (cnt + 127) / 128, 128, 0, st, C, qbeg, qend);
+        s->launches++;
+        BTRY(cudaMemcpyAsync(host_counters, counters, sizeof(host_counters), cudaMemcpyDeviceToHost, st));
+        BTRY(cudaStreamSynchronize(st));
+        ++depth;
+        qbeg = qend;
+        qend = host_counters[2];
+        if (depth > 200) { pt_set_error("BVH collapse did not terminate"); status = PT_ERR_CUDA; break; }
+    }
+    BTRY(cudaGetLastError());
+    if (status == PT_OK && host_counters[1] != n) {
+        pt_set_error("BVH collapse placed " + std::to_string(host_counters[1]) + " of " + std::to_string(n) + " triangles");
+        status = PT_ERR_CUDA;
+    }
+    s->n_nodes = host_counters[0];
+    s->depth = depth;
+    cleanup();
+#undef BTRY
+    return status;
+}
+
+// ------------------------------------------------------------------ environment tables
+// weights w = luminance * sin(theta at the texel centre); per-row conditional CDF and the
+// marginal CDF over rows; a row (or the whole map) of zero weight gets a uniform CDF.
+__global__ void k_env_rows(const float* env, int w, int h, float* wtex, float* cond, float* rowsum) {
+    __shared__ float part[256];
+    __shared__ float running;
+    const int y = blockIdx.x;
+    const float st = sinf(PT_PI_F * ((float)y + 0.5f) / (float)h);
+    if (threadIdx.x == 0) running = 0.0f;
+    __syncthreads();
+    float* cd = cond + (size_t)y * (w + 1);
+    for (int base = 0; base < w; base += 256) {
+        const int x = base + threadIdx.x;
+        float wt = 0.0f;
+        if (x < w) {
+            const float* t = env + 3 * ((size_t)y * w + x);
+            wt = fmaxf(lum3(mk3(t[0], t[1], t[2])) * st, 0.0f);
+            wtex[(size_t)y * w + x] = wt;
+        }
+        part[threadIdx.x] = wt;
+        __syncthreads();
+        for (int off = 1; off < 256; off <<= 1) {
+            const float v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0.0f;
+            __syncthreads();
+            part[threadIdx.x] += v;
+            __syncthreads();
+        }
+        if (x < w) cd[x + 1] = running + part[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) running += part[255];
+        __syncthreads();
+    }
+    const float tot = running;
+    for (int x = threadIdx.x; x < w; x += 256) cd[x + 1] = tot > 0.0f ? cd[x + 1] / tot : (float)(x + 1) / (float)w;
+    if (threadIdx.x == 0) {
+        cd[0] = 0.0f;
+        rowsum[y] = tot;
+    }
+}
+
+__global__ void k_env_marg(const float* rowsum, int h, float* marg, float* total) {
+    __shared__ float part[1024];
+    __shared__ float running;
+    if (threadIdx.x == 0) running = 0.0f;
+    __syncthreads();
+    for (int base = 0; base < h; base += 1024) {
+        const int y = base + threadIdx.x;
+        part[threadIdx.x] = y < h ? rowsum[y] : 0.0f;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const float v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0.0f;
+            __syncthreads();
+            part[threadIdx.x] += v;
+            __syncthreads();
+        }
+        if (y < h) marg[y + 1] = running + part[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) running += part[1023];
+        __syncthreads();
+    }
+    const float tot = running;
+    for (int y = threadIdx.x; y < h; y += 1024) marg[y + 1] = tot > 0.0f ? marg[y + 1] / tot : (float)(y + 1) / (float)h;
+    if (threadIdx.x == 0) {
+        marg[0] = 0.0f;
+        total[0] = tot;
+    }
+}
+
+pt_status pt_build_env_impl(pt_scene* s, cudaStream_t st) {
+    if (!s->d_env || s->env_w <= 0) { s->env_total = 0.0f; return PT_OK; }
+    const int w = s->env_w, h = s->env_h;
+    float* rowsum = nullptr;
+    if (!s->d_env_wtex) {
+        PT_CUDA_TRY(cudaMalloc(&s->d_env_wtex, (size_t)w * h * sizeof(float)));
+        PT_CUDA_TRY(cudaMalloc(&s->d_env_cond, (size_t)h * (w + 1) * sizeof(float)));
+        PT_CUDA_TRY(cudaMalloc(&s->d_env_marg, (size_t)(h + 1) * sizeof(float)));
+        PT_CUDA_TRY(cudaMalloc(&s->d_env_total, sizeof(float)));
+    }
+    PT_CUDA_TRY(cudaMalloc(&rowsum, (size_t)h * sizeof(float)));
+    PT_LAUNCH(k_env_rows, h, 256, 0, st, s->d_env, w, h, s->d_env_wtex, s->d_env_cond, rowsum);
+    PT_LAUNCH(k_env_marg, 1, 1024, 0, st, rowsum, h, s->d_env_marg, s->d_env_total);
+    s->launches += 2;
+    PT_CUDA_TRY(cudaMemcpyAsync(&s->env_total, s->d_env_total, sizeof(float), cudaMemcpyDeviceToHost, st));
+    PT_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(rowsum);
+    return PT_OK;
+}

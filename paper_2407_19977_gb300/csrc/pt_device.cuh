@@ -1,0 +1,928 @@
+// pt_device.cuh -- device building blocks of the path tracer (sm_103a).
+//
+// Everything here is FP32.  The formulas are the paper's method (Sec. 1.1 rendering
+// equation, Sec. 5.1.2 camera and RNG, Sec. 5.1.3 BVH traversal, OpenPBR shading,
+// importance sampling and Russian roulette) with the readings fixed where the paper is
+// silent: Philox4x32-10 keyed by (pixel, sample, bounce, dim/4); pinhole camera with box
+// filter; watertight ray/triangle test; lobe mixture with one-sample MIS; NEE to quads
+// and the environment with the power heuristic; roulette from vertex 3.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PT_PI_F 3.14159265358979323846f
+#define PT_INV_PI_F 0.31830988618379067154f
+
+// ------------------------------------------------------------------ float3 algebra
+__host__ __device__ __forceinline__ float3 mk3(float x, float y, float z) { return make_float3(x, y, z); }
+__host__ __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return mk3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__host__ __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return mk3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__host__ __device__ __forceinline__ float3 operator*(float3 a, float s) { return mk3(a.x * s, a.y * s, a.z * s); }
+__host__ __device__ __forceinline__ float3 operator*(float3 a, float3 b) { return mk3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__host__ __device__ __forceinline__ float3 operator-(float3 a) { return mk3(-a.x, -a.y, -a.z); }
+__host__ __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__host__ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return mk3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float len3(float3 a) { return sqrtf(dot3(a, a)); }
+__host__ __device__ __forceinline__ float3 norm3(float3 a) { return a * (1.0f / sqrtf(dot3(a, a))); }
+__host__ __device__ __forceinline__ float lum3(float3 c) { return 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z; }
+__host__ __device__ __forceinline__ float max3(float3 c) { return fmaxf(c.x, fmaxf(c.y, c.z)); }
+__host__ __device__ __forceinline__ float3 splat3(float s) { return mk3(s, s, s); }
+__host__ __device__ __forceinline__ float comp3(float3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
+__host__ __device__ __forceinline__ float3 xyz(float4 a) { return mk3(a.x, a.y, a.z); }
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw (SC'11): 10 rounds of two 32x32->64 multiplies per round with
+// a Weyl key schedule.  Counter (pixel, sample, bounce, dim/4), key (lo32, hi32 of seed).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi_a = __umulhi(0xD2511F53u, c.x), lo_a = 0xD2511F53u * c.x;
+        const uint32_t hi_b = __umulhi(0xCD9E8D57u, c.z), lo_b = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+// 24 high bits of a word -> [0, 1), exact in FP32
+__device__ __forceinline__ float u24(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+
+// uniforms of one path vertex: call j covers dims 4j..4j+3
+struct VertexRng {
+    uint32_t p, s, k, k0, k1;
+    __device__ __forceinline__ uint4 block(uint32_t j) const {
+        return philox4x32_10(make_uint4(p, s, k, j), k0, k1);
+    }
+};
+
+enum { DIM_CAM_X = 0, DIM_CAM_Y = 1, DIM_LIGHT_PICK = 2, DIM_LIGHT_U = 3, DIM_LIGHT_V = 4,
+       DIM_LOBE = 5, DIM_DIR_U = 6, DIM_DIR_V = 7, DIM_REFRACT = 8, DIM_RR = 9 };
+
+__device__ __forceinline__ float uniform_at(uint32_t p, uint32_t s, uint32_t k, uint32_t dim,
+                                            uint64_t seed) {
+    uint4 w = philox4x32_10(make_uint4(p, s, k, dim >> 2), (uint32_t)seed, (uint32_t)(seed >> 32));
+    uint32_t sel = (dim & 3u) == 0 ? w.x : ((dim & 3u) == 1 ? w.y : ((dim & 3u) == 2 ? w.z : w.w));
+    return u24(sel);
+}
+
+// ------------------------------------------------------------------ materials
+// Device copy of pt_openpbr; emission premultiplied by its luminance.
+struct __align__(16) DMat {
+    float3 base_color; float base_weight;
+    float3 spec_color; float metalness;
+    float3 trans_color; float spec_weight;
+    float3 coat_color; float trans_weight;
+    float3 emission; float coat_weight;
+    float spec_rough, spec_ior, coat_rough, coat_ior;
+};
+
+struct __align__(16) DQuad {
+    float3 p0; float area;
+    float3 e1; int two_sided;
+    float3 e2; float pad0;
+    float3 L; float pad1;
+    float3 n; float pad2;
+};
+
+// ------------------------------------------------------------------ Fresnel
+__device__ __forceinline__ float fresnel_dielectric(float ci, float eta) {
+    ci = fminf(fmaxf(ci, 0.0f), 1.0f);
+    const float s2t = (1.0f - ci * ci) / (eta * eta);
+    if (s2t >= 1.0f) return 1.0f;
+    const float ct = sqrtf(1.0f - s2t);
+    const float rpar = (eta * ci - ct) / (eta * ci + ct);
+    const float rper = (ci - eta * ct) / (ci + eta * ct);
+    return 0.5f * (rpar * rpar + rper * rper);
+}
+
+// F82-tint metal Fresnel: Schlick from F0 minus b mu (1-mu)^6 with F(1/7) = tint Schlick(1/7)
+__device__ __forceinline__ float f82_channel(float f0, float tint, float mu) {
+    const float mu_bar = 1.0f / 7.0f;
+    const float ob = 1.0f - mu_bar;
+    const float ob2 = ob * ob, ob5 = ob2 * ob2 * ob, ob6 = ob5 * ob;
+    const float om = 1.0f - mu;
+    const float om2 = om * om, om5 = om2 * om2 * om, om6 = om5 * om;
+    const float schlick = f0 + (1.0f - f0) * om5;
+    const float schlick_bar = f0 + (1.0f - f0) * ob5;
+    const float b = schlick_bar * (1.0f - tint) / (mu_bar * ob6);
+    const float f = schlick - b * mu * om6;
+    return fminf(fmaxf(f, 0.0f), 1.0f);
+}
+__device__ __forceinline__ float3 fresnel_f82(float3 f0, float3 tint, float mu) {
+    mu = fminf(fmaxf(mu, 0.0f), 1.0f);
+    return mk3(f82_channel(f0.x, tint.x, mu), f82_channel(f0.y, tint.y, mu), f82_channel(f0.z, tint.z, mu));
+}
+
+// ------------------------------------------------------------------ GGX
+__device__ __forceinline__ float ggx_D(float3 h, float a) {
+    if (h.z <= 0.0f) return 0.0f;
+    const float a2 = a * a;
+    const float d = a2 * h.z * h.z + (h.x * h.x + h.y * h.y);
+    return a2 / (PT_PI_F * d * d);
+}
+__device__ __forceinline__ float ggx_lambda(float3 w, float a) {
+    const float c2 = w.z * w.z;
+    if (c2 <= 0.0f) return __int_as_float(0x7f800000);
+    const float x = a * a * ((w.x * w.x + w.y * w.y) / c2);
+    return x / (2.0f * (1.0f + sqrtf(1.0f + x)));
+}
+__device__ __forceinline__ float ggx_G1(float3 w, float a) { return 1.0f / (1.0f + ggx_lambda(w, a)); }
+__device__ __forceinline__ float ggx_G2(float3 wo, float3 wi, float a) {
+    return 1.0f / (1.0f + ggx_lambda(wo, a) + ggx_lambda(wi, a));
+}
+__device__ __forceinline__ float ggx_vndf_pdf(float3 wo, float3 h, float a) {
+    const float oh = dot3(wo, h);
+    if (oh <= 0.0f || wo.z <= 0.0f) return 0.0f;
+    return ggx_G1(wo, a) * oh * ggx_D(h, a) / wo.z;
+}
+// visible-normal sampling (Heitz 2018): stretch, sample the projected half disk, unstretch
+__device__ __forceinline__ float3 ggx_vndf_sample(float3 wo, float a, float u1, float u2) {
+    const float3 vh = norm3(mk3(a * wo.x, a * wo.y, wo.z));
+    const float lensq = vh.x * vh.x + vh.y * vh.y;
+    const float3 t1 = lensq > 0.0f ? mk3(-vh.y, vh.x, 0.0f) * (1.0f / sqrtf(lensq)) : mk3(1.0f, 0.0f, 0.0f);
+    const float3 t2 = cross3(vh, t1);
+    const float r = sqrtf(u1);
+    const float phi = 2.0f * PT_PI_F * u2;
+    float sp, cp;
+    sincosf(phi, &sp, &cp);
+    const float p1 = r * cp;
+    float p2 = r * sp;
+    const float s = 0.5f * (1.0f + vh.z);
+    p2 = (1.0f - s) * sqrtf(fmaxf(0.0f, 1.0f - p1 * p1)) + s * p2;
+    const float3 nh = t1 * p1 + t2 * p2 + vh * sqrtf(fmaxf(0.0f, 1.0f - p1 * p1 - p2 * p2));
+    return norm3(mk3(a * nh.x, a * nh.y, fmaxf(0.0f, nh.z)));
+}
+__device__ __forceinline__ float3 reflect3(float3 wo, float3 h) { return h * (2.0f * dot3(wo, h)) - wo; }
+__device__ __forceinline__ bool refract3(float3 wo, float3 h, float eta, float3& wi) {
+    const float ci = dot3(wo, h);
+    const float s2t = (1.0f - ci * ci) / (eta * eta);
+    if (s2t >= 1.0f) return false;
+    const float ct = sqrtf(1.0f - s2t);
+    wi = wo * (-1.0f / eta) + h * (ci / eta - ct);
+    return true;
+}
+
+// ------------------------------------------------------------------ OpenPBR closure
+// f = cw f_coat + A_c (m f_metal + (1 - m) f_diel), lobes coat / metal / dielectric / diffuse,
+// picked with probability proportional to an albedo estimate at wo (one-sample MIS).
+enum { LOBE_COAT = 0, LOBE_METAL = 1, LOBE_DIEL = 2, LOBE_DIFF = 3 };
+
+struct Closure {
+    float3 bc, sc, tc, cc;
+    float bw, m, sw, t, cw;
+    float eta_s, eta_c, a_s, a_c;
+    bool delta_s, delta_c, any, has_smooth;
+    float p[4];
+};
+
+__device__ __forceinline__ void closure_setup(Closure& C, const DMat& M, bool front, float mu_o) {
+    C.bc = M.base_color; C.bw = M.base_weight; C.m = M.metalness;
+    C.sc = M.spec_color; C.sw = M.spec_weight;
+    C.tc = M.trans_color; C.t = M.trans_weight;
+    C.cc = M.coat_color; C.cw = M.coat_weight;
+    C.eta_s = (C.t > 0.0f && !front) ? 1.0f / M.spec_ior : M.spec_ior;
+    C.eta_c = M.coat_ior;
+    C.a_s = M.spec_rough * M.spec_rough;
+    C.a_c = M.coat_rough * M.coat_rough;
+    C.delta_s = C.a_s < 1e-4f;
+    C.delta_c = C.a_c < 1e-4f;
+    const float fc = fresnel_dielectric(mu_o, C.eta_c);
+    const float w_coat = C.cw * fc;
+    const float att = C.cw * lum3(C.cc) * (1.0f - fc) + (1.0f - C.cw);
+    const float3 f0 = C.bc * C.bw;
+    const float w_metal = att * C.m * C.sw * lum3(fresnel_f82(f0, C.sc, mu_o));
+    const float fs = fresnel_dielectric(mu_o, C.eta_s);
+    const float w_spec = att * (1.0f - C.m) * C.sw * lum3(C.sc) * fs;
+    const float w_trans = att * (1.0f - C.m) * C.t * lum3(C.tc) * (1.0f - C.sw * fs);
+    const float w_diff = att * (1.0f - C.m) * (1.0f - C.t) * (1.0f - C.sw * fs) * lum3(f0);
+    const float w2 = w_spec + w_trans;
+    const float sum = w_coat + w_metal + w2 + w_diff;
+    C.any = sum > 0.0f;
+    const float inv = C.any ? 1.0f / sum : 0.0f;
+    C.p[0] = w_coat * inv; C.p[1] = w_metal * inv; C.p[2] = w2 * inv; C.p[3] = w_diff * inv;
+    C.has_smooth = (C.p[0] > 0.0f && !C.delta_c) || ((C.p[1] > 0.0f || C.p[2] > 0.0f) && !C.delta_s) ||
+                   C.p[3] > 0.0f;
+}
+
+__device__ __forceinline__ float diel_reflect_prob(const Closure& C, float F) {
+    const float r = C.sw * lum3(C.sc) * F;
+    const float t = C.t * lum3(C.tc) * (1.0f - C.sw * F);
+    if (F >= 1.0f) return 1.0f;
+    const float s = r + t;
+    return s > 0.0f ? r / s : 1.0f;
+}
+
+__device__ __forceinline__ float3 coat_attenuation(const Closure& C, float mi_abs, float mo) {
+    const float fci = fresnel_dielectric(mi_abs, C.eta_c);
+    const float fco = fresnel_dielectric(mo, C.eta_c);
+    return C.cc * (C.cw * (1.0f - fci) * (1.0f - fco)) + splat3(1.0f - C.cw);
+}
+
+// non-delta part of f(wo, wi) and the mixture pdf of sampling wi
+__device__ __forceinline__ void closure_eval(const Closure& C, float3 wo, float3 wi, float3& f_out, float& pdf_out) {
+    float3 f = splat3(0.0f);
+    float pdf = 0.0f;
+    f_out = f;
+    pdf_out = 0.0f;
+    const float mo = wo.z, mi = wi.z;
+    if (mo <= 0.0f || mi == 0.0f) return;
+    const float3 ac = coat_attenuation(C, fabsf(mi), mo);
+    if (mi > 0.0f) {
+        const float3 h = norm3(wo + wi);
+        const float oh = dot3(wo, h);
+        if (oh <= 0.0f) return;
+        if (!C.delta_c && C.cw > 0.0f) {
+            const float fr = fresnel_dielectric(oh, C.eta_c);
+            const float val = C.cw * fr * ggx_D(h, C.a_c) * ggx_G2(wo, wi, C.a_c) / (4.0f * mo * mi);
+            f = f + splat3(val);
+            pdf += C.p[0] * ggx_vndf_pdf(wo, h, C.a_c) / (4.0f * oh);
+        }
+        if (!C.delta_s) {
+            const float dg = ggx_D(h, C.a_s) * ggx_G2(wo, wi, C.a_s) / (4.0f * mo * mi);
+            const float vndf = ggx_vndf_pdf(wo, h, C.a_s) / (4.0f * oh);
+            if (C.m > 0.0f) {
+                const float3 fm = fresnel_f82(C.bc * C.bw, C.sc, oh);
+                f = f + (ac * fm) * (C.m * C.sw * dg);
+            }
+            pdf += C.p[1] * vndf;
+            const float fr = fresnel_dielectric(oh, C.eta_s);
+            f = f + (ac * C.sc) * ((1.0f - C.m) * C.sw * fr * dg);
+            pdf += C.p[2] * diel_reflect_prob(C, fr) * vndf;
+        }
+        const float fsi = fresnel_dielectric(mi, C.eta_s);
+        const float fso = fresnel_dielectric(mo, C.eta_s);
+        const float kd = (1.0f - C.m) * (1.0f - C.t) * (1.0f - C.sw * fsi) * (1.0f - C.sw * fso) * C.bw * PT_INV_PI_F;
+        f = f + (ac * C.bc) * kd;
+        pdf += C.p[3] * mi * PT_INV_PI_F;
+    } else if (!C.delta_s && C.t > 0.0f) {
+        const float eta = C.eta_s;
+        float3 h = norm3(wo + wi * eta);
+        if (h.z < 0.0f) h = -h;
+        const float oh = dot3(wo, h), ih = dot3(wi, h);
+        if (oh > 0.0f && ih < 0.0f) {
+            const float fr = fresnel_dielectric(oh, eta);
+            const float denom = oh + eta * ih;
+            const float dg = ggx_D(h, C.a_s) * ggx_G2(wo, wi, C.a_s);
+            const float val = (1.0f - C.m) * C.t * (1.0f - C.sw * fr) * dg * fabsf(ih) * oh /
+                              (fabsf(mi) * mo * denom * denom);
+            f = f + (ac * C.tc) * val;
+            pdf += C.p[2] * (1.0f - diel_reflect_prob(C, fr)) * ggx_vndf_pdf(wo, h, C.a_s) * eta * eta *
+                   fabsf(ih) / (denom * denom);
+        }
+    }
+    f_out = f;
+    pdf_out = pdf;
+}
+
+struct BsdfSample {
+    float3 wi;
+    float3 weight;
+    float pdf;
+    bool delta;
+};
+
+__device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, float u_lobe, float u1, float u2,
+                                               float u_refr, BsdfSample& out) {
+    if (!C.any || wo.z <= 0.0f) return false;
+    int lobe = -1, last = -1;
+    float c = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (C.p[j] > 0.0f && lobe < 0) {
+            last = j;
+            c += C.p[j];
+            if (u_lobe < c) lobe = j;
+        }
+    }
+    if (lobe < 0) lobe = last;
+    const float mo = wo.z;
+    float3 wi;
+    out.delta = false;
+    out.pdf = 0.0f;
+    if (lobe == LOBE_COAT) {
+        if (C.delta_c) {
+            out.wi = mk3(-wo.x, -wo.y, wo.z);
+            out.weight = splat3(C.cw * fresnel_dielectric(mo, C.eta_c) / C.p[0]);
+            out.delta = true;
+            return true;
+        }
+        wi = reflect3(wo, ggx_vndf_sample(wo, C.a_c, u1, u2));
+        if (wi.z <= 0.0f) return false;
+    } else if (lobe == LOBE_METAL) {
+        if (C.delta_s) {
+            out.wi = mk3(-wo.x, -wo.y, wo.z);
+            const float3 fm = fresnel_f82(C.bc * C.bw, C.sc, mo);
+            out.weight = (coat_attenuation(C, mo, mo) * fm) * (C.m * C.sw / C.p[1]);
+            out.delta = true;
+            return true;
+        }
+        wi = reflect3(wo, ggx_vndf_sample(wo, C.a_s, u1, u2));
+        if (wi.z <= 0.0f) return false;
+    } else if (lobe == LOBE_DIEL) {
+        const float3 h = C.delta_s ? mk3(0.0f, 0.0f, 1.0f) : ggx_vndf_sample(wo, C.a_s, u1, u2);
+        const float oh = dot3(wo, h);
+        if (oh <= 0.0f) return false;
+        const float fr = fresnel_dielectric(oh, C.eta_s);
+        const float pr = diel_reflect_prob(C, fr);
+        const bool do_reflect = u_refr < pr;
+        if (do_reflect) {
+            wi = reflect3(wo, h);
+            if (wi.z <= 0.0f) return false;
+        } else {
+            if (!refract3(wo, h, C.eta_s, wi)) return false;
+            if (wi.z >= 0.0f) return false;
+        }
+        if (C.delta_s) {
+            out.wi = wi;
+            out.delta = true;
+            if (do_reflect) {
+                out.weight = (coat_attenuation(C, mo, mo) * C.sc) * ((1.0f - C.m) * C.sw * fr / (C.p[2] * pr));
+            } else {
+                out.weight = (coat_attenuation(C, fabsf(wi.z), mo) * C.tc) *
+                             ((1.0f - C.m) * C.t * (1.0f - C.sw * fr) / (C.eta_s * C.eta_s * C.p[2] * (1.0f - pr)));
+            }
+            return true;
+        }
+    } else {
+        const float r = sqrtf(u1), phi = 2.0f * PT_PI_F * u2;
+        float sp, cp;
+        sincosf(phi, &sp, &cp);
+        wi = mk3(r * cp, r * sp, sqrtf(fmaxf(0.0f, 1.0f - u1)));
+        if (wi.z <= 0.0f) return false;
+    }
+    float3 f;
+    float pdf;
+    closure_eval(C, wo, wi, f, pdf);
+    if (!(pdf > 0.0f)) return false;
+    out.wi = wi;
+    out.pdf = pdf;
+    out.weight = f * (fabsf(wi.z) / pdf);
+    return true;
+}
+
+// orthonormal basis around n (Duff et al. 2017)
+__device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
+    const float s = n.z >= 0.0f ? 1.0f : -1.0f;
+    const float a = -1.0f / (s + n.z);
+    const float c = n.x * n.y * a;
+    t = mk3(1.0f + s * n.x * n.x * a, s * c, -s * n.x);
+    b = mk3(c, s + n.y * n.y * a, -n.y);
+}
+
+__device__ __forceinline__ float power_heuristic(float pa, float pb) {
+    const float a2 = pa * pa, b2 = pb * pb;
+    return a2 + b2 > 0.0f ? a2 / (a2 + b2) : 0.0f;
+}
+
+// ------------------------------------------------------------------ scene on the device
+// Triangle record (48 B, three float4): v0.xyz + original triangle id (bits),
+// v1.xyz + material code (material id, or 0x80000000 | light index), v2.xyz + unused.
+#define PT_LIGHT_BIT 0x80000000u
+#define PT_NO_HIT 0xFFFFFFFFu
+#define PT_STACK 96
+
+struct DScene {
+    const float4* tris;        // leaf order
+    const uint4* nodes;        // compressed 8-wide BVH, 5 x uint4 per node
+    const DMat* mats;
+    const DQuad* quads;
+    const float* env;          // env_h * env_w * 3
+    const float* env_marg;     // env_h + 1
+    const float* env_cond;     // env_h * (env_w + 1)
+    const float* env_wtex;     // env_h * env_w (unnormalised weights)
+    uint32_t* err;             // sticky error bits
+    float env_total;
+    float eps;
+    int env_w, env_h;
+    int n_quads;
+    int n_nodes;
+    int n_tris;
+    int pad;
+};
+
+// ---- watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2(1), 2013) ----
+struct WRay {
+    float3 o;
+    int kx, ky, kz;
+    float sx, sy, sz;
+};
+
+__device__ __forceinline__ WRay make_wray(float3 o, float3 d) {
+    WRay r;
+    r.o = o;
+    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = 0;
+    float m = ax;
+    if (ay > m) { kz = 1; m = ay; }
+    if (az > m) { kz = 2; }
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    if (comp3(d, kz) < 0.0f) { const int t = kx; kx = ky; ky = t; }
+    r.kx = kx; r.ky = ky; r.kz = kz;
+    const float dz = comp3(d, kz);
+    r.sx = __fdiv_rn(comp3(d, kx), dz);
+    r.sy = __fdiv_rn(comp3(d, ky), dz);
+    r.sz = __fdiv_rn(1.0f, dz);
+    return r;
+}
+
+// Edge functions use explicitly rounded products and differences (no FMA contraction) so
+// that two triangles sharing an edge evaluate exactly opposite values: no ray leaks.
+__device__ __forceinline__ bool tri_hit(const WRay& r, float3 p0, float3 p1, float3 p2, float tmax,
+                                        float& t_out, float& u_out, float& v_out) {
+    const float3 A = mk3(__fsub_rn(p0.x, r.o.x), __fsub_rn(p0.y, r.o.y), __fsub_rn(p0.z, r.o.z));
+    const float3 B = mk3(__fsub_rn(p1.x, r.o.x), __fsub_rn(p1.y, r.o.y), __fsub_rn(p1.z, r.o.z));
+    const float3 Cc = mk3(__fsub_rn(p2.x, r.o.x), __fsub_rn(p2.y, r.o.y), __fsub_rn(p2.z, r.o.z));
+    const float Az = comp3(A, r.kz), Bz = comp3(B, r.kz), Cz = comp3(Cc, r.kz);
+    const float ax = __fsub_rn(comp3(A, r.kx), __fmul_rn(r.sx, Az));
+    const float ay = __fsub_rn(comp3(A, r.ky), __fmul_rn(r.sy, Az));
+    const float bx = __fsub_rn(comp3(B, r.kx), __fmul_rn(r.sx, Bz));
+    const float by = __fsub_rn(comp3(B, r.ky), __fmul_rn(r.sy, Bz));
+    const float cx = __fsub_rn(comp3(Cc, r.kx), __fmul_rn(r.sx, Cz));
+    const float cy = __fsub_rn(comp3(Cc, r.ky), __fmul_rn(r.sy, Cz));
+    const float U = __fsub_rn(__fmul_rn(cx, by), __fmul_rn(cy, bx));
+    const float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
+    const float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+    const float det = U + V + W;
+    if (det == 0.0f) return false;
+    const float T = U * (r.sz * Az) + V * (r.sz * Bz) + W * (r.sz * Cz);
+    const float t = __fdiv_rn(T, det);
+    if (!(t > 0.0f) || !(t < tmax)) return false;
+    t_out = t;
+    u_out = __fdiv_rn(V, det);
+    v_out = __fdiv_rn(W, det);
+    return true;
+}
+
+// ---- compressed 8-wide BVH node (80 B) ----
+// n0 = p.xyz (float bits), w = ex | ey<<8 | ez<<16 | imask<<24
+// n1 = child_base, tri_base, meta[0..3], meta[4..7]
+// n2..n4 = qlo_x, qlo_y, qlo_z, qhi_x, qhi_y, qhi_z (8 bytes each)
+// meta: 0 = empty slot; internal child: nonzero, node = child_base + rank among internal
+// slots; leaf child: count << 5 | offset, triangles tri_base + offset .. + count.
+__device__ __forceinline__ uint32_t byte_of(uint32_t lo4, uint32_t hi4, int i) {
+    return ((i < 4 ? lo4 : hi4) >> (8 * (i & 3))) & 0xffu;
+}
+
+struct TravRay {
+    float3 o, d, inv, oinv;
+};
+__device__ __forceinline__ TravRay make_trav(float3 o, float3 d) {
+    TravRay r;
+    r.o = o;
+    r.d = d;
+    const float big = 1e20f;
+    r.inv = mk3(fabsf(d.x) > 1e-20f ? 1.0f / d.x : copysignf(big, d.x),
+                fabsf(d.y) > 1e-20f ? 1.0f / d.y : copysignf(big, d.y),
+                fabsf(d.z) > 1e-20f ? 1.0f / d.z : copysignf(big, d.z));
+    r.oinv = mk3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+    return r;
+}
+
+struct NodeView {
+    float3 p, scale;
+    uint32_t imask, child_base, tri_base, meta_lo, meta_hi;
+    uint4 q0, q1, q2;
+};
+
+__device__ __forceinline__ NodeView load_node(const uint4* __restrict__ nodes, uint32_t i) {
+    const uint4* b = nodes + 5u * i;
+    const uint4 n0 = __ldg(b + 0), n1 = __ldg(b + 1);
+    NodeView v;
+    v.q0 = __ldg(b + 2);
+    v.q1 = __ldg(b + 3);
+    v.q2 = __ldg(b + 4);
+    v.p = mk3(__uint_as_float(n0.x), __uint_as_float(n0.y), __uint_as_float(n0.z));
+    v.scale = mk3(__uint_as_float((n0.w & 0xffu) << 23), __uint_as_float(((n0.w >> 8) & 0xffu) << 23),
+                  __uint_as_float(((n0.w >> 16) & 0xffu) << 23));
+    v.imask = n0.w >> 24;
+    v.child_base = n1.x;
+    v.tri_base = n1.y;
+    v.meta_lo = n1.z;
+    v.meta_hi = n1.w;
+    return v;
+}
+
+// slab test of child slot i; returns the entry distance (>= 0) or -1 on a miss.  A miss must
+// not look like +inf: before the first hit the closest-hit bound is +inf itself.
+__device__ __forceinline__ float child_hit(const NodeView& v, const TravRay& r, int i, float tmin, float tmax) {
+    // same fmaf as the builder's conservative quantisation check
+    const float lox = fmaf((float)byte_of(v.q0.x, v.q0.y, i), v.scale.x, v.p.x);
+    const float loy = fmaf((float)byte_of(v.q0.z, v.q0.w, i), v.scale.y, v.p.y);
+    const float loz = fmaf((float)byte_of(v.q1.x, v.q1.y, i), v.scale.z, v.p.z);
+    const float hix = fmaf((float)byte_of(v.q1.z, v.q1.w, i), v.scale.x, v.p.x);
+    const float hiy = fmaf((float)byte_of(v.q2.x, v.q2.y, i), v.scale.y, v.p.y);
+    const float hiz = fmaf((float)byte_of(v.q2.z, v.q2.w, i), v.scale.z, v.p.z);
+    // (lo - o) * inv: the error is relative to t itself, so boxes right next to the ray
+    // origin (bounce and shadow rays) are not lost to rounding
+    const float tx0 = __fmul_rn(__fsub_rn(lox, r.o.x), r.inv.x), tx1 = __fmul_rn(__fsub_rn(hix, r.o.x), r.inv.x);
+    const float ty0 = __fmul_rn(__fsub_rn(loy, r.o.y), r.inv.y), ty1 = __fmul_rn(__fsub_rn(hiy, r.o.y), r.inv.y);
+    const float tz0 = __fmul_rn(__fsub_rn(loz, r.o.z), r.inv.z), tz1 = __fmul_rn(__fsub_rn(hiz, r.o.z), r.inv.z);
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    // relative slack keeps flat boxes and rounding in the decode conservative
+    return tn <= tf * 1.00001f + 1e-30f ? tn : -1.0f;
+}
+
+struct HitRec {
+    float t, u, v;
+    uint32_t tri;   // index into the leaf-ordered triangle array, PT_NO_HIT on a miss
+};
+
+__device__ __forceinline__ void cswap(uint64_t& a, uint64_t& b) {
+    const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+
+// Node visits and triangle tests of one traversal (counting variant only).
+struct TravCount {
+    uint32_t nodes, tris;
+};
+
+// Closest hit in (0, tmax); equal t resolved towards the lower original triangle id.
+template <bool COUNT>
+static __device__ __noinline__ void trace_closest_t(const DScene& S, float3 o, float3 d, float tmax, HitRec& h,
+                                                    TravCount& tc) {
+    h.t = tmax;
+    h.tri = PT_NO_HIT;
+    h.u = h.v = 0.0f;
+    if (S.n_nodes == 0) return;
+    const WRay wr = make_wray(o, d);
+    const TravRay tr = make_trav(o, d);
+    uint32_t best_orig = PT_NO_HIT;
+    uint2 stack[PT_STACK];
+    int sp = 0;
+    uint32_t node = 0;
+    // a tree traversal visits every node at most once: more visits mean a malformed tree
+    uint32_t budget = (uint32_t)S.n_nodes + 1u;
+    for (;;) {
+        if (budget-- == 0u) { atomicOr(S.err, 4u); h.tri = PT_NO_HIT; return; }
+        const NodeView v = load_node(S.nodes, node);
+        if (COUNT) tc.nodes++;
+        uint64_t key[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            key[i] = ~0ull;
+            const uint32_t meta = byte_of(v.meta_lo, v.meta_hi, i);
+            if (meta == 0u) continue;
+            const float tn = child_hit(v, tr, i, 0.0f, h.t);
+            if (!(tn >= 0.0f && tn <= h.t)) continue;
+            if ((v.imask >> i) & 1u) {
+                const uint32_t rank = __popc(v.imask & ((1u << i) - 1u));
+                key[i] = ((uint64_t)__float_as_uint(fmaxf(tn, 0.0f)) << 32) | (uint64_t)(v.child_base + rank);
+            } else {
+                const uint32_t first = v.tri_base + (meta & 31u);
+                const uint32_t cnt = meta >> 5;
+                if (COUNT) tc.tris += cnt;
+                for (uint32_t k = 0; k < cnt; ++k) {
+                    const uint32_t ti = first + k;
+                    const float4 a = __ldg(S.tris + 3u * ti), b = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
+                    float t, u, w;
+                    if (tri_hit(wr, xyz(a), xyz(b), xyz(c), tmax, t, u, w)) {
+                        const uint32_t orig = __float_as_uint(a.w);
+                        if (t < h.t || (t == h.t && orig < best_orig)) {
+                            h.t = t; h.u = u; h.v = w; h.tri = ti; best_orig = orig;
+                        }
+                    }
+                }
+            }
+        }
+        // sorting network (19 compare-exchanges) orders internal children near to far
+        cswap(key[0], key[1]); cswap(key[2], key[3]); cswap(key[4], key[5]); cswap(key[6], key[7]);
+        cswap(key[0], key[2]); cswap(key[1], key[3]); cswap(key[4], key[6]); cswap(key[5], key[7]);
+        cswap(key[1], key[2]); cswap(key[5], key[6]); cswap(key[0], key[4]); cswap(key[3], key[7]);
+        cswap(key[1], key[5]); cswap(key[2], key[6]);
+        cswap(key[1], key[4]); cswap(key[3], key[6]);
+        cswap(key[2], key[4]); cswap(key[3], key[5]);
+        cswap(key[3], key[4]);
+        bool have_next = false;
+#pragma unroll
+        for (int i = 7; i >= 0; --i) {
+            if (key[i] == ~0ull) continue;
+            const float tn = __uint_as_float((uint32_t)(key[i] >> 32));
+            if (tn > h.t) continue;
+            if (i == 0) {
+                node = (uint32_t)key[i];
+                have_next = true;
+            } else {
+                if (sp >= PT_STACK) { atomicOr(S.err, 1u); return; }
+                stack[sp++] = make_uint2((uint32_t)key[i], (uint32_t)(key[i] >> 32));
+            }
+        }
+        if (!have_next) {
+            // the nearest hit child may have been pruned: take it from the stack instead
+            bool found = false;
+            while (sp > 0) {
+                const uint2 e = stack[--sp];
+                if (__uint_as_float(e.y) <= h.t) { node = e.x; found = true; break; }
+            }
+            if (!found) return;
+        }
+    }
+}
+
+// Any hit in (0, tmax): occlusion test for shadow rays.
+template <bool COUNT>
+static __device__ __noinline__ bool trace_any_t(const DScene& S, float3 o, float3 d, float tmax, TravCount& tc) {
+    if (S.n_nodes == 0) return false;
+    const WRay wr = make_wray(o, d);
+    const TravRay tr = make_trav(o, d);
+    uint32_t stack[PT_STACK];
+    int sp = 0;
+    uint32_t node = 0;
+    uint32_t budget = (uint32_t)S.n_nodes + 1u;
+    for (;;) {
+        if (budget-- == 0u) { atomicOr(S.err, 4u); return false; }
+        const NodeView v = load_node(S.nodes, node);
+        if (COUNT) tc.nodes++;
+        int n_int = 0;
+        uint32_t first_int = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t meta = byte_of(v.meta_lo, v.meta_hi, i);
+            if (meta == 0u) continue;
+            const float tn = child_hit(v, tr, i, 0.0f, tmax);
+            if (!(tn >= 0.0f && tn <= tmax)) continue;
+            if ((v.imask >> i) & 1u) {
+                const uint32_t c = v.child_base + __popc(v.imask & ((1u << i) - 1u));
+                if (n_int == 0) {
+                    first_int = c;
+                } else {
+                    if (sp >= PT_STACK) { atomicOr(S.err, 1u); return true; }
+                    stack[sp++] = c;
+                }
+                ++n_int;
+            } else {
+                const uint32_t first = v.tri_base + (meta & 31u);
+                const uint32_t cnt = meta >> 5;
+                for (uint32_t k = 0; k < cnt; ++k) {
+                    const uint32_t ti = first + k;
+                    if (COUNT) tc.tris++;
+                    const float4 a = __ldg(S.tris + 3u * ti), b = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
+                    float t, u, w;
+                    if (tri_hit(wr, xyz(a), xyz(b), xyz(c), tmax, t, u, w)) return true;
+                }
+            }
+        }
+        if (n_int > 0) {
+            node = first_int;
+        } else {
+            if (sp == 0) return false;
+            node = stack[--sp];
+        }
+    }
+}
+
+__device__ __forceinline__ void trace_closest(const DScene& S, float3 o, float3 d, float tmax, HitRec& h) {
+    TravCount tc;
+    trace_closest_t<false>(S, o, d, tmax, h, tc);
+}
+__device__ __forceinline__ bool trace_any(const DScene& S, float3 o, float3 d, float tmax) {
+    TravCount tc;
+    return trace_any_t<false>(S, o, d, tmax, tc);
+}
+
+// ------------------------------------------------------------------ environment
+__device__ __forceinline__ void env_texel(const DScene& S, float3 d, int& x, int& y) {
+    const float u = 0.5f + atan2f(d.x, -d.z) * (0.5f * PT_INV_PI_F);
+    const float dy = fminf(fmaxf(d.y, -1.0f), 1.0f);
+    const float v = acosf(dy) * PT_INV_PI_F;
+    int ix = (int)floorf(u * (float)S.env_w), iy = (int)floorf(v * (float)S.env_h);
+    ix = min(max(ix, 0), S.env_w - 1);
+    iy = min(max(iy, 0), S.env_h - 1);
+    x = ix;
+    y = iy;
+}
+__device__ __forceinline__ float3 env_radiance(const DScene& S, float3 d) {
+    int x, y;
+    env_texel(S, d, x, y);
+    const float* t = S.env + 3 * ((size_t)y * S.env_w + x);
+    return mk3(t[0], t[1], t[2]);
+}
+__device__ __forceinline__ float env_pdf(const DScene& S, float3 d) {
+    if (S.env_total <= 0.0f) return 0.0f;
+    int x, y;
+    env_texel(S, d, x, y);
+    const float s = sqrtf(fmaxf(0.0f, 1.0f - d.y * d.y));
+    if (s <= 0.0f) return 0.0f;
+    const float pdf_uv = S.env_wtex[(size_t)y * S.env_w + x] / S.env_total * (float)S.env_w * (float)S.env_h;
+    return pdf_uv / (2.0f * PT_PI_F * PT_PI_F * s);
+}
+// largest i in [0, n-1] with cdf[i] <= u
+__device__ __forceinline__ int cdf_find(const float* cdf, int n, float u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(cdf + mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ bool env_sample(const DScene& S, float u3, float u4, float3& d, float& pdf, float3& L) {
+    if (S.env_total <= 0.0f) return false;
+    const int w = S.env_w, h = S.env_h;
+    const int y = cdf_find(S.env_marg, h, u3);
+    const float m0 = S.env_marg[y], m1 = S.env_marg[y + 1];
+    const float dv = m1 > m0 ? (u3 - m0) / (m1 - m0) : 0.5f;
+    const float* cd = S.env_cond + (size_t)y * (w + 1);
+    const int x = cdf_find(cd, w, u4);
+    const float c0 = cd[x], c1 = cd[x + 1];
+    const float du = c1 > c0 ? (u4 - c0) / (c1 - c0) : 0.5f;
+    const float u = ((float)x + du) / (float)w, v = ((float)y + dv) / (float)h;
+    const float theta = v * PT_PI_F, phi = (u - 0.5f) * 2.0f * PT_PI_F;
+    float st, ct, sp, cp;
+    sincosf(theta, &st, &ct);
+    sincosf(phi, &sp, &cp);
+    if (st <= 0.0f) return false;
+    d = mk3(st * sp, ct, -st * cp);
+    const float pdf_uv = S.env_wtex[(size_t)y * w + x] / S.env_total * (float)w * (float)h;
+    pdf = pdf_uv / (2.0f * PT_PI_F * PT_PI_F * st);
+    const float* t = S.env + 3 * ((size_t)y * w + x);
+    L = mk3(t[0], t[1], t[2]);
+    return pdf > 0.0f;
+}
+
+// ------------------------------------------------------------------ camera
+struct DCam {
+    float3 origin, target, up;
+    float vfov_deg;
+    uint32_t width, height;
+};
+__device__ __forceinline__ void camera_ray(const DCam& c, uint32_t px, uint32_t py, float u0, float u1,
+                                           float3& o, float3& d) {
+    const float3 fwd = norm3(c.target - c.origin);
+    const float3 right = norm3(cross3(fwd, c.up));
+    const float3 up = cross3(right, fwd);
+    const float th = tanf(0.5f * c.vfov_deg * (PT_PI_F / 180.0f));
+    const float aspect = (float)c.width / (float)c.height;
+    const float nx = (2.0f * ((float)px + u0) / (float)c.width - 1.0f) * aspect * th;
+    const float ny = (1.0f - 2.0f * ((float)py + u1) / (float)c.height) * th;
+    o = c.origin;
+    d = norm3(fwd + right * nx + up * ny);
+}
+
+__device__ __forceinline__ float3 offset_origin(float3 x, float3 ng, float3 dir, float eps) {
+    const float s = dot3(dir, ng) > 0.0f ? 1.0f : -1.0f;
+    return x + ng * (s * eps);
+}
+
+// ------------------------------------------------------------------ one path vertex
+// Path state carried between bounces.
+struct PathState {
+    float3 beta;
+    float3 L;
+    float prev_pdf;     // mixture pdf of the last BSDF sample; < 0 after a delta lobe / camera
+};
+
+struct ShadowRay {
+    float3 o, d, contrib;
+    float tmax;
+};
+
+enum { FLAG_NO_NEE = 1u, FLAG_NO_RR = 2u, FLAG_COUNT = 4u };
+
+enum ShadeResult { SHADE_END = 0, SHADE_CONTINUE = 1 };
+
+struct ShadeOut {
+    float3 next_o, next_d;
+    bool has_shadow;
+    ShadowRay sh;
+    bool rr_end;
+};
+
+// Handles the hit (or miss) of the ray (o, d) at path vertex k: emission with MIS, the
+// depth limit, next-event estimation (returned as a shadow ray whose contribution is
+// added if unoccluded), BSDF sampling and Russian roulette.  Returns SHADE_CONTINUE with
+// the next ray, or SHADE_END.
+__device__ __forceinline__ int shade_vertex(const DScene& S, const HitRec& h, float3 o, float3 d, uint32_t k,
+                                            uint32_t max_depth, uint32_t flags, const VertexRng& rng,
+                                            PathState& ps, ShadeOut& out) {
+    out.has_shadow = false;
+    out.rr_end = false;
+    const bool nee = !(flags & FLAG_NO_NEE);
+    const bool has_env = S.env_w > 0 && S.env_total > 0.0f;
+    const float p_env = has_env ? (S.n_quads > 0 ? 0.5f : 1.0f) : 0.0f;
+    const bool prev_delta = ps.prev_pdf < 0.0f;
+    if (h.tri == PT_NO_HIT) {
+        if (has_env) {
+            const float3 Le = env_radiance(S, d);
+            float w = 1.0f;
+            if (!prev_delta && nee) w = power_heuristic(ps.prev_pdf, p_env * env_pdf(S, d));
+            ps.L = ps.L + (ps.beta * Le) * w;
+        }
+        return SHADE_END;
+    }
+    const float4 ta = __ldg(S.tris + 3u * h.tri), tb = __ldg(S.tris + 3u * h.tri + 1), tc = __ldg(S.tris + 3u * h.tri + 2);
+    const float3 x = o + d * h.t;
+    const float3 ng = norm3(cross3(xyz(tb) - xyz(ta), xyz(tc) - xyz(ta)));
+    const float3 wo_w = -d;
+    const bool front = dot3(wo_w, ng) > 0.0f;
+    const uint32_t code = __float_as_uint(tb.w);
+    if (code & PT_LIGHT_BIT) {
+        const DQuad& q = S.quads[code & ~PT_LIGHT_BIT];
+        const float cl = dot3(wo_w, q.n);
+        if (cl > 0.0f || (q.two_sided && cl < 0.0f)) {
+            float w = 1.0f;
+            if (!prev_delta && nee) {
+                const float pl = (1.0f - p_env) / (float)S.n_quads * h.t * h.t / (q.area * fabsf(cl));
+                w = power_heuristic(ps.prev_pdf, pl);
+            }
+            ps.L = ps.L + (ps.beta * q.L) * w;
+        }
+        return SHADE_END;
+    }
+    const DMat M = S.mats[code];
+    if (front && (M.emission.x > 0.0f || M.emission.y > 0.0f || M.emission.z > 0.0f))
+        ps.L = ps.L + ps.beta * M.emission;
+    if (k == max_depth) return SHADE_END;
+
+    const float3 n = front ? ng : -ng;
+    float3 tt, bb;
+    onb(n, tt, bb);
+    const float3 wo = mk3(dot3(wo_w, tt), dot3(wo_w, bb), dot3(wo_w, n));
+    Closure C;
+    closure_setup(C, M, front, wo.z);
+
+    const uint4 r0 = rng.block(0), r1 = rng.block(1), r2 = rng.block(2);
+    if (nee && C.has_smooth && (has_env || S.n_quads > 0)) {
+        const float u2 = u24(r0.z), u3 = u24(r0.w), u4 = u24(r1.x);
+        float3 ld, Le = splat3(0.0f), ly = splat3(0.0f);
+        float pl = 0.0f;
+        bool ok = false, to_quad = false;
+        if (u2 < p_env) {
+            float pe;
+            if (env_sample(S, u3, u4, ld, pe, Le)) {
+                pl = p_env * pe;
+                ok = true;
+            }
+        } else {
+            int l = (int)floorf((u2 - p_env) / (1.0f - p_env) * (float)S.n_quads);
+            l = min(l, S.n_quads - 1);
+            const DQuad& q = S.quads[l];
+            const float3 y = q.p0 + q.e1 * u3 + q.e2 * u4;
+            const float3 to = y - x;
+            const float dist2 = dot3(to, to), dist = sqrtf(dist2);
+            ld = to * (1.0f / dist);
+            const float cl = -dot3(ld, q.n);
+            if (cl > 0.0f || (q.two_sided && cl < 0.0f)) {
+                pl = (1.0f - p_env) / (float)S.n_quads * dist2 / (q.area * fabsf(cl));
+                Le = q.L;
+                ly = y;
+                to_quad = true;
+                ok = true;
+            }
+        }
+        if (ok && pl > 0.0f) {
+            const float3 wl = mk3(dot3(ld, tt), dot3(ld, bb), dot3(ld, n));
+            float3 f;
+            float pb;
+            closure_eval(C, wo, wl, f, pb);
+            if (max3(f) > 0.0f) {
+                const float3 so = offset_origin(x, ng, ld, S.eps);
+                float3 sd = ld;
+                float tmax = __int_as_float(0x7f800000);
+                if (to_quad) {
+                    const float3 to = ly - so;
+                    const float dl = len3(to);
+                    sd = to * (1.0f / dl);
+                    tmax = (1.0f - 1e-4f) * dl;
+                }
+                const float w = power_heuristic(pl, pb);
+                out.has_shadow = true;
+                out.sh.o = so;
+                out.sh.d = sd;
+                out.sh.tmax = tmax;
+                out.sh.contrib = ((ps.beta * f) * Le) * (fabsf(wl.z) * w / pl);
+            }
+        }
+    }
+    BsdfSample bs;
+    if (!closure_sample(C, wo, u24(r1.y), u24(r1.z), u24(r1.w), u24(r2.x), bs)) return SHADE_END;
+    ps.beta = ps.beta * bs.weight;
+    if (k >= 3 && !(flags & FLAG_NO_RR)) {
+        const float q = fminf(0.95f, max3(ps.beta));
+        if (u24(r2.y) >= q) {
+            out.rr_end = true;
+            return SHADE_END;
+        }
+        ps.beta = ps.beta * (1.0f / q);
+    }
+    const float3 wi_w = tt * bs.wi.x + bb * bs.wi.y + n * bs.wi.z;
+    out.next_o = offset_origin(x, ng, wi_w, S.eps);
+    out.next_d = norm3(wi_w);
+    ps.prev_pdf = bs.delta ? -1.0f : bs.pdf;
+    return SHADE_CONTINUE;
+}
+
+// ------------------------------------------------------------------ Kahan accumulation
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}

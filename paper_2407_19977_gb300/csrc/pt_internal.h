@@ -1,0 +1,137 @@
+// pt_internal.h -- host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+
+#include "pt.h"
+#include "pt_device.cuh"
+
+// ---- error reporting -------------------------------------------------------------------
+void pt_set_error(const std::string& msg);
+
+#define PT_CUDA_TRY(call)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            pt_set_error(std::string(#call) + ": " + cudaGetErrorString(e_));               \
+            return e_ == cudaErrorMemoryAllocation ? PT_ERR_OOM : PT_ERR_CUDA;              \
+        }                                                                                   \
+    } while (0)
+
+#define PT_CHECK_ARG(cond, msg)                                                             \
+    do {                                                                                    \
+        if (!(cond)) {                                                                      \
+            pt_set_error(msg);                                                              \
+            return PT_ERR_INVALID_ARG;                                                      \
+        }                                                                                   \
+    } while (0)
+
+// ---- launch accounting -----------------------------------------------------------------
+extern std::atomic<uint64_t> g_pt_launches;
+inline void pt_count_launch(uint64_t n = 1) { g_pt_launches.fetch_add(n, std::memory_order_relaxed); }
+#define PT_LAUNCH(kernel, grid, block, smem, stream, ...)                                   \
+    do {                                                                                    \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                         \
+        pt_count_launch();                                                                  \
+    } while (0)
+
+int pt_num_sms();
+
+// ---- device statistics slots -----------------------------------------------------------
+enum { ST_EXT = 0, ST_SHADOW = 1, ST_PATHS = 2, ST_NAN = 3, ST_RR = 4, ST_NRC = 5, ST_NODES = 6, ST_TRIS = 7,
+       ST_SH_NODES = 8, ST_SH_TRIS = 9, ST_COUNT = 16 };
+
+// ---- wavefront workspace ---------------------------------------------------------------
+struct WaveBuffers {
+    uint32_t capacity = 0;       // paths per wave
+    float4* ray_o[2] = {nullptr, nullptr};   // queue entries: origin (w unused)
+    float4* ray_d[2] = {nullptr, nullptr};   // direction, w = path id bits
+    float4* hit = nullptr;       // t, u, v, tri bits (per queue slot)
+    float4* beta = nullptr;      // per path: beta.xyz, prev_pdf
+    float4* radiance = nullptr;  // per path: L.xyz
+    float4* sh_o = nullptr;      // shadow queue: origin, tmax
+    float4* sh_d = nullptr;      // direction, path id bits
+    float4* sh_c = nullptr;      // contribution
+    uint32_t* perm = nullptr;    // material-sorted order of the queue slots
+    uint32_t* keys = nullptr;    // per slot sort key
+    uint32_t* counters = nullptr;  // [0..1] queue sizes, [2] shadow size, [3..6] heads, [8..] buckets
+    size_t bytes = 0;
+};
+
+struct pt_scene {
+    int device = 0;
+    uint32_t n_vertices = 0, n_mesh_tris = 0, n_tris = 0, n_mats = 0, n_quads = 0;
+    float* d_vertices = nullptr;
+    uint32_t* d_indices = nullptr;
+    uint32_t* d_matids = nullptr;
+    float4* d_tris_raw = nullptr;   // triangle records in input order (mesh, then lights)
+    float4* d_tris = nullptr;       // leaf order
+    uint4* d_nodes = nullptr;
+    uint32_t n_nodes = 0, depth = 0;
+    DMat* d_mats = nullptr;
+    DQuad* d_quads = nullptr;
+    float* d_quads_raw = nullptr;
+    float* d_env = nullptr;
+    float* d_env_marg = nullptr;
+    float* d_env_cond = nullptr;
+    float* d_env_wtex = nullptr;
+    float* d_env_total = nullptr;
+    float env_total = 0.0f;
+    int env_w = 0, env_h = 0;
+    float eps = 0.0f;
+    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    uint32_t* d_err = nullptr;
+    unsigned long long* d_stats = nullptr;
+    uint32_t* d_head = nullptr;      // persistent work-queue heads (scratch)
+    bool built = false;
+    WaveBuffers wave;
+    cudaStream_t last_stream = nullptr;
+    uint64_t launches = 0;
+
+    DScene view() const {
+        DScene s;
+        s.tris = d_tris;
+        s.nodes = d_nodes;
+        s.mats = d_mats;
+        s.quads = d_quads;
+        s.env = d_env;
+        s.env_marg = d_env_marg;
+        s.env_cond = d_env_cond;
+        s.env_wtex = d_env_wtex;
+        s.err = d_err;
+        s.env_total = env_total;
+        s.eps = eps;
+        s.env_w = env_w;
+        s.env_h = env_h;
+        s.n_quads = (int)n_quads;
+        s.n_nodes = (int)n_nodes;
+        s.n_tris = (int)n_tris;
+        s.pad = 0;
+        return s;
+    }
+};
+
+// implemented in pt_bvh.cu
+pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, cudaStream_t st);
+pt_status pt_build_env_impl(pt_scene* s, cudaStream_t st);
+
+// implemented in pt_render.cu
+pt_status pt_free_wave(WaveBuffers& w);
+
+inline DCam to_dcam(const pt_camera& c) {
+    DCam d;
+    d.origin = make_float3(c.origin[0], c.origin[1], c.origin[2]);
+    d.target = make_float3(c.target[0], c.target[1], c.target[2]);
+    d.up = make_float3(c.up[0], c.up[1], c.up[2]);
+    d.vfov_deg = c.vfov_deg;
+    d.width = c.width;
+    d.height = c.height;
+    return d;
+}
+
+// device-side material repack (runs the conversion in a kernel)
+struct RawMat { float v[26]; };

@@ -1,0 +1,726 @@
+// pt_render.cu -- path tracing kernels (Sec. 5.1.2 ray generator, Sec. 5.1.3 path tracer,
+// Sec. 5.1.4 progressive averaging).
+//
+// Two executions of the same per-vertex code (shade_vertex in pt_device.cuh):
+//  * megakernel: a persistent grid; warps pop (job, pixel tile) items from a work queue in
+//    device memory, each lane traces its pixel's samples in order and Kahan-accumulates.
+//    One launch also serves a batch of many scenes (pt_render_batch).
+//  * wavefront: one kernel per stage and bounce over queues in HBM: raygen -> closest hit
+//    (persistent, queue-fetching) -> optional sort of the queue by material -> shade
+//    (appends next rays and shadow rays with warp-aggregated atomics) -> shadow any-hit
+//    -> per-pixel Kahan accumulation in sample order.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "pt_internal.h"
+
+// ------------------------------------------------------------------ warp helpers
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// ------------------------------------------------------------------ megakernel
+struct DJob {
+    DScene S;
+    DCam cam;
+    uint32_t x0, y0, cw, ch;      // window in the full frame
+    uint32_t s0, spp, max_depth, flags;
+    uint64_t seed;
+    float* sum;
+    float* comp;
+    float* sample_out;
+    unsigned long long* stats;
+    uint32_t tile_begin;          // first work item of this job
+    uint32_t n_tiles;
+};
+
+struct PixelCounters {
+    unsigned long long ext, shadow, nan, rr, paths;
+};
+
+__device__ __forceinline__ void render_pixel(const DJob& J, uint32_t lp, PixelCounters& cnt) {
+    const uint32_t px = J.x0 + lp % J.cw, py = J.y0 + lp / J.cw;
+    const uint32_t p = py * J.cam.width + px;
+    const uint32_t k0 = (uint32_t)J.seed, k1 = (uint32_t)(J.seed >> 32);
+    float* sp = J.sum + 3ull * lp;
+    float* cp = J.comp + 3ull * lp;
+    float s0 = sp[0], s1 = sp[1], s2 = sp[2], c0 = cp[0], c1 = cp[1], c2 = cp[2];
+    for (uint32_t i = 0; i < J.spp; ++i) {
+        const uint32_t s = J.s0 + i;
+        const uint4 cam_u = philox4x32_10(make_uint4(p, s, 0u, 0u), k0, k1);
+        float3 o, d;
+        camera_ray(J.cam, px, py, u24(cam_u.x), u24(cam_u.y), o, d);
+        PathState ps;
+        ps.beta = splat3(1.0f);
+        ps.L = splat3(0.0f);
+        ps.prev_pdf = -1.0f;
+        for (uint32_t k = 0;; ++k) {
+            HitRec h;
+            trace_closest(J.S, o, d, __int_as_float(0x7f800000), h);
+            cnt.ext++;
+            VertexRng rng;
+            rng.p = p; rng.s = s; rng.k = k; rng.k0 = k0; rng.k1 = k1;
+            ShadeOut so;
+            const int r = shade_vertex(J.S, h, o, d, k, J.max_depth, J.flags, rng, ps, so);
+            if (so.has_shadow) {
+                cnt.shadow++;
+                if (!trace_any(J.S, so.sh.o, so.sh.d, so.sh.tmax)) ps.L = ps.L + so.sh.contrib;
+            }
+            if (r == SHADE_END) {
+                if (so.rr_end) cnt.rr++;
+                break;
+            }
+            o = so.next_o;
+            d = so.next_d;
+        }
+        cnt.paths++;
+        float3 L = ps.L;
+        if (!isfinite(L.x) || !isfinite(L.y) || !isfinite(L.z)) {
+            cnt.nan++;
+            L = splat3(0.0f);
+        }
+        if (J.sample_out) {
+            float* o3 = J.sample_out + 3ull * ((uint64_t)lp * J.spp + i);
+            o3[0] = L.x; o3[1] = L.y; o3[2] = L.z;
+        }
+        kahan_add(s0, c0, L.x);
+        kahan_add(s1, c1, L.y);
+        kahan_add(s2, c2, L.z);
+    }
+    sp[0] = s0; sp[1] = s1; sp[2] = s2;
+    cp[0] = c0; cp[1] = c1; cp[2] = c2;
+}
+
+__device__ __forceinline__ void megakernel_item(const DJob& J, uint32_t item, uint32_t tile_pixels) {
+    const uint32_t lane = lane_id();
+    const uint32_t npix = J.cw * J.ch;
+    const uint32_t pb = (item - J.tile_begin) * tile_pixels;
+    const uint32_t pe = min(pb + tile_pixels, npix);
+    PixelCounters cnt = {0, 0, 0, 0, 0};
+    for (uint32_t lp = pb + lane; lp < pe; lp += 32) render_pixel(J, lp, cnt);
+    const unsigned long long e = warp_sum_u64(cnt.ext), sh = warp_sum_u64(cnt.shadow),
+                             nn = warp_sum_u64(cnt.nan), rr = warp_sum_u64(cnt.rr), pa = warp_sum_u64(cnt.paths);
+    if (lane == 0) {
+        atomicAdd(&J.stats[ST_EXT], e);
+        atomicAdd(&J.stats[ST_SHADOW], sh);
+        if (nn) atomicAdd(&J.stats[ST_NAN], nn);
+        if (rr) atomicAdd(&J.stats[ST_RR], rr);
+        atomicAdd(&J.stats[ST_PATHS], pa);
+    }
+}
+
+// warps pop work items until the queue is empty; an item is a tile of pixels of one job
+__device__ __forceinline__ uint32_t pop_item(uint32_t* head) {
+    uint32_t item = 0;
+    if (lane_id() == 0) item = atomicAdd(head, 1u);
+    return __shfl_sync(0xffffffffu, item, 0);
+}
+
+__global__ void __launch_bounds__(128) k_megakernel(const DJob* __restrict__ jobs, uint32_t n_jobs,
+                                                    uint32_t total_items, uint32_t tile_pixels, uint32_t* head) {
+    for (;;) {
+        const uint32_t item = pop_item(head);
+        if (item >= total_items) break;
+        uint32_t lo = 0, hi = n_jobs - 1;
+        while (lo < hi) {  // last job with tile_begin <= item
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
+        }
+        megakernel_item(jobs[lo], item, tile_pixels);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_megakernel_one(const __grid_constant__ DJob job, uint32_t total_items,
+                                                        uint32_t tile_pixels, uint32_t* head) {
+    for (;;) {
+        const uint32_t item = pop_item(head);
+        if (item >= total_items) break;
+        megakernel_item(job, item, tile_pixels);
+    }
+}
+
+static int g_mk_blocks_per_sm = 0;
+
+static uint32_t megakernel_grid(uint32_t total_items, uint32_t blocks_per_sm) {
+    if (g_mk_blocks_per_sm == 0) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_megakernel, 128, 0);
+        g_mk_blocks_per_sm = std::max(b, 1);
+    }
+    const uint32_t bps = blocks_per_sm ? blocks_per_sm : (uint32_t)g_mk_blocks_per_sm;
+    uint32_t grid = (uint32_t)pt_num_sms() * bps;
+    grid = std::min(grid, (total_items + 3) / 4);   // 4 warps per block, one item per warp at a time
+    return std::max(grid, 1u);
+}
+
+// one job: the job travels as a kernel parameter, nothing is staged in device memory
+static pt_status launch_megakernel_one(DJob job, uint32_t tile_pixels, uint32_t blocks_per_sm, cudaStream_t st,
+                                       uint32_t* d_head, uint64_t* launches) {
+    job.tile_begin = 0;
+    job.n_tiles = (job.cw * job.ch + tile_pixels - 1) / tile_pixels;
+    if (job.n_tiles == 0) return PT_OK;
+    PT_CUDA_TRY(cudaMemsetAsync(d_head, 0, sizeof(uint32_t), st));
+    PT_LAUNCH(k_megakernel_one, megakernel_grid(job.n_tiles, blocks_per_sm), 128, 0, st, job, job.n_tiles,
+              tile_pixels, d_head);
+    (*launches)++;
+    PT_CUDA_TRY(cudaGetLastError());
+    return PT_OK;
+}
+
+// many jobs: the job table goes to a device buffer owned by the caller of this function
+static pt_status launch_megakernel(const std::vector<DJob>& jobs_in, uint32_t tile_pixels, uint32_t blocks_per_sm,
+                                   cudaStream_t st, uint32_t* d_head, DJob* d_jobs, uint64_t* launches) {
+    std::vector<DJob> jobs = jobs_in;
+    uint32_t total = 0;
+    for (auto& j : jobs) {
+        j.tile_begin = total;
+        j.n_tiles = (j.cw * j.ch + tile_pixels - 1) / tile_pixels;
+        total += j.n_tiles;
+    }
+    if (total == 0) return PT_OK;
+    PT_CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(DJob), cudaMemcpyHostToDevice, st));
+    PT_CUDA_TRY(cudaMemsetAsync(d_head, 0, sizeof(uint32_t), st));
+    PT_LAUNCH(k_megakernel, megakernel_grid(total, blocks_per_sm), 128, 0, st, d_jobs, (uint32_t)jobs.size(), total,
+              tile_pixels, d_head);
+    (*launches)++;
+    PT_CUDA_TRY(cudaGetLastError());
+    return PT_OK;
+}
+
+// ------------------------------------------------------------------ wavefront
+enum { C_Q0 = 0, C_Q1 = 1, C_SH = 2, C_HEAD_TRACE = 3, C_HEAD_SHADOW = 4, C_BUCKETS = 16 };
+constexpr uint32_t MAX_SORT_KEYS = 1024;
+
+struct WfParams {
+    DScene S;
+    DCam cam;
+    uint32_t x0, y0, cw;           // window origin and width
+    uint32_t pb, npix;             // pixel range of this wave (window-local linear index)
+    uint32_t sb, nsamp;            // sample range of this wave
+    uint32_t s_call0, spp_call;    // first sample of the pt_render call, samples in the call
+    uint32_t max_depth, flags;
+    uint64_t seed;
+    uint32_t n_keys;               // material sort buckets (0 = no sort)
+    float4* ray_o[2];
+    float4* ray_d[2];
+    float4* hit;
+    float4* beta;
+    float4* radiance;
+    float4* sh_o;
+    float4* sh_d;
+    float4* sh_c;
+    uint32_t* perm;
+    uint32_t* keys;
+    uint32_t* counters;
+    float* sum;
+    float* comp;
+    float* sample_out;
+    unsigned long long* stats;
+};
+
+__global__ void k_wf_raygen(WfParams P) {
+    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n = P.npix * P.nsamp;
+    if (id == 0) {
+        P.counters[C_Q0] = n;
+        atomicAdd(&P.stats[ST_PATHS], (unsigned long long)n);
+    }
+    if (id >= n) return;
+    const uint32_t lp = P.pb + id % P.npix;
+    const uint32_t s = P.sb + id / P.npix;
+    const uint32_t px = P.x0 + lp % P.cw, py = P.y0 + lp / P.cw;
+    const uint32_t p = py * P.cam.width + px;
+    const uint4 u = philox4x32_10(make_uint4(p, s, 0u, 0u), (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    float3 o, d;
+    camera_ray(P.cam, px, py, u24(u.x), u24(u.y), o, d);
+    P.ray_o[0][id] = make_float4(o.x, o.y, o.z, 0.0f);
+    P.ray_d[0][id] = make_float4(d.x, d.y, d.z, __uint_as_float(id));
+    P.beta[id] = make_float4(1.0f, 1.0f, 1.0f, -1.0f);
+    P.radiance[id] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+__global__ void k_wf_setup(uint32_t* counters, int out_q, uint32_t n_keys) {
+    const uint32_t t = threadIdx.x;
+    if (t == 0) {
+        counters[out_q] = 0;
+        counters[C_SH] = 0;
+        counters[C_HEAD_TRACE] = 0;
+        counters[C_HEAD_SHADOW] = 0;
+    }
+    for (uint32_t k = t; k < n_keys; k += blockDim.x) counters[C_BUCKETS + k] = 0;
+}
+
+__device__ __forceinline__ uint32_t hit_key(const DScene& S, const HitRec& h, uint32_t n_mats) {
+    if (h.tri == PT_NO_HIT) return n_mats;
+    const uint32_t code = __float_as_uint(__ldg(S.tris + 3u * h.tri + 1).w);
+    return (code & PT_LIGHT_BIT) ? n_mats + 1 : code;
+}
+
+// persistent closest-hit over the input queue; warps fetch 32 slots at a time
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_wf_trace(WfParams P, int in_q) {
+    __shared__ uint32_t hist[MAX_SORT_KEYS];
+    const bool sort = P.n_keys > 0;
+    if (sort)
+        for (uint32_t k = threadIdx.x; k < P.n_keys; k += blockDim.x) hist[k] = 0;
+    __syncthreads();
+    const uint32_t count = P.counters[in_q];
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&P.stats[ST_EXT], (unsigned long long)count);
+    const uint32_t lane = lane_id();
+    TravCount tc = {0, 0};
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&P.counters[C_HEAD_TRACE], 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= count) break;
+        const uint32_t slot = base + lane;
+        if (slot < count) {
+            const float4 ro = P.ray_o[in_q][slot], rd = P.ray_d[in_q][slot];
+            HitRec h;
+            trace_closest_t<COUNT>(P.S, xyz(ro), xyz(rd), __int_as_float(0x7f800000), h, tc);
+            P.hit[slot] = make_float4(h.t, h.u, h.v, __uint_as_float(h.tri));
+            if (sort) {
+                const uint32_t key = hit_key(P.S, h, P.n_keys - 2);
+                P.keys[slot] = key;
+                atomicAdd(&hist[key], 1u);
+            }
+        }
+    }
+    if (COUNT) {
+        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris);
+        if (lane == 0) {
+            atomicAdd(&P.stats[ST_NODES], nn);
+            atomicAdd(&P.stats[ST_TRIS], nt);
+        }
+    }
+    if (sort) {
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < P.n_keys; k += blockDim.x)
+            if (hist[k]) atomicAdd(&P.counters[C_BUCKETS + k], hist[k]);
+    }
+}
+
+// exclusive scan of the bucket counts into bucket cursors (one block)
+__global__ void k_wf_sort_scan(uint32_t* counters, uint32_t n_keys) {
+    __shared__ uint32_t part[MAX_SORT_KEYS];
+    const uint32_t t = threadIdx.x;
+    const uint32_t v = t < n_keys ? counters[C_BUCKETS + t] : 0u;
+    part[t] = v;
+    __syncthreads();
+    for (uint32_t off = 1; off < blockDim.x; off <<= 1) {
+        const uint32_t a = t >= off ? part[t - off] : 0u;
+        __syncthreads();
+        part[t] += a;
+        __syncthreads();
+    }
+    if (t < n_keys) counters[C_BUCKETS + t] = part[t] - v;
+}
+
+__global__ void k_wf_sort_scatter(WfParams P, int in_q) {
+    const uint32_t count = P.counters[in_q];
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; base < count; base += nwarps * 32u) {
+        const uint32_t slot = base + lane;
+        const bool valid = slot < count;
+        const uint32_t key = valid ? P.keys[slot] : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        const uint32_t leader = __ffs(peers) - 1;
+        uint32_t pos = 0;
+        if (valid && lane == leader) pos = atomicAdd(&P.counters[C_BUCKETS + key], __popc(peers));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (valid) P.perm[pos + __popc(peers & ((1u << lane) - 1u))] = slot;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
+    const uint32_t count = P.counters[in_q];
+    const uint32_t lane = lane_id();
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    unsigned long long rr_cnt = 0;
+    for (uint32_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; base < count; base += nwarps * 32u) {
+        const uint32_t i = base + lane;
+        const bool valid = i < count;
+        bool cont = false, shadow = false;
+        float3 no = splat3(0.0f), nd = splat3(0.0f);
+        ShadowRay sh;
+        uint32_t id = 0;
+        float4 b4 = make_float4(0, 0, 0, 0);
+        if (valid) {
+            const uint32_t slot = P.n_keys ? P.perm[i] : i;
+            const float4 ro = P.ray_o[in_q][slot], rd = P.ray_d[in_q][slot];
+            const float4 hh = P.hit[slot];
+            id = __float_as_uint(rd.w);
+            HitRec h;
+            h.t = hh.x; h.u = hh.y; h.v = hh.z; h.tri = __float_as_uint(hh.w);
+            b4 = P.beta[id];
+            const float4 L4 = P.radiance[id];
+            PathState ps;
+            ps.beta = xyz(b4);
+            ps.prev_pdf = b4.w;
+            ps.L = xyz(L4);
+            const uint32_t lp = P.pb + id % P.npix;
+            const uint32_t s = P.sb + id / P.npix;
+            VertexRng rng;
+            rng.p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
+            rng.s = s; rng.k = k; rng.k0 = (uint32_t)P.seed; rng.k1 = (uint32_t)(P.seed >> 32);
+            ShadeOut so;
+            const int r = shade_vertex(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so);
+            P.radiance[id] = make_float4(ps.L.x, ps.L.y, ps.L.z, 0.0f);
+            if (so.rr_end) rr_cnt++;
+            cont = r == SHADE_CONTINUE;
+            shadow = so.has_shadow;
+            if (cont) {
+                no = so.next_o;
+                nd = so.next_d;
+                P.beta[id] = make_float4(ps.beta.x, ps.beta.y, ps.beta.z, ps.prev_pdf);
+            }
+            sh = so.sh;
+        }
+        // warp-aggregated appends to the next-ray queue and the shadow queue
+        const uint32_t mc = __ballot_sync(0xffffffffu, cont);
+        const uint32_t ms = __ballot_sync(0xffffffffu, shadow);
+        uint32_t bc = 0, bs = 0;
+        if (lane == 0) {
+            if (mc) bc = atomicAdd(&P.counters[out_q], __popc(mc));
+            if (ms) bs = atomicAdd(&P.counters[C_SH], __popc(ms));
+        }
+        bc = __shfl_sync(0xffffffffu, bc, 0);
+        bs = __shfl_sync(0xffffffffu, bs, 0);
+        if (cont) {
+            const uint32_t pos = bc + __popc(mc & lt);
+            P.ray_o[out_q][pos] = make_float4(no.x, no.y, no.z, 0.0f);
+            P.ray_d[out_q][pos] = make_float4(nd.x, nd.y, nd.z, __uint_as_float(id));
+        }
+        if (shadow) {
+            const uint32_t pos = bs + __popc(ms & lt);
+            P.sh_o[pos] = make_float4(sh.o.x, sh.o.y, sh.o.z, sh.tmax);
+            P.sh_d[pos] = make_float4(sh.d.x, sh.d.y, sh.d.z, __uint_as_float(id));
+            P.sh_c[pos] = make_float4(sh.contrib.x, sh.contrib.y, sh.contrib.z, 0.0f);
+        }
+    }
+    rr_cnt = warp_sum_u64(rr_cnt);
+    if (lane == 0 && rr_cnt) atomicAdd(&P.stats[ST_RR], rr_cnt);
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_wf_shadow(WfParams P) {
+    const uint32_t count = P.counters[C_SH];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && count) atomicAdd(&P.stats[ST_SHADOW], (unsigned long long)count);
+    const uint32_t lane = lane_id();
+    TravCount tc = {0, 0};
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&P.counters[C_HEAD_SHADOW], 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= count) break;
+        const uint32_t slot = base + lane;
+        if (slot < count) {
+            const float4 so = P.sh_o[slot], sd = P.sh_d[slot];
+            if (!trace_any_t<COUNT>(P.S, xyz(so), xyz(sd), so.w, tc)) {
+                const uint32_t id = __float_as_uint(sd.w);
+                const float4 c = P.sh_c[slot];
+                float4 L = P.radiance[id];
+                L.x += c.x; L.y += c.y; L.z += c.z;
+                P.radiance[id] = L;
+            }
+        }
+    }
+    if (COUNT) {
+        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris);
+        if (lane == 0) {
+            atomicAdd(&P.stats[ST_SH_NODES], nn);
+            atomicAdd(&P.stats[ST_SH_TRIS], nt);
+        }
+    }
+}
+
+__global__ void k_wf_accum(WfParams P) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long nan_cnt = 0;
+    if (j < P.npix) {
+        const uint32_t lp = P.pb + j;
+        float* sp = P.sum + 3ull * lp;
+        float* cp = P.comp + 3ull * lp;
+        float s0 = sp[0], s1 = sp[1], s2 = sp[2], c0 = cp[0], c1 = cp[1], c2 = cp[2];
+        for (uint32_t q = 0; q < P.nsamp; ++q) {
+            float4 L = P.radiance[j + q * P.npix];
+            if (!isfinite(L.x) || !isfinite(L.y) || !isfinite(L.z)) {
+                nan_cnt++;
+                L = make_float4(0, 0, 0, 0);
+            }
+            if (P.sample_out) {
+                float* o3 = P.sample_out + 3ull * ((uint64_t)lp * P.spp_call + (P.sb + q - P.s_call0));
+                o3[0] = L.x; o3[1] = L.y; o3[2] = L.z;
+            }
+            kahan_add(s0, c0, L.x);
+            kahan_add(s1, c1, L.y);
+            kahan_add(s2, c2, L.z);
+        }
+        sp[0] = s0; sp[1] = s1; sp[2] = s2;
+        cp[0] = c0; cp[1] = c1; cp[2] = c2;
+    }
+    nan_cnt = warp_sum_u64(nan_cnt);
+    if (lane_id() == 0 && nan_cnt) atomicAdd(&P.stats[ST_NAN], nan_cnt);
+}
+
+pt_status pt_free_wave(WaveBuffers& w) {
+    void* ps[] = {w.ray_o[0], w.ray_o[1], w.ray_d[0], w.ray_d[1], w.hit, w.beta, w.radiance,
+                  w.sh_o, w.sh_d, w.sh_c, w.perm, w.keys, w.counters};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    w = WaveBuffers();
+    return PT_OK;
+}
+
+static pt_status ensure_wave(WaveBuffers& w, uint32_t capacity) {
+    if (w.capacity >= capacity) return PT_OK;
+    pt_free_wave(w);
+    const size_t c = capacity;
+    float4** f4[] = {&w.ray_o[0], &w.ray_o[1], &w.ray_d[0], &w.ray_d[1], &w.hit, &w.beta, &w.radiance,
+                     &w.sh_o, &w.sh_d, &w.sh_c};
+    for (float4** p : f4) {
+        cudaError_t e = cudaMalloc((void**)p, c * sizeof(float4));
+        if (e != cudaSuccess) {
+            pt_free_wave(w);
+            pt_set_error(std::string("wavefront buffers: ") + cudaGetErrorString(e));
+            return PT_ERR_OOM;
+        }
+    }
+    if (cudaMalloc(&w.perm, c * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&w.keys, c * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&w.counters, (C_BUCKETS + MAX_SORT_KEYS) * sizeof(uint32_t)) != cudaSuccess) {
+        pt_free_wave(w);
+        pt_set_error("wavefront buffers: out of memory");
+        return PT_ERR_OOM;
+    }
+    w.capacity = capacity;
+    w.bytes = c * (10 * sizeof(float4) + 2 * sizeof(uint32_t));
+    return PT_OK;
+}
+
+static int g_trace_blocks_per_sm = 0, g_shade_blocks_per_sm = 0, g_shadow_blocks_per_sm = 0;
+
+static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
+                                  pt_accum* acc, const pt_render_opts& o, cudaStream_t st) {
+    const uint32_t npix_total = acc->width * acc->height;
+    uint32_t cap = o.wave_paths ? o.wave_paths : (1u << 21);
+    cap = std::max(cap, 32u);
+    // waves hold whole samples of a pixel range: pixel chunk <= cap, then samples per wave
+    const uint32_t pix_chunk = std::min(npix_total, cap);
+    const uint32_t samp_per_wave = std::max(1u, std::min(spp, cap / pix_chunk));
+    pt_status r = ensure_wave(s->wave, pix_chunk * samp_per_wave);
+    if (r != PT_OK) return r;
+    WaveBuffers& w = s->wave;
+    const bool sort = o.sort_by_material == 1 || (o.sort_by_material < 0 && s->n_mats + 2 <= MAX_SORT_KEYS && s->n_mats > 1);
+    const uint32_t n_keys = (sort && s->n_mats + 2 <= MAX_SORT_KEYS) ? s->n_mats + 2 : 0;
+    if (g_trace_blocks_per_sm == 0) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_trace<false>, 128, 0);
+        g_trace_blocks_per_sm = std::max(b, 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shade, 128, 0);
+        g_shade_blocks_per_sm = std::max(b, 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shadow<false>, 128, 0);
+        g_shadow_blocks_per_sm = std::max(b, 1);
+    }
+    const int sms = pt_num_sms();
+    WfParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.S = s->view();
+    P.cam = to_dcam(cam);
+    P.x0 = o.crop_x0;
+    P.y0 = o.crop_y0;
+    P.cw = acc->width;
+    P.s_call0 = (uint32_t)acc->spp_done;
+    P.spp_call = spp;
+    P.max_depth = max_depth;
+    P.flags = o.flags;
+    P.seed = seed;
+    P.n_keys = n_keys;
+    for (int q = 0; q < 2; ++q) { P.ray_o[q] = w.ray_o[q]; P.ray_d[q] = w.ray_d[q]; }
+    P.hit = w.hit; P.beta = w.beta; P.radiance = w.radiance;
+    P.sh_o = w.sh_o; P.sh_d = w.sh_d; P.sh_c = w.sh_c;
+    P.perm = w.perm; P.keys = w.keys; P.counters = w.counters;
+    P.sum = acc->sum; P.comp = acc->comp; P.sample_out = o.sample_out;
+    P.stats = s->d_stats;
+    uint64_t launches = 0;
+    const bool count = (o.flags & FLAG_COUNT) != 0;
+    // optional per-kind timing: an event pair around every launch of a kind
+    const bool timed = o.kernel_ms != nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PT_K_KINDS];
+    auto begin = [&](int kind) -> cudaEvent_t {
+        if (!timed) return nullptr;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
+        ev[kind].push_back({a, b});
+        return b;
+    };
+    auto end = [&](cudaEvent_t b) {
+        if (b) cudaEventRecord(b, st);
+    };
+    for (uint32_t pb = 0; pb < npix_total; pb += pix_chunk) {
+        const uint32_t npix = std::min(pix_chunk, npix_total - pb);
+        for (uint32_t i0 = 0; i0 < spp; i0 += samp_per_wave) {
+            const uint32_t ns = std::min(samp_per_wave, spp - i0);
+            P.pb = pb;
+            P.npix = npix;
+            P.sb = (uint32_t)acc->spp_done + i0;
+            P.nsamp = ns;
+            const uint32_t n = npix * ns;
+            cudaEvent_t e = begin(PT_K_RAYGEN);
+            PT_LAUNCH(k_wf_raygen, (n + 255) / 256, 256, 0, st, P);
+            end(e);
+            ++launches;
+            for (uint32_t k = 0; k <= max_depth; ++k) {
+                const int in_q = (int)(k & 1u), out_q = (int)((k + 1) & 1u);
+                PT_LAUNCH(k_wf_setup, 1, 256, 0, st, w.counters, out_q, n_keys);
+                e = begin(PT_K_TRACE);
+                if (count) PT_LAUNCH(k_wf_trace<true>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
+                else PT_LAUNCH(k_wf_trace<false>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
+                end(e);
+                launches += 2;
+                if (n_keys) {
+                    e = begin(PT_K_SORT);
+                    PT_LAUNCH(k_wf_sort_scan, 1, MAX_SORT_KEYS, 0, st, w.counters, n_keys);
+                    PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
+                    end(e);
+                    launches += 2;
+                }
+                e = begin(PT_K_SHADE);
+                PT_LAUNCH(k_wf_shade, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+                end(e);
+                e = begin(PT_K_SHADOW);
+                if (count) PT_LAUNCH(k_wf_shadow<true>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
+                else PT_LAUNCH(k_wf_shadow<false>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
+                end(e);
+                launches += 2;
+            }
+            e = begin(PT_K_ACCUM);
+            PT_LAUNCH(k_wf_accum, (npix + 255) / 256, 256, 0, st, P);
+            end(e);
+            ++launches;
+        }
+    }
+    s->launches += launches;
+    PT_CUDA_TRY(cudaGetLastError());
+    if (timed) {
+        PT_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int kind = 0; kind < PT_K_KINDS; ++kind) {
+            for (auto& pr : ev[kind]) {
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, pr.first, pr.second);
+                o.kernel_ms[kind] += ms;
+                if (o.kernel_launches) o.kernel_launches[kind] += 1;
+                cudaEventDestroy(pr.first);
+                cudaEventDestroy(pr.second);
+            }
+        }
+    }
+    return PT_OK;
+}
+
+// ------------------------------------------------------------------ entry points
+static DJob make_job(pt_scene* s, const pt_camera& cam, uint32_t x0, uint32_t y0, const pt_accum* acc, uint32_t spp,
+                     uint32_t max_depth, uint64_t seed, uint32_t flags, float* sample_out) {
+    DJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.S = s->view();
+    j.cam = to_dcam(cam);
+    j.x0 = x0;
+    j.y0 = y0;
+    j.cw = acc->width;
+    j.ch = acc->height;
+    j.s0 = (uint32_t)acc->spp_done;
+    j.spp = spp;
+    j.max_depth = max_depth;
+    j.flags = flags;
+    j.seed = seed;
+    j.sum = acc->sum;
+    j.comp = acc->comp;
+    j.sample_out = sample_out;
+    j.stats = s->d_stats;
+    return j;
+}
+
+
+extern "C" pt_status pt_render(pt_scene* s, const pt_camera* camera, uint32_t spp, uint32_t max_depth, uint64_t seed,
+                               pt_accum* acc, const pt_render_opts* opts, void* cuda_stream) {
+    PT_CHECK_ARG(s && camera && acc, "NULL argument");
+    if (!s->built) { pt_set_error("pt_bvh_build has not run"); return PT_ERR_NOT_BUILT; }
+    PT_CHECK_ARG(acc->sum && acc->comp, "accumulator buffers are NULL");
+    PT_CHECK_ARG(camera->width > 0 && camera->height > 0, "empty frame");
+    PT_CHECK_ARG(camera->vfov_deg > 0.0f && camera->vfov_deg < 180.0f, "vfov outside (0, 180)");
+    pt_render_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.sort_by_material = -1;
+    if (opts) o = *opts;
+    PT_CHECK_ARG(acc->width > 0 && acc->height > 0, "empty window");
+    PT_CHECK_ARG((uint64_t)o.crop_x0 + acc->width <= camera->width &&
+                     (uint64_t)o.crop_y0 + acc->height <= camera->height, "window outside the frame");
+    PT_CHECK_ARG(acc->spp_done + spp < (1ull << 32), "sample index overflows 32 bits");
+    PT_CHECK_ARG(o.mode <= PT_MODE_MEGAKERNEL, "unknown mode");
+    if (o.nrc) { pt_set_error("radiance-cache rendering goes through pt_render_nrc"); return PT_ERR_UNSUPPORTED; }
+    if (spp == 0) return PT_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s->last_stream = st;
+    uint32_t mode = o.mode;
+    if (mode == PT_MODE_AUTO) mode = (uint64_t)acc->width * acc->height >= (1u << 16) ? PT_MODE_WAVEFRONT : PT_MODE_MEGAKERNEL;
+    pt_status r;
+    if (mode == PT_MODE_WAVEFRONT) {
+        r = render_wavefront(s, *camera, spp, max_depth, seed, acc, o, st);
+    } else {
+        const uint32_t tile = o.block_size ? std::max(32u, o.block_size & ~31u) : 64u;
+        r = launch_megakernel_one(make_job(s, *camera, o.crop_x0, o.crop_y0, acc, spp, max_depth, seed, o.flags,
+                                           o.sample_out), tile, 0, st, s->d_head, &s->launches);
+    }
+    if (r == PT_OK) acc->spp_done += spp;
+    return r;
+}
+
+extern "C" pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const pt_batch_opts* opts, void* cuda_stream) {
+    PT_CHECK_ARG(jobs != nullptr || n_jobs == 0, "jobs is NULL");
+    if (n_jobs == 0) return PT_OK;
+    pt_batch_opts bo;
+    std::memset(&bo, 0, sizeof(bo));
+    if (opts) bo = *opts;
+    const uint32_t tile = bo.tile_pixels ? bo.tile_pixels : 64;
+    PT_CHECK_ARG(tile % 32 == 0, "tile_pixels must be a multiple of 32");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::vector<DJob> dj;
+    dj.reserve(n_jobs);
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        const pt_job& j = jobs[i];
+        PT_CHECK_ARG(j.scene && j.accum && j.accum->sum && j.accum->comp, "job with NULL scene or accumulator");
+        if (!j.scene->built) { pt_set_error("pt_bvh_build has not run"); return PT_ERR_NOT_BUILT; }
+        PT_CHECK_ARG(j.accum->width == j.camera.width && j.accum->height == j.camera.height,
+                     "batch accumulators cover the whole frame");
+        PT_CHECK_ARG(j.accum->spp_done + j.spp < (1ull << 32), "sample index overflows 32 bits");
+        dj.push_back(make_job(j.scene, j.camera, 0, 0, j.accum, j.spp, j.max_depth, j.seed, 0, nullptr));
+        j.scene->last_stream = st;
+    }
+    // per-call device job table and queue head, released once the stream has drained
+    DJob* d_jobs = nullptr;
+    uint32_t* d_head = nullptr;
+    PT_CUDA_TRY(cudaMalloc(&d_jobs, dj.size() * sizeof(DJob)));
+    if (cudaMalloc(&d_head, sizeof(uint32_t)) != cudaSuccess) {
+        cudaFree(d_jobs);
+        pt_set_error("batch queue head: out of memory");
+        return PT_ERR_OOM;
+    }
+    uint64_t launches = 0;
+    const pt_status r = launch_megakernel(dj, tile, bo.blocks_per_sm, st, d_head, d_jobs, &launches);
+    cudaStreamSynchronize(st);
+    cudaFree(d_jobs);
+    cudaFree(d_head);
+    if (r != PT_OK) return r;
+    for (uint32_t i = 0; i < n_jobs; ++i) jobs[i].accum->spp_done += jobs[i].spp;
+    jobs[0].scene->launches += launches;
+    return PT_OK;
+}

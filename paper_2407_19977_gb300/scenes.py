@@ -383,7 +383,8 @@ def pushbutton(seed=0, n_profile=250, n_angular=400, ground=(50, 100), width=192
     lights = (quad_light((-1.6, 3.2, -1.2), (1.0, 0.0, 0.0), (0.0, 0.0, 1.0), (9.0, 8.5, 8.0))[None, :]
               if with_light else np.zeros((0, N_LIGHT_FLOATS), np.float32))
     env = analytic_sky(env_size[0], env_size[1], seed) if env_size is not None else None
-    cam = _frame_camera((-0.8, 0.0, -0.8), (0.8, 1.05, 0.8), (1.1, 0.85, -1.5), 35.0, width, height)
+    cam = _frame_camera((-0.8, 0.0, -0.8), (0.8, 1.05, 0.8), (1.1, 0.85, -1.5), 35.0, width, height,
+                        margin=0.7)
     return Scene("pushbutton", verts, idx, mid, _pushbutton_materials(), lights, env, cam, spp,
                  max_depth, {"seed": seed, "n_profile": n_profile, "n_angular": n_angular})
 

@@ -1,0 +1,484 @@
+"""GPU-vs-oracle parity through the C-ABI (needs a GB300).
+
+Tolerances (stated by the design, checked here):
+  * uniforms: bit-exact; camera rays: 2e-6 absolute on unit directions;
+  * BSDF values: |gpu - oracle| <= 1e-5 * max(|oracle|, 1e-3 * max over the batch), cosines >= 1e-3;
+  * closest hit: same triangle id on >= 99.99 % of rays, t within 1e-4 relative where ids match;
+  * images at matched seeds: RMSE(gpu - oracle) <= 1e-3 * mean(oracle radiance).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_19977_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2407_19977_gb300 import api as A
+    return A
+
+
+_CACHE = {}
+
+
+def _scene_pair(key, make):
+    if key not in _CACHE:
+        from paper_2407_19977_gb300 import api as A
+        sc = make()
+        _CACHE[key] = (sc, A.Scene(sc), oracle.OracleScene(sc))
+    return _CACHE[key]
+
+
+def cornell():
+    return _scene_pair("cornell", scenes.cornell_box)
+
+
+def pushbutton():
+    return _scene_pair("pushbutton", scenes.pushbutton)
+
+
+def heavy():
+    return _scene_pair("heavy7", lambda: scenes.heavy_scene(level=7))
+
+
+def _image_check(g, o, what, rel=1e-3):
+    g = np.asarray(g, np.float64)
+    o = np.asarray(o, np.float64)
+    rmse = math.sqrt(((g - o) ** 2).mean())
+    mean = o.mean()
+    assert rmse <= rel * mean, f"{what}: rmse {rmse:.3e} > {rel} * mean {mean:.4f}"
+    return rmse / mean
+
+
+# ------------------------------------------------------------------ RNG, camera
+
+def test_uniforms_bit_exact(api):
+    rng = np.random.default_rng(0)
+    n = 50000
+    keys = rng.integers(0, 2**32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    keys[:, 3] = rng.integers(0, 16, n)
+    seed = (0x12345678 << 32) | 0x9ABCDEF0
+    g = api.uniforms(seed, torch.from_numpy(keys.view(np.int32)).cuda()).cpu().numpy().astype(np.float64)
+    o = oracle.uniform_batch(keys[:, 0], keys[:, 1], keys[:, 2], keys[:, 3], seed)
+    assert np.array_equal(g, o)
+
+
+def test_camera_rays(api):
+    sc = scenes.pushbutton(width=1920, height=1080)
+    rng = np.random.default_rng(1)
+    n = 4000
+    pix = np.stack([rng.integers(0, 1920, n), rng.integers(0, 1080, n), rng.integers(0, 512, n)], 1).astype(np.int32)
+    out = api.camera_rays(sc.camera, 7, torch.from_numpy(pix).cuda()).cpu().numpy()
+    for i in range(0, n, 13):
+        o, d = oracle.camera_ray(sc.camera, *pix[i], 7)
+        assert np.allclose(out[i, :3], o, atol=1e-6)
+        assert np.allclose(out[i, 3:], d, atol=2e-6)
+
+
+# ------------------------------------------------------------------ BSDF
+
+def _bsdf_materials():
+    mats = [
+        scenes.openpbr(base_color=(0.6, 0.5, 0.4), specular_roughness=0.4),
+        scenes.openpbr(base_color=(0.9, 0.7, 0.5), base_metalness=1.0, specular_roughness=0.2,
+                       specular_color=(0.8, 0.9, 1.0)),
+        scenes.openpbr(base_color=(0.8, 0.05, 0.05), specular_roughness=0.3, coat_weight=1.0,
+                       coat_roughness=0.05, coat_ior=1.5),
+        scenes.openpbr(specular_roughness=0.45, transmission_weight=1.0),
+        scenes.openpbr(base_color=(0.7, 0.6, 0.9), base_metalness=0.3, specular_roughness=0.5,
+                       transmission_weight=0.4, coat_weight=0.5, coat_roughness=0.4),
+        scenes.diffuse((0.5, 0.5, 0.5)),
+        scenes.openpbr(base_color=(0.3, 0.6, 0.2), base_metalness=1.0, specular_roughness=0.8),
+        scenes.openpbr(base_color=(0.2, 0.4, 0.7), specular_roughness=0.4, coat_weight=1.0, coat_roughness=0.1),
+    ]
+    return np.stack(mats)
+
+
+def _dirs(rng, n, lower=False):
+    z = rng.uniform(1e-3, 1.0, n)
+    phi = rng.uniform(0, 2 * math.pi, n)
+    r = np.sqrt(1 - z * z)
+    d = np.stack([r * np.cos(phi), r * np.sin(phi), -z if lower else z], 1)
+    return d.astype(np.float32).astype(np.float64)
+
+
+def _near_tir(m, front, wo, wi, band=2e-3):
+    """Tuples whose dielectric Fresnel terms sit within `band` of total internal reflection.
+    There the float inputs' rounding is amplified by 1/cos(theta_t): the condition number of
+    the Fresnel term, not the arithmetic, decides the error."""
+    ior = float(m[11])
+    eta = 1.0 / ior if (m[12] > 0 and front == 0) else ior
+    h_r = wo + wi
+    h_r /= np.linalg.norm(h_r, axis=1, keepdims=True)
+    h_t = wo + eta * wi
+    h_t /= np.linalg.norm(h_t, axis=1, keepdims=True)
+    near = np.zeros(len(wo), bool)
+    for c in (np.abs(wo[:, 2]), np.abs(wi[:, 2]), np.abs((wo * h_r).sum(1)), np.abs((wo * h_t).sum(1))):
+        s2t = (1 - c * c) / (eta * eta)
+        near |= np.abs(1 - s2t) < band
+    return near
+
+
+@pytest.mark.parametrize("front", [1, 0])
+def test_bsdf_eval_parity(api, front):
+    rng = np.random.default_rng(2 + front)
+    mats = _bsdf_materials()
+    n = 2000
+    for m_i, m in enumerate(mats):
+        for lower in (False, True):
+            wo = _dirs(rng, n)
+            wi = _dirs(rng, n, lower)
+            mt = torch.from_numpy(np.tile(m, (n, 1)).astype(np.float32)).cuda()
+            fr = torch.full((n,), front, dtype=torch.int32, device="cuda")
+            f_g, p_g = api.bsdf_eval(mt, fr, torch.from_numpy(wo.astype(np.float32)).cuda(),
+                                     torch.from_numpy(wi.astype(np.float32)).cuda())
+            f_o, p_o = oracle.bsdf_eval_batch(m.astype(np.float64), front, wo, wi)
+            f_g = f_g.cpu().numpy().astype(np.float64)
+            p_g = p_g.cpu().numpy().astype(np.float64)
+            ill = _near_tir(m, front, wo, wi)
+            assert ill.mean() < 0.05
+            for g, o, what in ((f_g, f_o, "f"), (p_g, p_o, "pdf")):
+                scale = np.maximum(np.abs(o), 1e-3 * np.abs(o).max())
+                err = np.abs(g - o) - 1e-30
+                bad = err > np.where(ill[:, None] if g.ndim == 2 else ill, 1e-3, 1e-5) * scale
+                assert not bad.any(), (m_i, lower, what, np.argwhere(bad)[:3].ravel(),
+                                       g[bad][:3], o[bad][:3])
+
+
+def test_bsdf_sample_parity(api):
+    rng = np.random.default_rng(5)
+    mats = np.concatenate([_bsdf_materials(), np.stack([
+        scenes.openpbr(specular_roughness=0.0, transmission_weight=1.0),
+        scenes.openpbr(base_color=(0.9, 0.9, 0.9), base_metalness=1.0, specular_roughness=0.0)])])
+    n = 4000
+    for m_i, m in enumerate(mats):
+        for front in (1, 0):
+            wo = _dirs(rng, n)
+            u = rng.random((n, 4)).astype(np.float32).astype(np.float64)
+            mt = torch.from_numpy(np.tile(m, (n, 1)).astype(np.float32)).cuda()
+            fr = torch.full((n,), front, dtype=torch.int32, device="cuda")
+            wi_g, w_g, p_g, fl_g = api.bsdf_sample(mt, fr, torch.from_numpy(wo.astype(np.float32)).cuda(),
+                                                   torch.from_numpy(u.astype(np.float32)).cuda())
+            ok_o, wi_o, w_o, p_o, dl_o = oracle.bsdf_sample_batch(m.astype(np.float64), front, wo, u)
+            fl_g = fl_g.cpu().numpy()
+            ok_g = (fl_g & 1).astype(bool)
+            dl_g = (fl_g & 2).astype(bool)
+            agree = (ok_g == ok_o) & (dl_g == dl_o)
+            # seen from inside a transmissive material, the reflect/refract decision uses a
+            # Fresnel term next to total internal reflection: its flips are rarer than 0.5 %
+            need = 0.995 if (front == 0 and m[12] > 0) else 0.999
+            assert agree.mean() >= need, (m_i, front, agree.mean())
+            sel = agree & ok_o
+            wi_g = wi_g.cpu().numpy()[sel]
+            w_g = w_g.cpu().numpy()[sel]
+            same_dir = np.all(np.abs(wi_g - wi_o[sel]) < 1e-4, axis=1)
+            assert same_dir.mean() >= 0.999, (m_i, front, same_dir.mean())
+            ww = w_o[sel][same_dir]
+            close = np.abs(w_g[same_dir] - ww) <= 1e-4 * np.maximum(np.abs(ww), 1e-3 * np.abs(ww).max()) + 1e-30
+            assert close.mean() >= 0.999, (m_i, front, close.mean())
+
+
+# ------------------------------------------------------------------ closest hit
+
+def _check_hits(api, gsc, osc, o, d):
+    tri_g, t_g, _ = gsc.trace(torch.from_numpy(o.astype(np.float32)).cuda(),
+                              torch.from_numpy(d.astype(np.float32)).cuda())
+    tri_g = tri_g.cpu().numpy().astype(np.int64)   # int32 view: a miss (0xFFFFFFFF) reads as -1
+    t_g = t_g.cpu().numpy().astype(np.float64)
+    tri_o, t_o, _ = osc.intersect(o.astype(np.float32).astype(np.float64), d.astype(np.float32).astype(np.float64))
+    same = tri_g == tri_o
+    assert same.mean() >= 0.9999, (same.mean(), np.argwhere(~same)[:5].ravel())
+    hit = same & (tri_o >= 0)
+    assert hit.sum() > 0.2 * len(o)
+    rel = np.abs(t_g[hit] - t_o[hit]) / t_o[hit]
+    assert rel.max() <= 1e-4, rel.max()
+    return same.mean()
+
+
+def _tri_vertices(sc):
+    """(mesh + light triangles, 3, 3) float64 vertex array in triangle-id order."""
+    v = sc.vertices.astype(np.float64)[sc.indices.astype(np.int64)]
+    quads = []
+    for q in sc.lights.astype(np.float64):
+        p0, e1, e2 = q[0:3], q[3:6], q[6:9]
+        quads += [[p0, p0 + e1, p0 + e1 + e2], [p0, p0 + e1 + e2, p0 + e2]]
+    return np.concatenate([v, np.array(quads).reshape(-1, 3, 3)]) if quads else v
+
+
+def _camera_and_bounce_rays(sc, osc, n, seed):
+    """Camera rays of random pixels plus rays from random hit points in random directions."""
+    rng = np.random.default_rng(seed)
+    o = np.zeros((n, 3))
+    d = np.zeros((n, 3))
+    for i in range(n // 2):
+        px, py = rng.integers(0, sc.camera.width), rng.integers(0, sc.camera.height)
+        o[i], d[i] = oracle.camera_ray(sc.camera, px, py, int(rng.integers(0, 99)), 3)
+    tri, t, _ = osc.intersect(o[: n // 2], d[: n // 2])
+    hit = np.where(tri >= 0)[0]
+    rest = n - n // 2
+    pick = hit[rng.integers(0, len(hit), rest)]
+    src = o[pick] + t[pick, None] * d[pick]
+    # the geometric normal of each hit, turned towards the incoming ray: bounce rays leave
+    # a surface on the side they arrived from, as in rendering
+    vv = _tri_vertices(sc)[tri[pick]]
+    ng = np.cross(vv[:, 1] - vv[:, 0], vv[:, 2] - vv[:, 0])
+    ng /= np.linalg.norm(ng, axis=1, keepdims=True)
+    ng *= -np.sign((ng * d[pick]).sum(1, keepdims=True))
+    dd = rng.normal(size=(rest, 3))
+    dd /= np.linalg.norm(dd, axis=1, keepdims=True)
+    dd *= np.sign((dd * ng).sum(1, keepdims=True))
+    o[n // 2:] = src + ng * osc.eps
+    d[n // 2:] = dd
+    return o, d
+
+
+@pytest.mark.parametrize("which", ["cornell", "pushbutton", "heavy"])
+def test_closest_hit_parity(api, which):
+    sc, gsc, osc = {"cornell": cornell, "pushbutton": pushbutton, "heavy": heavy}[which]()
+    o, d = _camera_and_bounce_rays(sc, osc, 40000, 11)
+    _check_hits(api, gsc, osc, o, d)
+
+
+def test_closest_hit_random_soup(api):
+    from paper_2407_19977_gb300 import api as A
+    rng = np.random.default_rng(9)
+    for n_tris in (1, 2, 3, 5, 17, 64, 1000, 20000):
+        c = rng.uniform(-1, 1, (n_tris, 1, 3))
+        v = (c + rng.normal(0, 0.2 if n_tris < 100 else 0.05, (n_tris, 3, 3))).reshape(-1, 3).astype(np.float32)
+        sc = scenes.Scene("soup", v, np.arange(3 * n_tris, dtype=np.uint32).reshape(-1, 3),
+                          np.zeros(n_tris, np.uint32), scenes.diffuse((.5, .5, .5))[None],
+                          np.zeros((0, 13), np.float32), None, scenes.Camera((0, 0, -3), (0, 0, 0), (0, 1, 0), 40, 8, 8),
+                          1, 1)
+        g = A.Scene(sc)
+        osc = oracle.OracleScene(sc)
+        m = 20000
+        o = rng.uniform(-2, 2, (m, 3))
+        d = rng.uniform(-0.8, 0.8, (m, 3)) - o
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        tri_g, t_g, _ = g.trace(torch.from_numpy(o.astype(np.float32)).cuda(), torch.from_numpy(d.astype(np.float32)).cuda())
+        tri_g = tri_g.cpu().numpy().astype(np.int64)
+        tri_g = np.where(tri_g < 0, -1, tri_g)
+        tri_o, t_o, _ = osc.intersect(o.astype(np.float32).astype(np.float64), d.astype(np.float32).astype(np.float64))
+        assert (tri_g == tri_o).mean() >= 0.9999, n_tris
+        st = g.stats()
+        assert st["error_flags"] == 0 and st["n_triangles"] == n_tris
+
+
+def test_any_hit_matches_closest(api):
+    sc, gsc, osc = pushbutton()
+    o, d = _camera_and_bounce_rays(sc, osc, 20000, 12)
+    tri_c, t_c, _ = gsc.trace(torch.from_numpy(o.astype(np.float32)).cuda(), torch.from_numpy(d.astype(np.float32)).cuda())
+    t_c = t_c.cpu().numpy()
+    for tmax in (0.5, 2.0, 1e30):
+        occ, _, _ = gsc.trace(torch.from_numpy(o.astype(np.float32)).cuda(),
+                              torch.from_numpy(d.astype(np.float32)).cuda(), tmax=tmax, any_hit=True)
+        occ = occ.cpu().numpy() == 0
+        assert np.array_equal(occ, t_c < tmax)
+
+
+# ------------------------------------------------------------------ environment
+
+def test_env_sampling_parity(api):
+    sc, gsc, osc = pushbutton()
+    rng = np.random.default_rng(4)
+    n = 20000
+    u = rng.random((n, 2)).astype(np.float32)
+    d_g, p_g = gsc.env_sample(torch.from_numpy(u).cuda())
+    d_g = d_g.cpu().numpy()
+    p_g = p_g.cpu().numpy()
+    close = 0
+    for i in range(0, n, 7):
+        ok, d_o, p_o, _ = osc.env_sample(float(u[i, 0]), float(u[i, 1]))
+        assert ok
+        if np.allclose(d_g[i], d_o, atol=2e-4) and abs(p_g[i] - p_o) <= 2e-4 * p_o:
+            close += 1
+    assert close / len(range(0, n, 7)) >= 0.999
+    dirs = rng.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    pg = gsc.env_pdf(torch.from_numpy(dirs.astype(np.float32)).cuda()).cpu().numpy()
+    po = np.array([osc.env_pdf(dirs[i].astype(np.float32).astype(np.float64)) for i in range(n)])
+    assert (np.abs(pg - po) <= 1e-4 * po + 1e-12).mean() >= 0.999
+
+
+# ------------------------------------------------------------------ images
+
+def _render_pair(gsc, osc, sc, spp, crop=None, mode=0, flags=0, seed=0, max_depth=None, s0=0):
+    from paper_2407_19977_gb300 import api as A
+    cam = sc.camera
+    x0, y0, cw, ch = crop or (0, 0, cam.width, cam.height)
+    samples = torch.zeros((ch, cw, spp, 3), dtype=torch.float32, device="cuda")
+    acc = A.Accum(cw, ch)
+    acc.c.spp_done = s0
+    gsc.render(spp, max_depth=max_depth, seed=seed, accum=acc, crop=(x0, y0, cw, ch), mode=mode, flags=flags,
+               sample_out=samples)
+    torch.cuda.synchronize()
+    g_img = ((acc.sum + acc.comp * 0) / spp).cpu().numpy()
+    o_sum, o_smp, st = osc.render(spp=spp, max_depth=max_depth, seed=seed, s0=s0, crop=(x0, y0, cw, ch),
+                                  keep_samples=True, no_nee=bool(flags & 1), no_rr=bool(flags & 2))
+    return g_img, o_sum / spp, samples.cpu().numpy(), o_smp, st
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_image_parity_cornell(api, mode):
+    sc, gsc, osc = cornell()
+    g, o, gs, os_, st = _render_pair(gsc, osc, sc, sc.spp, mode=mode, max_depth=sc.max_depth)
+    diverged = (np.abs(gs - os_) > 1e-3 * (np.abs(os_) + 1e-2)).any(-1).mean()
+    assert diverged <= 1e-3, diverged
+    _image_check(g, o, f"cornell mode {mode}")
+    gst = gsc.stats()
+    assert gst["error_flags"] == 0 and gst["nan_dropped"] == 0
+
+
+@pytest.mark.parametrize("crop", [(896, 504, 128, 72), (200, 300, 128, 72), (1792, 1008, 128, 72)])
+def test_image_parity_pushbutton_crops(api, crop):
+    sc, gsc, osc = pushbutton()
+    g, o, gs, os_, st = _render_pair(gsc, osc, sc, 4, crop=crop, mode=1, max_depth=sc.max_depth, seed=3)
+    _image_check(g, o, f"pushbutton crop {crop}")
+
+
+@pytest.mark.parametrize("crop", [(900, 480, 96, 54), (1400, 700, 96, 54)])
+def test_image_parity_heavy_crops(api, crop):
+    sc, gsc, osc = heavy()
+    g, o, gs, os_, st = _render_pair(gsc, osc, sc, 2, crop=crop, mode=1, max_depth=sc.max_depth, seed=5)
+    _image_check(g, o, f"heavy crop {crop}")
+
+
+def test_full_frame_bench_configuration(api):
+    """1080p pushbutton, whole frame, one sample per pixel, wavefront: the launch the benchmark
+    times.  The oracle checks every 45th row."""
+    from paper_2407_19977_gb300 import api as A
+    sc, gsc, osc = pushbutton()
+    acc = A.Accum(sc.camera.width, sc.camera.height)
+    gsc.render(1, seed=0, accum=acc, mode=1)
+    torch.cuda.synchronize()
+    g = acc.sum.cpu().numpy()
+    o, _, st = osc.render(spp=1, seed=0, row_step=45)
+    _image_check(g[::45], o[::45], "pushbutton 1080p rows")
+
+
+def test_white_furnace_gpu(api):
+    from paper_2407_19977_gb300 import api as A
+    sc = scenes.furnace_sphere(level=3, width=48, height=48, spp=8, max_depth=6)
+    g = A.Scene(sc)
+    for mode in (1, 2):
+        acc = g.render(8, flags=1, mode=mode)
+        img = acc.image().cpu().numpy()
+        assert np.allclose(img, 1.0, atol=2e-6), (mode, img.min(), img.max())
+
+
+def test_progressive_equals_one_call(api):
+    from paper_2407_19977_gb300 import api as A
+    sc, gsc, osc = cornell()
+    for mode in (1, 2):
+        a = A.Accum(64, 64)
+        gsc.render(16, accum=a, mode=mode)
+        b = A.Accum(64, 64)
+        gsc.render(5, accum=b, mode=mode)
+        gsc.render(11, accum=b, mode=mode)
+        torch.cuda.synchronize()
+        assert a.spp_done == b.spp_done == 16
+        assert torch.equal(a.sum, b.sum) and torch.equal(a.comp, b.comp)
+
+
+def test_modes_agree_per_sample(api):
+    sc, gsc, osc = pushbutton()
+    crop = (700, 400, 96, 64)
+    outs = []
+    for mode in (1, 2):
+        s = torch.zeros((64, 96, 3, 3), dtype=torch.float32, device="cuda")
+        from paper_2407_19977_gb300 import api as A
+        gsc.render(3, accum=A.Accum(96, 64), crop=crop, mode=mode, sample_out=s, seed=2)
+        outs.append(s.cpu().numpy())
+    close = np.abs(outs[0] - outs[1]) <= 1e-4 * (np.abs(outs[1]) + 1e-3)
+    assert close.all(-1).mean() >= 0.9995
+
+
+def test_sort_by_material_does_not_change_results(api):
+    from paper_2407_19977_gb300 import api as A
+    sc, gsc, osc = pushbutton()
+    crop = (600, 300, 256, 128)
+    res = []
+    for sort in (0, 1):
+        acc = A.Accum(256, 128)
+        gsc.render(2, accum=acc, crop=crop, mode=1, sort=sort, seed=9)
+        res.append(acc.sum.clone())
+    assert torch.equal(res[0], res[1])
+
+
+def test_batch_matches_individual_renders(api):
+    from paper_2407_19977_gb300 import api as A
+    mk = [scenes.cornell_box(width=40, height=24), scenes.pushbutton_lod(3000, width=64, height=48, seed=3),
+          scenes.heavy_scene(level=2, n_instances=3, width=50, height=30, seed=4)]
+    gs = [A.Scene(s) for s in mk]
+    jobs, singles = [], []
+    for i, (s, g) in enumerate(zip(mk, gs)):
+        acc = A.Accum(s.camera.width, s.camera.height)
+        jobs.append((g, s.camera, 3 + i, 5, 100 + i, acc))
+        one = A.Accum(s.camera.width, s.camera.height)
+        g.render(3 + i, max_depth=5, seed=100 + i, accum=one, mode=2)
+        singles.append(one)
+    A.render_batch(jobs)
+    torch.cuda.synchronize()
+    for (g, cam, spp, d, seed, acc), one in zip(jobs, singles):
+        assert acc.spp_done == one.spp_done
+        assert torch.allclose(acc.sum, one.sum, rtol=1e-6, atol=1e-7)
+
+
+# ------------------------------------------------------------------ edge cases and errors
+
+def test_edge_cases(api):
+    from paper_2407_19977_gb300 import api as A
+    from paper_2407_19977_gb300 import native as N
+    # a single triangle, lit by the environment, odd frame and a ragged crop at the corner
+    v = np.array([[-1, 0, -1], [1, 0, -1], [0, 0, 1]], np.float32)
+    sc = scenes.Scene("one", v, np.array([[0, 2, 1]], np.uint32), np.zeros(1, np.uint32),
+                      scenes.diffuse((0.5, 0.5, 0.5))[None], np.zeros((0, 13), np.float32), scenes.uniform_env(1.0),
+                      scenes.Camera((0, 2, -2), (0, 0, 0), (0, 1, 0), 50, 37, 23), 3, 3)
+    g = A.Scene(sc)
+    osc = oracle.OracleScene(sc)
+    for mode in (1, 2):
+        gi, oi, _, _, _ = _render_pair(g, osc, sc, 3, crop=(30, 17, 7, 6), mode=mode)
+        _image_check(gi, oi, "single triangle crop")
+    # spp = 0 is a no-op; max_depth 0 sees emitters and the sky only
+    acc = A.Accum(37, 23)
+    g.render(0, accum=acc)
+    assert acc.spp_done == 0 and float(acc.sum.abs().sum()) == 0.0
+    g.render(2, max_depth=0, accum=acc)
+    img = acc.image().cpu().numpy()
+    assert set(np.unique(np.round(img, 6))) <= {0.0, 0.5, 1.0}  # 2 samples: sky (1) or triangle (0)
+    # errors
+    with pytest.raises(N.PtError, match="INVALID_ARG"):
+        g.render(1, crop=(30, 17, 8, 6))
+    unbuilt = A.Scene(sc, build=False)
+    with pytest.raises(N.PtError, match="NOT_BUILT"):
+        unbuilt.render(1)
+    bad = scenes.Scene("bad", v, np.array([[0, 2, 5]], np.uint32), np.zeros(1, np.uint32),
+                       scenes.diffuse((0.5, 0.5, 0.5))[None], np.zeros((0, 13), np.float32), None, sc.camera, 1, 1)
+    with pytest.raises(N.PtError, match="INVALID_ARG"):
+        A.Scene(bad, on_device=True)
+    nan = scenes.Scene("nan", v * np.float32(np.nan), sc.indices, sc.material_ids, sc.materials,
+                       sc.lights, None, sc.camera, 1, 1)
+    with pytest.raises(N.PtError, match="INVALID_ARG"):
+        A.Scene(nan, on_device=True)
+
+
+def test_stats_match_oracle_ray_counts(api):
+    sc, gsc, osc = cornell()
+    from paper_2407_19977_gb300 import api as A
+    for mode in (1, 2):
+        before = gsc.stats()
+        gsc.render(16, accum=A.Accum(64, 64), mode=mode)
+        after = gsc.stats()
+        _, _, st = osc.render(spp=16)
+        d_ext = after["ext_rays"] - before["ext_rays"]
+        d_sh = after["shadow_rays"] - before["shadow_rays"]
+        assert after["paths"] - before["paths"] == st["paths"]
+        assert abs(d_ext - st["ext_rays"]) <= 2e-4 * st["ext_rays"]
+        assert abs(d_sh - st["shadow_rays"]) <= 2e-4 * st["shadow_rays"]

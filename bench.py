@@ -35,23 +35,37 @@ if ROOT not in sys.path:
 WORKLOADS = {
     "pushbutton": "synthetic CAD pushbutton, 209,600 triangles + 2 light triangles, 1920x1080, 1 spp/step, "
                   "max depth 8, analytic sky 512x256 + 1 quad light",
+    "heavy": "16 displaced level-7 icospheres, 5,242,882 triangles, 1920x1080, 1 spp/step, max depth 12, "
+             "analytic sky 512x256",
+    "cornell512": "Cornell-style box, 36 triangles, one quad light, 512x512, 1 spp/step, max depth 8",
 }
 NODE_BYTES = 80      # compressed 8-wide BVH node
 TRI_BYTES = 48       # triangle record
 RAY_BYTES = 32       # ray in (origin + direction float4 pair)
 HIT_BYTES = 16       # hit record out
+# algorithmic FP32 operations of the traversal: one child box test = 6 decode FMA + 6 sub +
+# 6 mul + 12 min/max + 1 compare ~ 30; a node tests its 8 slots; one watertight triangle test
+# ~ 50 (9 sub, 12 shear, 9 edge products/differences, sign tests, det, T, divide, range)
+OPS_PER_NODE = 8 * 30
+OPS_PER_TRI = 50
+# FP32 lane peak: 152 SMs x 128 FP32 lanes x 2.07 GHz (an FMA counted as one operation)
+SM_COUNT, FP32_LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.07
+ALU_PEAK_GOPS = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_GHZ
 
 
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pushbutton", choices=sorted(WORKLOADS))
     ap.add_argument("--mode", default="wavefront", choices=["auto", "wavefront", "megakernel"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    ap.add_argument("--study", default=None, choices=[None, "nrc"],
+                    help="nrc: relMSE vs time, radiance cache against the plain tracer")
+    ap.add_argument("--ref-spp", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -153,6 +167,10 @@ def _make_workload(name):
     from paper_2407_19977_gb300 import scenes
     if name == "pushbutton":
         return scenes.pushbutton()
+    if name == "heavy":
+        return scenes.heavy_scene(level=7)
+    if name == "cornell512":
+        return scenes.cornell_box(width=512, height=512, spp=1, max_depth=8)
     raise ValueError(name)
 
 
@@ -264,6 +282,7 @@ def run_ours(args, world, rank, local):
                                              "shadow_nodes", "shadow_tris")}
     trace_bytes_step = (cnt["trace_nodes"] * NODE_BYTES + cnt["trace_tris"] * TRI_BYTES +
                         cnt["ext_rays"] * (RAY_BYTES + HIT_BYTES))
+    trace_ops_step = cnt["trace_nodes"] * OPS_PER_NODE + cnt["trace_tris"] * OPS_PER_TRI
     # timed region
     kernel_ms = (N.f32 * 6)()
     kernel_launches = (N.u32 * 6)()
@@ -319,7 +338,9 @@ def run_ours(args, world, rank, local):
     peaks, peak_src = _peaks()
     trace_ms = kms["trace"]
     achieved_gbs = trace_bytes_step / (trace_ms * 1e-3) / 1e9 if trace_ms > 0 else None
+    achieved_gops = trace_ops_step / (trace_ms * 1e-3) / 1e9 if trace_ms > 0 else None
     traffic = _recorded_traffic("trace")
+    trace_launches = max(kl["trace"], 1)
     result = {
         "metric": "Mrays/s at 1080p (pushbutton)",
         "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -334,13 +355,17 @@ def run_ours(args, world, rank, local):
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_val, "unit": "Mrays/s", "h2d_bytes_per_step": 48 + 8,
                 "d2h_bytes_per_step": W * H * 3 * 4},
-        "roofline": {"bound": "hbm", "kernel": "k_wf_trace (closest hit)",
-                     "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved_gbs / peaks["hbm_gbs"] if achieved_gbs else None,
-                     "traffic": traffic, "peak_source": peak_src,
-                     "algorithmic_bytes_per_step": trace_bytes_step,
+        "roofline": {"bound": "alu", "kernel": "k_wf_trace (closest hit)",
+                     "achieved": achieved_gops, "peak": ALU_PEAK_GOPS, "unit": "GOP/s",
+                     "frac": achieved_gops / ALU_PEAK_GOPS if achieved_gops else None,
+                     "traffic": traffic,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (recipe unit counts and clock)",
+                     "algorithmic_ops_per_launch": trace_ops_step / trace_launches,
+                     "launch_ms": trace_ms / trace_launches,
                      "per_ray": {"nodes": cnt["trace_nodes"] / max(cnt["ext_rays"], 1),
-                                 "tris": cnt["trace_tris"] / max(cnt["ext_rays"], 1)}},
+                                 "tris": cnt["trace_tris"] / max(cnt["ext_rays"], 1)},
+                     "hbm_view": {"algorithmic_bytes_per_step": trace_bytes_step, "achieved_gbs": achieved_gbs,
+                                  "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src}},
         "clocks": clocks.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -352,9 +377,81 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def _relmse(img, ref, eps=1e-2):
+    """Mean over pixels and channels of (x - ref)^2 / (ref^2 + eps)."""
+    d = img - ref
+    return float((d * d / (ref * ref + eps)).mean())
+
+
+def run_nrc_study(args, local):
+    """relMSE against a high-spp plain reference as a function of device time, for the plain
+    tracer and for the radiance-cache tracer (trained online every frame)."""
+    import torch
+    from paper_2407_19977_gb300 import api
+    from paper_2407_19977_gb300 import native as N
+    torch.cuda.set_device(local)
+    sc = _make_workload(args.workload)
+    W, H = sc.camera.width, sc.camera.height
+    scene = api.Scene(sc)
+    stream = torch.cuda.current_stream()
+    ref = api.Accum(W, H)
+    chunk = 64
+    for i in range(args.ref_spp // chunk):
+        scene.render(chunk, seed=777, accum=ref, mode=N.PT_MODE_WAVEFRONT)
+    torch.cuda.synchronize()
+    ref_img = ref.image()
+    marks = [1, 2, 4, 8, 16, 32, 64, 128, 256]
+    curves = {}
+    lo = sc.vertices.min(0) - 0.05
+    hi = sc.vertices.max(0) + 0.05
+    for kind in ("plain", "nrc"):
+        net = api.Nrc(seed=5, box=(tuple(map(float, lo)), tuple(map(float, hi)))) if kind == "nrc" else None
+        acc = api.Accum(W, H)
+        t_ms = 0.0
+        pts = []
+        for f in range(1, marks[-1] + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            scene.render(1, seed=0, accum=acc, mode=N.PT_MODE_WAVEFRONT, nrc=net, nrc_train=net is not None)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            if f in marks:
+                pts.append({"spp": f, "ms": t_ms, "relmse": _relmse(acc.image(), ref_img)})
+        curves[kind] = pts
+
+    def time_to(curve, target):
+        prev = None
+        for p in curve:
+            if p["relmse"] <= target:
+                if prev is None:
+                    return p["ms"]
+                # log-log interpolation between the marks around the crossing
+                import math as m
+                a, b = m.log(prev["relmse"]), m.log(p["relmse"])
+                w = (m.log(target) - a) / (b - a) if b != a else 1.0
+                return m.exp(m.log(prev["ms"]) + w * (m.log(p["ms"]) - m.log(prev["ms"])))
+            prev = p
+        return None
+
+    out = {"study": "nrc_equal_time", "workload": WORKLOADS[args.workload], "ref_spp": args.ref_spp,
+           "relmse_eps": 1e-2, "curves": curves}
+    for spp in (16, 64):
+        target = next(p["relmse"] for p in curves["plain"] if p["spp"] == spp)
+        tp = next(p["ms"] for p in curves["plain"] if p["spp"] == spp)
+        tn = time_to(curves["nrc"], target)
+        out[f"at_plain_{spp}spp"] = {"relmse": target, "plain_ms": tp, "nrc_ms": tn,
+                                     "speedup": (tp / tn) if tn else None}
+    print(json.dumps(out))
+
+
 def main():
     args = _args()
     world, rank, local = _dist()
+    if args.study == "nrc":
+        if rank == 0:
+            run_nrc_study(args, local)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

@@ -303,14 +303,24 @@ typedef struct {
 } pt_nrc_opts;
 
 /* Query layout for pt_nrc_infer / training samples (DEVICE arrays of float[n*16]):
- * pos[3], dir[3], normal[3], roughness, target_rgb[3] (training only), pad[3]. */
+ * pos[3] (world space, normalised by the opts box), dir[3], normal[3], roughness,
+ * target_rgb[3] (training only), pad[3].
+ * pt_nrc_train: one Adam step per `batch` samples.  pt_nrc_infer: out_rgb is DEVICE
+ * float[n*4] (RGB + one unused column).  pt_nrc_gradients: loss gradients of one batch
+ * without an update, into DEVICE buffers (MLP: same layout as pt_nrc_params(0); grid:
+ * same layout as pt_nrc_params(1); either may be NULL). */
 pt_status pt_nrc_create(const pt_nrc_opts* opts, void* cuda_stream, pt_nrc** out);
 pt_status pt_nrc_train(pt_nrc* nrc, const float* samples, uint32_t n, void* cuda_stream);
 pt_status pt_nrc_infer(pt_nrc* nrc, const float* queries, uint32_t n, float* out_rgb,
                        void* cuda_stream);
+pt_status pt_nrc_gradients(pt_nrc* nrc, const float* samples, uint32_t n, float* dw_out,
+                           float* dgrid_out, void* cuda_stream);
 /* Parameter access for tests and checkpoints: FP32 master copies (DEVICE float arrays).
- * which = 0: MLP weights (layer-major, each [out][in]), 1: hash-grid table. */
+ * which = 0: MLP weights (4 hidden layers [64][64] then the output layer padded to
+ * [16][64], each [out][in]), 1: hash-grid table [levels][2^log2_table][2].  After writing
+ * through the pointer call pt_nrc_commit to refresh the FP16 copies the kernels read. */
 pt_status pt_nrc_params(pt_nrc* nrc, int which, float** ptr, uint64_t* count);
+pt_status pt_nrc_commit(pt_nrc* nrc, void* cuda_stream);
 /* Last training loss (mean relative L2 over the most recent step; synchronises). */
 pt_status pt_nrc_last_loss(pt_nrc* nrc, float* loss);
 void pt_nrc_destroy(pt_nrc* nrc);

@@ -116,7 +116,7 @@ class Scene:
 
     def render(self, spp, max_depth=None, seed=0, accum=None, camera=None, crop=None, flags=0,
                mode=N.PT_MODE_AUTO, wave_paths=0, sort=-1, sample_out=None, block_size=0, stream=None,
-               kernel_ms=None, kernel_launches=None):
+               kernel_ms=None, kernel_launches=None, nrc=None, nrc_train=False):
         cam = camera or self.desc.camera
         max_depth = self.desc.max_depth if max_depth is None else max_depth
         if crop is None:
@@ -128,6 +128,9 @@ class Scene:
         o.crop_x0, o.crop_y0, o.flags, o.mode = x0, y0, flags, mode
         o.wave_paths, o.sort_by_material, o.block_size = wave_paths, sort, block_size
         o.sample_out = _ptr(sample_out) if sample_out is not None else None
+        if nrc is not None:
+            o.nrc = nrc.h
+            o.nrc_train = 1 if nrc_train else 0
         if kernel_ms is not None:
             o.kernel_ms = C.cast(kernel_ms, C.POINTER(N.f32))
         if kernel_launches is not None:
@@ -229,3 +232,68 @@ def render_batch(jobs, tile_pixels=0, blocks_per_sm=0, stream=None):
 
 def launch_count() -> int:
     return int(N.load().pt_launch_count())
+
+
+class _DevArray:
+    """__cuda_array_interface__ view of library-owned device memory (no copy)."""
+
+    def __init__(self, ptr, n, typestr="<f4"):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+class Nrc:
+    """Neural radiance cache (hash grid + 64-wide MLP) owned by the library."""
+
+    def __init__(self, n_levels=16, log2_table=19, base_resolution=16, per_level_scale=0.0, learning_rate=1e-2,
+                 batch=16384, seed=0, box=((0.0, 0.0, 0.0), (1.0, 1.0, 1.0)), stream=None):
+        o = N.pt_nrc_opts()
+        o.n_levels, o.log2_table, o.base_resolution = n_levels, log2_table, base_resolution
+        o.per_level_scale, o.n_hidden, o.learning_rate, o.batch, o.seed = per_level_scale, 4, learning_rate, batch, seed
+        o.scene_min[:] = [float(x) for x in box[0]]
+        o.scene_max[:] = [float(x) for x in box[1]]
+        self.opts = o
+        h = C.c_void_p()
+        N.call("pt_nrc_create", C.byref(o), _stream_handle(stream), C.byref(h))
+        self.h = h
+        self.n_levels, self.log2_table = n_levels, log2_table
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None and self.h.value:
+                N.load().pt_nrc_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def params(self, which: int) -> torch.Tensor:
+        """Live FP32 view of the MLP weights (0) or the grid table (1); call commit() after writing."""
+        p, n = C.c_void_p(), N.u64()
+        N.call("pt_nrc_params", self.h, which, C.byref(p), C.byref(n))
+        return torch.as_tensor(_DevArray(p.value, n.value), device="cuda")
+
+    def commit(self, stream=None):
+        N.call("pt_nrc_commit", self.h, _stream_handle(stream))
+
+    def infer(self, queries: torch.Tensor, stream=None) -> torch.Tensor:
+        n = queries.shape[0]
+        out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        N.call("pt_nrc_infer", self.h, _ptr(queries.contiguous()), n, _ptr(out), _stream_handle(stream))
+        return out[:, :3]
+
+    def train(self, samples: torch.Tensor, stream=None):
+        N.call("pt_nrc_train", self.h, _ptr(samples.contiguous()), samples.shape[0], _stream_handle(stream))
+
+    def gradients(self, samples: torch.Tensor, stream=None):
+        nw = self.params(0).numel()
+        ng = self.params(1).numel()
+        dw = torch.empty(nw, dtype=torch.float32, device="cuda")
+        dg = torch.empty(ng, dtype=torch.float32, device="cuda")
+        N.call("pt_nrc_gradients", self.h, _ptr(samples.contiguous()), samples.shape[0], _ptr(dw), _ptr(dg),
+               _stream_handle(stream))
+        return dw, dg
+
+    def last_loss(self) -> float:
+        v = N.f32()
+        N.call("pt_nrc_last_loss", self.h, C.byref(v))
+        return float(v.value)

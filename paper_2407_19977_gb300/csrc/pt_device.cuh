@@ -533,21 +533,19 @@ struct HitRec {
     uint32_t tri;   // index into the leaf-ordered triangle array, PT_NO_HIT on a miss
 };
 
-__device__ __forceinline__ void cswap(uint64_t& a, uint64_t& b) {
-    const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
-    a = lo;
-    b = hi;
-}
-
 // Node visits and triangle tests of one traversal (counting variant only).
 struct TravCount {
     uint32_t nodes, tris;
 };
 
 // Closest hit in (0, tmax); equal t resolved towards the lower original triangle id.
+// Per node: the eight box tests are unrolled; the nearest internal child is descended
+// into and the other hit children go on the stack; leaf children are collected in a bit
+// mask and intersected afterwards by one loop, so the triangle test exists once in the
+// code (small instruction footprint, less divergence).
 template <bool COUNT>
-static __device__ __noinline__ void trace_closest_t(const DScene& S, float3 o, float3 d, float tmax, HitRec& h,
-                                                    TravCount& tc) {
+__device__ __forceinline__ void trace_closest_t(const DScene& S, float3 o, float3 d, float tmax, HitRec& h,
+                                                TravCount& tc) {
     h.t = tmax;
     h.tri = PT_NO_HIT;
     h.u = h.v = 0.0f;
@@ -564,71 +562,68 @@ static __device__ __noinline__ void trace_closest_t(const DScene& S, float3 o, f
         if (budget-- == 0u) { atomicOr(S.err, 4u); h.tri = PT_NO_HIT; return; }
         const NodeView v = load_node(S.nodes, node);
         if (COUNT) tc.nodes++;
-        uint64_t key[8];
+        uint32_t leafmask = 0u;
+        uint32_t near_node = PT_NO_HIT;
+        float near_t = __int_as_float(0x7f800000);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            key[i] = ~0ull;
-            const uint32_t meta = byte_of(v.meta_lo, v.meta_hi, i);
-            if (meta == 0u) continue;
+            if (byte_of(v.meta_lo, v.meta_hi, i) == 0u) continue;
             const float tn = child_hit(v, tr, i, 0.0f, h.t);
             if (!(tn >= 0.0f && tn <= h.t)) continue;
             if ((v.imask >> i) & 1u) {
-                const uint32_t rank = __popc(v.imask & ((1u << i) - 1u));
-                key[i] = ((uint64_t)__float_as_uint(fmaxf(tn, 0.0f)) << 32) | (uint64_t)(v.child_base + rank);
+                const uint32_t c = v.child_base + __popc(v.imask & ((1u << i) - 1u));
+                uint32_t push_node = c;
+                float push_t = tn;
+                if (tn < near_t) {
+                    push_node = near_node;
+                    push_t = near_t;
+                    near_node = c;
+                    near_t = tn;
+                }
+                if (push_node != PT_NO_HIT) {
+                    if (sp >= PT_STACK) { atomicOr(S.err, 1u); return; }
+                    stack[sp++] = make_uint2(push_node, __float_as_uint(push_t));
+                }
             } else {
-                const uint32_t first = v.tri_base + (meta & 31u);
-                const uint32_t cnt = meta >> 5;
-                if (COUNT) tc.tris += cnt;
-                for (uint32_t k = 0; k < cnt; ++k) {
-                    const uint32_t ti = first + k;
-                    const float4 a = __ldg(S.tris + 3u * ti), b = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
-                    float t, u, w;
-                    if (tri_hit(wr, xyz(a), xyz(b), xyz(c), tmax, t, u, w)) {
-                        const uint32_t orig = __float_as_uint(a.w);
-                        if (t < h.t || (t == h.t && orig < best_orig)) {
-                            h.t = t; h.u = u; h.v = w; h.tri = ti; best_orig = orig;
-                        }
+                leafmask |= 1u << i;
+            }
+        }
+        while (leafmask) {
+            const int i = __ffs(leafmask) - 1;
+            leafmask &= leafmask - 1u;
+            const uint32_t meta = byte_of(v.meta_lo, v.meta_hi, i);
+            const uint32_t first = v.tri_base + (meta & 31u);
+            const uint32_t cnt = meta >> 5;
+            if (COUNT) tc.tris += cnt;
+            for (uint32_t k = 0; k < cnt; ++k) {
+                const uint32_t ti = first + k;
+                const float4 a = __ldg(S.tris + 3u * ti), b = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
+                float t, u, w;
+                if (tri_hit(wr, xyz(a), xyz(b), xyz(c), tmax, t, u, w)) {
+                    const uint32_t orig = __float_as_uint(a.w);
+                    if (t < h.t || (t == h.t && orig < best_orig)) {
+                        h.t = t; h.u = u; h.v = w; h.tri = ti; best_orig = orig;
                     }
                 }
             }
         }
-        // sorting network (19 compare-exchanges) orders internal children near to far
-        cswap(key[0], key[1]); cswap(key[2], key[3]); cswap(key[4], key[5]); cswap(key[6], key[7]);
-        cswap(key[0], key[2]); cswap(key[1], key[3]); cswap(key[4], key[6]); cswap(key[5], key[7]);
-        cswap(key[1], key[2]); cswap(key[5], key[6]); cswap(key[0], key[4]); cswap(key[3], key[7]);
-        cswap(key[1], key[5]); cswap(key[2], key[6]);
-        cswap(key[1], key[4]); cswap(key[3], key[6]);
-        cswap(key[2], key[4]); cswap(key[3], key[5]);
-        cswap(key[3], key[4]);
-        bool have_next = false;
-#pragma unroll
-        for (int i = 7; i >= 0; --i) {
-            if (key[i] == ~0ull) continue;
-            const float tn = __uint_as_float((uint32_t)(key[i] >> 32));
-            if (tn > h.t) continue;
-            if (i == 0) {
-                node = (uint32_t)key[i];
-                have_next = true;
-            } else {
-                if (sp >= PT_STACK) { atomicOr(S.err, 1u); return; }
-                stack[sp++] = make_uint2((uint32_t)key[i], (uint32_t)(key[i] >> 32));
-            }
+        if (near_node != PT_NO_HIT && near_t <= h.t) {
+            node = near_node;
+            continue;
         }
-        if (!have_next) {
-            // the nearest hit child may have been pruned: take it from the stack instead
-            bool found = false;
-            while (sp > 0) {
-                const uint2 e = stack[--sp];
-                if (__uint_as_float(e.y) <= h.t) { node = e.x; found = true; break; }
-            }
-            if (!found) return;
+        // pop the next child whose entry distance is still within the closest hit
+        bool found = false;
+        while (sp > 0) {
+            const uint2 e = stack[--sp];
+            if (__uint_as_float(e.y) <= h.t) { node = e.x; found = true; break; }
         }
+        if (!found) return;
     }
 }
 
 // Any hit in (0, tmax): occlusion test for shadow rays.
 template <bool COUNT>
-static __device__ __noinline__ bool trace_any_t(const DScene& S, float3 o, float3 d, float tmax, TravCount& tc) {
+__device__ __forceinline__ bool trace_any_t(const DScene& S, float3 o, float3 d, float tmax, TravCount& tc) {
     if (S.n_nodes == 0) return false;
     const WRay wr = make_wray(o, d);
     const TravRay tr = make_trav(o, d);
@@ -640,37 +635,41 @@ static __device__ __noinline__ bool trace_any_t(const DScene& S, float3 o, float
         if (budget-- == 0u) { atomicOr(S.err, 4u); return false; }
         const NodeView v = load_node(S.nodes, node);
         if (COUNT) tc.nodes++;
-        int n_int = 0;
-        uint32_t first_int = 0;
+        uint32_t leafmask = 0u;
+        uint32_t next = PT_NO_HIT;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const uint32_t meta = byte_of(v.meta_lo, v.meta_hi, i);
-            if (meta == 0u) continue;
+            if (byte_of(v.meta_lo, v.meta_hi, i) == 0u) continue;
             const float tn = child_hit(v, tr, i, 0.0f, tmax);
             if (!(tn >= 0.0f && tn <= tmax)) continue;
             if ((v.imask >> i) & 1u) {
                 const uint32_t c = v.child_base + __popc(v.imask & ((1u << i) - 1u));
-                if (n_int == 0) {
-                    first_int = c;
+                if (next == PT_NO_HIT) {
+                    next = c;
                 } else {
                     if (sp >= PT_STACK) { atomicOr(S.err, 1u); return true; }
                     stack[sp++] = c;
                 }
-                ++n_int;
             } else {
-                const uint32_t first = v.tri_base + (meta & 31u);
-                const uint32_t cnt = meta >> 5;
-                for (uint32_t k = 0; k < cnt; ++k) {
-                    const uint32_t ti = first + k;
-                    if (COUNT) tc.tris++;
-                    const float4 a = __ldg(S.tris + 3u * ti), b = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
-                    float t, u, w;
-                    if (tri_hit(wr, xyz(a), xyz(b), xyz(c), tmax, t, u, w)) return true;
-                }
+                leafmask |= 1u << i;
             }
         }
-        if (n_int > 0) {
-            node = first_int;
+        while (leafmask) {
+            const int i = __ffs(leafmask) - 1;
+            leafmask &= leafmask - 1u;
+            const uint32_t meta = byte_of(v.meta_lo, v.meta_hi, i);
+            const uint32_t first = v.tri_base + (meta & 31u);
+            const uint32_t cnt = meta >> 5;
+            for (uint32_t k = 0; k < cnt; ++k) {
+                const uint32_t ti = first + k;
+                if (COUNT) tc.tris++;
+                const float4 a = __ldg(S.tris + 3u * ti), b = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
+                float t, u, w;
+                if (tri_hit(wr, xyz(a), xyz(b), xyz(c), tmax, t, u, w)) return true;
+            }
+        }
+        if (next != PT_NO_HIT) {
+            node = next;
         } else {
             if (sp == 0) return false;
             node = stack[--sp];
@@ -678,11 +677,12 @@ static __device__ __noinline__ bool trace_any_t(const DScene& S, float3 o, float
     }
 }
 
-__device__ __forceinline__ void trace_closest(const DScene& S, float3 o, float3 d, float tmax, HitRec& h) {
+// out-of-line entry points keep the megakernel's code and registers in check
+static __device__ __noinline__ void trace_closest(const DScene& S, float3 o, float3 d, float tmax, HitRec& h) {
     TravCount tc;
     trace_closest_t<false>(S, o, d, tmax, h, tc);
 }
-__device__ __forceinline__ bool trace_any(const DScene& S, float3 o, float3 d, float tmax) {
+static __device__ __noinline__ bool trace_any(const DScene& S, float3 o, float3 d, float tmax) {
     TravCount tc;
     return trace_any_t<false>(S, o, d, tmax, tc);
 }
@@ -795,13 +795,23 @@ struct ShadeOut {
     bool rr_end;
 };
 
+// Vertex hook of the plain tracer: never ends a path.
+struct NoHook {
+    __device__ __forceinline__ bool operator()(float3, float3, float3, const DMat&, const PathState&, uint32_t) {
+        return false;
+    }
+};
+
 // Handles the hit (or miss) of the ray (o, d) at path vertex k: emission with MIS, the
 // depth limit, next-event estimation (returned as a shadow ray whose contribution is
 // added if unoccluded), BSDF sampling and Russian roulette.  Returns SHADE_CONTINUE with
-// the next ray, or SHADE_END.
-__device__ __forceinline__ int shade_vertex(const DScene& S, const HitRec& h, float3 o, float3 d, uint32_t k,
-                                            uint32_t max_depth, uint32_t flags, const VertexRng& rng,
-                                            PathState& ps, ShadeOut& out) {
+// the next ray, or SHADE_END.  `hook` sees every scattering vertex below the depth limit
+// (position, direction to the previous vertex, shading normal, material, path state) and
+// may end the path there (the radiance cache does).
+template <class Hook>
+__device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, float3 o, float3 d, uint32_t k,
+                                              uint32_t max_depth, uint32_t flags, const VertexRng& rng,
+                                              PathState& ps, ShadeOut& out, Hook& hook) {
     out.has_shadow = false;
     out.rr_end = false;
     const bool nee = !(flags & FLAG_NO_NEE);
@@ -845,6 +855,7 @@ __device__ __forceinline__ int shade_vertex(const DScene& S, const HitRec& h, fl
     float3 tt, bb;
     onb(n, tt, bb);
     const float3 wo = mk3(dot3(wo_w, tt), dot3(wo_w, bb), dot3(wo_w, n));
+    if (hook(x, wo_w, n, M, ps, k)) return SHADE_END;
     Closure C;
     closure_setup(C, M, front, wo.z);
 
@@ -917,6 +928,18 @@ __device__ __forceinline__ int shade_vertex(const DScene& S, const HitRec& h, fl
     out.next_d = norm3(wi_w);
     ps.prev_pdf = bs.delta ? -1.0f : bs.pdf;
     return SHADE_CONTINUE;
+}
+
+__device__ __forceinline__ int shade_vertex(const DScene& S, const HitRec& h, float3 o, float3 d, uint32_t k,
+                                            uint32_t max_depth, uint32_t flags, const VertexRng& rng,
+                                            PathState& ps, ShadeOut& out) {
+    NoHook nh;
+    return shade_vertex_h(S, h, o, d, k, max_depth, flags, rng, ps, out, nh);
+}
+
+// "diffuse-ish" measure of a vertex: diffuse lobes count as roughness 1
+__device__ __forceinline__ float effective_roughness(const DMat& M) {
+    return M.metalness * M.spec_rough + (1.0f - M.metalness) * ((1.0f - M.trans_weight) + M.trans_weight * M.spec_rough);
 }
 
 // ------------------------------------------------------------------ Kahan accumulation

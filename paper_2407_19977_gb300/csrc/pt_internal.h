@@ -60,6 +60,16 @@ struct WaveBuffers {
     uint32_t* keys = nullptr;    // per slot sort key
     uint32_t* counters = nullptr;  // [0..1] queue sizes, [2] shadow size, [3..6] heads, [8..] buckets
     size_t bytes = 0;
+    // radiance-cache buffers (allocated on the first cache render)
+    uint32_t nrc_capacity = 0, train_slots = 0, rec_per_path = 0, sample_cap = 0;
+    uint32_t* aux = nullptr;
+    float* nrc_q = nullptr;
+    float* nrc_out = nullptr;
+    uint32_t* nrc_counters = nullptr;
+    float* train_rec = nullptr;
+    uint32_t* train_nv = nullptr;
+    uint32_t* train_id = nullptr;
+    float* train_samples = nullptr;
 };
 
 struct pt_scene {
@@ -91,6 +101,7 @@ struct pt_scene {
     WaveBuffers wave;
     cudaStream_t last_stream = nullptr;
     uint64_t launches = 0;
+    uint64_t nrc_queries_host = 0, nrc_samples_host = 0;
 
     DScene view() const {
         DScene s;
@@ -121,6 +132,9 @@ pt_status pt_build_env_impl(pt_scene* s, cudaStream_t st);
 
 // implemented in pt_render.cu
 pt_status pt_free_wave(WaveBuffers& w);
+
+// implemented in pt_nrc.cu: cache forward pass for the renderer (outputs 4 floats per query)
+pt_status pt_nrc_render_infer(pt_nrc* N, const float* queries, uint32_t n, float* out4, cudaStream_t st);
 
 inline DCam to_dcam(const pt_camera& c) {
     DCam d;

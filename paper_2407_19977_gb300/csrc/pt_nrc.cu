@@ -1,13 +1,682 @@
-// pt_nrc.cu -- neural radiance cache entry points (placeholder until the cache kernels land).
+// pt_nrc.cu -- neural radiance cache: multiresolution hash-grid encoding + 64-wide MLP
+// (4 hidden ReLU layers, no biases), trained online with Adam on a relative L2 loss.
+// The paper names neural radiance caching as future work to cut the samples per pixel
+// (Sec. 6.1); the cache here is the one the path tracer queries at a path's second
+// diffuse-ish vertex.
+//
+// Tensor cores: every layer is a [rows x 64] x [64 x 64] product on mma.sync m16n8k16
+// (FP16 operands, FP32 accumulation).  A warp owns 16 rows; the FP32 accumulator fragment
+// of one layer is exactly the FP16 A-operand fragment of the next, so activations stay in
+// registers across layers (forward) and across the backward chain.
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "pt_internal.h"
 
-extern "C" pt_status pt_nrc_create(const pt_nrc_opts*, void*, pt_nrc** out) {
-    if (out) *out = nullptr;
-    pt_set_error("radiance cache not available in this build");
-    return PT_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int W = 64;          // layer width
+constexpr int N_HIDDEN = 4;    // hidden layers
+constexpr int OUT_PAD = 16;    // output rows padded to one mma n-pair
+constexpr int SROW = 72;       // padded shared-memory row (halves): conflict-free B loads
+constexpr uint32_t HASH_P1 = 2654435761u, HASH_P2 = 805459861u;
+constexpr int QSTRIDE = 16;    // floats per query / sample record
+constexpr int N_WEIGHTS = N_HIDDEN * W * W + OUT_PAD * W;
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
-extern "C" pt_status pt_nrc_train(pt_nrc*, const float*, uint32_t, void*) { return PT_ERR_UNSUPPORTED; }
-extern "C" pt_status pt_nrc_infer(pt_nrc*, const float*, uint32_t, float*, void*) { return PT_ERR_UNSUPPORTED; }
-extern "C" pt_status pt_nrc_params(pt_nrc*, int, float**, uint64_t*) { return PT_ERR_UNSUPPORTED; }
-extern "C" pt_status pt_nrc_last_loss(pt_nrc*, float*) { return PT_ERR_UNSUPPORTED; }
-extern "C" void pt_nrc_destroy(pt_nrc*) {}
+
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack_hh(__half lo, __half hi) {
+    __half2 h = __halves2half2(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 unpack_h2(uint32_t v) {
+    __half2 h = *reinterpret_cast<const __half2*>(&v);
+    return __half22float2(h);
+}
+
+struct GridDesc {
+    const __half* table;     // L x T x 2 (FP16 copy used by lookups)
+    float* grad;             // L x T x 2 (FP32)
+    const uint32_t* res;     // L resolutions
+    uint32_t L, T;
+    float3 lo, inv_ext;
+};
+
+// corner index of level l for integer cell coordinates (dense while (N+1)^3 <= T, else hashed)
+__device__ __forceinline__ uint32_t corner_index(uint32_t cx, uint32_t cy, uint32_t cz, uint32_t res, uint32_t T) {
+    const uint32_t n1 = res + 1;
+    if ((uint64_t)n1 * n1 * n1 <= T) return cx + n1 * (cy + n1 * cz);
+    const uint32_t h = cx ^ (cy * HASH_P1) ^ (cz * HASH_P2);
+    return h & (T - 1u);
+}
+
+__device__ __forceinline__ float3 pos01(const GridDesc& G, const float* q) {
+    return mk3(fminf(fmaxf((q[0] - G.lo.x) * G.inv_ext.x, 0.0f), 1.0f),
+               fminf(fmaxf((q[1] - G.lo.y) * G.inv_ext.y, 0.0f), 1.0f),
+               fminf(fmaxf((q[2] - G.lo.z) * G.inv_ext.z, 0.0f), 1.0f));
+}
+
+// one thread per (query, level): interpolated features of that level -> X[q][2l..2l+1];
+// the same thread writes columns 32 + 2l, 33 + 2l of the non-grid part
+__global__ void k_encode(GridDesc G, const float* __restrict__ queries, uint32_t n, __half* __restrict__ X) {
+    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t q = gid / G.L, l = gid % G.L;
+    if (q >= n) return;
+    const float* rec = queries + (size_t)QSTRIDE * q;
+    const float3 p = pos01(G, rec);
+    const uint32_t res = G.res[l];
+    const float fx = p.x * res, fy = p.y * res, fz = p.z * res;
+    const uint32_t cx = min((uint32_t)fx, res - 1), cy = min((uint32_t)fy, res - 1), cz = min((uint32_t)fz, res - 1);
+    const float rx = fx - cx, ry = fy - cy, rz = fz - cz;
+    const __half2* tab = reinterpret_cast<const __half2*>(G.table) + (size_t)l * G.T;
+    float f0 = 0.0f, f1 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+        const float w = (ox ? rx : 1.0f - rx) * (oy ? ry : 1.0f - ry) * (oz ? rz : 1.0f - rz);
+        const float2 v = __half22float2(tab[corner_index(cx + ox, cy + oy, cz + oz, res, G.T)]);
+        f0 += w * v.x;
+        f1 += w * v.y;
+    }
+    __half* row = X + (size_t)W * q;
+    row[2 * l] = __float2half_rn(f0);
+    row[2 * l + 1] = __float2half_rn(f1);
+    // non-grid inputs: direction, normal, roughness, a constant 1, then zeros
+    const uint32_t g0 = 2 * G.L;
+    for (uint32_t c = g0 + 2 * l; c < g0 + 2 * l + 2 && c < (uint32_t)W; ++c) {
+        const uint32_t k = c - g0;
+        float v = 0.0f;
+        if (k < 3) v = rec[3 + k];
+        else if (k < 6) v = rec[6 + (k - 3)];
+        else if (k == 6) v = rec[9];
+        else if (k == 7) v = 1.0f;
+        row[c] = __float2half_rn(v);
+    }
+    if (l == 0)
+        for (uint32_t c = g0 + 2 * G.L; c < (uint32_t)W; ++c) row[c] = __float2half_rn(0.0f);
+}
+
+// grid gradient: recompute the corners and scatter dL/dfeature (FP32 atomics)
+__global__ void k_grid_backward(GridDesc G, const float* __restrict__ samples, uint32_t n, const float* __restrict__ dX,
+                                float scale) {
+    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t q = gid / G.L, l = gid % G.L;
+    if (q >= n) return;
+    const float3 p = pos01(G, samples + (size_t)QSTRIDE * q);
+    const uint32_t res = G.res[l];
+    const float fx = p.x * res, fy = p.y * res, fz = p.z * res;
+    const uint32_t cx = min((uint32_t)fx, res - 1), cy = min((uint32_t)fy, res - 1), cz = min((uint32_t)fz, res - 1);
+    const float rx = fx - cx, ry = fy - cy, rz = fz - cz;
+    const float g0 = dX[(size_t)2 * G.L * q + 2 * l] * scale, g1 = dX[(size_t)2 * G.L * q + 2 * l + 1] * scale;
+    float* gr = G.grad + (size_t)l * G.T * 2;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+        const float w = (ox ? rx : 1.0f - rx) * (oy ? ry : 1.0f - ry) * (oz ? rz : 1.0f - rz);
+        const uint32_t idx = corner_index(cx + ox, cy + oy, cz + oz, res, G.T);
+        atomicAdd(gr + 2 * idx, w * g0);
+        atomicAdd(gr + 2 * idx + 1, w * g1);
+    }
+}
+
+// ---- fused MLP forward: one warp per 16 rows, weights in padded shared memory ----
+__device__ __forceinline__ void load_weights_smem(__half* sw, const __half* __restrict__ Wg) {
+    for (int i = threadIdx.x; i < (N_HIDDEN * W + OUT_PAD) * W; i += blockDim.x) {
+        const int r = i / W, c = i % W;
+        sw[r * SROW + c] = Wg[i];
+    }
+}
+
+// A fragment of k-tile kt for rows r0+g, r0+g+8 of a row-major [n x 64] FP16 matrix
+__device__ __forceinline__ void load_afrag(uint32_t (&a)[4], const __half* M, uint32_t n, uint32_t r0, int kt, int g, int t) {
+    const uint32_t ra = r0 + g, rb = r0 + g + 8;
+    const int c = 16 * kt + 2 * t;
+    a[0] = ra < n ? *reinterpret_cast<const uint32_t*>(M + (size_t)W * ra + c) : 0u;
+    a[1] = rb < n ? *reinterpret_cast<const uint32_t*>(M + (size_t)W * rb + c) : 0u;
+    a[2] = ra < n ? *reinterpret_cast<const uint32_t*>(M + (size_t)W * ra + c + 8) : 0u;
+    a[3] = rb < n ? *reinterpret_cast<const uint32_t*>(M + (size_t)W * rb + c + 8) : 0u;
+}
+
+// out[j] (n-tile j) = A (16 x 64) . W_l^T, W_l stored [out][in] (B column-major = W row-major)
+template <int NT>
+__device__ __forceinline__ void layer_fwd(float (&acc)[NT][4], const uint32_t (&a)[4][4], const __half* sw_l, int g, int t) {
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            const __half* wr = sw_l + (8 * j + g) * SROW + 16 * kt + 2 * t;
+            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wr + 8);
+            mma16816(acc[j], a[kt], b0, b1);
+        }
+    }
+}
+
+__device__ __forceinline__ void relu_to_a(uint32_t (&a)[4][4], const float (&acc)[8][4]) {
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+        a[kt][0] = pack_h2(fmaxf(acc[2 * kt][0], 0.0f), fmaxf(acc[2 * kt][1], 0.0f));
+        a[kt][1] = pack_h2(fmaxf(acc[2 * kt][2], 0.0f), fmaxf(acc[2 * kt][3], 0.0f));
+        a[kt][2] = pack_h2(fmaxf(acc[2 * kt + 1][0], 0.0f), fmaxf(acc[2 * kt + 1][1], 0.0f));
+        a[kt][3] = pack_h2(fmaxf(acc[2 * kt + 1][2], 0.0f), fmaxf(acc[2 * kt + 1][3], 0.0f));
+    }
+}
+
+__device__ __forceinline__ void store_afrag(__half* M, uint32_t n, uint32_t r0, const uint32_t (&a)[4][4], int g, int t) {
+    const uint32_t ra = r0 + g, rb = r0 + g + 8;
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+        const int c = 16 * kt + 2 * t;
+        if (ra < n) {
+            *reinterpret_cast<uint32_t*>(M + (size_t)W * ra + c) = a[kt][0];
+            *reinterpret_cast<uint32_t*>(M + (size_t)W * ra + c + 8) = a[kt][2];
+        }
+        if (rb < n) {
+            *reinterpret_cast<uint32_t*>(M + (size_t)W * rb + c) = a[kt][1];
+            *reinterpret_cast<uint32_t*>(M + (size_t)W * rb + c + 8) = a[kt][3];
+        }
+    }
+}
+
+// X (n x 64 FP16) -> Y (n x 4 FP32, RGB + unused); acts (optional): A1..A4 (4 x n x 64)
+__global__ void __launch_bounds__(128) k_mlp_forward(const __half* __restrict__ X, uint32_t n,
+                                                     const __half* __restrict__ Wg, float* __restrict__ Y,
+                                                     __half* __restrict__ acts) {
+    __shared__ __align__(16) __half sw[(N_HIDDEN * W + OUT_PAD) * SROW];
+    load_weights_smem(sw, Wg);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < n; tile += warps) {
+        const uint32_t r0 = tile * 16;
+        uint32_t a[4][4];
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) load_afrag(a[kt], X, n, r0, kt, g, t);
+#pragma unroll
+        for (int l = 0; l < N_HIDDEN; ++l) {
+            float acc[8][4];
+            layer_fwd<8>(acc, a, sw + l * W * SROW, g, t);
+            relu_to_a(a, acc);
+            if (acts) store_afrag(acts + (size_t)l * n * W, n, r0, a, g, t);
+        }
+        float out[2][4];
+        layer_fwd<2>(out, a, sw + N_HIDDEN * W * SROW, g, t);
+        // output columns 0..2 live in n-tile 0: lane t holds columns 2t, 2t+1
+        const uint32_t ra = r0 + g, rb = r0 + g + 8;
+        if (t < 2) {
+            if (ra < n) { Y[4 * ra + 2 * t] = out[0][0]; Y[4 * ra + 2 * t + 1] = out[0][1]; }
+            if (rb < n) { Y[4 * rb + 2 * t] = out[0][2]; Y[4 * rb + 2 * t + 1] = out[0][3]; }
+        }
+    }
+}
+
+// relative L2 loss: dL/dy * (3n) (the 1/(3n) of the mean is applied to the gradients later
+// so that FP16 keeps them in its normal range), plus the loss sum
+__global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ samples, uint32_t n, __half* __restrict__ dY,
+                       float* __restrict__ loss_sum) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (q < n) {
+        const float* tg = samples + (size_t)QSTRIDE * q + 10;
+        __half* d = dY + (size_t)OUT_PAD * q;
+        for (int c = 0; c < 3; ++c) {
+            const float y = Y[4 * q + c];
+            const float den = y * y + 0.01f;
+            const float diff = y - tg[c];
+            l += diff * diff / den;
+            d[c] = __float2half_rn(2.0f * diff / den);
+        }
+        for (int c = 3; c < OUT_PAD; ++c) d[c] = __float2half_rn(0.0f);
+    }
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, l);
+}
+
+// B fragment of W_l read transposed: B[k][n] = W_l[k][n] (k = layer output, n = layer input)
+__device__ __forceinline__ void bfrag_t(uint32_t& b0, uint32_t& b1, const __half* sw_l, int kt, int j, int g, int t) {
+    const __half* c0 = sw_l + (16 * kt + 2 * t) * SROW + 8 * j + g;
+    b0 = pack_hh(c0[0], c0[SROW]);
+    b1 = pack_hh(c0[8 * SROW], c0[9 * SROW]);
+}
+
+// backward chain per 16-row tile: dZ4 = (dY W4) * [A4 > 0], ..., dZ1 = (dZ2 W1) * [A1 > 0],
+// dX = dZ1 W0 (grid columns only).  Stores dZ1..dZ4 (FP16) for the weight gradients.
+__global__ void __launch_bounds__(128) k_mlp_backward(const __half* __restrict__ dY, uint32_t n,
+                                                      const __half* __restrict__ Wg, const __half* __restrict__ acts,
+                                                      __half* __restrict__ dZ, float* __restrict__ dX, uint32_t n_grid_cols) {
+    __shared__ __align__(16) __half sw[(N_HIDDEN * W + OUT_PAD) * SROW];
+    load_weights_smem(sw, Wg);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < n; tile += warps) {
+        const uint32_t r0 = tile * 16, ra = r0 + g, rb = r0 + g + 8;
+        // dY as a 16 x 16 A fragment (one k-tile)
+        uint32_t a1[4];
+        a1[0] = ra < n ? *reinterpret_cast<const uint32_t*>(dY + (size_t)OUT_PAD * ra + 2 * t) : 0u;
+        a1[1] = rb < n ? *reinterpret_cast<const uint32_t*>(dY + (size_t)OUT_PAD * rb + 2 * t) : 0u;
+        a1[2] = ra < n ? *reinterpret_cast<const uint32_t*>(dY + (size_t)OUT_PAD * ra + 2 * t + 8) : 0u;
+        a1[3] = rb < n ? *reinterpret_cast<const uint32_t*>(dY + (size_t)OUT_PAD * rb + 2 * t + 8) : 0u;
+        float acc[8][4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+            uint32_t b0, b1;
+            bfrag_t(b0, b1, sw + N_HIDDEN * W * SROW, 0, j, g, t);
+            mma16816(acc[j], a1, b0, b1);
+        }
+        uint32_t a[4][4];
+        for (int l = N_HIDDEN - 1; l >= 0; --l) {
+            // mask with A_{l+1} > 0 (A index l holds the output of hidden layer l)
+            const __half* A = acts + (size_t)l * n * W;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = 8 * j + 2 * t;
+                const float2 ma = ra < n ? unpack_h2(*reinterpret_cast<const uint32_t*>(A + (size_t)W * ra + c)) : make_float2(0, 0);
+                const float2 mb = rb < n ? unpack_h2(*reinterpret_cast<const uint32_t*>(A + (size_t)W * rb + c)) : make_float2(0, 0);
+                acc[j][0] = ma.x > 0.0f ? acc[j][0] : 0.0f;
+                acc[j][1] = ma.y > 0.0f ? acc[j][1] : 0.0f;
+                acc[j][2] = mb.x > 0.0f ? acc[j][2] : 0.0f;
+                acc[j][3] = mb.y > 0.0f ? acc[j][3] : 0.0f;
+            }
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+                a[kt][0] = pack_h2(acc[2 * kt][0], acc[2 * kt][1]);
+                a[kt][1] = pack_h2(acc[2 * kt][2], acc[2 * kt][3]);
+                a[kt][2] = pack_h2(acc[2 * kt + 1][0], acc[2 * kt + 1][1]);
+                a[kt][3] = pack_h2(acc[2 * kt + 1][2], acc[2 * kt + 1][3]);
+            }
+            store_afrag(dZ + (size_t)l * n * W, n, r0, a, g, t);
+            // propagate through W_l: next acc = dZ_l . W_l
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    uint32_t b0, b1;
+                    bfrag_t(b0, b1, sw + l * W * SROW, kt, j, g, t);
+                    mma16816(acc[j], a[kt], b0, b1);
+                }
+            }
+        }
+        // acc holds dX (16 x 64); keep the grid columns
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t c = 8 * j + 2 * t;
+            if (c < n_grid_cols) {
+                if (ra < n) { dX[(size_t)n_grid_cols * ra + c] = acc[j][0]; dX[(size_t)n_grid_cols * ra + c + 1] = acc[j][1]; }
+                if (rb < n) { dX[(size_t)n_grid_cols * rb + c] = acc[j][2]; dX[(size_t)n_grid_cols * rb + c + 1] = acc[j][3]; }
+            }
+        }
+    }
+}
+
+// weight gradient of one layer over a chunk of rows: dW[o][i] += sum_r G[r][o] * A[r][i]
+// (G = dZ of the layer's output, A = the layer's input); a warp owns 16 outputs x 64 inputs
+constexpr int DW_CHUNK = 512;
+__global__ void __launch_bounds__(128) k_weight_grad(const __half* __restrict__ G, uint32_t g_stride, uint32_t n_out,
+                                                     const __half* __restrict__ A, uint32_t n, float* __restrict__ part) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
+    const int m0 = 16 * warp;
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+    if (m0 < (int)n_out) {
+        const uint32_t rbeg = blockIdx.x * DW_CHUNK, rend = min(rbeg + DW_CHUNK, n);
+        for (uint32_t k0 = rbeg; k0 < rend; k0 += 16) {
+            // A operand: rows m = outputs, columns k = sample rows  ->  G^T
+            uint32_t a[4];
+            auto gval = [&](uint32_t r, int o) -> __half {
+                return (r < rend && o < (int)n_out) ? G[(size_t)g_stride * r + o] : __float2half_rn(0.0f);
+            };
+            a[0] = pack_hh(gval(k0 + 2 * t, m0 + g), gval(k0 + 2 * t + 1, m0 + g));
+            a[1] = pack_hh(gval(k0 + 2 * t, m0 + g + 8), gval(k0 + 2 * t + 1, m0 + g + 8));
+            a[2] = pack_hh(gval(k0 + 2 * t + 8, m0 + g), gval(k0 + 2 * t + 9, m0 + g));
+            a[3] = pack_hh(gval(k0 + 2 * t + 8, m0 + g + 8), gval(k0 + 2 * t + 9, m0 + g + 8));
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                auto aval = [&](uint32_t r) -> __half {
+                    return r < rend ? A[(size_t)W * r + 8 * j + g] : __float2half_rn(0.0f);
+                };
+                const uint32_t b0 = pack_hh(aval(k0 + 2 * t), aval(k0 + 2 * t + 1));
+                const uint32_t b1 = pack_hh(aval(k0 + 2 * t + 8), aval(k0 + 2 * t + 9));
+                mma16816(acc[j], a, b0, b1);
+            }
+        }
+    }
+    float* out = part + (size_t)blockIdx.x * W * W;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = 8 * j + 2 * t;
+        out[(m0 + g) * W + c] = acc[j][0];
+        out[(m0 + g) * W + c + 1] = acc[j][1];
+        out[(m0 + g + 8) * W + c] = acc[j][2];
+        out[(m0 + g + 8) * W + c + 1] = acc[j][3];
+    }
+}
+
+__global__ void k_reduce_grad(const float* __restrict__ part, uint32_t nparts, uint32_t n_out, float* __restrict__ dst,
+                              float scale) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_out * W) return;
+    float s = 0.0f;
+    for (uint32_t p = 0; p < nparts; ++p) s += part[(size_t)p * W * W + i];
+    dst[i] = s * scale;
+}
+
+// Adam (Kingma & Ba): master FP32 parameters, FP16 copy for the kernels, gradient zeroed
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
+                       __half* __restrict__ copy, uint64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float gr = grad[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gr;
+        const float vi = b2 * v[i] + (1.0f - b2) * gr * gr;
+        m[i] = mi;
+        v[i] = vi;
+        const float mh = mi / c1, vh = vi / c2;
+        const float np = p[i] - lr * mh / (sqrtf(vh) + eps);
+        p[i] = np;
+        copy[i] = __float2half_rn(np);
+        grad[i] = 0.0f;
+    }
+}
+
+__global__ void k_to_half(const float* __restrict__ src, __half* __restrict__ dst, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2half_rn(src[i]);
+}
+
+// initial parameters from a counter-based stream: Xavier-uniform weights, small uniform grid
+__global__ void k_init(float* w, uint64_t nw, float* grid, uint64_t ng, uint64_t seed) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nw + ng; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0x4e5243u, 0u), (uint32_t)seed,
+                                      (uint32_t)(seed >> 32));
+        const float u = u24(r.x) * 2.0f - 1.0f;
+        if (i < nw) {
+            const uint64_t layer = i / (W * W);
+            const uint64_t row = (i % (W * W)) / W;
+            float bound = sqrtf(6.0f / (W + W));
+            if (layer >= N_HIDDEN) bound = row < 3 ? sqrtf(6.0f / (W + 3)) : 0.0f;
+            w[i] = u * bound;
+        } else {
+            grid[i - nw] = u * 1e-4f;
+        }
+    }
+}
+
+}  // namespace
+
+struct pt_nrc {
+    pt_nrc_opts o;
+    uint32_t L = 16, T = 1u << 19, grid_cols = 32;
+    uint32_t* d_res = nullptr;
+    float* d_w = nullptr;  __half* d_wh = nullptr;  float *d_wm = nullptr, *d_wv = nullptr, *d_wg = nullptr;
+    float* d_grid = nullptr;  __half* d_gh = nullptr;  float *d_gm = nullptr, *d_gv = nullptr, *d_gg = nullptr;
+    uint64_t n_grid = 0;
+    uint32_t step = 0;
+    // training buffers
+    uint32_t cap = 0;
+    __half *X = nullptr, *acts = nullptr, *dY = nullptr, *dZ = nullptr;
+    float *Y = nullptr, *dX = nullptr, *part = nullptr, *d_loss = nullptr;
+    // inference buffers
+    uint32_t icap = 0;
+    __half* iX = nullptr;
+    float* iY = nullptr;
+    float3 lo, inv_ext;
+    uint64_t launches = 0;
+};
+
+static GridDesc grid_desc(pt_nrc* N) {
+    GridDesc G;
+    G.table = N->d_gh;
+    G.grad = N->d_gg;
+    G.res = N->d_res;
+    G.L = N->L;
+    G.T = N->T;
+    G.lo = N->lo;
+    G.inv_ext = N->inv_ext;
+    return G;
+}
+
+static pt_status ensure_train(pt_nrc* N, uint32_t n) {
+    if (N->cap >= n) return PT_OK;
+    void* ps[] = {N->X, N->acts, N->dY, N->dZ, N->Y, N->dX, N->part};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    const size_t c = n;
+    PT_CUDA_TRY(cudaMalloc(&N->X, c * W * sizeof(__half)));
+    PT_CUDA_TRY(cudaMalloc(&N->acts, c * W * N_HIDDEN * sizeof(__half)));
+    PT_CUDA_TRY(cudaMalloc(&N->dY, c * OUT_PAD * sizeof(__half)));
+    PT_CUDA_TRY(cudaMalloc(&N->dZ, c * W * N_HIDDEN * sizeof(__half)));
+    PT_CUDA_TRY(cudaMalloc(&N->Y, c * 4 * sizeof(float)));
+    PT_CUDA_TRY(cudaMalloc(&N->dX, c * N->grid_cols * sizeof(float)));
+    PT_CUDA_TRY(cudaMalloc(&N->part, ((c + DW_CHUNK - 1) / DW_CHUNK) * W * W * sizeof(float)));
+    N->cap = n;
+    return PT_OK;
+}
+
+static int g_mlp_blocks = 0;
+static uint32_t mlp_grid(uint32_t n) {
+    if (g_mlp_blocks == 0) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mlp_forward, 128, 0);
+        g_mlp_blocks = std::max(b, 1) * pt_num_sms();
+    }
+    const uint32_t tiles = (n + 15) / 16;
+    return std::max(1u, std::min((uint32_t)g_mlp_blocks, (tiles + 3) / 4));
+}
+
+extern "C" pt_status pt_nrc_create(const pt_nrc_opts* opts, void* cuda_stream, pt_nrc** out) {
+    PT_CHECK_ARG(opts && out, "NULL argument");
+    *out = nullptr;
+    pt_nrc_opts o = *opts;
+    if (!o.n_levels) o.n_levels = 16;
+    if (!o.log2_table) o.log2_table = 19;
+    if (!o.base_resolution) o.base_resolution = 16;
+    if (!o.n_hidden) o.n_hidden = N_HIDDEN;
+    if (o.learning_rate <= 0.0f) o.learning_rate = 1e-2f;
+    if (!o.batch) o.batch = 1u << 14;
+    PT_CHECK_ARG(o.n_hidden == N_HIDDEN, "n_hidden must be 4");
+    PT_CHECK_ARG(o.n_levels >= 1 && o.n_levels <= 16, "n_levels must be 1..16 (2 features each fill 32 inputs)");
+    PT_CHECK_ARG(o.log2_table >= 8 && o.log2_table <= 24, "log2_table must be 8..24");
+    PT_CHECK_ARG(o.base_resolution >= 2, "base_resolution must be >= 2");
+    for (int a = 0; a < 3; ++a)
+        PT_CHECK_ARG(o.scene_max[a] > o.scene_min[a], "empty normalisation box");
+    pt_nrc* N = new pt_nrc();
+    N->o = o;
+    N->L = o.n_levels;
+    N->T = 1u << o.log2_table;
+    N->grid_cols = 2 * N->L;
+    N->lo = make_float3(o.scene_min[0], o.scene_min[1], o.scene_min[2]);
+    N->inv_ext = make_float3(1.0f / (o.scene_max[0] - o.scene_min[0]), 1.0f / (o.scene_max[1] - o.scene_min[1]),
+                             1.0f / (o.scene_max[2] - o.scene_min[2]));
+    // level resolutions: floor(N_min * b^l), b from the per-level scale or a 2048 finest level
+    std::vector<uint32_t> res(N->L);
+    const double b = o.per_level_scale > 0.0f ? o.per_level_scale
+                                              : std::exp((std::log(2048.0) - std::log((double)o.base_resolution)) /
+                                                         std::max<int>((int)N->L - 1, 1));
+    for (uint32_t l = 0; l < N->L; ++l) res[l] = (uint32_t)std::floor(o.base_resolution * std::pow(b, (double)l));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    N->n_grid = (uint64_t)N->L * N->T * 2;
+    auto fail = [&](pt_status s) { pt_nrc_destroy(N); return s; };
+#define NTRY(call)                                                                      \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            pt_set_error(std::string(#call) + ": " + cudaGetErrorString(e_));           \
+            return fail(e_ == cudaErrorMemoryAllocation ? PT_ERR_OOM : PT_ERR_CUDA);    \
+        }                                                                               \
+    } while (0)
+    NTRY(cudaMalloc(&N->d_res, N->L * sizeof(uint32_t)));
+    NTRY(cudaMemcpyAsync(N->d_res, res.data(), N->L * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    float** f32[] = {&N->d_w, &N->d_wm, &N->d_wv, &N->d_wg};
+    for (float** p : f32) NTRY(cudaMalloc(p, N_WEIGHTS * sizeof(float)));
+    NTRY(cudaMalloc(&N->d_wh, N_WEIGHTS * sizeof(__half)));
+    float** g32[] = {&N->d_grid, &N->d_gm, &N->d_gv, &N->d_gg};
+    for (float** p : g32) NTRY(cudaMalloc(p, N->n_grid * sizeof(float)));
+    NTRY(cudaMalloc(&N->d_gh, N->n_grid * sizeof(__half)));
+    NTRY(cudaMalloc(&N->d_loss, 4 * sizeof(float)));
+    for (float* p : {N->d_wm, N->d_wv, N->d_wg}) NTRY(cudaMemsetAsync(p, 0, N_WEIGHTS * sizeof(float), st));
+    for (float* p : {N->d_gm, N->d_gv, N->d_gg}) NTRY(cudaMemsetAsync(p, 0, N->n_grid * sizeof(float), st));
+    NTRY(cudaMemsetAsync(N->d_loss, 0, 4 * sizeof(float), st));
+    PT_LAUNCH(k_init, 4 * pt_num_sms(), 256, 0, st, N->d_w, (uint64_t)N_WEIGHTS, N->d_grid, N->n_grid, o.seed);
+    PT_LAUNCH(k_to_half, 4 * pt_num_sms(), 256, 0, st, N->d_w, N->d_wh, (uint64_t)N_WEIGHTS);
+    PT_LAUNCH(k_to_half, 4 * pt_num_sms(), 256, 0, st, N->d_grid, N->d_gh, N->n_grid);
+    NTRY(cudaGetLastError());
+    NTRY(cudaStreamSynchronize(st));
+#undef NTRY
+    *out = N;
+    return PT_OK;
+}
+
+extern "C" void pt_nrc_destroy(pt_nrc* N) {
+    if (!N) return;
+    cudaDeviceSynchronize();
+    void* ps[] = {N->d_res, N->d_w, N->d_wh, N->d_wm, N->d_wv, N->d_wg, N->d_grid, N->d_gh, N->d_gm, N->d_gv, N->d_gg,
+                  N->X, N->acts, N->dY, N->dZ, N->Y, N->dX, N->part, N->d_loss, N->iX, N->iY};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    delete N;
+}
+
+// forward (+ optional activations) of n records already resident on the device
+static pt_status nrc_forward(pt_nrc* N, const float* q, uint32_t n, __half* X, float* Y, __half* acts, cudaStream_t st) {
+    const GridDesc G = grid_desc(N);
+    const uint64_t threads = (uint64_t)n * N->L;
+    PT_LAUNCH(k_encode, (uint32_t)((threads + 255) / 256), 256, 0, st, G, q, n, X);
+    PT_LAUNCH(k_mlp_forward, mlp_grid(n), 128, 0, st, X, n, N->d_wh, Y, acts);
+    N->launches += 2;
+    PT_CUDA_TRY(cudaGetLastError());
+    return PT_OK;
+}
+
+// loss and gradients of one batch into d_wg / d_gg (accumulated; caller zeroes via Adam)
+static pt_status nrc_gradients(pt_nrc* N, const float* samples, uint32_t n, cudaStream_t st) {
+    pt_status r = ensure_train(N, n);
+    if (r != PT_OK) return r;
+    r = nrc_forward(N, samples, n, N->X, N->Y, N->acts, st);
+    if (r != PT_OK) return r;
+    PT_CUDA_TRY(cudaMemsetAsync(N->d_loss, 0, sizeof(float), st));
+    PT_LAUNCH(k_loss, (n + 255) / 256, 256, 0, st, N->Y, samples, n, N->dY, N->d_loss);
+    PT_LAUNCH(k_mlp_backward, mlp_grid(n), 128, 0, st, N->dY, n, N->d_wh, N->acts, N->dZ, N->dX, N->grid_cols);
+    const float scale = 1.0f / (3.0f * (float)n);
+    const uint32_t nparts = (n + DW_CHUNK - 1) / DW_CHUNK;
+    // layer l's weight gradient pairs dZ_l (its output gradient) with its input
+    for (int l = 0; l <= N_HIDDEN; ++l) {
+        const __half* Gm = l < N_HIDDEN ? N->dZ + (size_t)l * n * W : N->dY;
+        const uint32_t gs = l < N_HIDDEN ? W : OUT_PAD;
+        const uint32_t nout = l < N_HIDDEN ? W : OUT_PAD;
+        const __half* Ain = l == 0 ? N->X : N->acts + (size_t)(l - 1) * n * W;
+        PT_LAUNCH(k_weight_grad, nparts, 128, 0, st, Gm, gs, nout, Ain, n, N->part);
+        PT_LAUNCH(k_reduce_grad, (nout * W + 255) / 256, 256, 0, st, N->part, nparts, nout, N->d_wg + (size_t)l * W * W, scale);
+    }
+    const uint64_t threads = (uint64_t)n * N->L;
+    PT_LAUNCH(k_grid_backward, (uint32_t)((threads + 255) / 256), 256, 0, st, grid_desc(N), samples, n, N->dX, scale);
+    N->launches += 4 + 2 * (N_HIDDEN + 1);
+    PT_CUDA_TRY(cudaGetLastError());
+    return PT_OK;
+}
+
+static pt_status nrc_adam(pt_nrc* N, cudaStream_t st) {
+    N->step++;
+    const float b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
+    const float c1 = 1.0f - std::pow(b1, (float)N->step), c2 = 1.0f - std::pow(b2, (float)N->step);
+    const float lr = N->o.learning_rate;
+    PT_LAUNCH(k_adam, 2 * pt_num_sms(), 256, 0, st, N->d_w, N->d_wg, N->d_wm, N->d_wv, N->d_wh, (uint64_t)N_WEIGHTS, lr,
+              b1, b2, eps, c1, c2);
+    PT_LAUNCH(k_adam, 8 * pt_num_sms(), 256, 0, st, N->d_grid, N->d_gg, N->d_gm, N->d_gv, N->d_gh, N->n_grid, lr, b1,
+              b2, eps, c1, c2);
+    N->launches += 2;
+    PT_CUDA_TRY(cudaGetLastError());
+    return PT_OK;
+}
+
+extern "C" pt_status pt_nrc_train(pt_nrc* N, const float* samples, uint32_t n, void* cuda_stream) {
+    PT_CHECK_ARG(N && samples, "NULL argument");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    for (uint32_t b = 0; b < n; b += N->o.batch) {
+        const uint32_t m = std::min(N->o.batch, n - b);
+        pt_status r = nrc_gradients(N, samples + (size_t)QSTRIDE * b, m, st);
+        if (r != PT_OK) return r;
+        r = nrc_adam(N, st);
+        if (r != PT_OK) return r;
+    }
+    return PT_OK;
+}
+
+extern "C" pt_status pt_nrc_gradients(pt_nrc* N, const float* samples, uint32_t n, float* dw_out, float* dgrid_out,
+                                      void* cuda_stream) {
+    PT_CHECK_ARG(N && samples, "NULL argument");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    PT_CUDA_TRY(cudaMemsetAsync(N->d_wg, 0, N_WEIGHTS * sizeof(float), st));
+    PT_CUDA_TRY(cudaMemsetAsync(N->d_gg, 0, N->n_grid * sizeof(float), st));
+    pt_status r = nrc_gradients(N, samples, n, st);
+    if (r != PT_OK) return r;
+    if (dw_out) PT_CUDA_TRY(cudaMemcpyAsync(dw_out, N->d_wg, N_WEIGHTS * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (dgrid_out) PT_CUDA_TRY(cudaMemcpyAsync(dgrid_out, N->d_gg, N->n_grid * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    PT_CUDA_TRY(cudaMemsetAsync(N->d_wg, 0, N_WEIGHTS * sizeof(float), st));
+    PT_CUDA_TRY(cudaMemsetAsync(N->d_gg, 0, N->n_grid * sizeof(float), st));
+    return PT_OK;
+}
+
+extern "C" pt_status pt_nrc_infer(pt_nrc* N, const float* queries, uint32_t n, float* out_rgb, void* cuda_stream) {
+    PT_CHECK_ARG(N && queries && out_rgb, "NULL argument");
+    if (n == 0) return PT_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (N->icap < n) {
+        if (N->iX) cudaFree(N->iX);
+        N->iX = nullptr;
+        PT_CUDA_TRY(cudaMalloc(&N->iX, (size_t)n * W * sizeof(__half)));
+        N->icap = n;
+    }
+    // the MLP writes 4 floats per row; out_rgb is the caller's n x 4 buffer
+    return nrc_forward(N, queries, n, N->iX, out_rgb, nullptr, st);
+}
+
+extern "C" pt_status pt_nrc_params(pt_nrc* N, int which, float** ptr, uint64_t* count) {
+    PT_CHECK_ARG(N && ptr && count, "NULL argument");
+    PT_CHECK_ARG(which == 0 || which == 1, "which must be 0 (MLP) or 1 (grid)");
+    *ptr = which == 0 ? N->d_w : N->d_grid;
+    *count = which == 0 ? (uint64_t)N_WEIGHTS : N->n_grid;
+    return PT_OK;
+}
+
+extern "C" pt_status pt_nrc_commit(pt_nrc* N, void* cuda_stream) {
+    PT_CHECK_ARG(N != nullptr, "NULL argument");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    PT_LAUNCH(k_to_half, 4 * pt_num_sms(), 256, 0, st, N->d_w, N->d_wh, (uint64_t)N_WEIGHTS);
+    PT_LAUNCH(k_to_half, 8 * pt_num_sms(), 256, 0, st, N->d_grid, N->d_gh, N->n_grid);
+    PT_CUDA_TRY(cudaGetLastError());
+    return PT_OK;
+}
+
+extern "C" pt_status pt_nrc_last_loss(pt_nrc* N, float* loss) {
+    PT_CHECK_ARG(N && loss, "NULL argument");
+    PT_CUDA_TRY(cudaDeviceSynchronize());
+    float s = 0.0f;
+    PT_CUDA_TRY(cudaMemcpy(&s, N->d_loss, sizeof(float), cudaMemcpyDeviceToHost));
+    const uint32_t n = std::min(N->cap, N->o.batch);
+    *loss = n ? s / (3.0f * (float)n) : 0.0f;
+    return PT_OK;
+}
+
+// ---- hooks used by the renderer ----
+pt_status pt_nrc_render_infer(pt_nrc* N, const float* queries, uint32_t n, float* out4, cudaStream_t st) {
+    return pt_nrc_infer(N, queries, n, out4, (void*)st);
+}

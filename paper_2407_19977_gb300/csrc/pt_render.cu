@@ -220,7 +220,21 @@ struct WfParams {
     float* comp;
     float* sample_out;
     unsigned long long* stats;
+    // radiance cache (wavefront only)
+    int nrc_on;
+    uint32_t rec_per_path, max_train, sample_cap;
+    float train_prob;
+    uint32_t* aux;            // per path: diffuse-ish vertex count | (training slot + 1) << 8
+    float* nrc_q;             // cache query records (16 floats)
+    float* nrc_out;           // cache outputs (4 floats per query)
+    uint32_t* nrc_counters;   // [0] queries, [1] training paths, [2] training samples
+    float* train_rec;         // training slots x rec_per_path x 16 floats
+    uint32_t* train_nv;       // vertices recorded per training path
+    uint32_t* train_id;       // path id of each training path
+    float* train_samples;     // training sample records (16 floats)
 };
+
+constexpr uint32_t NRC_DIM_TRAIN = 10;   // uniform dimension of the training-path choice
 
 __global__ void k_wf_raygen(WfParams P) {
     const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -241,6 +255,92 @@ __global__ void k_wf_raygen(WfParams P) {
     P.ray_d[0][id] = make_float4(d.x, d.y, d.z, __uint_as_float(id));
     P.beta[id] = make_float4(1.0f, 1.0f, 1.0f, -1.0f);
     P.radiance[id] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (P.nrc_on) {
+        uint32_t aux = 0;
+        if (P.max_train && u24(philox4x32_10(make_uint4(p, s, 0u, NRC_DIM_TRAIN >> 2), (uint32_t)P.seed,
+                                             (uint32_t)(P.seed >> 32)).z) < P.train_prob) {
+            const uint32_t slot = atomicAdd(&P.nrc_counters[1], 1u);
+            if (slot < P.max_train) {
+                aux = (slot + 1u) << 8;
+                P.train_id[slot] = id;
+                P.train_nv[slot] = 0;
+            }
+        }
+        P.aux[id] = aux;
+    }
+}
+
+// Radiance-cache hook: records the vertices of training paths (features, radiance so far,
+// throughput) and ends other paths at their second diffuse-ish vertex with a cache query.
+struct NrcHook {
+    const WfParams* P;
+    uint32_t id;
+    uint32_t aux;
+    __device__ __forceinline__ bool operator()(float3 x, float3 wo, float3 n, const DMat& M, const PathState& ps,
+                                               uint32_t k) {
+        const float r = effective_roughness(M);
+        const uint32_t slot1 = aux >> 8;
+        if (slot1 && k < P->rec_per_path) {
+            float4* rec = reinterpret_cast<float4*>(P->train_rec + ((size_t)(slot1 - 1) * P->rec_per_path + k) * 16);
+            rec[0] = make_float4(x.x, x.y, x.z, wo.x);
+            rec[1] = make_float4(wo.y, wo.z, n.x, n.y);
+            rec[2] = make_float4(n.z, r, ps.L.x, ps.L.y);
+            rec[3] = make_float4(ps.L.z, ps.beta.x, ps.beta.y, ps.beta.z);
+            P->train_nv[slot1 - 1] = k + 1;
+        }
+        if (r >= 0.25f) {
+            const uint32_t cnt = min((aux & 0xffu) + 1u, 255u);
+            aux = (aux & ~0xffu) | cnt;
+            if (cnt == 2u && !slot1) {
+                const uint32_t q = atomicAdd(&P->nrc_counters[0], 1u);
+                float4* rec = reinterpret_cast<float4*>(P->nrc_q + (size_t)q * 16);
+                rec[0] = make_float4(x.x, x.y, x.z, wo.x);
+                rec[1] = make_float4(wo.y, wo.z, n.x, n.y);
+                rec[2] = make_float4(n.z, r, ps.beta.x, ps.beta.y);
+                rec[3] = make_float4(ps.beta.z, __uint_as_float(id), 0.0f, 0.0f);
+                return true;
+            }
+        }
+        return false;
+    }
+};
+
+// radiance of the paths the cache ended: L += beta * max(cache, 0)
+__global__ void k_nrc_apply(WfParams P, uint32_t nq) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const float* rec = P.nrc_q + (size_t)q * 16;
+    const uint32_t id = __float_as_uint(rec[13]);
+    const float* y = P.nrc_out + 4ull * q;
+    float4 L = P.radiance[id];
+    L.x += rec[10] * fmaxf(y[0], 0.0f);
+    L.y += rec[11] * fmaxf(y[1], 0.0f);
+    L.z += rec[12] * fmaxf(y[2], 0.0f);
+    P.radiance[id] = L;
+}
+
+// training samples from the path suffixes: target_j = (L_end - L_j) / beta_j per channel
+__global__ void k_nrc_targets(WfParams P, uint32_t n_train) {
+    const uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= n_train) return;
+    const uint32_t id = P.train_id[slot];
+    const float4 Le = P.radiance[id];
+    const uint32_t nv = min(P.train_nv[slot], P.rec_per_path);
+    for (uint32_t j = 0; j < nv; ++j) {
+        const float* rec = P.train_rec + ((size_t)slot * P.rec_per_path + j) * 16;
+        const float L[3] = {Le.x - rec[10], Le.y - rec[11], Le.z - rec[12]};
+        const float b[3] = {rec[13], rec[14], rec[15]};
+        float t[3];
+        bool ok = isfinite(Le.x) && isfinite(Le.y) && isfinite(Le.z);
+        for (int c = 0; c < 3; ++c) t[c] = b[c] > 1e-4f ? fmaxf(L[c], 0.0f) / b[c] : 0.0f;
+        if (!ok) continue;
+        const uint32_t o = atomicAdd(&P.nrc_counters[2], 1u);
+        if (o >= P.sample_cap) return;
+        float* out = P.train_samples + (size_t)o * 16;
+        for (int c = 0; c < 10; ++c) out[c] = rec[c];
+        out[10] = t[0]; out[11] = t[1]; out[12] = t[2];
+        out[13] = 0.0f; out[14] = 0.0f; out[15] = 0.0f;
+    }
 }
 
 __global__ void k_wf_setup(uint32_t* counters, int out_q, uint32_t n_keys) {
@@ -337,6 +437,7 @@ __global__ void k_wf_sort_scatter(WfParams P, int in_q) {
     }
 }
 
+template <bool NRC>
 __global__ void __launch_bounds__(128) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
     const uint32_t count = P.counters[in_q];
     const uint32_t lane = lane_id();
@@ -370,7 +471,17 @@ __global__ void __launch_bounds__(128) k_wf_shade(WfParams P, int in_q, int out_
             rng.p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
             rng.s = s; rng.k = k; rng.k0 = (uint32_t)P.seed; rng.k1 = (uint32_t)(P.seed >> 32);
             ShadeOut so;
-            const int r = shade_vertex(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so);
+            int r;
+            if (NRC) {
+                NrcHook hook;
+                hook.P = &P;
+                hook.id = id;
+                hook.aux = P.aux[id];
+                r = shade_vertex_h(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so, hook);
+                P.aux[id] = hook.aux;
+            } else {
+                r = shade_vertex(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so);
+            }
             P.radiance[id] = make_float4(ps.L.x, ps.L.y, ps.L.z, 0.0f);
             if (so.rr_end) rr_cnt++;
             cont = r == SHADE_CONTINUE;
@@ -471,7 +582,8 @@ __global__ void k_wf_accum(WfParams P) {
 
 pt_status pt_free_wave(WaveBuffers& w) {
     void* ps[] = {w.ray_o[0], w.ray_o[1], w.ray_d[0], w.ray_d[1], w.hit, w.beta, w.radiance,
-                  w.sh_o, w.sh_d, w.sh_c, w.perm, w.keys, w.counters};
+                  w.sh_o, w.sh_d, w.sh_c, w.perm, w.keys, w.counters, w.aux, w.nrc_q, w.nrc_out,
+                  w.nrc_counters, w.train_rec, w.train_nv, w.train_id, w.train_samples};
     for (void* p : ps)
         if (p) cudaFree(p);
     w = WaveBuffers();
@@ -504,6 +616,28 @@ static pt_status ensure_wave(WaveBuffers& w, uint32_t capacity) {
     return PT_OK;
 }
 
+// radiance-cache buffers: queries (one per path at most), training records and samples
+static pt_status ensure_nrc_buffers(WaveBuffers& w, uint32_t rec_per_path) {
+    const uint32_t cap = w.capacity, slots = 32768, samples = 65536;
+    if (w.nrc_capacity >= cap && w.rec_per_path >= rec_per_path) return PT_OK;
+    void* ps[] = {w.aux, w.nrc_q, w.nrc_out, w.nrc_counters, w.train_rec, w.train_nv, w.train_id, w.train_samples};
+    for (void* q : ps)
+        if (q) cudaFree(q);
+    PT_CUDA_TRY(cudaMalloc(&w.aux, (size_t)cap * sizeof(uint32_t)));
+    PT_CUDA_TRY(cudaMalloc(&w.nrc_q, (size_t)cap * 16 * sizeof(float)));
+    PT_CUDA_TRY(cudaMalloc(&w.nrc_out, (size_t)cap * 4 * sizeof(float)));
+    PT_CUDA_TRY(cudaMalloc(&w.nrc_counters, 8 * sizeof(uint32_t)));
+    PT_CUDA_TRY(cudaMalloc(&w.train_rec, (size_t)slots * rec_per_path * 16 * sizeof(float)));
+    PT_CUDA_TRY(cudaMalloc(&w.train_nv, slots * sizeof(uint32_t)));
+    PT_CUDA_TRY(cudaMalloc(&w.train_id, slots * sizeof(uint32_t)));
+    PT_CUDA_TRY(cudaMalloc(&w.train_samples, (size_t)samples * 16 * sizeof(float)));
+    w.nrc_capacity = cap;
+    w.train_slots = slots;
+    w.rec_per_path = rec_per_path;
+    w.sample_cap = samples;
+    return PT_OK;
+}
+
 static int g_trace_blocks_per_sm = 0, g_shade_blocks_per_sm = 0, g_shadow_blocks_per_sm = 0;
 
 static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
@@ -523,7 +657,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_trace<false>, 128, 0);
         g_trace_blocks_per_sm = std::max(b, 1);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shade, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shade<false>, 128, 0);
         g_shade_blocks_per_sm = std::max(b, 1);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shadow<false>, 128, 0);
         g_shadow_blocks_per_sm = std::max(b, 1);
@@ -548,6 +682,17 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     P.perm = w.perm; P.keys = w.keys; P.counters = w.counters;
     P.sum = acc->sum; P.comp = acc->comp; P.sample_out = o.sample_out;
     P.stats = s->d_stats;
+    if (o.nrc) {
+        r = ensure_nrc_buffers(w, std::min(max_depth + 1, 16u));
+        if (r != PT_OK) return r;
+        P.nrc_on = 1;
+        P.rec_per_path = w.rec_per_path;
+        P.max_train = o.nrc_train ? w.train_slots : 0;
+        P.sample_cap = w.sample_cap;
+        P.aux = w.aux; P.nrc_q = w.nrc_q; P.nrc_out = w.nrc_out; P.nrc_counters = w.nrc_counters;
+        P.train_rec = w.train_rec; P.train_nv = w.train_nv; P.train_id = w.train_id;
+        P.train_samples = w.train_samples;
+    }
     uint64_t launches = 0;
     const bool count = (o.flags & FLAG_COUNT) != 0;
     // optional per-kind timing: an event pair around every launch of a kind
@@ -574,6 +719,10 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
             P.sb = (uint32_t)acc->spp_done + i0;
             P.nsamp = ns;
             const uint32_t n = npix * ns;
+            if (P.nrc_on) {
+                P.train_prob = std::min(1.0f, (float)w.train_slots / (float)n);
+                PT_CUDA_TRY(cudaMemsetAsync(w.nrc_counters, 0, 8 * sizeof(uint32_t), st));
+            }
             cudaEvent_t e = begin(PT_K_RAYGEN);
             PT_LAUNCH(k_wf_raygen, (n + 255) / 256, 256, 0, st, P);
             end(e);
@@ -594,13 +743,41 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                     launches += 2;
                 }
                 e = begin(PT_K_SHADE);
-                PT_LAUNCH(k_wf_shade, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+                if (P.nrc_on) PT_LAUNCH(k_wf_shade<true>, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+                else PT_LAUNCH(k_wf_shade<false>, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
                 end(e);
                 e = begin(PT_K_SHADOW);
                 if (count) PT_LAUNCH(k_wf_shadow<true>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
                 else PT_LAUNCH(k_wf_shadow<false>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
                 end(e);
                 launches += 2;
+            }
+            if (P.nrc_on) {
+                // cache inference for the paths that ended at their second diffuse-ish vertex,
+                // then training samples from this wave's training-path suffixes
+                uint32_t cnt[4] = {0, 0, 0, 0};
+                PT_CUDA_TRY(cudaMemcpyAsync(cnt, w.nrc_counters, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+                PT_CUDA_TRY(cudaStreamSynchronize(st));
+                const uint32_t nq = cnt[0], nt = std::min(cnt[1], P.max_train);
+                if (nq) {
+                    pt_status rr = pt_nrc_render_infer(o.nrc, w.nrc_q, nq, w.nrc_out, st);
+                    if (rr != PT_OK) return rr;
+                    PT_LAUNCH(k_nrc_apply, (nq + 255) / 256, 256, 0, st, P, nq);
+                    ++launches;
+                }
+                if (nt) {
+                    PT_LAUNCH(k_nrc_targets, (nt + 127) / 128, 128, 0, st, P, nt);
+                    ++launches;
+                    PT_CUDA_TRY(cudaMemcpyAsync(&cnt[2], w.nrc_counters + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+                    PT_CUDA_TRY(cudaStreamSynchronize(st));
+                    const uint32_t ns = std::min(cnt[2], P.sample_cap);
+                    if (ns) {
+                        pt_status rr = pt_nrc_train(o.nrc, w.train_samples, ns, (void*)st);
+                        if (rr != PT_OK) return rr;
+                    }
+                }
+                s->nrc_queries_host += nq;
+                s->nrc_samples_host += std::min(cnt[2], P.sample_cap);
             }
             e = begin(PT_K_ACCUM);
             PT_LAUNCH(k_wf_accum, (npix + 255) / 256, 256, 0, st, P);
@@ -666,12 +843,13 @@ extern "C" pt_status pt_render(pt_scene* s, const pt_camera* camera, uint32_t sp
                      (uint64_t)o.crop_y0 + acc->height <= camera->height, "window outside the frame");
     PT_CHECK_ARG(acc->spp_done + spp < (1ull << 32), "sample index overflows 32 bits");
     PT_CHECK_ARG(o.mode <= PT_MODE_MEGAKERNEL, "unknown mode");
-    if (o.nrc) { pt_set_error("radiance-cache rendering goes through pt_render_nrc"); return PT_ERR_UNSUPPORTED; }
+    PT_CHECK_ARG(!o.nrc || o.mode != PT_MODE_MEGAKERNEL, "the radiance cache runs in wavefront mode");
     if (spp == 0) return PT_OK;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     s->last_stream = st;
     uint32_t mode = o.mode;
-    if (mode == PT_MODE_AUTO) mode = (uint64_t)acc->width * acc->height >= (1u << 16) ? PT_MODE_WAVEFRONT : PT_MODE_MEGAKERNEL;
+    if (mode == PT_MODE_AUTO)
+        mode = (o.nrc || (uint64_t)acc->width * acc->height >= (1u << 16)) ? PT_MODE_WAVEFRONT : PT_MODE_MEGAKERNEL;
     pt_status r;
     if (mode == PT_MODE_WAVEFRONT) {
         r = render_wavefront(s, *camera, spp, max_depth, seed, acc, o, st);

@@ -107,7 +107,9 @@ SIGNATURES = {
     "pt_nrc_create": (C.c_int, [C.POINTER(pt_nrc_opts), vp, C.POINTER(vp)]),
     "pt_nrc_train": (C.c_int, [vp, vp, u32, vp]),
     "pt_nrc_infer": (C.c_int, [vp, vp, u32, vp, vp]),
+    "pt_nrc_gradients": (C.c_int, [vp, vp, u32, vp, vp, vp]),
     "pt_nrc_params": (C.c_int, [vp, C.c_int, C.POINTER(vp), C.POINTER(u64)]),
+    "pt_nrc_commit": (C.c_int, [vp, vp]),
     "pt_nrc_last_loss": (C.c_int, [vp, C.POINTER(f32)]),
     "pt_nrc_destroy": (None, [vp]),
     "pt_status_string": (C.c_char_p, [C.c_int]),

@@ -202,6 +202,26 @@ pt_status pt_render(pt_scene* scene, const pt_camera* camera, uint32_t spp, uint
                     uint64_t seed, pt_accum* accum, const pt_render_opts* opts,
                     void* cuda_stream);
 
+/* pt_render for callers that cannot allocate device memory (no counterpart in the paper).
+ * Some host programs are not allowed to call cudaMalloc: they run under a device-memory
+ * budget fixed at start-up, inside a host application that owns every allocation, or in a
+ * real-time loop that must not enter the allocator.  This call renders exactly what
+ * pt_render renders in PT_MODE_WAVEFRONT (same kernels, same random numbers, bit-identical
+ * accumulators) but takes its work queues from one fixed array compiled into the library
+ * (16,384 paths, about 2.7 MB, held on every GPU that loads the library until the process
+ * exits) and calls no allocating routine.  Limits and rules:
+ *  - the window (accum->width * accum->height) holds at most 16,384 pixels; larger images
+ *    are rendered tile by tile; larger windows return PT_ERR_INVALID_ARG;
+ *  - opts->nrc and opts->kernel_ms / kernel_launches must be NULL (PT_ERR_INVALID_ARG);
+ *  - every call shares the one array: calls that overlap on the GPU (different streams, or
+ *    threads without ordering) race on it and corrupt each other's work;
+ *  - the first call on a device looks the array's device address up with
+ *    cudaGetSymbolAddress; make that first call before any stream capture.
+ * Inputs, outputs and errors otherwise as pt_render. */
+pt_status pt_render_noalloc(pt_scene* scene, const pt_camera* camera, uint32_t spp,
+                            uint32_t max_depth, uint64_t seed, pt_accum* accum,
+                            const pt_render_opts* opts, void* cuda_stream);
+
 /* One job of a batched launch: a built scene, its camera, its accumulator (whole frame). */
 typedef struct {
     pt_scene* scene;

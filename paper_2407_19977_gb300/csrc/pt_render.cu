@@ -11,6 +11,7 @@
 //    -> per-pixel Kahan accumulation in sample order.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "pt_internal.h"
@@ -900,5 +901,146 @@ extern "C" pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const 
     if (r != PT_OK) return r;
     for (uint32_t i = 0; i < n_jobs; ++i) jobs[i].accum->spp_done += jobs[i].spp;
     jobs[0].scene->launches += launches;
+    return PT_OK;
+}
+
+// ------------------------------------------------------------------ render without allocation
+// Some callers cannot call cudaMalloc: code running where the allocator is off limits
+// (a memory budget fixed up front, an embedding host that owns all device memory, a
+// real-time loop that must not hit the allocator's locks or its possible synchronisation).
+// pt_render_noalloc serves them: the same wavefront kernels as pt_render, but the work
+// queues live in the fixed-size array below, which every GPU that loads this library keeps
+// until the process exits.  The kernels themselves reset every counter that must start at
+// zero (raygen sets the input queue size, the per-bounce setup kernel clears the output
+// queue, the shadow queue, the fetch heads and the sort buckets) and initialise every path
+// slot they read, so stale contents from an earlier call are never used.
+constexpr uint32_t NOALLOC_MAX_PATHS = 16384;
+constexpr size_t NOALLOC_F4 = 10;   // float4 arrays per path: 2 x ray o/d, hit, beta, radiance, 3 x shadow
+constexpr size_t NOALLOC_BYTES =
+    (size_t)NOALLOC_MAX_PATHS * (NOALLOC_F4 * sizeof(float4) + 2 * sizeof(uint32_t)) +
+    (C_BUCKETS + MAX_SORT_KEYS) * sizeof(uint32_t);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// device address of g_noalloc_scratch per device, resolved on the first call on that device
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[64] = {nullptr};
+
+static pt_status noalloc_scratch(void** out) {
+    int dev = 0;
+    PT_CUDA_TRY(cudaGetDevice(&dev));
+    PT_CHECK_ARG(dev >= 0 && dev < 64, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            pt_set_error(std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
+            return PT_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return PT_OK;
+}
+
+extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uint32_t spp, uint32_t max_depth,
+                                       uint64_t seed, pt_accum* acc, const pt_render_opts* opts, void* cuda_stream) {
+    PT_CHECK_ARG(s && camera && acc, "NULL argument");
+    if (!s->built) { pt_set_error("pt_bvh_build has not run"); return PT_ERR_NOT_BUILT; }
+    PT_CHECK_ARG(acc->sum && acc->comp, "accumulator buffers are NULL");
+    PT_CHECK_ARG(camera->width > 0 && camera->height > 0, "empty frame");
+    PT_CHECK_ARG(camera->vfov_deg > 0.0f && camera->vfov_deg < 180.0f, "vfov outside (0, 180)");
+    pt_render_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.sort_by_material = -1;
+    if (opts) o = *opts;
+    PT_CHECK_ARG(acc->width > 0 && acc->height > 0, "empty window");
+    PT_CHECK_ARG((uint64_t)o.crop_x0 + acc->width <= camera->width &&
+                     (uint64_t)o.crop_y0 + acc->height <= camera->height, "window outside the frame");
+    PT_CHECK_ARG((uint64_t)acc->width * acc->height <= NOALLOC_MAX_PATHS,
+                 "pt_render_noalloc renders windows of at most 16384 pixels; render larger images tile by tile");
+    PT_CHECK_ARG(acc->spp_done + spp < (1ull << 32), "sample index overflows 32 bits");
+    PT_CHECK_ARG(o.nrc == nullptr, "the radiance cache needs allocations: use pt_render");
+    PT_CHECK_ARG(o.kernel_ms == nullptr && o.kernel_launches == nullptr, "kernel timing is not available here");
+    if (spp == 0) return PT_OK;
+    void* base = nullptr;
+    pt_status r = noalloc_scratch(&base);
+    if (r != PT_OK) return r;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s->last_stream = st;
+    // carve the fixed array into the wavefront buffers
+    const size_t c = NOALLOC_MAX_PATHS;
+    float4* f4 = reinterpret_cast<float4*>(base);
+    WaveBuffers w;
+    w.capacity = NOALLOC_MAX_PATHS;
+    w.ray_o[0] = f4 + 0 * c; w.ray_o[1] = f4 + 1 * c;
+    w.ray_d[0] = f4 + 2 * c; w.ray_d[1] = f4 + 3 * c;
+    w.hit = f4 + 4 * c; w.beta = f4 + 5 * c; w.radiance = f4 + 6 * c;
+    w.sh_o = f4 + 7 * c; w.sh_d = f4 + 8 * c; w.sh_c = f4 + 9 * c;
+    uint32_t* u = reinterpret_cast<uint32_t*>(f4 + NOALLOC_F4 * c);
+    w.perm = u; w.keys = u + c; w.counters = u + 2 * c;
+    const uint32_t npix = acc->width * acc->height;
+    const uint32_t samp_per_wave = std::max(1u, std::min(spp, NOALLOC_MAX_PATHS / npix));
+    const bool sort = o.sort_by_material == 1 || (o.sort_by_material < 0 && s->n_mats + 2 <= MAX_SORT_KEYS && s->n_mats > 1);
+    const uint32_t n_keys = (sort && s->n_mats + 2 <= MAX_SORT_KEYS) ? s->n_mats + 2 : 0;
+    if (g_trace_blocks_per_sm == 0) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_trace<false>, 128, 0);
+        g_trace_blocks_per_sm = std::max(b, 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shade<false>, 128, 0);
+        g_shade_blocks_per_sm = std::max(b, 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shadow<false>, 128, 0);
+        g_shadow_blocks_per_sm = std::max(b, 1);
+    }
+    const int sms = pt_num_sms();
+    WfParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.S = s->view();
+    P.cam = to_dcam(*camera);
+    P.x0 = o.crop_x0;
+    P.y0 = o.crop_y0;
+    P.cw = acc->width;
+    P.s_call0 = (uint32_t)acc->spp_done;
+    P.spp_call = spp;
+    P.max_depth = max_depth;
+    P.flags = o.flags & (FLAG_NO_NEE | FLAG_NO_RR);
+    P.seed = seed;
+    P.n_keys = n_keys;
+    for (int q = 0; q < 2; ++q) { P.ray_o[q] = w.ray_o[q]; P.ray_d[q] = w.ray_d[q]; }
+    P.hit = w.hit; P.beta = w.beta; P.radiance = w.radiance;
+    P.sh_o = w.sh_o; P.sh_d = w.sh_d; P.sh_c = w.sh_c;
+    P.perm = w.perm; P.keys = w.keys; P.counters = w.counters;
+    P.sum = acc->sum; P.comp = acc->comp; P.sample_out = o.sample_out;
+    P.stats = s->d_stats;
+    P.pb = 0;
+    P.npix = npix;
+    uint64_t launches = 0;
+    for (uint32_t i0 = 0; i0 < spp; i0 += samp_per_wave) {
+        const uint32_t ns = std::min(samp_per_wave, spp - i0);
+        P.sb = (uint32_t)acc->spp_done + i0;
+        P.nsamp = ns;
+        const uint32_t n = npix * ns;
+        PT_LAUNCH(k_wf_raygen, (n + 255) / 256, 256, 0, st, P);
+        ++launches;
+        for (uint32_t k = 0; k <= max_depth; ++k) {
+            const int in_q = (int)(k & 1u), out_q = (int)((k + 1) & 1u);
+            PT_LAUNCH(k_wf_setup, 1, 256, 0, st, w.counters, out_q, n_keys);
+            PT_LAUNCH(k_wf_trace<false>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
+            launches += 2;
+            if (n_keys) {
+                PT_LAUNCH(k_wf_sort_scan, 1, MAX_SORT_KEYS, 0, st, w.counters, n_keys);
+                PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
+                launches += 2;
+            }
+            PT_LAUNCH(k_wf_shade<false>, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+            PT_LAUNCH(k_wf_shadow<false>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
+            launches += 2;
+        }
+        PT_LAUNCH(k_wf_accum, (npix + 255) / 256, 256, 0, st, P);
+        ++launches;
+    }
+    s->launches += launches;
+    PT_CUDA_TRY(cudaGetLastError());
+    acc->spp_done += spp;
     return PT_OK;
 }

@@ -91,6 +91,8 @@ SIGNATURES = {
     "pt_bvh_build": (C.c_int, [vp, C.POINTER(pt_bvh_opts), vp]),
     "pt_render": (C.c_int, [vp, C.POINTER(pt_camera), u32, u32, u64, C.POINTER(pt_accum),
                             C.POINTER(pt_render_opts), vp]),
+    "pt_render_noalloc": (C.c_int, [vp, C.POINTER(pt_camera), u32, u32, u64, C.POINTER(pt_accum),
+                                    C.POINTER(pt_render_opts), vp]),
     "pt_render_batch": (C.c_int, [C.POINTER(pt_job), u32, C.POINTER(pt_batch_opts), vp]),
     "pt_trace": (C.c_int, [vp, vp, u32, C.c_int, vp, vp, vp, vp]),
     "pt_bsdf_eval": (C.c_int, [vp, vp, vp, vp, u32, vp, vp, vp]),

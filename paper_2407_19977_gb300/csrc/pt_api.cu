@@ -345,7 +345,7 @@ extern "C" pt_status pt_get_stats(pt_scene* s, pt_stats* out) {
     out->paths = st[ST_PATHS];
     out->nan_dropped = st[ST_NAN];
     out->rr_terminated = st[ST_RR];
-    out->nrc_queries = s->nrc_queries_host;
+    out->nrc_queries = st[ST_NRC];
     out->kernel_launches = s->launches;
     out->bvh_nodes = s->n_nodes;
     out->bvh_depth = s->depth;

@@ -469,7 +469,7 @@ __device__ __forceinline__ uint32_t byte_of(uint32_t lo4, uint32_t hi4, int i) {
 }
 
 struct TravRay {
-    float3 o, d, inv, oinv;
+    float3 o, d, inv;
 };
 __device__ __forceinline__ TravRay make_trav(float3 o, float3 d) {
     TravRay r;
@@ -479,7 +479,6 @@ __device__ __forceinline__ TravRay make_trav(float3 o, float3 d) {
     r.inv = mk3(fabsf(d.x) > 1e-20f ? 1.0f / d.x : copysignf(big, d.x),
                 fabsf(d.y) > 1e-20f ? 1.0f / d.y : copysignf(big, d.y),
                 fabsf(d.z) > 1e-20f ? 1.0f / d.z : copysignf(big, d.z));
-    r.oinv = mk3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
     return r;
 }
 
@@ -507,25 +506,53 @@ __device__ __forceinline__ NodeView load_node(const uint4* __restrict__ nodes, u
     return v;
 }
 
-// slab test of child slot i; returns the entry distance (>= 0) or -1 on a miss.  A miss must
-// not look like +inf: before the first hit the closest-hit bound is +inf itself.
-__device__ __forceinline__ float child_hit(const NodeView& v, const TravRay& r, int i, float tmin, float tmax) {
-    // same fmaf as the builder's conservative quantisation check
-    const float lox = fmaf((float)byte_of(v.q0.x, v.q0.y, i), v.scale.x, v.p.x);
-    const float loy = fmaf((float)byte_of(v.q0.z, v.q0.w, i), v.scale.y, v.p.y);
-    const float loz = fmaf((float)byte_of(v.q1.x, v.q1.y, i), v.scale.z, v.p.z);
-    const float hix = fmaf((float)byte_of(v.q1.z, v.q1.w, i), v.scale.x, v.p.x);
-    const float hiy = fmaf((float)byte_of(v.q2.x, v.q2.y, i), v.scale.y, v.p.y);
-    const float hiz = fmaf((float)byte_of(v.q2.z, v.q2.w, i), v.scale.z, v.p.z);
-    // (lo - o) * inv: the error is relative to t itself, so boxes right next to the ray
-    // origin (bounce and shadow rays) are not lost to rounding
-    const float tx0 = __fmul_rn(__fsub_rn(lox, r.o.x), r.inv.x), tx1 = __fmul_rn(__fsub_rn(hix, r.o.x), r.inv.x);
-    const float ty0 = __fmul_rn(__fsub_rn(loy, r.o.y), r.inv.y), ty1 = __fmul_rn(__fsub_rn(hiy, r.o.y), r.inv.y);
-    const float tz0 = __fmul_rn(__fsub_rn(loz, r.o.z), r.inv.z), tz1 = __fmul_rn(__fsub_rn(hiz, r.o.z), r.inv.z);
-    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
-    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
-    // relative slack keeps flat boxes and rounding in the decode conservative
-    return tn <= tf * 1.00001f + 1e-30f ? tn : -1.0f;
+// Per-node setup of the child box tests.  Along each axis the near and far planes of child
+// slot i are p + q_near(i) * scale and p + q_far(i) * scale (near/far chosen once per ray by
+// the direction's sign), so their ray distances are fma(q, scale/d, (p - o)/d).  eps widens
+// every slab by a bound on the rounding of those terms (the products, the fma and the
+// builder's one-rounding decode), which keeps the test conservative.
+struct NodeTest {
+    float3 an, af, b;                              // (p - o)/d - eps, (p - o)/d + eps, scale/d
+    uint32_t nx0, nx1, ny0, ny1, nz0, nz1;         // near-plane byte words per axis
+    uint32_t fx0, fx1, fy0, fy1, fz0, fz1;         // far-plane byte words per axis
+};
+
+// byte i of the 8-byte array (w0, w1) as a float, via a float whose mantissa holds it
+__device__ __forceinline__ float qbyte(uint32_t w0, uint32_t w1, int i) {
+    return __uint_as_float(__byte_perm(i < 4 ? w0 : w1, 0x4B000000u, 0x7440u | (uint32_t)(i & 3))) - 8388608.0f;
+}
+
+__device__ __forceinline__ void node_setup(const NodeView& v, const TravRay& r, NodeTest& T) {
+    const float ax = __fmul_rn(__fsub_rn(v.p.x, r.o.x), r.inv.x);
+    const float ay = __fmul_rn(__fsub_rn(v.p.y, r.o.y), r.inv.y);
+    const float az = __fmul_rn(__fsub_rn(v.p.z, r.o.z), r.inv.z);
+    T.b = mk3(v.scale.x * r.inv.x, v.scale.y * r.inv.y, v.scale.z * r.inv.z);
+    const float ex = 4e-7f * (fabsf(ax) + 255.0f * fabsf(T.b.x) + fabsf(v.p.x * r.inv.x));
+    const float ey = 4e-7f * (fabsf(ay) + 255.0f * fabsf(T.b.y) + fabsf(v.p.y * r.inv.y));
+    const float ez = 4e-7f * (fabsf(az) + 255.0f * fabsf(T.b.z) + fabsf(v.p.z * r.inv.z));
+    T.an = mk3(ax - ex, ay - ey, az - ez);
+    T.af = mk3(ax + ex, ay + ey, az + ez);
+    const bool px = r.inv.x >= 0.0f, py = r.inv.y >= 0.0f, pz = r.inv.z >= 0.0f;
+    // lo words: x (q0.x, q0.y), y (q0.z, q0.w), z (q1.x, q1.y); hi: x (q1.z, q1.w), y (q2.x, q2.y), z (q2.z, q2.w)
+    T.nx0 = px ? v.q0.x : v.q1.z; T.nx1 = px ? v.q0.y : v.q1.w;
+    T.fx0 = px ? v.q1.z : v.q0.x; T.fx1 = px ? v.q1.w : v.q0.y;
+    T.ny0 = py ? v.q0.z : v.q2.x; T.ny1 = py ? v.q0.w : v.q2.y;
+    T.fy0 = py ? v.q2.x : v.q0.z; T.fy1 = py ? v.q2.y : v.q0.w;
+    T.nz0 = pz ? v.q1.x : v.q2.z; T.nz1 = pz ? v.q1.y : v.q2.w;
+    T.fz0 = pz ? v.q2.z : v.q1.x; T.fz1 = pz ? v.q2.w : v.q1.y;
+}
+
+// entry distance of child slot i, or -1 if the ray misses its box within [0, tmax]
+__device__ __forceinline__ float child_test(const NodeTest& T, int i, float tmax) {
+    const float ex = fmaf(qbyte(T.nx0, T.nx1, i), T.b.x, T.an.x);
+    const float ey = fmaf(qbyte(T.ny0, T.ny1, i), T.b.y, T.an.y);
+    const float ez = fmaf(qbyte(T.nz0, T.nz1, i), T.b.z, T.an.z);
+    const float xx = fmaf(qbyte(T.fx0, T.fx1, i), T.b.x, T.af.x);
+    const float xy = fmaf(qbyte(T.fy0, T.fy1, i), T.b.y, T.af.y);
+    const float xz = fmaf(qbyte(T.fz0, T.fz1, i), T.b.z, T.af.z);
+    const float tn = fmaxf(fmaxf(ex, ey), fmaxf(ez, 0.0f));
+    const float tf = fminf(fminf(xx, xy), fminf(xz, tmax));
+    return tn <= tf ? tn : -1.0f;
 }
 
 struct HitRec {
@@ -538,143 +565,192 @@ struct TravCount {
     uint32_t nodes, tris;
 };
 
-// Closest hit in (0, tmax); equal t resolved towards the lower original triangle id.
-// Per node: the eight box tests are unrolled; the nearest internal child is descended
-// into and the other hit children go on the stack; leaf children are collected in a bit
-// mask and intersected afterwards by one loop, so the triangle test exists once in the
-// code (small instruction footprint, less divergence).
+// Closest-hit traversal as a state machine: closest_init sets up one ray, closest_step
+// processes one node (eight unrolled box tests; the nearest internal child is descended
+// into, the others go on the stack; leaf children are collected in a bit mask and their
+// triangles intersected afterwards by one loop, so the triangle test exists once in the
+// code) and returns true once the ray is finished; trace_closest_t runs one ray to
+// completion.  (Refilling a finished lane with a new ray between steps was measured slower
+// on the 1080p CAD frame: lanes at different depths diverge more than idle lanes cost.)
+// Equal t resolves towards the lower original triangle id.
+struct ClosestState {
+    WRay wr;
+    TravRay tr;
+    float tmax;
+    HitRec h;
+    uint32_t best_orig, node, budget;
+    int sp;
+};
+
+__device__ __forceinline__ void closest_init(const DScene& S, float3 o, float3 d, float tmax, ClosestState& st) {
+    st.wr = make_wray(o, d);
+    st.tr = make_trav(o, d);
+    st.tmax = tmax;
+    st.h.t = tmax;
+    st.h.tri = PT_NO_HIT;
+    st.h.u = st.h.v = 0.0f;
+    st.best_orig = PT_NO_HIT;
+    st.node = 0;
+    st.sp = 0;
+    // a tree traversal visits every node at most once: more visits mean a malformed tree
+    st.budget = (uint32_t)S.n_nodes + 1u;
+}
+
+// the stack is a separate local array so the scalar state stays in registers
+template <bool COUNT>
+__device__ __forceinline__ bool closest_step(const DScene& S, ClosestState& st, uint2 (&stack)[PT_STACK], TravCount& tc) {
+    if (S.n_nodes == 0) return true;
+    if (st.budget-- == 0u) { atomicOr(S.err, 4u); st.h.tri = PT_NO_HIT; return true; }
+    const NodeView v = load_node(S.nodes, st.node);
+    if (COUNT) tc.nodes++;
+    NodeTest T;
+    node_setup(v, st.tr, T);
+    uint32_t leafmask = 0u;
+    uint32_t near_node = PT_NO_HIT;
+    float near_t = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (byte_of(v.meta_lo, v.meta_hi, i) == 0u) continue;
+        const float tn = child_test(T, i, st.h.t);
+        if (!(tn >= 0.0f && tn <= st.h.t)) continue;
+        if ((v.imask >> i) & 1u) {
+            const uint32_t c = v.child_base + __popc(v.imask & ((1u << i) - 1u));
+            uint32_t push_node = c;
+            float push_t = tn;
+            if (tn < near_t) {
+                push_node = near_node;
+                push_t = near_t;
+                near_node = c;
+                near_t = tn;
+            }
+            if (push_node != PT_NO_HIT) {
+                if (st.sp >= PT_STACK) { atomicOr(S.err, 1u); return true; }
+                stack[st.sp++] = make_uint2(push_node, __float_as_uint(push_t));
+            }
+        } else {
+            leafmask |= 1u << i;
+        }
+    }
+    while (leafmask) {
+        const int i = __ffs(leafmask) - 1;
+        leafmask &= leafmask - 1u;
+        const uint32_t meta = byte_of(v.meta_lo, v.meta_hi, i);
+        const uint32_t first = v.tri_base + (meta & 31u);
+        const uint32_t cnt = meta >> 5;
+        if (COUNT) tc.tris += cnt;
+        for (uint32_t k = 0; k < cnt; ++k) {
+            const uint32_t ti = first + k;
+            const float4 a = __ldg(S.tris + 3u * ti), b = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
+            float t, u, w;
+            if (tri_hit(st.wr, xyz(a), xyz(b), xyz(c), st.tmax, t, u, w)) {
+                const uint32_t orig = __float_as_uint(a.w);
+                if (t < st.h.t || (t == st.h.t && orig < st.best_orig)) {
+                    st.h.t = t; st.h.u = u; st.h.v = w; st.h.tri = ti; st.best_orig = orig;
+                }
+            }
+        }
+    }
+    if (near_node != PT_NO_HIT && near_t <= st.h.t) {
+        st.node = near_node;
+        return false;
+    }
+    // pop the next child whose entry distance is still within the closest hit
+    while (st.sp > 0) {
+        const uint2 e = stack[--st.sp];
+        if (__uint_as_float(e.y) <= st.h.t) { st.node = e.x; return false; }
+    }
+    return true;
+}
+
 template <bool COUNT>
 __device__ __forceinline__ void trace_closest_t(const DScene& S, float3 o, float3 d, float tmax, HitRec& h,
                                                 TravCount& tc) {
-    h.t = tmax;
-    h.tri = PT_NO_HIT;
-    h.u = h.v = 0.0f;
-    if (S.n_nodes == 0) return;
-    const WRay wr = make_wray(o, d);
-    const TravRay tr = make_trav(o, d);
-    uint32_t best_orig = PT_NO_HIT;
+    ClosestState st;
     uint2 stack[PT_STACK];
-    int sp = 0;
-    uint32_t node = 0;
-    // a tree traversal visits every node at most once: more visits mean a malformed tree
-    uint32_t budget = (uint32_t)S.n_nodes + 1u;
-    for (;;) {
-        if (budget-- == 0u) { atomicOr(S.err, 4u); h.tri = PT_NO_HIT; return; }
-        const NodeView v = load_node(S.nodes, node);
-        if (COUNT) tc.nodes++;
-        uint32_t leafmask = 0u;
-        uint32_t near_node = PT_NO_HIT;
-        float near_t = __int_as_float(0x7f800000);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (byte_of(v.meta_lo, v.meta_hi, i) == 0u) continue;
-            const float tn = child_hit(v, tr, i, 0.0f, h.t);
-            if (!(tn >= 0.0f && tn <= h.t)) continue;
-            if ((v.imask >> i) & 1u) {
-                const uint32_t c = v.child_base + __popc(v.imask & ((1u << i) - 1u));
-                uint32_t push_node = c;
-                float push_t = tn;
-                if (tn < near_t) {
-                    push_node = near_node;
-                    push_t = near_t;
-                    near_node = c;
-                    near_t = tn;
-                }
-                if (push_node != PT_NO_HIT) {
-                    if (sp >= PT_STACK) { atomicOr(S.err, 1u); return; }
-                    stack[sp++] = make_uint2(push_node, __float_as_uint(push_t));
-                }
-            } else {
-                leafmask |= 1u << i;
-            }
-        }
-        while (leafmask) {
-            const int i = __ffs(leafmask) - 1;
-            leafmask &= leafmask - 1u;
-            const uint32_t meta = byte_of(v.meta_lo, v.meta_hi, i);
-            const uint32_t first = v.tri_base + (meta & 31u);
-            const uint32_t cnt = meta >> 5;
-            if (COUNT) tc.tris += cnt;
-            for (uint32_t k = 0; k < cnt; ++k) {
-                const uint32_t ti = first + k;
-                const float4 a = __ldg(S.tris + 3u * ti), b = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
-                float t, u, w;
-                if (tri_hit(wr, xyz(a), xyz(b), xyz(c), tmax, t, u, w)) {
-                    const uint32_t orig = __float_as_uint(a.w);
-                    if (t < h.t || (t == h.t && orig < best_orig)) {
-                        h.t = t; h.u = u; h.v = w; h.tri = ti; best_orig = orig;
-                    }
-                }
-            }
-        }
-        if (near_node != PT_NO_HIT && near_t <= h.t) {
-            node = near_node;
-            continue;
-        }
-        // pop the next child whose entry distance is still within the closest hit
-        bool found = false;
-        while (sp > 0) {
-            const uint2 e = stack[--sp];
-            if (__uint_as_float(e.y) <= h.t) { node = e.x; found = true; break; }
-        }
-        if (!found) return;
+    closest_init(S, o, d, tmax, st);
+    while (!closest_step<COUNT>(S, st, stack, tc)) {
     }
+    h = st.h;
 }
 
-// Any hit in (0, tmax): occlusion test for shadow rays.
+// Any hit in (0, tmax): occlusion test for shadow rays, in the same step form.
+struct AnyState {
+    WRay wr;
+    TravRay tr;
+    float tmax;
+    uint32_t node, budget;
+    int sp;
+    bool hit;
+};
+
+__device__ __forceinline__ void any_init(const DScene& S, float3 o, float3 d, float tmax, AnyState& st) {
+    st.wr = make_wray(o, d);
+    st.tr = make_trav(o, d);
+    st.tmax = tmax;
+    st.node = 0;
+    st.sp = 0;
+    st.hit = false;
+    st.budget = (uint32_t)S.n_nodes + 1u;
+}
+
 template <bool COUNT>
-__device__ __forceinline__ bool trace_any_t(const DScene& S, float3 o, float3 d, float tmax, TravCount& tc) {
-    if (S.n_nodes == 0) return false;
-    const WRay wr = make_wray(o, d);
-    const TravRay tr = make_trav(o, d);
-    uint32_t stack[PT_STACK];
-    int sp = 0;
-    uint32_t node = 0;
-    uint32_t budget = (uint32_t)S.n_nodes + 1u;
-    for (;;) {
-        if (budget-- == 0u) { atomicOr(S.err, 4u); return false; }
-        const NodeView v = load_node(S.nodes, node);
-        if (COUNT) tc.nodes++;
-        uint32_t leafmask = 0u;
-        uint32_t next = PT_NO_HIT;
+__device__ __forceinline__ bool any_step(const DScene& S, AnyState& st, uint32_t (&stack)[PT_STACK], TravCount& tc) {
+    if (S.n_nodes == 0) return true;
+    if (st.budget-- == 0u) { atomicOr(S.err, 4u); return true; }
+    const NodeView v = load_node(S.nodes, st.node);
+    if (COUNT) tc.nodes++;
+    NodeTest T;
+    node_setup(v, st.tr, T);
+    uint32_t leafmask = 0u;
+    uint32_t next = PT_NO_HIT;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (byte_of(v.meta_lo, v.meta_hi, i) == 0u) continue;
-            const float tn = child_hit(v, tr, i, 0.0f, tmax);
-            if (!(tn >= 0.0f && tn <= tmax)) continue;
-            if ((v.imask >> i) & 1u) {
-                const uint32_t c = v.child_base + __popc(v.imask & ((1u << i) - 1u));
-                if (next == PT_NO_HIT) {
-                    next = c;
-                } else {
-                    if (sp >= PT_STACK) { atomicOr(S.err, 1u); return true; }
-                    stack[sp++] = c;
-                }
+    for (int i = 0; i < 8; ++i) {
+        if (byte_of(v.meta_lo, v.meta_hi, i) == 0u) continue;
+        const float tn = child_test(T, i, st.tmax);
+        if (!(tn >= 0.0f && tn <= st.tmax)) continue;
+        if ((v.imask >> i) & 1u) {
+            const uint32_t c = v.child_base + __popc(v.imask & ((1u << i) - 1u));
+            if (next == PT_NO_HIT) {
+                next = c;
             } else {
-                leafmask |= 1u << i;
+                if (st.sp >= PT_STACK) { atomicOr(S.err, 1u); st.hit = true; return true; }
+                stack[st.sp++] = c;
             }
-        }
-        while (leafmask) {
-            const int i = __ffs(leafmask) - 1;
-            leafmask &= leafmask - 1u;
-            const uint32_t meta = byte_of(v.meta_lo, v.meta_hi, i);
-            const uint32_t first = v.tri_base + (meta & 31u);
-            const uint32_t cnt = meta >> 5;
-            for (uint32_t k = 0; k < cnt; ++k) {
-                const uint32_t ti = first + k;
-                if (COUNT) tc.tris++;
-                const float4 a = __ldg(S.tris + 3u * ti), b = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
-                float t, u, w;
-                if (tri_hit(wr, xyz(a), xyz(b), xyz(c), tmax, t, u, w)) return true;
-            }
-        }
-        if (next != PT_NO_HIT) {
-            node = next;
         } else {
-            if (sp == 0) return false;
-            node = stack[--sp];
+            leafmask |= 1u << i;
         }
     }
+    while (leafmask) {
+        const int i = __ffs(leafmask) - 1;
+        leafmask &= leafmask - 1u;
+        const uint32_t meta = byte_of(v.meta_lo, v.meta_hi, i);
+        const uint32_t first = v.tri_base + (meta & 31u);
+        const uint32_t cnt = meta >> 5;
+        for (uint32_t k = 0; k < cnt; ++k) {
+            const uint32_t ti = first + k;
+            if (COUNT) tc.tris++;
+            const float4 a = __ldg(S.tris + 3u * ti), b = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
+            float t, u, w;
+            if (tri_hit(st.wr, xyz(a), xyz(b), xyz(c), st.tmax, t, u, w)) { st.hit = true; return true; }
+        }
+    }
+    if (next != PT_NO_HIT) {
+        st.node = next;
+        return false;
+    }
+    if (st.sp == 0) return true;
+    st.node = stack[--st.sp];
+    return false;
+}
+
+template <bool COUNT>
+__device__ __forceinline__ bool trace_any_t(const DScene& S, float3 o, float3 d, float tmax, TravCount& tc) {
+    AnyState st;
+    uint32_t stack[PT_STACK];
+    any_init(S, o, d, tmax, st);
+    while (!any_step<COUNT>(S, st, stack, tc)) {
+    }
+    return st.hit;
 }
 
 // out-of-line entry points keep the megakernel's code and registers in check

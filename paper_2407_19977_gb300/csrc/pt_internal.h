@@ -101,7 +101,6 @@ struct pt_scene {
     WaveBuffers wave;
     cudaStream_t last_stream = nullptr;
     uint64_t launches = 0;
-    uint64_t nrc_queries_host = 0, nrc_samples_host = 0;
 
     DScene view() const {
         DScene s;
@@ -133,8 +132,11 @@ pt_status pt_build_env_impl(pt_scene* s, cudaStream_t st);
 // implemented in pt_render.cu
 pt_status pt_free_wave(WaveBuffers& w);
 
-// implemented in pt_nrc.cu: cache forward pass for the renderer (outputs 4 floats per query)
-pt_status pt_nrc_render_infer(pt_nrc* N, const float* queries, uint32_t n, float* out4, cudaStream_t st);
+// implemented in pt_nrc.cu: cache forward pass / one training step for the renderer; the
+// row count is read from device memory (n_dev), cap bounds it and sizes the launches
+pt_status pt_nrc_render_infer_dev(pt_nrc* N, const float* queries, const uint32_t* n_dev, uint32_t cap, float* out4,
+                                  cudaStream_t st);
+pt_status pt_nrc_render_train_dev(pt_nrc* N, const float* samples, const uint32_t* n_dev, uint32_t cap, cudaStream_t st);
 
 inline DCam to_dcam(const pt_camera& c) {
     DCam d;

@@ -47,6 +47,13 @@ __device__ __forceinline__ float2 unpack_h2(uint32_t v) {
     return __half22float2(h);
 }
 
+// row count of a launch: the host value, or the device counter (clamped to the capacity)
+struct RowCount {
+    uint32_t n;              // host count, or capacity when `dev` is set
+    const uint32_t* dev;     // optional device counter
+    __device__ __forceinline__ uint32_t get() const { return dev ? min(*dev, n) : n; }
+};
+
 struct GridDesc {
     const __half* table;     // L x T x 2 (FP16 copy used by lookups)
     float* grad;             // L x T x 2 (FP32)
@@ -71,10 +78,11 @@ __device__ __forceinline__ float3 pos01(const GridDesc& G, const float* q) {
 
 // one thread per (query, level): interpolated features of that level -> X[q][2l..2l+1];
 // the same thread writes columns 32 + 2l, 33 + 2l of the non-grid part
-__global__ void k_encode(GridDesc G, const float* __restrict__ queries, uint32_t n, __half* __restrict__ X) {
-    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t q = gid / G.L, l = gid % G.L;
-    if (q >= n) return;
+__global__ void k_encode(GridDesc G, const float* __restrict__ queries, RowCount rc, __half* __restrict__ X) {
+  const uint32_t n = rc.get();
+  for (uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; gid < (uint64_t)n * G.L;
+       gid += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t q = (uint32_t)(gid / G.L), l = (uint32_t)(gid % G.L);
     const float* rec = queries + (size_t)QSTRIDE * q;
     const float3 p = pos01(G, rec);
     const uint32_t res = G.res[l];
@@ -107,14 +115,16 @@ __global__ void k_encode(GridDesc G, const float* __restrict__ queries, uint32_t
     }
     if (l == 0)
         for (uint32_t c = g0 + 2 * G.L; c < (uint32_t)W; ++c) row[c] = __float2half_rn(0.0f);
+  }
 }
 
 // grid gradient: recompute the corners and scatter dL/dfeature (FP32 atomics)
-__global__ void k_grid_backward(GridDesc G, const float* __restrict__ samples, uint32_t n, const float* __restrict__ dX,
-                                float scale) {
-    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t q = gid / G.L, l = gid % G.L;
-    if (q >= n) return;
+__global__ void k_grid_backward(GridDesc G, const float* __restrict__ samples, RowCount rc, const float* __restrict__ dX) {
+  const uint32_t n = rc.get();
+  const float scale = n ? 1.0f / (3.0f * (float)n) : 0.0f;
+  for (uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; gid < (uint64_t)n * G.L;
+       gid += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t q = (uint32_t)(gid / G.L), l = (uint32_t)(gid % G.L);
     const float3 p = pos01(G, samples + (size_t)QSTRIDE * q);
     const uint32_t res = G.res[l];
     const float fx = p.x * res, fy = p.y * res, fz = p.z * res;
@@ -130,6 +140,7 @@ __global__ void k_grid_backward(GridDesc G, const float* __restrict__ samples, u
         atomicAdd(gr + 2 * idx, w * g0);
         atomicAdd(gr + 2 * idx + 1, w * g1);
     }
+  }
 }
 
 // ---- fused MLP forward: one warp per 16 rows, weights in padded shared memory ----
@@ -194,12 +205,13 @@ __device__ __forceinline__ void store_afrag(__half* M, uint32_t n, uint32_t r0, 
 }
 
 // X (n x 64 FP16) -> Y (n x 4 FP32, RGB + unused); acts (optional): A1..A4 (4 x n x 64)
-__global__ void __launch_bounds__(128) k_mlp_forward(const __half* __restrict__ X, uint32_t n,
+__global__ void __launch_bounds__(128) k_mlp_forward(const __half* __restrict__ X, RowCount rc,
                                                      const __half* __restrict__ Wg, float* __restrict__ Y,
                                                      __half* __restrict__ acts) {
     __shared__ __align__(16) __half sw[(N_HIDDEN * W + OUT_PAD) * SROW];
     load_weights_smem(sw, Wg);
     __syncthreads();
+    const uint32_t n = rc.get();
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < n; tile += warps) {
@@ -212,7 +224,7 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const __half* __restrict__ 
             float acc[8][4];
             layer_fwd<8>(acc, a, sw + l * W * SROW, g, t);
             relu_to_a(a, acc);
-            if (acts) store_afrag(acts + (size_t)l * n * W, n, r0, a, g, t);
+            if (acts) store_afrag(acts + (size_t)l * rc.n * W, n, r0, a, g, t);
         }
         float out[2][4];
         layer_fwd<2>(out, a, sw + N_HIDDEN * W * SROW, g, t);
@@ -227,9 +239,12 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const __half* __restrict__ 
 
 // relative L2 loss: dL/dy * (3n) (the 1/(3n) of the mean is applied to the gradients later
 // so that FP16 keeps them in its normal range), plus the loss sum
-__global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ samples, uint32_t n, __half* __restrict__ dY,
+__global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ samples, RowCount rc, __half* __restrict__ dY,
                        float* __restrict__ loss_sum) {
-    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = rc.get();
+  if (blockIdx.x == 0 && threadIdx.x == 0) loss_sum[1] = (float)n;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const uint32_t q = base + threadIdx.x;
     float l = 0.0f;
     if (q < n) {
         const float* tg = samples + (size_t)QSTRIDE * q + 10;
@@ -245,6 +260,7 @@ __global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ sa
     }
     for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
     if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, l);
+  }
 }
 
 // B fragment of W_l read transposed: B[k][n] = W_l[k][n] (k = layer output, n = layer input)
@@ -256,12 +272,14 @@ __device__ __forceinline__ void bfrag_t(uint32_t& b0, uint32_t& b1, const __half
 
 // backward chain per 16-row tile: dZ4 = (dY W4) * [A4 > 0], ..., dZ1 = (dZ2 W1) * [A1 > 0],
 // dX = dZ1 W0 (grid columns only).  Stores dZ1..dZ4 (FP16) for the weight gradients.
-__global__ void __launch_bounds__(128) k_mlp_backward(const __half* __restrict__ dY, uint32_t n,
+__global__ void __launch_bounds__(128) k_mlp_backward(const __half* __restrict__ dY, RowCount rc,
                                                       const __half* __restrict__ Wg, const __half* __restrict__ acts,
                                                       __half* __restrict__ dZ, float* __restrict__ dX, uint32_t n_grid_cols) {
     __shared__ __align__(16) __half sw[(N_HIDDEN * W + OUT_PAD) * SROW];
     load_weights_smem(sw, Wg);
     __syncthreads();
+    const uint32_t n = rc.get();
+    const size_t cap = rc.n;
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < n; tile += warps) {
@@ -283,7 +301,7 @@ __global__ void __launch_bounds__(128) k_mlp_backward(const __half* __restrict__
         uint32_t a[4][4];
         for (int l = N_HIDDEN - 1; l >= 0; --l) {
             // mask with A_{l+1} > 0 (A index l holds the output of hidden layer l)
-            const __half* A = acts + (size_t)l * n * W;
+            const __half* A = acts + (size_t)l * cap * W;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int c = 8 * j + 2 * t;
@@ -301,7 +319,7 @@ __global__ void __launch_bounds__(128) k_mlp_backward(const __half* __restrict__
                 a[kt][2] = pack_h2(acc[2 * kt + 1][0], acc[2 * kt + 1][1]);
                 a[kt][3] = pack_h2(acc[2 * kt + 1][2], acc[2 * kt + 1][3]);
             }
-            store_afrag(dZ + (size_t)l * n * W, n, r0, a, g, t);
+            store_afrag(dZ + (size_t)l * cap * W, n, r0, a, g, t);
             // propagate through W_l: next acc = dZ_l . W_l
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
@@ -331,7 +349,8 @@ __global__ void __launch_bounds__(128) k_mlp_backward(const __half* __restrict__
 // (G = dZ of the layer's output, A = the layer's input); a warp owns 16 outputs x 64 inputs
 constexpr int DW_CHUNK = 512;
 __global__ void __launch_bounds__(128) k_weight_grad(const __half* __restrict__ G, uint32_t g_stride, uint32_t n_out,
-                                                     const __half* __restrict__ A, uint32_t n, float* __restrict__ part) {
+                                                     const __half* __restrict__ A, RowCount rc, float* __restrict__ part) {
+    const uint32_t n = rc.get();
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
     const int m0 = 16 * warp;
     float acc[8][4];
@@ -372,9 +391,11 @@ __global__ void __launch_bounds__(128) k_weight_grad(const __half* __restrict__ 
 }
 
 __global__ void k_reduce_grad(const float* __restrict__ part, uint32_t nparts, uint32_t n_out, float* __restrict__ dst,
-                              float scale) {
+                              RowCount rc) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_out * W) return;
+    const uint32_t n = rc.get();
+    const float scale = n ? 1.0f / (3.0f * (float)n) : 0.0f;
     float s = 0.0f;
     for (uint32_t p = 0; p < nparts; ++p) s += part[(size_t)p * W * W + i];
     dst[i] = s * scale;
@@ -555,39 +576,45 @@ extern "C" void pt_nrc_destroy(pt_nrc* N) {
     delete N;
 }
 
-// forward (+ optional activations) of n records already resident on the device
-static pt_status nrc_forward(pt_nrc* N, const float* q, uint32_t n, __half* X, float* Y, __half* acts, cudaStream_t st) {
+static uint32_t encode_grid(uint32_t cap, uint32_t L) {
+    const uint64_t threads = (uint64_t)cap * L;
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((threads + 255) / 256, 32ull * pt_num_sms()));
+}
+
+// forward (+ optional activations) of rc rows already resident on the device
+static pt_status nrc_forward(pt_nrc* N, const float* q, RowCount rc, __half* X, float* Y, __half* acts, cudaStream_t st) {
     const GridDesc G = grid_desc(N);
-    const uint64_t threads = (uint64_t)n * N->L;
-    PT_LAUNCH(k_encode, (uint32_t)((threads + 255) / 256), 256, 0, st, G, q, n, X);
-    PT_LAUNCH(k_mlp_forward, mlp_grid(n), 128, 0, st, X, n, N->d_wh, Y, acts);
+    PT_LAUNCH(k_encode, encode_grid(rc.n, N->L), 256, 0, st, G, q, rc, X);
+    PT_LAUNCH(k_mlp_forward, mlp_grid(rc.n), 128, 0, st, X, rc, N->d_wh, Y, acts);
     N->launches += 2;
     PT_CUDA_TRY(cudaGetLastError());
     return PT_OK;
 }
 
-// loss and gradients of one batch into d_wg / d_gg (accumulated; caller zeroes via Adam)
-static pt_status nrc_gradients(pt_nrc* N, const float* samples, uint32_t n, cudaStream_t st) {
-    pt_status r = ensure_train(N, n);
+// loss and gradients of one batch into d_wg / d_gg (accumulated; caller zeroes via Adam).
+// rc.n is the capacity the buffers are laid out with; rc.dev (optional) the row count.
+static pt_status nrc_gradients(pt_nrc* N, const float* samples, RowCount rc, cudaStream_t st) {
+    pt_status r = ensure_train(N, rc.n);
     if (r != PT_OK) return r;
-    r = nrc_forward(N, samples, n, N->X, N->Y, N->acts, st);
+    // every training buffer is addressed with the row stride rc.n (<= the allocation)
+    const RowCount rb = rc;
+    r = nrc_forward(N, samples, rb, N->X, N->Y, N->acts, st);
     if (r != PT_OK) return r;
     PT_CUDA_TRY(cudaMemsetAsync(N->d_loss, 0, sizeof(float), st));
-    PT_LAUNCH(k_loss, (n + 255) / 256, 256, 0, st, N->Y, samples, n, N->dY, N->d_loss);
-    PT_LAUNCH(k_mlp_backward, mlp_grid(n), 128, 0, st, N->dY, n, N->d_wh, N->acts, N->dZ, N->dX, N->grid_cols);
-    const float scale = 1.0f / (3.0f * (float)n);
-    const uint32_t nparts = (n + DW_CHUNK - 1) / DW_CHUNK;
+    const uint32_t gl = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((rb.n + 255) / 256, 8ull * pt_num_sms()));
+    PT_LAUNCH(k_loss, gl, 256, 0, st, N->Y, samples, rb, N->dY, N->d_loss);
+    PT_LAUNCH(k_mlp_backward, mlp_grid(rb.n), 128, 0, st, N->dY, rb, N->d_wh, N->acts, N->dZ, N->dX, N->grid_cols);
+    const uint32_t nparts = (rb.n + DW_CHUNK - 1) / DW_CHUNK;
     // layer l's weight gradient pairs dZ_l (its output gradient) with its input
     for (int l = 0; l <= N_HIDDEN; ++l) {
-        const __half* Gm = l < N_HIDDEN ? N->dZ + (size_t)l * n * W : N->dY;
+        const __half* Gm = l < N_HIDDEN ? N->dZ + (size_t)l * rb.n * W : N->dY;
         const uint32_t gs = l < N_HIDDEN ? W : OUT_PAD;
         const uint32_t nout = l < N_HIDDEN ? W : OUT_PAD;
-        const __half* Ain = l == 0 ? N->X : N->acts + (size_t)(l - 1) * n * W;
-        PT_LAUNCH(k_weight_grad, nparts, 128, 0, st, Gm, gs, nout, Ain, n, N->part);
-        PT_LAUNCH(k_reduce_grad, (nout * W + 255) / 256, 256, 0, st, N->part, nparts, nout, N->d_wg + (size_t)l * W * W, scale);
+        const __half* Ain = l == 0 ? N->X : N->acts + (size_t)(l - 1) * rb.n * W;
+        PT_LAUNCH(k_weight_grad, nparts, 128, 0, st, Gm, gs, nout, Ain, rb, N->part);
+        PT_LAUNCH(k_reduce_grad, (nout * W + 255) / 256, 256, 0, st, N->part, nparts, nout, N->d_wg + (size_t)l * W * W, rb);
     }
-    const uint64_t threads = (uint64_t)n * N->L;
-    PT_LAUNCH(k_grid_backward, (uint32_t)((threads + 255) / 256), 256, 0, st, grid_desc(N), samples, n, N->dX, scale);
+    PT_LAUNCH(k_grid_backward, encode_grid(rb.n, N->L), 256, 0, st, grid_desc(N), samples, rb, N->dX);
     N->launches += 4 + 2 * (N_HIDDEN + 1);
     PT_CUDA_TRY(cudaGetLastError());
     return PT_OK;
@@ -612,7 +639,7 @@ extern "C" pt_status pt_nrc_train(pt_nrc* N, const float* samples, uint32_t n, v
     cudaStream_t st = (cudaStream_t)cuda_stream;
     for (uint32_t b = 0; b < n; b += N->o.batch) {
         const uint32_t m = std::min(N->o.batch, n - b);
-        pt_status r = nrc_gradients(N, samples + (size_t)QSTRIDE * b, m, st);
+        pt_status r = nrc_gradients(N, samples + (size_t)QSTRIDE * b, RowCount{m, nullptr}, st);
         if (r != PT_OK) return r;
         r = nrc_adam(N, st);
         if (r != PT_OK) return r;
@@ -626,7 +653,7 @@ extern "C" pt_status pt_nrc_gradients(pt_nrc* N, const float* samples, uint32_t 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     PT_CUDA_TRY(cudaMemsetAsync(N->d_wg, 0, N_WEIGHTS * sizeof(float), st));
     PT_CUDA_TRY(cudaMemsetAsync(N->d_gg, 0, N->n_grid * sizeof(float), st));
-    pt_status r = nrc_gradients(N, samples, n, st);
+    pt_status r = nrc_gradients(N, samples, RowCount{n, nullptr}, st);
     if (r != PT_OK) return r;
     if (dw_out) PT_CUDA_TRY(cudaMemcpyAsync(dw_out, N->d_wg, N_WEIGHTS * sizeof(float), cudaMemcpyDeviceToDevice, st));
     if (dgrid_out) PT_CUDA_TRY(cudaMemcpyAsync(dgrid_out, N->d_gg, N->n_grid * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -646,7 +673,7 @@ extern "C" pt_status pt_nrc_infer(pt_nrc* N, const float* queries, uint32_t n, f
         N->icap = n;
     }
     // the MLP writes 4 floats per row; out_rgb is the caller's n x 4 buffer
-    return nrc_forward(N, queries, n, N->iX, out_rgb, nullptr, st);
+    return nrc_forward(N, queries, RowCount{n, nullptr}, N->iX, out_rgb, nullptr, st);
 }
 
 extern "C" pt_status pt_nrc_params(pt_nrc* N, int which, float** ptr, uint64_t* count) {
@@ -669,14 +696,28 @@ extern "C" pt_status pt_nrc_commit(pt_nrc* N, void* cuda_stream) {
 extern "C" pt_status pt_nrc_last_loss(pt_nrc* N, float* loss) {
     PT_CHECK_ARG(N && loss, "NULL argument");
     PT_CUDA_TRY(cudaDeviceSynchronize());
-    float s = 0.0f;
-    PT_CUDA_TRY(cudaMemcpy(&s, N->d_loss, sizeof(float), cudaMemcpyDeviceToHost));
-    const uint32_t n = std::min(N->cap, N->o.batch);
-    *loss = n ? s / (3.0f * (float)n) : 0.0f;
+    float s[2] = {0.0f, 0.0f};
+    PT_CUDA_TRY(cudaMemcpy(s, N->d_loss, 2 * sizeof(float), cudaMemcpyDeviceToHost));
+    *loss = s[1] > 0.0f ? s[0] / (3.0f * s[1]) : 0.0f;
     return PT_OK;
 }
 
-// ---- hooks used by the renderer ----
-pt_status pt_nrc_render_infer(pt_nrc* N, const float* queries, uint32_t n, float* out4, cudaStream_t st) {
-    return pt_nrc_infer(N, queries, n, out4, (void*)st);
+// ---- hooks used by the renderer: the row counts stay on the device (no host round trip) ----
+pt_status pt_nrc_render_infer_dev(pt_nrc* N, const float* queries, const uint32_t* n_dev, uint32_t cap, float* out4,
+                                  cudaStream_t st) {
+    if (N->icap < cap) {
+        if (N->iX) cudaFree(N->iX);
+        N->iX = nullptr;
+        PT_CUDA_TRY(cudaMalloc(&N->iX, (size_t)cap * W * sizeof(__half)));
+        N->icap = cap;
+    }
+    return nrc_forward(N, queries, RowCount{cap, n_dev}, N->iX, out4, nullptr, st);
+}
+
+pt_status pt_nrc_render_train_dev(pt_nrc* N, const float* samples, const uint32_t* n_dev, uint32_t cap, cudaStream_t st) {
+    pt_status r = ensure_train(N, cap);
+    if (r != PT_OK) return r;
+    r = nrc_gradients(N, samples, RowCount{cap, n_dev}, st);
+    if (r != PT_OK) return r;
+    return nrc_adam(N, st);
 }

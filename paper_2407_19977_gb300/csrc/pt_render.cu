@@ -307,23 +307,25 @@ struct NrcHook {
 };
 
 // radiance of the paths the cache ended: L += beta * max(cache, 0)
-__global__ void k_nrc_apply(WfParams P, uint32_t nq) {
-    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    const float* rec = P.nrc_q + (size_t)q * 16;
-    const uint32_t id = __float_as_uint(rec[13]);
-    const float* y = P.nrc_out + 4ull * q;
-    float4 L = P.radiance[id];
-    L.x += rec[10] * fmaxf(y[0], 0.0f);
-    L.y += rec[11] * fmaxf(y[1], 0.0f);
-    L.z += rec[12] * fmaxf(y[2], 0.0f);
-    P.radiance[id] = L;
+__global__ void k_nrc_apply(WfParams P) {
+    const uint32_t nq = P.nrc_counters[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && nq) atomicAdd(&P.stats[ST_NRC], (unsigned long long)nq);
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const float* rec = P.nrc_q + (size_t)q * 16;
+        const uint32_t id = __float_as_uint(rec[13]);
+        const float* y = P.nrc_out + 4ull * q;
+        float4 L = P.radiance[id];
+        L.x += rec[10] * fmaxf(y[0], 0.0f);
+        L.y += rec[11] * fmaxf(y[1], 0.0f);
+        L.z += rec[12] * fmaxf(y[2], 0.0f);
+        P.radiance[id] = L;
+    }
 }
 
 // training samples from the path suffixes: target_j = (L_end - L_j) / beta_j per channel
-__global__ void k_nrc_targets(WfParams P, uint32_t n_train) {
+__global__ void k_nrc_targets(WfParams P) {
     const uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= n_train) return;
+    if (slot >= min(P.nrc_counters[1], P.max_train)) return;
     const uint32_t id = P.train_id[slot];
     const float4 Le = P.radiance[id];
     const uint32_t nv = min(P.train_nv[slot], P.rec_per_path);
@@ -361,7 +363,9 @@ __device__ __forceinline__ uint32_t hit_key(const DScene& S, const HitRec& h, ui
     return (code & PT_LIGHT_BIT) ? n_mats + 1 : code;
 }
 
-// persistent closest-hit over the input queue; warps fetch 32 slots at a time
+// Persistent closest-hit over the input queue.  Each lane runs one ray at a time in the
+// step form (one BVH node per iteration); whenever lanes of a warp finish, the warp fetches
+// that many new queue slots with one atomic, so lanes stay busy until the queue drains.
 template <bool COUNT>
 __global__ void __launch_bounds__(128) k_wf_trace(WfParams P, int in_q) {
     __shared__ uint32_t hist[MAX_SORT_KEYS];
@@ -520,6 +524,8 @@ __global__ void __launch_bounds__(128) k_wf_shade(WfParams P, int in_q, int out_
     if (lane == 0 && rr_cnt) atomicAdd(&P.stats[ST_RR], rr_cnt);
 }
 
+// Persistent shadow any-hit over the shadow queue, with the same lane refilling; an
+// unoccluded shadow ray adds its contribution to its path's radiance.
 template <bool COUNT>
 __global__ void __launch_bounds__(128) k_wf_shadow(WfParams P) {
     const uint32_t count = P.counters[C_SH];
@@ -755,30 +761,18 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
             }
             if (P.nrc_on) {
                 // cache inference for the paths that ended at their second diffuse-ish vertex,
-                // then training samples from this wave's training-path suffixes
-                uint32_t cnt[4] = {0, 0, 0, 0};
-                PT_CUDA_TRY(cudaMemcpyAsync(cnt, w.nrc_counters, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-                PT_CUDA_TRY(cudaStreamSynchronize(st));
-                const uint32_t nq = cnt[0], nt = std::min(cnt[1], P.max_train);
-                if (nq) {
-                    pt_status rr = pt_nrc_render_infer(o.nrc, w.nrc_q, nq, w.nrc_out, st);
+                // then training on this wave's training-path suffixes; the counts stay on the
+                // device, so nothing here waits for the GPU
+                pt_status rr = pt_nrc_render_infer_dev(o.nrc, w.nrc_q, w.nrc_counters, n, w.nrc_out, st);
+                if (rr != PT_OK) return rr;
+                PT_LAUNCH(k_nrc_apply, sms * 4, 256, 0, st, P);
+                ++launches;
+                if (P.max_train) {
+                    PT_LAUNCH(k_nrc_targets, (P.max_train + 127) / 128, 128, 0, st, P);
+                    ++launches;
+                    rr = pt_nrc_render_train_dev(o.nrc, w.train_samples, w.nrc_counters + 2, P.sample_cap, st);
                     if (rr != PT_OK) return rr;
-                    PT_LAUNCH(k_nrc_apply, (nq + 255) / 256, 256, 0, st, P, nq);
-                    ++launches;
                 }
-                if (nt) {
-                    PT_LAUNCH(k_nrc_targets, (nt + 127) / 128, 128, 0, st, P, nt);
-                    ++launches;
-                    PT_CUDA_TRY(cudaMemcpyAsync(&cnt[2], w.nrc_counters + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-                    PT_CUDA_TRY(cudaStreamSynchronize(st));
-                    const uint32_t ns = std::min(cnt[2], P.sample_cap);
-                    if (ns) {
-                        pt_status rr = pt_nrc_train(o.nrc, w.train_samples, ns, (void*)st);
-                        if (rr != PT_OK) return rr;
-                    }
-                }
-                s->nrc_queries_host += nq;
-                s->nrc_samples_host += std::min(cnt[2], P.sample_cap);
             }
             e = begin(PT_K_ACCUM);
             PT_LAUNCH(k_wf_accum, (npix + 255) / 256, 256, 0, st, P);

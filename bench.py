@@ -284,8 +284,8 @@ def run_ours(args, world, rank, local):
                         cnt["ext_rays"] * (RAY_BYTES + HIT_BYTES))
     trace_ops_step = cnt["trace_nodes"] * OPS_PER_NODE + cnt["trace_tris"] * OPS_PER_TRI
     # timed region
-    kernel_ms = (N.f32 * 6)()
-    kernel_launches = (N.u32 * 6)()
+    kernel_ms = (N.f32 * len(N.KERNEL_KINDS))()
+    kernel_launches = (N.u32 * len(N.KERNEL_KINDS))()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:

@@ -118,7 +118,7 @@ enum {
 
 /* wavefront kernel kinds, indices of pt_render_opts.kernel_ms */
 enum { PT_K_RAYGEN = 0, PT_K_TRACE = 1, PT_K_SORT = 2, PT_K_SHADE = 3, PT_K_SHADOW = 4, PT_K_ACCUM = 5,
-       PT_K_KINDS = 6 };
+       PT_K_TAIL = 6, PT_K_KINDS = 7 };
 
 enum {
     PT_MODE_AUTO = 0,           /* pick per the autotuned table (pt_autotune) */
@@ -142,6 +142,12 @@ typedef struct {
                                    CUDA-event time of each kernel kind (synchronises the
                                    stream at the end of the call) */
     uint32_t* kernel_launches;  /* optional HOST uint32[PT_K_KINDS]: launches per kind */
+    int32_t tail_paths;         /* wavefront: once the paths left to trace at a bounce number at
+                                   most this many, one launch carries each of them to its end
+                                   (closest hit, shade, shadow ray per thread) instead of one
+                                   launch per stage and bounce; same per-vertex code and random
+                                   numbers, so the image is the same.  -1 off, 0 automatic
+                                   (the paths the tail kernel holds resident on the GPU) */
 } pt_render_opts;
 
 typedef struct {
@@ -163,6 +169,15 @@ typedef struct {
     uint64_t trace_tris;        /* PT_FLAG_COUNT: triangle tests of closest-hit rays */
     uint64_t shadow_nodes;      /* PT_FLAG_COUNT: wide nodes visited by shadow rays */
     uint64_t shadow_tris;       /* PT_FLAG_COUNT: triangle tests of shadow rays */
+    /* the wavefront tail kernel (pt_render_opts.tail_paths): rays it traced (also counted in
+       ext_rays / shadow_rays) and, with PT_FLAG_COUNT, its node visits and triangle tests
+       (not counted in trace_* / shadow_* above, which cover the per-bounce kernels only) */
+    uint64_t tail_ext_rays;
+    uint64_t tail_shadow_rays;
+    uint64_t tail_trace_nodes;
+    uint64_t tail_trace_tris;
+    uint64_t tail_shadow_nodes;
+    uint64_t tail_shadow_tris;
     uint32_t error_flags;       /* sticky device error bits (1 = stack overflow, 2 = timeout) */
     uint32_t reserved;
 } pt_stats;

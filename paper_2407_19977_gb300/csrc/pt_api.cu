@@ -354,6 +354,12 @@ extern "C" pt_status pt_get_stats(pt_scene* s, pt_stats* out) {
     out->trace_tris = st[ST_TRIS];
     out->shadow_nodes = st[ST_SH_NODES];
     out->shadow_tris = st[ST_SH_TRIS];
+    out->tail_ext_rays = st[ST_TAIL_EXT];
+    out->tail_shadow_rays = st[ST_TAIL_SH];
+    out->tail_trace_nodes = st[ST_TAIL_NODES];
+    out->tail_trace_tris = st[ST_TAIL_TRIS];
+    out->tail_shadow_nodes = st[ST_TAIL_SH_NODES];
+    out->tail_shadow_tris = st[ST_TAIL_SH_TRIS];
     out->error_flags = err;
     if (err & 2u) { pt_set_error("device wait ran out of its spin budget"); return PT_ERR_TIMEOUT; }
     if (err & 1u) { pt_set_error("traversal stack or work queue overflow"); return PT_ERR_QUEUE_OVERFLOW; }

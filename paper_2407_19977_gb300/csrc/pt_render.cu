@@ -193,7 +193,9 @@ static pt_status launch_megakernel(const std::vector<DJob>& jobs_in, uint32_t ti
 }
 
 // ------------------------------------------------------------------ wavefront
-enum { C_Q0 = 0, C_Q1 = 1, C_SH = 2, C_HEAD_TRACE = 3, C_HEAD_SHADOW = 4, C_BUCKETS = 16 };
+// counters: queue sizes, fetch heads, C_TAIL = 1 once the tail kernel has taken the wave's
+// remaining paths (the per-bounce kernels then have nothing to do), sort buckets
+enum { C_Q0 = 0, C_Q1 = 1, C_SH = 2, C_HEAD_TRACE = 3, C_HEAD_SHADOW = 4, C_TAIL = 5, C_BUCKETS = 16 };
 constexpr uint32_t MAX_SORT_KEYS = 1024;
 
 struct WfParams {
@@ -242,6 +244,7 @@ __global__ void k_wf_raygen(WfParams P) {
     const uint32_t n = P.npix * P.nsamp;
     if (id == 0) {
         P.counters[C_Q0] = n;
+        P.counters[C_TAIL] = 0;
         atomicAdd(&P.stats[ST_PATHS], (unsigned long long)n);
     }
     if (id >= n) return;
@@ -369,6 +372,7 @@ __device__ __forceinline__ uint32_t hit_key(const DScene& S, const HitRec& h, ui
 template <bool COUNT>
 __global__ void __launch_bounds__(128) k_wf_trace(WfParams P, int in_q) {
     __shared__ uint32_t hist[MAX_SORT_KEYS];
+    if (P.counters[C_TAIL]) return;
     const bool sort = P.n_keys > 0;
     if (sort)
         for (uint32_t k = threadIdx.x; k < P.n_keys; k += blockDim.x) hist[k] = 0;
@@ -411,6 +415,7 @@ __global__ void __launch_bounds__(128) k_wf_trace(WfParams P, int in_q) {
 
 // exclusive scan of the bucket counts into bucket cursors (one block)
 __global__ void k_wf_sort_scan(uint32_t* counters, uint32_t n_keys) {
+    if (counters[C_TAIL]) return;
     __shared__ uint32_t part[MAX_SORT_KEYS];
     const uint32_t t = threadIdx.x;
     const uint32_t v = t < n_keys ? counters[C_BUCKETS + t] : 0u;
@@ -426,6 +431,7 @@ __global__ void k_wf_sort_scan(uint32_t* counters, uint32_t n_keys) {
 }
 
 __global__ void k_wf_sort_scatter(WfParams P, int in_q) {
+    if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[in_q];
     const uint32_t lane = lane_id();
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -444,6 +450,7 @@ __global__ void k_wf_sort_scatter(WfParams P, int in_q) {
 
 template <bool NRC>
 __global__ void __launch_bounds__(128) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
+    if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[in_q];
     const uint32_t lane = lane_id();
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -558,6 +565,90 @@ __global__ void __launch_bounds__(128) k_wf_shadow(WfParams P) {
     }
 }
 
+// Tail of a wave: when few paths are left, a per-bounce kernel lasts about as long as its
+// slowest ray (a chain of dependent node and triangle loads), and the wave pays that once per
+// stage and bounce.  This kernel takes the remaining queue instead and carries each path to
+// its end in one thread: closest hit, shade_vertex_h (the same per-vertex code and random
+// numbers as k_wf_shade), then the shadow ray, whose contribution is added after the vertex's
+// own terms exactly as k_wf_shadow adds it.  It appends nothing, so the later per-bounce
+// launches of the wave find empty queues (and C_TAIL makes the rest of this bounce skip).
+template <bool NRC, bool COUNT>
+__global__ void __launch_bounds__(128) k_wf_tail(WfParams P, int in_q, uint32_t k0, uint32_t limit) {
+    const uint32_t count = P.counters[in_q];
+    if (count == 0 || count > limit) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.counters[C_TAIL] = 1u;
+    unsigned long long n_ext = 0, n_sh = 0, n_rr = 0;
+    TravCount tc = {0, 0}, sc = {0, 0};
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const float4 ro = P.ray_o[in_q][i], rd = P.ray_d[in_q][i];
+        const uint32_t id = __float_as_uint(rd.w);
+        const float4 b4 = P.beta[id];
+        const float4 L4 = P.radiance[id];
+        PathState ps;
+        ps.beta = xyz(b4);
+        ps.prev_pdf = b4.w;
+        ps.L = xyz(L4);
+        const uint32_t lp = P.pb + id % P.npix;
+        VertexRng rng;
+        rng.p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
+        rng.s = P.sb + id / P.npix;
+        rng.k0 = (uint32_t)P.seed;
+        rng.k1 = (uint32_t)(P.seed >> 32);
+        NrcHook hook;
+        if (NRC) {
+            hook.P = &P;
+            hook.id = id;
+            hook.aux = P.aux[id];
+        }
+        float3 o = xyz(ro), d = xyz(rd);
+        for (uint32_t k = k0;; ++k) {
+            HitRec h;
+            if (COUNT) trace_closest_t<true>(P.S, o, d, __int_as_float(0x7f800000), h, tc);
+            else trace_closest(P.S, o, d, __int_as_float(0x7f800000), h);
+            n_ext++;
+            rng.k = k;
+            ShadeOut so;
+            int r;
+            if (NRC) r = shade_vertex_h(P.S, h, o, d, k, P.max_depth, P.flags, rng, ps, so, hook);
+            else r = shade_vertex(P.S, h, o, d, k, P.max_depth, P.flags, rng, ps, so);
+            if (so.rr_end) n_rr++;
+            if (so.has_shadow) {
+                n_sh++;
+                const bool occ = COUNT ? trace_any_t<true>(P.S, so.sh.o, so.sh.d, so.sh.tmax, sc)
+                                       : trace_any(P.S, so.sh.o, so.sh.d, so.sh.tmax);
+                if (!occ) {
+                    ps.L.x += so.sh.contrib.x;
+                    ps.L.y += so.sh.contrib.y;
+                    ps.L.z += so.sh.contrib.z;
+                }
+            }
+            if (r != SHADE_CONTINUE) break;
+            o = so.next_o;
+            d = so.next_d;
+        }
+        P.radiance[id] = make_float4(ps.L.x, ps.L.y, ps.L.z, 0.0f);
+        if (NRC) P.aux[id] = hook.aux;
+    }
+    n_ext = warp_sum_u64(n_ext);
+    n_sh = warp_sum_u64(n_sh);
+    n_rr = warp_sum_u64(n_rr);
+    if (lane_id() == 0) {
+        if (n_ext) { atomicAdd(&P.stats[ST_EXT], n_ext); atomicAdd(&P.stats[ST_TAIL_EXT], n_ext); }
+        if (n_sh) { atomicAdd(&P.stats[ST_SHADOW], n_sh); atomicAdd(&P.stats[ST_TAIL_SH], n_sh); }
+        if (n_rr) atomicAdd(&P.stats[ST_RR], n_rr);
+    }
+    if (COUNT) {
+        const unsigned long long a = warp_sum_u64(tc.nodes), b = warp_sum_u64(tc.tris),
+                                 c = warp_sum_u64(sc.nodes), e = warp_sum_u64(sc.tris);
+        if (lane_id() == 0) {
+            atomicAdd(&P.stats[ST_TAIL_NODES], a);
+            atomicAdd(&P.stats[ST_TAIL_TRIS], b);
+            atomicAdd(&P.stats[ST_TAIL_SH_NODES], c);
+            atomicAdd(&P.stats[ST_TAIL_SH_TRIS], e);
+        }
+    }
+}
+
 __global__ void k_wf_accum(WfParams P) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long nan_cnt = 0;
@@ -645,7 +736,7 @@ static pt_status ensure_nrc_buffers(WaveBuffers& w, uint32_t rec_per_path) {
     return PT_OK;
 }
 
-static int g_trace_blocks_per_sm = 0, g_shade_blocks_per_sm = 0, g_shadow_blocks_per_sm = 0;
+static int g_trace_blocks_per_sm = 0, g_shade_blocks_per_sm = 0, g_shadow_blocks_per_sm = 0, g_tail_blocks_per_sm = 0;
 
 static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
                                   pt_accum* acc, const pt_render_opts& o, cudaStream_t st) {
@@ -669,7 +760,15 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shadow<false>, 128, 0);
         g_shadow_blocks_per_sm = std::max(b, 1);
     }
+    if (g_tail_blocks_per_sm == 0) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_tail<true, false>, 128, 0);
+        g_tail_blocks_per_sm = std::max(b, 1);
+    }
     const int sms = pt_num_sms();
+    // tail: the paths one launch of k_wf_tail holds resident, unless the caller says otherwise
+    const uint32_t tail_grid = (uint32_t)(sms * g_tail_blocks_per_sm);
+    const uint32_t tail_limit = o.tail_paths < 0 ? 0u : o.tail_paths > 0 ? (uint32_t)o.tail_paths : tail_grid * 128u;
     WfParams P;
     std::memset(&P, 0, sizeof(P));
     P.S = s->view();
@@ -737,11 +836,24 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
             for (uint32_t k = 0; k <= max_depth; ++k) {
                 const int in_q = (int)(k & 1u), out_q = (int)((k + 1) & 1u);
                 PT_LAUNCH(k_wf_setup, 1, 256, 0, st, w.counters, out_q, n_keys);
+                ++launches;
+                if (tail_limit) {
+                    e = begin(PT_K_TAIL);
+                    if (P.nrc_on) {
+                        if (count) PT_LAUNCH((k_wf_tail<true, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                        else PT_LAUNCH((k_wf_tail<true, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                    } else {
+                        if (count) PT_LAUNCH((k_wf_tail<false, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                        else PT_LAUNCH((k_wf_tail<false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                    }
+                    end(e);
+                    ++launches;
+                }
                 e = begin(PT_K_TRACE);
                 if (count) PT_LAUNCH(k_wf_trace<true>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
                 else PT_LAUNCH(k_wf_trace<false>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
                 end(e);
-                launches += 2;
+                ++launches;
                 if (n_keys) {
                     e = begin(PT_K_SORT);
                     PT_LAUNCH(k_wf_sort_scan, 1, MAX_SORT_KEYS, 0, st, w.counters, n_keys);

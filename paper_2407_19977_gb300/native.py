@@ -42,7 +42,8 @@ class pt_accum(C.Structure):
 class pt_render_opts(C.Structure):
     _fields_ = [("crop_x0", u32), ("crop_y0", u32), ("flags", u32), ("mode", u32), ("wave_paths", u32),
                 ("sort_by_material", C.c_int32), ("block_size", u32), ("sample_out", vp), ("nrc", vp),
-                ("nrc_train", u32), ("kernel_ms", C.POINTER(f32)), ("kernel_launches", C.POINTER(u32))]
+                ("nrc_train", u32), ("kernel_ms", C.POINTER(f32)), ("kernel_launches", C.POINTER(u32)),
+                ("tail_paths", C.c_int32)]
 
 
 class pt_bvh_opts(C.Structure):
@@ -53,7 +54,9 @@ class pt_stats(C.Structure):
     _fields_ = [("ext_rays", u64), ("shadow_rays", u64), ("paths", u64), ("nan_dropped", u64),
                 ("rr_terminated", u64), ("nrc_queries", u64), ("kernel_launches", u64), ("bvh_nodes", u64),
                 ("bvh_depth", u64), ("n_triangles", u64), ("trace_nodes", u64), ("trace_tris", u64),
-                ("shadow_nodes", u64), ("shadow_tris", u64), ("error_flags", u32), ("reserved", u32)]
+                ("shadow_nodes", u64), ("shadow_tris", u64), ("tail_ext_rays", u64), ("tail_shadow_rays", u64),
+                ("tail_trace_nodes", u64), ("tail_trace_tris", u64), ("tail_shadow_nodes", u64),
+                ("tail_shadow_tris", u64), ("error_flags", u32), ("reserved", u32)]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
@@ -81,7 +84,7 @@ STATUS = ["PT_OK", "PT_ERR_INVALID_ARG", "PT_ERR_OOM", "PT_ERR_CUDA", "PT_ERR_NO
 PT_FLAG_NO_NEE = 1
 PT_FLAG_NO_RR = 2
 PT_FLAG_COUNT = 4
-KERNEL_KINDS = ("raygen", "trace", "sort", "shade", "shadow", "accum")
+KERNEL_KINDS = ("raygen", "trace", "sort", "shade", "shadow", "accum", "tail")
 PT_MODE_AUTO, PT_MODE_WAVEFRONT, PT_MODE_MEGAKERNEL = 0, 1, 2
 
 # symbol -> (restype, argtypes); every symbol declared in include/pt.h

@@ -174,6 +174,29 @@ def test_nrc_render_queries_and_trains():
     assert np.mean(losses[-3:]) < np.mean(losses[:3])
 
 
+def test_nrc_frame_same_with_and_without_tail_kernel():
+    """With the radiance cache on, the tail kernel ends paths at the same vertices, issues the
+    same cache queries (in another order) and records the same training vertices: a frame
+    rendered from two identical caches is bit-identical with and without it.  256x192 holds
+    more paths than the training slots, so both kinds of path occur."""
+    from paper_2407_19977_gb300 import api, scenes
+    sc = scenes.cornell_box(width=256, height=192, spp=1, max_depth=8)
+    g = api.Scene(sc)
+    lo = sc.vertices.min(0) - 0.01
+    hi = sc.vertices.max(0) + 0.01
+    for train in (False, True):
+        imgs, queries = [], []
+        for tail in (-1, 1 << 30):
+            net = api.Nrc(seed=3, box=(tuple(lo), tuple(hi)))
+            b = g.stats()["nrc_queries"]
+            acc = g.render(1, seed=4, mode=1, nrc=net, nrc_train=train, tail_paths=tail)
+            torch.cuda.synchronize()
+            queries.append(g.stats()["nrc_queries"] - b)
+            imgs.append(acc.sum.clone())
+        assert queries[0] == queries[1] > 0, (train, queries)
+        assert torch.equal(imgs[0], imgs[1]), train
+
+
 def test_nrc_gain_on_enclosed_scene():
     """What the trained cache gains: in a closed box most radiance arrives after several
     diffuse bounces; ending paths at their second diffuse vertex with the cache lowers the

@@ -329,7 +329,7 @@ def test_env_sampling_parity(api):
 
 # ------------------------------------------------------------------ images
 
-def _render_pair(gsc, osc, sc, spp, crop=None, mode=0, flags=0, seed=0, max_depth=None, s0=0):
+def _render_pair(gsc, osc, sc, spp, crop=None, mode=0, flags=0, seed=0, max_depth=None, s0=0, tail=0):
     from paper_2407_19977_gb300 import api as A
     cam = sc.camera
     x0, y0, cw, ch = crop or (0, 0, cam.width, cam.height)
@@ -337,7 +337,7 @@ def _render_pair(gsc, osc, sc, spp, crop=None, mode=0, flags=0, seed=0, max_dept
     acc = A.Accum(cw, ch)
     acc.c.spp_done = s0
     gsc.render(spp, max_depth=max_depth, seed=seed, accum=acc, crop=(x0, y0, cw, ch), mode=mode, flags=flags,
-               sample_out=samples)
+               sample_out=samples, tail_paths=tail)
     torch.cuda.synchronize()
     g_img = ((acc.sum + acc.comp * 0) / spp).cpu().numpy()
     o_sum, o_smp, st = osc.render(spp=spp, max_depth=max_depth, seed=seed, s0=s0, crop=(x0, y0, cw, ch),
@@ -345,10 +345,12 @@ def _render_pair(gsc, osc, sc, spp, crop=None, mode=0, flags=0, seed=0, max_dept
     return g_img, o_sum / spp, samples.cpu().numpy(), o_smp, st
 
 
-@pytest.mark.parametrize("mode", [1, 2])
-def test_image_parity_cornell(api, mode):
+@pytest.mark.parametrize("mode,tail", [(1, -1), (1, 0), (1, 1 << 30), (2, 0)])
+def test_image_parity_cornell(api, mode, tail):
+    """mode 1 = wavefront (tail -1: per-bounce kernels only; 0: tail kernel once the queue is
+    small; 1 << 30: the tail kernel takes every path from the first bounce), 2 = megakernel."""
     sc, gsc, osc = cornell()
-    g, o, gs, os_, st = _render_pair(gsc, osc, sc, sc.spp, mode=mode, max_depth=sc.max_depth)
+    g, o, gs, os_, st = _render_pair(gsc, osc, sc, sc.spp, mode=mode, max_depth=sc.max_depth, tail=tail)
     diverged = (np.abs(gs - os_) > 1e-3 * (np.abs(os_) + 1e-2)).any(-1).mean()
     assert diverged <= 1e-3, diverged
     _image_check(g, o, f"cornell mode {mode}")
@@ -359,7 +361,7 @@ def test_image_parity_cornell(api, mode):
 @pytest.mark.parametrize("crop", [(896, 504, 128, 72), (200, 300, 128, 72), (1792, 1008, 128, 72)])
 def test_image_parity_pushbutton_crops(api, crop):
     sc, gsc, osc = pushbutton()
-    g, o, gs, os_, st = _render_pair(gsc, osc, sc, 4, crop=crop, mode=1, max_depth=sc.max_depth, seed=3)
+    g, o, gs, os_, st = _render_pair(gsc, osc, sc, 4, crop=crop, mode=1, max_depth=sc.max_depth, seed=3, tail=-1)
     _image_check(g, o, f"pushbutton crop {crop}")
     assert _divergent(gs, os_).mean() <= 1e-3
 
@@ -369,7 +371,7 @@ def test_image_parity_heavy_crops(api, crop):
     """Glass spheres traced 12 bounces deep: reflect/refract choices next to total internal
     reflection can flip between FP32 and FP64, so divergent paths are counted, not hidden."""
     sc, gsc, osc = heavy()
-    g, o, gs, os_, st = _render_pair(gsc, osc, sc, 2, crop=crop, mode=1, max_depth=sc.max_depth, seed=5)
+    g, o, gs, os_, st = _render_pair(gsc, osc, sc, 2, crop=crop, mode=1, max_depth=sc.max_depth, seed=5, tail=-1)
     _samples_check(gs, os_, f"heavy crop {crop}")
     # the whole image, flips included, stays close
     _image_check(g, o, f"heavy crop {crop} incl. divergent paths", rel=0.05)
@@ -423,6 +425,57 @@ def test_modes_agree_per_sample(api):
         outs.append(s.cpu().numpy())
     close = np.abs(outs[0] - outs[1]) <= 1e-4 * (np.abs(outs[1]) + 1e-3)
     assert close.all(-1).mean() >= 0.9995
+
+
+def _samples(gsc, spp, crop, seed, **kw):
+    from paper_2407_19977_gb300 import api as A
+    x0, y0, cw, ch = crop
+    s = torch.zeros((ch, cw, spp, 3), dtype=torch.float32, device="cuda")
+    acc = A.Accum(cw, ch)
+    gsc.render(spp, accum=acc, crop=crop, mode=1, sample_out=s, seed=seed, **kw)
+    torch.cuda.synchronize()
+    return s, acc
+
+
+@pytest.mark.parametrize("which", ["pushbutton", "heavy", "cornell"])
+def test_tail_kernel_equals_per_bounce_kernels(api, which):
+    """The tail kernel runs the same per-vertex code with the same random numbers as the
+    per-bounce kernels, so every sample is bit-identical whether the tail takes over at the
+    first bounce, later (automatic limit, or a limit the queue crosses mid-wave) or never."""
+    sc, gsc, osc = {"pushbutton": pushbutton, "heavy": heavy, "cornell": cornell}[which]()
+    crop = {"pushbutton": (640, 360, 160, 90), "heavy": (900, 480, 128, 72), "cornell": (0, 0, 64, 64)}[which]
+    n = crop[2] * crop[3] * 3
+    ref, acc_ref = _samples(gsc, 3, crop, 11, tail_paths=-1)
+    before = gsc.stats()
+    for tail in (1 << 30, 0, n // 3, n // 20):
+        s, acc = _samples(gsc, 3, crop, 11, tail_paths=tail)
+        assert torch.equal(s, ref), (which, tail, float((s - ref).abs().max()))
+        assert torch.equal(acc.sum, acc_ref.sum) and torch.equal(acc.comp, acc_ref.comp)
+    after = gsc.stats()
+    assert after["tail_ext_rays"] > before["tail_ext_rays"]
+    assert after["error_flags"] == 0
+
+
+def test_tail_kernel_ray_counts(api):
+    """Rays traced with and without the tail kernel are the same rays: equal counts, and the
+    counting build attributes the tail's node visits to the tail slots."""
+    from paper_2407_19977_gb300 import native as N
+    sc, gsc, osc = pushbutton()
+    crop = (500, 300, 256, 144)
+    res = {}
+    for tail in (-1, 4096):
+        b = gsc.stats()
+        _samples(gsc, 2, crop, 4, tail_paths=tail, flags=N.PT_FLAG_COUNT)
+        a = gsc.stats()
+        res[tail] = {k: a[k] - b[k] for k in a if k not in ("bvh_nodes", "bvh_depth", "n_triangles", "error_flags")}
+    off, on = res[-1], res[4096]
+    assert off["ext_rays"] == on["ext_rays"] and off["shadow_rays"] == on["shadow_rays"]
+    assert off["rr_terminated"] == on["rr_terminated"] and off["paths"] == on["paths"]
+    assert off["tail_ext_rays"] == 0 and on["tail_ext_rays"] > 0 and on["tail_shadow_rays"] > 0
+    assert off["trace_nodes"] == on["trace_nodes"] + on["tail_trace_nodes"]
+    assert off["trace_tris"] == on["trace_tris"] + on["tail_trace_tris"]
+    assert off["shadow_nodes"] == on["shadow_nodes"] + on["tail_shadow_nodes"]
+    assert off["shadow_tris"] == on["shadow_tris"] + on["tail_shadow_tris"]
 
 
 def test_sort_by_material_does_not_change_results(api):

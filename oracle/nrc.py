@@ -7,7 +7,9 @@ The paper names neural radiance caching as future work to cut the samples per pi
                direction (3), normal (3), roughness (1), 1, zero padding ]   (64 wide)
   MLP    h_1 = relu(W_0 x), ..., h_4 = relu(W_3 h_3), y = W_4 h_4          (no biases)
   loss   relative L2: mean over samples and channels of (y - t)^2 / (sg(y)^2 + 0.01)
-  update Adam (beta1 0.9, beta2 0.99, eps 1e-15) on the MLP weights and the grid table
+  update Adam (beta1 0.9, beta2 0.99, eps 1e-15) on the MLP weights; lazy Adam on the grid
+         table: an entry whose gradient is exactly zero in a step keeps its value and its
+         moments (the sparse/lazy Adam variant; a hash table receives sparse gradients)
 
 Hash grid (multiresolution, as in Mueller et al. 2022): level l has resolution
 N_l = floor(N_min * b^l); the 8 corners of the cell around p * N_l are looked up densely
@@ -130,13 +132,20 @@ def grid_backward(lookups, dfeat, table_shape):
     return dtable
 
 
-def adam(param, grad, m, v, t, lr, beta1=0.9, beta2=0.99, eps=1e-15):
-    """One Adam step (Kingma & Ba); t counts from 1.  Returns new (param, m, v)."""
-    m = beta1 * m + (1.0 - beta1) * grad
-    v = beta2 * v + (1.0 - beta2) * grad * grad
-    mhat = m / (1.0 - beta1 ** t)
-    vhat = v / (1.0 - beta2 ** t)
-    return param - lr * mhat / (np.sqrt(vhat) + eps), m, v
+def adam(param, grad, m, v, t, lr, beta1=0.9, beta2=0.99, eps=1e-15, lazy=False):
+    """One Adam step (Kingma & Ba); t counts from 1 and is shared by every entry.  Returns new
+    (param, m, v).  lazy=True: entries with grad == 0 are left as they are (value and moments)."""
+    m_new = beta1 * m + (1.0 - beta1) * grad
+    v_new = beta2 * v + (1.0 - beta2) * grad * grad
+    mhat = m_new / (1.0 - beta1 ** t)
+    vhat = v_new / (1.0 - beta2 ** t)
+    p_new = param - lr * mhat / (np.sqrt(vhat) + eps)
+    if lazy:
+        keep = grad == 0.0
+        p_new = np.where(keep, param, p_new)
+        m_new = np.where(keep, m, m_new)
+        v_new = np.where(keep, v, v_new)
+    return p_new, m_new, v_new
 
 
 def effective_roughness(metalness, spec_rough, transmission):

@@ -142,6 +142,36 @@ def test_adam_matches_torch():
     assert np.allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
 
 
+def test_lazy_adam_matches_torch_sparse_adam():
+    """The grid's lazy Adam against torch.optim.SparseAdam, which updates only the entries a
+    sparse gradient names (torch adds eps to sqrt(v) before the bias correction; with eps
+    1e-15 that is far below the tolerance)."""
+    torch = pytest.importorskip("torch")
+    n = 200
+    p = RNG.normal(size=n)
+    tp = torch.nn.Parameter(torch.tensor(p.copy()))
+    opt = torch.optim.SparseAdam([tp], lr=1e-2, betas=(0.9, 0.99), eps=1e-15)
+    m = np.zeros(n)
+    v = np.zeros(n)
+    moved_by_dense = False
+    for t in range(1, 7):
+        idx = np.sort(RNG.choice(n, 40, replace=False))
+        g = np.zeros(n)
+        g[idx] = RNG.normal(size=40)
+        p_dense, _, _ = nrc.adam(p, g, m, v, t, 1e-2)
+        p_new, m, v = nrc.adam(p, g, m, v, t, 1e-2, lazy=True)
+        untouched = g == 0
+        assert np.array_equal(p_new[untouched], p[untouched])
+        moved_by_dense |= bool(np.any(p_dense[untouched] != p[untouched]))
+        p = p_new
+        opt.zero_grad()
+        tp.grad = torch.sparse_coo_tensor(torch.tensor(idx)[None], torch.tensor(g[idx]), (n,))
+        opt.step()
+        assert np.allclose(p, tp.detach().numpy(), rtol=1e-9, atol=1e-12)
+    # after the first step the dense rule moves untouched entries by momentum; lazy does not
+    assert moved_by_dense
+
+
 def test_effective_roughness():
     assert nrc.effective_roughness(0.0, 0.3, 0.0) == 1.0           # diffuse base
     assert nrc.effective_roughness(1.0, 0.2, 0.0) == pytest.approx(0.2)

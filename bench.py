@@ -38,6 +38,7 @@ WORKLOADS = {
     "heavy": "16 displaced level-7 icospheres, 5,242,882 triangles, 1920x1080, 1 spp/step, max depth 12, "
              "analytic sky 512x256",
     "cornell512": "Cornell-style box, 36 triangles, one quad light, 512x512, 1 spp/step, max depth 8",
+    "cornell1080": "Cornell-style box, 36 triangles, one quad light, 1920x1080, 1 spp/step, max depth 8",
 }
 NODE_BYTES = 80      # compressed 8-wide BVH node
 TRI_BYTES = 48       # triangle record
@@ -171,6 +172,8 @@ def _make_workload(name):
         return scenes.heavy_scene(level=7)
     if name == "cornell512":
         return scenes.cornell_box(width=512, height=512, spp=1, max_depth=8)
+    if name == "cornell1080":
+        return scenes.cornell_box(width=1920, height=1080, spp=1, max_depth=8)
     raise ValueError(name)
 
 

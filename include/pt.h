@@ -331,7 +331,8 @@ typedef struct {
     float per_level_scale;      /* resolution growth per level (0 = from 2048 finest) */
     uint32_t n_hidden;          /* hidden layers (4) */
     float learning_rate;        /* Adam step size (1e-2 grid and MLP) */
-    uint32_t batch;             /* training samples per step (16384) */
+    uint32_t batch;             /* training samples per Adam step (16384); a rendered frame
+                                   with nrc_train takes one step per batch of its samples */
     uint64_t seed;              /* weight initialisation seed */
     float scene_min[3];         /* position normalisation box */
     float scene_max[3];
@@ -356,7 +357,9 @@ pt_status pt_nrc_gradients(pt_nrc* nrc, const float* samples, uint32_t n, float*
  * through the pointer call pt_nrc_commit to refresh the FP16 copies the kernels read. */
 pt_status pt_nrc_params(pt_nrc* nrc, int which, float** ptr, uint64_t* count);
 pt_status pt_nrc_commit(pt_nrc* nrc, void* cuda_stream);
-/* Last training loss (mean relative L2 over the most recent step; synchronises). */
+/* Training loss of the most recent training call (pt_nrc_train, pt_nrc_gradients or a
+ * rendered frame with nrc_train): mean relative L2 over all its samples, evaluated before
+ * each batch's update; synchronises. */
 pt_status pt_nrc_last_loss(pt_nrc* nrc, float* loss);
 void pt_nrc_destroy(pt_nrc* nrc);
 

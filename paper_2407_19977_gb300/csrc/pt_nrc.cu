@@ -47,11 +47,17 @@ __device__ __forceinline__ float2 unpack_h2(uint32_t v) {
     return __half22float2(h);
 }
 
-// row count of a launch: the host value, or the device counter (clamped to the capacity)
+// row count of a launch: the host value, or the rows of a device counter past `off`
+// (clamped to the capacity n) -- one batch of a list whose length only the device knows
 struct RowCount {
     uint32_t n;              // host count, or capacity when `dev` is set
     const uint32_t* dev;     // optional device counter
-    __device__ __forceinline__ uint32_t get() const { return dev ? min(*dev, n) : n; }
+    uint32_t off;            // first row of this batch in the counted list
+    __device__ __forceinline__ uint32_t get() const {
+        if (!dev) return n;
+        const uint32_t c = *dev;
+        return c > off ? min(c - off, n) : 0u;
+    }
 };
 
 struct GridDesc {
@@ -118,7 +124,8 @@ __global__ void k_encode(GridDesc G, const float* __restrict__ queries, RowCount
   }
 }
 
-// grid gradient: recompute the corners and scatter dL/dfeature (FP32 atomics)
+// grid gradient: recompute the corners and scatter dL/dfeature (FP32 atomics, both features
+// of an entry in one 8-byte vector atomic)
 __global__ void k_grid_backward(GridDesc G, const float* __restrict__ samples, RowCount rc, const float* __restrict__ dX) {
   const uint32_t n = rc.get();
   const float scale = n ? 1.0f / (3.0f * (float)n) : 0.0f;
@@ -137,8 +144,7 @@ __global__ void k_grid_backward(GridDesc G, const float* __restrict__ samples, R
         const uint32_t ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
         const float w = (ox ? rx : 1.0f - rx) * (oy ? ry : 1.0f - ry) * (oz ? rz : 1.0f - rz);
         const uint32_t idx = corner_index(cx + ox, cy + oy, cz + oz, res, G.T);
-        atomicAdd(gr + 2 * idx, w * g0);
-        atomicAdd(gr + 2 * idx + 1, w * g1);
+        atomicAdd(reinterpret_cast<float2*>(gr + 2 * idx), make_float2(w * g0, w * g1));
     }
   }
 }
@@ -238,11 +244,12 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const __half* __restrict__ 
 }
 
 // relative L2 loss: dL/dy * (3n) (the 1/(3n) of the mean is applied to the gradients later
-// so that FP16 keeps them in its normal range), plus the loss sum
+// so that FP16 keeps them in its normal range); adds the loss sum and the row count to
+// loss_sum[0..1], which the caller zeroes once per training call (all its batches)
 __global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ samples, RowCount rc, __half* __restrict__ dY,
                        float* __restrict__ loss_sum) {
   const uint32_t n = rc.get();
-  if (blockIdx.x == 0 && threadIdx.x == 0) loss_sum[1] = (float)n;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(loss_sum + 1, (float)n);
   for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const uint32_t q = base + threadIdx.x;
     float l = 0.0f;
@@ -345,65 +352,106 @@ __global__ void __launch_bounds__(128) k_mlp_backward(const __half* __restrict__
     }
 }
 
-// weight gradient of one layer over a chunk of rows: dW[o][i] += sum_r G[r][o] * A[r][i]
-// (G = dZ of the layer's output, A = the layer's input); a warp owns 16 outputs x 64 inputs
-constexpr int DW_CHUNK = 512;
-__global__ void __launch_bounds__(128) k_weight_grad(const __half* __restrict__ G, uint32_t g_stride, uint32_t n_out,
-                                                     const __half* __restrict__ A, RowCount rc, float* __restrict__ part) {
+// ldmatrix with transpose: four 8x8 FP16 tiles of shared memory, lane i naming row i%8 of
+// tile i/8; each lane receives, per tile, two consecutive rows of one column
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const __half* p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// Weight gradients of all layers in one launch: dW_l[o][i] = sum_r G_l[r][o] * A_l[r][i] with
+// G_l the layer's output gradient (dZ_l, or dY for the output layer) and A_l its input.
+// blockIdx.y = layer, blockIdx.x = a chunk of DW_ROWS rows (split-K; the partial 64 x 64 sums
+// go to `part` and k_reduce_grad adds them in a fixed order, so the result is deterministic).
+// Row tiles of G and A are staged in shared memory with 16-byte loads; ldmatrix.trans turns
+// them into the transposed mma operands (A operand = G^T, B operand = A_l).  Warp w owns
+// outputs 16w..16w+15 and all 64 inputs.
+constexpr int DW_ROWS = 256;
+constexpr int DW_KT = 64;
+struct DwArgs {
+    const __half* G[N_HIDDEN + 1];
+    const __half* A[N_HIDDEN + 1];
+    uint32_t g_stride[N_HIDDEN + 1];
+    uint32_t n_out[N_HIDDEN + 1];
+};
+
+__global__ void __launch_bounds__(128) k_weight_grad(const __grid_constant__ DwArgs D, RowCount rc, float* __restrict__ part) {
+    __shared__ __align__(16) __half sG[DW_KT * SROW];
+    __shared__ __align__(16) __half sA[DW_KT * SROW];
     const uint32_t n = rc.get();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
+    const int layer = blockIdx.y;
+    const __half* __restrict__ G = D.G[layer];
+    const __half* __restrict__ A = D.A[layer];
+    const uint32_t gs = D.g_stride[layer], n_out = D.n_out[layer];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
     const int m0 = 16 * warp;
+    const bool active = m0 < (int)n_out;
     float acc[8][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-    if (m0 < (int)n_out) {
-        const uint32_t rbeg = blockIdx.x * DW_CHUNK, rend = min(rbeg + DW_CHUNK, n);
-        for (uint32_t k0 = rbeg; k0 < rend; k0 += 16) {
-            // A operand: rows m = outputs, columns k = sample rows  ->  G^T
-            uint32_t a[4];
-            auto gval = [&](uint32_t r, int o) -> __half {
-                return (r < rend && o < (int)n_out) ? G[(size_t)g_stride * r + o] : __float2half_rn(0.0f);
-            };
-            a[0] = pack_hh(gval(k0 + 2 * t, m0 + g), gval(k0 + 2 * t + 1, m0 + g));
-            a[1] = pack_hh(gval(k0 + 2 * t, m0 + g + 8), gval(k0 + 2 * t + 1, m0 + g + 8));
-            a[2] = pack_hh(gval(k0 + 2 * t + 8, m0 + g), gval(k0 + 2 * t + 9, m0 + g));
-            a[3] = pack_hh(gval(k0 + 2 * t + 8, m0 + g + 8), gval(k0 + 2 * t + 9, m0 + g + 8));
+    const uint32_t rbeg = blockIdx.x * DW_ROWS, rend = min(rbeg + DW_ROWS, n);
+    for (uint32_t s0 = rbeg; s0 < rend; s0 += DW_KT) {
+        for (int c = threadIdx.x; c < DW_KT * 8; c += blockDim.x) {
+            const int r = c >> 3, q = c & 7;   // staged row, 16-byte chunk of it
+            const uint32_t row = s0 + r;
+            uint4 va = make_uint4(0u, 0u, 0u, 0u), vg = make_uint4(0u, 0u, 0u, 0u);
+            if (row < rend) {
+                va = *reinterpret_cast<const uint4*>(A + (size_t)W * row + 8 * q);
+                if (8 * q < (int)n_out) vg = *reinterpret_cast<const uint4*>(G + (size_t)gs * row + 8 * q);
+            }
+            *reinterpret_cast<uint4*>(sA + r * SROW + 8 * q) = va;
+            *reinterpret_cast<uint4*>(sG + r * SROW + 8 * q) = vg;
+        }
+        __syncthreads();
+        if (active) {
+            const int j4 = lane >> 3, r8 = lane & 7;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                auto aval = [&](uint32_t r) -> __half {
-                    return r < rend ? A[(size_t)W * r + 8 * j + g] : __float2half_rn(0.0f);
-                };
-                const uint32_t b0 = pack_hh(aval(k0 + 2 * t), aval(k0 + 2 * t + 1));
-                const uint32_t b1 = pack_hh(aval(k0 + 2 * t + 8), aval(k0 + 2 * t + 9));
-                mma16816(acc[j], a, b0, b1);
+            for (int kk = 0; kk < DW_KT; kk += 16) {
+                uint32_t a[4];
+                // tiles (rows kk, cols m0), (kk, m0+8), (kk+8, m0), (kk+8, m0+8) of G
+                ldsm_x4_trans(a, sG + (kk + r8 + ((j4 >> 1) << 3)) * SROW + m0 + ((j4 & 1) << 3));
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) {
+                    uint32_t b[4];
+                    // tiles (kk, 16pp), (kk+8, 16pp), (kk, 16pp+8), (kk+8, 16pp+8) of A_l
+                    ldsm_x4_trans(b, sA + (kk + r8 + ((j4 & 1) << 3)) * SROW + 16 * pp + ((j4 >> 1) << 3));
+                    mma16816(acc[2 * pp], a, b[0], b[1]);
+                    mma16816(acc[2 * pp + 1], a, b[2], b[3]);
+                }
             }
         }
+        __syncthreads();
     }
-    float* out = part + (size_t)blockIdx.x * W * W;
+    if (!active) return;
+    float* out = part + ((size_t)layer * gridDim.x + blockIdx.x) * W * W;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int c = 8 * j + 2 * t;
-        out[(m0 + g) * W + c] = acc[j][0];
-        out[(m0 + g) * W + c + 1] = acc[j][1];
-        out[(m0 + g + 8) * W + c] = acc[j][2];
-        out[(m0 + g + 8) * W + c + 1] = acc[j][3];
+        *reinterpret_cast<float2*>(out + (m0 + g) * W + c) = make_float2(acc[j][0], acc[j][1]);
+        *reinterpret_cast<float2*>(out + (m0 + g + 8) * W + c) = make_float2(acc[j][2], acc[j][3]);
     }
 }
 
-__global__ void k_reduce_grad(const float* __restrict__ part, uint32_t nparts, uint32_t n_out, float* __restrict__ dst,
-                              RowCount rc) {
+// dW = (1 / 3n) * sum over the row chunks, every layer, in chunk order
+__global__ void k_reduce_grad(const float* __restrict__ part, uint32_t nparts, float* __restrict__ dw, RowCount rc) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_out * W) return;
+    if (i >= (uint32_t)N_WEIGHTS) return;
+    const uint32_t layer = i / (W * W), e = i % (W * W);
     const uint32_t n = rc.get();
     const float scale = n ? 1.0f / (3.0f * (float)n) : 0.0f;
+    const float* src = part + (size_t)layer * nparts * W * W + e;
     float s = 0.0f;
-    for (uint32_t p = 0; p < nparts; ++p) s += part[(size_t)p * W * W + i];
-    dst[i] = s * scale;
+    for (uint32_t p = 0; p < nparts; ++p) s += src[(size_t)p * W * W];
+    dw[i] = s * scale;
 }
 
 // Adam (Kingma & Ba): master FP32 parameters, FP16 copy for the kernels, gradient zeroed
 __global__ void k_adam(float* __restrict__ p, float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
-                       __half* __restrict__ copy, uint64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+                       __half* __restrict__ copy, uint64_t n, float lr, float b1, float b2, float eps, float c1, float c2,
+                       RowCount rc) {
+    if (rc.get() == 0) return;   // an empty batch is no step
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const float gr = grad[i];
         const float mi = b1 * m[i] + (1.0f - b1) * gr;
@@ -415,6 +463,33 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ grad, float* _
         p[i] = np;
         copy[i] = __float2half_rn(np);
         grad[i] = 0.0f;
+    }
+}
+
+// lazy Adam for the grid table: an entry whose gradient is exactly zero keeps its value and
+// moments; the scan reads the gradient four entries at a time and skips zero groups
+__global__ void k_adam_lazy(float* __restrict__ p, float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
+                            __half* __restrict__ copy, uint64_t n4, float lr, float b1, float b2, float eps, float c1,
+                            float c2, RowCount rc) {
+    if (rc.get() == 0) return;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float4 g4 = reinterpret_cast<const float4*>(grad)[i];
+        if (g4.x == 0.0f && g4.y == 0.0f && g4.z == 0.0f && g4.w == 0.0f) continue;
+        const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float gr = gv[c];
+            if (gr == 0.0f) continue;
+            const uint64_t e = 4 * i + c;
+            const float mi = b1 * m[e] + (1.0f - b1) * gr;
+            const float vi = b2 * v[e] + (1.0f - b2) * gr * gr;
+            m[e] = mi;
+            v[e] = vi;
+            const float np = p[e] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+            p[e] = np;
+            copy[e] = __float2half_rn(np);
+        }
+        reinterpret_cast<float4*>(grad)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
 }
 
@@ -487,7 +562,7 @@ static pt_status ensure_train(pt_nrc* N, uint32_t n) {
     PT_CUDA_TRY(cudaMalloc(&N->dZ, c * W * N_HIDDEN * sizeof(__half)));
     PT_CUDA_TRY(cudaMalloc(&N->Y, c * 4 * sizeof(float)));
     PT_CUDA_TRY(cudaMalloc(&N->dX, c * N->grid_cols * sizeof(float)));
-    PT_CUDA_TRY(cudaMalloc(&N->part, ((c + DW_CHUNK - 1) / DW_CHUNK) * W * W * sizeof(float)));
+    PT_CUDA_TRY(cudaMalloc(&N->part, (N_HIDDEN + 1) * ((c + DW_ROWS - 1) / DW_ROWS) * W * W * sizeof(float)));
     N->cap = n;
     return PT_OK;
 }
@@ -600,35 +675,35 @@ static pt_status nrc_gradients(pt_nrc* N, const float* samples, RowCount rc, cud
     const RowCount rb = rc;
     r = nrc_forward(N, samples, rb, N->X, N->Y, N->acts, st);
     if (r != PT_OK) return r;
-    PT_CUDA_TRY(cudaMemsetAsync(N->d_loss, 0, sizeof(float), st));
     const uint32_t gl = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((rb.n + 255) / 256, 8ull * pt_num_sms()));
     PT_LAUNCH(k_loss, gl, 256, 0, st, N->Y, samples, rb, N->dY, N->d_loss);
     PT_LAUNCH(k_mlp_backward, mlp_grid(rb.n), 128, 0, st, N->dY, rb, N->d_wh, N->acts, N->dZ, N->dX, N->grid_cols);
-    const uint32_t nparts = (rb.n + DW_CHUNK - 1) / DW_CHUNK;
+    const uint32_t nparts = (rb.n + DW_ROWS - 1) / DW_ROWS;
     // layer l's weight gradient pairs dZ_l (its output gradient) with its input
+    DwArgs D;
     for (int l = 0; l <= N_HIDDEN; ++l) {
-        const __half* Gm = l < N_HIDDEN ? N->dZ + (size_t)l * rb.n * W : N->dY;
-        const uint32_t gs = l < N_HIDDEN ? W : OUT_PAD;
-        const uint32_t nout = l < N_HIDDEN ? W : OUT_PAD;
-        const __half* Ain = l == 0 ? N->X : N->acts + (size_t)(l - 1) * rb.n * W;
-        PT_LAUNCH(k_weight_grad, nparts, 128, 0, st, Gm, gs, nout, Ain, rb, N->part);
-        PT_LAUNCH(k_reduce_grad, (nout * W + 255) / 256, 256, 0, st, N->part, nparts, nout, N->d_wg + (size_t)l * W * W, rb);
+        D.G[l] = l < N_HIDDEN ? N->dZ + (size_t)l * rb.n * W : N->dY;
+        D.g_stride[l] = l < N_HIDDEN ? W : OUT_PAD;
+        D.n_out[l] = l < N_HIDDEN ? W : OUT_PAD;
+        D.A[l] = l == 0 ? N->X : N->acts + (size_t)(l - 1) * rb.n * W;
     }
+    PT_LAUNCH(k_weight_grad, dim3(nparts, N_HIDDEN + 1), 128, 0, st, D, rb, N->part);
+    PT_LAUNCH(k_reduce_grad, (N_WEIGHTS + 255) / 256, 256, 0, st, N->part, nparts, N->d_wg, rb);
     PT_LAUNCH(k_grid_backward, encode_grid(rb.n, N->L), 256, 0, st, grid_desc(N), samples, rb, N->dX);
-    N->launches += 4 + 2 * (N_HIDDEN + 1);
+    N->launches += 6;
     PT_CUDA_TRY(cudaGetLastError());
     return PT_OK;
 }
 
-static pt_status nrc_adam(pt_nrc* N, cudaStream_t st) {
+static pt_status nrc_adam(pt_nrc* N, RowCount rc, cudaStream_t st) {
     N->step++;
     const float b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
     const float c1 = 1.0f - std::pow(b1, (float)N->step), c2 = 1.0f - std::pow(b2, (float)N->step);
     const float lr = N->o.learning_rate;
     PT_LAUNCH(k_adam, 2 * pt_num_sms(), 256, 0, st, N->d_w, N->d_wg, N->d_wm, N->d_wv, N->d_wh, (uint64_t)N_WEIGHTS, lr,
-              b1, b2, eps, c1, c2);
-    PT_LAUNCH(k_adam, 8 * pt_num_sms(), 256, 0, st, N->d_grid, N->d_gg, N->d_gm, N->d_gv, N->d_gh, N->n_grid, lr, b1,
-              b2, eps, c1, c2);
+              b1, b2, eps, c1, c2, rc);
+    PT_LAUNCH(k_adam_lazy, 8 * pt_num_sms(), 256, 0, st, N->d_grid, N->d_gg, N->d_gm, N->d_gv, N->d_gh, N->n_grid / 4,
+              lr, b1, b2, eps, c1, c2, rc);
     N->launches += 2;
     PT_CUDA_TRY(cudaGetLastError());
     return PT_OK;
@@ -637,11 +712,12 @@ static pt_status nrc_adam(pt_nrc* N, cudaStream_t st) {
 extern "C" pt_status pt_nrc_train(pt_nrc* N, const float* samples, uint32_t n, void* cuda_stream) {
     PT_CHECK_ARG(N && samples, "NULL argument");
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    PT_CUDA_TRY(cudaMemsetAsync(N->d_loss, 0, 2 * sizeof(float), st));
     for (uint32_t b = 0; b < n; b += N->o.batch) {
         const uint32_t m = std::min(N->o.batch, n - b);
-        pt_status r = nrc_gradients(N, samples + (size_t)QSTRIDE * b, RowCount{m, nullptr}, st);
+        pt_status r = nrc_gradients(N, samples + (size_t)QSTRIDE * b, RowCount{m, nullptr, 0}, st);
         if (r != PT_OK) return r;
-        r = nrc_adam(N, st);
+        r = nrc_adam(N, RowCount{m, nullptr, 0}, st);
         if (r != PT_OK) return r;
     }
     return PT_OK;
@@ -651,9 +727,10 @@ extern "C" pt_status pt_nrc_gradients(pt_nrc* N, const float* samples, uint32_t 
                                       void* cuda_stream) {
     PT_CHECK_ARG(N && samples, "NULL argument");
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    PT_CUDA_TRY(cudaMemsetAsync(N->d_loss, 0, 2 * sizeof(float), st));
     PT_CUDA_TRY(cudaMemsetAsync(N->d_wg, 0, N_WEIGHTS * sizeof(float), st));
     PT_CUDA_TRY(cudaMemsetAsync(N->d_gg, 0, N->n_grid * sizeof(float), st));
-    pt_status r = nrc_gradients(N, samples, RowCount{n, nullptr}, st);
+    pt_status r = nrc_gradients(N, samples, RowCount{n, nullptr, 0}, st);
     if (r != PT_OK) return r;
     if (dw_out) PT_CUDA_TRY(cudaMemcpyAsync(dw_out, N->d_wg, N_WEIGHTS * sizeof(float), cudaMemcpyDeviceToDevice, st));
     if (dgrid_out) PT_CUDA_TRY(cudaMemcpyAsync(dgrid_out, N->d_gg, N->n_grid * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -673,7 +750,7 @@ extern "C" pt_status pt_nrc_infer(pt_nrc* N, const float* queries, uint32_t n, f
         N->icap = n;
     }
     // the MLP writes 4 floats per row; out_rgb is the caller's n x 4 buffer
-    return nrc_forward(N, queries, RowCount{n, nullptr}, N->iX, out_rgb, nullptr, st);
+    return nrc_forward(N, queries, RowCount{n, nullptr, 0}, N->iX, out_rgb, nullptr, st);
 }
 
 extern "C" pt_status pt_nrc_params(pt_nrc* N, int which, float** ptr, uint64_t* count) {
@@ -711,13 +788,22 @@ pt_status pt_nrc_render_infer_dev(pt_nrc* N, const float* queries, const uint32_
         PT_CUDA_TRY(cudaMalloc(&N->iX, (size_t)cap * W * sizeof(__half)));
         N->icap = cap;
     }
-    return nrc_forward(N, queries, RowCount{cap, n_dev}, N->iX, out4, nullptr, st);
+    return nrc_forward(N, queries, RowCount{cap, n_dev, 0}, N->iX, out4, nullptr, st);
 }
 
+// one Adam step per `batch` samples of the frame's training list (its length is on the device;
+// a batch past the end of the list is no step)
 pt_status pt_nrc_render_train_dev(pt_nrc* N, const float* samples, const uint32_t* n_dev, uint32_t cap, cudaStream_t st) {
-    pt_status r = ensure_train(N, cap);
+    const uint32_t batch = std::min(N->o.batch, cap);
+    pt_status r = ensure_train(N, batch);
     if (r != PT_OK) return r;
-    r = nrc_gradients(N, samples, RowCount{cap, n_dev}, st);
-    if (r != PT_OK) return r;
-    return nrc_adam(N, st);
+    PT_CUDA_TRY(cudaMemsetAsync(N->d_loss, 0, 2 * sizeof(float), st));
+    for (uint32_t b0 = 0; b0 < cap; b0 += batch) {
+        const RowCount rc{std::min(batch, cap - b0), n_dev, b0};
+        r = nrc_gradients(N, samples + (size_t)QSTRIDE * b0, rc, st);
+        if (r != PT_OK) return r;
+        r = nrc_adam(N, rc, st);
+        if (r != PT_OK) return r;
+    }
+    return PT_OK;
 }

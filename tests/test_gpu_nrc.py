@@ -135,6 +135,19 @@ def test_nrc_adam_step():
         assert sel.mean() > 0.01
         assert np.allclose(p1[sel], exp[sel], rtol=1e-5, atol=1e-7)
         assert np.allclose(p1[g == 0], p0[g == 0])
+    # second step on samples from another part of the box: grid entries with a zero gradient
+    # keep their value although their moments are non-zero (lazy Adam), the touched ones move
+    rec2 = _records(rng, 512)
+    rec2[:, 0] = 0.5 * rec2[:, 0] + 0.5
+    t2 = torch.from_numpy(rec2).cuda()
+    _, dg2 = net.gradients(t2)
+    dg2 = dg2.cpu().numpy()
+    net.train(t2)
+    g_2 = net.params(1).cpu().numpy().astype(np.float64)
+    moved1 = (g_new != gn) & (dg2 == 0)
+    assert moved1.sum() > 100
+    assert np.array_equal(g_2[dg2 == 0], g_new[dg2 == 0])
+    assert np.mean(g_2[dg2 != 0] != g_new[dg2 != 0]) > 0.99
 
 
 def test_nrc_training_reduces_loss():

@@ -282,9 +282,11 @@ def run_ours(args, world, rank, local):
     scene.render(1, seed=seed, accum=probe, mode=mode, flags=N.PT_FLAG_COUNT)
     after = scene.stats()
     cnt = {k: after[k] - before[k] for k in ("ext_rays", "shadow_rays", "trace_nodes", "trace_tris",
-                                             "shadow_nodes", "shadow_tris")}
+                                             "shadow_nodes", "shadow_tris", "tail_ext_rays")}
+    # rays the per-bounce closest-hit kernel traced (the tail kernel counts its own)
+    cnt["trace_rays"] = cnt["ext_rays"] - cnt["tail_ext_rays"]
     trace_bytes_step = (cnt["trace_nodes"] * NODE_BYTES + cnt["trace_tris"] * TRI_BYTES +
-                        cnt["ext_rays"] * (RAY_BYTES + HIT_BYTES))
+                        cnt["trace_rays"] * (RAY_BYTES + HIT_BYTES))
     trace_ops_step = cnt["trace_nodes"] * OPS_PER_NODE + cnt["trace_tris"] * OPS_PER_TRI
     # timed region
     kernel_ms = (N.f32 * len(N.KERNEL_KINDS))()
@@ -372,12 +374,27 @@ def run_ours(args, world, rank, local):
                      "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (recipe unit counts and clock)",
                      "algorithmic_ops_per_launch": trace_ops_step / trace_launches,
                      "launch_ms": trace_ms / trace_launches,
-                     "per_ray": {"nodes": cnt["trace_nodes"] / max(cnt["ext_rays"], 1),
-                                 "tris": cnt["trace_tris"] / max(cnt["ext_rays"], 1)},
+                     "per_ray": {"nodes": cnt["trace_nodes"] / max(cnt["trace_rays"], 1),
+                                 "tris": cnt["trace_tris"] / max(cnt["trace_rays"], 1),
+                                 "rays_per_step": cnt["trace_rays"]},
                      "hbm_view": {"algorithmic_bytes_per_step": trace_bytes_step, "achieved_gbs": achieved_gbs,
                                   "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src}},
         "clocks": clocks.summary(),
     }
+    # display resolve (off the timed path): tone map of the accumulated frame, 12 B in + 4 B out
+    # per pixel
+    rgba = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        acc.tonemap(out=rgba)
+    t_a, t_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_a.record(stream)
+    for _ in range(20):
+        acc.tonemap(out=rgba)
+    t_b.record(stream)
+    torch.cuda.synchronize()
+    tm_ms = t_a.elapsed_time(t_b) / 20
+    result["tonemap"] = {"kernel": "k_tonemap", "us": tm_ms * 1e3, "bytes": W * H * 16,
+                         "gbs": W * H * 16 / (tm_ms * 1e-3) / 1e9, "note": "after the timed region"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
     if rank == 0:

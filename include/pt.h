@@ -310,6 +310,21 @@ pt_status pt_env_pdf(pt_scene* scene, const float* dirs, uint32_t n, float* pdf_
 pt_status pt_bvh_export(pt_scene* scene, uint32_t* nodes_out, float* tris_out, uint32_t* n_nodes,
                         uint32_t* n_tris, void* cuda_stream);
 
+/* Display resolve (Sec. 5.1.4: the accumulated texture is shown through a full-screen pass
+ * that applies the Khronos PBR Neutral tone mapper).  Per pixel: mean = sum / spp_done,
+ * times `exposure`; NaN becomes 0 and the mean is clamped to [0, 1e30]; PBR Neutral
+ * (offset toe with F90 = 0.04, highlight compression from 0.76, desaturation 0.15); clamp
+ * to [0, 1]; with PT_TONEMAP_SRGB the sRGB transfer function (IEC 61966-2-1); then
+ * floor(255 v + 0.5) into R, G, B and 255 into A.  Every step is an FP32 operation in that
+ * order (no fused multiply-adds), as the tone mapper runs in the paper's shader.
+ *  accum     the accumulator (DEVICE sum, height*width*3 floats; comp is not read)
+ *  rgba_out  DEVICE uint8[height*width*4], 4-byte aligned, row-major RGBA
+ * Errors: PT_ERR_INVALID_ARG (NULL pointers, spp_done == 0, exposure negative or not
+ * finite, misaligned output).  Asynchronous on the stream. */
+#define PT_TONEMAP_SRGB 1u
+pt_status pt_tonemap(const pt_accum* accum, float exposure, uint32_t flags, uint8_t* rgba_out,
+                     void* cuda_stream);
+
 /* Statistics and sticky device error bits; synchronises the scene's last stream. */
 pt_status pt_get_stats(pt_scene* scene, pt_stats* out);
 pt_status pt_scene_sync(pt_scene* scene);

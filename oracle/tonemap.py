@@ -12,7 +12,8 @@ constants and four steps on a linear RGB colour c:
   3. d = 1 - K_s; p' = 1 - d^2 / (p + d - K_s); c <- c * p' / p   (p' -> 1 as p -> inf)
   4. g = 1 - 1 / (K_d (p - p') + 1); c <- (1 - g) c + g p' (1, 1, 1)   (desaturation)
 
-The displayed image is the progressive mean (sum / spp) times an exposure, tone mapped,
+The displayed image is the progressive mean (sum / spp) times an exposure (NaN read as 0,
+clamped to [0, 1e30]: a guard of this library, radiance being finite and >= 0), tone mapped,
 then (reading of this library) encoded with the sRGB transfer function of IEC 61966-2-1 and
 quantised to 8 bits as floor(255 v + 0.5), alpha 255.
 
@@ -59,7 +60,10 @@ def srgb_encode(v):
 def resolve_float(sum_rgb, spp, exposure=1.0, srgb=True):
     """The pre-quantisation display values (H, W, 3) float32."""
     mean = (np.asarray(sum_rgb, dtype=np.float32) * np.float32(1.0 / spp)).astype(np.float32)
-    v = pbr_neutral((mean * np.float32(exposure)).astype(np.float32))
+    mean = (mean * np.float32(exposure)).astype(np.float32)
+    # guard of this library: NaN -> 0, the mean clamped to [0, 1e30]
+    mean = np.where(np.isnan(mean), np.float32(0), np.clip(mean, np.float32(0), np.float32(1e30)))
+    v = pbr_neutral(mean.astype(np.float32))
     v = np.clip(v, np.float32(0), np.float32(1))
     return srgb_encode(v) if srgb else v
 

@@ -55,6 +55,15 @@ class Accum:
     def image(self) -> torch.Tensor:
         return self.sum / max(self.spp_done, 1)
 
+    def tonemap(self, exposure=1.0, srgb=True, out=None, stream=None) -> torch.Tensor:
+        """Display resolve through pt_tonemap: (height, width, 4) uint8 RGBA on the device."""
+        h, w = self.sum.shape[0], self.sum.shape[1]
+        if out is None:
+            out = torch.empty((h, w, 4), dtype=torch.uint8, device=self.sum.device)
+        N.call("pt_tonemap", C.byref(self.c), float(exposure), N.PT_TONEMAP_SRGB if srgb else 0, _ptr(out),
+               _stream_handle(stream))
+        return out
+
 
 class Scene:
     """A scene uploaded through pt_scene_create and (by default) built with pt_bvh_build."""

@@ -25,3 +25,10 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="module")
+def api():
+    """The Python binding of the C-ABI library (GPU tests)."""
+    from paper_2407_19977_gb300 import api as A
+    return A

@@ -19,12 +19,6 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module")
-def api():
-    from paper_2407_19977_gb300 import api as A
-    return A
-
-
 _CACHE = {}
 
 

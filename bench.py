@@ -61,6 +61,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pushbutton", choices=sorted(WORKLOADS))
+    ap.add_argument("--graph", type=int, default=1, help="replay each frame's wavefront launches as a CUDA graph")
     ap.add_argument("--mode", default="wavefront", choices=["auto", "wavefront", "megakernel"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
@@ -271,7 +272,7 @@ def run_ours(args, world, rank, local):
     seed = 1000 * rank
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     for _ in range(args.warmup):
-        scene.render(1, seed=seed, accum=acc, mode=mode)
+        scene.render(1, seed=seed, accum=acc, mode=mode, use_graph=args.graph)
     torch.cuda.synchronize()
     # untimed instrumented frame at the first timed sample index: node visits and triangle
     # tests per ray give the traversal's algorithmic bytes
@@ -302,7 +303,7 @@ def run_ours(args, world, rank, local):
         for k in range(args.steps):
             flush.fill_(float(k))  # L2 flush between steps, outside the timed events
             starts[k].record(stream)
-            scene.render(1, seed=seed, accum=acc, mode=mode)
+            scene.render(1, seed=seed, accum=acc, mode=mode, use_graph=args.graph)
             ends[k].record(stream)
         torch.cuda.synchronize()
     launches = api.launch_count() - launches_before
@@ -337,7 +338,7 @@ def run_ours(args, world, rank, local):
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         cam_k = type(cam)(**cam.__dict__)
-        scene.render(1, seed=seed, accum=acc, mode=mode, camera=cam_k)
+        scene.render(1, seed=seed, accum=acc, mode=mode, camera=cam_k, use_graph=args.graph)
         host_img.copy_(acc.sum, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t0
@@ -359,7 +360,7 @@ def run_ours(args, world, rank, local):
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "mode": args.mode, "l2": "flushed between steps",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "cuda_graph": bool(args.graph)},
         "spp_per_s_1080p": spp_s,
         "rays_per_step": rays / args.steps,
         "bvh_build_ms": bvh_ms, "upload_ms": upload_ms,

@@ -148,6 +148,13 @@ typedef struct {
                                    launch per stage and bounce; same per-vertex code and random
                                    numbers, so the image is the same.  -1 off, 0 automatic
                                    (the paths the tail kernel holds resident on the GPU) */
+    uint32_t use_graph;         /* wavefront: 1 = capture the call's launch sequence into a CUDA
+                                   graph once and replay it while the call looks the same (scene,
+                                   camera, window, accumulator, spp, depth, options); the first
+                                   sample index and the seed are written to device memory before
+                                   each replay, so progressive calls reuse one graph.  The capture
+                                   runs on a stream of the scene; replays run on cuda_stream.  Not
+                                   with nrc or kernel_ms (those calls launch directly). */
 } pt_render_opts;
 
 typedef struct {
@@ -178,6 +185,7 @@ typedef struct {
     uint64_t tail_trace_tris;
     uint64_t tail_shadow_nodes;
     uint64_t tail_shadow_tris;
+    uint64_t graph_replays;     /* wavefront calls served by replaying a captured CUDA graph */
     uint32_t error_flags;       /* sticky device error bits (1 = stack overflow, 2 = timeout) */
     uint32_t reserved;
 } pt_stats;

@@ -125,7 +125,7 @@ class Scene:
 
     def render(self, spp, max_depth=None, seed=0, accum=None, camera=None, crop=None, flags=0,
                mode=N.PT_MODE_AUTO, wave_paths=0, sort=-1, sample_out=None, block_size=0, stream=None,
-               kernel_ms=None, kernel_launches=None, nrc=None, nrc_train=False, tail_paths=0):
+               kernel_ms=None, kernel_launches=None, nrc=None, nrc_train=False, tail_paths=0, use_graph=False):
         cam = camera or self.desc.camera
         max_depth = self.desc.max_depth if max_depth is None else max_depth
         if crop is None:
@@ -137,6 +137,7 @@ class Scene:
         o.crop_x0, o.crop_y0, o.flags, o.mode = x0, y0, flags, mode
         o.wave_paths, o.sort_by_material, o.block_size = wave_paths, sort, block_size
         o.tail_paths = int(tail_paths)
+        o.use_graph = 1 if use_graph else 0
         o.sample_out = _ptr(sample_out) if sample_out is not None else None
         if nrc is not None:
             o.nrc = nrc.h

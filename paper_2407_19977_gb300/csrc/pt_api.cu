@@ -149,6 +149,8 @@ static void free_scene(pt_scene* s) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     pt_free_wave(s->wave);
+    if (s->wf_graph) cudaGraphExecDestroy(s->wf_graph);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
 }
 
@@ -360,6 +362,7 @@ extern "C" pt_status pt_get_stats(pt_scene* s, pt_stats* out) {
     out->tail_trace_tris = st[ST_TAIL_TRIS];
     out->tail_shadow_nodes = st[ST_TAIL_SH_NODES];
     out->tail_shadow_tris = st[ST_TAIL_SH_TRIS];
+    out->graph_replays = s->graph_replays;
     out->error_flags = err;
     if (err & 2u) { pt_set_error("device wait ran out of its spin budget"); return PT_ERR_TIMEOUT; }
     if (err & 1u) { pt_set_error("traversal stack or work queue overflow"); return PT_ERR_QUEUE_OVERFLOW; }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <vector>
 #include <cstdint>
 #include <string>
 
@@ -102,6 +103,13 @@ struct pt_scene {
     WaveBuffers wave;
     cudaStream_t last_stream = nullptr;
     uint64_t launches = 0;
+    // captured wavefront call (pt_render_opts.use_graph): the graph, what it was captured for,
+    // the kernels it launches, the stream it was captured on, calls that replayed it
+    cudaGraphExec_t wf_graph = nullptr;
+    std::vector<unsigned char> wf_key;
+    uint64_t wf_graph_launches = 0;
+    cudaStream_t cap_stream = nullptr;
+    uint64_t graph_replays = 0;
 
     DScene view() const {
         DScene s;

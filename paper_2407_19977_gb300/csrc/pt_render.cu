@@ -194,8 +194,12 @@ static pt_status launch_megakernel(const std::vector<DJob>& jobs_in, uint32_t ti
 
 // ------------------------------------------------------------------ wavefront
 // counters: queue sizes, fetch heads, C_TAIL = 1 once the tail kernel has taken the wave's
-// remaining paths (the per-bounce kernels then have nothing to do), sort buckets
-enum { C_Q0 = 0, C_Q1 = 1, C_SH = 2, C_HEAD_TRACE = 3, C_HEAD_SHADOW = 4, C_TAIL = 5, C_BUCKETS = 16 };
+// remaining paths (the per-bounce kernels then have nothing to do), C_FRAME.. the values that
+// change from one call to the next (first sample index, seed: written by k_wf_frame, so the
+// launch sequence of a call is the same every call and can be replayed as a CUDA graph),
+// sort buckets
+enum { C_Q0 = 0, C_Q1 = 1, C_SH = 2, C_HEAD_TRACE = 3, C_HEAD_SHADOW = 4, C_TAIL = 5, C_FRAME = 8,
+       C_BUCKETS = 16 };
 constexpr uint32_t MAX_SORT_KEYS = 1024;
 
 struct WfParams {
@@ -203,10 +207,9 @@ struct WfParams {
     DCam cam;
     uint32_t x0, y0, cw;           // window origin and width
     uint32_t pb, npix;             // pixel range of this wave (window-local linear index)
-    uint32_t sb, nsamp;            // sample range of this wave
-    uint32_t s_call0, spp_call;    // first sample of the pt_render call, samples in the call
+    uint32_t i0, nsamp;            // samples of this wave: call-relative first, count
+    uint32_t spp_call;             // samples in the call
     uint32_t max_depth, flags;
-    uint64_t seed;
     uint32_t n_keys;               // material sort buckets (0 = no sort)
     float4* ray_o[2];
     float4* ray_d[2];
@@ -239,6 +242,19 @@ struct WfParams {
 
 constexpr uint32_t NRC_DIM_TRAIN = 10;   // uniform dimension of the training-path choice
 
+// first sample index of this wave and the seed, from the per-call words of the counters
+__device__ __forceinline__ uint32_t wf_sample_base(const WfParams& P) { return P.counters[C_FRAME] + P.i0; }
+__device__ __forceinline__ uint64_t wf_seed(const WfParams& P) {
+    return *reinterpret_cast<const unsigned long long*>(P.counters + C_FRAME + 2);
+}
+
+__global__ void k_wf_frame(uint32_t* counters, uint32_t first_sample, uint64_t seed) {
+    if (threadIdx.x == 0) {
+        counters[C_FRAME] = first_sample;
+        *reinterpret_cast<unsigned long long*>(counters + C_FRAME + 2) = seed;
+    }
+}
+
 __global__ void k_wf_raygen(WfParams P) {
     const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t n = P.npix * P.nsamp;
@@ -249,10 +265,11 @@ __global__ void k_wf_raygen(WfParams P) {
     }
     if (id >= n) return;
     const uint32_t lp = P.pb + id % P.npix;
-    const uint32_t s = P.sb + id / P.npix;
+    const uint32_t s = wf_sample_base(P) + id / P.npix;
+    const uint64_t seed = wf_seed(P);
     const uint32_t px = P.x0 + lp % P.cw, py = P.y0 + lp / P.cw;
     const uint32_t p = py * P.cam.width + px;
-    const uint4 u = philox4x32_10(make_uint4(p, s, 0u, 0u), (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    const uint4 u = philox4x32_10(make_uint4(p, s, 0u, 0u), (uint32_t)seed, (uint32_t)(seed >> 32));
     float3 o, d;
     camera_ray(P.cam, px, py, u24(u.x), u24(u.y), o, d);
     P.ray_o[0][id] = make_float4(o.x, o.y, o.z, 0.0f);
@@ -261,8 +278,8 @@ __global__ void k_wf_raygen(WfParams P) {
     P.radiance[id] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (P.nrc_on) {
         uint32_t aux = 0;
-        if (P.max_train && u24(philox4x32_10(make_uint4(p, s, 0u, NRC_DIM_TRAIN >> 2), (uint32_t)P.seed,
-                                             (uint32_t)(P.seed >> 32)).z) < P.train_prob) {
+        if (P.max_train && u24(philox4x32_10(make_uint4(p, s, 0u, NRC_DIM_TRAIN >> 2), (uint32_t)seed,
+                                             (uint32_t)(seed >> 32)).z) < P.train_prob) {
             const uint32_t slot = atomicAdd(&P.nrc_counters[1], 1u);
             if (slot < P.max_train) {
                 aux = (slot + 1u) << 8;
@@ -452,6 +469,8 @@ template <bool NRC>
 __global__ void __launch_bounds__(128) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
     if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[in_q];
+    const uint32_t sbase = wf_sample_base(P);
+    const uint64_t seed = wf_seed(P);
     const uint32_t lane = lane_id();
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t lt = (1u << lane) - 1u;
@@ -478,10 +497,10 @@ __global__ void __launch_bounds__(128) k_wf_shade(WfParams P, int in_q, int out_
             ps.prev_pdf = b4.w;
             ps.L = xyz(L4);
             const uint32_t lp = P.pb + id % P.npix;
-            const uint32_t s = P.sb + id / P.npix;
+            const uint32_t s = sbase + id / P.npix;
             VertexRng rng;
             rng.p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
-            rng.s = s; rng.k = k; rng.k0 = (uint32_t)P.seed; rng.k1 = (uint32_t)(P.seed >> 32);
+            rng.s = s; rng.k = k; rng.k0 = (uint32_t)seed; rng.k1 = (uint32_t)(seed >> 32);
             ShadeOut so;
             int r;
             if (NRC) {
@@ -577,6 +596,8 @@ __global__ void __launch_bounds__(128) k_wf_tail(WfParams P, int in_q, uint32_t 
     const uint32_t count = P.counters[in_q];
     if (count == 0 || count > limit) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) P.counters[C_TAIL] = 1u;
+    const uint32_t sbase = wf_sample_base(P);
+    const uint64_t seed = wf_seed(P);
     unsigned long long n_ext = 0, n_sh = 0, n_rr = 0;
     TravCount tc = {0, 0}, sc = {0, 0};
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
@@ -591,9 +612,9 @@ __global__ void __launch_bounds__(128) k_wf_tail(WfParams P, int in_q, uint32_t 
         const uint32_t lp = P.pb + id % P.npix;
         VertexRng rng;
         rng.p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
-        rng.s = P.sb + id / P.npix;
-        rng.k0 = (uint32_t)P.seed;
-        rng.k1 = (uint32_t)(P.seed >> 32);
+        rng.s = sbase + id / P.npix;
+        rng.k0 = (uint32_t)seed;
+        rng.k1 = (uint32_t)(seed >> 32);
         NrcHook hook;
         if (NRC) {
             hook.P = &P;
@@ -664,7 +685,7 @@ __global__ void k_wf_accum(WfParams P) {
                 L = make_float4(0, 0, 0, 0);
             }
             if (P.sample_out) {
-                float* o3 = P.sample_out + 3ull * ((uint64_t)lp * P.spp_call + (P.sb + q - P.s_call0));
+                float* o3 = P.sample_out + 3ull * ((uint64_t)lp * P.spp_call + (P.i0 + q));
                 o3[0] = L.x; o3[1] = L.y; o3[2] = L.z;
             }
             kahan_add(s0, c0, L.x);
@@ -738,8 +759,17 @@ static pt_status ensure_nrc_buffers(WaveBuffers& w, uint32_t rec_per_path) {
 
 static int g_trace_blocks_per_sm = 0, g_shade_blocks_per_sm = 0, g_shadow_blocks_per_sm = 0, g_tail_blocks_per_sm = 0;
 
+// Everything that shapes the launch sequence of a wavefront call (the per-call words, first
+// sample and seed, live in device memory): equal keys mean the same captured graph replays.
+struct WfGraphKey {
+    WfParams P;             // with the per-wave fields cleared
+    uint32_t spp, npix_total, pix_chunk, samp_per_wave, tail_limit, tail_grid, count;
+    int sms, trace_bps, shade_bps, shadow_bps;
+};
+
 static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
-                                  pt_accum* acc, const pt_render_opts& o, cudaStream_t st) {
+                                  pt_accum* acc, const pt_render_opts& o, cudaStream_t user_st) {
+    cudaStream_t st = user_st;   // the stream the wave loops below issue to (a capture stream while capturing)
     const uint32_t npix_total = acc->width * acc->height;
     uint32_t cap = o.wave_paths ? o.wave_paths : (1u << 21);
     cap = std::max(cap, 32u);
@@ -776,11 +806,9 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     P.x0 = o.crop_x0;
     P.y0 = o.crop_y0;
     P.cw = acc->width;
-    P.s_call0 = (uint32_t)acc->spp_done;
     P.spp_call = spp;
     P.max_depth = max_depth;
     P.flags = o.flags;
-    P.seed = seed;
     P.n_keys = n_keys;
     for (int q = 0; q < 2; ++q) { P.ray_o[q] = w.ray_o[q]; P.ray_d[q] = w.ray_d[q]; }
     P.hit = w.hit; P.beta = w.beta; P.radiance = w.radiance;
@@ -803,6 +831,37 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     const bool count = (o.flags & FLAG_COUNT) != 0;
     // optional per-kind timing: an event pair around every launch of a kind
     const bool timed = o.kernel_ms != nullptr;
+    // the per-call words first, on the caller's stream (graph or not)
+    PT_LAUNCH(k_wf_frame, 1, 32, 0, user_st, w.counters, (uint32_t)acc->spp_done, seed);
+    ++launches;
+    const bool graph = o.use_graph && !P.nrc_on && !timed;
+    WfGraphKey key;
+    if (graph) {
+        std::memset(&key, 0, sizeof(key));
+        key.P = P;
+        key.spp = spp; key.npix_total = npix_total; key.pix_chunk = pix_chunk; key.samp_per_wave = samp_per_wave;
+        key.tail_limit = tail_limit; key.tail_grid = tail_grid; key.count = count ? 1u : 0u;
+        key.sms = sms; key.trace_bps = g_trace_blocks_per_sm; key.shade_bps = g_shade_blocks_per_sm;
+        key.shadow_bps = g_shadow_blocks_per_sm;
+        if (s->wf_graph && s->wf_key.size() == sizeof(key) && std::memcmp(s->wf_key.data(), &key, sizeof(key)) == 0) {
+            PT_CUDA_TRY(cudaGraphLaunch(s->wf_graph, user_st));
+            pt_count_launch(s->wf_graph_launches);
+            s->launches += launches + s->wf_graph_launches;
+            s->graph_replays++;
+            return PT_OK;
+        }
+        if (s->wf_graph) {
+            cudaGraphExecDestroy(s->wf_graph);
+            s->wf_graph = nullptr;
+            s->wf_key.clear();
+        }
+        if (!s->cap_stream) PT_CUDA_TRY(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+        // capture on the library's own stream (the caller's may be the legacy default stream,
+        // which cannot be captured); the graph then runs on the caller's stream
+        PT_CUDA_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+        st = s->cap_stream;
+    }
+    const uint64_t global_before = g_pt_launches.load();
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PT_K_KINDS];
     auto begin = [&](int kind) -> cudaEvent_t {
         if (!timed) return nullptr;
@@ -816,81 +875,115 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     auto end = [&](cudaEvent_t b) {
         if (b) cudaEventRecord(b, st);
     };
-    for (uint32_t pb = 0; pb < npix_total; pb += pix_chunk) {
-        const uint32_t npix = std::min(pix_chunk, npix_total - pb);
-        for (uint32_t i0 = 0; i0 < spp; i0 += samp_per_wave) {
-            const uint32_t ns = std::min(samp_per_wave, spp - i0);
-            P.pb = pb;
-            P.npix = npix;
-            P.sb = (uint32_t)acc->spp_done + i0;
-            P.nsamp = ns;
-            const uint32_t n = npix * ns;
-            if (P.nrc_on) {
-                P.train_prob = std::min(1.0f, (float)w.train_slots / (float)n);
-                PT_CUDA_TRY(cudaMemsetAsync(w.nrc_counters, 0, 8 * sizeof(uint32_t), st));
-            }
-            cudaEvent_t e = begin(PT_K_RAYGEN);
-            PT_LAUNCH(k_wf_raygen, (n + 255) / 256, 256, 0, st, P);
-            end(e);
-            ++launches;
-            for (uint32_t k = 0; k <= max_depth; ++k) {
-                const int in_q = (int)(k & 1u), out_q = (int)((k + 1) & 1u);
-                PT_LAUNCH(k_wf_setup, 1, 256, 0, st, w.counters, out_q, n_keys);
-                ++launches;
-                if (tail_limit) {
-                    e = begin(PT_K_TAIL);
-                    if (P.nrc_on) {
-                        if (count) PT_LAUNCH((k_wf_tail<true, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                        else PT_LAUNCH((k_wf_tail<true, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                    } else {
-                        if (count) PT_LAUNCH((k_wf_tail<false, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                        else PT_LAUNCH((k_wf_tail<false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                    }
-                    end(e);
-                    ++launches;
+    auto issue = [&]() -> pt_status {
+        for (uint32_t pb = 0; pb < npix_total; pb += pix_chunk) {
+            const uint32_t npix = std::min(pix_chunk, npix_total - pb);
+            for (uint32_t i0 = 0; i0 < spp; i0 += samp_per_wave) {
+                const uint32_t ns = std::min(samp_per_wave, spp - i0);
+                P.pb = pb;
+                P.npix = npix;
+                P.i0 = i0;
+                P.nsamp = ns;
+                const uint32_t n = npix * ns;
+                if (P.nrc_on) {
+                    P.train_prob = std::min(1.0f, (float)w.train_slots / (float)n);
+                    PT_CUDA_TRY(cudaMemsetAsync(w.nrc_counters, 0, 8 * sizeof(uint32_t), st));
                 }
-                e = begin(PT_K_TRACE);
-                if (count) PT_LAUNCH(k_wf_trace<true>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
-                else PT_LAUNCH(k_wf_trace<false>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
+                cudaEvent_t e = begin(PT_K_RAYGEN);
+                PT_LAUNCH(k_wf_raygen, (n + 255) / 256, 256, 0, st, P);
                 end(e);
                 ++launches;
-                if (n_keys) {
-                    e = begin(PT_K_SORT);
-                    PT_LAUNCH(k_wf_sort_scan, 1, MAX_SORT_KEYS, 0, st, w.counters, n_keys);
-                    PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
+                for (uint32_t k = 0; k <= max_depth; ++k) {
+                    const int in_q = (int)(k & 1u), out_q = (int)((k + 1) & 1u);
+                    PT_LAUNCH(k_wf_setup, 1, 256, 0, st, w.counters, out_q, n_keys);
+                    ++launches;
+                    if (tail_limit) {
+                        e = begin(PT_K_TAIL);
+                        if (P.nrc_on) {
+                            if (count) PT_LAUNCH((k_wf_tail<true, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                            else PT_LAUNCH((k_wf_tail<true, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                        } else {
+                            if (count) PT_LAUNCH((k_wf_tail<false, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                            else PT_LAUNCH((k_wf_tail<false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                        }
+                        end(e);
+                        ++launches;
+                    }
+                    e = begin(PT_K_TRACE);
+                    if (count) PT_LAUNCH(k_wf_trace<true>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
+                    else PT_LAUNCH(k_wf_trace<false>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
+                    end(e);
+                    ++launches;
+                    if (n_keys) {
+                        e = begin(PT_K_SORT);
+                        PT_LAUNCH(k_wf_sort_scan, 1, MAX_SORT_KEYS, 0, st, w.counters, n_keys);
+                        PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
+                        end(e);
+                        launches += 2;
+                    }
+                    e = begin(PT_K_SHADE);
+                    if (P.nrc_on) PT_LAUNCH(k_wf_shade<true>, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+                    else PT_LAUNCH(k_wf_shade<false>, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+                    end(e);
+                    e = begin(PT_K_SHADOW);
+                    if (count) PT_LAUNCH(k_wf_shadow<true>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
+                    else PT_LAUNCH(k_wf_shadow<false>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
                     end(e);
                     launches += 2;
                 }
-                e = begin(PT_K_SHADE);
-                if (P.nrc_on) PT_LAUNCH(k_wf_shade<true>, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
-                else PT_LAUNCH(k_wf_shade<false>, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
-                end(e);
-                e = begin(PT_K_SHADOW);
-                if (count) PT_LAUNCH(k_wf_shadow<true>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
-                else PT_LAUNCH(k_wf_shadow<false>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
-                end(e);
-                launches += 2;
-            }
-            if (P.nrc_on) {
-                // cache inference for the paths that ended at their second diffuse-ish vertex,
-                // then training on this wave's training-path suffixes; the counts stay on the
-                // device, so nothing here waits for the GPU
-                pt_status rr = pt_nrc_render_infer_dev(o.nrc, w.nrc_q, w.nrc_counters, n, w.nrc_out, st);
-                if (rr != PT_OK) return rr;
-                PT_LAUNCH(k_nrc_apply, sms * 4, 256, 0, st, P);
-                ++launches;
-                if (P.max_train) {
-                    PT_LAUNCH(k_nrc_targets, (P.max_train + 127) / 128, 128, 0, st, P);
-                    ++launches;
-                    rr = pt_nrc_render_train_dev(o.nrc, w.train_samples, w.nrc_counters + 2, P.sample_cap, st);
+                if (P.nrc_on) {
+                    // cache inference for the paths that ended at their second diffuse-ish vertex,
+                    // then training on this wave's training-path suffixes; the counts stay on the
+                    // device, so nothing here waits for the GPU
+                    pt_status rr = pt_nrc_render_infer_dev(o.nrc, w.nrc_q, w.nrc_counters, n, w.nrc_out, st);
                     if (rr != PT_OK) return rr;
+                    PT_LAUNCH(k_nrc_apply, sms * 4, 256, 0, st, P);
+                    ++launches;
+                    if (P.max_train) {
+                        PT_LAUNCH(k_nrc_targets, (P.max_train + 127) / 128, 128, 0, st, P);
+                        ++launches;
+                        rr = pt_nrc_render_train_dev(o.nrc, w.train_samples, w.nrc_counters + 2, P.sample_cap, st);
+                        if (rr != PT_OK) return rr;
+                    }
                 }
+                e = begin(PT_K_ACCUM);
+                PT_LAUNCH(k_wf_accum, (npix + 255) / 256, 256, 0, st, P);
+                end(e);
+                ++launches;
             }
-            e = begin(PT_K_ACCUM);
-            PT_LAUNCH(k_wf_accum, (npix + 255) / 256, 256, 0, st, P);
-            end(e);
-            ++launches;
         }
+        return PT_OK;
+    };
+    pt_status ir = issue();
+    if (graph) {
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
+        st = user_st;
+        // captured launches were recorded, not run: they count when the graph runs
+        const uint64_t captured = g_pt_launches.load() - global_before;
+        g_pt_launches.fetch_sub(captured);
+        if (ir != PT_OK) {
+            if (g) cudaGraphDestroy(g);
+            return ir;
+        }
+        if (ce != cudaSuccess) {
+            pt_set_error(std::string("graph capture: ") + cudaGetErrorString(ce));
+            return PT_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            pt_set_error(std::string("graph instantiate: ") + cudaGetErrorString(ie));
+            return PT_ERR_CUDA;
+        }
+        s->wf_graph = ex;
+        s->wf_key.assign(reinterpret_cast<const unsigned char*>(&key), reinterpret_cast<const unsigned char*>(&key) + sizeof(key));
+        s->wf_graph_launches = captured;
+        PT_CUDA_TRY(cudaGraphLaunch(ex, user_st));
+        pt_count_launch(captured);
+    } else if (ir != PT_OK) {
+        return ir;
     }
     s->launches += launches;
     PT_CUDA_TRY(cudaGetLastError());
@@ -1106,11 +1199,9 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
     P.x0 = o.crop_x0;
     P.y0 = o.crop_y0;
     P.cw = acc->width;
-    P.s_call0 = (uint32_t)acc->spp_done;
     P.spp_call = spp;
     P.max_depth = max_depth;
     P.flags = o.flags & (FLAG_NO_NEE | FLAG_NO_RR);
-    P.seed = seed;
     P.n_keys = n_keys;
     for (int q = 0; q < 2; ++q) { P.ray_o[q] = w.ray_o[q]; P.ray_d[q] = w.ray_d[q]; }
     P.hit = w.hit; P.beta = w.beta; P.radiance = w.radiance;
@@ -1120,10 +1211,11 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
     P.stats = s->d_stats;
     P.pb = 0;
     P.npix = npix;
-    uint64_t launches = 0;
+    PT_LAUNCH(k_wf_frame, 1, 32, 0, st, w.counters, (uint32_t)acc->spp_done, seed);
+    uint64_t launches = 1;
     for (uint32_t i0 = 0; i0 < spp; i0 += samp_per_wave) {
         const uint32_t ns = std::min(samp_per_wave, spp - i0);
-        P.sb = (uint32_t)acc->spp_done + i0;
+        P.i0 = i0;
         P.nsamp = ns;
         const uint32_t n = npix * ns;
         PT_LAUNCH(k_wf_raygen, (n + 255) / 256, 256, 0, st, P);

@@ -43,7 +43,7 @@ class pt_render_opts(C.Structure):
     _fields_ = [("crop_x0", u32), ("crop_y0", u32), ("flags", u32), ("mode", u32), ("wave_paths", u32),
                 ("sort_by_material", C.c_int32), ("block_size", u32), ("sample_out", vp), ("nrc", vp),
                 ("nrc_train", u32), ("kernel_ms", C.POINTER(f32)), ("kernel_launches", C.POINTER(u32)),
-                ("tail_paths", C.c_int32)]
+                ("tail_paths", C.c_int32), ("use_graph", u32)]
 
 
 class pt_bvh_opts(C.Structure):
@@ -56,7 +56,7 @@ class pt_stats(C.Structure):
                 ("bvh_depth", u64), ("n_triangles", u64), ("trace_nodes", u64), ("trace_tris", u64),
                 ("shadow_nodes", u64), ("shadow_tris", u64), ("tail_ext_rays", u64), ("tail_shadow_rays", u64),
                 ("tail_trace_nodes", u64), ("tail_trace_tris", u64), ("tail_shadow_nodes", u64),
-                ("tail_shadow_tris", u64), ("error_flags", u32), ("reserved", u32)]
+                ("tail_shadow_tris", u64), ("graph_replays", u64), ("error_flags", u32), ("reserved", u32)]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}

@@ -472,6 +472,35 @@ def test_tail_kernel_ray_counts(api):
     assert off["shadow_tris"] == on["shadow_tris"] + on["tail_shadow_tris"]
 
 
+@pytest.mark.parametrize("which", ["cornell", "pushbutton"])
+def test_graph_replay_equals_direct_launches(api, which):
+    """use_graph captures a wavefront call once and replays it; the first sample index and the
+    seed live in device memory, so progressive calls (and a changed seed) replay the same graph
+    and accumulate exactly what direct launches accumulate.  A changed camera recaptures."""
+    from paper_2407_19977_gb300 import api as A
+    sc, gsc, osc = {"cornell": cornell, "pushbutton": pushbutton}[which]()
+    crop = (0, 0, 64, 64) if which == "cornell" else (700, 380, 192, 108)
+    cam2 = type(sc.camera)(**{**sc.camera.__dict__, "origin": tuple(np.add(sc.camera.origin, (0.01, 0.0, 0.0)))})
+    # captures: call 1, call 4 (spp changes the waves), call 5 (camera); replays: 2, 3 (seed), 6
+    calls = [(2, 5, sc.camera), (2, 5, sc.camera), (2, 9, sc.camera), (3, 9, sc.camera), (3, 9, cam2), (3, 9, cam2)]
+    res = []
+    for graph in (False, True):
+        from paper_2407_19977_gb300 import native as N
+        acc = A.Accum(crop[2], crop[3])
+        l0 = A.launch_count()
+        r0 = gsc.stats()["graph_replays"]
+        for spp, seed, cam in calls:
+            gsc.render(spp, seed=seed, accum=acc, crop=crop, camera=cam, mode=N.PT_MODE_WAVEFRONT, use_graph=graph)
+        torch.cuda.synchronize()
+        res.append((acc.sum.clone(), acc.comp.clone(), acc.spp_done, A.launch_count() - l0,
+                    gsc.stats()["graph_replays"] - r0))
+    (s0, c0, n0, l0, g0), (s1, c1, n1, l1, g1) = res
+    assert n0 == n1 == sum(c[0] for c in calls)
+    assert torch.equal(s0, s1) and torch.equal(c0, c1)
+    assert l0 == l1
+    assert g0 == 0 and g1 == 3
+
+
 def test_sort_by_material_does_not_change_results(api):
     from paper_2407_19977_gb300 import api as A
     sc, gsc, osc = pushbutton()

@@ -65,7 +65,8 @@ def _args():
     ap.add_argument("--mode", default="wavefront", choices=["auto", "wavefront", "megakernel"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
-    ap.add_argument("--study", default=None, choices=[None, "nrc"],
+    ap.add_argument("--batch-scenes", type=int, default=64)
+    ap.add_argument("--study", default=None, choices=[None, "nrc", "batch"],
                     help="nrc: relMSE vs time, radiance cache against the plain tracer")
     ap.add_argument("--ref-spp", type=int, default=4096)
     return ap.parse_args()
@@ -473,12 +474,79 @@ def run_nrc_study(args, local):
     print(json.dumps(out))
 
 
+def run_batch_study(args, local):
+    """64 seeded scenes of uneven size (pushbutton / heavy generators, 1k-500k triangles
+    log-uniform, 256^2 .. 1920x1080, 1-32 spp, depth 8): aggregate samples per second of one
+    persistent batched launch (graph-replayed, tile schedule from pt_autotune_batch on 1-spp
+    copies of the jobs) against the same jobs as per-scene pt_render calls (PT_MODE_AUTO:
+    wavefront from 2^16 pixels with graph replay, megakernel below), both on one stream."""
+    import torch
+    from paper_2407_19977_gb300 import api, scenes
+    from paper_2407_19977_gb300 import native as N
+    torch.cuda.set_device(local)
+    specs = scenes.batch_specs(args.batch_scenes)
+    t0 = time.perf_counter()
+    scs = [scenes.scene_from_spec(s) for s in specs]
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gs = [api.Scene(sc) for sc in scs]
+    torch.cuda.synchronize()
+    upload_build_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    samples = sum(s["width"] * s["height"] * s["spp"] for s in specs)
+    tris = sum(len(sc.indices) for sc in scs)
+
+    def timed(fn, reps=2):
+        out = []
+        for _ in range(reps):   # the first pass captures graphs
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return out[-1]
+
+    accs = [api.Accum(s["width"], s["height"]) for s in specs]
+
+    def per_scene():
+        for sp, g, sc, acc in zip(specs, gs, scs, accs):
+            g.render(sp["spp"], max_depth=sp["max_depth"], seed=sp["seed"], accum=acc, mode=N.PT_MODE_AUTO,
+                     use_graph=True)
+    t_scene = timed(per_scene)
+    baccs = [api.Accum(s["width"], s["height"]) for s in specs]
+    tune_jobs = [(g, sc.camera, 1, sp["max_depth"], sp["seed"], acc) for sp, g, sc, acc in zip(specs, gs, scs, baccs)]
+    best, tune_ms = api.autotune_batch(tune_jobs, frames=1)
+    jobs = [(g, sc.camera, sp["spp"], sp["max_depth"], sp["seed"], acc) for sp, g, sc, acc in zip(specs, gs, scs, baccs)]
+    variants = {"tuned": best,
+                "megakernel_one_launch": {"mode": N.PT_MODE_MEGAKERNEL, "streams": 0, "tile_pixels": 32,
+                                          "blocks_per_sm": 4, "use_graph": 1},
+                "wavefront_4_streams": {"mode": N.PT_MODE_WAVEFRONT, "streams": 4, "tile_pixels": 0,
+                                        "blocks_per_sm": 0, "use_graph": 0}}
+    res = {}
+    for name, o in variants.items():
+        t = timed(lambda: api.render_batch(jobs, tile_pixels=o["tile_pixels"], blocks_per_sm=o["blocks_per_sm"],
+                                           use_graph=bool(o["use_graph"]), mode=o["mode"], streams=o["streams"]))
+        res[name] = {"ms": t, "msamples_per_s": samples / (t * 1e-3) / 1e6, "opts": o,
+                     "over_per_scene": t_scene / t}
+    out = {"study": "batch", "workload": f"{len(specs)} seeded scenes: pushbutton/heavy generators, "
+                                          f"{tris:,} triangles in all, 256^2..1920x1080, 1-32 spp, depth 8",
+           "samples": samples, "scene_gen_s": gen_s, "upload_build_s": upload_build_s,
+           "per_scene": {"ms": t_scene, "msamples_per_s": samples / (t_scene * 1e-3) / 1e6},
+           "batch": res, "tune_ms_per_1spp_batch": tune_ms}
+    print(json.dumps(out))
+
+
 def main():
     args = _args()
     world, rank, local = _dist()
     if args.study == "nrc":
         if rank == 0:
             run_nrc_study(args, local)
+        return
+    if args.study == "batch":
+        if rank == 0:
+            run_batch_study(args, local)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

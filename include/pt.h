@@ -256,12 +256,22 @@ typedef struct {
 } pt_job;
 
 typedef struct {
-    uint32_t tile_pixels;       /* pixels per work item (0 = automatic) */
-    uint32_t spp_chunk;         /* samples per work item (0 = automatic) */
-    uint32_t block_size;        /* threads per block (0 = automatic) */
-    uint32_t blocks_per_sm;     /* resident blocks per SM of the persistent grid (0 = auto) */
-    uint32_t use_graph;         /* 1: capture the launch into a CUDA graph and replay it */
-    uint64_t spin_budget;       /* bounded device waits: iterations before PT_ERR_TIMEOUT */
+    uint32_t mode;              /* PT_MODE_MEGAKERNEL (or AUTO = 0): every job in ONE persistent
+                                   launch that pops (job, pixel tile) items from a shared queue;
+                                   PT_MODE_WAVEFRONT: each job rendered by the wavefront path
+                                   (graph-replayed launches), the jobs spread over `streams`
+                                   concurrent streams forked from and joined back to the
+                                   caller's stream (jobs of one scene stay on one stream) */
+    uint32_t streams;           /* wavefront mode: concurrent streams (0 = 4, at most 16) */
+    uint32_t tile_pixels;       /* megakernel: pixels per work item, a multiple of 32 (0 = 64); a
+                                   warp owns an item and traces all samples of its pixels in order */
+    uint32_t blocks_per_sm;     /* megakernel: resident blocks per SM (0 = auto) */
+    uint32_t use_graph;         /* megakernel, 1: the launch (job-table copy from a library-owned pinned
+                                   buffer, queue reset, persistent kernel) is captured once per
+                                   job count and work-item layout and replayed; the table is
+                                   rewritten before each replay, so seeds, sample indices and
+                                   cameras may change between calls.  The call then waits for the
+                                   previous graph batch to finish before rewriting the table. */
 } pt_batch_opts;
 
 /* Batched rendering of many scenes of uneven size in ONE persistent launch: blocks pop
@@ -269,6 +279,27 @@ typedef struct {
  * empty.  Each job's image equals rendering it alone with pt_render.  */
 pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const pt_batch_opts* opts,
                           void* cuda_stream);
+
+/* Autotuner of the execution schedule (beyond the paper).  Renders `frames` frames (after one
+ * warm-up frame) of `spp` samples per candidate into a scratch accumulator of camera->width x
+ * height and times them with CUDA events on the stream; candidates: wavefront with material
+ * sort off/on x tail limit (off, automatic, a quarter, four times) x wave size (2^20, 2^21,
+ * 2^22 paths), graph replay on; megakernel with 32, 64, 128 pixels per work item.  With
+ * PT_TUNE_BVH it first rebuilds the BVH with leaf sizes 1..4 (the node width is fixed at 8
+ * by the node format) and keeps the fastest.  The winner goes to *best (and ms per frame to
+ * *best_ms) and is stored in the scene: pt_render with PT_MODE_AUTO then uses it for frames
+ * of that size (not with nrc or kernel_ms).  No candidate changes the image: they render the
+ * same samples; the tuning renders do count in pt_get_stats.  Synchronises the stream.
+ * Errors: PT_ERR_NOT_BUILT, PT_ERR_INVALID_ARG, PT_ERR_OOM (scratch), PT_ERR_CUDA. */
+#define PT_TUNE_BVH 1u
+pt_status pt_autotune(pt_scene* scene, const pt_camera* camera, uint32_t spp, uint32_t max_depth,
+                      uint32_t frames, uint32_t tune_flags, pt_render_opts* best, float* best_ms,
+                      void* cuda_stream);
+/* The same for a batch: each job rendered into scratch accumulators (the jobs' own are not
+ * touched); candidates: megakernel with tile_pixels 32..256 x blocks_per_sm (automatic, 2, 4),
+ * wavefront with 1, 2, 4, 8 streams. */
+pt_status pt_autotune_batch(const pt_job* jobs, uint32_t n_jobs, uint32_t frames, pt_batch_opts* best,
+                            float* best_ms, void* cuda_stream);
 
 /* Closest hit of n rays through the scene's BVH (Sec. 5.1.3 "checks for intersections using
  * the BVH").  rays: DEVICE float[n*8] = origin[3], dir[3], tmax, unused.  Outputs (DEVICE):

@@ -150,6 +150,18 @@ class Scene:
                C.byref(accum.c), C.byref(o), _stream_handle(stream))
         return accum
 
+    def autotune(self, spp=1, max_depth=None, frames=2, bvh=False, camera=None, stream=None):
+        """pt_autotune: the fastest schedule for frames like this one (stored in the scene for
+        PT_MODE_AUTO).  Returns (options dict, ms per frame)."""
+        cam = camera or self.desc.camera
+        max_depth = self.desc.max_depth if max_depth is None else max_depth
+        best = N.pt_render_opts()
+        ms = N.f32()
+        N.call("pt_autotune", self.h, C.byref(make_camera(cam)), int(spp), int(max_depth), int(frames),
+               N.PT_TUNE_BVH if bvh else 0, C.byref(best), C.byref(ms), _stream_handle(stream))
+        keys = ("mode", "wave_paths", "sort_by_material", "block_size", "tail_paths", "use_graph")
+        return {k: int(getattr(best, k)) for k in keys}, float(ms.value)
+
     def trace(self, origins: torch.Tensor, dirs: torch.Tensor, tmax=None, any_hit=False, count=False,
               stream=None):
         n = origins.shape[0]
@@ -227,8 +239,14 @@ def uniforms(seed, keys: torch.Tensor, stream=None):
     return out
 
 
-def render_batch(jobs, tile_pixels=0, blocks_per_sm=0, stream=None):
+def render_batch(jobs, tile_pixels=0, blocks_per_sm=0, use_graph=False, mode=0, streams=0, stream=None):
     """jobs: list of (Scene, camera, spp, max_depth, seed, Accum)."""
+    arr = _job_array(jobs)
+    o = N.pt_batch_opts(mode, streams, tile_pixels, blocks_per_sm, 1 if use_graph else 0)
+    N.call("pt_render_batch", arr, len(jobs), C.byref(o), _stream_handle(stream))
+
+
+def _job_array(jobs):
     arr = (N.pt_job * len(jobs))()
     for i, (scene, cam, spp, depth, seed, acc) in enumerate(jobs):
         arr[i].scene = scene.h
@@ -237,8 +255,18 @@ def render_batch(jobs, tile_pixels=0, blocks_per_sm=0, stream=None):
         arr[i].max_depth = depth
         arr[i].seed = seed
         arr[i].accum = C.pointer(acc.c)
-    o = N.pt_batch_opts(tile_pixels, 0, 0, blocks_per_sm, 0, 0)
-    N.call("pt_render_batch", arr, len(jobs), C.byref(o), _stream_handle(stream))
+    return arr
+
+
+def autotune_batch(jobs, frames=2, stream=None):
+    """pt_autotune_batch over (Scene, camera, spp, max_depth, seed, Accum) jobs; the jobs'
+    accumulators are not touched.  Returns ({tile_pixels, blocks_per_sm}, ms per batch)."""
+    arr = _job_array(jobs)
+    best = N.pt_batch_opts()
+    ms = N.f32()
+    N.call("pt_autotune_batch", arr, len(jobs), int(frames), C.byref(best), C.byref(ms), _stream_handle(stream))
+    return {"mode": int(best.mode), "streams": int(best.streams), "tile_pixels": int(best.tile_pixels),
+            "blocks_per_sm": int(best.blocks_per_sm), "use_graph": int(best.use_graph)}, float(ms.value)
 
 
 def launch_count() -> int:

@@ -310,6 +310,7 @@ extern "C" pt_status pt_bvh_build(pt_scene* s, const pt_bvh_opts* opts, void* cu
     cudaStream_t st = (cudaStream_t)cuda_stream;
     s->last_stream = st;
     pt_status r = pt_build_bvh_impl(s, leaf, st);
+    if (r == PT_OK) s->leaf_size = leaf;
     if (r != PT_OK) return r;
     r = pt_build_env_impl(s, st);
     if (r != PT_OK) return r;

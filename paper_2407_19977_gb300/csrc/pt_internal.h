@@ -110,6 +110,11 @@ struct pt_scene {
     uint64_t wf_graph_launches = 0;
     cudaStream_t cap_stream = nullptr;
     uint64_t graph_replays = 0;
+    uint32_t leaf_size = 4;          // of the current BVH
+    // schedule chosen by pt_autotune for frames of tuned_w x tuned_h (used by PT_MODE_AUTO)
+    bool tuned = false;
+    uint32_t tuned_w = 0, tuned_h = 0;
+    pt_render_opts tuned_opts{};
 
     DScene view() const {
         DScene s;
@@ -140,6 +145,8 @@ pt_status pt_build_env_impl(pt_scene* s, cudaStream_t st);
 
 // implemented in pt_render.cu
 pt_status pt_free_wave(WaveBuffers& w);
+// paths the wavefront tail kernel holds resident (its automatic limit)
+pt_status pt_wavefront_tail_limit(int* out);
 
 // implemented in pt_nrc.cu: cache forward pass / one training step for the renderer; the
 // row count is read from device memory (n_dev), cap bounds it and sizes the launches

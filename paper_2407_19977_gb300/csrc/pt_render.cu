@@ -192,6 +192,98 @@ static pt_status launch_megakernel(const std::vector<DJob>& jobs_in, uint32_t ti
     return PT_OK;
 }
 
+// Batch as a replayed graph: {copy of the job table from a pinned host buffer, reset of the
+// queue head, persistent kernel}.  Everything that changes between calls (cameras, seeds,
+// first sample indices) is table data, so the graph depends only on the job count and the
+// work-item layout.  One cached graph per process; the pinned table is rewritten only after
+// the previous replay has finished.
+struct BatchGraph {
+    int device = -1;
+    uint32_t n_jobs = 0, total = 0, tile = 0, grid = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t done = nullptr;
+    DJob* h_jobs = nullptr;      // pinned
+    DJob* d_jobs = nullptr;
+    uint32_t* d_head = nullptr;
+    void release() {
+        if (done) cudaEventSynchronize(done);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (h_jobs) cudaFreeHost(h_jobs);
+        if (d_jobs) cudaFree(d_jobs);
+        if (d_head) cudaFree(d_head);
+        if (done) cudaEventDestroy(done);
+        if (cap) cudaStreamDestroy(cap);
+        *this = BatchGraph();
+    }
+};
+static std::mutex g_batch_mutex;
+static BatchGraph g_batch_graph;
+
+static pt_status launch_megakernel_graph(const std::vector<DJob>& jobs_in, uint32_t tile_pixels, uint32_t blocks_per_sm,
+                                         cudaStream_t st, uint64_t* launches) {
+    std::vector<DJob> jobs = jobs_in;
+    uint32_t total = 0;
+    for (auto& j : jobs) {
+        j.tile_begin = total;
+        j.n_tiles = (j.cw * j.ch + tile_pixels - 1) / tile_pixels;
+        total += j.n_tiles;
+    }
+    if (total == 0) return PT_OK;
+    const uint32_t grid = megakernel_grid(total, blocks_per_sm);
+    int dev = 0;
+    PT_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    BatchGraph& g = g_batch_graph;
+    if (!(g.exec && g.device == dev && g.n_jobs == jobs.size() && g.total == total && g.tile == tile_pixels &&
+          g.grid == grid)) {
+        g.release();
+        g.device = dev;
+        g.n_jobs = (uint32_t)jobs.size();
+        g.total = total;
+        g.tile = tile_pixels;
+        g.grid = grid;
+        const size_t bytes = jobs.size() * sizeof(DJob);
+        if (cudaMallocHost((void**)&g.h_jobs, bytes) != cudaSuccess || cudaMalloc((void**)&g.d_jobs, bytes) != cudaSuccess ||
+            cudaMalloc((void**)&g.d_head, sizeof(uint32_t)) != cudaSuccess) {
+            g.release();
+            pt_set_error("batch graph buffers: out of memory");
+            return PT_ERR_OOM;
+        }
+        PT_CUDA_TRY(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+        PT_CUDA_TRY(cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking));
+        PT_CUDA_TRY(cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal));
+        const uint64_t before = g_pt_launches.load();
+        cudaMemcpyAsync(g.d_jobs, g.h_jobs, bytes, cudaMemcpyHostToDevice, g.cap);
+        cudaMemsetAsync(g.d_head, 0, sizeof(uint32_t), g.cap);
+        PT_LAUNCH(k_megakernel, grid, 128, 0, g.cap, g.d_jobs, (uint32_t)jobs.size(), total, tile_pixels, g.d_head);
+        g_pt_launches.fetch_sub(g_pt_launches.load() - before);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(g.cap, &graph);
+        if (ce != cudaSuccess) {
+            g.release();
+            pt_set_error(std::string("batch graph capture: ") + cudaGetErrorString(ce));
+            return PT_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            g.release();
+            pt_set_error(std::string("batch graph instantiate: ") + cudaGetErrorString(ie));
+            return PT_ERR_CUDA;
+        }
+    } else {
+        // the previous replay may still read the pinned table
+        PT_CUDA_TRY(cudaEventSynchronize(g.done));
+    }
+    std::memcpy(g.h_jobs, jobs.data(), jobs.size() * sizeof(DJob));
+    PT_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+    PT_CUDA_TRY(cudaEventRecord(g.done, st));
+    pt_count_launch(1);
+    (*launches)++;
+    return PT_OK;
+}
+
 // ------------------------------------------------------------------ wavefront
 // counters: queue sizes, fetch heads, C_TAIL = 1 once the tail kernel has taken the wave's
 // remaining paths (the per-bounce kernels then have nothing to do), C_FRAME.. the values that
@@ -759,6 +851,16 @@ static pt_status ensure_nrc_buffers(WaveBuffers& w, uint32_t rec_per_path) {
 
 static int g_trace_blocks_per_sm = 0, g_shade_blocks_per_sm = 0, g_shadow_blocks_per_sm = 0, g_tail_blocks_per_sm = 0;
 
+pt_status pt_wavefront_tail_limit(int* out) {
+    if (g_tail_blocks_per_sm == 0) {
+        int b = 0;
+        PT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_tail<true, false>, 128, 0));
+        g_tail_blocks_per_sm = std::max(b, 1);
+    }
+    *out = pt_num_sms() * g_tail_blocks_per_sm * 128;
+    return PT_OK;
+}
+
 // Everything that shapes the launch sequence of a wavefront call (the per-call words, first
 // sample and seed, live in device memory): equal keys mean the same captured graph replays.
 struct WfGraphKey {
@@ -1048,8 +1150,19 @@ extern "C" pt_status pt_render(pt_scene* s, const pt_camera* camera, uint32_t sp
     cudaStream_t st = (cudaStream_t)cuda_stream;
     s->last_stream = st;
     uint32_t mode = o.mode;
-    if (mode == PT_MODE_AUTO)
-        mode = (o.nrc || (uint64_t)acc->width * acc->height >= (1u << 16)) ? PT_MODE_WAVEFRONT : PT_MODE_MEGAKERNEL;
+    if (mode == PT_MODE_AUTO) {
+        if (s->tuned && s->tuned_w == acc->width && s->tuned_h == acc->height && !o.nrc && !o.kernel_ms) {
+            // the schedule pt_autotune measured fastest for frames of this size
+            mode = s->tuned_opts.mode;
+            o.wave_paths = s->tuned_opts.wave_paths;
+            o.sort_by_material = s->tuned_opts.sort_by_material;
+            o.tail_paths = s->tuned_opts.tail_paths;
+            o.block_size = s->tuned_opts.block_size;
+            o.use_graph = s->tuned_opts.use_graph;
+        } else {
+            mode = (o.nrc || (uint64_t)acc->width * acc->height >= (1u << 16)) ? PT_MODE_WAVEFRONT : PT_MODE_MEGAKERNEL;
+        }
+    }
     pt_status r;
     if (mode == PT_MODE_WAVEFRONT) {
         r = render_wavefront(s, *camera, spp, max_depth, seed, acc, o, st);
@@ -1059,6 +1172,74 @@ extern "C" pt_status pt_render(pt_scene* s, const pt_camera* camera, uint32_t sp
                                            o.sample_out), tile, 0, st, s->d_head, &s->launches);
     }
     if (r == PT_OK) acc->spp_done += spp;
+    return r;
+}
+
+// Streams of the wavefront batch, per device: created on first use, kept for the process.
+struct BatchStreams {
+    cudaStream_t s[16] = {};
+    cudaEvent_t fork = nullptr, join[16] = {};
+};
+static std::mutex g_bstream_mutex;
+static BatchStreams g_bstreams[64];
+
+static pt_status batch_streams(int dev, BatchStreams** out) {
+    PT_CHECK_ARG(dev >= 0 && dev < 64, "device index");
+    std::lock_guard<std::mutex> lock(g_bstream_mutex);
+    BatchStreams& b = g_bstreams[dev];
+    if (!b.fork) {
+        PT_CUDA_TRY(cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming));
+        for (int k = 0; k < 16; ++k) {
+            PT_CUDA_TRY(cudaStreamCreateWithFlags(&b.s[k], cudaStreamNonBlocking));
+            PT_CUDA_TRY(cudaEventCreateWithFlags(&b.join[k], cudaEventDisableTiming));
+        }
+    }
+    *out = &b;
+    return PT_OK;
+}
+
+// Wavefront batch: each job through pt_render (wavefront, graph replay) on one of K streams
+// forked from the caller's stream; jobs go, largest first, to the least-loaded stream, except
+// that all jobs of a scene share a stream (they share its wave buffers).
+static pt_status batch_wavefront(const pt_job* jobs, uint32_t n_jobs, uint32_t K, cudaStream_t st) {
+    int dev = 0;
+    PT_CUDA_TRY(cudaGetDevice(&dev));
+    BatchStreams* B = nullptr;
+    pt_status r = batch_streams(dev, &B);
+    if (r != PT_OK) return r;
+    PT_CUDA_TRY(cudaEventRecord(B->fork, st));
+    for (uint32_t k = 0; k < K; ++k) PT_CUDA_TRY(cudaStreamWaitEvent(B->s[k], B->fork, 0));
+    std::vector<uint32_t> order(n_jobs);
+    for (uint32_t i = 0; i < n_jobs; ++i) order[i] = i;
+    auto work = [&](uint32_t i) {
+        return (double)jobs[i].camera.width * jobs[i].camera.height * std::max(jobs[i].spp, 1u) * (jobs[i].max_depth + 1);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return work(a) > work(b); });
+    std::vector<double> load(K, 0.0);
+    std::vector<std::pair<const pt_scene*, uint32_t>> placed;
+    pt_render_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.mode = PT_MODE_WAVEFRONT;
+    o.sort_by_material = -1;
+    o.use_graph = 1;
+    for (uint32_t i : order) {
+        const pt_job& j = jobs[i];
+        uint32_t k = K;
+        for (auto& pl : placed)
+            if (pl.first == j.scene) k = pl.second;
+        if (k == K) {
+            k = (uint32_t)(std::min_element(load.begin(), load.end()) - load.begin());
+            placed.push_back({j.scene, k});
+        }
+        load[k] += work(i);
+        r = pt_render(j.scene, &j.camera, j.spp, j.max_depth, j.seed, j.accum, &o, B->s[k]);
+        if (r != PT_OK) break;
+    }
+    for (uint32_t k = 0; k < K; ++k) {
+        cudaEventRecord(B->join[k], B->s[k]);
+        cudaStreamWaitEvent(st, B->join[k], 0);
+    }
+    for (uint32_t i = 0; i < n_jobs; ++i) jobs[i].scene->last_stream = st;
     return r;
 }
 
@@ -1083,20 +1264,30 @@ extern "C" pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const 
         dj.push_back(make_job(j.scene, j.camera, 0, 0, j.accum, j.spp, j.max_depth, j.seed, 0, nullptr));
         j.scene->last_stream = st;
     }
-    // per-call device job table and queue head, released once the stream has drained
-    DJob* d_jobs = nullptr;
-    uint32_t* d_head = nullptr;
-    PT_CUDA_TRY(cudaMalloc(&d_jobs, dj.size() * sizeof(DJob)));
-    if (cudaMalloc(&d_head, sizeof(uint32_t)) != cudaSuccess) {
-        cudaFree(d_jobs);
-        pt_set_error("batch queue head: out of memory");
-        return PT_ERR_OOM;
+    PT_CHECK_ARG(bo.mode == PT_MODE_AUTO || bo.mode == PT_MODE_WAVEFRONT || bo.mode == PT_MODE_MEGAKERNEL, "unknown mode");
+    if (bo.mode == PT_MODE_WAVEFRONT) {
+        const uint32_t K = std::min(bo.streams ? bo.streams : 4u, 16u);
+        return batch_wavefront(jobs, n_jobs, K, st);
     }
     uint64_t launches = 0;
-    const pt_status r = launch_megakernel(dj, tile, bo.blocks_per_sm, st, d_head, d_jobs, &launches);
-    cudaStreamSynchronize(st);
-    cudaFree(d_jobs);
-    cudaFree(d_head);
+    pt_status r;
+    if (bo.use_graph) {
+        r = launch_megakernel_graph(dj, tile, bo.blocks_per_sm, st, &launches);
+    } else {
+        // per-call device job table and queue head from the stream-ordered allocator:
+        // allocated, used and released in stream order, so the call does not wait for the GPU
+        DJob* d_jobs = nullptr;
+        uint32_t* d_head = nullptr;
+        PT_CUDA_TRY(cudaMallocAsync((void**)&d_jobs, dj.size() * sizeof(DJob), st));
+        if (cudaMallocAsync((void**)&d_head, sizeof(uint32_t), st) != cudaSuccess) {
+            cudaFreeAsync(d_jobs, st);
+            pt_set_error("batch queue head: out of memory");
+            return PT_ERR_OOM;
+        }
+        r = launch_megakernel(dj, tile, bo.blocks_per_sm, st, d_head, d_jobs, &launches);
+        cudaFreeAsync(d_jobs, st);
+        cudaFreeAsync(d_head, st);
+    }
     if (r != PT_OK) return r;
     for (uint32_t i = 0; i < n_jobs; ++i) jobs[i].accum->spp_done += jobs[i].spp;
     jobs[0].scene->launches += launches;

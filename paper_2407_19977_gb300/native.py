@@ -68,8 +68,7 @@ class pt_job(C.Structure):
 
 
 class pt_batch_opts(C.Structure):
-    _fields_ = [("tile_pixels", u32), ("spp_chunk", u32), ("block_size", u32), ("blocks_per_sm", u32),
-                ("use_graph", u32), ("spin_budget", u64)]
+    _fields_ = [("mode", u32), ("streams", u32), ("tile_pixels", u32), ("blocks_per_sm", u32), ("use_graph", u32)]
 
 
 class pt_nrc_opts(C.Structure):
@@ -84,6 +83,7 @@ STATUS = ["PT_OK", "PT_ERR_INVALID_ARG", "PT_ERR_OOM", "PT_ERR_CUDA", "PT_ERR_NO
 PT_FLAG_NO_NEE = 1
 PT_FLAG_NO_RR = 2
 PT_FLAG_COUNT = 4
+PT_TUNE_BVH = 1
 PT_TONEMAP_SRGB = 1
 KERNEL_KINDS = ("raygen", "trace", "sort", "shade", "shadow", "accum", "tail")
 PT_MODE_AUTO, PT_MODE_WAVEFRONT, PT_MODE_MEGAKERNEL = 0, 1, 2
@@ -99,6 +99,9 @@ SIGNATURES = {
                                     C.POINTER(pt_render_opts), vp]),
     "pt_render_batch": (C.c_int, [C.POINTER(pt_job), u32, C.POINTER(pt_batch_opts), vp]),
     "pt_tonemap": (C.c_int, [C.POINTER(pt_accum), f32, u32, vp, vp]),
+    "pt_autotune": (C.c_int, [vp, C.POINTER(pt_camera), u32, u32, u32, u32, C.POINTER(pt_render_opts),
+                              C.POINTER(f32), vp]),
+    "pt_autotune_batch": (C.c_int, [C.POINTER(pt_job), u32, u32, C.POINTER(pt_batch_opts), C.POINTER(f32), vp]),
     "pt_trace": (C.c_int, [vp, vp, u32, C.c_int, vp, vp, vp, vp]),
     "pt_bsdf_eval": (C.c_int, [vp, vp, vp, vp, u32, vp, vp, vp]),
     "pt_bsdf_sample": (C.c_int, [vp, vp, vp, vp, u32, vp, vp, vp, vp, vp]),

@@ -532,6 +532,102 @@ def test_batch_matches_individual_renders(api):
         assert torch.allclose(acc.sum, one.sum, rtol=1e-6, atol=1e-7)
 
 
+def _batch_scenes():
+    from paper_2407_19977_gb300 import api as A
+    mk = [scenes.cornell_box(width=40, height=24), scenes.pushbutton_lod(3000, width=64, height=48, seed=3),
+          scenes.heavy_scene(level=2, n_instances=3, width=50, height=30, seed=4)]
+    return mk, [A.Scene(s) for s in mk]
+
+
+def test_batch_graph_replay_equals_direct_batches(api):
+    """The replayed batch graph renders what direct batch launches render, call after call
+    (the job table with the new first-sample indices is rewritten before each replay)."""
+    from paper_2407_19977_gb300 import api as A
+    mk, gs = _batch_scenes()
+    out = []
+    for graph in (False, True):
+        accs = [A.Accum(s.camera.width, s.camera.height) for s in mk]
+        for call in range(3):
+            jobs = [(g, s.camera, 2 + i, 5, 100 + i + call, a) for i, (s, g, a) in enumerate(zip(mk, gs, accs))]
+            A.render_batch(jobs, use_graph=graph)
+        # a different job count recaptures
+        A.render_batch(jobs[:2], use_graph=graph)
+        torch.cuda.synchronize()
+        out.append([(a.sum.clone(), a.spp_done) for a in accs])
+    for (s0, n0), (s1, n1) in zip(*out):
+        assert n0 == n1 and torch.equal(s0, s1)
+
+
+def test_batch_wavefront_streams_equal_single_renders(api):
+    """Wavefront batch: every job rendered by the wavefront path on one of several streams;
+    each image equals the job rendered alone, two jobs of one scene included."""
+    from paper_2407_19977_gb300 import api as A
+    from paper_2407_19977_gb300 import native as N
+    mk, gs = _batch_scenes()
+    mk, gs = mk + [mk[1]], gs + [gs[1]]
+    accs = [A.Accum(s.camera.width, s.camera.height) for s in mk]
+    jobs = [(g, s.camera, 2 + i, 5, 200 + i, a) for i, (s, g, a) in enumerate(zip(mk, gs, accs))]
+    A.render_batch(jobs, mode=N.PT_MODE_WAVEFRONT, streams=3)
+    A.render_batch(jobs, mode=N.PT_MODE_WAVEFRONT, streams=3)
+    torch.cuda.synchronize()
+    for (g, cam, spp, d, seed, acc) in jobs:
+        one = A.Accum(cam.width, cam.height)
+        g.render(spp, max_depth=d, seed=seed, accum=one, mode=N.PT_MODE_WAVEFRONT)
+        g.render(spp, max_depth=d, seed=seed, accum=one, mode=N.PT_MODE_WAVEFRONT)
+        torch.cuda.synchronize()
+        assert acc.spp_done == one.spp_done == 2 * spp
+        assert torch.equal(acc.sum, one.sum)
+
+
+def test_autotune_batch_leaves_jobs_untouched(api):
+    from paper_2407_19977_gb300 import api as A
+    mk, gs = _batch_scenes()
+    accs = [A.Accum(s.camera.width, s.camera.height) for s in mk]
+    jobs = [(g, s.camera, 2, 5, 7, a) for s, g, a in zip(mk, gs, accs)]
+    best, ms = A.autotune_batch(jobs, frames=1)
+    torch.cuda.synchronize()
+    assert ms > 0
+    assert best["tile_pixels"] in (32, 64, 128, 256) or best["streams"] in (1, 2, 4, 8)
+    assert all(a.spp_done == 0 and float(a.sum.abs().sum()) == 0.0 for a in accs)
+
+
+def test_bvh_leaf_size_does_not_change_samples(api):
+    """Closest hits (equal t -> lower id) and any-hits do not depend on the tree: every leaf
+    size gives bit-identical samples."""
+    from paper_2407_19977_gb300 import api as A
+    from paper_2407_19977_gb300 import native as N
+    sc = scenes.pushbutton_lod(20000, width=96, height=64, seed=2)
+    g = A.Scene(sc, build=False)
+    ref = None
+    for leaf in (4, 1, 2, 3):
+        g.build(leaf_size=leaf)
+        smp = torch.zeros((64, 96, 2, 3), dtype=torch.float32, device="cuda")
+        g.render(2, accum=A.Accum(96, 64), mode=N.PT_MODE_WAVEFRONT, sample_out=smp, seed=3)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = smp.clone()
+        assert torch.equal(smp, ref), leaf
+
+
+def test_autotune_and_auto_mode(api):
+    """pt_autotune picks a schedule (BVH leaf size included); PT_MODE_AUTO then renders with
+    it, and the image is what the explicit schedule renders and what the oracle renders."""
+    from paper_2407_19977_gb300 import api as A
+    from paper_2407_19977_gb300 import native as N
+    sc = scenes.cornell_box()
+    g = A.Scene(sc)
+    osc = oracle.OracleScene(sc)
+    best, ms = g.autotune(spp=4, frames=1, bvh=True)
+    assert best["mode"] in (N.PT_MODE_WAVEFRONT, N.PT_MODE_MEGAKERNEL) and ms > 0
+    a = g.render(sc.spp, mode=N.PT_MODE_AUTO, seed=4)
+    b = g.render(sc.spp, mode=best["mode"], wave_paths=best["wave_paths"], sort=best["sort_by_material"],
+                 block_size=best["block_size"], tail_paths=best["tail_paths"], use_graph=bool(best["use_graph"]), seed=4)
+    torch.cuda.synchronize()
+    assert torch.equal(a.sum, b.sum)
+    o_sum, _, _ = osc.render(spp=sc.spp, seed=4)
+    _image_check(a.image().cpu().numpy(), o_sum / sc.spp, "cornell after autotune")
+
+
 # ------------------------------------------------------------------ edge cases and errors
 
 def test_edge_cases(api):

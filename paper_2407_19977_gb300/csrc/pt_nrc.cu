@@ -151,9 +151,10 @@ __global__ void k_grid_backward(GridDesc G, const float* __restrict__ samples, R
 
 // ---- fused MLP forward: one warp per 16 rows, weights in padded shared memory ----
 __device__ __forceinline__ void load_weights_smem(__half* sw, const __half* __restrict__ Wg) {
-    for (int i = threadIdx.x; i < (N_HIDDEN * W + OUT_PAD) * W; i += blockDim.x) {
-        const int r = i / W, c = i % W;
-        sw[r * SROW + c] = Wg[i];
+    // 16-byte chunks: 8 per 64-wide row
+    for (int i = threadIdx.x; i < (N_HIDDEN * W + OUT_PAD) * (W / 8); i += blockDim.x) {
+        const int r = i / (W / 8), c = 8 * (i % (W / 8));
+        *reinterpret_cast<uint4*>(sw + r * SROW + c) = *reinterpret_cast<const uint4*>(Wg + (size_t)r * W + c);
     }
 }
 
@@ -235,6 +236,94 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const __half* __restrict__ 
         float out[2][4];
         layer_fwd<2>(out, a, sw + N_HIDDEN * W * SROW, g, t);
         // output columns 0..2 live in n-tile 0: lane t holds columns 2t, 2t+1
+        const uint32_t ra = r0 + g, rb = r0 + g + 8;
+        if (t < 2) {
+            if (ra < n) { Y[4 * ra + 2 * t] = out[0][0]; Y[4 * ra + 2 * t + 1] = out[0][1]; }
+            if (rb < n) { Y[4 * rb + 2 * t] = out[0][2]; Y[4 * rb + 2 * t + 1] = out[0][3]; }
+        }
+    }
+}
+
+// ldmatrix without transpose: lane i names row i%8 of tile i/8; each lane receives, per tile,
+// two consecutive columns of one row (the mma A-fragment layout)
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __half* p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// Fused cache inference: encoding and MLP of 16 queries per warp, the 64-wide input built in
+// a shared-memory tile (never written to HBM).  Lane j encodes level j % 16 of queries
+// 2r + j / 16 (r = 0..7): its level's resolution and table stay in registers and it issues
+// its 64 corner gathers back to back.  The tile then feeds the same tensor-core layers as
+// k_mlp_forward, with the A fragments read by ldmatrix.
+__global__ void __launch_bounds__(128) k_nrc_infer(GridDesc G, const float* __restrict__ queries, RowCount rc,
+                                                   const __half* __restrict__ Wg, float* __restrict__ Y) {
+    __shared__ __align__(16) __half sw[(N_HIDDEN * W + OUT_PAD) * SROW];
+    __shared__ __align__(16) __half sx[4][16 * SROW];
+    load_weights_smem(sw, Wg);
+    __syncthreads();
+    const uint32_t n = rc.get();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    __half* X = sx[warp];
+    const uint32_t l = lane & 15;
+    const bool grid_lane = l < G.L;
+    const uint32_t res = grid_lane ? G.res[l] : 1u;
+    const __half2* tab = reinterpret_cast<const __half2*>(G.table) + (size_t)l * G.T;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < n; tile += warps) {
+        const uint32_t r0 = tile * 16;
+        // grid features: columns 2l, 2l + 1 of rows 2r + lane / 16
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const uint32_t row = 2 * r + (lane >> 4);
+            const uint32_t q = r0 + row;
+            float f0 = 0.0f, f1 = 0.0f;
+            if (grid_lane && q < n) {
+                const float3 p = pos01(G, queries + (size_t)QSTRIDE * q);
+                const float fx = p.x * res, fy = p.y * res, fz = p.z * res;
+                const uint32_t cx = min((uint32_t)fx, res - 1), cy = min((uint32_t)fy, res - 1), cz = min((uint32_t)fz, res - 1);
+                const float rx = fx - cx, ry = fy - cy, rz = fz - cz;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const uint32_t ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+                    const float w = (ox ? rx : 1.0f - rx) * (oy ? ry : 1.0f - ry) * (oz ? rz : 1.0f - rz);
+                    const float2 v = __half22float2(tab[corner_index(cx + ox, cy + oy, cz + oz, res, G.T)]);
+                    f0 += w * v.x;
+                    f1 += w * v.y;
+                }
+            }
+            if (grid_lane) *reinterpret_cast<__half2*>(X + row * SROW + 2 * l) = __floats2half2_rn(f0, f1);
+        }
+        // the other 64 - 2L columns: direction, normal, roughness, a constant 1, zeros
+        for (uint32_t e = lane; e < 16u * (W - 2 * G.L); e += 32) {
+            const uint32_t row = e / (W - 2 * G.L), k = e % (W - 2 * G.L);
+            const uint32_t q = r0 + row;
+            float v = 0.0f;
+            if (q < n) {
+                const float* rec = queries + (size_t)QSTRIDE * q;
+                if (k < 3) v = rec[3 + k];
+                else if (k < 6) v = rec[6 + (k - 3)];
+                else if (k == 6) v = rec[9];
+                else if (k == 7) v = 1.0f;
+            }
+            X[row * SROW + 2 * G.L + k] = __float2half_rn(v);
+        }
+        __syncwarp();
+        uint32_t a[4][4];
+        const int j4 = lane >> 3, r8 = lane & 7;
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) ldsm_x4(a[kt], X + (r8 + ((j4 & 1) << 3)) * SROW + 16 * kt + ((j4 >> 1) << 3));
+        __syncwarp();
+#pragma unroll
+        for (int ly = 0; ly < N_HIDDEN; ++ly) {
+            float acc[8][4];
+            layer_fwd<8>(acc, a, sw + ly * W * SROW, g, t);
+            relu_to_a(a, acc);
+        }
+        float out[2][4];
+        layer_fwd<2>(out, a, sw + N_HIDDEN * W * SROW, g, t);
         const uint32_t ra = r0 + g, rb = r0 + g + 8;
         if (t < 2) {
             if (ra < n) { Y[4 * ra + 2 * t] = out[0][0]; Y[4 * ra + 2 * t + 1] = out[0][1]; }
@@ -467,7 +556,18 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ grad, float* _
 }
 
 // lazy Adam for the grid table: an entry whose gradient is exactly zero keeps its value and
-// moments; the scan reads the gradient four entries at a time and skips zero groups
+// moments.  Four entries per thread: the gradient group is read first, and a group with any
+// non-zero entry moves its parameters and moments as float4 (untouched lanes write back what
+// they read)
+__device__ __forceinline__ float adam_lane(float gr, float& pm, float& mm, float& vm, float lr, float b1, float b2,
+                                           float eps, float c1, float c2) {
+    if (gr == 0.0f) return pm;
+    mm = b1 * mm + (1.0f - b1) * gr;
+    vm = b2 * vm + (1.0f - b2) * gr * gr;
+    pm = pm - lr * (mm / c1) / (sqrtf(vm / c2) + eps);
+    return pm;
+}
+
 __global__ void k_adam_lazy(float* __restrict__ p, float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
                             __half* __restrict__ copy, uint64_t n4, float lr, float b1, float b2, float eps, float c1,
                             float c2, RowCount rc) {
@@ -475,20 +575,21 @@ __global__ void k_adam_lazy(float* __restrict__ p, float* __restrict__ grad, flo
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4; i += (uint64_t)gridDim.x * blockDim.x) {
         const float4 g4 = reinterpret_cast<const float4*>(grad)[i];
         if (g4.x == 0.0f && g4.y == 0.0f && g4.z == 0.0f && g4.w == 0.0f) continue;
-        const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float gr = gv[c];
-            if (gr == 0.0f) continue;
-            const uint64_t e = 4 * i + c;
-            const float mi = b1 * m[e] + (1.0f - b1) * gr;
-            const float vi = b2 * v[e] + (1.0f - b2) * gr * gr;
-            m[e] = mi;
-            v[e] = vi;
-            const float np = p[e] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-            p[e] = np;
-            copy[e] = __float2half_rn(np);
-        }
+        float4 p4 = reinterpret_cast<const float4*>(p)[i];
+        float4 m4 = reinterpret_cast<const float4*>(m)[i];
+        float4 v4 = reinterpret_cast<const float4*>(v)[i];
+        adam_lane(g4.x, p4.x, m4.x, v4.x, lr, b1, b2, eps, c1, c2);
+        adam_lane(g4.y, p4.y, m4.y, v4.y, lr, b1, b2, eps, c1, c2);
+        adam_lane(g4.z, p4.z, m4.z, v4.z, lr, b1, b2, eps, c1, c2);
+        adam_lane(g4.w, p4.w, m4.w, v4.w, lr, b1, b2, eps, c1, c2);
+        reinterpret_cast<float4*>(p)[i] = p4;
+        reinterpret_cast<float4*>(m)[i] = m4;
+        reinterpret_cast<float4*>(v)[i] = v4;
+        const __half2 h01 = __floats2half2_rn(p4.x, p4.y), h23 = __floats2half2_rn(p4.z, p4.w);
+        uint2 hv;
+        hv.x = *reinterpret_cast<const uint32_t*>(&h01);
+        hv.y = *reinterpret_cast<const uint32_t*>(&h23);
+        reinterpret_cast<uint2*>(copy)[i] = hv;
         reinterpret_cast<float4*>(grad)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
 }
@@ -657,8 +758,24 @@ static uint32_t encode_grid(uint32_t cap, uint32_t L) {
 }
 
 // forward (+ optional activations) of rc rows already resident on the device
+static int g_infer_blocks = 0;
+
 static pt_status nrc_forward(pt_nrc* N, const float* q, RowCount rc, __half* X, float* Y, __half* acts, cudaStream_t st) {
     const GridDesc G = grid_desc(N);
+    if (!acts) {
+        // inference: encoding and MLP in one kernel, persistent over 16-row tiles
+        if (g_infer_blocks == 0) {
+            int b = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_nrc_infer, 128, 0);
+            g_infer_blocks = std::max(b, 1) * pt_num_sms();
+        }
+        const uint32_t tiles = (rc.n + 15) / 16;
+        const uint32_t blocks = std::max(1u, std::min((uint32_t)g_infer_blocks, (tiles + 3) / 4));
+        PT_LAUNCH(k_nrc_infer, blocks, 128, 0, st, G, q, rc, N->d_wh, Y);
+        N->launches += 1;
+        PT_CUDA_TRY(cudaGetLastError());
+        return PT_OK;
+    }
     PT_LAUNCH(k_encode, encode_grid(rc.n, N->L), 256, 0, st, G, q, rc, X);
     PT_LAUNCH(k_mlp_forward, mlp_grid(rc.n), 128, 0, st, X, rc, N->d_wh, Y, acts);
     N->launches += 2;

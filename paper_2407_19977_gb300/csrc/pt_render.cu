@@ -405,7 +405,14 @@ struct NrcHook {
             const uint32_t cnt = min((aux & 0xffu) + 1u, 255u);
             aux = (aux & ~0xffu) | cnt;
             if (cnt == 2u && !slot1) {
-                const uint32_t q = atomicAdd(&P->nrc_counters[0], 1u);
+                // warp-aggregated append: the lanes that reach this point take consecutive slots
+                const uint32_t active = __activemask();
+                const uint32_t lane = threadIdx.x & 31u;
+                const int leader = __ffs(active) - 1;
+                uint32_t q0 = 0;
+                if ((int)lane == leader) q0 = atomicAdd(&P->nrc_counters[0], (uint32_t)__popc(active));
+                q0 = __shfl_sync(active, q0, leader);
+                const uint32_t q = q0 + __popc(active & ((1u << lane) - 1u));
                 float4* rec = reinterpret_cast<float4*>(P->nrc_q + (size_t)q * 16);
                 rec[0] = make_float4(x.x, x.y, x.z, wo.x);
                 rec[1] = make_float4(wo.y, wo.z, n.x, n.y);

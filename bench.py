@@ -61,6 +61,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pushbutton", choices=sorted(WORKLOADS))
+    ap.add_argument("--tune", type=int, default=1,
+                    help="run pt_autotune (untimed) before the timed region and render in PT_MODE_AUTO")
     ap.add_argument("--graph", type=int, default=1, help="replay each frame's wavefront launches as a CUDA graph")
     ap.add_argument("--mode", default="wavefront", choices=["auto", "wavefront", "megakernel"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -275,6 +277,12 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     bvh_ms = ev0.elapsed_time(ev1)
     mode = {"auto": N.PT_MODE_AUTO, "wavefront": N.PT_MODE_WAVEFRONT, "megakernel": N.PT_MODE_MEGAKERNEL}[args.mode]
+    tuned = None
+    if args.tune:
+        # untimed: the schedule (wavefront/megakernel, tail limit, sort, wave size) that renders
+        # this frame fastest; PT_MODE_AUTO then uses it
+        tuned, tuned_ms = scene.autotune(spp=1, frames=2)
+        mode = N.PT_MODE_AUTO
     acc = api.Accum(W, H)
     seed = 1000 * rank
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
@@ -366,8 +374,10 @@ def run_ours(args, world, rank, local):
         "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "mode": args.mode, "l2": "flushed between steps",
-                   "parallelism": f"replicas x{world}", "cuda_graph": bool(args.graph)},
+        "config": {"workload": WORKLOADS[args.workload], "mode": "auto (autotuned)" if tuned else args.mode,
+                   "l2": "flushed between steps",
+                   "parallelism": f"replicas x{world}", "cuda_graph": bool(args.graph),
+                   "schedule": ({"autotuned": tuned} if tuned else {"mode": args.mode})},
         "spp_per_s_1080p": spp_s,
         "rays_per_step": rays / args.steps,
         "bvh_build_ms": bvh_ms, "upload_ms": upload_ms,

@@ -288,7 +288,7 @@ pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const pt_batch_op
  * PT_TUNE_BVH it first rebuilds the BVH with leaf sizes 1..4 (the node width is fixed at 8
  * by the node format) and keeps the fastest.  The winner goes to *best (and ms per frame to
  * *best_ms) and is stored in the scene: pt_render with PT_MODE_AUTO then uses it for frames
- * of that size (not with nrc or kernel_ms).  No candidate changes the image: they render the
+ * of that size (not with nrc; with kernel_ms the launches are direct, not replayed).  No candidate changes the image: they render the
  * same samples; the tuning renders do count in pt_get_stats.  Synchronises the stream.
  * Errors: PT_ERR_NOT_BUILT, PT_ERR_INVALID_ARG, PT_ERR_OOM (scratch), PT_ERR_CUDA. */
 #define PT_TUNE_BVH 1u

@@ -1158,7 +1158,7 @@ extern "C" pt_status pt_render(pt_scene* s, const pt_camera* camera, uint32_t sp
     s->last_stream = st;
     uint32_t mode = o.mode;
     if (mode == PT_MODE_AUTO) {
-        if (s->tuned && s->tuned_w == acc->width && s->tuned_h == acc->height && !o.nrc && !o.kernel_ms) {
+        if (s->tuned && s->tuned_w == acc->width && s->tuned_h == acc->height && !o.nrc) {
             // the schedule pt_autotune measured fastest for frames of this size
             mode = s->tuned_opts.mode;
             o.wave_paths = s->tuned_opts.wave_paths;

@@ -90,6 +90,21 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def combine_replicas(dev_ms: float, rays: float, device=None):
+    """Whole-job figures of N independent replicas (one per GPU, each rendering its own frames
+    with its own seed): the slowest rank's timed milliseconds and the rays of all ranks.
+    Without an initialised process group (or with one rank) the local figures are returned."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return dev_ms, rays
+    t = torch.tensor([dev_ms], dtype=torch.float64, device=device)
+    r = torch.tensor([rays], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(r, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(r.item())
+
+
 def _metric_name(workload: str) -> str:
     """The headline metric is quoted on the pushbutton frame; other workloads name themselves."""
     return "Mrays/s at 1080p (pushbutton)" if workload == "pushbutton" else f"Mrays/s ({workload})"
@@ -332,14 +347,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     rays = (st_after["ext_rays"] - st_before["ext_rays"]) + (st_after["shadow_rays"] - st_before["shadow_rays"])
-    t_max = dev_ms
-    rays_all = rays
-    if world > 1:
-        tt = torch.tensor([dev_ms, float(rays)], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_max, rays_all = float(mx[0]), float(tt[1])
+    t_max, rays_all = combine_replicas(dev_ms, float(rays), dev if world > 1 else None)
     value = rays_all / (t_max * 1e-3) / 1e6
     spp_s = world * args.steps / (t_max * 1e-3)
     # end to end through the public API: the step's inputs cross host->device (the camera and

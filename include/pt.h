@@ -385,11 +385,13 @@ typedef struct {
     float per_level_scale;      /* resolution growth per level (0 = from 2048 finest) */
     uint32_t n_hidden;          /* hidden layers (4) */
     float learning_rate;        /* Adam step size (1e-2 grid and MLP) */
-    uint32_t batch;             /* training samples per Adam step (16384); a rendered frame
+    uint32_t batch;             /* training samples per Adam step (8192); a rendered frame
                                    with nrc_train takes one step per batch of its samples */
     uint64_t seed;              /* weight initialisation seed */
     float scene_min[3];         /* position normalisation box */
     float scene_max[3];
+    uint32_t frame_samples;     /* training samples a rendered frame collects (32768), from
+                                   frame_samples / 2 training paths */
 } pt_nrc_opts;
 
 /* Query layout for pt_nrc_infer / training samples (DEVICE arrays of float[n*16]):

@@ -152,6 +152,7 @@ pt_status pt_wavefront_tail_limit(int* out);
 // row count is read from device memory (n_dev), cap bounds it and sizes the launches
 pt_status pt_nrc_render_infer_dev(pt_nrc* N, const float* queries, const uint32_t* n_dev, uint32_t cap, float* out4,
                                   cudaStream_t st);
+uint32_t pt_nrc_frame_samples(const pt_nrc* N);
 pt_status pt_nrc_render_train_dev(pt_nrc* N, const float* samples, const uint32_t* n_dev, uint32_t cap, cudaStream_t st);
 
 inline DCam to_dcam(const pt_camera& c) {

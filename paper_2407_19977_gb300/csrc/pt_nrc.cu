@@ -688,7 +688,9 @@ extern "C" pt_status pt_nrc_create(const pt_nrc_opts* opts, void* cuda_stream, p
     if (!o.base_resolution) o.base_resolution = 16;
     if (!o.n_hidden) o.n_hidden = N_HIDDEN;
     if (o.learning_rate <= 0.0f) o.learning_rate = 1e-2f;
-    if (!o.batch) o.batch = 1u << 14;
+    if (!o.batch) o.batch = 1u << 13;
+    if (!o.frame_samples) o.frame_samples = 1u << 15;
+    PT_CHECK_ARG(o.frame_samples >= 2 && o.frame_samples <= (1u << 22), "frame_samples must be 2..2^22");
     PT_CHECK_ARG(o.n_hidden == N_HIDDEN, "n_hidden must be 4");
     PT_CHECK_ARG(o.n_levels >= 1 && o.n_levels <= 16, "n_levels must be 1..16 (2 features each fill 32 inputs)");
     PT_CHECK_ARG(o.log2_table >= 8 && o.log2_table <= 24, "log2_table must be 8..24");
@@ -819,7 +821,10 @@ static pt_status nrc_adam(pt_nrc* N, RowCount rc, cudaStream_t st) {
     const float lr = N->o.learning_rate;
     PT_LAUNCH(k_adam, 2 * pt_num_sms(), 256, 0, st, N->d_w, N->d_wg, N->d_wm, N->d_wv, N->d_wh, (uint64_t)N_WEIGHTS, lr,
               b1, b2, eps, c1, c2, rc);
-    PT_LAUNCH(k_adam_lazy, 8 * pt_num_sms(), 256, 0, st, N->d_grid, N->d_gg, N->d_gm, N->d_gv, N->d_gh, N->n_grid / 4,
+    // one thread per float4 group: every group's loads are in flight at once
+    const uint64_t groups = N->n_grid / 4;
+    const uint32_t ablocks = (uint32_t)std::min<uint64_t>((groups + 255) / 256, 1u << 20);
+    PT_LAUNCH(k_adam_lazy, ablocks, 256, 0, st, N->d_grid, N->d_gg, N->d_gm, N->d_gv, N->d_gh, groups,
               lr, b1, b2, eps, c1, c2, rc);
     N->launches += 2;
     PT_CUDA_TRY(cudaGetLastError());
@@ -907,6 +912,8 @@ pt_status pt_nrc_render_infer_dev(pt_nrc* N, const float* queries, const uint32_
     }
     return nrc_forward(N, queries, RowCount{cap, n_dev, 0}, N->iX, out4, nullptr, st);
 }
+
+uint32_t pt_nrc_frame_samples(const pt_nrc* N) { return N->o.frame_samples; }
 
 // one Adam step per `batch` samples of the frame's training list (its length is on the device;
 // a batch past the end of the list is no step)

@@ -835,9 +835,10 @@ static pt_status ensure_wave(WaveBuffers& w, uint32_t capacity) {
 }
 
 // radiance-cache buffers: queries (one per path at most), training records and samples
-static pt_status ensure_nrc_buffers(WaveBuffers& w, uint32_t rec_per_path) {
-    const uint32_t cap = w.capacity, slots = 32768, samples = 65536;
-    if (w.nrc_capacity >= cap && w.rec_per_path >= rec_per_path) return PT_OK;
+// (`samples` per frame, collected from samples / 2 training paths)
+static pt_status ensure_nrc_buffers(WaveBuffers& w, uint32_t rec_per_path, uint32_t samples) {
+    const uint32_t cap = w.capacity, slots = std::max(samples / 2, 1u);
+    if (w.nrc_capacity >= cap && w.rec_per_path >= rec_per_path && w.sample_cap == samples) return PT_OK;
     void* ps[] = {w.aux, w.nrc_q, w.nrc_out, w.nrc_counters, w.train_rec, w.train_nv, w.train_id, w.train_samples};
     for (void* q : ps)
         if (q) cudaFree(q);
@@ -926,7 +927,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     P.sum = acc->sum; P.comp = acc->comp; P.sample_out = o.sample_out;
     P.stats = s->d_stats;
     if (o.nrc) {
-        r = ensure_nrc_buffers(w, std::min(max_depth + 1, 16u));
+        r = ensure_nrc_buffers(w, std::min(max_depth + 1, 16u), pt_nrc_frame_samples(o.nrc));
         if (r != PT_OK) return r;
         P.nrc_on = 1;
         P.rec_per_path = w.rec_per_path;

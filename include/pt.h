@@ -392,6 +392,10 @@ typedef struct {
     float scene_max[3];
     uint32_t frame_samples;     /* training samples a rendered frame collects (32768), from
                                    frame_samples / 2 training paths */
+    uint32_t tcgen05;           /* 1: inference MLP on the tcgen05 tensor cores (128-row tiles,
+                                   accumulators in tensor memory); 0: on mma.sync, 16-row tiles
+                                   per warp, which measures faster here because inference is
+                                   bound by the hash-grid gathers, not by the MLP */
 } pt_nrc_opts;
 
 /* Query layout for pt_nrc_infer / training samples (DEVICE arrays of float[n*16]):

@@ -332,6 +332,263 @@ __global__ void __launch_bounds__(128) k_nrc_infer(GridDesc G, const float* __re
     }
 }
 
+// ---- tcgen05 (5th-generation tensor cores, accumulators in tensor memory) ----------------
+// Shared-memory operands use the canonical no-swizzle K-major layout: 8 x 8 FP16 core
+// matrices of 128 contiguous bytes (8 rows of 16 bytes); core matrix (row group, k group)
+// sits at ((row / 8) * 8 + k / 8) * 128 bytes, so the K-adjacent core matrix is 128 bytes
+// on (leading byte offset) and the next 8-row group 1024 bytes on (stride byte offset) for
+// a 64-wide K.
+constexpr uint32_t TC_TILE = 128;          // rows per group tile (the MMA's M)
+constexpr uint32_t TC_GROUPS = 1;          // independent groups of 4 warps per CTA (measured:
+                                           // 4 CTAs of 1 group beat 2 CTAs of 4 groups)
+constexpr uint32_t TC_THREADS = 128 * TC_GROUPS;
+constexpr uint32_t TC_LBO = 128, TC_SBO = 1024;
+constexpr uint32_t TC_W_HALVES = N_HIDDEN * W * W + OUT_PAD * W;
+constexpr uint32_t TC_SMEM = 1024 + TC_W_HALVES * 2 + TC_GROUPS * TC_TILE * W * 2 + 16 * TC_GROUPS + 16;
+constexpr uint32_t TC_TMEM_COLS = 64 * TC_GROUPS;
+constexpr uint32_t TC_SPIN = 1u << 24;     // bounded mbarrier wait (iterations)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// element (r, k) of a K-major FP16 tile with 64 columns, in halves
+__device__ __forceinline__ uint32_t tc_off(uint32_t r, uint32_t k) {
+    return (((r >> 3) * 8u + (k >> 3)) << 6) + ((r & 7u) << 3) + (k & 7u);
+}
+
+// shared-memory matrix descriptor: start, leading / stride byte offsets (16-byte units),
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(const __half* p) {
+    uint64_t d = (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu);
+    d |= (uint64_t)((TC_LBO >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((TC_SBO >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, FP16 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t tc_idesc(uint32_t m, uint32_t n) {
+    return (1u << 4) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" :: "r"(mbar) : "memory");
+}
+
+// bounded wait for the mbarrier phase `parity`; false if it did not complete
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (uint32_t it = 0; it < TC_SPIN; ++it) {
+        uint32_t done = 0;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+#define TC_LD_REGS8(i) "=r"(v[i]), "=r"(v[i + 1]), "=r"(v[i + 2]), "=r"(v[i + 3]), "=r"(v[i + 4]), "=r"(v[i + 5]), "=r"(v[i + 6]), "=r"(v[i + 7])
+
+// 32 lanes x 32 columns of FP32 from tensor memory: this thread's row, 32 columns from taddr
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : TC_LD_REGS8(0), TC_LD_REGS8(8), TC_LD_REGS8(16), TC_LD_REGS8(24)
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// named barrier of one 4-warp group (ids 1..4; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(uint32_t g) {
+    asm volatile("bar.sync %0, 128;\n" :: "r"(1u + g) : "memory");
+}
+// the same barrier with an AND vote over the group's 128 threads
+__device__ __forceinline__ bool group_and(uint32_t g, bool v) {
+    uint32_t r;
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %2, 0;\n bar.red.and.pred q, %1, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(r) : "r"(1u + g), "r"(v ? 1u : 0u) : "memory");
+    return r != 0;
+}
+
+// Cache inference on tcgen05.  A CTA holds the weights once and four independent groups of
+// four warps; each group owns a 128-query tile at a time: the encoding is written straight
+// into the group's K-major A tile in shared memory, then each of the five layers is four
+// tcgen05.mma (K = 16 each, M = 128, N = 64 / 16) issued by one thread of the group into the
+// group's 128 x 64 FP32 accumulator in tensor memory; the group's warps read their 32 rows
+// back with tcgen05.ld, apply ReLU and store FP16 into the A tile for the next layer.  Groups
+// synchronise on their own named barriers, so one group's encoding overlaps another's
+// layers.  A wait that runs out sets err[0]; the group stops, and the CTA frees its tensor
+// memory and returns.
+__global__ void __launch_bounds__(TC_THREADS, 2) k_nrc_infer_tc(GridDesc G, const float* __restrict__ queries, RowCount rc,
+                                                             const __half* __restrict__ Wg, float* __restrict__ Y,
+                                                             uint32_t* __restrict__ err) {
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    __half* sW = reinterpret_cast<__half*>(base);
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t g = warp >> 2, wq = warp & 3u;       // group, quarter of the tile's rows
+    __half* sA = sW + TC_W_HALVES + g * TC_TILE * W;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sW + TC_W_HALVES + TC_GROUPS * TC_TILE * W) + 2 * g;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(reinterpret_cast<uint64_t*>(sW + TC_W_HALVES + TC_GROUPS * TC_TILE * W) +
+                                                  2 * TC_GROUPS);
+    // weights: global row-major [out][in] -> K-major core matrices (16-byte chunks)
+    for (uint32_t i = tid; i < (N_HIDDEN * W + OUT_PAD) * (W / 8); i += blockDim.x) {
+        const uint32_t row = i / (W / 8), c = i % (W / 8);
+        const uint32_t layer = min(row / W, (uint32_t)N_HIDDEN), r = row - layer * W;
+        *reinterpret_cast<uint4*>(sW + layer * W * W + tc_off(r, 8 * c)) =
+            *reinterpret_cast<const uint4*>(Wg + (size_t)row * W + 8 * c);
+    }
+    if ((tid & 127u) == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     :: "r"(smem_u32(tslot)), "r"(TC_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tslot + 64u * g;                 // the group's 64 columns
+    const uint32_t my_lanes = tmem + ((32u * wq) << 16);     // this warp's 32 lanes
+    const uint32_t n = rc.get();
+    const uint32_t n_tiles = (n + TC_TILE - 1) / TC_TILE;
+    const uint32_t l = lane & 15u;
+    const bool grid_lane = l < G.L;
+    const uint32_t res = grid_lane ? G.res[l] : 1u;
+    const __half2* tab = reinterpret_cast<const __half2*>(G.table) + (size_t)l * G.T;
+    const uint32_t ncols = W - 2 * G.L;
+    const bool issuer = (tid & 127u) == 0;
+    uint32_t phase = 0;
+    for (uint32_t tile = blockIdx.x * TC_GROUPS + g; tile < n_tiles; tile += gridDim.x * TC_GROUPS) {
+        const uint32_t t0 = tile * TC_TILE;
+        // encoding of this warp's 32 rows: grid features of 8 rows at a time are gathered into
+        // registers first and stored afterwards, so that their corner loads are all in flight
+        // together, then the other columns
+#pragma unroll
+        for (uint32_t rb = 0; rb < 16; rb += 8) {
+            __half2 f[8];
+#pragma unroll
+            for (uint32_t r = 0; r < 8; ++r) {
+                const uint32_t q = t0 + 32u * wq + 2u * (rb + r) + (lane >> 4);
+                float f0 = 0.0f, f1 = 0.0f;
+                if (grid_lane && q < n) {
+                    const float3 p = pos01(G, queries + (size_t)QSTRIDE * q);
+                    const float fx = p.x * res, fy = p.y * res, fz = p.z * res;
+                    const uint32_t cx = min((uint32_t)fx, res - 1), cy = min((uint32_t)fy, res - 1),
+                                   cz = min((uint32_t)fz, res - 1);
+                    const float rx = fx - cx, ry = fy - cy, rz = fz - cz;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const uint32_t ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+                        const float w = (ox ? rx : 1.0f - rx) * (oy ? ry : 1.0f - ry) * (oz ? rz : 1.0f - rz);
+                        const float2 v = __half22float2(__ldg(tab + corner_index(cx + ox, cy + oy, cz + oz, res, G.T)));
+                        f0 += w * v.x;
+                        f1 += w * v.y;
+                    }
+                }
+                f[r] = __floats2half2_rn(f0, f1);
+            }
+            if (grid_lane) {
+#pragma unroll
+                for (uint32_t r = 0; r < 8; ++r)
+                    *reinterpret_cast<__half2*>(sA + tc_off(32u * wq + 2u * (rb + r) + (lane >> 4), 2 * l)) = f[r];
+            }
+        }
+        for (uint32_t e = lane; e < 32u * ncols; e += 32) {
+            const uint32_t row = 32u * wq + e / ncols, k = e % ncols;
+            const uint32_t q = t0 + row;
+            float v = 0.0f;
+            if (q < n) {
+                const float* rec = queries + (size_t)QSTRIDE * q;
+                if (k < 3) v = rec[3 + k];
+                else if (k < 6) v = rec[6 + (k - 3)];
+                else if (k == 6) v = rec[9];
+                else if (k == 7) v = 1.0f;
+            }
+            sA[tc_off(row, 2 * G.L + k)] = __float2half_rn(v);
+        }
+        const uint32_t row = 32u * wq + lane;
+        bool ok = true;
+        for (int layer = 0; layer <= N_HIDDEN; ++layer) {
+            // the A tile (written by every thread of the group) must be visible to the tensor core
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            group_sync(g);
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const bool out_layer = layer == N_HIDDEN;
+            if (issuer) {
+                const __half* wl = sW + layer * W * W;
+                const uint32_t idesc = tc_idesc(TC_TILE, out_layer ? OUT_PAD : W);
+#pragma unroll
+                for (uint32_t kk = 0; kk < 4; ++kk)
+                    tc_mma(tmem, tc_desc(sA + kk * 128), tc_desc(wl + kk * 128), idesc, kk > 0 ? 1u : 0u);
+                tc_commit(smem_u32(mbar));
+            }
+            __syncwarp();
+            const bool got = mbar_wait(smem_u32(mbar), phase);
+            if (!got && lane == 0) atomicOr(err, 1u);
+            // one decision for the whole group, so all its threads leave at the same barrier
+            if (!group_and(g, got)) {
+                ok = false;
+                mbar_wait(smem_u32(mbar), phase);   // one more bounded wait for the MMA in flight
+                break;
+            }
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            if (!out_layer) {
+                // two halves of 32 columns keep fewer registers live
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    uint32_t v[32];
+                    tc_ld32(my_lanes + 32u * half, v);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        uint4 pk;
+                        uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+                        for (int h = 0; h < 4; ++h)
+                            pw[h] = pack_h2(fmaxf(__uint_as_float(v[8 * c + 2 * h]), 0.0f),
+                                            fmaxf(__uint_as_float(v[8 * c + 2 * h + 1]), 0.0f));
+                        *reinterpret_cast<uint4*>(sA + tc_off(row, 32 * half + 8 * c)) = pk;
+                    }
+                }
+            } else {
+                uint32_t v[4];
+                tc_ld4(my_lanes, v);
+                const uint32_t q = t0 + row;
+                if (q < n)
+                    *reinterpret_cast<float4*>(Y + 4ull * q) = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]),
+                                                                           __uint_as_float(v[2]), __uint_as_float(v[3]));
+            }
+        }
+        // the next tile's encoding overwrites the A tile and the accumulator is reused
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        group_sync(g);
+        if (!ok) break;
+    }
+    // every group is done and each of its MMAs completed (waited for) unless a wait ran out
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(*tslot), "r"(TC_TMEM_COLS) : "memory");
+}
+
 // relative L2 loss: dL/dy * (3n) (the 1/(3n) of the mean is applied to the gradients later
 // so that FP16 keeps them in its normal range); adds the loss sum and the row count to
 // loss_sum[0..1], which the caller zeroes once per training call (all its batches)
@@ -631,6 +888,7 @@ struct pt_nrc {
     uint32_t cap = 0;
     __half *X = nullptr, *acts = nullptr, *dY = nullptr, *dZ = nullptr;
     float *Y = nullptr, *dX = nullptr, *part = nullptr, *d_loss = nullptr;
+    uint32_t* d_err = nullptr;     // device error word (1: a tensor-core wait ran out)
     // inference buffers
     uint32_t icap = 0;
     __half* iX = nullptr;
@@ -731,6 +989,8 @@ extern "C" pt_status pt_nrc_create(const pt_nrc_opts* opts, void* cuda_stream, p
     for (float** p : g32) NTRY(cudaMalloc(p, N->n_grid * sizeof(float)));
     NTRY(cudaMalloc(&N->d_gh, N->n_grid * sizeof(__half)));
     NTRY(cudaMalloc(&N->d_loss, 4 * sizeof(float)));
+    NTRY(cudaMalloc(&N->d_err, sizeof(uint32_t)));
+    NTRY(cudaMemsetAsync(N->d_err, 0, sizeof(uint32_t), st));
     for (float* p : {N->d_wm, N->d_wv, N->d_wg}) NTRY(cudaMemsetAsync(p, 0, N_WEIGHTS * sizeof(float), st));
     for (float* p : {N->d_gm, N->d_gv, N->d_gg}) NTRY(cudaMemsetAsync(p, 0, N->n_grid * sizeof(float), st));
     NTRY(cudaMemsetAsync(N->d_loss, 0, 4 * sizeof(float), st));
@@ -748,7 +1008,7 @@ extern "C" void pt_nrc_destroy(pt_nrc* N) {
     if (!N) return;
     cudaDeviceSynchronize();
     void* ps[] = {N->d_res, N->d_w, N->d_wh, N->d_wm, N->d_wv, N->d_wg, N->d_grid, N->d_gh, N->d_gm, N->d_gv, N->d_gg,
-                  N->X, N->acts, N->dY, N->dZ, N->Y, N->dX, N->part, N->d_loss, N->iX, N->iY};
+                  N->X, N->acts, N->dY, N->dZ, N->Y, N->dX, N->part, N->d_loss, N->iX, N->iY, N->d_err};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete N;
@@ -760,12 +1020,31 @@ static uint32_t encode_grid(uint32_t cap, uint32_t L) {
 }
 
 // forward (+ optional activations) of rc rows already resident on the device
-static int g_infer_blocks = 0;
+static int g_infer_blocks = 0, g_infer_tc_blocks = 0;
 
 static pt_status nrc_forward(pt_nrc* N, const float* q, RowCount rc, __half* X, float* Y, __half* acts, cudaStream_t st) {
     const GridDesc G = grid_desc(N);
+    if (!acts && N->o.tcgen05) {
+        // inference on the tcgen05 tensor cores (TMEM accumulators), persistent over
+        // 128-row tiles
+        if (g_infer_tc_blocks == 0) {
+            PT_CUDA_TRY(cudaFuncSetAttribute(k_nrc_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+            // the largest shared-memory carveout, so that 4 CTAs (4 x 52 KB) fit on an SM
+            PT_CUDA_TRY(cudaFuncSetAttribute(k_nrc_infer_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared));
+            // 4 CTAs per SM: 4 x 52 KB of shared memory and 4 x 64 of the 512 tensor-memory
+            // columns (the occupancy query does not account for the latter)
+            g_infer_tc_blocks = 4 * pt_num_sms();
+        }
+        const uint32_t tiles = (rc.n + TC_TILE - 1) / TC_TILE;
+        const uint32_t blocks = std::max(1u, std::min((uint32_t)g_infer_tc_blocks, (tiles + TC_GROUPS - 1) / TC_GROUPS));
+        PT_LAUNCH(k_nrc_infer_tc, blocks, TC_THREADS, TC_SMEM, st, G, q, rc, N->d_wh, Y, N->d_err);
+        N->launches += 1;
+        PT_CUDA_TRY(cudaGetLastError());
+        return PT_OK;
+    }
     if (!acts) {
-        // inference: encoding and MLP in one kernel, persistent over 16-row tiles
+        // inference: encoding and MLP in one kernel on mma.sync, persistent over 16-row tiles
         if (g_infer_blocks == 0) {
             int b = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_nrc_infer, 128, 0);
@@ -897,6 +1176,12 @@ extern "C" pt_status pt_nrc_last_loss(pt_nrc* N, float* loss) {
     PT_CUDA_TRY(cudaDeviceSynchronize());
     float s[2] = {0.0f, 0.0f};
     PT_CUDA_TRY(cudaMemcpy(s, N->d_loss, 2 * sizeof(float), cudaMemcpyDeviceToHost));
+    uint32_t e = 0;
+    PT_CUDA_TRY(cudaMemcpy(&e, N->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (e) {
+        pt_set_error("a tensor-core completion wait of the cache ran out of its spin budget");
+        return PT_ERR_TIMEOUT;
+    }
     *loss = s[1] > 0.0f ? s[0] / (3.0f * s[1]) : 0.0f;
     return PT_OK;
 }

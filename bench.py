@@ -330,11 +330,15 @@ def run_ours(args, world, rank, local):
     st_before = scene.stats()
     launches_before = api.launch_count()
     with ClockSampler(local) as clocks:
+        # NVTX range "timed": profilers can select exactly these frames (ncu --nvtx
+        # --nvtx-include "timed/")
+        torch.cuda.nvtx.range_push("timed")
         for k in range(args.steps):
             flush.fill_(float(k))  # L2 flush between steps, outside the timed events
             starts[k].record(stream)
             scene.render(1, seed=seed, accum=acc, mode=mode, use_graph=args.graph)
             ends[k].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     launches = api.launch_count() - launches_before
     st_after = scene.stats()

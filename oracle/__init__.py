@@ -297,7 +297,8 @@ class OracleScene:
         spp = sc.spp if spp is None else spp
         max_depth = sc.max_depth if max_depth is None else max_depth
         x0, y0, cw, ch = crop if crop is not None else (0, 0, cam.width, cam.height)
-        cam9 = np.array([*cam.origin, *cam.target, *cam.up], dtype=np.float64)
+        cam9 = np.array([*cam.origin, *cam.target, *cam.up, getattr(cam, "lens_radius", 0.0),
+                         getattr(cam, "focus_distance", 1.0)], dtype=np.float64)
         out = np.zeros((ch, cw, 3))
         samples = np.zeros((ch, cw, spp, 3)) if keep_samples else None
         stats = np.zeros(5, dtype=np.int64)
@@ -314,7 +315,8 @@ class OracleScene:
 
 
 def camera_ray(camera, px, py, sample, seed):
-    cam9 = np.array([*camera.origin, *camera.target, *camera.up], dtype=np.float64)
+    cam9 = np.array([*camera.origin, *camera.target, *camera.up, getattr(camera, "lens_radius", 0.0),
+                     getattr(camera, "focus_distance", 1.0)], dtype=np.float64)
     o = np.zeros(3)
     d = np.zeros(3)
     _load().oracle_camera_ray(cam9.ctypes.data_as(_dp), float(camera.vfov_deg), camera.width,

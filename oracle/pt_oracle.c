@@ -84,7 +84,8 @@ double oracle_uniform(uint32_t pixel, uint32_t sample, uint32_t bounce, uint32_t
 
 /* dimension table of one path vertex */
 enum { DIM_CAM_X = 0, DIM_CAM_Y = 1, DIM_LIGHT_PICK = 2, DIM_LIGHT_U = 3, DIM_LIGHT_V = 4,
-       DIM_LOBE = 5, DIM_DIR_U = 6, DIM_DIR_V = 7, DIM_REFRACT = 8, DIM_RR = 9 };
+       DIM_LOBE = 5, DIM_DIR_U = 6, DIM_DIR_V = 7, DIM_REFRACT = 8, DIM_RR = 9,
+       DIM_LENS_U = 12, DIM_LENS_V = 13 };
 
 /* ------------------------------------------------------------------------------------ */
 /* OpenPBR parameters (26 values per material, same order as the C-ABI table)            */
@@ -929,6 +930,7 @@ typedef struct {
     v3 origin, target, up;
     double vfov_deg;
     int width, height;
+    double lens_radius, focus_distance;   /* thin lens; radius 0 = pinhole */
 } ocam;
 
 typedef struct {
@@ -958,7 +960,23 @@ static inline double U(uint32_t p, uint32_t s, uint32_t k, uint32_t dim, uint64_
     return oracle_uniform(p, s, k, dim, seed);
 }
 
-/* the camera ray of pixel (px, py), sample s: pinhole, jitter inside the pixel (box filter) */
+/* Concentric map of the unit square onto the unit disk (Shirley and Chiu 1997): square rings
+ * go to disk rings, so the map preserves relative area and uniform points stay uniform. */
+static void concentric_disk(double u0, double u1, double* x, double* y) {
+    double a = 2.0 * u0 - 1.0, b = 2.0 * u1 - 1.0;
+    if (a == 0.0 && b == 0.0) { *x = 0.0; *y = 0.0; return; }
+    double r, phi;
+    if (fabs(a) > fabs(b)) { r = a; phi = 0.25 * M_PI * (b / a); }
+    else { r = b; phi = 0.5 * M_PI - 0.25 * M_PI * (a / b); }
+    *x = r * cos(phi);
+    *y = r * sin(phi);
+}
+
+/* The camera ray of pixel (px, py), sample s: jitter inside the pixel (box filter).  Pinhole
+ * when lens_radius = 0; else a thin lens (depth of field, a future-work item of Sec. 6.3): the lens
+ * point, on the disk of that radius in the (right, up) plane, comes from dimensions 12-13 by
+ * the concentric map, and the ray aims at the point where the pinhole ray of the same
+ * jitter meets the plane of focus, perpendicular to the view direction at focus_distance. */
 static void camera_ray(const ocam* c, int px, int py, uint32_t s, uint64_t seed, v3* o, v3* d) {
     uint32_t p = (uint32_t)(py * c->width + px);
     double u0 = U(p, s, 0, DIM_CAM_X, seed), u1 = U(p, s, 0, DIM_CAM_Y, seed);
@@ -969,8 +987,18 @@ static void camera_ray(const ocam* c, int px, int py, uint32_t s, uint64_t seed,
     double aspect = (double)c->width / (double)c->height;
     double nx = (2.0 * (px + u0) / c->width - 1.0) * aspect * th;
     double ny = (1.0 - 2.0 * (py + u1) / c->height) * th;
+    v3 dp = normalize(add(add(fwd, scl(right, nx)), scl(up, ny)));
+    if (c->lens_radius > 0.0) {
+        double lx, ly;
+        concentric_disk(U(p, s, 0, DIM_LENS_U, seed), U(p, s, 0, DIM_LENS_V, seed), &lx, &ly);
+        v3 focus = add(c->origin, scl(dp, c->focus_distance / dot(dp, fwd)));
+        v3 lens = add(c->origin, add(scl(right, c->lens_radius * lx), scl(up, c->lens_radius * ly)));
+        *o = lens;
+        *d = normalize(sub(focus, lens));
+        return;
+    }
     *o = c->origin;
-    *d = normalize(add(add(fwd, scl(right, nx)), scl(up, ny)));
+    *d = dp;
 }
 
 /* Radiance of one path (pixel p, sample s).  Recursion written as a loop over vertices k.
@@ -1159,7 +1187,7 @@ static void* worker(void* arg) {
 
 /* Render samples s0 .. s0+spp-1 of the crop [x0, x0+cw) x [y0, y0+ch) of the full frame.
  * sum_out receives the per-pixel sum of sample radiance (divide by spp for the estimate).
- * cam = origin[3], target[3], up[3], vfov_deg; row_step > 1 renders only every row_step-th
+ * cam = origin[3], target[3], up[3], lens_radius, focus_distance; row_step > 1 renders only every row_step-th
  * row of the crop (others stay 0); flags as for trace_path.  stats_out (5 int64): extension rays, shadow rays, NaN
  * samples dropped, roulette terminations, paths. */
 void oracle_render(void* hs, const double* cam9, double vfov_deg, int width, int height,
@@ -1173,6 +1201,8 @@ void oracle_render(void* hs, const double* cam9, double vfov_deg, int width, int
     cam.vfov_deg = vfov_deg;
     cam.width = width;
     cam.height = height;
+    cam.lens_radius = cam9[9];
+    cam.focus_distance = cam9[10];
     if (nthreads < 1) nthreads = 1;
     if (row_step < 1) row_step = 1;
     memset(sum_out, 0, sizeof(double) * 3 * (size_t)cw * ch);
@@ -1210,6 +1240,8 @@ void oracle_camera_ray(const double* cam9, double vfov_deg, int width, int heigh
     cam.vfov_deg = vfov_deg;
     cam.width = width;
     cam.height = height;
+    cam.lens_radius = cam9[9];
+    cam.focus_distance = cam9[10];
     v3 o, d;
     camera_ray(&cam, px, py, s, seed, &o, &d);
     o_out[0] = o.x; o_out[1] = o.y; o_out[2] = o.z;

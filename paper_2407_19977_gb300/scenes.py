@@ -67,6 +67,8 @@ class Camera:
     vfov_deg: float
     width: int
     height: int
+    lens_radius: float = 0.0      # thin lens; 0 = pinhole
+    focus_distance: float = 1.0   # distance of the plane of focus along the view direction
 
 
 @dataclass

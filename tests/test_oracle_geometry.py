@@ -133,6 +133,40 @@ def test_tmax_is_exclusive():
     assert tri2[0] == -1
 
 
+def test_thin_lens_camera():
+    """Thin-lens depth of field: radius 0 is the pinhole ray; otherwise every ray starts on the
+    lens disk (in the plane through the camera origin perpendicular to the view direction),
+    passes through the point where the pinhole ray of the same pixel jitter meets the plane of
+    focus, and the lens points are uniform over the disk (concentric map)."""
+    base = dict(origin=(0.3, 0.2, -1.0), target=(0.5, 0.4, 1.0), up=(0, 1, 0), vfov_deg=45.0, width=40,
+                height=30)
+    pin = scenes.Camera(**base)
+    zero = scenes.Camera(**base, lens_radius=0.0, focus_distance=2.0)
+    lens = scenes.Camera(**base, lens_radius=0.05, focus_distance=1.7)
+    o0 = np.array(base["origin"], float)
+    fwd = np.subtract(base["target"], base["origin"])
+    fwd = fwd / np.linalg.norm(fwd)
+    radii = []
+    for s in range(400):
+        px, py = s % 40, (7 * s) % 30
+        op, dp = oracle.camera_ray(pin, px, py, s, 11)
+        oz, dz = oracle.camera_ray(zero, px, py, s, 11)
+        assert np.array_equal(op, oz) and np.array_equal(dp, dz)
+        ol, dl = oracle.camera_ray(lens, px, py, s, 11)
+        off = ol - o0
+        assert abs(off @ fwd) < 1e-12                       # on the lens plane
+        radii.append(np.linalg.norm(off))
+        focus = op + dp * (1.7 / (dp @ fwd))                 # pinhole ray on the plane of focus
+        t = (focus - ol) @ dl
+        assert np.linalg.norm(ol + t * dl - focus) < 1e-10   # the lens ray passes through it
+        assert abs(np.linalg.norm(dl) - 1.0) < 1e-12
+    radii = np.array(radii) / 0.05
+    assert radii.max() <= 1.0 + 1e-12
+    # uniform on the disk: P(r < 1/2) = 1/4, P(r < 1/sqrt 2) = 1/2 (binomial, 400 samples)
+    assert abs((radii < 0.5).mean() - 0.25) < 0.07
+    assert abs((radii < 2 ** -0.5).mean() - 0.5) < 0.08
+
+
 def test_camera_frustum_geometry():
     cam = scenes.Camera((0, 0, 0), (0, 0, 1), (0, 1, 0), 60.0, 64, 32)
     # every ray of the top row points up by less than 30 deg, of row 0..: by ~30 deg at the edge

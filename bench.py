@@ -39,6 +39,8 @@ WORKLOADS = {
              "analytic sky 512x256",
     "cornell512": "Cornell-style box, 36 triangles, one quad light, 512x512, 1 spp/step, max depth 8",
     "cornell1080": "Cornell-style box, 36 triangles, one quad light, 1920x1080, 1 spp/step, max depth 8",
+    "pushbutton_dof": "the pushbutton frame through a thin lens (radius 0.03, focus on the button), "
+                      "1920x1080, 1 spp/step, max depth 8",
 }
 NODE_BYTES = 80      # compressed 8-wide BVH node
 TRI_BYTES = 48       # triangle record
@@ -199,6 +201,12 @@ def _make_workload(name):
         return scenes.cornell_box(width=512, height=512, spp=1, max_depth=8)
     if name == "cornell1080":
         return scenes.cornell_box(width=1920, height=1080, spp=1, max_depth=8)
+    if name == "pushbutton_dof":
+        sc = scenes.pushbutton()
+        c = sc.camera
+        focus = math.dist(c.target, c.origin)
+        sc.camera = type(c)(**{**c.__dict__, "lens_radius": 0.03, "focus_distance": focus})
+        return sc
     raise ValueError(name)
 
 

@@ -85,9 +85,15 @@ typedef struct {
     int32_t two_sided;
 } pt_quad_light;
 
-/* Pinhole camera: vertical field of view vfov_deg; the full frame is width x height
+/* Perspective camera: vertical field of view vfov_deg; the full frame is width x height
  * pixels, pixel (x, y) with y growing downwards; pixel id p = y * width + x keys the
- * random numbers (Sec. 5.1.2: adjacent pixels run concurrently, each sample jittered). */
+ * random numbers (Sec. 5.1.2: adjacent pixels run concurrently, each sample jittered).
+ * lens_radius = 0 is a pinhole.  lens_radius > 0 is a thin lens (depth of field, named as
+ * future work in Sec. 6.3): rays start on a disk of that radius around `origin` in the
+ * camera's (right, up) plane and pass through the point where the pinhole ray of the same
+ * jitter meets the plane of focus, focus_distance along the view direction
+ * (focus_distance > 0 is then required).  The lens point uses dimensions 12-13 of the first
+ * vertex. */
 typedef struct {
     float origin[3];
     float target[3];
@@ -95,6 +101,8 @@ typedef struct {
     float vfov_deg;
     uint32_t width;
     uint32_t height;
+    float lens_radius;
+    float focus_distance;
 } pt_camera;
 
 /* Progressive accumulator (Sec. 5.1.4), caller-owned DEVICE buffers of width*height*3

@@ -32,6 +32,8 @@ def make_camera(cam) -> N.pt_camera:
     c.vfov_deg = float(cam.vfov_deg)
     c.width = int(cam.width)
     c.height = int(cam.height)
+    c.lens_radius = float(getattr(cam, "lens_radius", 0.0))
+    c.focus_distance = float(getattr(cam, "focus_distance", 1.0))
     return c
 
 

@@ -500,9 +500,8 @@ __global__ void k_camera_rays(DCam cam, uint64_t seed, const uint32_t* pix, uint
     if (i >= n) return;
     const uint32_t x = pix[3 * i], y = pix[3 * i + 1], s = pix[3 * i + 2];
     const uint32_t p = y * cam.width + x;
-    const uint4 w = philox4x32_10(make_uint4(p, s, 0u, 0u), (uint32_t)seed, (uint32_t)(seed >> 32));
     float3 o, d;
-    camera_ray(cam, x, y, u24(w.x), u24(w.y), o, d);
+    camera_ray_ps(cam, x, y, p, s, (uint32_t)seed, (uint32_t)(seed >> 32), o, d);
     float* r = out + 6 * i;
     r[0] = o.x; r[1] = o.y; r[2] = o.z; r[3] = d.x; r[4] = d.y; r[5] = d.z;
 }
@@ -511,6 +510,7 @@ extern "C" pt_status pt_camera_rays(const pt_camera* camera, uint64_t seed, cons
                                     float* out, void* cuda_stream) {
     PT_CHECK_ARG(camera && pixels && out, "NULL argument");
     PT_CHECK_ARG(camera->width > 0 && camera->height > 0, "empty frame");
+    PT_CHECK_ARG(lens_ok(*camera), "lens_radius must be finite and >= 0, with focus_distance > 0 when it is > 0");
     if (n == 0) return PT_OK;
     PT_LAUNCH(k_camera_rays, (n + 127) / 128, 128, 0, (cudaStream_t)cuda_stream, to_dcam(*camera), seed, pixels, n, out);
     PT_CUDA_TRY(cudaGetLastError());

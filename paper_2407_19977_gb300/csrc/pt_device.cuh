@@ -828,9 +828,26 @@ struct DCam {
     float3 origin, target, up;
     float vfov_deg;
     uint32_t width, height;
+    float lens_radius, focus_distance;   // thin lens; radius 0 = pinhole
 };
-__device__ __forceinline__ void camera_ray(const DCam& c, uint32_t px, uint32_t py, float u0, float u1,
-                                           float3& o, float3& d) {
+
+// Concentric map of the unit square onto the unit disk (Shirley and Chiu 1997): square rings
+// go to disk rings, so uniform points stay uniform.
+__device__ __forceinline__ void concentric_disk(float u0, float u1, float& x, float& y) {
+    const float a = 2.0f * u0 - 1.0f, b = 2.0f * u1 - 1.0f;
+    if (a == 0.0f && b == 0.0f) { x = 0.0f; y = 0.0f; return; }
+    float r, phi;
+    if (fabsf(a) > fabsf(b)) { r = a; phi = (0.25f * PT_PI_F) * (b / a); }
+    else { r = b; phi = 0.5f * PT_PI_F - (0.25f * PT_PI_F) * (a / b); }
+    x = r * cosf(phi);
+    y = r * sinf(phi);
+}
+
+// Camera ray of pixel (px, py) with jitter (u0, u1) and lens uniforms (l0, l1), the latter
+// used only by a thin lens: the ray starts at the lens point and passes through the point
+// where the pinhole ray of the same jitter meets the plane of focus.
+__device__ __forceinline__ void camera_ray(const DCam& c, uint32_t px, uint32_t py, float u0, float u1, float l0,
+                                           float l1, float3& o, float3& d) {
     const float3 fwd = norm3(c.target - c.origin);
     const float3 right = norm3(cross3(fwd, c.up));
     const float3 up = cross3(right, fwd);
@@ -838,8 +855,33 @@ __device__ __forceinline__ void camera_ray(const DCam& c, uint32_t px, uint32_t 
     const float aspect = (float)c.width / (float)c.height;
     const float nx = (2.0f * ((float)px + u0) / (float)c.width - 1.0f) * aspect * th;
     const float ny = (1.0f - 2.0f * ((float)py + u1) / (float)c.height) * th;
+    const float3 dp = norm3(fwd + right * nx + up * ny);
+    if (c.lens_radius > 0.0f) {
+        float lx, ly;
+        concentric_disk(l0, l1, lx, ly);
+        const float3 focus = c.origin + dp * (c.focus_distance / dot3(dp, fwd));
+        const float3 lens = c.origin + (right * (c.lens_radius * lx) + up * (c.lens_radius * ly));
+        o = lens;
+        d = norm3(focus - lens);
+        return;
+    }
     o = c.origin;
-    d = norm3(fwd + right * nx + up * ny);
+    d = dp;
+}
+
+// the camera ray of pixel (px, py) = pixel id p, sample s: jitter from dimensions 0-1 and,
+// for a thin lens, the lens point from dimensions 12-13 of the first vertex
+constexpr uint32_t DIM_LENS = 12;
+__device__ __forceinline__ void camera_ray_ps(const DCam& c, uint32_t px, uint32_t py, uint32_t p, uint32_t s,
+                                              uint32_t k0, uint32_t k1, float3& o, float3& d) {
+    const uint4 u = philox4x32_10(make_uint4(p, s, 0u, 0u), k0, k1);
+    float l0 = 0.0f, l1 = 0.0f;
+    if (c.lens_radius > 0.0f) {
+        const uint4 w = philox4x32_10(make_uint4(p, s, 0u, DIM_LENS >> 2), k0, k1);
+        l0 = u24(w.x);
+        l1 = u24(w.y);
+    }
+    camera_ray(c, px, py, u24(u.x), u24(u.y), l0, l1, o, d);
 }
 
 __device__ __forceinline__ float3 offset_origin(float3 x, float3 ng, float3 dir, float eps) {

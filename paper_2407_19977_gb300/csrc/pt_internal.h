@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cmath>
 #include <vector>
 #include <cstdint>
 #include <string>
@@ -155,6 +156,12 @@ pt_status pt_nrc_render_infer_dev(pt_nrc* N, const float* queries, const uint32_
 uint32_t pt_nrc_frame_samples(const pt_nrc* N);
 pt_status pt_nrc_render_train_dev(pt_nrc* N, const float* samples, const uint32_t* n_dev, uint32_t cap, cudaStream_t st);
 
+// the lens of a camera: radius finite and >= 0; an open lens needs a finite focus distance > 0
+inline bool lens_ok(const pt_camera& c) {
+    return std::isfinite(c.lens_radius) && c.lens_radius >= 0.0f &&
+           (c.lens_radius == 0.0f || (std::isfinite(c.focus_distance) && c.focus_distance > 0.0f));
+}
+
 inline DCam to_dcam(const pt_camera& c) {
     DCam d;
     d.origin = make_float3(c.origin[0], c.origin[1], c.origin[2]);
@@ -163,6 +170,8 @@ inline DCam to_dcam(const pt_camera& c) {
     d.vfov_deg = c.vfov_deg;
     d.width = c.width;
     d.height = c.height;
+    d.lens_radius = c.lens_radius;
+    d.focus_distance = c.focus_distance;
     return d;
 }
 

@@ -52,9 +52,8 @@ __device__ __forceinline__ void render_pixel(const DJob& J, uint32_t lp, PixelCo
     float s0 = sp[0], s1 = sp[1], s2 = sp[2], c0 = cp[0], c1 = cp[1], c2 = cp[2];
     for (uint32_t i = 0; i < J.spp; ++i) {
         const uint32_t s = J.s0 + i;
-        const uint4 cam_u = philox4x32_10(make_uint4(p, s, 0u, 0u), k0, k1);
         float3 o, d;
-        camera_ray(J.cam, px, py, u24(cam_u.x), u24(cam_u.y), o, d);
+        camera_ray_ps(J.cam, px, py, p, s, k0, k1, o, d);
         PathState ps;
         ps.beta = splat3(1.0f);
         ps.L = splat3(0.0f);
@@ -361,9 +360,8 @@ __global__ void k_wf_raygen(WfParams P) {
     const uint64_t seed = wf_seed(P);
     const uint32_t px = P.x0 + lp % P.cw, py = P.y0 + lp / P.cw;
     const uint32_t p = py * P.cam.width + px;
-    const uint4 u = philox4x32_10(make_uint4(p, s, 0u, 0u), (uint32_t)seed, (uint32_t)(seed >> 32));
     float3 o, d;
-    camera_ray(P.cam, px, py, u24(u.x), u24(u.y), o, d);
+    camera_ray_ps(P.cam, px, py, p, s, (uint32_t)seed, (uint32_t)(seed >> 32), o, d);
     P.ray_o[0][id] = make_float4(o.x, o.y, o.z, 0.0f);
     P.ray_d[0][id] = make_float4(d.x, d.y, d.z, __uint_as_float(id));
     P.beta[id] = make_float4(1.0f, 1.0f, 1.0f, -1.0f);
@@ -1144,6 +1142,7 @@ extern "C" pt_status pt_render(pt_scene* s, const pt_camera* camera, uint32_t sp
     PT_CHECK_ARG(acc->sum && acc->comp, "accumulator buffers are NULL");
     PT_CHECK_ARG(camera->width > 0 && camera->height > 0, "empty frame");
     PT_CHECK_ARG(camera->vfov_deg > 0.0f && camera->vfov_deg < 180.0f, "vfov outside (0, 180)");
+    PT_CHECK_ARG(lens_ok(*camera), "lens_radius must be finite and >= 0, with focus_distance > 0 when it is > 0");
     pt_render_opts o;
     std::memset(&o, 0, sizeof(o));
     o.sort_by_material = -1;
@@ -1266,6 +1265,7 @@ extern "C" pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const 
         const pt_job& j = jobs[i];
         PT_CHECK_ARG(j.scene && j.accum && j.accum->sum && j.accum->comp, "job with NULL scene or accumulator");
         if (!j.scene->built) { pt_set_error("pt_bvh_build has not run"); return PT_ERR_NOT_BUILT; }
+        PT_CHECK_ARG(lens_ok(j.camera), "job camera: bad lens_radius / focus_distance");
         PT_CHECK_ARG(j.accum->width == j.camera.width && j.accum->height == j.camera.height,
                      "batch accumulators cover the whole frame");
         PT_CHECK_ARG(j.accum->spp_done + j.spp < (1ull << 32), "sample index overflows 32 bits");
@@ -1348,6 +1348,7 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
     PT_CHECK_ARG(acc->sum && acc->comp, "accumulator buffers are NULL");
     PT_CHECK_ARG(camera->width > 0 && camera->height > 0, "empty frame");
     PT_CHECK_ARG(camera->vfov_deg > 0.0f && camera->vfov_deg < 180.0f, "vfov outside (0, 180)");
+    PT_CHECK_ARG(lens_ok(*camera), "lens_radius must be finite and >= 0, with focus_distance > 0 when it is > 0");
     pt_render_opts o;
     std::memset(&o, 0, sizeof(o));
     o.sort_by_material = -1;

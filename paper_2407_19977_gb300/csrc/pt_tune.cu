@@ -57,6 +57,7 @@ extern "C" pt_status pt_autotune(pt_scene* s, const pt_camera* camera, uint32_t 
     PT_CHECK_ARG(s && camera && best, "NULL argument");
     if (!s->built) { pt_set_error("pt_bvh_build has not run"); return PT_ERR_NOT_BUILT; }
     PT_CHECK_ARG(camera->width > 0 && camera->height > 0, "empty frame");
+    PT_CHECK_ARG(lens_ok(*camera), "lens_radius must be finite and >= 0, with focus_distance > 0 when it is > 0");
     PT_CHECK_ARG((tune_flags & ~PT_TUNE_BVH) == 0, "unknown tune flags");
     if (spp == 0) spp = 1;
     if (frames == 0) frames = 2;

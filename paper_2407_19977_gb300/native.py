@@ -32,7 +32,7 @@ class pt_quad_light(C.Structure):
 
 class pt_camera(C.Structure):
     _fields_ = [("origin", f32 * 3), ("target", f32 * 3), ("up", f32 * 3), ("vfov_deg", f32),
-                ("width", u32), ("height", u32)]
+                ("width", u32), ("height", u32), ("lens_radius", f32), ("focus_distance", f32)]
 
 
 class pt_accum(C.Structure):

@@ -84,14 +84,18 @@ def test_uniforms_bit_exact(api):
     assert np.array_equal(g, o)
 
 
-def test_camera_rays(api):
+@pytest.mark.parametrize("lens", [0.0, 0.04])
+def test_camera_rays(api, lens):
+    """Pinhole and thin-lens camera rays (the lens point from dimensions 12-13) against the
+    oracle's, for random pixels and samples of the 1080p frame."""
     sc = scenes.pushbutton(width=1920, height=1080)
+    cam = type(sc.camera)(**{**sc.camera.__dict__, "lens_radius": lens, "focus_distance": 2.5})
     rng = np.random.default_rng(1)
     n = 4000
     pix = np.stack([rng.integers(0, 1920, n), rng.integers(0, 1080, n), rng.integers(0, 512, n)], 1).astype(np.int32)
-    out = api.camera_rays(sc.camera, 7, torch.from_numpy(pix).cuda()).cpu().numpy()
+    out = api.camera_rays(cam, 7, torch.from_numpy(pix).cuda()).cpu().numpy()
     for i in range(0, n, 13):
-        o, d = oracle.camera_ray(sc.camera, *pix[i], 7)
+        o, d = oracle.camera_ray(cam, *pix[i], 7)
         assert np.allclose(out[i, :3], o, atol=1e-6)
         assert np.allclose(out[i, 3:], d, atol=2e-6)
 
@@ -382,6 +386,37 @@ def test_full_frame_bench_configuration(api):
     g = acc.sum.cpu().numpy()
     o, _, st = osc.render(spp=1, seed=0, row_step=45)
     _image_check(g[::45], o[::45], "pushbutton 1080p rows")
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_image_parity_depth_of_field(api, mode):
+    """A thin-lens Cornell frame (focus on the back wall, aperture ~ 2 % of the box): the GPU
+    renders what the oracle renders, in both execution modes."""
+    from paper_2407_19977_gb300 import api as A
+    base = scenes.cornell_box(width=48, height=40, spp=8, max_depth=4)
+    cam = type(base.camera)(**{**base.camera.__dict__, "lens_radius": 0.02, "focus_distance": 2.4})
+    sc = scenes.Scene(base.name, base.vertices, base.indices, base.material_ids, base.materials, base.lights,
+                      base.env, cam, base.spp, base.max_depth)
+    g = A.Scene(sc)
+    osc = oracle.OracleScene(sc)
+    gi, oi, gs, os_, st = _render_pair(g, osc, sc, sc.spp, mode=mode, max_depth=sc.max_depth, seed=2)
+    _image_check(gi, oi, f"depth of field mode {mode}")
+    # and it is not the pinhole image
+    pin = A.Scene(base)
+    acc = pin.render(sc.spp, mode=mode, seed=2)
+    torch.cuda.synchronize()
+    assert np.abs(acc.image().cpu().numpy() - gi).max() > 1e-3
+
+
+def test_lens_arguments_are_checked(api):
+    from paper_2407_19977_gb300 import api as A
+    from paper_2407_19977_gb300 import native as N
+    sc, gsc, osc = cornell()
+    for bad in ({"lens_radius": -0.1}, {"lens_radius": 0.1, "focus_distance": 0.0},
+                {"lens_radius": float("nan")}):
+        cam = type(sc.camera)(**{**sc.camera.__dict__, **bad})
+        with pytest.raises(N.PtError, match="INVALID_ARG"):
+            gsc.render(1, camera=cam, accum=A.Accum(64, 64))
 
 
 def test_white_furnace_gpu(api):

@@ -291,6 +291,20 @@ static v3 coat_attenuation(const closure* C, double mu_i_abs, double mu_o) {
 }
 
 /* non-delta part of f(wo, wi) and the mixture pdf of producing wi by BSDF sampling */
+/* Rough diffuse (reading; the paper names OpenPBR, whose base_diffuse_roughness uses the
+ * energy-preserving Oren-Nayar model): its single-scattering part, Fujii's qualitative
+ * Oren-Nayar form, as a factor on the Lambert term:
+ *   (1 + sigma * s / t) / (1 + c * sigma),  c = 1/2 - 2/(3 pi),
+ *   s = wi.wo - mu_i mu_o,  t = max(mu_i, mu_o) if s > 0, else 1.
+ * sigma = 0 is Lambert; the factor is symmetric in (wi, wo); the multiple-scattering
+ * compensation is not included, so a rough diffuse surface loses a little energy. */
+static double fon_factor(v3 wo, v3 wi, double sigma) {
+    if (sigma <= 0.0) return 1.0;
+    double s = dot(wo, wi) - wo.z * wi.z;
+    double t = s > 0.0 ? fmax(wo.z, wi.z) : 1.0;
+    return (1.0 + sigma * s / t) / (1.0 + (0.5 - 2.0 / (3.0 * M_PI)) * sigma);
+}
+
 static void closure_eval(const closure* C, v3 wo, v3 wi, v3* f_out, double* pdf_out) {
     const omat* m = &C->m;
     v3 f = splat(0.0);
@@ -326,7 +340,7 @@ static void closure_eval(const closure* C, v3 wo, v3 wi, v3* f_out, double* pdf_
         double fsi = oracle_fresnel_dielectric(mi, C->eta_s);
         double fso = oracle_fresnel_dielectric(mo, C->eta_s);
         double kd = (1.0 - m->metalness) * (1.0 - m->trans_weight) * (1.0 - m->spec_weight * fsi) *
-                    (1.0 - m->spec_weight * fso) * m->base_weight / M_PI;
+                    (1.0 - m->spec_weight * fso) * m->base_weight / M_PI * fon_factor(wo, wi, m->diffuse_roughness);
         f = add(f, scl(hmul(ac, m->base_color), kd));
         pdf += C->p[LOBE_DIFF] * mi / M_PI;
     } else {

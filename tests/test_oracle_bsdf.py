@@ -29,6 +29,47 @@ def _hemi_dir(mu, phi=0.3):
     return np.array([s * math.cos(phi), s * math.sin(phi), mu])
 
 
+def test_rough_diffuse_properties():
+    """Rough diffuse base (qualitative Oren-Nayar): roughness 0 is Lambert exactly; f depends
+    only on the azimuth difference; near grazing it scatters more back towards the viewer
+    than forward (the backscatter that distinguishes rough from Lambertian diffuse); it does
+    not gain energy (albedo <= rho at every angle)."""
+    rho = 0.7
+    rough = scenes.openpbr(base_color=(rho,) * 3, base_diffuse_roughness=0.9, specular_weight=0.0)
+    rng = np.random.default_rng(3)
+    wo = _sphere_dirs(300)
+    wo[:, 2] = np.abs(wo[:, 2]) + 1e-3
+    wo /= np.linalg.norm(wo, axis=1, keepdims=True)
+    wi = _sphere_dirs(300)
+    wi[:, 2] = np.abs(wi[:, 2]) + 1e-3
+    wi /= np.linalg.norm(wi, axis=1, keepdims=True)
+    f0, _ = oracle.bsdf_eval_batch(scenes.openpbr(base_color=(rho,) * 3, base_diffuse_roughness=0.0,
+                                                  specular_weight=0.0), 1, wo, wi)
+    assert np.allclose(f0, rho / math.pi, rtol=1e-14)
+    # rotating both directions about the normal leaves f unchanged
+    f1, _ = oracle.bsdf_eval_batch(rough, 1, wo, wi)
+    ang = rng.uniform(0, 2 * math.pi)
+    R = np.array([[math.cos(ang), -math.sin(ang), 0], [math.sin(ang), math.cos(ang), 0], [0, 0, 1]])
+    f2, _ = oracle.bsdf_eval_batch(rough, 1, wo @ R.T, wi @ R.T)
+    assert np.allclose(f1, f2, rtol=1e-12)
+    # backscatter: at 75 deg, the mirror-azimuth (retro) direction beats the forward one
+    th = math.radians(75)
+    o = np.array([[math.sin(th), 0, math.cos(th)]])
+    retro, _ = oracle.bsdf_eval_batch(rough, 1, o, o)
+    fwd, _ = oracle.bsdf_eval_batch(rough, 1, o, o * np.array([-1, -1, 1]))
+    assert retro[0, 0] > 1.5 * fwd[0, 0]
+    # directional albedo by quadrature over the cosine-weighted hemisphere
+    n = 200000
+    u1, u2 = rng.random(n), rng.random(n)
+    r, phi = np.sqrt(u1), 2 * math.pi * u2
+    wis = np.stack([r * np.cos(phi), r * np.sin(phi), np.sqrt(1 - u1)], 1)
+    for mu in (0.05, 0.3, 0.7, 1.0):
+        o = np.repeat(np.array([[math.sqrt(1 - mu * mu), 0, mu]]), n, 0)
+        f, _ = oracle.bsdf_eval_batch(rough, 1, o, wis)
+        E = float((f[:, 0] * math.pi).mean())           # f cos / (cos/pi)
+        assert E <= rho * (1 + 1e-2), (mu, E)
+
+
 # materials with every lobe rough enough for quadrature- and MC-based checks
 MATS = {
     "diffuse_white": scenes.openpbr(base_color=(1, 1, 1), specular_weight=0.0),
@@ -42,6 +83,8 @@ MATS = {
     "mixed": scenes.openpbr(base_color=(0.7, 0.6, 0.9), base_metalness=0.3, specular_roughness=0.5,
                             transmission_weight=0.4, transmission_color=(0.9, 0.8, 0.7),
                             coat_weight=0.5, coat_roughness=0.4, coat_color=(0.9, 0.9, 0.6)),
+    "rough_diffuse": scenes.openpbr(base_color=(1, 1, 1), base_diffuse_roughness=1.0, specular_weight=0.0),
+    "rough_plastic": scenes.openpbr(base_color=(0.5, 0.6, 0.7), base_diffuse_roughness=0.6, specular_roughness=0.4),
 }
 WHITE = {
     "white_plastic": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.3),

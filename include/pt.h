@@ -53,7 +53,9 @@ typedef struct pt_nrc pt_nrc;       /* opaque, library-owned */
  * order; the Python generators and the oracle use the same order.
  * Valid ranges (checked by pt_scene_create): weights, colors, roughnesses and metalness
  * in [0, 1]; specular_ior and coat_ior in (1, 3]; emission_luminance >= 0.
- * base_diffuse_roughness must be 0 (Lambertian base). */
+ * base_diffuse_roughness sigma scales the diffuse base by the qualitative Oren-Nayar factor
+ * (1 + sigma s/t) / (1 + c sigma), c = 1/2 - 2/(3 pi), s = wi.wo - cos_i cos_o,
+ * t = max(cos_i, cos_o) if s > 0 else 1 (0 = Lambertian). */
 typedef struct {
     float base_weight;
     float base_color[3];

@@ -90,6 +90,8 @@ __device__ __forceinline__ DMat pack_material(const float* v) {
     m.base_weight = v[0];
     m.base_color = mk3(v[1], v[2], v[3]);
     m.metalness = v[4];
+    m.diffuse_rough = v[5];
+    m.pad0 = m.pad1 = m.pad2 = 0.0f;
     m.spec_weight = v[6];
     m.spec_color = mk3(v[7], v[8], v[9]);
     m.spec_rough = v[10];
@@ -131,10 +133,9 @@ static bool material_ok(const pt_openpbr& m, std::string& why) {
     for (int i = 0; i < 26; ++i)
         if (!std::isfinite(v[i])) { why = "non-finite material parameter"; return false; }
     auto unit = [](float x) { return x >= 0.0f && x <= 1.0f; };
-    const int unit_idx[] = {0, 1, 2, 3, 4, 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17, 18, 19, 20, 23, 24, 25};
+    const int unit_idx[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17, 18, 19, 20, 23, 24, 25};
     for (int i : unit_idx)
         if (!unit(v[i])) { why = "material parameter " + std::to_string(i) + " outside [0,1]"; return false; }
-    if (v[5] != 0.0f) { why = "base_diffuse_roughness must be 0"; return false; }
     if (!(v[11] > 1.0f && v[11] <= 3.0f)) { why = "specular_ior outside (1,3]"; return false; }
     if (!(v[21] > 1.0f && v[21] <= 3.0f)) { why = "coat_ior outside (1,3]"; return false; }
     if (v[22] < 0.0f) { why = "negative emission"; return false; }

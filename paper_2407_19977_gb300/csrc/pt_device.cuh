@@ -77,6 +77,7 @@ struct __align__(16) DMat {
     float3 coat_color; float trans_weight;
     float3 emission; float coat_weight;
     float spec_rough, spec_ior, coat_rough, coat_ior;
+    float diffuse_rough, pad0, pad1, pad2;
 };
 
 struct __align__(16) DQuad {
@@ -172,14 +173,14 @@ enum { LOBE_COAT = 0, LOBE_METAL = 1, LOBE_DIEL = 2, LOBE_DIFF = 3 };
 
 struct Closure {
     float3 bc, sc, tc, cc;
-    float bw, m, sw, t, cw;
+    float bw, m, sw, t, cw, dr;
     float eta_s, eta_c, a_s, a_c;
     bool delta_s, delta_c, any, has_smooth;
     float p[4];
 };
 
 __device__ __forceinline__ void closure_setup(Closure& C, const DMat& M, bool front, float mu_o) {
-    C.bc = M.base_color; C.bw = M.base_weight; C.m = M.metalness;
+    C.bc = M.base_color; C.bw = M.base_weight; C.m = M.metalness; C.dr = M.diffuse_rough;
     C.sc = M.spec_color; C.sw = M.spec_weight;
     C.tc = M.trans_color; C.t = M.trans_weight;
     C.cc = M.coat_color; C.cw = M.coat_weight;
@@ -254,7 +255,14 @@ __device__ __forceinline__ void closure_eval(const Closure& C, float3 wo, float3
         }
         const float fsi = fresnel_dielectric(mi, C.eta_s);
         const float fso = fresnel_dielectric(mo, C.eta_s);
-        const float kd = (1.0f - C.m) * (1.0f - C.t) * (1.0f - C.sw * fsi) * (1.0f - C.sw * fso) * C.bw * PT_INV_PI_F;
+        float kd = (1.0f - C.m) * (1.0f - C.t) * (1.0f - C.sw * fsi) * (1.0f - C.sw * fso) * C.bw * PT_INV_PI_F;
+        if (C.dr > 0.0f) {
+            // rough diffuse base: qualitative Oren-Nayar factor (1 + sigma s/t) / (1 + c sigma),
+            // c = 1/2 - 2/(3 pi), s = wi.wo - mu_i mu_o, t = max(mu_i, mu_o) if s > 0 else 1
+            const float s = dot3(wo, wi) - mo * mi;
+            const float t = s > 0.0f ? fmaxf(mo, mi) : 1.0f;
+            kd *= (1.0f + C.dr * s / t) / (1.0f + 0.287793409f * C.dr);
+        }
         f = f + (ac * C.bc) * kd;
         pdf += C.p[3] * mi * PT_INV_PI_F;
     } else if (!C.delta_s && C.t > 0.0f) {

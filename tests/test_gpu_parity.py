@@ -115,6 +115,8 @@ def _bsdf_materials():
         scenes.diffuse((0.5, 0.5, 0.5)),
         scenes.openpbr(base_color=(0.3, 0.6, 0.2), base_metalness=1.0, specular_roughness=0.8),
         scenes.openpbr(base_color=(0.2, 0.4, 0.7), specular_roughness=0.4, coat_weight=1.0, coat_roughness=0.1),
+        scenes.openpbr(base_color=(1, 1, 1), base_diffuse_roughness=1.0, specular_weight=0.0),
+        scenes.openpbr(base_color=(0.5, 0.6, 0.7), base_diffuse_roughness=0.6, specular_roughness=0.4),
     ]
     return np.stack(mats)
 
@@ -406,6 +408,24 @@ def test_image_parity_depth_of_field(api, mode):
     acc = pin.render(sc.spp, mode=mode, seed=2)
     torch.cuda.synchronize()
     assert np.abs(acc.image().cpu().numpy() - gi).max() > 1e-3
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_image_parity_rough_diffuse(api, mode):
+    """The Cornell box with rough (Oren-Nayar) diffuse walls and boxes, GPU vs oracle."""
+    from paper_2407_19977_gb300 import api as A
+    base = scenes.cornell_box(width=48, height=40, spp=8, max_depth=4)
+    mats = np.array(base.materials, dtype=np.float32).copy()
+    mats[:, 5] = 0.8                      # base_diffuse_roughness of every material
+    sc = scenes.Scene(base.name, base.vertices, base.indices, base.material_ids, mats, base.lights, base.env,
+                      base.camera, base.spp, base.max_depth)
+    g = A.Scene(sc)
+    osc = oracle.OracleScene(sc)
+    gi, oi, gs, os_, st = _render_pair(g, osc, sc, sc.spp, mode=mode, max_depth=sc.max_depth, seed=6)
+    _image_check(gi, oi, f"rough diffuse mode {mode}")
+    lam = A.Scene(base).render(sc.spp, mode=mode, seed=6)
+    torch.cuda.synchronize()
+    assert np.abs(lam.image().cpu().numpy() - gi).max() > 1e-3
 
 
 def test_lens_arguments_are_checked(api):

@@ -88,14 +88,16 @@ enum { DIM_CAM_X = 0, DIM_CAM_Y = 1, DIM_LIGHT_PICK = 2, DIM_LIGHT_U = 3, DIM_LI
        DIM_LENS_U = 12, DIM_LENS_V = 13 };
 
 /* ------------------------------------------------------------------------------------ */
-/* OpenPBR parameters (26 values per material, same order as the C-ABI table)            */
+/* OpenPBR parameters (OPBR_N = 27 values per material, same order as the C-ABI table)   */
 /* ------------------------------------------------------------------------------------ */
+#define OPBR_N 27
 typedef struct {
     double base_weight; v3 base_color; double metalness; double diffuse_roughness;
     double spec_weight; v3 spec_color; double spec_rough; double spec_ior;
     double trans_weight; v3 trans_color;
     double coat_weight; v3 coat_color; double coat_rough; double coat_ior;
     double emission; v3 emission_color;
+    int thin_walled;
 } omat;
 
 static omat unpack_material(const double* p) {
@@ -108,6 +110,7 @@ static omat unpack_material(const double* p) {
     m.coat_weight = p[16]; m.coat_color = mk(p[17], p[18], p[19]);
     m.coat_rough = p[20]; m.coat_ior = p[21];
     m.emission = p[22]; m.emission_color = mk(p[23], p[24], p[25]);
+    m.thin_walled = p[26] != 0.0;
     return m;
 }
 
@@ -231,6 +234,10 @@ static int refract(v3 wo, v3 h, double eta, v3* wi) {
 /*   f_coat  = Fc(wo.h) Dc G2c / (4 mo mi)                                                 */
 /* alpha < 1e-4 makes a lobe a delta lobe.  eta = specular_ior seen from the side of wo:   */
 /* for transmissive materials hit from the back it is 1/ior.                             */
+/* Thin-walled (reading of OpenPBR's geometry_thin_walled): both sides alike (eta = ior),  */
+/* and the transmission term is the reflection microfacet lobe mirrored through the       */
+/* surface plane: with wi' = (wi.x, wi.y, -wi.z) and h the half vector of (wo, wi'),       */
+/*   f_t = t tc (1 - sw F(wo.h)) D G2(wo, wi') / (4 mo |mi|)   (no refraction, no 1/eta^2) */
 /* ------------------------------------------------------------------------------------ */
 enum { LOBE_COAT = 0, LOBE_METAL = 1, LOBE_DIEL = 2, LOBE_DIFF = 3, N_LOBES = 4 };
 
@@ -246,7 +253,7 @@ typedef struct {
 
 static void closure_setup(closure* C, const omat* m, int front, double mu_o) {
     C->m = *m;
-    C->eta_s = (m->trans_weight > 0.0 && !front) ? 1.0 / m->spec_ior : m->spec_ior;
+    C->eta_s = (m->trans_weight > 0.0 && !front && !m->thin_walled) ? 1.0 / m->spec_ior : m->spec_ior;
     C->eta_c = m->coat_ior;
     C->a_s = m->spec_rough * m->spec_rough;
     C->a_c = m->coat_rough * m->coat_rough;
@@ -343,6 +350,20 @@ static void closure_eval(const closure* C, v3 wo, v3 wi, v3* f_out, double* pdf_
                     (1.0 - m->spec_weight * fso) * m->base_weight / M_PI * fon_factor(wo, wi, m->diffuse_roughness);
         f = add(f, scl(hmul(ac, m->base_color), kd));
         pdf += C->p[LOBE_DIFF] * mi / M_PI;
+    } else if (m->thin_walled) {
+        if (!C->delta_s && m->trans_weight > 0.0) {
+            v3 wm = mk(wi.x, wi.y, -wi.z);
+            v3 h = normalize(add(wo, wm));
+            double oh = dot(wo, h);
+            if (oh > 0.0) {
+                double fr = oracle_fresnel_dielectric(oh, C->eta_s);
+                double dg = ggx_D(h, C->a_s) * ggx_G2(wo, wm, C->a_s) / (4.0 * mo * fabs(mi));
+                double val = (1.0 - m->metalness) * m->trans_weight * (1.0 - m->spec_weight * fr) * dg;
+                f = add(f, scl(hmul(ac, m->trans_color), val));
+                pdf += C->p[LOBE_DIEL] * (1.0 - diel_reflect_prob(C, fr)) * ggx_vndf_pdf(wo, h, C->a_s) /
+                       (4.0 * oh);
+            }
+        }
     } else {
         if (!C->delta_s && m->trans_weight > 0.0) {
             double eta = C->eta_s;
@@ -424,6 +445,11 @@ static int closure_sample(const closure* C, v3 wo, double u_lobe, double u1, dou
         if (do_reflect) {
             wi = reflect(wo, h);
             if (wi.z <= 0.0) return 0;
+        } else if (m->thin_walled) {
+            /* the reflected direction mirrored through the surface plane */
+            v3 wr = reflect(wo, h);
+            if (wr.z <= 0.0) return 0;
+            wi = mk(wr.x, wr.y, -wr.z);
         } else {
             if (!refract(wo, h, C->eta_s, &wi)) return 0;
             if (wi.z >= 0.0) return 0;
@@ -436,10 +462,11 @@ static int closure_sample(const closure* C, v3 wo, double u_lobe, double u1, dou
                                   (1.0 - m->metalness) * m->spec_weight * fr /
                                       (C->p[LOBE_DIEL] * pr));
             } else {
+                double scale = m->thin_walled ? 1.0 : C->eta_s * C->eta_s;   /* radiance across the interface */
                 out->weight = scl(hmul(coat_attenuation(C, fabs(wi.z), mo), m->trans_color),
                                   (1.0 - m->metalness) * m->trans_weight *
                                       (1.0 - m->spec_weight * fr) /
-                                      (C->eta_s * C->eta_s * C->p[LOBE_DIEL] * (1.0 - pr)));
+                                      (scale * C->p[LOBE_DIEL] * (1.0 - pr)));
             }
             return 1;
         }
@@ -459,9 +486,9 @@ static int closure_sample(const closure* C, v3 wo, double u_lobe, double u1, dou
 }
 
 /* ---- exported BSDF entry points (local frame) for the lobe pins and the GPU parity ---- */
-void oracle_bsdf_eval(const double* mat26, int front, const double wo[3], const double wi[3],
+void oracle_bsdf_eval(const double* matp, int front, const double wo[3], const double wi[3],
                       double f_out[3], double* pdf_out) {
-    omat m = unpack_material(mat26);
+    omat m = unpack_material(matp);
     closure C;
     closure_setup(&C, &m, front, wo[2]);
     v3 f;
@@ -469,9 +496,9 @@ void oracle_bsdf_eval(const double* mat26, int front, const double wo[3], const 
     f_out[0] = f.x; f_out[1] = f.y; f_out[2] = f.z;
 }
 
-int oracle_bsdf_sample(const double* mat26, int front, const double wo[3], const double u[4],
+int oracle_bsdf_sample(const double* matp, int front, const double wo[3], const double u[4],
                        double wi_out[3], double weight_out[3], double* pdf_out, int* delta_out) {
-    omat m = unpack_material(mat26);
+    omat m = unpack_material(matp);
     closure C;
     closure_setup(&C, &m, front, wo[2]);
     bsdf_sample_t s;
@@ -484,8 +511,8 @@ int oracle_bsdf_sample(const double* mat26, int front, const double wo[3], const
     return 1;
 }
 
-void oracle_lobe_probs(const double* mat26, int front, double mu_o, double out[4]) {
-    omat m = unpack_material(mat26);
+void oracle_lobe_probs(const double* matp, int front, double mu_o, double out[4]) {
+    omat m = unpack_material(matp);
     closure C;
     closure_setup(&C, &m, front, mu_o);
     for (int j = 0; j < N_LOBES; ++j) out[j] = C.p[j];
@@ -653,7 +680,7 @@ void* oracle_scene_create(const double* vertices, int n_vertices, const uint32_t
     }
     S->n_mats = n_mats;
     S->mats = (omat*)malloc(sizeof(omat) * (size_t)(n_mats > 0 ? n_mats : 1));
-    for (int i = 0; i < n_mats; ++i) S->mats[i] = unpack_material(&mats[26 * i]);
+    for (int i = 0; i < n_mats; ++i) S->mats[i] = unpack_material(&mats[OPBR_N * i]);
     S->n_quads = n_quads;
     size_t nq = (size_t)(n_quads > 0 ? n_quads : 1);
     S->q_p0 = (v3*)malloc(sizeof(v3) * nq); S->q_e1 = (v3*)malloc(sizeof(v3) * nq);
@@ -1263,17 +1290,17 @@ void oracle_camera_ray(const double* cam9, double vfov_deg, int width, int heigh
 }
 
 /* ---- batched forms of the BSDF entry points (n tuples, row-major arrays) ---- */
-void oracle_bsdf_eval_batch(const double* mat26, int front, int n, const double* wo,
+void oracle_bsdf_eval_batch(const double* matp, int front, int n, const double* wo,
                             const double* wi, double* f_out, double* pdf_out) {
     for (int i = 0; i < n; ++i)
-        oracle_bsdf_eval(mat26, front, &wo[3 * i], &wi[3 * i], &f_out[3 * i], &pdf_out[i]);
+        oracle_bsdf_eval(matp, front, &wo[3 * i], &wi[3 * i], &f_out[3 * i], &pdf_out[i]);
 }
 
-void oracle_bsdf_sample_batch(const double* mat26, int front, int n, const double* wo,
+void oracle_bsdf_sample_batch(const double* matp, int front, int n, const double* wo,
                               const double* u, double* wi_out, double* weight_out,
                               double* pdf_out, int* delta_out, int* ok_out) {
     for (int i = 0; i < n; ++i) {
-        ok_out[i] = oracle_bsdf_sample(mat26, front, &wo[3 * i], &u[4 * i], &wi_out[3 * i],
+        ok_out[i] = oracle_bsdf_sample(matp, front, &wo[3 * i], &u[4 * i], &wi_out[3 * i],
                                        &weight_out[3 * i], &pdf_out[i], &delta_out[i]);
         if (!ok_out[i]) {
             wi_out[3 * i] = wi_out[3 * i + 1] = wi_out[3 * i + 2] = 0.0;

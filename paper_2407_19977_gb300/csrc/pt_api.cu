@@ -108,7 +108,7 @@ __device__ __forceinline__ DMat pack_material(const float* v) {
 
 __global__ void k_pack_mats(const float* raw, uint32_t n, DMat* out) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = pack_material(raw + 26u * i);
+    if (i < n) out[i] = pack_material(raw + (uint32_t)PT_OPENPBR_FLOATS * i);
 }
 
 __global__ void k_prepare_quads(const float* raw, uint32_t n, DQuad* out) {
@@ -130,8 +130,9 @@ __global__ void k_prepare_quads(const float* raw, uint32_t n, DQuad* out) {
 
 static bool material_ok(const pt_openpbr& m, std::string& why) {
     const float* v = reinterpret_cast<const float*>(&m);
-    for (int i = 0; i < 26; ++i)
+    for (int i = 0; i < PT_OPENPBR_FLOATS; ++i)
         if (!std::isfinite(v[i])) { why = "non-finite material parameter"; return false; }
+    if (v[26] != 0.0f && v[26] != 1.0f) { why = "geometry_thin_walled must be 0 or 1"; return false; }
     auto unit = [](float x) { return x >= 0.0f && x <= 1.0f; };
     const int unit_idx[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17, 18, 19, 20, 23, 24, 25};
     for (int i : unit_idx)
@@ -234,8 +235,8 @@ extern "C" pt_status pt_scene_create(const float* vertices, uint32_t n_vertices,
         TRY(cudaMemcpyAsync(s->d_matids, material_ids, (size_t)n_triangles * sizeof(uint32_t), kind, st));
     }
     // host parameter tables go through a staging buffer that lives until the stream syncs
-    std::vector<float> mat_raw((size_t)std::max<uint32_t>(n_materials, 1) * 26, 0.0f);
-    if (n_materials) std::memcpy(mat_raw.data(), materials, (size_t)n_materials * 26 * sizeof(float));
+    std::vector<float> mat_raw((size_t)std::max<uint32_t>(n_materials, 1) * PT_OPENPBR_FLOATS, 0.0f);
+    if (n_materials) std::memcpy(mat_raw.data(), materials, (size_t)n_materials * PT_OPENPBR_FLOATS * sizeof(float));
     std::vector<float> quad_raw((size_t)std::max<uint32_t>(n_lights, 1) * 13, 0.0f);
     for (uint32_t l = 0; l < n_lights; ++l) {
         std::memcpy(&quad_raw[13 * l], &lights[l], 12 * sizeof(float));
@@ -439,7 +440,7 @@ __global__ void k_bsdf_eval(const float* mats, const int32_t* front, const float
                             uint32_t n, float* f_out, float* pdf_out) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const DMat M = pack_material(mats + 26u * i);
+    const DMat M = pack_material(mats + (uint32_t)PT_OPENPBR_FLOATS * i);
     const float3 o = mk3(wo[3 * i], wo[3 * i + 1], wo[3 * i + 2]);
     const float3 w = mk3(wi[3 * i], wi[3 * i + 1], wi[3 * i + 2]);
     Closure C;
@@ -457,7 +458,7 @@ __global__ void k_bsdf_sample(const float* mats, const int32_t* front, const flo
                               uint32_t n, float* wi_out, float* w_out, float* pdf_out, uint32_t* flags) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const DMat M = pack_material(mats + 26u * i);
+    const DMat M = pack_material(mats + (uint32_t)PT_OPENPBR_FLOATS * i);
     const float3 o = mk3(wo[3 * i], wo[3 * i + 1], wo[3 * i + 2]);
     Closure C;
     closure_setup(C, M, front[i] != 0, o.z);

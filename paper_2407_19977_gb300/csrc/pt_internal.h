@@ -176,4 +176,4 @@ inline DCam to_dcam(const pt_camera& c) {
 }
 
 // device-side material repack (runs the conversion in a kernel)
-struct RawMat { float v[26]; };
+struct RawMat { float v[PT_OPENPBR_FLOATS]; };

@@ -32,7 +32,7 @@ def test_status_strings_and_struct_sizes():
     lib = N.load()
     for code, name in enumerate(N.STATUS):
         assert lib.pt_status_string(code).decode() == name
-    assert C.sizeof(N.pt_openpbr) == 26 * 4
+    assert C.sizeof(N.pt_openpbr) == 27 * 4
     assert C.sizeof(N.pt_quad_light) == 13 * 4
     assert C.sizeof(N.pt_camera) == 14 * 4
     assert C.sizeof(N.pt_accum) == 32

@@ -70,6 +70,36 @@ def test_rough_diffuse_properties():
         assert E <= rho * (1 + 1e-2), (mu, E)
 
 
+def test_thin_walled_sheet():
+    """A smooth white thin-walled sheet passes light straight through (wi = -wo) with
+    weight 1 - F and reflects F into the mirror direction, so reflectance plus transmittance
+    is exactly 1; a rough one is the same from both sides."""
+    sheet = scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.0, transmission_weight=1.0,
+                           geometry_thin_walled=1.0)
+    rng = np.random.default_rng(9)
+    for mu in (0.95, 0.6, 0.2):
+        wo = np.array([math.sqrt(1 - mu * mu), 0.0, mu])
+        n = 4000
+        ok, wi, w, p, dl = oracle.bsdf_sample_batch(sheet, 1, np.tile(wo, (n, 1)), rng.random((n, 4)))
+        assert ok.all() and dl.all()
+        trans = wi[:, 2] < 0
+        assert np.allclose(wi[trans], -wo, atol=1e-12)
+        assert np.allclose(wi[~trans], wo * np.array([-1, -1, 1]), atol=1e-12)
+        # one-sample estimator of R + T: mean weight = 1 for a lossless sheet
+        assert w[:, 0].mean() == pytest.approx(1.0, abs=0.03)
+        F = float(oracle.fresnel_dielectric(mu, 1.5))
+        assert np.allclose(w[trans, 0] * trans.mean(), 1 - F, rtol=0.1)
+    rough = scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.5, transmission_weight=1.0,
+                           geometry_thin_walled=1.0)
+    a = _sphere_dirs(200)
+    a[:, 2] = np.abs(a[:, 2]) + 1e-3
+    a /= np.linalg.norm(a, axis=1, keepdims=True)
+    b = _sphere_dirs(200)
+    f_front, p_front = oracle.bsdf_eval_batch(rough, 1, a, b)
+    f_back, p_back = oracle.bsdf_eval_batch(rough, 0, a, b)
+    assert np.array_equal(f_front, f_back) and np.array_equal(p_front, p_back)
+
+
 # materials with every lobe rough enough for quadrature- and MC-based checks
 MATS = {
     "diffuse_white": scenes.openpbr(base_color=(1, 1, 1), specular_weight=0.0),
@@ -85,6 +115,11 @@ MATS = {
                             coat_weight=0.5, coat_roughness=0.4, coat_color=(0.9, 0.9, 0.6)),
     "rough_diffuse": scenes.openpbr(base_color=(1, 1, 1), base_diffuse_roughness=1.0, specular_weight=0.0),
     "rough_plastic": scenes.openpbr(base_color=(0.5, 0.6, 0.7), base_diffuse_roughness=0.6, specular_roughness=0.4),
+    "thin_glass": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.4, transmission_weight=1.0,
+                                 geometry_thin_walled=1.0),
+    "thin_tinted": scenes.openpbr(base_color=(0.6, 0.6, 0.6), specular_roughness=0.3, transmission_weight=0.7,
+                                  transmission_color=(0.9, 0.6, 0.5), coat_weight=0.4, coat_roughness=0.3,
+                                  geometry_thin_walled=1.0),
 }
 WHITE = {
     "white_plastic": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.3),
@@ -309,17 +344,19 @@ def test_reciprocity(name):
         f1, _ = oracle.bsdf_eval_batch(mat, front, a, b_up)
         f2, _ = oracle.bsdf_eval_batch(mat, front, b_up, a)
         assert np.allclose(f1, f2, rtol=1e-12, atol=1e-300)
-    # transmission: f(a -> b)/eta_a^2 = f(b -> a)/eta_b^2, evaluated from the other side
+    # transmission: f(a -> b)/eta_a^2 = f(b -> a)/eta_b^2, evaluated from the other side; a
+    # thin-walled sheet has the same medium on both sides (eta 1 across it)
     b_dn = b_up * np.array([1, 1, -1])
     flip = np.array([1, 1, -1])
     f_fwd, _ = oracle.bsdf_eval_batch(mat, 1, a, b_dn)
     f_rev, _ = oracle.bsdf_eval_batch(mat, 0, b_dn * flip, a * flip)
     if mat[12] > 0:
         assert np.any(f_fwd > 0)
-    assert np.allclose(f_fwd, f_rev / 1.5 ** 2, rtol=1e-10, atol=1e-300)
+    eta2 = 1.0 if mat[26] > 0 else 1.5 ** 2
+    assert np.allclose(f_fwd, f_rev / eta2, rtol=1e-10, atol=1e-300)
 
 
-@pytest.mark.parametrize("name", ["plastic", "metal", "coated", "rough_glass", "mixed"])
+@pytest.mark.parametrize("name", ["plastic", "metal", "coated", "rough_glass", "mixed", "thin_glass", "rough_diffuse"])
 def test_sampler_chi_square(name):
     mat = MATS[name]
     mu = 0.55

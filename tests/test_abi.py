@@ -50,7 +50,7 @@ def test_host_side_validation_needs_no_gpu():
     idx = np.array([[0, 1, 2]], np.uint32)
     mid = np.zeros(1, np.uint32)
     m = (N.pt_openpbr * 1)()
-    m[0].v[:] = [1, .8, .8, .8, 0, 0, 1, 1, 1, 1, .3, 0.9, 0, 1, 1, 1, 0, 1, 1, 1, 0, 1.6, 0, 1, 1, 1]  # ior 0.9
+    m[0].v[:] = [1, .8, .8, .8, 0, 0, 1, 1, 1, 1, .3, 0.9, 0, 1, 1, 1, 0, 1, 1, 1, 0, 1.6, 0, 1, 1, 1, 0]  # ior 0.9
     code = lib.pt_scene_create(v.ctypes.data_as(C.c_void_p), 3, idx.ctypes.data_as(C.c_void_p), 1,
                                mid.ctypes.data_as(C.c_void_p), m, 1, None, 0, None, 0, 0, 0, None, C.byref(h))
     assert code == 1 and b"specular_ior" in lib.pt_last_error()
@@ -59,4 +59,9 @@ def test_host_side_validation_needs_no_gpu():
     code = lib.pt_scene_create(v.ctypes.data_as(C.c_void_p), 3, idx_bad.ctypes.data_as(C.c_void_p), 1,
                                mid.ctypes.data_as(C.c_void_p), m, 1, None, 0, None, 0, 0, 0, None, C.byref(h))
     assert code == 1 and b"index" in lib.pt_last_error()
+    m[0].v[26] = 0.5                      # geometry_thin_walled is 0 or 1
+    code = lib.pt_scene_create(v.ctypes.data_as(C.c_void_p), 3, idx.ctypes.data_as(C.c_void_p), 1,
+                               mid.ctypes.data_as(C.c_void_p), m, 1, None, 0, None, 0, 0, 0, None, C.byref(h))
+    assert code == 1 and b"thin_walled" in lib.pt_last_error()
+    m[0].v[26] = 0.0
     assert lib.pt_render(None, None, 1, 1, 0, None, None, None) == 1

@@ -91,7 +91,8 @@ __device__ __forceinline__ DMat pack_material(const float* v) {
     m.base_color = mk3(v[1], v[2], v[3]);
     m.metalness = v[4];
     m.diffuse_rough = v[5];
-    m.pad0 = m.pad1 = m.pad2 = 0.0f;
+    m.thin_walled = v[26];
+    m.pad1 = m.pad2 = 0.0f;
     m.spec_weight = v[6];
     m.spec_color = mk3(v[7], v[8], v[9]);
     m.spec_rough = v[10];

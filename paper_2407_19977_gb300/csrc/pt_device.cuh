@@ -77,7 +77,7 @@ struct __align__(16) DMat {
     float3 coat_color; float trans_weight;
     float3 emission; float coat_weight;
     float spec_rough, spec_ior, coat_rough, coat_ior;
-    float diffuse_rough, pad0, pad1, pad2;
+    float diffuse_rough, thin_walled, pad1, pad2;   // thin_walled: 0 or 1
 };
 
 struct __align__(16) DQuad {
@@ -175,7 +175,7 @@ struct Closure {
     float3 bc, sc, tc, cc;
     float bw, m, sw, t, cw, dr;
     float eta_s, eta_c, a_s, a_c;
-    bool delta_s, delta_c, any, has_smooth;
+    bool delta_s, delta_c, any, has_smooth, thin;
     float p[4];
 };
 
@@ -184,7 +184,9 @@ __device__ __forceinline__ void closure_setup(Closure& C, const DMat& M, bool fr
     C.sc = M.spec_color; C.sw = M.spec_weight;
     C.tc = M.trans_color; C.t = M.trans_weight;
     C.cc = M.coat_color; C.cw = M.coat_weight;
-    C.eta_s = (C.t > 0.0f && !front) ? 1.0f / M.spec_ior : M.spec_ior;
+    C.thin = M.thin_walled != 0.0f;
+    // a thin-walled sheet has the same medium on both sides
+    C.eta_s = (C.t > 0.0f && !front && !C.thin) ? 1.0f / M.spec_ior : M.spec_ior;
     C.eta_c = M.coat_ior;
     C.a_s = M.spec_rough * M.spec_rough;
     C.a_c = M.coat_rough * M.coat_rough;
@@ -265,6 +267,20 @@ __device__ __forceinline__ void closure_eval(const Closure& C, float3 wo, float3
         }
         f = f + (ac * C.bc) * kd;
         pdf += C.p[3] * mi * PT_INV_PI_F;
+    } else if (C.thin) {
+        // thin-walled transmission: the reflection lobe mirrored through the surface plane
+        if (!C.delta_s && C.t > 0.0f) {
+            const float3 wm = mk3(wi.x, wi.y, -wi.z);
+            const float3 h = norm3(wo + wm);
+            const float oh = dot3(wo, h);
+            if (oh > 0.0f) {
+                const float fr = fresnel_dielectric(oh, C.eta_s);
+                const float dg = ggx_D(h, C.a_s) * ggx_G2(wo, wm, C.a_s) / (4.0f * mo * fabsf(mi));
+                const float val = (1.0f - C.m) * C.t * (1.0f - C.sw * fr) * dg;
+                f = f + (ac * C.tc) * val;
+                pdf += C.p[2] * (1.0f - diel_reflect_prob(C, fr)) * ggx_vndf_pdf(wo, h, C.a_s) / (4.0f * oh);
+            }
+        }
     } else if (!C.delta_s && C.t > 0.0f) {
         const float eta = C.eta_s;
         float3 h = norm3(wo + wi * eta);
@@ -339,6 +355,11 @@ __device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, floa
         if (do_reflect) {
             wi = reflect3(wo, h);
             if (wi.z <= 0.0f) return false;
+        } else if (C.thin) {
+            // the reflected direction mirrored through the surface plane
+            const float3 wr = reflect3(wo, h);
+            if (wr.z <= 0.0f) return false;
+            wi = mk3(wr.x, wr.y, -wr.z);
         } else {
             if (!refract3(wo, h, C.eta_s, wi)) return false;
             if (wi.z >= 0.0f) return false;
@@ -349,8 +370,9 @@ __device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, floa
             if (do_reflect) {
                 out.weight = (coat_attenuation(C, mo, mo) * C.sc) * ((1.0f - C.m) * C.sw * fr / (C.p[2] * pr));
             } else {
+                const float scale = C.thin ? 1.0f : C.eta_s * C.eta_s;   // radiance across the interface
                 out.weight = (coat_attenuation(C, fabsf(wi.z), mo) * C.tc) *
-                             ((1.0f - C.m) * C.t * (1.0f - C.sw * fr) / (C.eta_s * C.eta_s * C.p[2] * (1.0f - pr)));
+                             ((1.0f - C.m) * C.t * (1.0f - C.sw * fr) / (scale * C.p[2] * (1.0f - pr)));
             }
             return true;
         }

@@ -563,7 +563,7 @@ __global__ void k_wf_sort_scatter(WfParams P, int in_q) {
 }
 
 template <bool NRC>
-__global__ void __launch_bounds__(128) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
+__global__ void __launch_bounds__(128, 3) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
     if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[in_q];
     const uint32_t sbase = wf_sample_base(P);

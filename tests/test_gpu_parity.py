@@ -117,6 +117,9 @@ def _bsdf_materials():
         scenes.openpbr(base_color=(0.2, 0.4, 0.7), specular_roughness=0.4, coat_weight=1.0, coat_roughness=0.1),
         scenes.openpbr(base_color=(1, 1, 1), base_diffuse_roughness=1.0, specular_weight=0.0),
         scenes.openpbr(base_color=(0.5, 0.6, 0.7), base_diffuse_roughness=0.6, specular_roughness=0.4),
+        scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.4, transmission_weight=1.0, geometry_thin_walled=1.0),
+        scenes.openpbr(base_color=(0.6, 0.6, 0.6), specular_roughness=0.3, transmission_weight=0.7,
+                       transmission_color=(0.9, 0.6, 0.5), coat_weight=0.4, coat_roughness=0.3, geometry_thin_walled=1.0),
     ]
     return np.stack(mats)
 
@@ -192,8 +195,11 @@ def test_bsdf_sample_parity(api):
             dl_g = (fl_g & 2).astype(bool)
             agree = (ok_g == ok_o) & (dl_g == dl_o)
             # seen from inside a transmissive material, the reflect/refract decision uses a
-            # Fresnel term next to total internal reflection: its flips are rarer than 0.5 %
-            need = 0.995 if (front == 0 and m[12] > 0) else 0.999
+            # Fresnel term next to total internal reflection: its flips are rarer than 0.5 %.
+            # A thin-walled sheet's transmitted samples all rebuild the half vector from
+            # wo + mirror(wi), of length 2 wo.h, which loses relative precision on grazing
+            # microfacets: their weights may differ beyond 1e-4 on up to 0.2 %
+            need = 0.995 if (front == 0 and m[12] > 0) else (0.998 if m[26] > 0 else 0.999)
             assert agree.mean() >= need, (m_i, front, agree.mean())
             sel = agree & ok_o
             wi_g = wi_g.cpu().numpy()[sel]
@@ -426,6 +432,30 @@ def test_image_parity_rough_diffuse(api, mode):
     lam = A.Scene(base).render(sc.spp, mode=mode, seed=6)
     torch.cuda.synchronize()
     assert np.abs(lam.image().cpu().numpy() - gi).max() > 1e-3
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_image_parity_thin_walled(api, mode):
+    """A thin-walled rough glass pane hanging in the Cornell box between the camera and the
+    boxes (light passes through without refraction), GPU vs oracle.  (Boxes made of glass
+    would not do: their edges and interfaces let FP32 and FP64 paths part ways on about 1 %
+    of the paths, thin-walled or not.)"""
+    from paper_2407_19977_gb300 import api as A
+    base = scenes.cornell_box(width=48, height=40, spp=8, max_depth=6)
+    mats = np.concatenate([np.array(base.materials, dtype=np.float32),
+                           scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.25, transmission_weight=1.0,
+                                          transmission_color=(0.95, 0.9, 0.8), geometry_thin_walled=1.0)[None]])
+    nv = len(base.vertices)
+    pane = np.array([[0.2, 0.15, 0.35], [0.8, 0.15, 0.35], [0.8, 0.75, 0.35], [0.2, 0.75, 0.35]], np.float32)
+    verts = np.concatenate([np.asarray(base.vertices, np.float32), pane])
+    idx = np.concatenate([np.asarray(base.indices, np.uint32),
+                          np.array([[nv, nv + 2, nv + 1], [nv, nv + 3, nv + 2]], np.uint32)])
+    mid = np.concatenate([np.asarray(base.material_ids, np.uint32), np.full(2, len(mats) - 1, np.uint32)])
+    sc = scenes.Scene(base.name, verts, idx, mid, mats, base.lights, base.env, base.camera, base.spp, base.max_depth)
+    g = A.Scene(sc)
+    osc = oracle.OracleScene(sc)
+    gi, oi, gs, os_, st = _render_pair(g, osc, sc, sc.spp, mode=mode, max_depth=sc.max_depth, seed=8)
+    _samples_check(gs, os_, f"thin-walled pane mode {mode}")
 
 
 def test_lens_arguments_are_checked(api):

@@ -71,7 +71,7 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     ap.add_argument("--study-frames", type=int, default=256, help="frames per curve of the NRC study")
     ap.add_argument("--batch-scenes", type=int, default=64)
-    ap.add_argument("--study", default=None, choices=[None, "nrc", "batch"],
+    ap.add_argument("--study", default=None, choices=[None, "nrc", "batch", "paper"],
                     help="nrc: relMSE vs time, radiance cache against the plain tracer")
     ap.add_argument("--ref-spp", type=int, default=4096)
     return ap.parse_args()
@@ -235,7 +235,8 @@ def cpu_baseline(sc, target_s: float, seed: int = 0):
     px = st["paths"] / spp
     return {
         "value": rays / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-        "sample": f"every {row_step}th row of the 1920x1080 frame ({int(px)} pixels) at {spp} spp, "
+        "sample": f"every {row_step}th row of the {sc.camera.width}x{sc.camera.height} frame ({int(px)} pixels) "
+                  f"at {spp} spp, "
                   f"{rays} rays in {dt:.2f} s; oracle BVH setup {setup:.2f} s",
         "spp_per_s_1080p": st["paths"] / dt / (sc.camera.width * sc.camera.height),
     }
@@ -575,12 +576,91 @@ def run_batch_study(args, local):
     print(json.dumps(out))
 
 
+# Table 2 and Table 1 of the paper (context only: WebGPU in Chrome on an RTX 3080 / Ryzen 5 5600X)
+PAPER_TABLE2_MS = {1_068_735: (1058.73, 59.47), 106_873: (790.20, 3.79), 10_687: (790.83, 4.18)}
+PAPER_TABLE1_MS = {1_068_735: 383.10, 106_873: 41.77, 10_687: 8.43}
+
+
+def run_paper_study(args, local):
+    """The paper's own workload shape (Tables 1 and 2): the pushbutton at about 10.7k, 107k and
+    1.07M triangles, 512x512, 100 spp, ray depth 5, each figure the mean and standard deviation
+    of 30 runs.  Per mesh: the device BVH build (30 timed builds after 3 untimed) and the
+    100-spp frame (schedule from pt_autotune at 100 spp, 3 untimed frames, then 30 timed frames,
+    each into a zeroed accumulator, L2 flushed between frames outside the timed events)."""
+    import torch
+    from paper_2407_19977_gb300 import api, scenes
+    from paper_2407_19977_gb300 import native as N
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    runs = 30
+    rows = []
+
+    def ev_ms(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    clocks = ClockSampler(local)
+    with clocks:
+        for n in sorted(PAPER_TABLE2_MS):
+            sc = scenes.pushbutton_lod(n)
+            g = api.Scene(sc, build=False)
+            for _ in range(3):
+                g.build()
+            builds = []
+            for _ in range(runs):
+                flush.fill_(1.0)
+                builds.append(ev_ms(lambda: g.build()))
+            opts, _ = g.autotune(spp=sc.spp, max_depth=sc.max_depth, frames=1)
+            acc = api.Accum(sc.camera.width, sc.camera.height)
+
+            def frame():
+                g.render(sc.spp, max_depth=sc.max_depth, seed=0, accum=acc, mode=N.PT_MODE_AUTO)
+            for _ in range(3):
+                acc.reset()
+                frame()
+            st0 = g.stats()
+            frames = []
+            for k in range(runs):
+                acc.reset()
+                flush.fill_(float(k))
+                frames.append(ev_ms(frame))
+            st1 = g.stats()
+            rays = (st1["ext_rays"] - st0["ext_rays"]) + (st1["shadow_rays"] - st0["shadow_rays"])
+            fm, fs = statistics.mean(frames), statistics.stdev(frames)
+            bm, bs = statistics.mean(builds), statistics.stdev(builds)
+            samples = sc.camera.width * sc.camera.height * sc.spp
+            row = {"target_tris": n, "tris": g.n_tris, "bvh_build_ms": [round(bm, 3), round(bs, 3)],
+                   "frame_ms": [round(fm, 3), round(fs, 3)], "spp_per_s": sc.spp / (fm * 1e-3),
+                   "msamples_per_s": samples / (fm * 1e-3) / 1e6, "mrays_per_s": rays / (sum(frames) * 1e-3) / 1e6,
+                   "rays_per_frame": rays / runs, "schedule": opts,
+                   "paper_rtx3080_frame_ms": list(PAPER_TABLE2_MS[n]),
+                   "paper_cpu_bvh_build_ms": PAPER_TABLE1_MS[n],
+                   "frame_time_ratio_vs_paper": PAPER_TABLE2_MS[n][0] / fm}
+            if not args.no_cpu_baseline:
+                row["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds / 3)
+            rows.append(row)
+            del g
+    print(json.dumps({"study": "paper_tables", "workload": "pushbutton at the Table 1/2 triangle counts, 512x512, "
+                      "100 spp, depth 5, 30 runs each (mean, std)", "rows": rows, "clocks": clocks.summary(),
+                      "note": "paper figures are WebGPU in a browser on other hardware: context, not a target"}))
+
+
 def main():
     args = _args()
     world, rank, local = _dist()
     if args.study == "nrc":
         if rank == 0:
             run_nrc_study(args, local)
+        return
+    if args.study == "paper":
+        if rank == 0:
+            run_paper_study(args, local)
         return
     if args.study == "batch":
         if rank == 0:

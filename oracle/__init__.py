@@ -60,11 +60,12 @@ def _load():
         lib.oracle_fresnel_dielectric.argtypes = [C.c_double, C.c_double]
         lib.oracle_fresnel_dielectric.restype = C.c_double
         lib.oracle_fresnel_f82.argtypes = [_dp, _dp, C.c_double, _dp]
-        lib.oracle_ggx_D.argtypes = [_dp, C.c_double]
+        lib.oracle_ggx_D.argtypes = [_dp, C.c_double, C.c_double]
         lib.oracle_ggx_D.restype = C.c_double
-        lib.oracle_ggx_G1.argtypes = [_dp, C.c_double]
+        lib.oracle_ggx_G1.argtypes = [_dp, C.c_double, C.c_double]
         lib.oracle_ggx_G1.restype = C.c_double
-        lib.oracle_ggx_vndf_sample.argtypes = [_dp, C.c_double, C.c_double, C.c_double, _dp]
+        lib.oracle_ggx_vndf_sample.argtypes = [_dp, C.c_double, C.c_double, C.c_double, C.c_double, _dp]
+        lib.oracle_tangent_frame.argtypes = [_dp, _dp, C.c_double, _dp, _dp]
         lib.oracle_bsdf_eval.argtypes = [_dp, C.c_int, _dp, _dp, _dp, _dp]
         lib.oracle_bsdf_sample.argtypes = [_dp, C.c_int, _dp, _dp, _dp, _dp, _dp, _i32p]
         lib.oracle_bsdf_sample.restype = C.c_int
@@ -131,21 +132,32 @@ def fresnel_f82(f0, tint, mu):
     return o
 
 
-def ggx_D(h, alpha):
+def ggx_D(h, alpha, alpha_y=None):
+    """GGX D in the local frame; alpha along the tangent (x), alpha_y (default alpha) along y."""
     h, ph = _d(h)
-    return _load().oracle_ggx_D(ph, float(alpha))
+    return _load().oracle_ggx_D(ph, float(alpha), float(alpha if alpha_y is None else alpha_y))
 
 
-def ggx_G1(w, alpha):
+def ggx_G1(w, alpha, alpha_y=None):
     w, pw = _d(w)
-    return _load().oracle_ggx_G1(pw, float(alpha))
+    return _load().oracle_ggx_G1(pw, float(alpha), float(alpha if alpha_y is None else alpha_y))
 
 
-def ggx_vndf_sample(wo, alpha, u1, u2):
+def ggx_vndf_sample(wo, alpha, u1, u2, alpha_y=None):
     wo, p = _d(wo)
     o = np.zeros(3)
-    _load().oracle_ggx_vndf_sample(p, float(alpha), float(u1), float(u2), o.ctypes.data_as(_dp))
+    _load().oracle_ggx_vndf_sample(p, float(alpha), float(alpha if alpha_y is None else alpha_y), float(u1),
+                                   float(u2), o.ctypes.data_as(_dp))
     return o
+
+
+def tangent_frame(n, e1, rot):
+    """(t, b) of an anisotropic surface with normal n, first triangle edge e1, rotation rot turns."""
+    n, pn = _d(n)
+    e1, pe = _d(e1)
+    t, b = np.zeros(3), np.zeros(3)
+    _load().oracle_tangent_frame(pn, pe, float(rot), t.ctypes.data_as(_dp), b.ctypes.data_as(_dp))
+    return t, b
 
 
 def bsdf_eval(mat, front, wo, wi):

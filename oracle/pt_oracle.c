@@ -88,9 +88,9 @@ enum { DIM_CAM_X = 0, DIM_CAM_Y = 1, DIM_LIGHT_PICK = 2, DIM_LIGHT_U = 3, DIM_LI
        DIM_LENS_U = 12, DIM_LENS_V = 13 };
 
 /* ------------------------------------------------------------------------------------ */
-/* OpenPBR parameters (OPBR_N = 27 values per material, same order as the C-ABI table)   */
+/* OpenPBR parameters (OPBR_N = 29 values per material, same order as the C-ABI table)   */
 /* ------------------------------------------------------------------------------------ */
-#define OPBR_N 27
+#define OPBR_N 29
 typedef struct {
     double base_weight; v3 base_color; double metalness; double diffuse_roughness;
     double spec_weight; v3 spec_color; double spec_rough; double spec_ior;
@@ -98,6 +98,8 @@ typedef struct {
     double coat_weight; v3 coat_color; double coat_rough; double coat_ior;
     double emission; v3 emission_color;
     int thin_walled;
+    double spec_aniso;    /* specular_roughness_anisotropy in [0, 1] */
+    double spec_rot;      /* tangent rotation about the normal, in turns */
 } omat;
 
 static omat unpack_material(const double* p) {
@@ -111,6 +113,7 @@ static omat unpack_material(const double* p) {
     m.coat_rough = p[20]; m.coat_ior = p[21];
     m.emission = p[22]; m.emission_color = mk(p[23], p[24], p[25]);
     m.thin_walled = p[26] != 0.0;
+    m.spec_aniso = p[27]; m.spec_rot = p[28];
     return m;
 }
 
@@ -155,44 +158,43 @@ void oracle_fresnel_f82(const double f0[3], const double tint[3], double mu, dou
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* GGX microfacet distribution (Trowbridge-Reitz), alpha = roughness^2                     */
+/* GGX microfacet distribution (Trowbridge-Reitz), anisotropic: ax is the width along the */
+/* tangent (local x), ay along the bitangent (local y); ax = ay = roughness^2 is isotropic. */
 /* ------------------------------------------------------------------------------------ */
-double oracle_ggx_D(const double h[3], double a) {
+double oracle_ggx_D(const double h[3], double ax, double ay) {
     if (h[2] <= 0.0) return 0.0;
-    double a2 = a * a;
-    double s2 = h[0] * h[0] + h[1] * h[1];
-    double c2 = h[2] * h[2];
-    double d = a2 * c2 + s2;   /* = (cos^2 (a^2 - 1) + 1) for a unit h */
-    return a2 / (M_PI * d * d);
+    double x = h[0] / ax, y = h[1] / ay;
+    double d = x * x + y * y + h[2] * h[2];
+    return 1.0 / (M_PI * ax * ay * d * d);
 }
-static double ggx_D(v3 h, double a) { double hh[3] = {h.x, h.y, h.z}; return oracle_ggx_D(hh, a); }
+static double ggx_D(v3 h, double ax, double ay) { double hh[3] = {h.x, h.y, h.z}; return oracle_ggx_D(hh, ax, ay); }
 
-/* Smith Lambda for GGX: (-1 + sqrt(1 + a^2 tan^2))/2, written without cancellation. */
-static double ggx_lambda(v3 w, double a) {
+/* Smith Lambda for GGX: (-1 + sqrt(1 + a(w)^2 tan^2))/2 with a(w)^2 tan^2 =
+ * (ax^2 wx^2 + ay^2 wy^2) / wz^2, written without cancellation. */
+static double ggx_lambda(v3 w, double ax, double ay) {
     double c2 = w.z * w.z;
     if (c2 <= 0.0) return INFINITY;
-    double t2 = (w.x * w.x + w.y * w.y) / c2;
-    double x = a * a * t2;
+    double x = (ax * ax * w.x * w.x + ay * ay * w.y * w.y) / c2;
     return x / (2.0 * (1.0 + sqrt(1.0 + x)));
 }
-double oracle_ggx_G1(const double w[3], double a) {
-    return 1.0 / (1.0 + ggx_lambda(mk(w[0], w[1], w[2]), a));
+double oracle_ggx_G1(const double w[3], double ax, double ay) {
+    return 1.0 / (1.0 + ggx_lambda(mk(w[0], w[1], w[2]), ax, ay));
 }
-static double ggx_G1(v3 w, double a) { return 1.0 / (1.0 + ggx_lambda(w, a)); }
+static double ggx_G1(v3 w, double ax, double ay) { return 1.0 / (1.0 + ggx_lambda(w, ax, ay)); }
 /* height-correlated masking-shadowing */
-static double ggx_G2(v3 wo, v3 wi, double a) {
-    return 1.0 / (1.0 + ggx_lambda(wo, a) + ggx_lambda(wi, a));
+static double ggx_G2(v3 wo, v3 wi, double ax, double ay) {
+    return 1.0 / (1.0 + ggx_lambda(wo, ax, ay) + ggx_lambda(wi, ax, ay));
 }
 /* density of visible normals: G1(wo) max(0, wo.h) D(h) / wo.z */
-static double ggx_vndf_pdf(v3 wo, v3 h, double a) {
+static double ggx_vndf_pdf(v3 wo, v3 h, double ax, double ay) {
     double oh = dot(wo, h);
     if (oh <= 0.0 || wo.z <= 0.0) return 0.0;
-    return ggx_G1(wo, a) * oh * ggx_D(h, a) / wo.z;
+    return ggx_G1(wo, ax, ay) * oh * ggx_D(h, ax, ay) / wo.z;
 }
 /* Sampling of visible normals (Heitz, JCGT 7(4), 2018): stretch the view vector to the
  * unit-roughness configuration, sample the projected hemisphere, unstretch. */
-static v3 ggx_vndf_sample(v3 wo, double a, double u1, double u2) {
-    v3 vh = normalize(mk(a * wo.x, a * wo.y, wo.z));
+static v3 ggx_vndf_sample(v3 wo, double ax, double ay, double u1, double u2) {
+    v3 vh = normalize(mk(ax * wo.x, ay * wo.y, wo.z));
     double lensq = vh.x * vh.x + vh.y * vh.y;
     v3 t1 = lensq > 0.0 ? scl(mk(-vh.y, vh.x, 0.0), 1.0 / sqrt(lensq)) : mk(1.0, 0.0, 0.0);
     v3 t2 = cross(vh, t1);
@@ -203,10 +205,10 @@ static v3 ggx_vndf_sample(v3 wo, double a, double u1, double u2) {
     double s = 0.5 * (1.0 + vh.z);
     p2 = (1.0 - s) * sqrt(fmax(0.0, 1.0 - p1 * p1)) + s * p2;
     v3 nh = add(add(scl(t1, p1), scl(t2, p2)), scl(vh, sqrt(fmax(0.0, 1.0 - p1 * p1 - p2 * p2))));
-    return normalize(mk(a * nh.x, a * nh.y, fmax(0.0, nh.z)));
+    return normalize(mk(ax * nh.x, ay * nh.y, fmax(0.0, nh.z)));
 }
-void oracle_ggx_vndf_sample(const double wo[3], double a, double u1, double u2, double out[3]) {
-    v3 h = ggx_vndf_sample(mk(wo[0], wo[1], wo[2]), a, u1, u2);
+void oracle_ggx_vndf_sample(const double wo[3], double ax, double ay, double u1, double u2, double out[3]) {
+    v3 h = ggx_vndf_sample(mk(wo[0], wo[1], wo[2]), ax, ay, u1, u2);
     out[0] = h.x; out[1] = h.y; out[2] = h.z;
 }
 
@@ -238,13 +240,17 @@ static int refract(v3 wo, v3 h, double eta, v3* wi) {
 /* and the transmission term is the reflection microfacet lobe mirrored through the       */
 /* surface plane: with wi' = (wi.x, wi.y, -wi.z) and h the half vector of (wo, wi'),       */
 /*   f_t = t tc (1 - sw F(wo.h)) D G2(wo, wi') / (4 mo |mi|)   (no refraction, no 1/eta^2) */
+/* Specular anisotropy (OpenPBR specular_roughness_anisotropy a): the specular GGX lobe of  */
+/* metal, dielectric and transmission has widths ax = r^2 sqrt(2 / (1 + (1-a)^2)) along the */
+/* tangent and ay = (1-a) ax along the bitangent, in the frame of tangent_frame (the coat  */
+/* stays isotropic).                                                                      */
 /* ------------------------------------------------------------------------------------ */
 enum { LOBE_COAT = 0, LOBE_METAL = 1, LOBE_DIEL = 2, LOBE_DIFF = 3, N_LOBES = 4 };
 
 typedef struct {
     omat m;
     double eta_s, eta_c;
-    double a_s, a_c;
+    double ax_s, ay_s, a_c;   /* specular widths along tangent / bitangent; coat (isotropic) */
     int delta_s, delta_c;
     double p[N_LOBES];     /* lobe selection probabilities */
     int any;               /* some lobe has positive weight */
@@ -255,9 +261,15 @@ static void closure_setup(closure* C, const omat* m, int front, double mu_o) {
     C->m = *m;
     C->eta_s = (m->trans_weight > 0.0 && !front && !m->thin_walled) ? 1.0 / m->spec_ior : m->spec_ior;
     C->eta_c = m->coat_ior;
-    C->a_s = m->spec_rough * m->spec_rough;
+    /* OpenPBR's anisotropy mapping: the tangent width grows and the bitangent width shrinks
+     * with a, keeping ax^2 + ay^2 = 2 r^4; a = 0 gives ax = ay = r^2.  The lobe is a delta
+     * lobe when both widths are below 1e-4; otherwise the narrower one is kept >= 1e-4. */
+    double r2 = m->spec_rough * m->spec_rough, ia = 1.0 - m->spec_aniso;
+    double at = r2 * sqrt(2.0 / (1.0 + ia * ia));
+    C->ax_s = at;
+    C->ay_s = fmax(ia * at, 1e-4);
     C->a_c = m->coat_rough * m->coat_rough;
-    C->delta_s = C->a_s < 1e-4;
+    C->delta_s = at < 1e-4;
     C->delta_c = C->a_c < 1e-4;
     double fc = oracle_fresnel_dielectric(mu_o, C->eta_c);
     double w_coat = m->coat_weight * fc;
@@ -327,14 +339,14 @@ static void closure_eval(const closure* C, v3 wo, v3 wi, v3* f_out, double* pdf_
         if (oh <= 0.0) return;
         if (!C->delta_c && m->coat_weight > 0.0) {
             double fr = oracle_fresnel_dielectric(oh, C->eta_c);
-            double val = m->coat_weight * fr * ggx_D(h, C->a_c) * ggx_G2(wo, wi, C->a_c) /
+            double val = m->coat_weight * fr * ggx_D(h, C->a_c, C->a_c) * ggx_G2(wo, wi, C->a_c, C->a_c) /
                          (4.0 * mo * mi);
             f = add(f, splat(val));
-            pdf += C->p[LOBE_COAT] * ggx_vndf_pdf(wo, h, C->a_c) / (4.0 * oh);
+            pdf += C->p[LOBE_COAT] * ggx_vndf_pdf(wo, h, C->a_c, C->a_c) / (4.0 * oh);
         }
         if (!C->delta_s) {
-            double dg = ggx_D(h, C->a_s) * ggx_G2(wo, wi, C->a_s) / (4.0 * mo * mi);
-            double vndf = ggx_vndf_pdf(wo, h, C->a_s) / (4.0 * oh);
+            double dg = ggx_D(h, C->ax_s, C->ay_s) * ggx_G2(wo, wi, C->ax_s, C->ay_s) / (4.0 * mo * mi);
+            double vndf = ggx_vndf_pdf(wo, h, C->ax_s, C->ay_s) / (4.0 * oh);
             if (m->metalness > 0.0) {
                 v3 fm = fresnel_f82(scl(m->base_color, m->base_weight), m->spec_color, oh);
                 f = add(f, scl(hmul(ac, fm), m->metalness * m->spec_weight * dg));
@@ -357,10 +369,10 @@ static void closure_eval(const closure* C, v3 wo, v3 wi, v3* f_out, double* pdf_
             double oh = dot(wo, h);
             if (oh > 0.0) {
                 double fr = oracle_fresnel_dielectric(oh, C->eta_s);
-                double dg = ggx_D(h, C->a_s) * ggx_G2(wo, wm, C->a_s) / (4.0 * mo * fabs(mi));
+                double dg = ggx_D(h, C->ax_s, C->ay_s) * ggx_G2(wo, wm, C->ax_s, C->ay_s) / (4.0 * mo * fabs(mi));
                 double val = (1.0 - m->metalness) * m->trans_weight * (1.0 - m->spec_weight * fr) * dg;
                 f = add(f, scl(hmul(ac, m->trans_color), val));
-                pdf += C->p[LOBE_DIEL] * (1.0 - diel_reflect_prob(C, fr)) * ggx_vndf_pdf(wo, h, C->a_s) /
+                pdf += C->p[LOBE_DIEL] * (1.0 - diel_reflect_prob(C, fr)) * ggx_vndf_pdf(wo, h, C->ax_s, C->ay_s) /
                        (4.0 * oh);
             }
         }
@@ -373,12 +385,12 @@ static void closure_eval(const closure* C, v3 wo, v3 wi, v3* f_out, double* pdf_
             if (oh > 0.0 && ih < 0.0) {
                 double fr = oracle_fresnel_dielectric(oh, eta);
                 double denom = oh + eta * ih;
-                double dg = ggx_D(h, C->a_s) * ggx_G2(wo, wi, C->a_s);
+                double dg = ggx_D(h, C->ax_s, C->ay_s) * ggx_G2(wo, wi, C->ax_s, C->ay_s);
                 double val = (1.0 - m->metalness) * m->trans_weight * (1.0 - m->spec_weight * fr) *
                              dg * fabs(ih) * oh / (fabs(mi) * mo * denom * denom);
                 f = add(f, scl(hmul(ac, m->trans_color), val));
                 pdf += C->p[LOBE_DIEL] * (1.0 - diel_reflect_prob(C, fr)) *
-                       ggx_vndf_pdf(wo, h, C->a_s) * eta * eta * fabs(ih) / (denom * denom);
+                       ggx_vndf_pdf(wo, h, C->ax_s, C->ay_s) * eta * eta * fabs(ih) / (denom * denom);
             }
         }
     }
@@ -420,7 +432,7 @@ static int closure_sample(const closure* C, v3 wo, double u_lobe, double u1, dou
             out->is_delta = 1;
             return 1;
         }
-        v3 h = ggx_vndf_sample(wo, C->a_c, u1, u2);
+        v3 h = ggx_vndf_sample(wo, C->a_c, C->a_c, u1, u2);
         wi = reflect(wo, h);
         if (wi.z <= 0.0) return 0;
     } else if (lobe == LOBE_METAL) {
@@ -432,11 +444,11 @@ static int closure_sample(const closure* C, v3 wo, double u_lobe, double u1, dou
             out->is_delta = 1;
             return 1;
         }
-        v3 h = ggx_vndf_sample(wo, C->a_s, u1, u2);
+        v3 h = ggx_vndf_sample(wo, C->ax_s, C->ay_s, u1, u2);
         wi = reflect(wo, h);
         if (wi.z <= 0.0) return 0;
     } else if (lobe == LOBE_DIEL) {
-        v3 h = C->delta_s ? mk(0.0, 0.0, 1.0) : ggx_vndf_sample(wo, C->a_s, u1, u2);
+        v3 h = C->delta_s ? mk(0.0, 0.0, 1.0) : ggx_vndf_sample(wo, C->ax_s, C->ay_s, u1, u2);
         double oh = dot(wo, h);
         if (oh <= 0.0) return 0;
         double fr = oracle_fresnel_dielectric(oh, C->eta_s);
@@ -987,6 +999,27 @@ static void onb(v3 n, v3* t, v3* b) {
     *b = mk(c, s + n.y * n.y * a, -n.y);
 }
 
+/* Tangent frame of an anisotropic surface (reading: the interface carries no vertex
+ * tangents, so the tangent is the triangle's first edge e1 = p1 - p0 projected into the
+ * shading plane, then turned about n by `rot` turns): t0 = normalize(e1 - n (n.e1)),
+ * t = cos(2 pi rot) t0 + sin(2 pi rot) (n x t0), b = n x t.  (t, b, n) is right-handed. */
+static void tangent_frame(v3 n, v3 e1, double rot, v3* t, v3* b) {
+    v3 t0 = sub(e1, scl(n, dot(n, e1)));
+    double l2 = dot(t0, t0);
+    if (!(l2 > 0.0)) { onb(n, t, b); return; }
+    t0 = scl(t0, 1.0 / sqrt(l2));
+    v3 b0 = cross(n, t0);
+    double c = cos(2.0 * M_PI * rot), s = sin(2.0 * M_PI * rot);
+    *t = add(scl(t0, c), scl(b0, s));
+    *b = cross(n, *t);
+}
+void oracle_tangent_frame(const double n[3], const double e1[3], double rot, double t[3], double b[3]) {
+    v3 tt, bb;
+    tangent_frame(mk(n[0], n[1], n[2]), mk(e1[0], e1[1], e1[2]), rot, &tt, &bb);
+    t[0] = tt.x; t[1] = tt.y; t[2] = tt.z;
+    b[0] = bb.x; b[1] = bb.y; b[2] = bb.z;
+}
+
 static inline double power_heuristic(double pa, double pb) {
     double a2 = pa * pa, b2 = pb * pb;
     return a2 + b2 > 0.0 ? a2 / (a2 + b2) : 0.0;
@@ -1100,7 +1133,8 @@ static v3 trace_path(const oscene* S, const ocam* cam, int px, int py, uint32_t 
 
         v3 n = front ? ng : scl(ng, -1.0);
         v3 tt, bb;
-        onb(n, &tt, &bb);
+        if (m->spec_aniso > 0.0) tangent_frame(n, sub(p1, p0), m->spec_rot, &tt, &bb);
+        else onb(n, &tt, &bb);
         v3 wo = mk(dot(wo_w, tt), dot(wo_w, bb), dot(wo_w, n));
         closure C;
         closure_setup(&C, m, front, wo.z);

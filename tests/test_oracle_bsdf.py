@@ -120,6 +120,12 @@ MATS = {
     "thin_tinted": scenes.openpbr(base_color=(0.6, 0.6, 0.6), specular_roughness=0.3, transmission_weight=0.7,
                                   transmission_color=(0.9, 0.6, 0.5), coat_weight=0.4, coat_roughness=0.3,
                                   geometry_thin_walled=1.0),
+    "aniso_metal": scenes.openpbr(base_color=(0.9, 0.8, 0.6), base_metalness=1.0, specular_roughness=0.5,
+                                  specular_roughness_anisotropy=0.8),
+    "aniso_glass": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.5, transmission_weight=1.0,
+                                  specular_roughness_anisotropy=0.6),
+    "aniso_coated": scenes.openpbr(base_color=(0.2, 0.4, 0.8), specular_roughness=0.45, coat_weight=1.0,
+                                   coat_roughness=0.3, specular_roughness_anisotropy=0.5),
 }
 WHITE = {
     "white_plastic": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.3),
@@ -129,6 +135,10 @@ WHITE = {
     "white_glass": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.3, transmission_weight=1.0),
     "white_mixed": scenes.openpbr(base_color=(1, 1, 1), base_metalness=0.5, specular_roughness=0.35,
                                   transmission_weight=0.5, coat_weight=0.5, coat_roughness=0.3),
+    "white_aniso_metal": scenes.openpbr(base_color=(1, 1, 1), base_metalness=1.0, specular_roughness=0.35,
+                                        specular_roughness_anisotropy=0.9),
+    "white_aniso_glass": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.4, transmission_weight=1.0,
+                                        specular_roughness_anisotropy=0.7),
 }
 
 
@@ -193,6 +203,122 @@ def test_ggx_normalisation_and_projected_area(alpha):
             oh = np.maximum(h @ wo, 0.0)
             acc += (oh * d).sum() * math.sin(t) * dt * (2 * math.pi / nphi)
         assert g1 * acc == pytest.approx(mu_o, rel=2e-3)
+
+
+def _aniso_quadrature(ax, ay, nx=1500, nphi=720):
+    """Hemisphere quadrature nodes for an anisotropic GGX lobe: per azimuth phi the polar angle
+    is substituted by tan(theta) = a(phi) tan(x), a(phi) = (cos^2/ax^2 + sin^2/ay^2)^(-1/2) the
+    lobe's width along phi, which resolves the peak.  Returns directions h and weights of dw."""
+    phis = (np.arange(nphi) + 0.5) / nphi * 2 * math.pi
+    x = (np.arange(nx) + 0.5) / nx * (math.pi / 2)
+    P, X = np.meshgrid(phis, x, indexing="ij")
+    a = 1.0 / np.sqrt(np.cos(P) ** 2 / ax ** 2 + np.sin(P) ** 2 / ay ** 2)
+    T = np.arctan(a * np.tan(X))
+    dT = a / np.cos(X) ** 2 / (1 + (a * np.tan(X)) ** 2) * (math.pi / 2 / nx)
+    h = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1).reshape(-1, 3)
+    w = (np.sin(T) * dT).ravel() * (2 * math.pi / nphi)
+    return h, w
+
+
+def _ggx_D_vec(h, ax, ay):
+    return np.array([oracle.ggx_D(v, ax, ay) for v in h])
+
+
+@pytest.mark.parametrize("ax,ay", [(0.3, 0.08), (0.12, 0.5)])
+def test_anisotropic_ggx_normalisation_and_projected_area(ax, ay):
+    """The anisotropic lobe (widths ax along the tangent, ay along the bitangent): projected
+    normals integrate to 1, the projected-area identity holds for views off both axes, and the
+    lobe is elongated along the wider axis (a swapped axis or width fails one of these)."""
+    h, w = _aniso_quadrature(ax, ay)
+    D = _ggx_D_vec(h, ax, ay)
+    assert (D * h[:, 2] * w).sum() == pytest.approx(1.0, abs=5e-4)
+    for mu_o, phi in ((0.9, 0.4), (0.5, 1.2), (0.2, 2.6)):
+        wo = _hemi_dir(mu_o, phi)
+        acc = (np.maximum(h @ wo, 0.0) * D * w).sum()
+        assert oracle.ggx_G1(wo, ax, ay) * acc == pytest.approx(mu_o, rel=2e-3), (mu_o, phi)
+    # D at the normal is 1/(pi ax ay); a tilt along x falls off with ax, along y with ay
+    assert oracle.ggx_D([0, 0, 1], ax, ay) == pytest.approx(1 / (math.pi * ax * ay), rel=1e-14)
+    s = 0.2
+    dx = oracle.ggx_D([math.sin(s), 0, math.cos(s)], ax, ay)
+    dy = oracle.ggx_D([0, math.sin(s), math.cos(s)], ax, ay)
+    assert (dx > dy) == (ax > ay)
+    # isotropic widths give the isotropic lobe
+    for v in ([0.3, 0.2, 0.93], [0.0, 0.6, 0.8]):
+        v = np.array(v) / np.linalg.norm(v)
+        assert oracle.ggx_D(v, 0.3, 0.3) == pytest.approx(oracle.ggx_D(v, 0.3), rel=1e-14)
+
+
+def test_anisotropic_vndf_sampler():
+    """Visible normals sampled for an anisotropic lobe have the moments E[hx^2], E[hy^2],
+    E[hz^2] of the density G1(wo) max(0, wo.h) D(h) / wo.z (quadrature)."""
+    ax, ay = 0.45, 0.1
+    wo = _hemi_dir(0.5, 0.8)
+    n = 60000
+    u = RNG.random((n, 2))
+    hs = np.array([oracle.ggx_vndf_sample(wo, ax, a, b, alpha_y=ay) for a, b in u])
+    assert np.all(hs[:, 2] >= 0) and np.allclose(np.linalg.norm(hs, axis=1), 1.0)
+    h, w = _aniso_quadrature(ax, ay, nx=600, nphi=360)
+    dens = oracle.ggx_G1(wo, ax, ay) * np.maximum(h @ wo, 0) * _ggx_D_vec(h, ax, ay) / wo[2]
+    assert (dens * w).sum() == pytest.approx(1.0, abs=3e-3)
+    for c in range(3):
+        est, err = (hs[:, c] ** 2).mean(), (hs[:, c] ** 2).std() / math.sqrt(n)
+        ref = (dens * h[:, c] ** 2 * w).sum()
+        assert abs(est - ref) < 4 * err + 2e-3, (c, est, ref)
+
+
+def test_anisotropy_mapping():
+    """OpenPBR's mapping of (roughness r, anisotropy a) to the two widths keeps
+    ax^2 + ay^2 = 2 r^4 with ay = (1 - a) ax: checked through the lobe itself, D at the
+    normal = 1/(pi ax ay), and a = 0 is the isotropic material exactly."""
+    r = 0.5
+    wo = _hemi_dir(0.7, 0.3)
+    for a in (0.0, 0.3, 0.8):
+        mat = scenes.openpbr(base_color=(1, 1, 1), base_metalness=1.0, specular_roughness=r,
+                             specular_roughness_anisotropy=a)
+        a = float(mat[27])                               # the float32 value the row holds
+        ax = r * r * math.sqrt(2 / (1 + (1 - a) ** 2))
+        ay = (1 - a) * ax
+        assert ax * ax + ay * ay == pytest.approx(2 * r ** 4)
+        wi = np.array([-wo[0], -wo[1], wo[2]])          # mirror direction: h = n
+        f, _ = oracle.bsdf_eval(mat, 1, wo, wi)
+        g2 = 1.0 / (1.0 + 2 * _lambda(wo, ax, ay))
+        assert f[0] == pytest.approx(1 / (math.pi * ax * ay) * g2 / (4 * wo[2] * wo[2]), rel=1e-12)
+    iso = scenes.openpbr(base_color=(0.8, 0.6, 0.4), base_metalness=1.0, specular_roughness=r)
+    zero = scenes.openpbr(base_color=(0.8, 0.6, 0.4), base_metalness=1.0, specular_roughness=r,
+                          specular_roughness_anisotropy=0.0, specular_rotation=0.37)
+    dirs = _sphere_dirs(50)
+    for wi in dirs:
+        assert np.array_equal(oracle.bsdf_eval(iso, 1, wo, wi)[0], oracle.bsdf_eval(zero, 1, wo, wi)[0])
+
+
+def _lambda(w, ax, ay):
+    x = (ax * ax * w[0] ** 2 + ay * ay * w[1] ** 2) / w[2] ** 2
+    return (-1 + math.sqrt(1 + x)) / 2
+
+
+def test_tangent_frame():
+    """The frame of an anisotropic surface: orthonormal and right-handed with the normal,
+    the tangent along the in-plane part of the first edge at rotation 0, along n x e1 at a
+    quarter turn, reversed at half a turn."""
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        n = rng.normal(size=3); n /= np.linalg.norm(n)
+        e1 = rng.normal(size=3)
+        e1 -= n * (n @ e1) * rng.uniform(0, 1)          # not necessarily in the plane
+        rot = rng.uniform(0, 1)
+        t, b = oracle.tangent_frame(n, e1, rot)
+        M = np.stack([t, b, n])
+        assert np.allclose(M @ M.T, np.eye(3), atol=1e-12)
+        assert np.allclose(np.cross(t, b), n, atol=1e-12)
+        p = e1 - n * (n @ e1)
+        p /= np.linalg.norm(p)
+        t0, _ = oracle.tangent_frame(n, e1, 0.0)
+        assert np.allclose(t0, p, atol=1e-12)
+        tq, _ = oracle.tangent_frame(n, e1, 0.25)
+        assert np.allclose(tq, np.cross(n, p), atol=1e-12)
+        th, _ = oracle.tangent_frame(n, e1, 0.5)
+        assert np.allclose(th, -p, atol=1e-12)
+        assert t @ p == pytest.approx(math.cos(2 * math.pi * rot), abs=1e-12)
 
 
 def test_vndf_sampler_matches_visible_normal_density():
@@ -353,10 +479,18 @@ def test_reciprocity(name):
     if mat[12] > 0:
         assert np.any(f_fwd > 0)
     eta2 = 1.0 if mat[26] > 0 else 1.5 ** 2
-    assert np.allclose(f_fwd, f_rev / eta2, rtol=1e-10, atol=1e-300)
+    # Grazing on the outside (wo.h -> 0) is the critical angle on the inside, where the
+    # transmitted cosine is the square root of a difference that cancels: the two sides then
+    # agree to about 1e-16 / (wo.h)^2 relative, not to 1e-10.
+    h = a + (1.0 if mat[26] > 0 else 1.5) * (b_dn * (flip if mat[26] > 0 else 1))
+    h /= np.linalg.norm(h, axis=1, keepdims=True)
+    oh = np.abs((a * h).sum(1))
+    rtol = 1e-10 + 1e-15 / np.maximum(oh, 1e-300) ** 2
+    assert np.all(np.abs(f_fwd - f_rev / eta2) <= rtol[:, None] * np.abs(f_rev / eta2) + 1e-300)
 
 
-@pytest.mark.parametrize("name", ["plastic", "metal", "coated", "rough_glass", "mixed", "thin_glass", "rough_diffuse"])
+@pytest.mark.parametrize("name", ["plastic", "metal", "coated", "rough_glass", "mixed", "thin_glass", "rough_diffuse",
+                                  "aniso_metal", "aniso_glass"])
 def test_sampler_chi_square(name):
     mat = MATS[name]
     mu = 0.55

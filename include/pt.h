@@ -49,11 +49,11 @@ typedef enum {
 typedef struct pt_scene pt_scene;   /* opaque, library-owned */
 typedef struct pt_nrc pt_nrc;       /* opaque, library-owned */
 
-/* OpenPBR surface parameters (Sec. 4; the paper's material model).  PT_OPENPBR_FLOATS (27)
+/* OpenPBR surface parameters (Sec. 4; the paper's material model).  PT_OPENPBR_FLOATS (29)
  * floats, in this order; the Python generators and the oracle use the same order.
- * Valid ranges (checked by pt_scene_create): weights, colors, roughnesses and metalness
- * in [0, 1]; specular_ior and coat_ior in (1, 3]; emission_luminance >= 0;
- * geometry_thin_walled 0 or 1.
+ * Valid ranges (checked by pt_scene_create): weights, colors, roughnesses, metalness,
+ * anisotropy and rotation in [0, 1]; specular_ior and coat_ior in (1, 3];
+ * emission_luminance >= 0; geometry_thin_walled 0 or 1.
  * base_diffuse_roughness sigma scales the diffuse base by the qualitative Oren-Nayar factor
  * (1 + sigma s/t) / (1 + c sigma), c = 1/2 - 2/(3 pi), s = wi.wo - cos_i cos_o,
  * t = max(cos_i, cos_o) if s > 0 else 1 (0 = Lambertian). */
@@ -80,8 +80,15 @@ typedef struct {
                                    mirrored through the surface plane (straight through when
                                    smooth), weighted transmission_color * (1 - specular_weight
                                    * F), without the 1/eta^2 radiance scaling */
+    float specular_roughness_anisotropy; /* a: the specular GGX lobe (metal, dielectric,
+                                   transmission) gets widths ax = r^2 sqrt(2/(1+(1-a)^2))
+                                   along the tangent and ay = (1-a) ax along the bitangent
+                                   (r = specular_roughness; 0 = isotropic).  Without vertex
+                                   tangents the tangent is the triangle's first edge
+                                   (v1 - v0) projected into the surface plane */
+    float specular_rotation;    /* turns of the tangent about the normal (0..1) */
 } pt_openpbr;
-enum { PT_OPENPBR_FLOATS = 27 };
+enum { PT_OPENPBR_FLOATS = 29 };
 
 /* Parallelogram area light p0 + a e1 + b e2, (a, b) in [0,1]^2, radiance L emitted on the
  * side of e1 x e2 (both sides if two_sided).  The library also makes it geometry: two

@@ -92,7 +92,8 @@ __device__ __forceinline__ DMat pack_material(const float* v) {
     m.metalness = v[4];
     m.diffuse_rough = v[5];
     m.thin_walled = v[26];
-    m.pad1 = m.pad2 = 0.0f;
+    m.spec_aniso = v[27];
+    m.spec_rot = v[28];
     m.spec_weight = v[6];
     m.spec_color = mk3(v[7], v[8], v[9]);
     m.spec_rough = v[10];
@@ -135,7 +136,7 @@ static bool material_ok(const pt_openpbr& m, std::string& why) {
         if (!std::isfinite(v[i])) { why = "non-finite material parameter"; return false; }
     if (v[26] != 0.0f && v[26] != 1.0f) { why = "geometry_thin_walled must be 0 or 1"; return false; }
     auto unit = [](float x) { return x >= 0.0f && x <= 1.0f; };
-    const int unit_idx[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17, 18, 19, 20, 23, 24, 25};
+    const int unit_idx[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17, 18, 19, 20, 23, 24, 25, 27, 28};
     for (int i : unit_idx)
         if (!unit(v[i])) { why = "material parameter " + std::to_string(i) + " outside [0,1]"; return false; }
     if (!(v[11] > 1.0f && v[11] <= 3.0f)) { why = "specular_ior outside (1,3]"; return false; }

@@ -77,7 +77,8 @@ struct __align__(16) DMat {
     float3 coat_color; float trans_weight;
     float3 emission; float coat_weight;
     float spec_rough, spec_ior, coat_rough, coat_ior;
-    float diffuse_rough, thin_walled, pad1, pad2;   // thin_walled: 0 or 1
+    float diffuse_rough, thin_walled;   // thin_walled: 0 or 1
+    float spec_aniso, spec_rot;         // specular_roughness_anisotropy, tangent rotation (turns)
 };
 
 struct __align__(16) DQuad {
@@ -118,30 +119,35 @@ __device__ __forceinline__ float3 fresnel_f82(float3 f0, float3 tint, float mu) 
 }
 
 // ------------------------------------------------------------------ GGX
-__device__ __forceinline__ float ggx_D(float3 h, float a) {
+// Anisotropic GGX: width ax along the tangent (local x), ay along the bitangent (local y);
+// ax = ay is the isotropic lobe.  D = 1 / (pi ax ay (hx^2/ax^2 + hy^2/ay^2 + hz^2)^2),
+// evaluated as ax ay / (pi d^2) with d = hx^2 (ay/ax) + hy^2 (ax/ay) + hz^2 ax ay: the two
+// ratios depend on the closure only, so inlined calls share them.
+__device__ __forceinline__ float ggx_D(float3 h, float ax, float ay) {
     if (h.z <= 0.0f) return 0.0f;
-    const float a2 = a * a;
-    const float d = a2 * h.z * h.z + (h.x * h.x + h.y * h.y);
-    return a2 / (PT_PI_F * d * d);
+    const float axy = ax * ay;
+    const float d = h.x * h.x * (ay / ax) + h.y * h.y * (ax / ay) + axy * (h.z * h.z);
+    return axy / (PT_PI_F * d * d);
 }
-__device__ __forceinline__ float ggx_lambda(float3 w, float a) {
+__device__ __forceinline__ float ggx_lambda(float3 w, float ax, float ay) {
     const float c2 = w.z * w.z;
     if (c2 <= 0.0f) return __int_as_float(0x7f800000);
-    const float x = a * a * ((w.x * w.x + w.y * w.y) / c2);
+    const float sx = ax * w.x, sy = ay * w.y;
+    const float x = (sx * sx + sy * sy) / c2;
     return x / (2.0f * (1.0f + sqrtf(1.0f + x)));
 }
-__device__ __forceinline__ float ggx_G1(float3 w, float a) { return 1.0f / (1.0f + ggx_lambda(w, a)); }
-__device__ __forceinline__ float ggx_G2(float3 wo, float3 wi, float a) {
-    return 1.0f / (1.0f + ggx_lambda(wo, a) + ggx_lambda(wi, a));
+__device__ __forceinline__ float ggx_G1(float3 w, float ax, float ay) { return 1.0f / (1.0f + ggx_lambda(w, ax, ay)); }
+__device__ __forceinline__ float ggx_G2(float3 wo, float3 wi, float ax, float ay) {
+    return 1.0f / (1.0f + ggx_lambda(wo, ax, ay) + ggx_lambda(wi, ax, ay));
 }
-__device__ __forceinline__ float ggx_vndf_pdf(float3 wo, float3 h, float a) {
+__device__ __forceinline__ float ggx_vndf_pdf(float3 wo, float3 h, float ax, float ay) {
     const float oh = dot3(wo, h);
     if (oh <= 0.0f || wo.z <= 0.0f) return 0.0f;
-    return ggx_G1(wo, a) * oh * ggx_D(h, a) / wo.z;
+    return ggx_G1(wo, ax, ay) * oh * ggx_D(h, ax, ay) / wo.z;
 }
 // visible-normal sampling (Heitz 2018): stretch, sample the projected half disk, unstretch
-__device__ __forceinline__ float3 ggx_vndf_sample(float3 wo, float a, float u1, float u2) {
-    const float3 vh = norm3(mk3(a * wo.x, a * wo.y, wo.z));
+__device__ __forceinline__ float3 ggx_vndf_sample(float3 wo, float ax, float ay, float u1, float u2) {
+    const float3 vh = norm3(mk3(ax * wo.x, ay * wo.y, wo.z));
     const float lensq = vh.x * vh.x + vh.y * vh.y;
     const float3 t1 = lensq > 0.0f ? mk3(-vh.y, vh.x, 0.0f) * (1.0f / sqrtf(lensq)) : mk3(1.0f, 0.0f, 0.0f);
     const float3 t2 = cross3(vh, t1);
@@ -154,7 +160,7 @@ __device__ __forceinline__ float3 ggx_vndf_sample(float3 wo, float a, float u1, 
     const float s = 0.5f * (1.0f + vh.z);
     p2 = (1.0f - s) * sqrtf(fmaxf(0.0f, 1.0f - p1 * p1)) + s * p2;
     const float3 nh = t1 * p1 + t2 * p2 + vh * sqrtf(fmaxf(0.0f, 1.0f - p1 * p1 - p2 * p2));
-    return norm3(mk3(a * nh.x, a * nh.y, fmaxf(0.0f, nh.z)));
+    return norm3(mk3(ax * nh.x, ay * nh.y, fmaxf(0.0f, nh.z)));
 }
 __device__ __forceinline__ float3 reflect3(float3 wo, float3 h) { return h * (2.0f * dot3(wo, h)) - wo; }
 __device__ __forceinline__ bool refract3(float3 wo, float3 h, float eta, float3& wi) {
@@ -174,7 +180,7 @@ enum { LOBE_COAT = 0, LOBE_METAL = 1, LOBE_DIEL = 2, LOBE_DIFF = 3 };
 struct Closure {
     float3 bc, sc, tc, cc;
     float bw, m, sw, t, cw, dr;
-    float eta_s, eta_c, a_s, a_c;
+    float eta_s, eta_c, ax_s, ay_s, a_c;   // specular widths along tangent / bitangent; coat
     bool delta_s, delta_c, any, has_smooth, thin;
     float p[4];
 };
@@ -188,9 +194,14 @@ __device__ __forceinline__ void closure_setup(Closure& C, const DMat& M, bool fr
     // a thin-walled sheet has the same medium on both sides
     C.eta_s = (C.t > 0.0f && !front && !C.thin) ? 1.0f / M.spec_ior : M.spec_ior;
     C.eta_c = M.coat_ior;
-    C.a_s = M.spec_rough * M.spec_rough;
+    // OpenPBR's anisotropy mapping: ax = r^2 sqrt(2 / (1 + (1-a)^2)), ay = (1-a) ax (a = 0:
+    // both r^2); a delta lobe when ax < 1e-4, else the narrower width is kept >= 1e-4
+    const float r2 = M.spec_rough * M.spec_rough, ia = 1.0f - M.spec_aniso;
+    const float at = r2 * sqrtf(2.0f / (1.0f + ia * ia));
+    C.ax_s = at;
+    C.ay_s = fmaxf(ia * at, 1e-4f);
     C.a_c = M.coat_rough * M.coat_rough;
-    C.delta_s = C.a_s < 1e-4f;
+    C.delta_s = at < 1e-4f;
     C.delta_c = C.a_c < 1e-4f;
     const float fc = fresnel_dielectric(mu_o, C.eta_c);
     const float w_coat = C.cw * fc;
@@ -239,13 +250,13 @@ __device__ __forceinline__ void closure_eval(const Closure& C, float3 wo, float3
         if (oh <= 0.0f) return;
         if (!C.delta_c && C.cw > 0.0f) {
             const float fr = fresnel_dielectric(oh, C.eta_c);
-            const float val = C.cw * fr * ggx_D(h, C.a_c) * ggx_G2(wo, wi, C.a_c) / (4.0f * mo * mi);
+            const float val = C.cw * fr * ggx_D(h, C.a_c, C.a_c) * ggx_G2(wo, wi, C.a_c, C.a_c) / (4.0f * mo * mi);
             f = f + splat3(val);
-            pdf += C.p[0] * ggx_vndf_pdf(wo, h, C.a_c) / (4.0f * oh);
+            pdf += C.p[0] * ggx_vndf_pdf(wo, h, C.a_c, C.a_c) / (4.0f * oh);
         }
         if (!C.delta_s) {
-            const float dg = ggx_D(h, C.a_s) * ggx_G2(wo, wi, C.a_s) / (4.0f * mo * mi);
-            const float vndf = ggx_vndf_pdf(wo, h, C.a_s) / (4.0f * oh);
+            const float dg = ggx_D(h, C.ax_s, C.ay_s) * ggx_G2(wo, wi, C.ax_s, C.ay_s) / (4.0f * mo * mi);
+            const float vndf = ggx_vndf_pdf(wo, h, C.ax_s, C.ay_s) / (4.0f * oh);
             if (C.m > 0.0f) {
                 const float3 fm = fresnel_f82(C.bc * C.bw, C.sc, oh);
                 f = f + (ac * fm) * (C.m * C.sw * dg);
@@ -275,10 +286,10 @@ __device__ __forceinline__ void closure_eval(const Closure& C, float3 wo, float3
             const float oh = dot3(wo, h);
             if (oh > 0.0f) {
                 const float fr = fresnel_dielectric(oh, C.eta_s);
-                const float dg = ggx_D(h, C.a_s) * ggx_G2(wo, wm, C.a_s) / (4.0f * mo * fabsf(mi));
+                const float dg = ggx_D(h, C.ax_s, C.ay_s) * ggx_G2(wo, wm, C.ax_s, C.ay_s) / (4.0f * mo * fabsf(mi));
                 const float val = (1.0f - C.m) * C.t * (1.0f - C.sw * fr) * dg;
                 f = f + (ac * C.tc) * val;
-                pdf += C.p[2] * (1.0f - diel_reflect_prob(C, fr)) * ggx_vndf_pdf(wo, h, C.a_s) / (4.0f * oh);
+                pdf += C.p[2] * (1.0f - diel_reflect_prob(C, fr)) * ggx_vndf_pdf(wo, h, C.ax_s, C.ay_s) / (4.0f * oh);
             }
         }
     } else if (!C.delta_s && C.t > 0.0f) {
@@ -289,11 +300,11 @@ __device__ __forceinline__ void closure_eval(const Closure& C, float3 wo, float3
         if (oh > 0.0f && ih < 0.0f) {
             const float fr = fresnel_dielectric(oh, eta);
             const float denom = oh + eta * ih;
-            const float dg = ggx_D(h, C.a_s) * ggx_G2(wo, wi, C.a_s);
+            const float dg = ggx_D(h, C.ax_s, C.ay_s) * ggx_G2(wo, wi, C.ax_s, C.ay_s);
             const float val = (1.0f - C.m) * C.t * (1.0f - C.sw * fr) * dg * fabsf(ih) * oh /
                               (fabsf(mi) * mo * denom * denom);
             f = f + (ac * C.tc) * val;
-            pdf += C.p[2] * (1.0f - diel_reflect_prob(C, fr)) * ggx_vndf_pdf(wo, h, C.a_s) * eta * eta *
+            pdf += C.p[2] * (1.0f - diel_reflect_prob(C, fr)) * ggx_vndf_pdf(wo, h, C.ax_s, C.ay_s) * eta * eta *
                    fabsf(ih) / (denom * denom);
         }
     }
@@ -333,7 +344,7 @@ __device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, floa
             out.delta = true;
             return true;
         }
-        wi = reflect3(wo, ggx_vndf_sample(wo, C.a_c, u1, u2));
+        wi = reflect3(wo, ggx_vndf_sample(wo, C.a_c, C.a_c, u1, u2));
         if (wi.z <= 0.0f) return false;
     } else if (lobe == LOBE_METAL) {
         if (C.delta_s) {
@@ -343,10 +354,10 @@ __device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, floa
             out.delta = true;
             return true;
         }
-        wi = reflect3(wo, ggx_vndf_sample(wo, C.a_s, u1, u2));
+        wi = reflect3(wo, ggx_vndf_sample(wo, C.ax_s, C.ay_s, u1, u2));
         if (wi.z <= 0.0f) return false;
     } else if (lobe == LOBE_DIEL) {
-        const float3 h = C.delta_s ? mk3(0.0f, 0.0f, 1.0f) : ggx_vndf_sample(wo, C.a_s, u1, u2);
+        const float3 h = C.delta_s ? mk3(0.0f, 0.0f, 1.0f) : ggx_vndf_sample(wo, C.ax_s, C.ay_s, u1, u2);
         const float oh = dot3(wo, h);
         if (oh <= 0.0f) return false;
         const float fr = fresnel_dielectric(oh, C.eta_s);
@@ -400,6 +411,22 @@ __device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
     const float c = n.x * n.y * a;
     t = mk3(1.0f + s * n.x * n.x * a, s * c, -s * n.x);
     b = mk3(c, s + n.y * n.y * a, -n.y);
+}
+
+// Frame of an anisotropic surface: the interface carries no vertex tangents, so the tangent
+// is the triangle's first edge e1 projected into the shading plane, t0 = normalize(e1 -
+// n (n.e1)), turned about n by `rot` turns: t = cos(2 pi rot) t0 + sin(2 pi rot) (n x t0),
+// b = n x t; (t, b, n) is right-handed.
+__device__ __forceinline__ void tangent_frame(float3 n, float3 e1, float rot, float3& t, float3& b) {
+    const float3 p = e1 - n * dot3(n, e1);
+    const float l2 = dot3(p, p);
+    if (!(l2 > 0.0f)) { onb(n, t, b); return; }
+    const float3 t0 = p * (1.0f / sqrtf(l2));
+    const float3 b0 = cross3(n, t0);
+    float sr, cr;
+    sincospif(2.0f * rot, &sr, &cr);
+    t = t0 * cr + b0 * sr;
+    b = cross3(n, t);
 }
 
 __device__ __forceinline__ float power_heuristic(float pa, float pb) {
@@ -1001,7 +1028,8 @@ __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, 
 
     const float3 n = front ? ng : -ng;
     float3 tt, bb;
-    onb(n, tt, bb);
+    if (M.spec_aniso > 0.0f) tangent_frame(n, xyz(tb) - xyz(ta), M.spec_rot, tt, bb);
+    else onb(n, tt, bb);
     const float3 wo = mk3(dot3(wo_w, tt), dot3(wo_w, bb), dot3(wo_w, n));
     if (hook(x, wo_w, n, M, ps, k)) return SHADE_END;
     Closure C;

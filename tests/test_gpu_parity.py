@@ -120,6 +120,13 @@ def _bsdf_materials():
         scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.4, transmission_weight=1.0, geometry_thin_walled=1.0),
         scenes.openpbr(base_color=(0.6, 0.6, 0.6), specular_roughness=0.3, transmission_weight=0.7,
                        transmission_color=(0.9, 0.6, 0.5), coat_weight=0.4, coat_roughness=0.3, geometry_thin_walled=1.0),
+        scenes.openpbr(base_color=(0.9, 0.8, 0.6), base_metalness=1.0, specular_roughness=0.5,
+                       specular_roughness_anisotropy=0.8),
+        scenes.openpbr(specular_roughness=0.5, transmission_weight=1.0, specular_roughness_anisotropy=0.6),
+        scenes.openpbr(base_color=(0.2, 0.4, 0.8), specular_roughness=0.45, coat_weight=1.0, coat_roughness=0.3,
+                       specular_roughness_anisotropy=0.5),
+        scenes.openpbr(base_color=(0.8, 0.8, 0.8), base_metalness=1.0, specular_roughness=0.7,
+                       specular_roughness_anisotropy=1.0),
     ]
     return np.stack(mats)
 
@@ -207,8 +214,13 @@ def test_bsdf_sample_parity(api):
             same_dir = np.all(np.abs(wi_g - wi_o[sel]) < 1e-4, axis=1)
             assert same_dir.mean() >= need, (m_i, front, same_dir.mean())
             ww = w_o[sel][same_dir]
-            close = np.abs(w_g[same_dir] - ww) <= 1e-4 * np.maximum(np.abs(ww), 1e-3 * np.abs(ww).max()) + 1e-30
-            assert close.mean() >= need, (m_i, front, close.mean())
+            # a reflected direction near the horizon carries the FP32 error of its unit vector
+            # (a few 1e-7) into wi.z, and the weight's Smith term (1 + Lambda(wi))^-1 grows
+            # like wi.z there: the weight's relative error is about 3e-7 / |wi.z| on top
+            mu_i = np.abs(wi_o[sel][same_dir][:, 2:3])
+            rel = 1e-4 + 3e-7 / np.maximum(mu_i, 1e-12)
+            close = np.abs(w_g[same_dir] - ww) <= rel * np.maximum(np.abs(ww), 1e-3 * np.abs(ww).max()) + 1e-30
+            assert close.mean() >= need, (m_i, front, close.mean(), mu_i[~close.all(1)][:5].ravel())
 
 
 # ------------------------------------------------------------------ closest hit
@@ -432,6 +444,35 @@ def test_image_parity_rough_diffuse(api, mode):
     lam = A.Scene(base).render(sc.spp, mode=mode, seed=6)
     torch.cuda.synchronize()
     assert np.abs(lam.image().cpu().numpy() - gi).max() > 1e-3
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_image_parity_anisotropic(api, mode):
+    """The Cornell box with brushed-metal boxes (anisotropy 0.85, tangent turned by 1/8) and an
+    anisotropic glossy back wall, GPU vs oracle; turning the tangent changes the picture."""
+    from paper_2407_19977_gb300 import api as A
+    base = scenes.cornell_box(width=48, height=40, spp=8, max_depth=4)
+    mats = np.array(base.materials, dtype=np.float32).copy()
+    brushed = scenes.openpbr(base_color=(0.9, 0.75, 0.5), base_metalness=1.0, specular_roughness=0.45,
+                             specular_roughness_anisotropy=0.85, specular_rotation=0.125)
+    glossy = scenes.openpbr(base_color=(0.7, 0.7, 0.7), specular_roughness=0.3, specular_roughness_anisotropy=0.6)
+    mats = np.concatenate([mats, brushed[None], glossy[None]])
+    mid = np.asarray(base.material_ids, np.uint32).copy()
+    mid[10:] = len(mats) - 2                # the two boxes (triangles after the 10 wall triangles)
+    mid[:2] = len(mats) - 1                 # one wall
+    sc = scenes.Scene(base.name, base.vertices, base.indices, mid, mats, base.lights, base.env,
+                      base.camera, base.spp, base.max_depth)
+    g = A.Scene(sc)
+    osc = oracle.OracleScene(sc)
+    gi, oi, gs, os_, st = _render_pair(g, osc, sc, sc.spp, mode=mode, max_depth=sc.max_depth, seed=9)
+    _image_check(gi, oi, f"anisotropic mode {mode}")
+    turned = mats.copy()
+    turned[-2, 28] = 0.375
+    sc2 = scenes.Scene(base.name, base.vertices, base.indices, mid, turned, base.lights, base.env,
+                       base.camera, base.spp, base.max_depth)
+    acc = A.Scene(sc2).render(sc.spp, mode=mode, seed=9)
+    torch.cuda.synchronize()
+    assert np.abs(acc.image().cpu().numpy() - gi).max() > 1e-3
 
 
 @pytest.mark.parametrize("mode", [1, 2])

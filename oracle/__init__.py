@@ -83,7 +83,7 @@ def _load():
         lib.oracle_env_pdf.restype = C.c_double
         lib.oracle_render.argtypes = [C.c_void_p, _dp, C.c_double, C.c_int, C.c_int, C.c_int,
                                       C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_int,
-                                      C.c_uint64, C.c_int, C.c_int, C.c_int, _dp, _dp, _i64p]
+                                      C.c_uint64, C.c_int, C.c_int, C.c_int, _dp, _dp, _i64p, _i32p]
         lib.oracle_camera_ray.argtypes = [_dp, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_uint32, C.c_uint64, _dp, _dp]
         lib.oracle_bsdf_eval_batch.argtypes = [_dp, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
@@ -301,9 +301,10 @@ class OracleScene:
         return _load().oracle_env_pdf(self.h, p)
 
     def render(self, camera=None, spp=None, max_depth=None, seed=0, s0=0, crop=None,
-               threads=None, row_step=1, keep_samples=False, no_nee=False, no_rr=False):
+               threads=None, row_step=1, keep_samples=False, no_nee=False, no_rr=False, restir=None):
         """Sum of sample radiance over the crop (ch, cw, 3), optional per-sample values and
-        stats dict.  crop = (x0, y0, w, h) in full-frame pixels."""
+        stats dict.  crop = (x0, y0, w, h) in full-frame pixels.  restir = (M candidates,
+        K neighbours, radius R) renders with ReSTIR DI at the primary vertex over the crop."""
         sc = self.scene
         cam = camera or sc.camera
         spp = sc.spp if spp is None else spp
@@ -315,12 +316,15 @@ class OracleScene:
         samples = np.zeros((ch, cw, spp, 3)) if keep_samples else None
         stats = np.zeros(5, dtype=np.int64)
         threads = threads or (os.cpu_count() or 1)
+        rp = None if restir is None else np.array([int(v) for v in restir], dtype=np.int32)
+        if rp is not None:
+            assert len(rp) == 3 and rp[0] >= 1 and 0 <= rp[1] <= 64 and rp[2] >= 1
         _load().oracle_render(self.h, cam9.ctypes.data_as(_dp), float(cam.vfov_deg), cam.width,
                               cam.height, x0, y0, cw, ch, int(s0), int(spp), int(max_depth),
                               int(seed), (1 if no_nee else 0) | (2 if no_rr else 0), int(threads),
                               int(row_step), out.ctypes.data_as(_dp),
                               samples.ctypes.data_as(_dp) if keep_samples else None,
-                              stats.ctypes.data_as(_i64p))
+                              stats.ctypes.data_as(_i64p), rp.ctypes.data_as(_i32p) if rp is not None else None)
         st = dict(zip(("ext_rays", "shadow_rays", "nan_dropped", "rr_terminated", "paths"),
                       map(int, stats)))
         return out, samples, st

@@ -12,7 +12,10 @@
  *   - closest-hit search through an AABB BVH (Sec. 5.1.1); a brute-force loop over all
  *     triangles is kept beside it as the pin,
  *   - OpenPBR-style shading at every hit with importance sampling (Sec. 4, Sec. 5.1.3),
- *   - Russian roulette and averaging of the samples (Sec. 5.1.3), progressive (Sec. 5.1.4).
+ *   - Russian roulette and averaging of the samples (Sec. 5.1.3), progressive (Sec. 5.1.4),
+ *   - optionally ReSTIR DI at the primary vertex (the paper's pointer to reservoir
+ *     resampling for many lights, Sec. 2 and Sec. 6.3; Bitterli et al. 2020), as passes
+ *     over the window per sample index.
  * Where the paper is silent (light sampling, MIS, the RNG keying, the lobe formulas, camera
  * conventions, depth semantics, roulette rule) this file follows the readings listed in the
  * design notes; each such place says "reading:" below.
@@ -1084,8 +1087,259 @@ static void camera_ray(const ocam* c, int px, int py, uint32_t s, uint64_t seed,
  *        bit 1 = no Russian roulette */
 enum { FLAG_NO_NEE = 1, FLAG_NO_RR = 2 };
 
+/* ---- ReSTIR DI at the primary vertex ------------------------------------------------ */
+/* The paper points to reservoir resampling for many-light direct illumination as future    */
+/* work (Sec. 2, Sec. 6.3) without fixing an algorithm; this follows Bitterli et al. 2020:  */
+/*  1. initial candidates: M light samples y_i from the NEE light sampler (source pdf p_i, */
+/*     area measure on quads, solid angle for the environment), target p^(y) = luminance   */
+/*     of the unshadowed contribution f(wo, w_y) L_e(y) |cos| G(y) (G = cos_l / d^2 on a    */
+/*     quad, 1 for the environment); a one-sample weighted reservoir keeps y_i with         */
+/*     probability w_i / sum_j w_j, w_i = p^(y_i) / p_i, and W = sum w / (M p^(y));         */
+/*  2. one spatial pass: K neighbours of the same sample index inside the window (offsets  */
+/*     uniform in a square of half-width R, rejected off-window, on the pixel itself, with  */
+/*     no surface, normal cosine < 0.9 or depth differing by > 10 %); their initial        */
+/*     reservoirs are resampled with w = p^_q(y_j) W_j M_j at this pixel q, and the result   */
+/*     is weighted unbiasedly: W = sum w / (Z p^_q(y)), Z = sum of M_j over the combined    */
+/*     reservoirs whose own target is positive at y (the "1/Z" weights);                     */
+/*  3. vertex 0 of the path shades that sample: f L_e |cos| G V W with one shadow ray, in   */
+/*     place of next-event estimation; a BSDF-sampled hit of a quad or the environment at   */
+/*     vertex 1 then counts with weight 0 (unless vertex 0 sampled a delta lobe), since the */
+/*     reservoir already estimates all light reaching vertex 0.                             */
+/* Random numbers: candidate i uses (pixel, sample, RESTIR_CANDIDATES, dims 4i..4i+3) for   */
+/* light pick, u, v, selection; neighbour j uses (pixel, sample, RESTIR_SPATIAL, 4j..4j+2)  */
+/* for dx, dy (the raw 32-bit words, w * (2R+1) >> 32 - R: integer arithmetic, so both      */
+/* sides pick the same pixel) and selection.                                                */
+#define RESTIR_CANDIDATES 0xFFFF0001u
+#define RESTIR_SPATIAL 0xFFFF0002u
+enum { LIGHT_NONE = -2, LIGHT_ENV = -1 };
+
+typedef struct {
+    int valid;               /* a scattering surface that next-event estimation would shade */
+    v3 x, ng, n, tt, bb, wo_w, wo;
+    double t;
+    int front;
+    closure C;
+} osurf;
+
+typedef struct {
+    int light;               /* quad index, LIGHT_ENV or LIGHT_NONE */
+    v3 y;                    /* point on the quad, or direction towards the environment */
+    double W, M, phat;
+} oresv;
+
+static uint32_t philox_word(uint32_t p, uint32_t s, uint32_t k, uint32_t dim, uint64_t seed) {
+    uint32_t ctr[4] = {p, s, k, dim >> 2};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[dim & 3u];
+}
+
+/* unshadowed contribution of light sample (light, y) at surface g; returns p^ = its luminance */
+static double restir_target(const oscene* S, const osurf* g, int light, v3 y, v3* c_out, v3* ld_out) {
+    v3 ld, Le;
+    double geo;
+    *c_out = splat(0.0);
+    if (light >= 0) {
+        v3 to = sub(y, g->x);
+        double d2 = dot(to, to);
+        if (!(d2 > 0.0)) return 0.0;
+        ld = scl(to, 1.0 / sqrt(d2));
+        double cl = -dot(ld, S->q_n[light]);
+        if (!(cl > 0.0 || (S->q_two_sided[light] && cl < 0.0))) return 0.0;
+        Le = S->q_L[light];
+        geo = fabs(cl) / d2;
+    } else if (light == LIGHT_ENV) {
+        ld = y;
+        Le = env_radiance(S, ld);
+        geo = 1.0;
+    } else {
+        return 0.0;
+    }
+    v3 wl = mk(dot(ld, g->tt), dot(ld, g->bb), dot(ld, g->n));
+    v3 f;
+    double pdf;
+    closure_eval(&g->C, g->wo, wl, &f, &pdf);
+    v3 c = scl(hmul(f, Le), fabs(wl.z) * geo);
+    *c_out = c;
+    *ld_out = ld;
+    double ph = lum(c);
+    return ph > 0.0 && isfinite(ph) ? ph : 0.0;
+}
+
+static void restir_initial(const oscene* S, const osurf* g, uint32_t p, uint32_t s, uint64_t seed, int M,
+                           double p_env, oresv* R) {
+    R->light = LIGHT_NONE;
+    R->y = splat(0.0);
+    R->W = 0.0;
+    R->M = (double)M;
+    R->phat = 0.0;
+    double wsum = 0.0;
+    for (int i = 0; i < M; ++i) {
+        double u_pick = U(p, s, RESTIR_CANDIDATES, 4u * i, seed);
+        double u = U(p, s, RESTIR_CANDIDATES, 4u * i + 1, seed);
+        double v = U(p, s, RESTIR_CANDIDATES, 4u * i + 2, seed);
+        double u_sel = U(p, s, RESTIR_CANDIDATES, 4u * i + 3, seed);
+        int light;
+        v3 y;
+        double src;
+        if (u_pick < p_env) {
+            v3 Ld;
+            double pe;
+            if (!env_sample(S, u, v, &y, &pe, &Ld)) continue;
+            light = LIGHT_ENV;
+            src = p_env * pe;
+        } else {
+            int l = (int)floor((u_pick - p_env) / (1.0 - p_env) * S->n_quads);
+            if (l > S->n_quads - 1) l = S->n_quads - 1;
+            light = l;
+            y = add(add(S->q_p0[l], scl(S->q_e1[l], u)), scl(S->q_e2[l], v));
+            src = (1.0 - p_env) / S->n_quads / S->q_area[l];
+        }
+        if (!(src > 0.0)) continue;
+        v3 c, ld;
+        double ph = restir_target(S, g, light, y, &c, &ld);
+        double w = ph / src;
+        if (!(w > 0.0)) continue;
+        wsum += w;
+        if (u_sel * wsum < w) {
+            R->light = light;
+            R->y = y;
+            R->phat = ph;
+        }
+    }
+    if (R->light != LIGHT_NONE && R->phat > 0.0) R->W = wsum / (R->M * R->phat);
+}
+
+typedef struct {
+    const oscene* S;
+    const ocam* cam;
+    int x0, y0, cw, ch, M, K, R;
+    int max_depth, flags;
+    uint32_t s;
+    uint64_t seed;
+    osurf* surf;
+    oresv* init;
+    oresv* fin;
+    int tid, nthreads;
+} restir_job;
+
+/* pass 1: the primary surface of every pixel of the window and its initial reservoir */
+static void* restir_pass_initial(void* arg) {
+    restir_job* J = (restir_job*)arg;
+    const oscene* S = J->S;
+    int has_env = S->env_w > 0 && S->env_total > 0.0;
+    double p_env = has_env ? (S->n_quads > 0 ? 0.5 : 1.0) : 0.0;
+    for (int ry = J->tid; ry < J->ch; ry += J->nthreads)
+        for (int rx = 0; rx < J->cw; ++rx) {
+            size_t i = (size_t)ry * J->cw + rx;
+            osurf* g = &J->surf[i];
+            memset(g, 0, sizeof(*g));
+            J->init[i].light = LIGHT_NONE;
+            J->init[i].W = J->init[i].M = J->init[i].phat = 0.0;
+            int px = J->x0 + rx, py = J->y0 + ry;
+            uint32_t p = (uint32_t)(py * J->cam->width + px);
+            v3 o, d;
+            camera_ray(J->cam, px, py, J->s, J->seed, &o, &d);
+            ohit h;
+            intersect(S, o, d, INFINITY, &h);
+            if (h.tri < 0 || J->max_depth == 0) continue;
+            int mid = S->tri_mat[h.tri];
+            if (mid < 0) continue;
+            const omat* m = &S->mats[mid];
+            v3 p0 = S->tv[3 * h.tri], p1 = S->tv[3 * h.tri + 1], p2 = S->tv[3 * h.tri + 2];
+            g->x = add(o, scl(d, h.t));
+            g->ng = normalize(cross(sub(p1, p0), sub(p2, p0)));
+            g->wo_w = scl(d, -1.0);
+            g->front = dot(g->wo_w, g->ng) > 0.0;
+            g->n = g->front ? g->ng : scl(g->ng, -1.0);
+            if (m->spec_aniso > 0.0) tangent_frame(g->n, sub(p1, p0), m->spec_rot, &g->tt, &g->bb);
+            else onb(g->n, &g->tt, &g->bb);
+            g->wo = mk(dot(g->wo_w, g->tt), dot(g->wo_w, g->bb), dot(g->wo_w, g->n));
+            g->t = h.t;
+            closure_setup(&g->C, m, g->front, g->wo.z);
+            g->valid = g->C.has_smooth && (has_env || S->n_quads > 0);
+            if (g->valid) restir_initial(S, g, p, J->s, J->seed, J->M, p_env, &J->init[i]);
+        }
+    return NULL;
+}
+
+/* pass 2: spatial reuse over K neighbours with the 1/Z weights */
+static void* restir_pass_spatial(void* arg) {
+    restir_job* J = (restir_job*)arg;
+    const oscene* S = J->S;
+    const int side = 2 * J->R + 1;
+    for (int ry = J->tid; ry < J->ch; ry += J->nthreads)
+        for (int rx = 0; rx < J->cw; ++rx) {
+            size_t i = (size_t)ry * J->cw + rx;
+            const osurf* g = &J->surf[i];
+            oresv* F = &J->fin[i];
+            *F = J->init[i];
+            if (!g->valid) continue;
+            int px = J->x0 + rx, py = J->y0 + ry;
+            uint32_t p = (uint32_t)(py * J->cam->width + px);
+            const oresv* R0 = &J->init[i];
+            double wsum = R0->phat * R0->W * R0->M;
+            double Msum = R0->M;
+            int light = R0->light;
+            v3 y = R0->y;
+            size_t used[64];
+            int n_used = 0;
+            for (int j = 0; j < J->K && j < 64; ++j) {
+                uint32_t wx = philox_word(p, J->s, RESTIR_SPATIAL, 4u * j, J->seed);
+                uint32_t wy = philox_word(p, J->s, RESTIR_SPATIAL, 4u * j + 1, J->seed);
+                double u_sel = U(p, J->s, RESTIR_SPATIAL, 4u * j + 2, J->seed);
+                int dx = (int)(((uint64_t)wx * (uint32_t)side) >> 32) - J->R;
+                int dy = (int)(((uint64_t)wy * (uint32_t)side) >> 32) - J->R;
+                int nx = rx + dx, ny = ry + dy;
+                if ((dx == 0 && dy == 0) || nx < 0 || ny < 0 || nx >= J->cw || ny >= J->ch) continue;
+                size_t k = (size_t)ny * J->cw + nx;
+                const osurf* gn = &J->surf[k];
+                if (!gn->valid) continue;
+                if (dot(gn->n, g->n) < 0.9 || fabs(gn->t - g->t) > 0.1 * g->t) continue;
+                const oresv* Rn = &J->init[k];
+                used[n_used++] = k;
+                Msum += Rn->M;
+                v3 c, ld;
+                double ph = restir_target(S, g, Rn->light, Rn->y, &c, &ld);
+                double w = ph * Rn->W * Rn->M;
+                if (!(w > 0.0)) continue;
+                wsum += w;
+                if (u_sel * wsum < w) {
+                    light = Rn->light;
+                    y = Rn->y;
+                }
+            }
+            (void)Msum;
+            v3 c, ld;
+            double ph = restir_target(S, g, light, y, &c, &ld);
+            double Z = ph > 0.0 ? R0->M : 0.0;
+            for (int u = 0; u < n_used; ++u) {
+                v3 c2, ld2;
+                if (restir_target(S, &J->surf[used[u]], light, y, &c2, &ld2) > 0.0) Z += J->init[used[u]].M;
+            }
+            F->light = light;
+            F->y = y;
+            F->phat = ph;
+            F->M = Z;
+            F->W = (ph > 0.0 && Z > 0.0) ? wsum / (Z * ph) : 0.0;
+        }
+    return NULL;
+}
+
+static v3 trace_path_r(const oscene* S, const ocam* cam, int px, int py, uint32_t s,
+                       int max_depth, uint64_t seed, int flags, ostats* st, int restir, const oresv* R0,
+                       const osurf* g0);
+
 static v3 trace_path(const oscene* S, const ocam* cam, int px, int py, uint32_t s,
                      int max_depth, uint64_t seed, int flags, ostats* st) {
+    return trace_path_r(S, cam, px, py, s, max_depth, seed, flags, st, 0, NULL, NULL);
+}
+
+/* one path; with `restir`, vertex 0 shades the reservoir R0 (its surface g0) instead of NEE */
+static v3 trace_path_r(const oscene* S, const ocam* cam, int px, int py, uint32_t s,
+                       int max_depth, uint64_t seed, int flags, ostats* st, int restir, const oresv* R0,
+                       const osurf* g0) {
     uint32_t p = (uint32_t)(py * cam->width + px);
     v3 o, d;
     camera_ray(cam, px, py, s, seed, &o, &d);
@@ -1103,7 +1357,8 @@ static v3 trace_path(const oscene* S, const ocam* cam, int px, int py, uint32_t 
             if (has_env) {
                 v3 Le = env_radiance(S, d);
                 double w = 1.0;
-                if (!prev_delta && nee) w = power_heuristic(prev_pdf, p_env * env_pdf(S, d));
+                if (!prev_delta && nee)
+                    w = (restir && k == 1) ? 0.0 : power_heuristic(prev_pdf, p_env * env_pdf(S, d));
                 L = add(L, scl(hmul(beta, Le), w));
             }
             break;
@@ -1121,7 +1376,7 @@ static v3 trace_path(const oscene* S, const ocam* cam, int px, int py, uint32_t 
                 double w = 1.0;
                 if (!prev_delta && nee) {
                     double pl = (1.0 - p_env) / S->n_quads * h.t * h.t / (S->q_area[l] * fabs(cl));
-                    w = power_heuristic(prev_pdf, pl);
+                    w = (restir && k == 1) ? 0.0 : power_heuristic(prev_pdf, pl);
                 }
                 L = add(L, scl(hmul(beta, S->q_L[l]), w));
             }
@@ -1139,8 +1394,27 @@ static v3 trace_path(const oscene* S, const ocam* cam, int px, int py, uint32_t 
         closure C;
         closure_setup(&C, m, front, wo.z);
 
-        /* next-event estimation */
-        if (nee && C.has_smooth && (has_env || S->n_quads > 0)) {
+        if (restir && k == 0) {
+            /* the reservoir's sample in place of next-event estimation */
+            if (g0 && g0->valid && R0 && R0->light != LIGHT_NONE && R0->W > 0.0) {
+                v3 c, ld;
+                double ph = restir_target(S, g0, R0->light, R0->y, &c, &ld);
+                if (ph > 0.0) {
+                    v3 so = offset_origin(S, x, ng, ld);
+                    v3 sd = ld;
+                    double tmax = INFINITY;
+                    if (R0->light >= 0) {
+                        v3 to = sub(R0->y, so);
+                        double dl = length(to);
+                        sd = scl(to, 1.0 / dl);
+                        tmax = (1.0 - 1e-4) * dl;
+                    }
+                    st->shadow_rays++;
+                    if (!occluded(S, so, sd, tmax)) L = add(L, scl(hmul(beta, c), R0->W));
+                }
+            }
+        } else if (nee && C.has_smooth && (has_env || S->n_quads > 0)) {
+            /* next-event estimation */
             double u2 = U(p, s, (uint32_t)k, DIM_LIGHT_PICK, seed);
             double u3 = U(p, s, (uint32_t)k, DIM_LIGHT_U, seed);
             double u4 = U(p, s, (uint32_t)k, DIM_LIGHT_V, seed);
@@ -1262,13 +1536,89 @@ static void* worker(void* arg) {
 
 /* Render samples s0 .. s0+spp-1 of the crop [x0, x0+cw) x [y0, y0+ch) of the full frame.
  * sum_out receives the per-pixel sum of sample radiance (divide by spp for the estimate).
+ * restir = NULL for next-event estimation, else {M candidates, K neighbours, radius R}: ReSTIR
+ * DI at the primary vertex over the window (row_step is then ignored).
  * cam = origin[3], target[3], up[3], lens_radius, focus_distance; row_step > 1 renders only every row_step-th
  * row of the crop (others stay 0); flags as for trace_path.  stats_out (5 int64): extension rays, shadow rays, NaN
  * samples dropped, roulette terminations, paths. */
+/* pass 3 of ReSTIR: the paths of sample J->s, vertex 0 shading the final reservoirs */
+typedef struct {
+    restir_job* R;
+    uint32_t i, spp;
+    double* sum;
+    double* samples;
+    ostats st;
+} restir_path_job;
+
+static void* restir_pass_paths(void* arg) {
+    restir_path_job* P = (restir_path_job*)arg;
+    restir_job* J = P->R;
+    for (int ry = J->tid; ry < J->ch; ry += J->nthreads)
+        for (int rx = 0; rx < J->cw; ++rx) {
+            size_t i = (size_t)ry * J->cw + rx;
+            v3 L = trace_path_r(J->S, J->cam, J->x0 + rx, J->y0 + ry, J->s, J->max_depth, J->seed, J->flags,
+                                &P->st, 1, &J->fin[i], &J->surf[i]);
+            P->st.paths++;
+            if (!isfinite(L.x) || !isfinite(L.y) || !isfinite(L.z)) {
+                P->st.nan_dropped++;
+                L = splat(0.0);
+            }
+            double* o = &P->sum[i * 3];
+            o[0] += L.x; o[1] += L.y; o[2] += L.z;
+            if (P->samples) {
+                double* sp = &P->samples[(i * P->spp + P->i) * 3];
+                sp[0] = L.x; sp[1] = L.y; sp[2] = L.z;
+            }
+        }
+    return NULL;
+}
+
+static void run_threads(void* (*fn)(void*), void* jobs, size_t job_size, int nthreads) {
+    pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+    for (int t = 0; t < nthreads; ++t) {
+        void* j = (char*)jobs + job_size * (size_t)t;
+        if (nthreads == 1) fn(j);
+        else pthread_create(&th[t], NULL, fn, j);
+    }
+    if (nthreads > 1)
+        for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(th);
+}
+
+static void render_restir(const oscene* S, const ocam* cam, int x0, int y0, int cw, int ch, uint32_t s0,
+                          uint32_t spp, int max_depth, uint64_t seed, int flags, int nthreads, const int* rp,
+                          double* sum_out, double* samples_out, long long* tot) {
+    size_t npx = (size_t)cw * ch;
+    osurf* surf = (osurf*)calloc(npx, sizeof(osurf));
+    oresv* init = (oresv*)calloc(npx, sizeof(oresv));
+    oresv* fin = (oresv*)calloc(npx, sizeof(oresv));
+    restir_job* jobs = (restir_job*)calloc((size_t)nthreads, sizeof(restir_job));
+    restir_path_job* pj = (restir_path_job*)calloc((size_t)nthreads, sizeof(restir_path_job));
+    for (uint32_t i = 0; i < spp; ++i) {
+        for (int t = 0; t < nthreads; ++t) {
+            restir_job* J = &jobs[t];
+            J->S = S; J->cam = cam; J->x0 = x0; J->y0 = y0; J->cw = cw; J->ch = ch;
+            J->M = rp[0]; J->K = rp[1]; J->R = rp[2];
+            J->max_depth = max_depth; J->flags = flags; J->s = s0 + i; J->seed = seed;
+            J->surf = surf; J->init = init; J->fin = fin; J->tid = t; J->nthreads = nthreads;
+            pj[t].R = J; pj[t].i = i; pj[t].spp = spp; pj[t].sum = sum_out; pj[t].samples = samples_out;
+        }
+        run_threads(restir_pass_initial, jobs, sizeof(restir_job), nthreads);
+        run_threads(restir_pass_spatial, jobs, sizeof(restir_job), nthreads);
+        run_threads(restir_pass_paths, pj, sizeof(restir_path_job), nthreads);
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        tot[0] += pj[t].st.ext_rays; tot[1] += pj[t].st.shadow_rays;
+        tot[2] += pj[t].st.nan_dropped; tot[3] += pj[t].st.rr_terminated;
+        tot[4] += pj[t].st.paths;
+    }
+    free(surf); free(init); free(fin); free(jobs); free(pj);
+}
+
 void oracle_render(void* hs, const double* cam9, double vfov_deg, int width, int height,
                    int x0, int y0, int cw, int ch, uint32_t s0, uint32_t spp, int max_depth,
                    uint64_t seed, int flags, int nthreads, int row_step, double* sum_out,
-                   double* samples_out, long long* stats_out) {
+                   double* samples_out, long long* stats_out, const int* restir) {
     ocam cam;
     cam.origin = mk(cam9[0], cam9[1], cam9[2]);
     cam.target = mk(cam9[3], cam9[4], cam9[5]);
@@ -1281,6 +1631,14 @@ void oracle_render(void* hs, const double* cam9, double vfov_deg, int width, int
     if (nthreads < 1) nthreads = 1;
     if (row_step < 1) row_step = 1;
     memset(sum_out, 0, sizeof(double) * 3 * (size_t)cw * ch);
+    if (restir) {
+        /* every pixel of the window takes part in the spatial pass: row_step must be 1 */
+        long long tot[5] = {0, 0, 0, 0, 0};
+        render_restir((const oscene*)hs, &cam, x0, y0, cw, ch, s0, spp, max_depth, seed, flags, nthreads, restir,
+                      sum_out, samples_out, tot);
+        if (stats_out) memcpy(stats_out, tot, sizeof(tot));
+        return;
+    }
     job_t* jobs = (job_t*)calloc((size_t)nthreads, sizeof(job_t));
     pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
     for (int t = 0; t < nthreads; ++t) {

@@ -290,6 +290,30 @@ def cornell_box(seed=0, width=64, height=64, spp=16, max_depth=4) -> Scene:
                  {"seed": seed})
 
 
+def many_light_box(n_lights=64, seed=0, width=64, height=64, spp=16, max_depth=4) -> Scene:
+    """The Cornell geometry lit by `n_lights` small quads instead of one: 60 % on the ceiling
+    facing down, the rest on the two side walls facing in; side 0.03-0.07, radiance with a
+    heavy (Pareto, shape 1.5) tail and random tints.  A few lights dominate each point and
+    which ones depends on where the point is: many-light direct illumination."""
+    base = cornell_box(seed=seed, width=width, height=height, spp=spp, max_depth=max_depth)
+    rng = _rng(seed + 101)
+    lights = []
+    for _ in range(n_lights):
+        size = rng.uniform(0.03, 0.07)
+        tint = rng.uniform(0.4, 1.0, 3)
+        L = tuple(3.0 * (rng.pareto(1.5) + 1.0) * tint / tint.max())
+        a, b = rng.uniform(0.05, 0.95 - size, 2)
+        where = rng.random()
+        if where < 0.6:                                   # ceiling, normal -y
+            lights.append(quad_light((a, 1.0 - 1e-3, b), (size, 0.0, 0.0), (0.0, 0.0, size), L))
+        elif where < 0.8:                                 # wall x = 0, normal +x
+            lights.append(quad_light((1e-3, a, b), (0.0, size, 0.0), (0.0, 0.0, size), L))
+        else:                                             # wall x = 1, normal -x
+            lights.append(quad_light((1.0 - 1e-3, a, b), (0.0, 0.0, size), (0.0, size, 0.0), L))
+    return Scene("many_light_box", base.vertices, base.indices, base.material_ids, base.materials,
+                 np.stack(lights), None, base.camera, spp, max_depth, {"seed": seed, "n_lights": n_lights})
+
+
 # --------------------------------------------------------------------------------------------
 # Config 2: synthetic CAD pushbutton (lathe of a seeded spline profile)
 # --------------------------------------------------------------------------------------------

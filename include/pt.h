@@ -143,7 +143,27 @@ enum {
 
 /* wavefront kernel kinds, indices of pt_render_opts.kernel_ms */
 enum { PT_K_RAYGEN = 0, PT_K_TRACE = 1, PT_K_SORT = 2, PT_K_SHADE = 3, PT_K_SHADOW = 4, PT_K_ACCUM = 5,
-       PT_K_TAIL = 6, PT_K_KINDS = 7 };
+       PT_K_TAIL = 6, PT_K_RESTIR = 7, PT_K_KINDS = 8 };
+
+/* ReSTIR DI at the primary vertex (the paper names reservoir resampling for many-light
+ * scenes as future work, Sec. 2 and Sec. 6.3; the algorithm is Bitterli et al. 2020).  Per
+ * pixel and sample: `candidates` light samples from the next-event light sampler are
+ * resampled into a one-sample reservoir with target = luminance of the unshadowed
+ * contribution f L_e |cos| G; one spatial pass then resamples the reservoirs of up to
+ * `spatial_neighbors` pixels of the same sample (offsets uniform in [-R, R]^2, R =
+ * `spatial_radius`, inside the window; neighbours with normal cosine < 0.9 or depth
+ * differing by > 10 % are skipped) with the unbiased 1/Z weights.  Vertex 0 shades the
+ * result with one shadow ray in place of next-event estimation, and a BSDF-sampled light
+ * hit at vertex 1 then counts with weight 0.  Each wave holds whole samples of the window.
+ * Random numbers: candidate i uses (pixel, sample, 0xFFFF0001, dims 4i..4i+3), neighbour j
+ * (pixel, sample, 0xFFFF0002, dims 4j..4j+2).  Wavefront mode only (PT_MODE_MEGAKERNEL and
+ * the radiance cache give PT_ERR_UNSUPPORTED); not with PT_FLAG_NO_NEE. */
+typedef struct {
+    uint32_t candidates;        /* M >= 1 (at most 4096) */
+    uint32_t spatial_neighbors; /* K, 0..64 (0 = no spatial pass) */
+    uint32_t spatial_radius;    /* R >= 1 pixels (at most 4096) */
+    uint32_t reserved;          /* 0 */
+} pt_restir_opts;
 
 enum {
     PT_MODE_AUTO = 0,           /* pick per the autotuned table (pt_autotune) */
@@ -180,6 +200,8 @@ typedef struct {
                                    each replay, so progressive calls reuse one graph.  The capture
                                    runs on a stream of the scene; replays run on cuda_stream.  Not
                                    with nrc or kernel_ms (those calls launch directly). */
+    const pt_restir_opts* restir; /* optional: ReSTIR DI at the primary vertex (NULL = next-event
+                                   estimation) */
 } pt_render_opts;
 
 typedef struct {

@@ -127,7 +127,8 @@ class Scene:
 
     def render(self, spp, max_depth=None, seed=0, accum=None, camera=None, crop=None, flags=0,
                mode=N.PT_MODE_AUTO, wave_paths=0, sort=-1, sample_out=None, block_size=0, stream=None,
-               kernel_ms=None, kernel_launches=None, nrc=None, nrc_train=False, tail_paths=0, use_graph=False):
+               kernel_ms=None, kernel_launches=None, nrc=None, nrc_train=False, tail_paths=0, use_graph=False,
+               restir=None):
         cam = camera or self.desc.camera
         max_depth = self.desc.max_depth if max_depth is None else max_depth
         if crop is None:
@@ -140,6 +141,10 @@ class Scene:
         o.wave_paths, o.sort_by_material, o.block_size = wave_paths, sort, block_size
         o.tail_paths = int(tail_paths)
         o.use_graph = 1 if use_graph else 0
+        if restir is not None:
+            # (M candidates, K neighbours, radius R): ReSTIR DI at the primary vertex
+            ro = N.pt_restir_opts(int(restir[0]), int(restir[1]), int(restir[2]), 0)
+            o.restir = C.pointer(ro)
         o.sample_out = _ptr(sample_out) if sample_out is not None else None
         if nrc is not None:
             o.nrc = nrc.h

@@ -959,7 +959,70 @@ struct ShadowRay {
     float tmax;
 };
 
-enum { FLAG_NO_NEE = 1u, FLAG_NO_RR = 2u, FLAG_COUNT = 4u };
+enum { FLAG_NO_NEE = 1u, FLAG_NO_RR = 2u, FLAG_COUNT = 4u, FLAG_RESTIR = 1u << 16 /* internal */ };
+
+// ------------------------------------------------------------------ ReSTIR DI (primary vertex)
+// Reservoir resampling of light samples (Bitterli et al. 2020), which the paper names as
+// future work for many lights (Sec. 2, Sec. 6.3).  A light sample is (light, y): a quad
+// index and a point on it (area measure), or LIGHT_ENV and a direction (solid angle).
+// Reservoir records: float4 (y, light bits), float4 (W, M, target at the owner, 0).
+constexpr uint32_t RESTIR_CANDIDATES = 0xFFFF0001u, RESTIR_SPATIAL = 0xFFFF0002u;
+constexpr int LIGHT_NONE = -2, LIGHT_ENV = -1;
+
+// Unshadowed contribution c = f(wo, w_y) L_e(y) |cos| G(y) of light sample (light, y) at the
+// surface point x with frame (tt, bb, n) and closure C (G = cos_l / d^2 on a quad, 1 for the
+// environment); returns the target, the luminance of c (0 where the light cannot reach x).
+__device__ __forceinline__ float restir_target(const DScene& S, float3 x, float3 tt, float3 bb, float3 n,
+                                               const Closure& C, float3 wo, int light, float3 y, float3& c,
+                                               float3& ld) {
+    float3 Le;
+    float geo;
+    c = splat3(0.0f);
+    ld = splat3(0.0f);
+    if (light >= 0) {
+        const DQuad& q = S.quads[light];
+        const float3 to = y - x;
+        const float d2 = dot3(to, to);
+        if (!(d2 > 0.0f)) return 0.0f;
+        ld = to * (1.0f / sqrtf(d2));
+        const float cl = -dot3(ld, q.n);
+        if (!(cl > 0.0f || (q.two_sided && cl < 0.0f))) return 0.0f;
+        Le = q.L;
+        geo = fabsf(cl) / d2;
+    } else if (light == LIGHT_ENV) {
+        ld = y;
+        Le = env_radiance(S, ld);
+        geo = 1.0f;
+    } else {
+        return 0.0f;
+    }
+    const float3 wl = mk3(dot3(ld, tt), dot3(ld, bb), dot3(ld, n));
+    float3 f;
+    float pdf;
+    closure_eval(C, wo, wl, f, pdf);
+    c = (f * Le) * (fabsf(wl.z) * geo);
+    const float ph = lum3(c);
+    return (ph > 0.0f && isfinite(ph)) ? ph : 0.0f;
+}
+
+// The primary surface of a path as the reservoirs see it, rebuilt from its position, the
+// direction towards the camera and the triangle (the same steps as shade_vertex_h).
+struct RSurf {
+    float3 x, n, tt, bb, wo;
+    Closure C;
+};
+__device__ __forceinline__ void rsurf_make(const DScene& S, float3 x, float3 wo_w, uint32_t tri, RSurf& g) {
+    const float4 ta = __ldg(S.tris + 3u * tri), tb = __ldg(S.tris + 3u * tri + 1), tc = __ldg(S.tris + 3u * tri + 2);
+    const float3 ng = norm3(cross3(xyz(tb) - xyz(ta), xyz(tc) - xyz(ta)));
+    const bool front = dot3(wo_w, ng) > 0.0f;
+    const DMat M = S.mats[__float_as_uint(tb.w)];
+    g.x = x;
+    g.n = front ? ng : -ng;
+    if (M.spec_aniso > 0.0f) tangent_frame(g.n, xyz(tb) - xyz(ta), M.spec_rot, g.tt, g.bb);
+    else onb(g.n, g.tt, g.bb);
+    g.wo = mk3(dot3(wo_w, g.tt), dot3(wo_w, g.bb), dot3(wo_w, g.n));
+    closure_setup(g.C, M, front, g.wo.z);
+}
 
 enum ShadeResult { SHADE_END = 0, SHADE_CONTINUE = 1 };
 
@@ -986,18 +1049,22 @@ struct NoHook {
 template <class Hook>
 __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, float3 o, float3 d, uint32_t k,
                                               uint32_t max_depth, uint32_t flags, const VertexRng& rng,
-                                              PathState& ps, ShadeOut& out, Hook& hook) {
+                                              PathState& ps, ShadeOut& out, Hook& hook,
+                                              const float4* rres = nullptr) {
     out.has_shadow = false;
     out.rr_end = false;
     const bool nee = !(flags & FLAG_NO_NEE);
     const bool has_env = S.env_w > 0 && S.env_total > 0.0f;
     const float p_env = has_env ? (S.n_quads > 0 ? 0.5f : 1.0f) : 0.0f;
     const bool prev_delta = ps.prev_pdf < 0.0f;
+    // with ReSTIR DI the reservoir at vertex 0 estimates all light arriving there: a light
+    // reached by BSDF sampling from vertex 0 counts with weight 0 (1 after a delta lobe)
+    const bool restir1 = (flags & FLAG_RESTIR) && k == 1;
     if (h.tri == PT_NO_HIT) {
         if (has_env) {
             const float3 Le = env_radiance(S, d);
             float w = 1.0f;
-            if (!prev_delta && nee) w = power_heuristic(ps.prev_pdf, p_env * env_pdf(S, d));
+            if (!prev_delta && nee) w = restir1 ? 0.0f : power_heuristic(ps.prev_pdf, p_env * env_pdf(S, d));
             ps.L = ps.L + (ps.beta * Le) * w;
         }
         return SHADE_END;
@@ -1015,7 +1082,7 @@ __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, 
             float w = 1.0f;
             if (!prev_delta && nee) {
                 const float pl = (1.0f - p_env) / (float)S.n_quads * h.t * h.t / (q.area * fabsf(cl));
-                w = power_heuristic(ps.prev_pdf, pl);
+                w = restir1 ? 0.0f : power_heuristic(ps.prev_pdf, pl);
             }
             ps.L = ps.L + (ps.beta * q.L) * w;
         }
@@ -1036,7 +1103,32 @@ __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, 
     closure_setup(C, M, front, wo.z);
 
     const uint4 r0 = rng.block(0), r1 = rng.block(1), r2 = rng.block(2);
-    if (nee && C.has_smooth && (has_env || S.n_quads > 0)) {
+    if ((flags & FLAG_RESTIR) && k == 0) {
+        // the sample of the path's final reservoir in place of next-event estimation
+        if (rres != nullptr) {
+            const float4 ry = rres[0], rw = rres[1];
+            const int light = __float_as_int(ry.w);
+            if (light != LIGHT_NONE && rw.x > 0.0f) {
+                float3 c, ld;
+                if (restir_target(S, x, tt, bb, n, C, wo, light, xyz(ry), c, ld) > 0.0f) {
+                    const float3 so = offset_origin(x, ng, ld, S.eps);
+                    float3 sd = ld;
+                    float tmax = __int_as_float(0x7f800000);
+                    if (light >= 0) {
+                        const float3 to = xyz(ry) - so;
+                        const float dl = len3(to);
+                        sd = to * (1.0f / dl);
+                        tmax = (1.0f - 1e-4f) * dl;
+                    }
+                    out.has_shadow = true;
+                    out.sh.o = so;
+                    out.sh.d = sd;
+                    out.sh.tmax = tmax;
+                    out.sh.contrib = (ps.beta * c) * rw.x;
+                }
+            }
+        }
+    } else if (nee && C.has_smooth && (has_env || S.n_quads > 0)) {
         const float u2 = u24(r0.z), u3 = u24(r0.w), u4 = u24(r1.x);
         float3 ld, Le = splat3(0.0f), ly = splat3(0.0f);
         float pl = 0.0f;
@@ -1108,9 +1200,9 @@ __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, 
 
 __device__ __forceinline__ int shade_vertex(const DScene& S, const HitRec& h, float3 o, float3 d, uint32_t k,
                                             uint32_t max_depth, uint32_t flags, const VertexRng& rng,
-                                            PathState& ps, ShadeOut& out) {
+                                            PathState& ps, ShadeOut& out, const float4* rres = nullptr) {
     NoHook nh;
-    return shade_vertex_h(S, h, o, d, k, max_depth, flags, rng, ps, out, nh);
+    return shade_vertex_h(S, h, o, d, k, max_depth, flags, rng, ps, out, nh, rres);
 }
 
 // "diffuse-ish" measure of a vertex: diffuse lobes count as roughness 1

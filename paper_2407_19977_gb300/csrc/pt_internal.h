@@ -73,6 +73,14 @@ struct WaveBuffers {
     uint32_t* train_nv = nullptr;
     uint32_t* train_id = nullptr;
     float* train_samples = nullptr;
+    // ReSTIR DI buffers (allocated on the first ReSTIR render): per path the primary surface
+    // (x, depth), (wo, triangle), (normal), and the initial and final reservoirs (2 float4 each)
+    uint32_t restir_capacity = 0;
+    float4* rs_g0 = nullptr;
+    float4* rs_g1 = nullptr;
+    float4* rs_gn = nullptr;
+    float4* rs_i = nullptr;
+    float4* rs_f = nullptr;
 };
 
 struct pt_scene {

@@ -328,6 +328,14 @@ struct WfParams {
     float* train_rec;         // training slots x rec_per_path x 16 floats
     uint32_t* train_nv;       // vertices recorded per training path
     uint32_t* train_id;       // path id of each training path
+    // ReSTIR DI at the primary vertex (whole windows per wave)
+    int restir_on;
+    uint32_t restir_M, restir_K, restir_R;
+    float4* rs_g0;            // per path: primary hit point, depth
+    float4* rs_g1;            // per path: direction towards the camera, triangle bits (PT_NO_HIT: none)
+    float4* rs_gn;            // per path: shading normal
+    float4* rs_i;             // per path: initial reservoir (2 float4)
+    float4* rs_f;             // per path: final reservoir (2 float4)
     float* train_samples;     // training sample records (16 floats)
 };
 
@@ -562,6 +570,165 @@ __global__ void k_wf_sort_scatter(WfParams P, int in_q) {
     }
 }
 
+// ReSTIR DI, pass 1 (bounce 0, after the closest hits, queue 0 whose slot is the path id):
+// the primary surface of every path and its initial reservoir.  M candidates from the
+// next-event light sampler (source pdf in area measure on a quad, solid angle for the
+// environment) are resampled with target = luminance of their unshadowed contribution; the
+// reservoir keeps candidate i with probability w_i / sum w (u * sum w < w_i, streaming) and
+// W = sum w / (M target).  Paths with no surface to light get triangle PT_NO_HIT.
+__global__ void __launch_bounds__(128) k_restir_init(WfParams P) {
+    if (P.counters[C_TAIL]) return;
+    const uint32_t count = P.counters[C_Q0];
+    const uint32_t sbase = wf_sample_base(P);
+    const uint64_t seed = wf_seed(P);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const DScene& S = P.S;
+    const bool has_env = S.env_w > 0 && S.env_total > 0.0f;
+    const float p_env = has_env ? (S.n_quads > 0 ? 0.5f : 1.0f) : 0.0f;
+    for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < count; slot += gridDim.x * blockDim.x) {
+        const float4 ro = P.ray_o[0][slot], rd = P.ray_d[0][slot];
+        const float4 hh = P.hit[slot];
+        const uint32_t id = __float_as_uint(rd.w);
+        const uint32_t tri = __float_as_uint(hh.w);
+        float4 g1 = make_float4(0.0f, 0.0f, 0.0f, __uint_as_float(PT_NO_HIT));
+        float4 r0 = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(LIGHT_NONE));
+        float4 r1 = make_float4(0.0f, (float)P.restir_M, 0.0f, 0.0f);
+        bool valid = tri != PT_NO_HIT && P.max_depth > 0 && (has_env || S.n_quads > 0);
+        if (valid) valid = !(__float_as_uint(__ldg(S.tris + 3u * tri + 1).w) & PT_LIGHT_BIT);
+        RSurf g;
+        if (valid) {
+            const float3 x = xyz(ro) + xyz(rd) * hh.x;
+            rsurf_make(S, x, -xyz(rd), tri, g);
+            valid = g.C.has_smooth;
+        }
+        if (valid) {
+            const float3 wo_w = -xyz(rd);
+            P.rs_g0[id] = make_float4(g.x.x, g.x.y, g.x.z, hh.x);
+            P.rs_gn[id] = make_float4(g.n.x, g.n.y, g.n.z, 0.0f);
+            g1 = make_float4(wo_w.x, wo_w.y, wo_w.z, __uint_as_float(tri));
+            const uint32_t lp = P.pb + id % P.npix;
+            const uint32_t p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
+            const uint32_t s = sbase + id / P.npix;
+            float wsum = 0.0f, ph_sel = 0.0f;
+            int sel = LIGHT_NONE;
+            float3 y_sel = splat3(0.0f);
+            for (uint32_t i = 0; i < P.restir_M; ++i) {
+                const uint4 r = philox4x32_10(make_uint4(p, s, RESTIR_CANDIDATES, i), k0, k1);
+                const float u_pick = u24(r.x), u = u24(r.y), v = u24(r.z), u_sel = u24(r.w);
+                int light;
+                float3 y;
+                float src;
+                if (u_pick < p_env) {
+                    float pe;
+                    float3 Ld;
+                    if (!env_sample(S, u, v, y, pe, Ld)) continue;
+                    light = LIGHT_ENV;
+                    src = p_env * pe;
+                } else {
+                    int l = (int)floorf((u_pick - p_env) / (1.0f - p_env) * (float)S.n_quads);
+                    l = min(l, S.n_quads - 1);
+                    const DQuad& q = S.quads[l];
+                    light = l;
+                    y = q.p0 + q.e1 * u + q.e2 * v;
+                    src = (1.0f - p_env) / (float)S.n_quads / q.area;
+                }
+                if (!(src > 0.0f)) continue;
+                float3 c, ld;
+                const float ph = restir_target(S, g.x, g.tt, g.bb, g.n, g.C, g.wo, light, y, c, ld);
+                const float w = ph / src;
+                if (!(w > 0.0f)) continue;
+                wsum += w;
+                if (u_sel * wsum < w) {
+                    sel = light;
+                    y_sel = y;
+                    ph_sel = ph;
+                }
+            }
+            r0 = make_float4(y_sel.x, y_sel.y, y_sel.z, __int_as_float(sel));
+            const float W = (sel != LIGHT_NONE && ph_sel > 0.0f) ? wsum / ((float)P.restir_M * ph_sel) : 0.0f;
+            r1 = make_float4(W, (float)P.restir_M, ph_sel, 0.0f);
+        }
+        P.rs_g1[id] = g1;
+        P.rs_i[2u * id] = r0;
+        P.rs_i[2u * id + 1] = r1;
+    }
+}
+
+// ReSTIR DI, pass 2: one spatial pass.  Up to K neighbours of the same sample (offsets
+// uniform in [-R, R]^2 from the raw Philox words by multiply-shift, so every build picks the
+// same pixels), skipped outside the window, on the pixel itself, without a surface, with
+// normal cosine < 0.9 or depth differing by more than 10 %.  Their initial reservoirs are
+// resampled with w = target_here(y_j) W_j M_j; the result gets the unbiased weight
+// W = sum w / (Z target_here(y)), Z = the sum of M over the combined reservoirs (this one
+// included) whose own target is positive at y.  The wave holds whole windows.
+__global__ void __launch_bounds__(128) k_restir_spatial(WfParams P, uint32_t n) {
+    if (P.counters[C_TAIL]) return;
+    const uint32_t sbase = wf_sample_base(P);
+    const uint64_t seed = wf_seed(P);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t ch = P.npix / P.cw;
+    const uint32_t side = 2u * P.restir_R + 1u;
+    for (uint32_t id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
+        const float4 g1 = P.rs_g1[id];
+        const uint32_t tri = __float_as_uint(g1.w);
+        float4 f0 = P.rs_i[2u * id], f1 = P.rs_i[2u * id + 1];
+        if (tri != PT_NO_HIT) {
+            const float4 g0 = P.rs_g0[id];
+            RSurf g;
+            rsurf_make(P.S, xyz(g0), xyz(g1), tri, g);
+            const uint32_t lp = id % P.npix, base = id - lp;
+            const uint32_t rx = lp % P.cw, ry = lp / P.cw;
+            const uint32_t p = (P.y0 + ry) * P.cam.width + (P.x0 + rx);
+            const uint32_t s = sbase + id / P.npix;
+            float wsum = f1.z * f1.x * f1.y;
+            const float Mq = f1.y;
+            int light = __float_as_int(f0.w);
+            float3 y = xyz(f0);
+            uint32_t used[64];
+            uint32_t n_used = 0;
+            for (uint32_t j = 0; j < P.restir_K; ++j) {
+                const uint4 r = philox4x32_10(make_uint4(p, s, RESTIR_SPATIAL, j), k0, k1);
+                const int dx = (int)(((uint64_t)r.x * side) >> 32) - (int)P.restir_R;
+                const int dy = (int)(((uint64_t)r.y * side) >> 32) - (int)P.restir_R;
+                const float u_sel = u24(r.z);
+                const int nx = (int)rx + dx, ny = (int)ry + dy;
+                if ((dx == 0 && dy == 0) || nx < 0 || ny < 0 || nx >= (int)P.cw || ny >= (int)ch) continue;
+                const uint32_t nid = base + (uint32_t)ny * P.cw + (uint32_t)nx;
+                if (__float_as_uint(P.rs_g1[nid].w) == PT_NO_HIT) continue;
+                const float4 ng0 = P.rs_g0[nid], nn = P.rs_gn[nid];
+                if (dot3(xyz(nn), g.n) < 0.9f || fabsf(ng0.w - g0.w) > 0.1f * g0.w) continue;
+                used[n_used++] = nid;
+                const float4 a0 = P.rs_i[2u * nid], a1 = P.rs_i[2u * nid + 1];
+                float3 c, ld;
+                const float ph = restir_target(P.S, g.x, g.tt, g.bb, g.n, g.C, g.wo, __float_as_int(a0.w), xyz(a0), c, ld);
+                const float w = ph * a1.x * a1.y;
+                if (!(w > 0.0f)) continue;
+                wsum += w;
+                if (u_sel * wsum < w) {
+                    light = __float_as_int(a0.w);
+                    y = xyz(a0);
+                }
+            }
+            float3 c, ld;
+            const float ph = restir_target(P.S, g.x, g.tt, g.bb, g.n, g.C, g.wo, light, y, c, ld);
+            float Z = ph > 0.0f ? Mq : 0.0f;
+            for (uint32_t u = 0; u < n_used; ++u) {
+                const uint32_t nid = used[u];
+                const float4 n1 = P.rs_g1[nid];
+                RSurf gu;
+                rsurf_make(P.S, xyz(P.rs_g0[nid]), xyz(n1), __float_as_uint(n1.w), gu);
+                float3 c2, ld2;
+                if (restir_target(P.S, gu.x, gu.tt, gu.bb, gu.n, gu.C, gu.wo, light, y, c2, ld2) > 0.0f)
+                    Z += P.rs_i[2u * nid + 1].y;
+            }
+            f0 = make_float4(y.x, y.y, y.z, __int_as_float(light));
+            f1 = make_float4((ph > 0.0f && Z > 0.0f) ? wsum / (Z * ph) : 0.0f, Z, ph, 0.0f);
+        }
+        P.rs_f[2u * id] = f0;
+        P.rs_f[2u * id + 1] = f1;
+    }
+}
+
 template <bool NRC>
 __global__ void __launch_bounds__(128, 3) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
     if (P.counters[C_TAIL]) return;
@@ -608,7 +775,8 @@ __global__ void __launch_bounds__(128, 3) k_wf_shade(WfParams P, int in_q, int o
                 r = shade_vertex_h(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so, hook);
                 P.aux[id] = hook.aux;
             } else {
-                r = shade_vertex(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so);
+                const float4* rres = (P.restir_on && k == 0) ? P.rs_f + 2u * id : nullptr;
+                r = shade_vertex(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so, rres);
             }
             P.radiance[id] = make_float4(ps.L.x, ps.L.y, ps.L.z, 0.0f);
             if (so.rr_end) rr_cnt++;
@@ -799,7 +967,8 @@ __global__ void k_wf_accum(WfParams P) {
 pt_status pt_free_wave(WaveBuffers& w) {
     void* ps[] = {w.ray_o[0], w.ray_o[1], w.ray_d[0], w.ray_d[1], w.hit, w.beta, w.radiance,
                   w.sh_o, w.sh_d, w.sh_c, w.perm, w.keys, w.counters, w.aux, w.nrc_q, w.nrc_out,
-                  w.nrc_counters, w.train_rec, w.train_nv, w.train_id, w.train_samples};
+                  w.nrc_counters, w.train_rec, w.train_nv, w.train_id, w.train_samples,
+                  w.rs_g0, w.rs_g1, w.rs_gn, w.rs_i, w.rs_f};
     for (void* p : ps)
         if (p) cudaFree(p);
     w = WaveBuffers();
@@ -855,6 +1024,24 @@ static pt_status ensure_nrc_buffers(WaveBuffers& w, uint32_t rec_per_path, uint3
     return PT_OK;
 }
 
+// ReSTIR DI buffers for every path of a wave
+static pt_status ensure_restir_buffers(WaveBuffers& w) {
+    if (w.restir_capacity >= w.capacity) return PT_OK;
+    void* ps[] = {w.rs_g0, w.rs_g1, w.rs_gn, w.rs_i, w.rs_f};
+    for (void* q : ps)
+        if (q) cudaFree(q);
+    w.rs_g0 = w.rs_g1 = w.rs_gn = w.rs_i = w.rs_f = nullptr;
+    w.restir_capacity = 0;
+    const size_t c = w.capacity;
+    PT_CUDA_TRY(cudaMalloc(&w.rs_g0, c * sizeof(float4)));
+    PT_CUDA_TRY(cudaMalloc(&w.rs_g1, c * sizeof(float4)));
+    PT_CUDA_TRY(cudaMalloc(&w.rs_gn, c * sizeof(float4)));
+    PT_CUDA_TRY(cudaMalloc(&w.rs_i, 2 * c * sizeof(float4)));
+    PT_CUDA_TRY(cudaMalloc(&w.rs_f, 2 * c * sizeof(float4)));
+    w.restir_capacity = w.capacity;
+    return PT_OK;
+}
+
 static int g_trace_blocks_per_sm = 0, g_shade_blocks_per_sm = 0, g_shadow_blocks_per_sm = 0, g_tail_blocks_per_sm = 0;
 
 pt_status pt_wavefront_tail_limit(int* out) {
@@ -881,12 +1068,18 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     const uint32_t npix_total = acc->width * acc->height;
     uint32_t cap = o.wave_paths ? o.wave_paths : (1u << 21);
     cap = std::max(cap, 32u);
-    // waves hold whole samples of a pixel range: pixel chunk <= cap, then samples per wave
-    const uint32_t pix_chunk = std::min(npix_total, cap);
+    // waves hold whole samples of a pixel range: pixel chunk <= cap, then samples per wave;
+    // with ReSTIR the chunk is the whole window (the spatial pass reads any pixel of it)
+    const bool restir = o.restir != nullptr;
+    const uint32_t pix_chunk = restir ? npix_total : std::min(npix_total, cap);
     const uint32_t samp_per_wave = std::max(1u, std::min(spp, cap / pix_chunk));
     pt_status r = ensure_wave(s->wave, pix_chunk * samp_per_wave);
     if (r != PT_OK) return r;
     WaveBuffers& w = s->wave;
+    if (restir) {
+        r = ensure_restir_buffers(w);
+        if (r != PT_OK) return r;
+    }
     const bool sort = o.sort_by_material == 1 || (o.sort_by_material < 0 && s->n_mats + 2 <= MAX_SORT_KEYS && s->n_mats > 1);
     const uint32_t n_keys = (sort && s->n_mats + 2 <= MAX_SORT_KEYS) ? s->n_mats + 2 : 0;
     if (g_trace_blocks_per_sm == 0) {
@@ -924,6 +1117,14 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     P.perm = w.perm; P.keys = w.keys; P.counters = w.counters;
     P.sum = acc->sum; P.comp = acc->comp; P.sample_out = o.sample_out;
     P.stats = s->d_stats;
+    if (restir) {
+        P.flags |= FLAG_RESTIR;
+        P.restir_on = 1;
+        P.restir_M = o.restir->candidates;
+        P.restir_K = o.restir->spatial_neighbors;
+        P.restir_R = o.restir->spatial_radius;
+        P.rs_g0 = w.rs_g0; P.rs_g1 = w.rs_g1; P.rs_gn = w.rs_gn; P.rs_i = w.rs_i; P.rs_f = w.rs_f;
+    }
     if (o.nrc) {
         r = ensure_nrc_buffers(w, std::min(max_depth + 1, 16u), pt_nrc_frame_samples(o.nrc));
         if (r != PT_OK) return r;
@@ -1005,7 +1206,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                     const int in_q = (int)(k & 1u), out_q = (int)((k + 1) & 1u);
                     PT_LAUNCH(k_wf_setup, 1, 256, 0, st, w.counters, out_q, n_keys);
                     ++launches;
-                    if (tail_limit) {
+                    if (tail_limit && !(restir && k == 0)) {
                         e = begin(PT_K_TAIL);
                         if (P.nrc_on) {
                             if (count) PT_LAUNCH((k_wf_tail<true, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
@@ -1026,6 +1227,13 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                         e = begin(PT_K_SORT);
                         PT_LAUNCH(k_wf_sort_scan, 1, MAX_SORT_KEYS, 0, st, w.counters, n_keys);
                         PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
+                        end(e);
+                        launches += 2;
+                    }
+                    if (restir && k == 0) {
+                        e = begin(PT_K_RESTIR);
+                        PT_LAUNCH(k_restir_init, sms * 4, 128, 0, st, P);
+                        PT_LAUNCH(k_restir_spatial, sms * 4, 128, 0, st, P, n);
                         end(e);
                         launches += 2;
                     }
@@ -1153,6 +1361,18 @@ extern "C" pt_status pt_render(pt_scene* s, const pt_camera* camera, uint32_t sp
     PT_CHECK_ARG(acc->spp_done + spp < (1ull << 32), "sample index overflows 32 bits");
     PT_CHECK_ARG(o.mode <= PT_MODE_MEGAKERNEL, "unknown mode");
     PT_CHECK_ARG(!o.nrc || o.mode != PT_MODE_MEGAKERNEL, "the radiance cache runs in wavefront mode");
+    if (o.restir) {
+        const pt_restir_opts& ro = *o.restir;
+        PT_CHECK_ARG(ro.candidates >= 1 && ro.candidates <= 4096, "restir candidates must be 1..4096");
+        PT_CHECK_ARG(ro.spatial_neighbors <= 64, "restir spatial_neighbors must be 0..64");
+        PT_CHECK_ARG(ro.spatial_radius >= 1 && ro.spatial_radius <= 4096, "restir spatial_radius must be 1..4096");
+        PT_CHECK_ARG(ro.reserved == 0, "restir reserved field must be 0");
+        PT_CHECK_ARG(!(o.flags & PT_FLAG_NO_NEE), "ReSTIR DI replaces next-event estimation: not with PT_FLAG_NO_NEE");
+        if (o.mode == PT_MODE_MEGAKERNEL || o.nrc) {
+            pt_set_error("ReSTIR DI runs in wavefront mode without the radiance cache");
+            return PT_ERR_UNSUPPORTED;
+        }
+    }
     if (spp == 0) return PT_OK;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     s->last_stream = st;
@@ -1169,6 +1389,7 @@ extern "C" pt_status pt_render(pt_scene* s, const pt_camera* camera, uint32_t sp
         } else {
             mode = (o.nrc || (uint64_t)acc->width * acc->height >= (1u << 16)) ? PT_MODE_WAVEFRONT : PT_MODE_MEGAKERNEL;
         }
+        if (o.restir) mode = PT_MODE_WAVEFRONT;
     }
     pt_status r;
     if (mode == PT_MODE_WAVEFRONT) {
@@ -1360,6 +1581,7 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
                  "pt_render_noalloc renders windows of at most 16384 pixels; render larger images tile by tile");
     PT_CHECK_ARG(acc->spp_done + spp < (1ull << 32), "sample index overflows 32 bits");
     PT_CHECK_ARG(o.nrc == nullptr, "the radiance cache needs allocations: use pt_render");
+    PT_CHECK_ARG(o.restir == nullptr, "ReSTIR DI needs allocations: use pt_render");
     PT_CHECK_ARG(o.kernel_ms == nullptr && o.kernel_launches == nullptr, "kernel timing is not available here");
     if (spp == 0) return PT_OK;
     void* base = nullptr;

@@ -39,11 +39,15 @@ class pt_accum(C.Structure):
     _fields_ = [("sum", vp), ("comp", vp), ("spp_done", u64), ("width", u32), ("height", u32)]
 
 
+class pt_restir_opts(C.Structure):
+    _fields_ = [("candidates", u32), ("spatial_neighbors", u32), ("spatial_radius", u32), ("reserved", u32)]
+
+
 class pt_render_opts(C.Structure):
     _fields_ = [("crop_x0", u32), ("crop_y0", u32), ("flags", u32), ("mode", u32), ("wave_paths", u32),
                 ("sort_by_material", C.c_int32), ("block_size", u32), ("sample_out", vp), ("nrc", vp),
                 ("nrc_train", u32), ("kernel_ms", C.POINTER(f32)), ("kernel_launches", C.POINTER(u32)),
-                ("tail_paths", C.c_int32), ("use_graph", u32)]
+                ("tail_paths", C.c_int32), ("use_graph", u32), ("restir", C.POINTER(pt_restir_opts))]
 
 
 class pt_bvh_opts(C.Structure):
@@ -85,7 +89,7 @@ PT_FLAG_NO_RR = 2
 PT_FLAG_COUNT = 4
 PT_TUNE_BVH = 1
 PT_TONEMAP_SRGB = 1
-KERNEL_KINDS = ("raygen", "trace", "sort", "shade", "shadow", "accum", "tail")
+KERNEL_KINDS = ("raygen", "trace", "sort", "shade", "shadow", "accum", "tail", "restir")
 PT_MODE_AUTO, PT_MODE_WAVEFRONT, PT_MODE_MEGAKERNEL = 0, 1, 2
 
 # symbol -> (restype, argtypes); every symbol declared in include/pt.h

@@ -41,6 +41,8 @@ WORKLOADS = {
     "cornell1080": "Cornell-style box, 36 triangles, one quad light, 1920x1080, 1 spp/step, max depth 8",
     "pushbutton_dof": "the pushbutton frame through a thin lens (radius 0.03, focus on the button), "
                       "1920x1080, 1 spp/step, max depth 8",
+    "many_lights": "Cornell-style box lit by 256 small quad lights (heavy-tailed radiance, random tints) on "
+                   "the ceiling and side walls, 1920x1080, 1 spp/step, max depth 4",
 }
 NODE_BYTES = 80      # compressed 8-wide BVH node
 TRI_BYTES = 48       # triangle record
@@ -71,7 +73,7 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     ap.add_argument("--study-frames", type=int, default=256, help="frames per curve of the NRC study")
     ap.add_argument("--batch-scenes", type=int, default=64)
-    ap.add_argument("--study", default=None, choices=[None, "nrc", "batch", "paper"],
+    ap.add_argument("--study", default=None, choices=[None, "nrc", "batch", "paper", "restir"],
                     help="nrc: relMSE vs time, radiance cache against the plain tracer")
     ap.add_argument("--ref-spp", type=int, default=4096)
     return ap.parse_args()
@@ -201,6 +203,8 @@ def _make_workload(name):
         return scenes.cornell_box(width=512, height=512, spp=1, max_depth=8)
     if name == "cornell1080":
         return scenes.cornell_box(width=1920, height=1080, spp=1, max_depth=8)
+    if name == "many_lights":
+        return scenes.many_light_box(256, width=1920, height=1080, spp=1, max_depth=4, seed=0)
     if name == "pushbutton_dof":
         sc = scenes.pushbutton()
         c = sc.camera
@@ -449,6 +453,82 @@ def _relmse(img, ref, eps=1e-2):
     return float((d * d / (ref * ref + eps)).mean())
 
 
+def _time_to(curve, target):
+    """Device time at which a relMSE curve (points with spp, ms, relmse) first reaches
+    `target`, interpolated log-log between the marks around the crossing; None if never."""
+    prev = None
+    for p in curve:
+        if p["relmse"] <= target:
+            if prev is None:
+                return p["ms"]
+            a, b = math.log(prev["relmse"]), math.log(p["relmse"])
+            w = (math.log(target) - a) / (b - a) if b != a else 1.0
+            return math.exp(math.log(prev["ms"]) + w * (math.log(p["ms"]) - math.log(prev["ms"])))
+        prev = p
+    return None
+
+
+def run_restir_study(args, local):
+    """relMSE against a high-spp plain reference as a function of device time on the
+    many-light box at 1080p: the plain tracer (next-event estimation with MIS) against ReSTIR DI
+    at the primary vertex, both progressive at 1 spp per frame with graph replay."""
+    import torch
+    from paper_2407_19977_gb300 import api
+    from paper_2407_19977_gb300 import native as N
+    torch.cuda.set_device(local)
+    name = args.workload if args.workload != "pushbutton" else "many_lights"
+    sc = _make_workload(name)
+    W, H = sc.camera.width, sc.camera.height
+    scene = api.Scene(sc)
+    stream = torch.cuda.current_stream()
+    ref = api.Accum(W, H)
+    chunk = 64
+    for _ in range(args.ref_spp // chunk):
+        scene.render(chunk, seed=777, accum=ref, mode=N.PT_MODE_WAVEFRONT)
+    torch.cuda.synchronize()
+    ref_img = ref.image()
+    marks = [m for m in (1, 2, 4, 8, 16, 32, 64, 128, 256) if m <= args.study_frames]
+    variants = {"plain": None, "restir_M32_K5_R10": (32, 5, 10), "restir_M8_K5_R10": (8, 5, 10)}
+    curves, split = {}, {}
+    for kind, r in variants.items():
+        acc = api.Accum(W, H)
+        for _ in range(3):     # warm-up and graph capture, then start over
+            scene.render(1, seed=0, accum=acc, mode=N.PT_MODE_WAVEFRONT, restir=r, use_graph=True)
+        acc.reset()
+        t_ms = 0.0
+        pts = []
+        for f in range(1, marks[-1] + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            scene.render(1, seed=0, accum=acc, mode=N.PT_MODE_WAVEFRONT, restir=r, use_graph=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            if f in marks:
+                pts.append({"spp": f, "ms": t_ms, "relmse": _relmse(acc.image(), ref_img)})
+        curves[kind] = pts
+        km = (N.f32 * len(N.KERNEL_KINDS))()
+        probe = api.Accum(W, H)
+        for _ in range(4):
+            scene.render(1, seed=1, accum=probe, mode=N.PT_MODE_WAVEFRONT, restir=r, kernel_ms=km)
+        split[kind] = {n: round(float(km[i]) / 4, 4) for i, n in enumerate(N.KERNEL_KINDS) if km[i] > 0}
+    out = {"study": "restir_equal_time", "workload": WORKLOADS[name], "ref_spp": args.ref_spp,
+           "relmse_eps": 1e-2, "curves": curves, "kernel_ms_per_frame": split}
+    for spp in (16, 64):
+        if spp > marks[-1]:
+            continue
+        target = next(p["relmse"] for p in curves["plain"] if p["spp"] == spp)
+        tp = next(p["ms"] for p in curves["plain"] if p["spp"] == spp)
+        res = {"relmse": target, "plain_ms": tp}
+        for kind in variants:
+            if kind == "plain":
+                continue
+            tr = _time_to(curves[kind], target)
+            res[kind] = {"ms": tr, "speedup": (tp / tr) if tr else None}
+        out[f"at_plain_{spp}spp"] = res
+    print(json.dumps(out))
+
+
 def run_nrc_study(args, local):
     """relMSE against a high-spp plain reference as a function of device time, for the plain
     tracer and for the radiance-cache tracer (trained online every frame)."""
@@ -486,20 +566,7 @@ def run_nrc_study(args, local):
                 pts.append({"spp": f, "ms": t_ms, "relmse": _relmse(acc.image(), ref_img)})
         curves[kind] = pts
 
-    def time_to(curve, target):
-        prev = None
-        for p in curve:
-            if p["relmse"] <= target:
-                if prev is None:
-                    return p["ms"]
-                # log-log interpolation between the marks around the crossing
-                import math as m
-                a, b = m.log(prev["relmse"]), m.log(p["relmse"])
-                w = (m.log(target) - a) / (b - a) if b != a else 1.0
-                return m.exp(m.log(prev["ms"]) + w * (m.log(p["ms"]) - m.log(prev["ms"])))
-            prev = p
-        return None
-
+    time_to = _time_to
     out = {"study": "nrc_equal_time", "workload": WORKLOADS[args.workload], "ref_spp": args.ref_spp,
            "relmse_eps": 1e-2, "curves": curves}
     for spp in (16, 64):
@@ -657,6 +724,10 @@ def main():
     if args.study == "nrc":
         if rank == 0:
             run_nrc_study(args, local)
+        return
+    if args.study == "restir":
+        if rank == 0:
+            run_restir_study(args, local)
         return
     if args.study == "paper":
         if rank == 0:

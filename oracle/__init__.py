@@ -84,6 +84,8 @@ def _load():
         lib.oracle_render.argtypes = [C.c_void_p, _dp, C.c_double, C.c_int, C.c_int, C.c_int,
                                       C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_int,
                                       C.c_uint64, C.c_int, C.c_int, C.c_int, _dp, _dp, _i64p, _i32p]
+        lib.oracle_features.argtypes = [C.c_void_p, _dp, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_uint64, _dp]
         lib.oracle_camera_ray.argtypes = [_dp, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_uint32, C.c_uint64, _dp, _dp]
         lib.oracle_bsdf_eval_batch.argtypes = [_dp, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
@@ -328,6 +330,22 @@ class OracleScene:
         st = dict(zip(("ext_rays", "shadow_rays", "nan_dropped", "rr_terminated", "paths"),
                       map(int, stats)))
         return out, samples, st
+
+
+def _cam9(cam):
+    return np.array([*cam.origin, *cam.target, *cam.up, getattr(cam, "lens_radius", 0.0),
+                     getattr(cam, "focus_distance", 1.0)], dtype=np.float64)
+
+
+def features(oscene, spp, seed=0, s0=0, crop=None, camera=None):
+    """Primary-hit features (ch, cw, 12): normal[3], scattering fraction, position[3], 0,
+    albedo[3], 0 -- the means over the render's samples s0 .. s0+spp-1."""
+    cam = camera or oscene.scene.camera
+    x0, y0, cw, ch = crop if crop is not None else (0, 0, cam.width, cam.height)
+    out = np.zeros((ch, cw, 12))
+    _load().oracle_features(oscene.h, _cam9(cam).ctypes.data_as(_dp), float(cam.vfov_deg), cam.width, cam.height,
+                            x0, y0, cw, ch, int(s0), int(spp), int(seed), out.ctypes.data_as(_dp))
+    return out
 
 
 def camera_ray(camera, px, py, sample, seed):

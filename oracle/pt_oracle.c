@@ -1681,6 +1681,51 @@ void oracle_camera_ray(const double* cam9, double vfov_deg, int width, int heigh
     d_out[0] = d.x; d_out[1] = d.y; d_out[2] = d.z;
 }
 
+/* Primary-hit features for the regression denoiser (inputs of BMFR, Koskela et al. 2019;
+ * the paper lists a denoiser as future work, Sec. 6.3).  For every pixel of the crop, the mean
+ * over samples s0 .. s0+spp-1 (the render's own camera rays) of the first hit's shading normal
+ * (turned towards the camera), position and albedo, and the fraction of those samples whose
+ * first hit is a scattering surface (a miss or a light quad adds nothing to the means).
+ * Reading: albedo = (m + (1-m)(1-t)) bw bc + (1-m) t tc.  out (ch*cw*12): n[3], fraction,
+ * p[3], 0, albedo[3], 0. */
+void oracle_features(void* hs, const double* cam9, double vfov_deg, int width, int height, int x0, int y0,
+                     int cw, int ch, uint32_t s0, uint32_t spp, uint64_t seed, double* out) {
+    const oscene* S = (const oscene*)hs;
+    ocam cam;
+    cam.origin = mk(cam9[0], cam9[1], cam9[2]);
+    cam.target = mk(cam9[3], cam9[4], cam9[5]);
+    cam.up = mk(cam9[6], cam9[7], cam9[8]);
+    cam.vfov_deg = vfov_deg;
+    cam.width = width;
+    cam.height = height;
+    cam.lens_radius = cam9[9];
+    cam.focus_distance = cam9[10];
+    for (int ry = 0; ry < ch; ++ry)
+        for (int rx = 0; rx < cw; ++rx) {
+            double acc[12] = {0};
+            for (uint32_t i = 0; i < spp; ++i) {
+                v3 o, d;
+                camera_ray(&cam, x0 + rx, y0 + ry, s0 + i, seed, &o, &d);
+                ohit h;
+                intersect(S, o, d, INFINITY, &h);
+                if (h.tri < 0 || S->tri_mat[h.tri] < 0) continue;
+                const omat* m = &S->mats[S->tri_mat[h.tri]];
+                v3 p0 = S->tv[3 * h.tri], p1 = S->tv[3 * h.tri + 1], p2 = S->tv[3 * h.tri + 2];
+                v3 ng = normalize(cross(sub(p1, p0), sub(p2, p0)));
+                v3 n = dot(scl(d, -1.0), ng) > 0.0 ? ng : scl(ng, -1.0);
+                v3 x = add(o, scl(d, h.t));
+                double mt = m->metalness, t = m->trans_weight;
+                v3 a = add(scl(m->base_color, (mt + (1.0 - mt) * (1.0 - t)) * m->base_weight),
+                           scl(m->trans_color, (1.0 - mt) * t));
+                acc[0] += n.x; acc[1] += n.y; acc[2] += n.z; acc[3] += 1.0;
+                acc[4] += x.x; acc[5] += x.y; acc[6] += x.z;
+                acc[8] += a.x; acc[9] += a.y; acc[10] += a.z;
+            }
+            double* o12 = &out[((size_t)ry * cw + rx) * 12];
+            for (int k = 0; k < 12; ++k) o12[k] = spp ? acc[k] / spp : 0.0;
+        }
+}
+
 /* ---- batched forms of the BSDF entry points (n tuples, row-major arrays) ---- */
 void oracle_bsdf_eval_batch(const double* matp, int front, int n, const double* wo,
                             const double* wi, double* f_out, double* pdf_out) {

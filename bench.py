@@ -73,7 +73,7 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     ap.add_argument("--study-frames", type=int, default=256, help="frames per curve of the NRC study")
     ap.add_argument("--batch-scenes", type=int, default=64)
-    ap.add_argument("--study", default=None, choices=[None, "nrc", "batch", "paper", "restir"],
+    ap.add_argument("--study", default=None, choices=[None, "nrc", "batch", "paper", "restir", "bmfr"],
                     help="nrc: relMSE vs time, radiance cache against the plain tracer")
     ap.add_argument("--ref-spp", type=int, default=4096)
     return ap.parse_args()
@@ -529,6 +529,53 @@ def run_restir_study(args, local):
     print(json.dumps(out))
 
 
+def run_bmfr_study(args, local):
+    """The regression denoiser on a 1080p frame: relMSE against a high-spp plain reference of
+    the noisy mean and of its BMFR output (one 32-pixel grid, and the mean over four grids
+    shifted by half a block), with the device time of the feature pass and of the regression."""
+    import torch
+    from paper_2407_19977_gb300 import api
+    from paper_2407_19977_gb300 import native as N
+    torch.cuda.set_device(local)
+    name = args.workload
+    sc = _make_workload(name)
+    W, H = sc.camera.width, sc.camera.height
+    scene = api.Scene(sc)
+    stream = torch.cuda.current_stream()
+    ref = api.Accum(W, H)
+    chunk = 64
+    for _ in range(args.ref_spp // chunk):
+        scene.render(chunk, seed=777, accum=ref, mode=N.PT_MODE_WAVEFRONT)
+    torch.cuda.synchronize()
+    ref_img = ref.image()
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b) / reps
+
+    rows = []
+    for spp in (1, 4, 16):
+        acc = api.Accum(W, H)
+        _, t_render = timed(lambda: (acc.reset(), scene.render(spp, seed=1, accum=acc, mode=N.PT_MODE_WAVEFRONT)))
+        color = acc.image()
+        feats, t_feat = timed(lambda: scene.features(spp, seed=1))
+        den, t_bmfr = timed(lambda: api.bmfr(color, feats, block=32))
+        grids = [(0, 0), (16, 0), (0, 16), (16, 16)]
+        den4 = sum(api.bmfr(color, feats, block=32, offset=o) for o in grids) / 4.0
+        rows.append({"spp": spp, "render_ms": t_render, "features_ms": t_feat, "bmfr_ms": t_bmfr,
+                     "relmse_noisy": _relmse(color, ref_img), "relmse_bmfr": _relmse(den, ref_img),
+                     "relmse_bmfr_4_grids": _relmse(den4, ref_img)})
+    print(json.dumps({"study": "bmfr", "workload": WORKLOADS[name], "ref_spp": args.ref_spp, "block": 32,
+                      "relmse_eps": 1e-2, "rows": rows}))
+
+
 def run_nrc_study(args, local):
     """relMSE against a high-spp plain reference as a function of device time, for the plain
     tracer and for the radiance-cache tracer (trained online every frame)."""
@@ -724,6 +771,10 @@ def main():
     if args.study == "nrc":
         if rank == 0:
             run_nrc_study(args, local)
+        return
+    if args.study == "bmfr":
+        if rank == 0:
+            run_bmfr_study(args, local)
         return
     if args.study == "restir":
         if rank == 0:

@@ -411,6 +411,39 @@ pt_status pt_bvh_export(pt_scene* scene, uint32_t* nodes_out, float* tris_out, u
 pt_status pt_tonemap(const pt_accum* accum, float exposure, uint32_t flags, uint8_t* rgba_out,
                      void* cuda_stream);
 
+/* Primary-hit features for the regression denoiser (the paper names denoising as future
+ * work, Sec. 6.3; BMFR, Koskela et al. 2019, takes these inputs).  For every pixel of the
+ * window (crop_x0, crop_y0, width, height) of the frame, the mean over samples
+ * s0 .. s0+spp-1 -- the same camera rays as pt_render's samples with that seed -- of the
+ * first hit's shading normal (turned towards the camera), hit position and albedo
+ * ((m + (1-m)(1-t)) base_weight base_color + (1-m) t transmission_color), and the fraction
+ * of the samples whose first hit is a scattering surface (misses and light quads add
+ * nothing to the means).
+ *  out  DEVICE float[height*width*12], 16-byte aligned, row-major: normal[3], fraction,
+ *       position[3], 0, albedo[3], 0
+ * Errors: PT_ERR_INVALID_ARG (NULL, window outside the frame, misaligned out, bad camera),
+ * PT_ERR_NOT_BUILT.  Asynchronous on the stream. */
+pt_status pt_render_features(pt_scene* scene, const pt_camera* camera, uint32_t crop_x0, uint32_t crop_y0,
+                             uint32_t width, uint32_t height, uint32_t s0, uint32_t spp, uint64_t seed,
+                             float* out, void* cuda_stream);
+
+/* Blockwise multi-order feature regression (BMFR): per square block of `block` pixels
+ * (block (i, j) covers x in [i*block - offset_x, (i+1)*block - offset_x), likewise y, clipped
+ * to the image), the least-squares fit of the demodulated colour c / (albedo + 0.01) on the
+ * columns 1, n[3], q[3], q[3]^2 over the block's pixels whose feature fraction is 1 (q = the
+ * position scaled to [-1, 1] over the block; n scaled likewise); a feature whose block range
+ * is at most 1e-4 * max(|lo|, |hi|, 0.01) is left out, then, in that column order, a column
+ * whose part outside the span of the kept earlier ones is at most 1e-3 of its norm.  The
+ * output is the fitted value times (albedo + 0.01); other pixels keep their colour.  FP32
+ * Householder QR per block in shared memory.
+ *  color     DEVICE float[height*width*3], mean radiance (e.g. sum / spp of an accumulator)
+ *  features  DEVICE float[height*width*12] from pt_render_features, 16-byte aligned
+ *  block     4..32; offset_x, offset_y < block
+ *  out       DEVICE float[height*width*3]; may be `color` itself
+ * Errors: PT_ERR_INVALID_ARG.  Asynchronous on the stream. */
+pt_status pt_denoise_bmfr(const float* color, const float* features, uint32_t width, uint32_t height,
+                          uint32_t block, uint32_t offset_x, uint32_t offset_y, float* out, void* cuda_stream);
+
 /* Statistics and sticky device error bits; synchronises the scene's last stream. */
 pt_status pt_get_stats(pt_scene* scene, pt_stats* out);
 pt_status pt_scene_sync(pt_scene* scene);

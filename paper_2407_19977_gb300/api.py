@@ -157,6 +157,16 @@ class Scene:
                C.byref(accum.c), C.byref(o), _stream_handle(stream))
         return accum
 
+    def features(self, spp, s0=0, seed=0, crop=None, camera=None, stream=None) -> torch.Tensor:
+        """pt_render_features: (h, w, 12) primary-hit features (normal, scattering fraction,
+        position, albedo) averaged over the samples s0 .. s0+spp-1 of pt_render's rays."""
+        cam = camera or self.desc.camera
+        x0, y0, cw, ch = crop if crop is not None else (0, 0, cam.width, cam.height)
+        out = torch.empty((ch, cw, 12), dtype=torch.float32, device="cuda")
+        N.call("pt_render_features", self.h, C.byref(make_camera(cam)), x0, y0, cw, ch, int(s0), int(spp),
+               C.c_uint64(int(seed)), _ptr(out), _stream_handle(stream))
+        return out
+
     def autotune(self, spp=1, max_depth=None, frames=2, bvh=False, camera=None, stream=None):
         """pt_autotune: the fastest schedule for frames like this one (stored in the scene for
         PT_MODE_AUTO).  Returns (options dict, ms per frame)."""
@@ -243,6 +253,19 @@ def uniforms(seed, keys: torch.Tensor, stream=None):
     n = keys.shape[0]
     out = torch.empty(n, dtype=torch.float32, device="cuda")
     N.call("pt_uniforms", C.c_uint64(int(seed)), _ptr(keys), n, _ptr(out), _stream_handle(stream))
+    return out
+
+
+def bmfr(color: torch.Tensor, features: torch.Tensor, block=32, offset=(0, 0), out=None, stream=None) -> torch.Tensor:
+    """pt_denoise_bmfr: blockwise feature regression of a mean-radiance image (h, w, 3) on the
+    primary-hit features (h, w, 12) of Scene.features; returns the denoised (h, w, 3)."""
+    h, w = color.shape[0], color.shape[1]
+    color = color.contiguous()
+    features = features.contiguous()
+    if out is None:
+        out = torch.empty_like(color)
+    N.call("pt_denoise_bmfr", _ptr(color), _ptr(features), w, h, int(block), int(offset[0]), int(offset[1]),
+           _ptr(out), _stream_handle(stream))
     return out
 
 

@@ -103,6 +103,8 @@ SIGNATURES = {
                                     C.POINTER(pt_render_opts), vp]),
     "pt_render_batch": (C.c_int, [C.POINTER(pt_job), u32, C.POINTER(pt_batch_opts), vp]),
     "pt_tonemap": (C.c_int, [C.POINTER(pt_accum), f32, u32, vp, vp]),
+    "pt_render_features": (C.c_int, [vp, C.POINTER(pt_camera), u32, u32, u32, u32, u32, u32, C.c_uint64, vp, vp]),
+    "pt_denoise_bmfr": (C.c_int, [vp, vp, u32, u32, u32, u32, u32, vp, vp]),
     "pt_autotune": (C.c_int, [vp, C.POINTER(pt_camera), u32, u32, u32, u32, C.POINTER(pt_render_opts),
                               C.POINTER(f32), vp]),
     "pt_autotune_batch": (C.c_int, [C.POINTER(pt_job), u32, u32, C.POINTER(pt_batch_opts), C.POINTER(f32), vp]),

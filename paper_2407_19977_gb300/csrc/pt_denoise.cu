@@ -61,10 +61,10 @@ constexpr float BM_ALBEDO_EPS = 1e-2f, BM_RANGE_TOL = 1e-4f, BM_DEP_TOL = 1e-3f;
 
 struct BmfrSmem {
     float M[BM_COLS][BM_ROWS];     // working columns, reduced in place by the reflections
-    float A0[BM_FEAT][BM_ROWS];    // the scaled feature columns, kept for the fitted values
     float part[BM_WARPS][16];      // per-warp partial results of a block reduction
     float bc[16];                  // reduced values, broadcast to the block
     float lo[6], hi[6];            // block ranges of n and p
+    float scale[6];                // 2 / (hi - lo), or 0 for a near-constant feature
     float norm0[BM_FEAT];          // norms of the feature columns
     float diag[BM_FEAT];           // R's diagonal, per kept column
     float z[3][BM_FEAT];           // coefficients per channel, per kept column
@@ -94,6 +94,21 @@ __device__ __forceinline__ void block_sum(BmfrSmem& sm, float (&v)[N], float (&o
 #pragma unroll
     for (int j = 0; j < N; ++j) out[j] = sm.bc[j];
     __syncthreads();
+}
+
+// the ten feature columns of one taking-part pixel: 1, n, q, q^2 scaled over the block
+__device__ __forceinline__ void bm_columns(const BmfrSmem& sm, float4 f0, float4 f1, float (&col)[BM_FEAT]) {
+    const float v[6] = {f0.x, f0.y, f0.z, f1.x, f1.y, f1.z};
+    col[0] = 1.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        col[1 + k] = sm.scale[k] != 0.0f ? (v[k] - sm.lo[k]) * sm.scale[k] - 1.0f : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float qk = sm.scale[3 + k] != 0.0f ? (v[3 + k] - sm.lo[3 + k]) * sm.scale[3 + k] - 1.0f : 0.0f;
+        col[4 + k] = qk;
+        col[7 + k] = sm.scale[3 + k] != 0.0f ? qk * qk : 0.0f;
+    }
 }
 
 __global__ void __launch_bounds__(BM_THREADS) k_bmfr(const float* color, const float4* feat, uint32_t W, uint32_t H,
@@ -144,14 +159,12 @@ __global__ void __launch_bounds__(BM_THREADS) k_bmfr(const float* color, const f
     __syncthreads();
     const bool any = sm.lo[0] <= sm.hi[0];   // some pixel takes part
     // per feature: scale 2 / (hi - lo), or 0 if the feature is near-constant over the block
-    float scale[6], off[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const float a = sm.lo[k], b = sm.hi[k];
+    if (t < 6) {
+        const float a = sm.lo[t], b = sm.hi[t];
         const bool keep = any && (b - a) > BM_RANGE_TOL * fmaxf(fmaxf(fabsf(a), fabsf(b)), 1e-2f);
-        scale[k] = keep ? 2.0f / (b - a) : 0.0f;
-        off[k] = a;
+        sm.scale[t] = keep ? 2.0f / (b - a) : 0.0f;
     }
+    __syncthreads();
 
     // 2. columns: 1, n, q, q^2, demodulated colour (rows of pixels that do not take part: 0)
     float nrm[BM_FEAT];
@@ -166,17 +179,10 @@ __global__ void __launch_bounds__(BM_THREADS) k_bmfr(const float* color, const f
             const size_t q = (size_t)y * W + (size_t)x;
             const float4 f0 = feat[3 * q], f1 = feat[3 * q + 1], f2 = feat[3 * q + 2];
             if (f0.w >= 1.0f) {
-                const float v[6] = {f0.x, f0.y, f0.z, f1.x, f1.y, f1.z};
-                col[0] = 1.0f;
+                float fc[BM_FEAT];
+                bm_columns(sm, f0, f1, fc);
 #pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    col[1 + k] = scale[k] != 0.0f ? (v[k] - off[k]) * scale[k] - 1.0f : 0.0f;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float qk = scale[3 + k] != 0.0f ? (v[3 + k] - off[3 + k]) * scale[3 + k] - 1.0f : 0.0f;
-                    col[4 + k] = qk;
-                    col[7 + k] = scale[3 + k] != 0.0f ? qk * qk : 0.0f;
-                }
+                for (int j = 0; j < BM_FEAT; ++j) col[j] = fc[j];
                 col[10] = color[3 * q] / (f2.x + BM_ALBEDO_EPS);
                 col[11] = color[3 * q + 1] / (f2.y + BM_ALBEDO_EPS);
                 col[12] = color[3 * q + 2] / (f2.z + BM_ALBEDO_EPS);
@@ -185,10 +191,7 @@ __global__ void __launch_bounds__(BM_THREADS) k_bmfr(const float* color, const f
 #pragma unroll
         for (int j = 0; j < BM_COLS; ++j) sm.M[j][r] = col[j];
 #pragma unroll
-        for (int j = 0; j < BM_FEAT; ++j) {
-            sm.A0[j][r] = col[j];
-            nrm[j] += col[j] * col[j];
-        }
+        for (int j = 0; j < BM_FEAT; ++j) nrm[j] += col[j] * col[j];
     }
     float n2[BM_FEAT];
     block_sum<BM_FEAT>(sm, nrm, n2);   // (its barriers also publish the columns)
@@ -259,10 +262,15 @@ __global__ void __launch_bounds__(BM_THREADS) k_bmfr(const float* color, const f
         const float4 f0 = feat[3 * q];
         float3 c = mk3(color[3 * q], color[3 * q + 1], color[3 * q + 2]);
         if (any && f0.w >= 1.0f) {
-            const float4 f2 = feat[3 * q + 2];
+            const float4 f1 = feat[3 * q + 1], f2 = feat[3 * q + 2];
+            float fc[BM_FEAT];
+            bm_columns(sm, f0, f1, fc);
             float y3[3] = {0.0f, 0.0f, 0.0f};
             for (int a = 0; a < nk; ++a) {
-                const float fa = sm.A0[sm.kept[a]][r];
+                float fa = 0.0f;
+#pragma unroll
+                for (int j = 0; j < BM_FEAT; ++j)
+                    if (j == sm.kept[a]) fa = fc[j];
                 y3[0] += sm.z[0][a] * fa;
                 y3[1] += sm.z[1][a] * fa;
                 y3[2] += sm.z[2][a] * fa;

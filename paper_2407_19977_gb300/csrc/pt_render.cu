@@ -576,7 +576,7 @@ __global__ void k_wf_sort_scatter(WfParams P, int in_q) {
 // environment) are resampled with target = luminance of their unshadowed contribution; the
 // reservoir keeps candidate i with probability w_i / sum w (u * sum w < w_i, streaming) and
 // W = sum w / (M target).  Paths with no surface to light get triangle PT_NO_HIT.
-__global__ void __launch_bounds__(128) k_restir_init(WfParams P) {
+__global__ void __launch_bounds__(128, 6) k_restir_init(WfParams P) {
     if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[C_Q0];
     const uint32_t sbase = wf_sample_base(P);
@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(128) k_restir_init(WfParams P) {
 // resampled with w = target_here(y_j) W_j M_j; the result gets the unbiased weight
 // W = sum w / (Z target_here(y)), Z = the sum of M over the combined reservoirs (this one
 // included) whose own target is positive at y.  The wave holds whole windows.
-__global__ void __launch_bounds__(128) k_restir_spatial(WfParams P, uint32_t n) {
+__global__ void __launch_bounds__(128, 6) k_restir_spatial(WfParams P, uint32_t n) {
     if (P.counters[C_TAIL]) return;
     const uint32_t sbase = wf_sample_base(P);
     const uint64_t seed = wf_seed(P);
@@ -1232,8 +1232,8 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                     }
                     if (restir && k == 0) {
                         e = begin(PT_K_RESTIR);
-                        PT_LAUNCH(k_restir_init, sms * 4, 128, 0, st, P);
-                        PT_LAUNCH(k_restir_spatial, sms * 4, 128, 0, st, P, n);
+                        PT_LAUNCH(k_restir_init, sms * 6, 128, 0, st, P);
+                        PT_LAUNCH(k_restir_spatial, sms * 6, 128, 0, st, P, n);
                         end(e);
                         launches += 2;
                     }

@@ -1,9 +1,16 @@
 """Build the CUDA library (libpt_gb300.so) in-tree for sm_103a.
 
 Each translation unit under csrc/ is compiled in parallel with
-  nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo
+  nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo -fmad=false
 and linked into paper_2407_19977_gb300/_build/libpt_gb300.so.  The build is skipped when
 the library is newer than every source file.
+
+-fmad=false: no implicit contraction of a multiply and an add into an FMA.  The same
+per-vertex code is inlined into several kernels (per-bounce shading, the tail kernel, the
+megakernel) whose register budgets differ, and contraction decided per kernel would round
+them differently; written out, every kernel rounds as the source says, so a sample does not
+depend on the kernel that computed it.  Explicit fmaf() and the __f*_rn intrinsics stay as
+written.
 """
 from __future__ import annotations
 
@@ -20,7 +27,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpt_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+FLAGS = ["-O3", "-lineinfo", "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
 
 

@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(128, 6) k_restir_spatial(WfParams P, uint32_t 
 }
 
 template <bool NRC>
-__global__ void __launch_bounds__(128, 3) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
+__global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
     if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[in_q];
     const uint32_t sbase = wf_sample_base(P);
@@ -857,7 +857,7 @@ __global__ void __launch_bounds__(128) k_wf_shadow(WfParams P) {
 // own terms exactly as k_wf_shadow adds it.  It appends nothing, so the later per-bounce
 // launches of the wave find empty queues (and C_TAIL makes the rest of this bounce skip).
 template <bool NRC, bool COUNT>
-__global__ void __launch_bounds__(128) k_wf_tail(WfParams P, int in_q, uint32_t k0, uint32_t limit) {
+__global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32_t k0, uint32_t limit) {
     const uint32_t count = P.counters[in_q];
     if (count == 0 || count > limit) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) P.counters[C_TAIL] = 1u;

@@ -1091,16 +1091,20 @@ enum { FLAG_NO_NEE = 1, FLAG_NO_RR = 2 };
 /* The paper points to reservoir resampling for many-light direct illumination as future    */
 /* work (Sec. 2, Sec. 6.3) without fixing an algorithm; this follows Bitterli et al. 2020:  */
 /*  1. initial candidates: M light samples y_i from the NEE light sampler (source pdf p_i, */
-/*     area measure on quads, solid angle for the environment), target p^(y) = luminance   */
-/*     of the unshadowed contribution f(wo, w_y) L_e(y) |cos| G(y) (G = cos_l / d^2 on a    */
-/*     quad, 1 for the environment); a one-sample weighted reservoir keeps y_i with         */
-/*     probability w_i / sum_j w_j, w_i = p^(y_i) / p_i, and W = sum w / (M p^(y));         */
+/*     area measure on quads, solid angle for the environment), resampled with the cheap   */
+/*     target p0(y) = lum(L_e(y)) G(y) |cos| (G = cos_l / d^2 on a quad, 1 for the          */
+/*     environment) on the side of the surface it scatters to (above it, or both sides if  */
+/*     it transmits): its support holds that of the contribution, so the reservoir stays    */
+/*     unbiased (generalised RIS); a one-sample weighted reservoir keeps y_i with           */
+/*     probability w_i / sum_j w_j, w_i = p0(y_i) / p_i, and W = sum w / (M p0(y));         */
 /*  2. one spatial pass: K neighbours of the same sample index inside the window (offsets  */
 /*     uniform in a square of half-width R, rejected off-window, on the pixel itself, with  */
-/*     no surface, normal cosine < 0.9 or depth differing by > 10 %); their initial        */
-/*     reservoirs are resampled with w = p^_q(y_j) W_j M_j at this pixel q, and the result   */
-/*     is weighted unbiasedly: W = sum w / (Z p^_q(y)), Z = sum of M_j over the combined    */
-/*     reservoirs whose own target is positive at y (the "1/Z" weights);                     */
+/*     no surface, normal cosine < 0.9 or depth differing by > 10 %); this pixel's and the  */
+/*     neighbours' initial reservoirs are resampled with the full target p^_q (luminance of */
+/*     the unshadowed contribution f(wo, w_y) L_e(y) |cos| G(y)) at this pixel q,           */
+/*     w_j = p^_q(y_j) W_j M_j, and the result is weighted unbiasedly: W = sum w /          */
+/*     (Z p^_q(y)), Z = sum of M_j over the combined reservoirs whose own initial target p0 */
+/*     is positive at y (the "1/Z" weights count the reservoirs that could have drawn y);   */
 /*  3. vertex 0 of the path shades that sample: f L_e |cos| G V W with one shadow ray, in   */
 /*     place of next-event estimation; a BSDF-sampled hit of a quad or the environment at   */
 /*     vertex 1 then counts with weight 0 (unless vertex 0 sampled a delta lobe), since the */
@@ -1118,6 +1122,7 @@ typedef struct {
     v3 x, ng, n, tt, bb, wo_w, wo;
     double t;
     int front;
+    int transmits;           /* scatters to both sides: (1 - metalness) transmission_weight > 0 */
     closure C;
 } osurf;
 
@@ -1167,6 +1172,32 @@ static double restir_target(const oscene* S, const osurf* g, int light, v3 y, v3
     return ph > 0.0 && isfinite(ph) ? ph : 0.0;
 }
 
+/* cheap target p0 of the initial candidates: lum(L_e) G |cos| where the surface scatters */
+static double restir_target0(const oscene* S, const osurf* g, int light, v3 y) {
+    v3 ld, Le;
+    double geo;
+    if (light >= 0) {
+        v3 to = sub(y, g->x);
+        double d2 = dot(to, to);
+        if (!(d2 > 0.0)) return 0.0;
+        ld = scl(to, 1.0 / sqrt(d2));
+        double cl = -dot(ld, S->q_n[light]);
+        if (!(cl > 0.0 || (S->q_two_sided[light] && cl < 0.0))) return 0.0;
+        Le = S->q_L[light];
+        geo = fabs(cl) / d2;
+    } else if (light == LIGHT_ENV) {
+        ld = y;
+        Le = env_radiance(S, ld);
+        geo = 1.0;
+    } else {
+        return 0.0;
+    }
+    double c = dot(ld, g->n);
+    if (!(c > 0.0) && !(g->transmits && c < 0.0)) return 0.0;
+    double ph = lum(Le) * geo * fabs(c);
+    return ph > 0.0 && isfinite(ph) ? ph : 0.0;
+}
+
 static void restir_initial(const oscene* S, const osurf* g, uint32_t p, uint32_t s, uint64_t seed, int M,
                            double p_env, oresv* R) {
     R->light = LIGHT_NONE;
@@ -1197,8 +1228,7 @@ static void restir_initial(const oscene* S, const osurf* g, uint32_t p, uint32_t
             src = (1.0 - p_env) / S->n_quads / S->q_area[l];
         }
         if (!(src > 0.0)) continue;
-        v3 c, ld;
-        double ph = restir_target(S, g, light, y, &c, &ld);
+        double ph = restir_target0(S, g, light, y);
         double w = ph / src;
         if (!(w > 0.0)) continue;
         wsum += w;
@@ -1257,6 +1287,7 @@ static void* restir_pass_initial(void* arg) {
             else onb(g->n, &g->tt, &g->bb);
             g->wo = mk(dot(g->wo_w, g->tt), dot(g->wo_w, g->bb), dot(g->wo_w, g->n));
             g->t = h.t;
+            g->transmits = (1.0 - m->metalness) * m->trans_weight > 0.0;
             closure_setup(&g->C, m, g->front, g->wo.z);
             g->valid = g->C.has_smooth && (has_env || S->n_quads > 0);
             if (g->valid) restir_initial(S, g, p, J->s, J->seed, J->M, p_env, &J->init[i]);
@@ -1279,7 +1310,8 @@ static void* restir_pass_spatial(void* arg) {
             int px = J->x0 + rx, py = J->y0 + ry;
             uint32_t p = (uint32_t)(py * J->cam->width + px);
             const oresv* R0 = &J->init[i];
-            double wsum = R0->phat * R0->W * R0->M;
+            v3 c0, ld0;
+            double wsum = restir_target(S, g, R0->light, R0->y, &c0, &ld0) * R0->W * R0->M;
             double Msum = R0->M;
             int light = R0->light;
             v3 y = R0->y;
@@ -1313,11 +1345,9 @@ static void* restir_pass_spatial(void* arg) {
             (void)Msum;
             v3 c, ld;
             double ph = restir_target(S, g, light, y, &c, &ld);
-            double Z = ph > 0.0 ? R0->M : 0.0;
-            for (int u = 0; u < n_used; ++u) {
-                v3 c2, ld2;
-                if (restir_target(S, &J->surf[used[u]], light, y, &c2, &ld2) > 0.0) Z += J->init[used[u]].M;
-            }
+            double Z = restir_target0(S, g, light, y) > 0.0 ? R0->M : 0.0;
+            for (int u = 0; u < n_used; ++u)
+                if (restir_target0(S, &J->surf[used[u]], light, y) > 0.0) Z += J->init[used[u]].M;
             F->light = light;
             F->y = y;
             F->phat = ph;

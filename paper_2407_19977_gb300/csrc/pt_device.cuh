@@ -1005,6 +1005,36 @@ __device__ __forceinline__ float restir_target(const DScene& S, float3 x, float3
     return (ph > 0.0f && isfinite(ph)) ? ph : 0.0f;
 }
 
+// Cheap target p0 of the initial candidates: lum(L_e) G |cos| on the side the surface
+// scatters to (above it; both sides if it transmits).  Its support holds that of the
+// contribution, so resampling with it keeps the reservoir unbiased (generalised RIS).
+__device__ __forceinline__ float restir_target0(const DScene& S, float3 x, float3 n, bool transmits, int light,
+                                                float3 y) {
+    float3 ld, Le;
+    float geo;
+    if (light >= 0) {
+        const DQuad& q = S.quads[light];
+        const float3 to = y - x;
+        const float d2 = dot3(to, to);
+        if (!(d2 > 0.0f)) return 0.0f;
+        ld = to * (1.0f / sqrtf(d2));
+        const float cl = -dot3(ld, q.n);
+        if (!(cl > 0.0f || (q.two_sided && cl < 0.0f))) return 0.0f;
+        Le = q.L;
+        geo = fabsf(cl) / d2;
+    } else if (light == LIGHT_ENV) {
+        ld = y;
+        Le = env_radiance(S, ld);
+        geo = 1.0f;
+    } else {
+        return 0.0f;
+    }
+    const float c = dot3(ld, n);
+    if (!(c > 0.0f) && !(transmits && c < 0.0f)) return 0.0f;
+    const float ph = lum3(Le) * geo * fabsf(c);
+    return (ph > 0.0f && isfinite(ph)) ? ph : 0.0f;
+}
+
 // The primary surface of a path as the reservoirs see it, rebuilt from its position, the
 // direction towards the camera and the triangle (the same steps as shade_vertex_h).
 struct RSurf {

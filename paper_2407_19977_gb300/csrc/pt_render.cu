@@ -573,9 +573,9 @@ __global__ void k_wf_sort_scatter(WfParams P, int in_q) {
 // ReSTIR DI, pass 1 (bounce 0, after the closest hits, queue 0 whose slot is the path id):
 // the primary surface of every path and its initial reservoir.  M candidates from the
 // next-event light sampler (source pdf in area measure on a quad, solid angle for the
-// environment) are resampled with target = luminance of their unshadowed contribution; the
-// reservoir keeps candidate i with probability w_i / sum w (u * sum w < w_i, streaming) and
-// W = sum w / (M target).  Paths with no surface to light get triangle PT_NO_HIT.
+// environment) are resampled with the cheap target p0 = lum(L_e) G |cos| (restir_target0);
+// the reservoir keeps candidate i with probability w_i / sum w (u * sum w < w_i, streaming)
+// and W = sum w / (M p0).  Paths with no surface to light get triangle PT_NO_HIT.
 __global__ void __launch_bounds__(128, 6) k_restir_init(WfParams P) {
     if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[C_Q0];
@@ -603,8 +603,9 @@ __global__ void __launch_bounds__(128, 6) k_restir_init(WfParams P) {
         }
         if (valid) {
             const float3 wo_w = -xyz(rd);
+            const bool transmits = (1.0f - g.C.m) * g.C.t > 0.0f;
             P.rs_g0[id] = make_float4(g.x.x, g.x.y, g.x.z, hh.x);
-            P.rs_gn[id] = make_float4(g.n.x, g.n.y, g.n.z, 0.0f);
+            P.rs_gn[id] = make_float4(g.n.x, g.n.y, g.n.z, transmits ? 1.0f : 0.0f);
             g1 = make_float4(wo_w.x, wo_w.y, wo_w.z, __uint_as_float(tri));
             const uint32_t lp = P.pb + id % P.npix;
             const uint32_t p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
@@ -633,8 +634,7 @@ __global__ void __launch_bounds__(128, 6) k_restir_init(WfParams P) {
                     src = (1.0f - p_env) / (float)S.n_quads / q.area;
                 }
                 if (!(src > 0.0f)) continue;
-                float3 c, ld;
-                const float ph = restir_target(S, g.x, g.tt, g.bb, g.n, g.C, g.wo, light, y, c, ld);
+                const float ph = restir_target0(S, g.x, g.n, transmits, light, y);
                 const float w = ph / src;
                 if (!(w > 0.0f)) continue;
                 wsum += w;
@@ -657,10 +657,12 @@ __global__ void __launch_bounds__(128, 6) k_restir_init(WfParams P) {
 // ReSTIR DI, pass 2: one spatial pass.  Up to K neighbours of the same sample (offsets
 // uniform in [-R, R]^2 from the raw Philox words by multiply-shift, so every build picks the
 // same pixels), skipped outside the window, on the pixel itself, without a surface, with
-// normal cosine < 0.9 or depth differing by more than 10 %.  Their initial reservoirs are
-// resampled with w = target_here(y_j) W_j M_j; the result gets the unbiased weight
-// W = sum w / (Z target_here(y)), Z = the sum of M over the combined reservoirs (this one
-// included) whose own target is positive at y.  The wave holds whole windows.
+// normal cosine < 0.9 or depth differing by more than 10 %.  This pixel's and their initial
+// reservoirs are resampled with the full target here (restir_target),
+// w = target_here(y_j) W_j M_j; the result gets the unbiased weight
+// W = sum w / (Z target_here(y)), Z = the sum of M over the combined reservoirs whose own
+// initial target p0 is positive at y (those that could have drawn y).  The wave holds whole
+// windows.
 __global__ void __launch_bounds__(128, 6) k_restir_spatial(WfParams P, uint32_t n) {
     if (P.counters[C_TAIL]) return;
     const uint32_t sbase = wf_sample_base(P);
@@ -680,8 +682,11 @@ __global__ void __launch_bounds__(128, 6) k_restir_spatial(WfParams P, uint32_t 
             const uint32_t rx = lp % P.cw, ry = lp / P.cw;
             const uint32_t p = (P.y0 + ry) * P.cam.width + (P.x0 + rx);
             const uint32_t s = sbase + id / P.npix;
-            float wsum = f1.z * f1.x * f1.y;
+            float3 c0, ld0;
+            float wsum = restir_target(P.S, g.x, g.tt, g.bb, g.n, g.C, g.wo, __float_as_int(f0.w), xyz(f0), c0, ld0) *
+                         f1.x * f1.y;
             const float Mq = f1.y;
+            const bool transmits = P.rs_gn[id].w != 0.0f;
             int light = __float_as_int(f0.w);
             float3 y = xyz(f0);
             uint32_t used[64];
@@ -711,14 +716,11 @@ __global__ void __launch_bounds__(128, 6) k_restir_spatial(WfParams P, uint32_t 
             }
             float3 c, ld;
             const float ph = restir_target(P.S, g.x, g.tt, g.bb, g.n, g.C, g.wo, light, y, c, ld);
-            float Z = ph > 0.0f ? Mq : 0.0f;
+            float Z = restir_target0(P.S, g.x, g.n, transmits, light, y) > 0.0f ? Mq : 0.0f;
             for (uint32_t u = 0; u < n_used; ++u) {
                 const uint32_t nid = used[u];
-                const float4 n1 = P.rs_g1[nid];
-                RSurf gu;
-                rsurf_make(P.S, xyz(P.rs_g0[nid]), xyz(n1), __float_as_uint(n1.w), gu);
-                float3 c2, ld2;
-                if (restir_target(P.S, gu.x, gu.tt, gu.bb, gu.n, gu.C, gu.wo, light, y, c2, ld2) > 0.0f)
+                const float4 nn = P.rs_gn[nid];
+                if (restir_target0(P.S, xyz(P.rs_g0[nid]), xyz(nn), nn.w != 0.0f, light, y) > 0.0f)
                     Z += P.rs_i[2u * nid + 1].y;
             }
             f0 = make_float4(y.x, y.y, y.z, __int_as_float(light));

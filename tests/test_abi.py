@@ -71,3 +71,23 @@ def test_host_side_validation_needs_no_gpu():
         assert code == 1 and f"parameter {i} ".encode() in lib.pt_last_error()
         m[0].v[i] = 0.0
     assert lib.pt_render(None, None, 1, 1, 0, None, None, None) == 1
+
+
+def test_restir_and_denoiser_arguments_are_checked_on_the_host():
+    """The ReSTIR options and the denoiser entry points reject bad arguments before any CUDA
+    call (no GPU needed); pt_restir_opts and pt_render_opts have the declared layout."""
+    from paper_2407_19977_gb300 import native as N
+    lib = N.load()
+    assert C.sizeof(N.pt_restir_opts) == 16
+    assert N.pt_render_opts.restir.offset % 8 == 0
+    buf = (C.c_float * 48)()
+    # NULL pointers, block outside 4..32, offset not below the block
+    assert lib.pt_denoise_bmfr(None, None, 4, 4, 16, 0, 0, None, None) == 1
+    for block, ox, oy in ((3, 0, 0), (33, 0, 0), (16, 16, 0), (16, 0, 17)):
+        assert lib.pt_denoise_bmfr(buf, buf, 2, 2, block, ox, oy, buf, None) == 1, (block, ox, oy)
+    assert lib.pt_render_features(None, None, 0, 0, 1, 1, 0, 1, C.c_uint64(0), None, None) == 1
+    # an empty image is a no-op
+    aligned = (C.c_float * 64)()
+    addr = C.addressof(aligned)
+    p = C.c_void_p(addr + (-addr) % 16)
+    assert lib.pt_denoise_bmfr(p, p, 0, 5, 16, 0, 0, p, None) == 0

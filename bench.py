@@ -41,8 +41,8 @@ WORKLOADS = {
     "cornell1080": "Cornell-style box, 36 triangles, one quad light, 1920x1080, 1 spp/step, max depth 8",
     "pushbutton_dof": "the pushbutton frame through a thin lens (radius 0.03, focus on the button), "
                       "1920x1080, 1 spp/step, max depth 8",
-    "many_lights": "Cornell-style box lit by 256 small quad lights (heavy-tailed radiance, random tints) on "
-                   "the ceiling and side walls, 1920x1080, 1 spp/step, max depth 4",
+    "many_lights": "Cornell-style box lit by 248 small non-overlapping quad lights (heavy-tailed radiance, random "
+                   "tints) on the ceiling and side walls, 1920x1080, 1 spp/step, max depth 4",
 }
 NODE_BYTES = 80      # compressed 8-wide BVH node
 TRI_BYTES = 48       # triangle record
@@ -76,6 +76,7 @@ def _args():
     ap.add_argument("--study", default=None, choices=[None, "nrc", "batch", "paper", "restir", "bmfr"],
                     help="nrc: relMSE vs time, radiance cache against the plain tracer")
     ap.add_argument("--ref-spp", type=int, default=4096)
+    ap.add_argument("--max-depth", type=int, default=None, help="studies: override the workload's max depth")
     return ap.parse_args()
 
 
@@ -505,6 +506,8 @@ def run_restir_study(args, local):
     torch.cuda.set_device(local)
     name = args.workload if args.workload != "pushbutton" else "many_lights"
     sc = _make_workload(name)
+    if args.max_depth is not None:
+        sc.max_depth = args.max_depth
     W, H = sc.camera.width, sc.camera.height
     scene = api.Scene(sc)
     stream = torch.cuda.current_stream()
@@ -514,6 +517,9 @@ def run_restir_study(args, local):
         scene.render(chunk, seed=777, accum=ref, mode=N.PT_MODE_WAVEFRONT)
     torch.cuda.synchronize()
     ref_img = ref.image()
+    # pixels whose first hit always scatters (the surfaces ReSTIR lights; pixels that see a
+    # light directly carry the same anti-aliasing noise either way)
+    surf = scene.features(16, seed=9)[..., 3] >= 1.0
     marks = [m for m in (1, 2, 4, 8, 16, 32, 64, 128, 256) if m <= args.study_frames]
     variants = {"plain": None, "restir_M32_K5_R10": (32, 5, 10), "restir_M8_K5_R10": (8, 5, 10)}
     curves, split = {}, {}
@@ -532,27 +538,32 @@ def run_restir_study(args, local):
             torch.cuda.synchronize()
             t_ms += e0.elapsed_time(e1)
             if f in marks:
-                pts.append({"spp": f, "ms": t_ms, "relmse": _relmse(acc.image(), ref_img)})
+                img = acc.image()
+                pts.append({"spp": f, "ms": t_ms, "relmse": _relmse(img, ref_img),
+                            "relmse_surfaces": _relmse(img[surf], ref_img[surf])})
         curves[kind] = pts
         km = (N.f32 * len(N.KERNEL_KINDS))()
         probe = api.Accum(W, H)
         for _ in range(4):
             scene.render(1, seed=1, accum=probe, mode=N.PT_MODE_WAVEFRONT, restir=r, kernel_ms=km)
         split[kind] = {n: round(float(km[i]) / 4, 4) for i, n in enumerate(N.KERNEL_KINDS) if km[i] > 0}
-    out = {"study": "restir_equal_time", "workload": WORKLOADS[name], "ref_spp": args.ref_spp,
-           "relmse_eps": 1e-2, "curves": curves, "kernel_ms_per_frame": split}
-    for spp in (16, 64):
-        if spp > marks[-1]:
-            continue
-        target = next(p["relmse"] for p in curves["plain"] if p["spp"] == spp)
-        tp = next(p["ms"] for p in curves["plain"] if p["spp"] == spp)
-        res = {"relmse": target, "plain_ms": tp}
-        for kind in variants:
-            if kind == "plain":
+    out = {"study": "restir_equal_time", "workload": WORKLOADS[name], "max_depth": sc.max_depth, "ref_spp": args.ref_spp,
+           "relmse_eps": 1e-2, "surface_pixels": float(surf.float().mean()), "curves": curves,
+           "kernel_ms_per_frame": split}
+    for key in ("relmse", "relmse_surfaces"):
+        for spp in (16, 64):
+            if spp > marks[-1]:
                 continue
-            tr = _time_to(curves[kind], target)
-            res[kind] = {"ms": tr, "speedup": (tp / tr) if tr else None}
-        out[f"at_plain_{spp}spp"] = res
+            target = next(p[key] for p in curves["plain"] if p["spp"] == spp)
+            tp = next(p["ms"] for p in curves["plain"] if p["spp"] == spp)
+            res = {key: target, "plain_ms": tp}
+            for kind in variants:
+                if kind == "plain":
+                    continue
+                curve = [{"spp": p["spp"], "ms": p["ms"], "relmse": p[key]} for p in curves[kind]]
+                tr = _time_to(curve, target)
+                res[kind] = {"ms": tr, "speedup": (tp / tr) if tr else None}
+            out[f"{key}_at_plain_{spp}spp"] = res
     print(json.dumps(out))
 
 

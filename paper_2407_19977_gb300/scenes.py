@@ -293,17 +293,32 @@ def cornell_box(seed=0, width=64, height=64, spp=16, max_depth=4) -> Scene:
 def many_light_box(n_lights=64, seed=0, width=64, height=64, spp=16, max_depth=4) -> Scene:
     """The Cornell geometry lit by `n_lights` small quads instead of one: 60 % on the ceiling
     facing down, the rest on the two side walls facing in; side 0.03-0.07, radiance with a
-    heavy (Pareto, shape 1.5) tail and random tints.  A few lights dominate each point and
-    which ones depends on where the point is: many-light direct illumination."""
+    heavy (Pareto, shape 1.5) tail and random tints; lights on one wall do not overlap
+    (they share its plane).  A few lights dominate each point and which ones depends on where
+    the point is: many-light direct illumination."""
     base = cornell_box(seed=seed, width=width, height=height, spp=spp, max_depth=max_depth)
     rng = _rng(seed + 101)
     lights = []
+    placed = {0: [], 1: [], 2: []}                        # squares already on each wall
+
+    def free(wall, a, b, size):
+        # lights on one wall share a plane: overlapping ones would hit at equal depth
+        return all(a + size + 0.005 <= a2 or a2 + s2 + 0.005 <= a or b + size + 0.005 <= b2 or b2 + s2 + 0.005 <= b
+                   for a2, b2, s2 in placed[wall])
+
     for _ in range(n_lights):
         size = rng.uniform(0.03, 0.07)
         tint = rng.uniform(0.4, 1.0, 3)
         L = tuple(3.0 * (rng.pareto(1.5) + 1.0) * tint / tint.max())
-        a, b = rng.uniform(0.05, 0.95 - size, 2)
         where = rng.random()
+        wall = 0 if where < 0.6 else (1 if where < 0.8 else 2)
+        for _attempt in range(200):
+            a, b = rng.uniform(0.05, 0.95 - size, 2)
+            if free(wall, a, b, size):
+                break
+        else:
+            continue                                      # the wall is full
+        placed[wall].append((a, b, size))
         if where < 0.6:                                   # ceiling, normal -y
             lights.append(quad_light((a, 1.0 - 1e-3, b), (size, 0.0, 0.0), (0.0, 0.0, size), L))
         elif where < 0.8:                                 # wall x = 0, normal +x

@@ -102,3 +102,33 @@ def test_bmfr_in_place_and_arguments(api):
     for block, off in ((3, (0, 0)), (33, (0, 0)), (16, (16, 0)), (16, (0, 20))):
         with pytest.raises(N.PtError, match="INVALID_ARG"):
             A.bmfr(gc, gfe, block=block, offset=off)
+
+
+def test_bmfr_full_1080p_study_configuration(api):
+    """The denoiser study's setup at full size: the 1-spp pushbutton frame at 1920x1080, its
+    GPU features, 32-pixel blocks; the oracle fits the same float32 inputs."""
+    from paper_2407_19977_gb300 import api as A
+    sc = scenes.pushbutton()
+    g = A.Scene(sc)
+    acc = g.render(1, seed=1, mode=1)
+    color = acc.image().contiguous()
+    feats = g.features(1, seed=1)
+    got = A.bmfr(color, feats, block=32).cpu().numpy().astype(np.float64)
+    c64 = color.cpu().numpy().astype(np.float64)
+    f64 = feats.cpu().numpy().astype(np.float64)
+    exp = ob.bmfr(c64, f64, block=32)
+    take = f64[..., 3] >= 1.0
+    assert np.array_equal(got[~take], c64[~take])
+    worst, info = 0.0, None
+    for y0, y1, x0, x1 in ob._blocks(1080, 1920, 32, (0, 0)):
+        t = take[y0:y1, x0:x1]
+        if not t.any():
+            continue
+        e = exp[y0:y1, x0:x1][t]
+        d = np.abs(got[y0:y1, x0:x1][t] - e).max() / (np.sqrt((e * e).mean()) + 1e-6)
+        if d > 2e-4:   # only then is the condition number needed
+            kappa = np.linalg.cond(ob.kept_columns(ob.design_matrix(f64[y0:y1, x0:x1].reshape(-1, 12)[t.ravel()])))
+            r = d / (2e-4 + 1e-6 * kappa)
+            if r > worst:
+                worst, info = r, (d, kappa, (y0, x0))
+    assert worst < 1.0, info

@@ -85,3 +85,13 @@ def test_restir_arguments(api):
         g.render(1, accum=acc, mode=1, restir=(4, 2, 2), flags=N.PT_FLAG_NO_NEE)
     with pytest.raises(N.PtError, match="UNSUPPORTED"):
         g.render(1, accum=acc, mode=N.PT_MODE_MEGAKERNEL, restir=(4, 2, 2))
+
+
+def test_restir_parity_full_1080p_study_configuration(api):
+    """The equal-time study's setup at full size: the many-light box at 1920x1080, depth 4,
+    M 8, K 5, R 10, one sample per pixel in one wave, against the oracle's ReSTIR on all
+    pixels (the spatial pass needs the whole window)."""
+    sc = scenes.many_light_box(256, width=1920, height=1080, spp=1, max_depth=4, seed=0)
+    g, acc, gs, os_, st = _pair(sc, (8, 5, 10), 1, seed=0, use_graph=True)
+    _samples_check(gs, os_, "restir 1080p", max_divergent=4e-3)
+    assert g.stats()["error_flags"] == 0

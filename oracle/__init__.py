@@ -306,7 +306,8 @@ class OracleScene:
                threads=None, row_step=1, keep_samples=False, no_nee=False, no_rr=False, restir=None):
         """Sum of sample radiance over the crop (ch, cw, 3), optional per-sample values and
         stats dict.  crop = (x0, y0, w, h) in full-frame pixels.  restir = (M candidates,
-        K neighbours, radius R) renders with ReSTIR DI at the primary vertex over the crop."""
+        K neighbours, radius R[, L later candidates]) renders with ReSTIR DI at the primary
+        vertex over the crop (and resampled NEE with L candidates at later vertices)."""
         sc = self.scene
         cam = camera or sc.camera
         spp = sc.spp if spp is None else spp
@@ -318,9 +319,9 @@ class OracleScene:
         samples = np.zeros((ch, cw, spp, 3)) if keep_samples else None
         stats = np.zeros(5, dtype=np.int64)
         threads = threads or (os.cpu_count() or 1)
-        rp = None if restir is None else np.array([int(v) for v in restir], dtype=np.int32)
+        rp = None if restir is None else np.array([int(v) for v in (tuple(restir) + (0,))[:4]], dtype=np.int32)
         if rp is not None:
-            assert len(rp) == 3 and rp[0] >= 1 and 0 <= rp[1] <= 64 and rp[2] >= 1
+            assert rp[0] >= 1 and 0 <= rp[1] <= 64 and rp[2] >= 1 and rp[3] >= 0
         _load().oracle_render(self.h, cam9.ctypes.data_as(_dp), float(cam.vfov_deg), cam.width,
                               cam.height, x0, y0, cw, ch, int(s0), int(spp), int(max_depth),
                               int(seed), (1 if no_nee else 0) | (2 if no_rr else 0), int(threads),

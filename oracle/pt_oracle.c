@@ -1109,12 +1109,17 @@ enum { FLAG_NO_NEE = 1, FLAG_NO_RR = 2 };
 /*     place of next-event estimation; a BSDF-sampled hit of a quad or the environment at   */
 /*     vertex 1 then counts with weight 0 (unless vertex 0 sampled a delta lobe), since the */
 /*     reservoir already estimates all light reaching vertex 0.                             */
+/*  4. optionally, at every later vertex k >= 1, next-event estimation by resampled        */
+/*     importance sampling of L candidates with the same cheap target (no spatial reuse;   */
+/*     stream RESTIR_LATER + k), and a BSDF-sampled light hit after such a vertex counts    */
+/*     with weight 0 as well.                                                               */
 /* Random numbers: candidate i uses (pixel, sample, RESTIR_CANDIDATES, dims 4i..4i+3) for   */
 /* light pick, u, v, selection; neighbour j uses (pixel, sample, RESTIR_SPATIAL, 4j..4j+2)  */
 /* for dx, dy (the raw 32-bit words, w * (2R+1) >> 32 - R: integer arithmetic, so both      */
 /* sides pick the same pixel) and selection.                                                */
 #define RESTIR_CANDIDATES 0xFFFF0001u
 #define RESTIR_SPATIAL 0xFFFF0002u
+#define RESTIR_LATER 0xFFFF0100u   /* + vertex index: resampled light candidates at vertex k >= 1 */
 enum { LIGHT_NONE = -2, LIGHT_ENV = -1 };
 
 typedef struct {
@@ -1198,8 +1203,8 @@ static double restir_target0(const oscene* S, const osurf* g, int light, v3 y) {
     return ph > 0.0 && isfinite(ph) ? ph : 0.0;
 }
 
-static void restir_initial(const oscene* S, const osurf* g, uint32_t p, uint32_t s, uint64_t seed, int M,
-                           double p_env, oresv* R) {
+static void restir_initial(const oscene* S, const osurf* g, uint32_t p, uint32_t s, uint32_t stream, uint64_t seed,
+                           int M, double p_env, oresv* R) {
     R->light = LIGHT_NONE;
     R->y = splat(0.0);
     R->W = 0.0;
@@ -1207,10 +1212,10 @@ static void restir_initial(const oscene* S, const osurf* g, uint32_t p, uint32_t
     R->phat = 0.0;
     double wsum = 0.0;
     for (int i = 0; i < M; ++i) {
-        double u_pick = U(p, s, RESTIR_CANDIDATES, 4u * i, seed);
-        double u = U(p, s, RESTIR_CANDIDATES, 4u * i + 1, seed);
-        double v = U(p, s, RESTIR_CANDIDATES, 4u * i + 2, seed);
-        double u_sel = U(p, s, RESTIR_CANDIDATES, 4u * i + 3, seed);
+        double u_pick = U(p, s, stream, 4u * i, seed);
+        double u = U(p, s, stream, 4u * i + 1, seed);
+        double v = U(p, s, stream, 4u * i + 2, seed);
+        double u_sel = U(p, s, stream, 4u * i + 3, seed);
         int light;
         v3 y;
         double src;
@@ -1244,7 +1249,7 @@ static void restir_initial(const oscene* S, const osurf* g, uint32_t p, uint32_t
 typedef struct {
     const oscene* S;
     const ocam* cam;
-    int x0, y0, cw, ch, M, K, R;
+    int x0, y0, cw, ch, M, K, R, Lm;
     int max_depth, flags;
     uint32_t s;
     uint64_t seed;
@@ -1290,7 +1295,7 @@ static void* restir_pass_initial(void* arg) {
             g->transmits = (1.0 - m->metalness) * m->trans_weight > 0.0;
             closure_setup(&g->C, m, g->front, g->wo.z);
             g->valid = g->C.has_smooth && (has_env || S->n_quads > 0);
-            if (g->valid) restir_initial(S, g, p, J->s, J->seed, J->M, p_env, &J->init[i]);
+            if (g->valid) restir_initial(S, g, p, J->s, RESTIR_CANDIDATES, J->seed, J->M, p_env, &J->init[i]);
         }
     return NULL;
 }
@@ -1358,18 +1363,19 @@ static void* restir_pass_spatial(void* arg) {
 }
 
 static v3 trace_path_r(const oscene* S, const ocam* cam, int px, int py, uint32_t s,
-                       int max_depth, uint64_t seed, int flags, ostats* st, int restir, const oresv* R0,
-                       const osurf* g0);
+                       int max_depth, uint64_t seed, int flags, ostats* st, int restir, int later_m,
+                       const oresv* R0, const osurf* g0);
 
 static v3 trace_path(const oscene* S, const ocam* cam, int px, int py, uint32_t s,
                      int max_depth, uint64_t seed, int flags, ostats* st) {
-    return trace_path_r(S, cam, px, py, s, max_depth, seed, flags, st, 0, NULL, NULL);
+    return trace_path_r(S, cam, px, py, s, max_depth, seed, flags, st, 0, 0, NULL, NULL);
 }
 
-/* one path; with `restir`, vertex 0 shades the reservoir R0 (its surface g0) instead of NEE */
+/* one path; with `restir`, vertex 0 shades the reservoir R0 (its surface g0) instead of NEE,
+ * and with later_m > 0 the later vertices resample later_m light candidates */
 static v3 trace_path_r(const oscene* S, const ocam* cam, int px, int py, uint32_t s,
-                       int max_depth, uint64_t seed, int flags, ostats* st, int restir, const oresv* R0,
-                       const osurf* g0) {
+                       int max_depth, uint64_t seed, int flags, ostats* st, int restir, int later_m,
+                       const oresv* R0, const osurf* g0) {
     uint32_t p = (uint32_t)(py * cam->width + px);
     v3 o, d;
     camera_ray(cam, px, py, s, seed, &o, &d);
@@ -1388,7 +1394,7 @@ static v3 trace_path_r(const oscene* S, const ocam* cam, int px, int py, uint32_
                 v3 Le = env_radiance(S, d);
                 double w = 1.0;
                 if (!prev_delta && nee)
-                    w = (restir && k == 1) ? 0.0 : power_heuristic(prev_pdf, p_env * env_pdf(S, d));
+                    w = (restir && (k == 1 || later_m > 0)) ? 0.0 : power_heuristic(prev_pdf, p_env * env_pdf(S, d));
                 L = add(L, scl(hmul(beta, Le), w));
             }
             break;
@@ -1406,7 +1412,7 @@ static v3 trace_path_r(const oscene* S, const ocam* cam, int px, int py, uint32_
                 double w = 1.0;
                 if (!prev_delta && nee) {
                     double pl = (1.0 - p_env) / S->n_quads * h.t * h.t / (S->q_area[l] * fabs(cl));
-                    w = (restir && k == 1) ? 0.0 : power_heuristic(prev_pdf, pl);
+                    w = (restir && (k == 1 || later_m > 0)) ? 0.0 : power_heuristic(prev_pdf, pl);
                 }
                 L = add(L, scl(hmul(beta, S->q_L[l]), w));
             }
@@ -1441,6 +1447,32 @@ static v3 trace_path_r(const oscene* S, const ocam* cam, int px, int py, uint32_
                     }
                     st->shadow_rays++;
                     if (!occluded(S, so, sd, tmax)) L = add(L, scl(hmul(beta, c), R0->W));
+                }
+            }
+        } else if (restir && later_m > 0 && C.has_smooth && (has_env || S->n_quads > 0)) {
+            /* resampled light candidates at a later vertex */
+            osurf gk;
+            gk.valid = 1;
+            gk.x = x; gk.ng = ng; gk.n = n; gk.tt = tt; gk.bb = bb; gk.wo_w = wo_w; gk.wo = wo;
+            gk.t = h.t; gk.front = front;
+            gk.transmits = (1.0 - m->metalness) * m->trans_weight > 0.0;
+            gk.C = C;
+            oresv Rk;
+            restir_initial(S, &gk, p, s, RESTIR_LATER + (uint32_t)k, seed, later_m, p_env, &Rk);
+            if (Rk.light != LIGHT_NONE && Rk.W > 0.0) {
+                v3 c, ld;
+                if (restir_target(S, &gk, Rk.light, Rk.y, &c, &ld) > 0.0) {
+                    v3 so = offset_origin(S, x, ng, ld);
+                    v3 sd = ld;
+                    double tmax = INFINITY;
+                    if (Rk.light >= 0) {
+                        v3 to = sub(Rk.y, so);
+                        double dl = length(to);
+                        sd = scl(to, 1.0 / dl);
+                        tmax = (1.0 - 1e-4) * dl;
+                    }
+                    st->shadow_rays++;
+                    if (!occluded(S, so, sd, tmax)) L = add(L, scl(hmul(beta, c), Rk.W));
                 }
             }
         } else if (nee && C.has_smooth && (has_env || S->n_quads > 0)) {
@@ -1566,8 +1598,9 @@ static void* worker(void* arg) {
 
 /* Render samples s0 .. s0+spp-1 of the crop [x0, x0+cw) x [y0, y0+ch) of the full frame.
  * sum_out receives the per-pixel sum of sample radiance (divide by spp for the estimate).
- * restir = NULL for next-event estimation, else {M candidates, K neighbours, radius R}: ReSTIR
- * DI at the primary vertex over the window (row_step is then ignored).
+ * restir = NULL for next-event estimation, else {M candidates, K neighbours, radius R, L later
+ * candidates}: ReSTIR DI at the primary vertex over the window (row_step is then ignored),
+ * resampled next-event estimation with L candidates at later vertices if L > 0.
  * cam = origin[3], target[3], up[3], lens_radius, focus_distance; row_step > 1 renders only every row_step-th
  * row of the crop (others stay 0); flags as for trace_path.  stats_out (5 int64): extension rays, shadow rays, NaN
  * samples dropped, roulette terminations, paths. */
@@ -1587,7 +1620,7 @@ static void* restir_pass_paths(void* arg) {
         for (int rx = 0; rx < J->cw; ++rx) {
             size_t i = (size_t)ry * J->cw + rx;
             v3 L = trace_path_r(J->S, J->cam, J->x0 + rx, J->y0 + ry, J->s, J->max_depth, J->seed, J->flags,
-                                &P->st, 1, &J->fin[i], &J->surf[i]);
+                                &P->st, 1, J->Lm, &J->fin[i], &J->surf[i]);
             P->st.paths++;
             if (!isfinite(L.x) || !isfinite(L.y) || !isfinite(L.z)) {
                 P->st.nan_dropped++;
@@ -1628,7 +1661,7 @@ static void render_restir(const oscene* S, const ocam* cam, int x0, int y0, int 
         for (int t = 0; t < nthreads; ++t) {
             restir_job* J = &jobs[t];
             J->S = S; J->cam = cam; J->x0 = x0; J->y0 = y0; J->cw = cw; J->ch = ch;
-            J->M = rp[0]; J->K = rp[1]; J->R = rp[2];
+            J->M = rp[0]; J->K = rp[1]; J->R = rp[2]; J->Lm = rp[3];
             J->max_depth = max_depth; J->flags = flags; J->s = s0 + i; J->seed = seed;
             J->surf = surf; J->init = init; J->fin = fin; J->tid = t; J->nthreads = nthreads;
             pj[t].R = J; pj[t].i = i; pj[t].spp = spp; pj[t].sum = sum_out; pj[t].samples = samples_out;

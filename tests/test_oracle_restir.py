@@ -20,7 +20,7 @@ def _per_sample_means(smp):
 
 
 @pytest.mark.parametrize("restir,max_depth", [((1, 0, 1), 1), ((8, 0, 1), 1), ((8, 5, 4), 1),
-                                              ((32, 5, 6), 3)])
+                                              ((32, 5, 6), 3), ((8, 5, 4, 1), 3), ((8, 5, 4, 8), 3)])
 def test_restir_agrees_with_plain_tracer_in_expectation(restir, max_depth):
     sc = scenes.many_light_box(24, width=20, height=16, spp=192, max_depth=max_depth, seed=3)
     osc = oracle.OracleScene(sc)
@@ -121,3 +121,18 @@ def test_restir_is_deterministic_and_progressive():
     assert np.allclose(a + b, full, rtol=1e-12, atol=1e-15)
     # one shadow ray per pixel whose reservoir holds a sample, at most
     assert 0 < st["shadow_rays"] and st["paths"] == 18 * 14 * 6
+
+
+def test_later_candidates_lower_variance_of_indirect_light():
+    """Depth 3 with 64 lights: resampling 32 candidates at the later vertices too lowers the
+    per-pixel variance below ReSTIR at the primary vertex alone (measured median ratio 1.23;
+    next-event selection is only part of the indirect noise here)."""
+    sc = scenes.many_light_box(64, width=20, height=16, spp=96, max_depth=3, seed=5)
+    osc = oracle.OracleScene(sc)
+    _, a, _ = osc.render(keep_samples=True, restir=(8, 5, 6, 32))
+    _, b, _ = osc.render(keep_samples=True, restir=(8, 5, 6, 0))
+    va = a.var(axis=2, ddof=1).sum(-1)
+    vb = b.var(axis=2, ddof=1).sum(-1)
+    keep = (va > 0) & (vb > 0)
+    ratio = np.median(vb[keep] / va[keep])
+    assert ratio > 1.1, ratio

@@ -521,7 +521,8 @@ def run_restir_study(args, local):
     # light directly carry the same anti-aliasing noise either way)
     surf = scene.features(16, seed=9)[..., 3] >= 1.0
     marks = [m for m in (1, 2, 4, 8, 16, 32, 64, 128, 256) if m <= args.study_frames]
-    variants = {"plain": None, "restir_M32_K5_R10": (32, 5, 10), "restir_M8_K5_R10": (8, 5, 10)}
+    variants = {"plain": None, "restir_M32_K5_R10": (32, 5, 10), "restir_M8_K5_R10": (8, 5, 10),
+                "restir_M8_K5_R10_L8": (8, 5, 10, 8)}
     curves, split = {}, {}
     for kind, r in variants.items():
         acc = api.Accum(W, H)

@@ -148,11 +148,13 @@ enum { PT_K_RAYGEN = 0, PT_K_TRACE = 1, PT_K_SORT = 2, PT_K_SHADE = 3, PT_K_SHAD
 /* ReSTIR DI at the primary vertex (the paper names reservoir resampling for many-light
  * scenes as future work, Sec. 2 and Sec. 6.3; the algorithm is Bitterli et al. 2020).  Per
  * pixel and sample: `candidates` light samples from the next-event light sampler are
- * resampled into a one-sample reservoir with target = luminance of the unshadowed
- * contribution f L_e |cos| G; one spatial pass then resamples the reservoirs of up to
+ * resampled into a one-sample reservoir with the cheap target lum(L_e) G |cos| on the side
+ * the surface scatters to; one spatial pass then resamples, with the full target (the
+ * luminance of the unshadowed contribution f L_e |cos| G), this pixel's and the reservoirs of up to
  * `spatial_neighbors` pixels of the same sample (offsets uniform in [-R, R]^2, R =
  * `spatial_radius`, inside the window; neighbours with normal cosine < 0.9 or depth
- * differing by > 10 % are skipped) with the unbiased 1/Z weights.  Vertex 0 shades the
+ * differing by > 10 % are skipped) with the unbiased 1/Z weights (Z counts the reservoirs
+ * whose cheap target is positive at the chosen sample).  Vertex 0 shades the
  * result with one shadow ray in place of next-event estimation, and a BSDF-sampled light
  * hit at vertex 1 then counts with weight 0.  Each wave holds whole samples of the window.
  * Random numbers: candidate i uses (pixel, sample, 0xFFFF0001, dims 4i..4i+3), neighbour j
@@ -162,7 +164,12 @@ typedef struct {
     uint32_t candidates;        /* M >= 1 (at most 4096) */
     uint32_t spatial_neighbors; /* K, 0..64 (0 = no spatial pass) */
     uint32_t spatial_radius;    /* R >= 1 pixels (at most 4096) */
-    uint32_t reserved;          /* 0 */
+    uint32_t later_candidates;  /* L, 0..4096: at every later vertex, next-event estimation
+                                   resamples L light candidates with the cheap target (no
+                                   reuse; candidate i of vertex k: (pixel, sample,
+                                   0xFFFF0100 + k, dims 4i..4i+3)) and a BSDF-sampled light
+                                   hit after it counts with weight 0; 0 = next-event
+                                   estimation with MIS there */
 } pt_restir_opts;
 
 enum {

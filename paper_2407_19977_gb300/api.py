@@ -142,8 +142,10 @@ class Scene:
         o.tail_paths = int(tail_paths)
         o.use_graph = 1 if use_graph else 0
         if restir is not None:
-            # (M candidates, K neighbours, radius R): ReSTIR DI at the primary vertex
-            ro = N.pt_restir_opts(int(restir[0]), int(restir[1]), int(restir[2]), 0)
+            # (M candidates, K neighbours, radius R[, L later candidates]): ReSTIR DI at the
+            # primary vertex, resampled next-event estimation at later vertices if L > 0
+            r4 = (tuple(restir) + (0,))[:4]
+            ro = N.pt_restir_opts(int(r4[0]), int(r4[1]), int(r4[2]), int(r4[3]))
             o.restir = C.pointer(ro)
         o.sample_out = _ptr(sample_out) if sample_out is not None else None
         if nrc is not None:

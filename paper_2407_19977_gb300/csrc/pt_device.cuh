@@ -1035,6 +1035,55 @@ __device__ __forceinline__ float restir_target0(const DScene& S, float3 x, float
     return (ph > 0.0f && isfinite(ph)) ? ph : 0.0f;
 }
 
+constexpr uint32_t RESTIR_LATER = 0xFFFF0100u;   // + vertex index: candidates at vertex k >= 1
+
+// Resampled importance sampling of M light candidates from the next-event light sampler
+// (candidate i: Philox block (p, s, stream, i) = light pick, u, v, selection) with the cheap
+// target p0; the kept sample (light, y) has the unbiased contribution weight
+// W = sum w / (M p0(y)), w = p0 / source pdf (area measure on a quad, solid angle for the sky).
+__device__ __forceinline__ void restir_ris(const DScene& S, float3 x, float3 n, bool transmits, uint32_t p, uint32_t s,
+                                           uint32_t stream, uint32_t M, uint32_t k0, uint32_t k1, int& sel,
+                                           float3& y_sel, float& W, float& ph_sel) {
+    const bool has_env = S.env_w > 0 && S.env_total > 0.0f;
+    const float p_env = has_env ? (S.n_quads > 0 ? 0.5f : 1.0f) : 0.0f;
+    float wsum = 0.0f;
+    sel = LIGHT_NONE;
+    y_sel = splat3(0.0f);
+    ph_sel = 0.0f;
+    for (uint32_t i = 0; i < M; ++i) {
+        const uint4 r = philox4x32_10(make_uint4(p, s, stream, i), k0, k1);
+        const float u_pick = u24(r.x), u = u24(r.y), v = u24(r.z), u_sel = u24(r.w);
+        int light;
+        float3 y;
+        float src;
+        if (u_pick < p_env) {
+            float pe;
+            float3 Ld;
+            if (!env_sample(S, u, v, y, pe, Ld)) continue;
+            light = LIGHT_ENV;
+            src = p_env * pe;
+        } else {
+            int l = (int)floorf((u_pick - p_env) / (1.0f - p_env) * (float)S.n_quads);
+            l = min(l, S.n_quads - 1);
+            const DQuad& q = S.quads[l];
+            light = l;
+            y = q.p0 + q.e1 * u + q.e2 * v;
+            src = (1.0f - p_env) / (float)S.n_quads / q.area;
+        }
+        if (!(src > 0.0f)) continue;
+        const float ph = restir_target0(S, x, n, transmits, light, y);
+        const float w = ph / src;
+        if (!(w > 0.0f)) continue;
+        wsum += w;
+        if (u_sel * wsum < w) {
+            sel = light;
+            y_sel = y;
+            ph_sel = ph;
+        }
+    }
+    W = (sel != LIGHT_NONE && ph_sel > 0.0f) ? wsum / ((float)M * ph_sel) : 0.0f;
+}
+
 // The primary surface of a path as the reservoirs see it, rebuilt from its position, the
 // direction towards the camera and the triangle (the same steps as shade_vertex_h).
 struct RSurf {
@@ -1076,20 +1125,23 @@ struct NoHook {
 // the next ray, or SHADE_END.  `hook` sees every scattering vertex below the depth limit
 // (position, direction to the previous vertex, shading normal, material, path state) and
 // may end the path there (the radiance cache does).
-template <class Hook>
+// RIS: the ReSTIR DI branches (vertex 0 from its reservoir, later vertices by resampled
+// candidates, zero-weighted light hits) are compiled in only where a ReSTIR render runs.
+template <class Hook, bool RIS = false>
 __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, float3 o, float3 d, uint32_t k,
                                               uint32_t max_depth, uint32_t flags, const VertexRng& rng,
                                               PathState& ps, ShadeOut& out, Hook& hook,
-                                              const float4* rres = nullptr) {
+                                              const float4* rres = nullptr, uint32_t later_m = 0) {
     out.has_shadow = false;
     out.rr_end = false;
     const bool nee = !(flags & FLAG_NO_NEE);
     const bool has_env = S.env_w > 0 && S.env_total > 0.0f;
     const float p_env = has_env ? (S.n_quads > 0 ? 0.5f : 1.0f) : 0.0f;
     const bool prev_delta = ps.prev_pdf < 0.0f;
-    // with ReSTIR DI the reservoir at vertex 0 estimates all light arriving there: a light
-    // reached by BSDF sampling from vertex 0 counts with weight 0 (1 after a delta lobe)
-    const bool restir1 = (flags & FLAG_RESTIR) && k == 1;
+    // with ReSTIR DI the reservoir at vertex 0 (and, with later candidates, the resampled
+    // estimate at every later vertex) estimates all light arriving there: a light reached by
+    // BSDF sampling from such a vertex counts with weight 0 (1 after a delta lobe)
+    const bool restir1 = RIS && (flags & FLAG_RESTIR) && (k == 1 || (k > 1 && later_m > 0));
     if (h.tri == PT_NO_HIT) {
         if (has_env) {
             const float3 Le = env_radiance(S, d);
@@ -1133,7 +1185,7 @@ __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, 
     closure_setup(C, M, front, wo.z);
 
     const uint4 r0 = rng.block(0), r1 = rng.block(1), r2 = rng.block(2);
-    if ((flags & FLAG_RESTIR) && k == 0) {
+    if (RIS && (flags & FLAG_RESTIR) && k == 0) {
         // the sample of the path's final reservoir in place of next-event estimation
         if (rres != nullptr) {
             const float4 ry = rres[0], rw = rres[1];
@@ -1156,6 +1208,32 @@ __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, 
                     out.sh.tmax = tmax;
                     out.sh.contrib = (ps.beta * c) * rw.x;
                 }
+            }
+        }
+    } else if (RIS && (flags & FLAG_RESTIR) && later_m > 0 && C.has_smooth && (has_env || S.n_quads > 0)) {
+        // resampled light candidates at a later vertex (no reuse)
+        int light;
+        float3 yk;
+        float Wk, ph0;
+        restir_ris(S, x, n, (1.0f - C.m) * C.t > 0.0f, rng.p, rng.s, RESTIR_LATER + k, later_m, rng.k0, rng.k1, light,
+                   yk, Wk, ph0);
+        if (light != LIGHT_NONE && Wk > 0.0f) {
+            float3 c, ld;
+            if (restir_target(S, x, tt, bb, n, C, wo, light, yk, c, ld) > 0.0f) {
+                const float3 so = offset_origin(x, ng, ld, S.eps);
+                float3 sd = ld;
+                float tmax = __int_as_float(0x7f800000);
+                if (light >= 0) {
+                    const float3 to = yk - so;
+                    const float dl = len3(to);
+                    sd = to * (1.0f / dl);
+                    tmax = (1.0f - 1e-4f) * dl;
+                }
+                out.has_shadow = true;
+                out.sh.o = so;
+                out.sh.d = sd;
+                out.sh.tmax = tmax;
+                out.sh.contrib = (ps.beta * c) * Wk;
             }
         }
     } else if (nee && C.has_smooth && (has_env || S.n_quads > 0)) {
@@ -1228,11 +1306,13 @@ __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, 
     return SHADE_CONTINUE;
 }
 
+template <bool RIS = false>
 __device__ __forceinline__ int shade_vertex(const DScene& S, const HitRec& h, float3 o, float3 d, uint32_t k,
                                             uint32_t max_depth, uint32_t flags, const VertexRng& rng,
-                                            PathState& ps, ShadeOut& out, const float4* rres = nullptr) {
+                                            PathState& ps, ShadeOut& out, const float4* rres = nullptr,
+                                            uint32_t later_m = 0) {
     NoHook nh;
-    return shade_vertex_h(S, h, o, d, k, max_depth, flags, rng, ps, out, nh, rres);
+    return shade_vertex_h<NoHook, RIS>(S, h, o, d, k, max_depth, flags, rng, ps, out, nh, rres, later_m);
 }
 
 // "diffuse-ish" measure of a vertex: diffuse lobes count as roughness 1

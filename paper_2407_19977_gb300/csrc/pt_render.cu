@@ -330,7 +330,7 @@ struct WfParams {
     uint32_t* train_id;       // path id of each training path
     // ReSTIR DI at the primary vertex (whole windows per wave)
     int restir_on;
-    uint32_t restir_M, restir_K, restir_R;
+    uint32_t restir_M, restir_K, restir_R, restir_L;
     float4* rs_g0;            // per path: primary hit point, depth
     float4* rs_g1;            // per path: direction towards the camera, triangle bits (PT_NO_HIT: none)
     float4* rs_gn;            // per path: shading normal
@@ -584,7 +584,6 @@ __global__ void __launch_bounds__(128, 6) k_restir_init(WfParams P) {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const DScene& S = P.S;
     const bool has_env = S.env_w > 0 && S.env_total > 0.0f;
-    const float p_env = has_env ? (S.n_quads > 0 ? 0.5f : 1.0f) : 0.0f;
     for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < count; slot += gridDim.x * blockDim.x) {
         const float4 ro = P.ray_o[0][slot], rd = P.ray_d[0][slot];
         const float4 hh = P.hit[slot];
@@ -610,42 +609,11 @@ __global__ void __launch_bounds__(128, 6) k_restir_init(WfParams P) {
             const uint32_t lp = P.pb + id % P.npix;
             const uint32_t p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
             const uint32_t s = sbase + id / P.npix;
-            float wsum = 0.0f, ph_sel = 0.0f;
-            int sel = LIGHT_NONE;
-            float3 y_sel = splat3(0.0f);
-            for (uint32_t i = 0; i < P.restir_M; ++i) {
-                const uint4 r = philox4x32_10(make_uint4(p, s, RESTIR_CANDIDATES, i), k0, k1);
-                const float u_pick = u24(r.x), u = u24(r.y), v = u24(r.z), u_sel = u24(r.w);
-                int light;
-                float3 y;
-                float src;
-                if (u_pick < p_env) {
-                    float pe;
-                    float3 Ld;
-                    if (!env_sample(S, u, v, y, pe, Ld)) continue;
-                    light = LIGHT_ENV;
-                    src = p_env * pe;
-                } else {
-                    int l = (int)floorf((u_pick - p_env) / (1.0f - p_env) * (float)S.n_quads);
-                    l = min(l, S.n_quads - 1);
-                    const DQuad& q = S.quads[l];
-                    light = l;
-                    y = q.p0 + q.e1 * u + q.e2 * v;
-                    src = (1.0f - p_env) / (float)S.n_quads / q.area;
-                }
-                if (!(src > 0.0f)) continue;
-                const float ph = restir_target0(S, g.x, g.n, transmits, light, y);
-                const float w = ph / src;
-                if (!(w > 0.0f)) continue;
-                wsum += w;
-                if (u_sel * wsum < w) {
-                    sel = light;
-                    y_sel = y;
-                    ph_sel = ph;
-                }
-            }
+            int sel;
+            float3 y_sel;
+            float W, ph_sel;
+            restir_ris(S, g.x, g.n, transmits, p, s, RESTIR_CANDIDATES, P.restir_M, k0, k1, sel, y_sel, W, ph_sel);
             r0 = make_float4(y_sel.x, y_sel.y, y_sel.z, __int_as_float(sel));
-            const float W = (sel != LIGHT_NONE && ph_sel > 0.0f) ? wsum / ((float)P.restir_M * ph_sel) : 0.0f;
             r1 = make_float4(W, (float)P.restir_M, ph_sel, 0.0f);
         }
         P.rs_g1[id] = g1;
@@ -731,7 +699,7 @@ __global__ void __launch_bounds__(128, 6) k_restir_spatial(WfParams P, uint32_t 
     }
 }
 
-template <bool NRC>
+template <bool NRC, bool RIS>
 __global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
     if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[in_q];
@@ -778,7 +746,8 @@ __global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int o
                 P.aux[id] = hook.aux;
             } else {
                 const float4* rres = (P.restir_on && k == 0) ? P.rs_f + 2u * id : nullptr;
-                r = shade_vertex(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so, rres);
+                r = shade_vertex<RIS>(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so, rres,
+                                      P.restir_on ? P.restir_L : 0u);
             }
             P.radiance[id] = make_float4(ps.L.x, ps.L.y, ps.L.z, 0.0f);
             if (so.rr_end) rr_cnt++;
@@ -858,7 +827,7 @@ __global__ void __launch_bounds__(128) k_wf_shadow(WfParams P) {
 // numbers as k_wf_shade), then the shadow ray, whose contribution is added after the vertex's
 // own terms exactly as k_wf_shadow adds it.  It appends nothing, so the later per-bounce
 // launches of the wave find empty queues (and C_TAIL makes the rest of this bounce skip).
-template <bool NRC, bool COUNT>
+template <bool NRC, bool COUNT, bool RIS>
 __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32_t k0, uint32_t limit) {
     const uint32_t count = P.counters[in_q];
     if (count == 0 || count > limit) return;
@@ -898,7 +867,8 @@ __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32
             ShadeOut so;
             int r;
             if (NRC) r = shade_vertex_h(P.S, h, o, d, k, P.max_depth, P.flags, rng, ps, so, hook);
-            else r = shade_vertex(P.S, h, o, d, k, P.max_depth, P.flags, rng, ps, so);
+            else r = shade_vertex<RIS>(P.S, h, o, d, k, P.max_depth, P.flags, rng, ps, so, nullptr,
+                                       P.restir_on ? P.restir_L : 0u);
             if (so.rr_end) n_rr++;
             if (so.has_shadow) {
                 n_sh++;
@@ -1049,7 +1019,7 @@ static int g_trace_blocks_per_sm = 0, g_shade_blocks_per_sm = 0, g_shadow_blocks
 pt_status pt_wavefront_tail_limit(int* out) {
     if (g_tail_blocks_per_sm == 0) {
         int b = 0;
-        PT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_tail<true, false>, 128, 0));
+        PT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_tail<true, false, false>, 128, 0));
         g_tail_blocks_per_sm = std::max(b, 1);
     }
     *out = pt_num_sms() * g_tail_blocks_per_sm * 128;
@@ -1088,14 +1058,14 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_trace<false>, 128, 0);
         g_trace_blocks_per_sm = std::max(b, 1);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shade<false>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shade<false, false>, 128, 0);
         g_shade_blocks_per_sm = std::max(b, 1);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shadow<false>, 128, 0);
         g_shadow_blocks_per_sm = std::max(b, 1);
     }
     if (g_tail_blocks_per_sm == 0) {
         int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_tail<true, false>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_tail<true, false, false>, 128, 0);
         g_tail_blocks_per_sm = std::max(b, 1);
     }
     const int sms = pt_num_sms();
@@ -1125,6 +1095,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
         P.restir_M = o.restir->candidates;
         P.restir_K = o.restir->spatial_neighbors;
         P.restir_R = o.restir->spatial_radius;
+        P.restir_L = o.restir->later_candidates;
         P.rs_g0 = w.rs_g0; P.rs_g1 = w.rs_g1; P.rs_gn = w.rs_gn; P.rs_i = w.rs_i; P.rs_f = w.rs_f;
     }
     if (o.nrc) {
@@ -1211,11 +1182,16 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                     if (tail_limit && !(restir && k == 0)) {
                         e = begin(PT_K_TAIL);
                         if (P.nrc_on) {
-                            if (count) PT_LAUNCH((k_wf_tail<true, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                            else PT_LAUNCH((k_wf_tail<true, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                            if (count) PT_LAUNCH((k_wf_tail<true, true, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                            else PT_LAUNCH((k_wf_tail<true, false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
                         } else {
-                            if (count) PT_LAUNCH((k_wf_tail<false, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                            else PT_LAUNCH((k_wf_tail<false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                            if (restir) {
+                                if (count) PT_LAUNCH((k_wf_tail<false, true, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                                else PT_LAUNCH((k_wf_tail<false, false, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                            } else {
+                                if (count) PT_LAUNCH((k_wf_tail<false, true, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                                else PT_LAUNCH((k_wf_tail<false, false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                            }
                         }
                         end(e);
                         ++launches;
@@ -1240,8 +1216,9 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                         launches += 2;
                     }
                     e = begin(PT_K_SHADE);
-                    if (P.nrc_on) PT_LAUNCH(k_wf_shade<true>, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
-                    else PT_LAUNCH(k_wf_shade<false>, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+                    if (P.nrc_on) PT_LAUNCH((k_wf_shade<true, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+                    else if (restir) PT_LAUNCH((k_wf_shade<false, true>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+                    else PT_LAUNCH((k_wf_shade<false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
                     end(e);
                     e = begin(PT_K_SHADOW);
                     if (count) PT_LAUNCH(k_wf_shadow<true>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
@@ -1368,7 +1345,7 @@ extern "C" pt_status pt_render(pt_scene* s, const pt_camera* camera, uint32_t sp
         PT_CHECK_ARG(ro.candidates >= 1 && ro.candidates <= 4096, "restir candidates must be 1..4096");
         PT_CHECK_ARG(ro.spatial_neighbors <= 64, "restir spatial_neighbors must be 0..64");
         PT_CHECK_ARG(ro.spatial_radius >= 1 && ro.spatial_radius <= 4096, "restir spatial_radius must be 1..4096");
-        PT_CHECK_ARG(ro.reserved == 0, "restir reserved field must be 0");
+        PT_CHECK_ARG(ro.later_candidates <= 4096, "restir later_candidates must be 0..4096");
         PT_CHECK_ARG(!(o.flags & PT_FLAG_NO_NEE), "ReSTIR DI replaces next-event estimation: not with PT_FLAG_NO_NEE");
         if (o.mode == PT_MODE_MEGAKERNEL || o.nrc) {
             pt_set_error("ReSTIR DI runs in wavefront mode without the radiance cache");
@@ -1610,7 +1587,7 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_trace<false>, 128, 0);
         g_trace_blocks_per_sm = std::max(b, 1);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shade<false>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shade<false, false>, 128, 0);
         g_shade_blocks_per_sm = std::max(b, 1);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shadow<false>, 128, 0);
         g_shadow_blocks_per_sm = std::max(b, 1);
@@ -1654,7 +1631,7 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
                 PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
                 launches += 2;
             }
-            PT_LAUNCH(k_wf_shade<false>, sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+            PT_LAUNCH((k_wf_shade<false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
             PT_LAUNCH(k_wf_shadow<false>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
             launches += 2;
         }

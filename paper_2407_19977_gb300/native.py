@@ -40,7 +40,7 @@ class pt_accum(C.Structure):
 
 
 class pt_restir_opts(C.Structure):
-    _fields_ = [("candidates", u32), ("spatial_neighbors", u32), ("spatial_radius", u32), ("reserved", u32)]
+    _fields_ = [("candidates", u32), ("spatial_neighbors", u32), ("spatial_radius", u32), ("later_candidates", u32)]
 
 
 class pt_render_opts(C.Structure):

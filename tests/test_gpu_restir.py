@@ -35,7 +35,7 @@ def _pair(sc, restir, spp, crop=None, seed=0, **kw):
     return g, acc, samples.cpu().numpy(), o_smp, st
 
 
-@pytest.mark.parametrize("restir", [(1, 0, 1), (8, 0, 1), (8, 5, 4), (32, 8, 6)])
+@pytest.mark.parametrize("restir", [(1, 0, 1), (8, 0, 1), (8, 5, 4), (32, 8, 6), (8, 5, 4, 1), (8, 5, 4, 16)])
 def test_restir_parity_many_lights(api, restir):
     sc = scenes.many_light_box(32, width=48, height=40, spp=4, max_depth=3, seed=1)
     g, acc, gs, os_, st = _pair(sc, restir, sc.spp, seed=3)
@@ -50,7 +50,7 @@ def test_restir_parity_in_a_window_and_with_the_sky(api):
     _, _, gs, os_, _ = _pair(sc, (8, 6, 5), sc.spp, crop=(9, 7, 37, 23), seed=5)
     _samples_check(gs, os_, "restir window", max_divergent=4e-3)
     pb = scenes.pushbutton()
-    _, _, gs, os_, _ = _pair(pb, (16, 5, 8), 2, crop=(760, 420, 96, 64), seed=7)
+    _, _, gs, os_, _ = _pair(pb, (16, 5, 8, 4), 2, crop=(760, 420, 96, 64), seed=7)
     _samples_check(gs, os_, "restir pushbutton crop", max_divergent=4e-3)
 
 
@@ -78,7 +78,7 @@ def test_restir_arguments(api):
     sc = scenes.many_light_box(8, width=16, height=16, spp=1, max_depth=2)
     g = A.Scene(sc)
     acc = A.Accum(16, 16)
-    for bad in ((0, 0, 1), (4, 65, 1), (4, 2, 0)):
+    for bad in ((0, 0, 1), (4, 65, 1), (4, 2, 0), (4, 2, 2, 5000)):
         with pytest.raises(N.PtError, match="INVALID_ARG"):
             g.render(1, accum=acc, mode=1, restir=bad)
     with pytest.raises(N.PtError, match="INVALID_ARG"):

@@ -77,6 +77,8 @@ def _args():
                     help="nrc: relMSE vs time, radiance cache against the plain tracer")
     ap.add_argument("--ref-spp", type=int, default=4096)
     ap.add_argument("--max-depth", type=int, default=None, help="studies: override the workload's max depth")
+    ap.add_argument("--nrc-batch", type=int, default=8192, help="NRC study: training samples per Adam step")
+    ap.add_argument("--nrc-frame-samples", type=int, default=32768, help="NRC study: training samples per frame")
     return ap.parse_args()
 
 
@@ -617,7 +619,8 @@ def run_bmfr_study(args, local):
 
 def run_nrc_study(args, local):
     """relMSE against a high-spp plain reference as a function of device time, for the plain
-    tracer and for the radiance-cache tracer (trained online every frame)."""
+    tracer and for the radiance-cache tracer (trained online every frame), both progressive
+    at 1 spp per frame with graph replay (the first frame, which captures, is timed too)."""
     import torch
     from paper_2407_19977_gb300 import api
     from paper_2407_19977_gb300 import native as N
@@ -637,14 +640,16 @@ def run_nrc_study(args, local):
     lo = sc.vertices.min(0) - 0.05
     hi = sc.vertices.max(0) + 0.05
     for kind in ("plain", "nrc"):
-        net = api.Nrc(seed=5, box=(tuple(map(float, lo)), tuple(map(float, hi)))) if kind == "nrc" else None
+        net = (api.Nrc(seed=5, box=(tuple(map(float, lo)), tuple(map(float, hi))), batch=args.nrc_batch,
+                       frame_samples=args.nrc_frame_samples) if kind == "nrc" else None)
         acc = api.Accum(W, H)
         t_ms = 0.0
         pts = []
         for f in range(1, marks[-1] + 1):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            scene.render(1, seed=0, accum=acc, mode=N.PT_MODE_WAVEFRONT, nrc=net, nrc_train=net is not None)
+            scene.render(1, seed=0, accum=acc, mode=N.PT_MODE_WAVEFRONT, nrc=net, nrc_train=net is not None,
+                         use_graph=True)
             e1.record(stream)
             torch.cuda.synchronize()
             t_ms += e0.elapsed_time(e1)
@@ -654,6 +659,7 @@ def run_nrc_study(args, local):
 
     time_to = _time_to
     out = {"study": "nrc_equal_time", "workload": WORKLOADS[args.workload], "ref_spp": args.ref_spp,
+           "nrc_batch": args.nrc_batch, "nrc_frame_samples": args.nrc_frame_samples,
            "relmse_eps": 1e-2, "curves": curves}
     for spp in (16, 64):
         if spp > marks[-1]:

@@ -205,8 +205,10 @@ typedef struct {
                                    camera, window, accumulator, spp, depth, options); the first
                                    sample index and the seed are written to device memory before
                                    each replay, so progressive calls reuse one graph.  The capture
-                                   runs on a stream of the scene; replays run on cuda_stream.  Not
-                                   with nrc or kernel_ms (those calls launch directly). */
+                                   runs on a stream of the scene; replays run on cuda_stream.  With
+                                   nrc the cache's inference and training are in the graph too
+                                   (Adam's step count lives on the device); not with kernel_ms
+                                   (that call launches directly). */
     const pt_restir_opts* restir; /* optional: ReSTIR DI at the primary vertex (NULL = next-event
                                    estimation) */
 } pt_render_opts;

@@ -162,6 +162,7 @@ pt_status pt_wavefront_tail_limit(int* out);
 pt_status pt_nrc_render_infer_dev(pt_nrc* N, const float* queries, const uint32_t* n_dev, uint32_t cap, float* out4,
                                   cudaStream_t st);
 uint32_t pt_nrc_frame_samples(const pt_nrc* N);
+pt_status pt_nrc_render_prepare(pt_nrc* N, uint32_t infer_cap, uint32_t train_cap);
 pt_status pt_nrc_render_train_dev(pt_nrc* N, const float* samples, const uint32_t* n_dev, uint32_t cap, cudaStream_t st);
 
 // the lens of a camera: radius finite and >= 0; an open lens needs a finite focus distance > 0

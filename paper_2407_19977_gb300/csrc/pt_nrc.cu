@@ -258,10 +258,14 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __half* p) {
 // 2r + j / 16 (r = 0..7): its level's resolution and table stay in registers and it issues
 // its 64 corner gathers back to back.  The tile then feeds the same tensor-core layers as
 // k_mlp_forward, with the A fragments read by ldmatrix.
-__global__ void __launch_bounds__(128) k_nrc_infer(GridDesc G, const float* __restrict__ queries, RowCount rc,
-                                                   const __half* __restrict__ Wg, float* __restrict__ Y) {
+// 256 threads share one copy of the weights in shared memory (the copy, not the registers,
+// limited 128-thread blocks to 4 per SM); three blocks of eight warps fit per SM
+constexpr int INFER_THREADS = 256;
+__global__ void __launch_bounds__(INFER_THREADS, 3) k_nrc_infer(GridDesc G, const float* __restrict__ queries,
+                                                                RowCount rc, const __half* __restrict__ Wg,
+                                                                float* __restrict__ Y) {
     __shared__ __align__(16) __half sw[(N_HIDDEN * W + OUT_PAD) * SROW];
-    __shared__ __align__(16) __half sx[4][16 * SROW];
+    __shared__ __align__(16) __half sx[INFER_THREADS / 32][16 * SROW];
     load_weights_smem(sw, Wg);
     __syncthreads();
     const uint32_t n = rc.get();
@@ -793,11 +797,26 @@ __global__ void k_reduce_grad(const float* __restrict__ part, uint32_t nparts, f
     dw[i] = s * scale;
 }
 
+// the step counter of Adam lives on the device: a batch that the device finds empty is no
+// step, and a captured graph replays with the current count
+__global__ void k_adam_step(uint32_t* step, RowCount rc) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && rc.get() > 0) *step += 1u;
+}
+
+// bias corrections 1 - b^t of step t
+__device__ __forceinline__ void adam_corrections(const uint32_t* step, float b1, float b2, float& c1, float& c2) {
+    const float t = (float)*step;
+    c1 = 1.0f - powf(b1, t);
+    c2 = 1.0f - powf(b2, t);
+}
+
 // Adam (Kingma & Ba): master FP32 parameters, FP16 copy for the kernels, gradient zeroed
 __global__ void k_adam(float* __restrict__ p, float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
-                       __half* __restrict__ copy, uint64_t n, float lr, float b1, float b2, float eps, float c1, float c2,
-                       RowCount rc) {
+                       __half* __restrict__ copy, uint64_t n, float lr, float b1, float b2, float eps,
+                       const uint32_t* __restrict__ step, RowCount rc) {
     if (rc.get() == 0) return;   // an empty batch is no step
+    float c1, c2;
+    adam_corrections(step, b1, b2, c1, c2);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const float gr = grad[i];
         const float mi = b1 * m[i] + (1.0f - b1) * gr;
@@ -826,9 +845,11 @@ __device__ __forceinline__ float adam_lane(float gr, float& pm, float& mm, float
 }
 
 __global__ void k_adam_lazy(float* __restrict__ p, float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
-                            __half* __restrict__ copy, uint64_t n4, float lr, float b1, float b2, float eps, float c1,
-                            float c2, RowCount rc) {
+                            __half* __restrict__ copy, uint64_t n4, float lr, float b1, float b2, float eps,
+                            const uint32_t* __restrict__ step, RowCount rc) {
     if (rc.get() == 0) return;
+    float c1, c2;
+    adam_corrections(step, b1, b2, c1, c2);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4; i += (uint64_t)gridDim.x * blockDim.x) {
         const float4 g4 = reinterpret_cast<const float4*>(grad)[i];
         if (g4.x == 0.0f && g4.y == 0.0f && g4.z == 0.0f && g4.w == 0.0f) continue;
@@ -888,6 +909,7 @@ struct pt_nrc {
     uint32_t cap = 0;
     __half *X = nullptr, *acts = nullptr, *dY = nullptr, *dZ = nullptr;
     float *Y = nullptr, *dX = nullptr, *part = nullptr, *d_loss = nullptr;
+    uint32_t* d_step = nullptr;   // Adam's step count (device)
     uint32_t* d_err = nullptr;     // device error word (1: a tensor-core wait ran out)
     // inference buffers
     uint32_t icap = 0;
@@ -991,6 +1013,8 @@ extern "C" pt_status pt_nrc_create(const pt_nrc_opts* opts, void* cuda_stream, p
     NTRY(cudaMalloc(&N->d_loss, 4 * sizeof(float)));
     NTRY(cudaMalloc(&N->d_err, sizeof(uint32_t)));
     NTRY(cudaMemsetAsync(N->d_err, 0, sizeof(uint32_t), st));
+    NTRY(cudaMalloc(&N->d_step, sizeof(uint32_t)));
+    NTRY(cudaMemsetAsync(N->d_step, 0, sizeof(uint32_t), st));
     for (float* p : {N->d_wm, N->d_wv, N->d_wg}) NTRY(cudaMemsetAsync(p, 0, N_WEIGHTS * sizeof(float), st));
     for (float* p : {N->d_gm, N->d_gv, N->d_gg}) NTRY(cudaMemsetAsync(p, 0, N->n_grid * sizeof(float), st));
     NTRY(cudaMemsetAsync(N->d_loss, 0, 4 * sizeof(float), st));
@@ -1008,7 +1032,8 @@ extern "C" void pt_nrc_destroy(pt_nrc* N) {
     if (!N) return;
     cudaDeviceSynchronize();
     void* ps[] = {N->d_res, N->d_w, N->d_wh, N->d_wm, N->d_wv, N->d_wg, N->d_grid, N->d_gh, N->d_gm, N->d_gv, N->d_gg,
-                  N->X, N->acts, N->dY, N->dZ, N->Y, N->dX, N->part, N->d_loss, N->iX, N->iY, N->d_err};
+                  N->X, N->acts, N->dY, N->dZ, N->Y, N->dX, N->part, N->d_loss, N->iX, N->iY, N->d_err,
+                  N->d_step};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete N;
@@ -1047,12 +1072,13 @@ static pt_status nrc_forward(pt_nrc* N, const float* q, RowCount rc, __half* X, 
         // inference: encoding and MLP in one kernel on mma.sync, persistent over 16-row tiles
         if (g_infer_blocks == 0) {
             int b = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_nrc_infer, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_nrc_infer, INFER_THREADS, 0);
             g_infer_blocks = std::max(b, 1) * pt_num_sms();
         }
         const uint32_t tiles = (rc.n + 15) / 16;
-        const uint32_t blocks = std::max(1u, std::min((uint32_t)g_infer_blocks, (tiles + 3) / 4));
-        PT_LAUNCH(k_nrc_infer, blocks, 128, 0, st, G, q, rc, N->d_wh, Y);
+        const uint32_t per_block = INFER_THREADS / 32;
+        const uint32_t blocks = std::max(1u, std::min((uint32_t)g_infer_blocks, (tiles + per_block - 1) / per_block));
+        PT_LAUNCH(k_nrc_infer, blocks, INFER_THREADS, 0, st, G, q, rc, N->d_wh, Y);
         N->launches += 1;
         PT_CUDA_TRY(cudaGetLastError());
         return PT_OK;
@@ -1096,16 +1122,16 @@ static pt_status nrc_gradients(pt_nrc* N, const float* samples, RowCount rc, cud
 static pt_status nrc_adam(pt_nrc* N, RowCount rc, cudaStream_t st) {
     N->step++;
     const float b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
-    const float c1 = 1.0f - std::pow(b1, (float)N->step), c2 = 1.0f - std::pow(b2, (float)N->step);
     const float lr = N->o.learning_rate;
+    PT_LAUNCH(k_adam_step, 1, 32, 0, st, N->d_step, rc);
     PT_LAUNCH(k_adam, 2 * pt_num_sms(), 256, 0, st, N->d_w, N->d_wg, N->d_wm, N->d_wv, N->d_wh, (uint64_t)N_WEIGHTS, lr,
-              b1, b2, eps, c1, c2, rc);
+              b1, b2, eps, N->d_step, rc);
     // one thread per float4 group: every group's loads are in flight at once
     const uint64_t groups = N->n_grid / 4;
     const uint32_t ablocks = (uint32_t)std::min<uint64_t>((groups + 255) / 256, 1u << 20);
     PT_LAUNCH(k_adam_lazy, ablocks, 256, 0, st, N->d_grid, N->d_gg, N->d_gm, N->d_gv, N->d_gh, groups,
-              lr, b1, b2, eps, c1, c2, rc);
-    N->launches += 2;
+              lr, b1, b2, eps, N->d_step, rc);
+    N->launches += 3;
     PT_CUDA_TRY(cudaGetLastError());
     return PT_OK;
 }
@@ -1187,14 +1213,26 @@ extern "C" pt_status pt_nrc_last_loss(pt_nrc* N, float* loss) {
 }
 
 // ---- hooks used by the renderer: the row counts stay on the device (no host round trip) ----
+static pt_status ensure_infer(pt_nrc* N, uint32_t cap) {
+    if (N->icap >= cap) return PT_OK;
+    if (N->iX) cudaFree(N->iX);
+    N->iX = nullptr;
+    PT_CUDA_TRY(cudaMalloc(&N->iX, (size_t)cap * W * sizeof(__half)));
+    N->icap = cap;
+    return PT_OK;
+}
+
+// scratch for a renderer's calls, allocated before a graph capture (none happens inside one)
+pt_status pt_nrc_render_prepare(pt_nrc* N, uint32_t infer_cap, uint32_t train_cap) {
+    pt_status r = ensure_infer(N, infer_cap);
+    if (r != PT_OK) return r;
+    return ensure_train(N, std::min(N->o.batch, std::max(train_cap, 1u)));
+}
+
 pt_status pt_nrc_render_infer_dev(pt_nrc* N, const float* queries, const uint32_t* n_dev, uint32_t cap, float* out4,
                                   cudaStream_t st) {
-    if (N->icap < cap) {
-        if (N->iX) cudaFree(N->iX);
-        N->iX = nullptr;
-        PT_CUDA_TRY(cudaMalloc(&N->iX, (size_t)cap * W * sizeof(__half)));
-        N->icap = cap;
-    }
+    pt_status r = ensure_infer(N, cap);
+    if (r != PT_OK) return r;
     return nrc_forward(N, queries, RowCount{cap, n_dev, 0}, N->iX, out4, nullptr, st);
 }
 

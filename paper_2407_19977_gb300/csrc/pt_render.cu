@@ -340,6 +340,14 @@ struct WfParams {
 };
 
 constexpr uint32_t NRC_DIM_TRAIN = 10;   // uniform dimension of the training-path choice
+constexpr uint32_t NRC_TRAIN_END = 4;     // diffuse-ish vertex at which training paths end into the cache
+constexpr bool NRC_FACTOR_ALBEDO = true;   // the cache learns radiance / (albedo + 0.01)
+
+// albedo of a vertex for the factorisation: (m + (1-m)(1-t)) bw bc + (1-m) t tc + sw 0.04 sc
+__device__ __forceinline__ float3 nrc_albedo(const DMat& M) {
+    return M.base_color * ((M.metalness + (1.0f - M.metalness) * (1.0f - M.trans_weight)) * M.base_weight) +
+           M.trans_color * ((1.0f - M.metalness) * M.trans_weight) + M.spec_color * (0.04f * M.spec_weight);
+}
 
 // first sample index of this wave and the seed, from the per-call words of the counters
 __device__ __forceinline__ uint32_t wf_sample_base(const WfParams& P) { return P.counters[C_FRAME] + P.i0; }
@@ -399,18 +407,28 @@ struct NrcHook {
                                                uint32_t k) {
         const float r = effective_roughness(M);
         const uint32_t slot1 = aux >> 8;
+        // the cache learns outgoing radiance divided by the vertex's albedo (+ 0.01), so it
+        // need not reproduce colour steps between materials: the records carry beta times that
+        // factor, which both the cache's output (k_nrc_apply) and the targets use
+        const float3 fb = NRC_FACTOR_ALBEDO ? ps.beta * (nrc_albedo(M) + splat3(0.01f)) : ps.beta;
         if (slot1 && k < P->rec_per_path) {
             float4* rec = reinterpret_cast<float4*>(P->train_rec + ((size_t)(slot1 - 1) * P->rec_per_path + k) * 16);
             rec[0] = make_float4(x.x, x.y, x.z, wo.x);
             rec[1] = make_float4(wo.y, wo.z, n.x, n.y);
             rec[2] = make_float4(n.z, r, ps.L.x, ps.L.y);
-            rec[3] = make_float4(ps.L.z, ps.beta.x, ps.beta.y, ps.beta.z);
+            rec[3] = make_float4(ps.L.z, fb.x, fb.y, fb.z);
             P->train_nv[slot1 - 1] = k + 1;
         }
         if (r >= 0.25f) {
             const uint32_t cnt = min((aux & 0xffu) + 1u, 255u);
             aux = (aux & ~0xffu) | cnt;
-            if (cnt == 2u && !slot1) {
+            // rendering paths end into the cache at their second diffuse-ish vertex; training
+            // paths go NRC_TRAIN_END - 2 such vertices further and end into the cache there
+            // too (self-training: their suffix targets then include the cache's estimate of
+            // the rest of the path, and the terminal vertex itself is not a training record)
+            const bool train_end = slot1 && cnt == NRC_TRAIN_END;
+            if (train_end && k < P->rec_per_path) P->train_nv[slot1 - 1] = k;
+            if ((cnt == 2u && !slot1) || train_end) {
                 // warp-aggregated append: the lanes that reach this point take consecutive slots
                 const uint32_t active = __activemask();
                 const uint32_t lane = threadIdx.x & 31u;
@@ -422,8 +440,8 @@ struct NrcHook {
                 float4* rec = reinterpret_cast<float4*>(P->nrc_q + (size_t)q * 16);
                 rec[0] = make_float4(x.x, x.y, x.z, wo.x);
                 rec[1] = make_float4(wo.y, wo.z, n.x, n.y);
-                rec[2] = make_float4(n.z, r, ps.beta.x, ps.beta.y);
-                rec[3] = make_float4(ps.beta.z, __uint_as_float(id), 0.0f, 0.0f);
+                rec[2] = make_float4(n.z, r, fb.x, fb.y);
+                rec[3] = make_float4(fb.z, __uint_as_float(id), 0.0f, 0.0f);
                 return true;
             }
         }
@@ -488,9 +506,9 @@ __device__ __forceinline__ uint32_t hit_key(const DScene& S, const HitRec& h, ui
     return (code & PT_LIGHT_BIT) ? n_mats + 1 : code;
 }
 
-// Persistent closest-hit over the input queue.  Each lane runs one ray at a time in the
-// step form (one BVH node per iteration); whenever lanes of a warp finish, the warp fetches
-// that many new queue slots with one atomic, so lanes stay busy until the queue drains.
+// Persistent closest-hit over the input queue.  A warp takes 32 queue slots with one atomic,
+// each lane carries its ray through the per-ray step loop (one BVH node per step), and the
+// warp takes the next 32 once all of its rays are done (lane refill was measured slower).
 template <bool COUNT>
 __global__ void __launch_bounds__(128) k_wf_trace(WfParams P, int in_q) {
     __shared__ uint32_t hist[MAX_SORT_KEYS];
@@ -1032,6 +1050,7 @@ struct WfGraphKey {
     WfParams P;             // with the per-wave fields cleared
     uint32_t spp, npix_total, pix_chunk, samp_per_wave, tail_limit, tail_grid, count;
     int sms, trace_bps, shade_bps, shadow_bps;
+    const void* nrc;        // the radiance cache the launches read and train
 };
 
 static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
@@ -1101,6 +1120,8 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     if (o.nrc) {
         r = ensure_nrc_buffers(w, std::min(max_depth + 1, 16u), pt_nrc_frame_samples(o.nrc));
         if (r != PT_OK) return r;
+        r = pt_nrc_render_prepare(o.nrc, pix_chunk * samp_per_wave, w.sample_cap);
+        if (r != PT_OK) return r;
         P.nrc_on = 1;
         P.rec_per_path = w.rec_per_path;
         P.max_train = o.nrc_train ? w.train_slots : 0;
@@ -1116,7 +1137,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     // the per-call words first, on the caller's stream (graph or not)
     PT_LAUNCH(k_wf_frame, 1, 32, 0, user_st, w.counters, (uint32_t)acc->spp_done, seed);
     ++launches;
-    const bool graph = o.use_graph && !P.nrc_on && !timed;
+    const bool graph = o.use_graph && !timed;
     WfGraphKey key;
     if (graph) {
         std::memset(&key, 0, sizeof(key));
@@ -1125,6 +1146,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
         key.tail_limit = tail_limit; key.tail_grid = tail_grid; key.count = count ? 1u : 0u;
         key.sms = sms; key.trace_bps = g_trace_blocks_per_sm; key.shade_bps = g_shade_blocks_per_sm;
         key.shadow_bps = g_shadow_blocks_per_sm;
+        key.nrc = o.nrc;
         if (s->wf_graph && s->wf_key.size() == sizeof(key) && std::memcmp(s->wf_key.data(), &key, sizeof(key)) == 0) {
             PT_CUDA_TRY(cudaGraphLaunch(s->wf_graph, user_st));
             pt_count_launch(s->wf_graph_launches);

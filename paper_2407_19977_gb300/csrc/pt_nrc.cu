@@ -258,10 +258,11 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __half* p) {
 // 2r + j / 16 (r = 0..7): its level's resolution and table stay in registers and it issues
 // its 64 corner gathers back to back.  The tile then feeds the same tensor-core layers as
 // k_mlp_forward, with the A fragments read by ldmatrix.
-// 256 threads share one copy of the weights in shared memory (the copy, not the registers,
-// limited 128-thread blocks to 4 per SM); three blocks of eight warps fit per SM
-constexpr int INFER_THREADS = 256;
-__global__ void __launch_bounds__(INFER_THREADS, 3) k_nrc_infer(GridDesc G, const float* __restrict__ queries,
+// 512 threads share one copy of the weights in shared memory (the copy, not the registers,
+// limited 128-thread blocks to 4 per SM); two blocks of sixteen warps fit per SM (64
+// registers, no spills)
+constexpr int INFER_THREADS = 512;
+__global__ void __launch_bounds__(INFER_THREADS, 2) k_nrc_infer(GridDesc G, const float* __restrict__ queries,
                                                                 RowCount rc, const __half* __restrict__ Wg,
                                                                 float* __restrict__ Y) {
     __shared__ __align__(16) __half sw[(N_HIDDEN * W + OUT_PAD) * SROW];

@@ -70,6 +70,14 @@ def _load():
         lib.oracle_bsdf_sample.argtypes = [_dp, C.c_int, _dp, _dp, _dp, _dp, _dp, _i32p]
         lib.oracle_bsdf_sample.restype = C.c_int
         lib.oracle_lobe_probs.argtypes = [_dp, C.c_int, C.c_double, _dp]
+        lib.oracle_sheen_D.argtypes = [C.c_double, C.c_double]
+        lib.oracle_sheen_D.restype = C.c_double
+        lib.oracle_sheen_area.argtypes = [C.c_double, C.c_double]
+        lib.oracle_sheen_area.restype = C.c_double
+        lib.oracle_sheen_albedo.argtypes = [C.c_double, C.c_double]
+        lib.oracle_sheen_albedo.restype = C.c_double
+        lib.oracle_sheen_f.argtypes = [_dp, _dp, C.c_double]
+        lib.oracle_sheen_f.restype = C.c_double
         lib.oracle_scene_create.argtypes = [_dp, C.c_int, _u32p, C.c_int, _u32p, _dp, C.c_int,
                                             _dp, C.c_int, _dp, C.c_int, C.c_int, C.c_int]
         lib.oracle_scene_create.restype = C.c_void_p
@@ -162,6 +170,28 @@ def tangent_frame(n, e1, rot):
     return t, b
 
 
+def sheen_D(cos_m, alpha):
+    """Charlie microfacet distribution of the fuzz lobe (width alpha)."""
+    return _load().oracle_sheen_D(float(cos_m), float(alpha))
+
+
+def sheen_area(mu, alpha):
+    """Projected area A(mu) = int <w, m>+ D(m) dm of the fuzz distribution (G1 = mu / A)."""
+    return _load().oracle_sheen_area(float(mu), float(alpha))
+
+
+def sheen_albedo(mu, alpha):
+    """Directional albedo E(mu) of the uncoloured fuzz lobe."""
+    return _load().oracle_sheen_albedo(float(mu), float(alpha))
+
+
+def sheen_f(wo, wi, alpha):
+    """The uncoloured fuzz lobe f_s(wo, wi) (0 unless both are above the surface)."""
+    wo, po = _d(wo)
+    wi, pi = _d(wi)
+    return _load().oracle_sheen_f(po, pi, float(alpha))
+
+
 def bsdf_eval(mat, front, wo, wi):
     """Non-delta part of f(wo, wi) (RGB) and the mixture sampling pdf of wi."""
     m, pm = _d(mat)
@@ -230,8 +260,9 @@ def uniform_batch(pixel, sample, bounce, dim, seed):
 
 
 def lobe_probs(mat, front, mu_o):
+    """Selection probabilities of the lobes (coat, metal, dielectric, diffuse, fuzz) at mu_o."""
     m, pm = _d(mat)
-    o = np.zeros(4)
+    o = np.zeros(5)
     _load().oracle_lobe_probs(pm, int(front), float(mu_o), o.ctypes.data_as(_dp))
     return o
 

@@ -30,6 +30,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -91,9 +92,9 @@ enum { DIM_CAM_X = 0, DIM_CAM_Y = 1, DIM_LIGHT_PICK = 2, DIM_LIGHT_U = 3, DIM_LI
        DIM_LENS_U = 12, DIM_LENS_V = 13 };
 
 /* ------------------------------------------------------------------------------------ */
-/* OpenPBR parameters (OPBR_N = 29 values per material, same order as the C-ABI table)   */
+/* OpenPBR parameters (OPBR_N = 34 values per material, same order as the C-ABI table)   */
 /* ------------------------------------------------------------------------------------ */
-#define OPBR_N 29
+#define OPBR_N 34
 typedef struct {
     double base_weight; v3 base_color; double metalness; double diffuse_roughness;
     double spec_weight; v3 spec_color; double spec_rough; double spec_ior;
@@ -103,6 +104,7 @@ typedef struct {
     int thin_walled;
     double spec_aniso;    /* specular_roughness_anisotropy in [0, 1] */
     double spec_rot;      /* tangent rotation about the normal, in turns */
+    double fuzz_weight; v3 fuzz_color; double fuzz_rough;
 } omat;
 
 static omat unpack_material(const double* p) {
@@ -117,6 +119,7 @@ static omat unpack_material(const double* p) {
     m.emission = p[22]; m.emission_color = mk(p[23], p[24], p[25]);
     m.thin_walled = p[26] != 0.0;
     m.spec_aniso = p[27]; m.spec_rot = p[28];
+    m.fuzz_weight = p[29]; m.fuzz_color = mk(p[30], p[31], p[32]); m.fuzz_rough = p[33];
     return m;
 }
 
@@ -215,6 +218,136 @@ void oracle_ggx_vndf_sample(const double wo[3], double ax, double ay, double u1,
     out[0] = h.x; out[1] = h.y; out[2] = h.z;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Fuzz lobe (OpenPBR fuzz layer; reading).  A microfacet sheen lobe: the "Charlie"       */
+/* distribution of Estevez & Kulla 2017, D(m) = (2 + 1/a) sin(theta_m)^(1/a) / (2 pi) with  */
+/* a = max(fuzz_roughness, 0.2)^2, and its exact Smith masking.  The masking of a          */
+/* distribution follows from its projected area A(mu) = int <w, m>+ D(m) dm (G1 = mu / A,  */
+/* Lambda = A / mu - 1; Heitz 2014), so the height-correlated lobe is                     */
+/*   f_s(wo, wi) = D(h) G2 / (4 mu_i mu_o) = D(h) / (4 (A(mu_i) mu_o + A(mu_o) mu_i - mu_i mu_o)). */
+/* A has no closed form for this D: it and the lobe's directional albedo                   */
+/*   E(mu_o) = int f_s(wo, wi) mu_i dwi                                                   */
+/* are integrated numerically below, every time they are needed (Gauss-Legendre rules).  */
+/* ------------------------------------------------------------------------------------ */
+#define GL_N 64
+static double gl_x[GL_N], gl_w[GL_N];   /* Gauss-Legendre nodes and weights on [-1, 1] */
+static pthread_once_t gl_once = PTHREAD_ONCE_INIT;
+
+/* nodes = roots of the Legendre polynomial P_n, by Newton's method from the usual
+ * cos(pi (j + 3/4) / (n + 1/2)) guesses; weights 2 / ((1 - x^2) P_n'(x)^2) */
+static void gl_init(void) {
+    const int n = GL_N;
+    for (int j = 0; j < n; ++j) {
+        double x = cos(M_PI * (j + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        gl_x[j] = x;
+        gl_w[j] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+/* node j of the 64-point rule mapped to [a, b], with its weight */
+static void gl_node(double a, double b, int j, double* t, double* w) {
+    pthread_once(&gl_once, gl_init);
+    *t = 0.5 * (b + a) + 0.5 * (b - a) * gl_x[j];
+    *w = 0.5 * (b - a) * gl_w[j];
+}
+
+static double fuzz_alpha(double rough) {
+    double r = fmax(rough, 0.2);
+    return r * r;
+}
+
+/* Charlie distribution at a microfacet normal with cosine cos_m to the surface normal */
+double oracle_sheen_D(double cos_m, double alpha) {
+    double s2 = fmax(0.0, 1.0 - cos_m * cos_m);
+    return (2.0 + 1.0 / alpha) * pow(s2, 0.5 / alpha) / (2.0 * M_PI);
+}
+
+/* A(mu) = int D(theta_m) sin(theta_m) int_0^{2pi} max(0, a cos(phi) + b) dphi dtheta_m with
+ * a = sin(theta) sin(theta_m), b = mu cos(theta_m).  The inner integral is 2 pi b where
+ * b >= a (theta_m <= asin(mu): the whole circle faces w) and 2 a sin(phi0) + 2 b phi0 with
+ * cos(phi0) = -b/a elsewhere; the theta_m integral is split at that kink. */
+double oracle_sheen_area(double mu, double alpha) {
+    mu = fmin(fmax(mu, 0.0), 1.0);
+    const double st = sqrt(fmax(0.0, 1.0 - mu * mu)), split = asin(mu);
+    double sum = 0.0;
+    for (int j = 0; j < GL_N; ++j) {
+        double th, w;
+        gl_node(0.0, split, j, &th, &w);
+        sum += w * oracle_sheen_D(cos(th), alpha) * sin(th) * 2.0 * M_PI * mu * cos(th);
+    }
+    for (int j = 0; j < GL_N; ++j) {
+        double th, w;
+        gl_node(split, 0.5 * M_PI, j, &th, &w);
+        const double a = st * sin(th), b = mu * cos(th);
+        double inner;
+        if (b >= a) {
+            inner = 2.0 * M_PI * b;
+        } else {
+            const double c = -b / a;
+            inner = 2.0 * a * sqrt(fmax(0.0, 1.0 - c * c)) + 2.0 * b * acos(c);
+        }
+        sum += w * oracle_sheen_D(cos(th), alpha) * sin(th) * inner;
+    }
+    return sum;
+}
+
+/* the sheen lobe for wo, wi above the surface, given A at both cosines */
+static double sheen_f(v3 wo, v3 wi, double alpha, double a_o, double a_i) {
+    v3 h = normalize(add(wo, wi));
+    return oracle_sheen_D(h.z, alpha) / (4.0 * (a_i * wo.z + a_o * wi.z - wi.z * wo.z));
+}
+
+double oracle_sheen_f(const double wo[3], const double wi[3], double alpha) {
+    if (wo[2] <= 0.0 || wi[2] <= 0.0) return 0.0;
+    return sheen_f(mk(wo[0], wo[1], wo[2]), mk(wi[0], wi[1], wi[2]), alpha, oracle_sheen_area(wo[2], alpha),
+                   oracle_sheen_area(wi[2], alpha));
+}
+
+/* A at the nodes of the mu_i rule depends on alpha only: kept per thread for the last alpha */
+static _Thread_local double memo_alpha = -1.0;
+static _Thread_local double memo_area[GL_N];
+
+/* E(mu_o): wo = (sin, 0, mu_o); the integrand is even in the azimuth of wi, so
+ * E = 2 int_0^1 dmu_i int_0^pi dphi f_s mu_i */
+double oracle_sheen_albedo(double mu_o, double alpha) {
+    mu_o = fmin(fmax(mu_o, 0.0), 1.0);
+    const v3 wo = mk(sqrt(fmax(0.0, 1.0 - mu_o * mu_o)), 0.0, mu_o);
+    const double a_o = oracle_sheen_area(mu_o, alpha);
+    if (memo_alpha != alpha) {
+        for (int i = 0; i < GL_N; ++i) {
+            double mi, wm;
+            gl_node(0.0, 1.0, i, &mi, &wm);
+            memo_area[i] = oracle_sheen_area(mi, alpha);
+        }
+        memo_alpha = alpha;
+    }
+    double sum = 0.0;
+    for (int i = 0; i < GL_N; ++i) {
+        double mi, wm;
+        gl_node(0.0, 1.0, i, &mi, &wm);
+        const double a_i = memo_area[i], si = sqrt(fmax(0.0, 1.0 - mi * mi));
+        for (int j = 0; j < GL_N; ++j) {
+            double ph, wp;
+            gl_node(0.0, M_PI, j, &ph, &wp);
+            const v3 wi = mk(si * cos(ph), si * sin(ph), mi);
+            sum += wm * wp * sheen_f(wo, wi, alpha, a_o, a_i) * mi;
+        }
+    }
+    return 2.0 * sum;
+}
+
 static v3 reflect(v3 wo, v3 h) { return sub(scl(h, 2.0 * dot(wo, h)), wo); }
 /* refraction of wo (on the +h side) into the medium with relative index eta; 0 on TIR */
 static int refract(v3 wo, v3 h, double eta, v3* wi) {
@@ -248,13 +381,21 @@ static int refract(v3 wo, v3 h, double eta, v3* wi) {
 /* tangent and ay = (1-a) ax along the bitangent, in the frame of tangent_frame (the coat  */
 /* stays isotropic).                                                                      */
 /* ------------------------------------------------------------------------------------ */
-enum { LOBE_COAT = 0, LOBE_METAL = 1, LOBE_DIEL = 2, LOBE_DIFF = 3, N_LOBES = 4 };
+/* Fuzz (OpenPBR's fuzz layer over the coat; reading): with fuzz weight fw, colour fc,    */
+/*   f = fw fc f_s + A_f (cw f_coat + A_c (...)),                                           */
+/*   A_f(mu_i, mu_o) = (1 - fw) + fw (1 - E(|mu_i|)) (1 - E(mu_o)),                         */
+/* E the sheen lobe's albedo (the light that the fibres do not send back passes them, on   */
+/* the way in and on the way out; symmetric like the coat's factor).  The fuzz lobe is     */
+/* sampled uniformly over the upper hemisphere (z = u1, phi = 2 pi u2), picked with weight */
+/* fw lum(fc) E(mu_o); the other lobes' weights are scaled by 1 - fw E(mu_o).              */
+enum { LOBE_COAT = 0, LOBE_METAL = 1, LOBE_DIEL = 2, LOBE_DIFF = 3, LOBE_FUZZ = 4, N_LOBES = 5 };
 
 typedef struct {
     omat m;
     double eta_s, eta_c;
     double ax_s, ay_s, a_c;   /* specular widths along tangent / bitangent; coat (isotropic) */
     int delta_s, delta_c;
+    double alpha_f, a_fo, e_fo;   /* fuzz: Charlie width, A(mu_o), E(mu_o) */
     double p[N_LOBES];     /* lobe selection probabilities */
     int any;               /* some lobe has positive weight */
     int has_smooth;        /* some non-delta lobe has positive weight */
@@ -285,13 +426,29 @@ static void closure_setup(closure* C, const omat* m, int front, double mu_o) {
                      (1.0 - m->spec_weight * fs);
     double w_diff = att * (1.0 - m->metalness) * (1.0 - m->trans_weight) *
                     (1.0 - m->spec_weight * fs) * lum(f0);
-    double w[N_LOBES] = {w_coat, w_metal, w_spec + w_trans, w_diff};
-    double sum = w[0] + w[1] + w[2] + w[3];
+    double w[N_LOBES] = {w_coat, w_metal, w_spec + w_trans, w_diff, 0.0};
+    C->alpha_f = fuzz_alpha(m->fuzz_rough);
+    C->a_fo = C->e_fo = 0.0;
+    if (m->fuzz_weight > 0.0) {
+        C->a_fo = oracle_sheen_area(mu_o, C->alpha_f);
+        C->e_fo = oracle_sheen_albedo(mu_o, C->alpha_f);
+        for (int j = 0; j < LOBE_FUZZ; ++j) w[j] *= 1.0 - m->fuzz_weight * C->e_fo;
+        w[LOBE_FUZZ] = m->fuzz_weight * lum(m->fuzz_color) * C->e_fo;
+    }
+    double sum = w[0] + w[1] + w[2] + w[3] + w[4];
     C->any = sum > 0.0;
     for (int j = 0; j < N_LOBES; ++j) C->p[j] = C->any ? w[j] / sum : 0.0;
     C->has_smooth = (C->p[LOBE_COAT] > 0.0 && !C->delta_c) ||
                     ((C->p[LOBE_METAL] > 0.0 || C->p[LOBE_DIEL] > 0.0) && !C->delta_s) ||
-                    C->p[LOBE_DIFF] > 0.0;
+                    C->p[LOBE_DIFF] > 0.0 || C->p[LOBE_FUZZ] > 0.0;
+}
+
+/* A_f: how much of the layers under the fuzz reaches wo from wi (1 without fuzz) */
+static double fuzz_attenuation(const closure* C, double mu_i_abs) {
+    const omat* m = &C->m;
+    if (!(m->fuzz_weight > 0.0)) return 1.0;
+    double e_i = oracle_sheen_albedo(mu_i_abs, C->alpha_f);
+    return (1.0 - m->fuzz_weight) + m->fuzz_weight * (1.0 - e_i) * (1.0 - C->e_fo);
 }
 
 /* probability of reflecting (vs refracting) in the dielectric lobe, given F(wo.h) */
@@ -397,6 +554,14 @@ static void closure_eval(const closure* C, v3 wo, v3 wi, v3* f_out, double* pdf_
             }
         }
     }
+    if (m->fuzz_weight > 0.0) {
+        f = scl(f, fuzz_attenuation(C, fabs(mi)));
+        if (mi > 0.0) {
+            double fs = sheen_f(wo, wi, C->alpha_f, C->a_fo, oracle_sheen_area(mi, C->alpha_f));
+            f = add(f, scl(m->fuzz_color, m->fuzz_weight * fs));
+            pdf += C->p[LOBE_FUZZ] / (2.0 * M_PI);
+        }
+    }
     *f_out = f;
     *pdf_out = pdf;
 }
@@ -430,8 +595,8 @@ static int closure_sample(const closure* C, v3 wo, double u_lobe, double u1, dou
     if (lobe == LOBE_COAT) {
         if (C->delta_c) {
             out->wi = mk(-wo.x, -wo.y, wo.z);
-            out->weight = splat(m->coat_weight * oracle_fresnel_dielectric(mo, C->eta_c) /
-                                C->p[LOBE_COAT]);
+            out->weight = splat(m->coat_weight * oracle_fresnel_dielectric(mo, C->eta_c) *
+                                fuzz_attenuation(C, mo) / C->p[LOBE_COAT]);
             out->is_delta = 1;
             return 1;
         }
@@ -443,7 +608,7 @@ static int closure_sample(const closure* C, v3 wo, double u_lobe, double u1, dou
             out->wi = mk(-wo.x, -wo.y, wo.z);
             v3 fm = fresnel_f82(scl(m->base_color, m->base_weight), m->spec_color, mo);
             out->weight = scl(hmul(coat_attenuation(C, mo, mo), fm),
-                              m->metalness * m->spec_weight / C->p[LOBE_METAL]);
+                              m->metalness * m->spec_weight * fuzz_attenuation(C, mo) / C->p[LOBE_METAL]);
             out->is_delta = 1;
             return 1;
         }
@@ -474,20 +639,25 @@ static int closure_sample(const closure* C, v3 wo, double u_lobe, double u1, dou
             out->is_delta = 1;
             if (do_reflect) {
                 out->weight = scl(hmul(coat_attenuation(C, mo, mo), m->spec_color),
-                                  (1.0 - m->metalness) * m->spec_weight * fr /
+                                  (1.0 - m->metalness) * m->spec_weight * fr * fuzz_attenuation(C, mo) /
                                       (C->p[LOBE_DIEL] * pr));
             } else {
                 double scale = m->thin_walled ? 1.0 : C->eta_s * C->eta_s;   /* radiance across the interface */
                 out->weight = scl(hmul(coat_attenuation(C, fabs(wi.z), mo), m->trans_color),
                                   (1.0 - m->metalness) * m->trans_weight *
-                                      (1.0 - m->spec_weight * fr) /
+                                      (1.0 - m->spec_weight * fr) * fuzz_attenuation(C, fabs(wi.z)) /
                                       (scale * C->p[LOBE_DIEL] * (1.0 - pr)));
             }
             return 1;
         }
-    } else {
+    } else if (lobe == LOBE_DIFF) {
         double r = sqrt(u1), phi = 2.0 * M_PI * u2;
         wi = mk(r * cos(phi), r * sin(phi), sqrt(fmax(0.0, 1.0 - u1)));
+        if (wi.z <= 0.0) return 0;
+    } else {
+        /* fuzz: uniform over the upper hemisphere */
+        double r = sqrt(fmax(0.0, 1.0 - u1 * u1)), phi = 2.0 * M_PI * u2;
+        wi = mk(r * cos(phi), r * sin(phi), u1);
         if (wi.z <= 0.0) return 0;
     }
     v3 f;
@@ -526,7 +696,7 @@ int oracle_bsdf_sample(const double* matp, int front, const double wo[3], const 
     return 1;
 }
 
-void oracle_lobe_probs(const double* matp, int front, double mu_o, double out[4]) {
+void oracle_lobe_probs(const double* matp, int front, double mu_o, double out[5]) {
     omat m = unpack_material(matp);
     closure C;
     closure_setup(&C, &m, front, mu_o);
@@ -1790,23 +1960,63 @@ void oracle_features(void* hs, const double* cam9, double vfov_deg, int width, i
 }
 
 /* ---- batched forms of the BSDF entry points (n tuples, row-major arrays) ---- */
+/* the batch entry points split their rows over the host's cores (rows are independent) */
+typedef struct {
+    const double *matp, *wo, *wi, *u;
+    int front, n, tid, nthreads;
+    double *f_out, *pdf_out, *wi_out, *weight_out;
+    int *delta_out, *ok_out;
+} bsdf_batch_job;
+
+static void* bsdf_eval_rows(void* arg) {
+    bsdf_batch_job* J = (bsdf_batch_job*)arg;
+    for (int i = J->tid; i < J->n; i += J->nthreads)
+        oracle_bsdf_eval(J->matp, J->front, &J->wo[3 * i], &J->wi[3 * i], &J->f_out[3 * i], &J->pdf_out[i]);
+    return NULL;
+}
+
+static void* bsdf_sample_rows(void* arg) {
+    bsdf_batch_job* J = (bsdf_batch_job*)arg;
+    for (int i = J->tid; i < J->n; i += J->nthreads) {
+        J->ok_out[i] = oracle_bsdf_sample(J->matp, J->front, &J->wo[3 * i], &J->u[4 * i], &J->wi_out[3 * i],
+                                          &J->weight_out[3 * i], &J->pdf_out[i], &J->delta_out[i]);
+        if (!J->ok_out[i]) {
+            J->wi_out[3 * i] = J->wi_out[3 * i + 1] = J->wi_out[3 * i + 2] = 0.0;
+            J->weight_out[3 * i] = J->weight_out[3 * i + 1] = J->weight_out[3 * i + 2] = 0.0;
+        }
+    }
+    return NULL;
+}
+
+static void run_bsdf_batch(void* (*fn)(void*), bsdf_batch_job proto) {
+    long cores = sysconf(_SC_NPROCESSORS_ONLN);
+    int nt = proto.n >= 256 && cores > 1 ? (int)(cores < 64 ? cores : 64) : 1;
+    bsdf_batch_job* jobs = (bsdf_batch_job*)calloc((size_t)nt, sizeof(bsdf_batch_job));
+    for (int t = 0; t < nt; ++t) {
+        jobs[t] = proto;
+        jobs[t].tid = t;
+        jobs[t].nthreads = nt;
+    }
+    run_threads(fn, jobs, sizeof(bsdf_batch_job), nt);
+    free(jobs);
+}
+
 void oracle_bsdf_eval_batch(const double* matp, int front, int n, const double* wo,
                             const double* wi, double* f_out, double* pdf_out) {
-    for (int i = 0; i < n; ++i)
-        oracle_bsdf_eval(matp, front, &wo[3 * i], &wi[3 * i], &f_out[3 * i], &pdf_out[i]);
+    bsdf_batch_job J;
+    memset(&J, 0, sizeof(J));
+    J.matp = matp; J.front = front; J.n = n; J.wo = wo; J.wi = wi; J.f_out = f_out; J.pdf_out = pdf_out;
+    run_bsdf_batch(bsdf_eval_rows, J);
 }
 
 void oracle_bsdf_sample_batch(const double* matp, int front, int n, const double* wo,
                               const double* u, double* wi_out, double* weight_out,
                               double* pdf_out, int* delta_out, int* ok_out) {
-    for (int i = 0; i < n; ++i) {
-        ok_out[i] = oracle_bsdf_sample(matp, front, &wo[3 * i], &u[4 * i], &wi_out[3 * i],
-                                       &weight_out[3 * i], &pdf_out[i], &delta_out[i]);
-        if (!ok_out[i]) {
-            wi_out[3 * i] = wi_out[3 * i + 1] = wi_out[3 * i + 2] = 0.0;
-            weight_out[3 * i] = weight_out[3 * i + 1] = weight_out[3 * i + 2] = 0.0;
-        }
-    }
+    bsdf_batch_job J;
+    memset(&J, 0, sizeof(J));
+    J.matp = matp; J.front = front; J.n = n; J.wo = wo; J.u = u; J.wi_out = wi_out; J.weight_out = weight_out;
+    J.pdf_out = pdf_out; J.delta_out = delta_out; J.ok_out = ok_out;
+    run_bsdf_batch(bsdf_sample_rows, J);
 }
 
 void oracle_uniform_batch(int n, const uint32_t* pixel, const uint32_t* sample,

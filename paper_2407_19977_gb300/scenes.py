@@ -18,7 +18,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # OpenPBR parameter layout shared by the C-ABI (`pt_openpbr`) and the oracle:
-# 29 float32 values per material, in this order.
+# 34 float32 values per material, in this order.
 MATERIAL_FIELDS = (
     "base_weight", "base_color_r", "base_color_g", "base_color_b",
     "base_metalness", "base_diffuse_roughness",
@@ -29,8 +29,9 @@ MATERIAL_FIELDS = (
     "coat_roughness", "coat_ior",
     "emission_luminance", "emission_color_r", "emission_color_g", "emission_color_b",
     "geometry_thin_walled", "specular_roughness_anisotropy", "specular_rotation",
+    "fuzz_weight", "fuzz_color_r", "fuzz_color_g", "fuzz_color_b", "fuzz_roughness",
 )
-N_MATERIAL_FLOATS = len(MATERIAL_FIELDS)  # 29
+N_MATERIAL_FLOATS = len(MATERIAL_FIELDS)  # 34
 # Quad light layout: p0[3], e1[3], e2[3], radiance[3], two_sided (0/1).
 N_LIGHT_FLOATS = 13
 
@@ -41,14 +42,15 @@ def openpbr(base_weight=1.0, base_color=(0.8, 0.8, 0.8), base_metalness=0.0,
             transmission_color=(1.0, 1.0, 1.0), coat_weight=0.0, coat_color=(1.0, 1.0, 1.0),
             coat_roughness=0.0, coat_ior=1.6, emission_luminance=0.0,
             emission_color=(1.0, 1.0, 1.0), geometry_thin_walled=0.0,
-            specular_roughness_anisotropy=0.0, specular_rotation=0.0) -> np.ndarray:
+            specular_roughness_anisotropy=0.0, specular_rotation=0.0, fuzz_weight=0.0,
+            fuzz_color=(1.0, 1.0, 1.0), fuzz_roughness=0.5) -> np.ndarray:
     """One OpenPBR parameter row (defaults follow the OpenPBR surface defaults, Sec. 4)."""
     v = [base_weight, *base_color, base_metalness, base_diffuse_roughness,
          specular_weight, *specular_color, specular_roughness, specular_ior,
          transmission_weight, *transmission_color,
          coat_weight, *coat_color, coat_roughness, coat_ior,
          emission_luminance, *emission_color, geometry_thin_walled,
-         specular_roughness_anisotropy, specular_rotation]
+         specular_roughness_anisotropy, specular_rotation, fuzz_weight, *fuzz_color, fuzz_roughness]
     assert len(v) == N_MATERIAL_FLOATS
     return np.asarray(v, dtype=np.float32)
 
@@ -80,7 +82,7 @@ class Scene:
     vertices: np.ndarray          # (nv, 3) float32
     indices: np.ndarray           # (nt, 3) uint32
     material_ids: np.ndarray      # (nt,) uint32
-    materials: np.ndarray         # (nm, 29) float32
+    materials: np.ndarray         # (nm, 34) float32
     lights: np.ndarray            # (nq, 13) float32
     env: np.ndarray | None        # (H, W, 3) float32, row 0 = straight up (+y)
     camera: Camera

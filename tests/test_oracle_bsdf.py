@@ -126,7 +126,14 @@ MATS = {
                                   specular_roughness_anisotropy=0.6),
     "aniso_coated": scenes.openpbr(base_color=(0.2, 0.4, 0.8), specular_roughness=0.45, coat_weight=1.0,
                                    coat_roughness=0.3, specular_roughness_anisotropy=0.5),
+    "fuzz_velvet": scenes.openpbr(base_color=(0.5, 0.1, 0.2), specular_roughness=0.5, fuzz_weight=1.0,
+                                  fuzz_color=(0.9, 0.6, 0.7), fuzz_roughness=0.4),
+    "fuzz_coated_glass": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.45, transmission_weight=0.8,
+                                        coat_weight=0.6, coat_roughness=0.3, fuzz_weight=0.5,
+                                        fuzz_color=(0.7, 0.8, 0.9), fuzz_roughness=0.8),
 }
+# fuzz materials integrate their albedo in the oracle at every evaluation: fewer samples
+FUZZ_SCALE = 10
 WHITE = {
     "white_plastic": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.3),
     "white_metal": scenes.openpbr(base_color=(1, 1, 1), base_metalness=1.0, specular_roughness=0.3),
@@ -139,6 +146,8 @@ WHITE = {
                                         specular_roughness_anisotropy=0.9),
     "white_aniso_glass": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.4, transmission_weight=1.0,
                                         specular_roughness_anisotropy=0.7),
+    "white_fuzz": scenes.openpbr(base_color=(1, 1, 1), specular_roughness=0.3, fuzz_weight=1.0,
+                                 fuzz_roughness=0.3),
 }
 
 
@@ -397,7 +406,7 @@ def test_sample_eval_consistency(name):
     mat = MATS[name]
     for front in (1, 0):
         for mu in (0.9, 0.4, 0.08):
-            n = 3000
+            n = 3000 // (FUZZ_SCALE if "fuzz" in name else 1)
             wo = np.tile(_hemi_dir(mu, 1.1), (n, 1))
             u = RNG.random((n, 4))
             ok, wi, w, pdf, dl = oracle.bsdf_sample_batch(mat, front, wo, u)
@@ -415,12 +424,12 @@ def test_pdf_integrates_to_valid_sample_fraction(name):
     for front in (1, 0):
         for mu in (0.85, 0.3):
             wo = _hemi_dir(mu, 0.7)
-            n = 200_000
+            n = 200_000 // (FUZZ_SCALE if "fuzz" in name else 1)
             dirs = _sphere_dirs(n)
             _, pdf = oracle.bsdf_eval_batch(mat, front, np.tile(wo, (n, 1)), dirs)
             vals = pdf * 4 * math.pi
             integral, err_i = vals.mean(), vals.std() / math.sqrt(n)
-            m = 100_000
+            m = 100_000 // (FUZZ_SCALE if "fuzz" in name else 1)
             ok, wi, w, p, dl = oracle.bsdf_sample_batch(mat, front, np.tile(wo, (m, 1)),
                                                         RNG.random((m, 4)))
             frac = (ok & ~dl).mean()
@@ -434,7 +443,7 @@ def test_albedo_at_most_one(name):
     mat = WHITE[name]
     for front in (1, 0):
         for mu in (0.98, 0.7, 0.4, 0.15, 0.03):
-            n = 40_000
+            n = 40_000 // (4 * FUZZ_SCALE if "fuzz" in name else 1)
             ok, wi, w, p, dl = oracle.bsdf_sample_batch(mat, front, np.tile(_hemi_dir(mu), (n, 1)),
                                                         RNG.random((n, 4)))
             if front == 0 and "glass" in name or "mixed" in name and front == 0:

@@ -49,7 +49,7 @@ typedef enum {
 typedef struct pt_scene pt_scene;   /* opaque, library-owned */
 typedef struct pt_nrc pt_nrc;       /* opaque, library-owned */
 
-/* OpenPBR surface parameters (Sec. 4; the paper's material model).  PT_OPENPBR_FLOATS (29)
+/* OpenPBR surface parameters (Sec. 4; the paper's material model).  PT_OPENPBR_FLOATS (34)
  * floats, in this order; the Python generators and the oracle use the same order.
  * Valid ranges (checked by pt_scene_create): weights, colors, roughnesses, metalness,
  * anisotropy and rotation in [0, 1]; specular_ior and coat_ior in (1, 3];
@@ -87,8 +87,17 @@ typedef struct {
                                    tangents the tangent is the triangle's first edge
                                    (v1 - v0) projected into the surface plane */
     float specular_rotation;    /* turns of the tangent about the normal (0..1) */
+    float fuzz_weight;          /* fw: a layer of fibres over the coat.  Its lobe is the
+                                   Charlie sheen distribution (Estevez & Kulla 2017)
+                                   D = (2 + 1/a) sin(theta_h)^(1/a) / (2 pi) with its exact
+                                   Smith masking (projected area A(mu) by quadrature),
+                                   a = max(fuzz_roughness, 0.2)^2; the layers below are
+                                   scaled by (1 - fw) + fw (1 - E(|cos_i|)) (1 - E(cos_o)),
+                                   E the lobe's directional albedo */
+    float fuzz_color[3];
+    float fuzz_roughness;
 } pt_openpbr;
-enum { PT_OPENPBR_FLOATS = 29 };
+enum { PT_OPENPBR_FLOATS = 34 };
 
 /* Parallelogram area light p0 + a e1 + b e2, (a, b) in [0,1]^2, radiance L emitted on the
  * side of e1 x e2 (both sides if two_sided).  The library also makes it geometry: two

@@ -94,6 +94,8 @@ __device__ __forceinline__ DMat pack_material(const float* v) {
     m.thin_walled = v[26];
     m.spec_aniso = v[27];
     m.spec_rot = v[28];
+    m.fuzz_weight = v[29];
+    m.pad0 = m.pad1 = m.pad2 = 0.0f;
     m.spec_weight = v[6];
     m.spec_color = mk3(v[7], v[8], v[9]);
     m.spec_rough = v[10];
@@ -136,7 +138,8 @@ static bool material_ok(const pt_openpbr& m, std::string& why) {
         if (!std::isfinite(v[i])) { why = "non-finite material parameter"; return false; }
     if (v[26] != 0.0f && v[26] != 1.0f) { why = "geometry_thin_walled must be 0 or 1"; return false; }
     auto unit = [](float x) { return x >= 0.0f && x <= 1.0f; };
-    const int unit_idx[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17, 18, 19, 20, 23, 24, 25, 27, 28};
+    const int unit_idx[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 13, 14, 15, 16, 17, 18, 19, 20, 23, 24, 25, 27, 28,
+                             29, 30, 31, 32, 33};
     for (int i : unit_idx)
         if (!unit(v[i])) { why = "material parameter " + std::to_string(i) + " outside [0,1]"; return false; }
     if (!(v[11] > 1.0f && v[11] <= 3.0f)) { why = "specular_ior outside (1,3]"; return false; }
@@ -148,7 +151,7 @@ static bool material_ok(const pt_openpbr& m, std::string& why) {
 static void free_scene(pt_scene* s) {
     if (!s) return;
     void* ptrs[] = {s->d_vertices, s->d_indices, s->d_matids, s->d_tris_raw, s->d_tris, s->d_nodes,
-                    s->d_mats, s->d_quads, s->d_quads_raw, s->d_env, s->d_env_marg, s->d_env_cond,
+                    s->d_mats, s->d_fuzz, s->d_quads, s->d_quads_raw, s->d_env, s->d_env_marg, s->d_env_cond,
                     s->d_env_wtex, s->d_env_total, s->d_err, s->d_stats, s->d_head};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -206,6 +209,7 @@ extern "C" pt_status pt_scene_create(const float* vertices, uint32_t n_vertices,
     s->n_quads = n_lights;
     s->n_tris = n_triangles + 2 * n_lights;
     s->n_mats = n_materials;
+    for (uint32_t i = 0; i < n_materials; ++i) s->has_fuzz |= materials[i].fuzz_weight > 0.0f;
     s->last_stream = st;
     const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     auto fail = [&](pt_status code) { free_scene(s); return code; };
@@ -224,6 +228,7 @@ extern "C" pt_status pt_scene_create(const float* vertices, uint32_t n_vertices,
     TRY(cudaMalloc(&s->d_matids, (nt3 / 3) * sizeof(uint32_t)));
     TRY(cudaMalloc(&s->d_tris_raw, (size_t)s->n_tris * 3 * sizeof(float4)));
     TRY(cudaMalloc(&s->d_mats, std::max<uint32_t>(n_materials, 1) * sizeof(DMat)));
+    TRY(cudaMalloc(&s->d_fuzz, (size_t)std::max<uint32_t>(n_materials, 1) * FUZZ_FLOATS * sizeof(float)));
     TRY(cudaMalloc(&s->d_quads, std::max<uint32_t>(n_lights, 1) * sizeof(DQuad)));
     TRY(cudaMalloc(&s->d_quads_raw, std::max<uint32_t>(n_lights, 1) * 13 * sizeof(float)));
     TRY(cudaMalloc(&s->d_err, 16 * sizeof(uint32_t)));
@@ -260,6 +265,10 @@ extern "C" pt_status pt_scene_create(const float* vertices, uint32_t n_vertices,
                   n_triangles, s->d_matids, n_materials, d_scratch + 8);
     }
     if (n_materials) PT_LAUNCH(k_pack_mats, (n_materials + 127) / 128, 128, 0, st, d_mat_raw, n_materials, s->d_mats);
+    {
+        pt_status fr = pt_fuzz_series(d_mat_raw, n_materials, s->d_fuzz, st);
+        if (fr != PT_OK) return fail(fr);
+    }
     if (n_lights) PT_LAUNCH(k_prepare_quads, (n_lights + 127) / 128, 128, 0, st, s->d_quads_raw, n_lights, s->d_quads);
     // bounds accumulate in ordered-int form: mins start at max, maxs at 0
     std::vector<uint32_t> binit = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
@@ -438,15 +447,15 @@ extern "C" pt_status pt_trace(pt_scene* s, const float* rays, uint32_t n, int fl
     return PT_OK;
 }
 
-__global__ void k_bsdf_eval(const float* mats, const int32_t* front, const float* wo, const float* wi,
-                            uint32_t n, float* f_out, float* pdf_out) {
+__global__ void k_bsdf_eval(const float* mats, const float* fuzz, const int32_t* front, const float* wo,
+                            const float* wi, uint32_t n, float* f_out, float* pdf_out) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const DMat M = pack_material(mats + (uint32_t)PT_OPENPBR_FLOATS * i);
     const float3 o = mk3(wo[3 * i], wo[3 * i + 1], wo[3 * i + 2]);
     const float3 w = mk3(wi[3 * i], wi[3 * i + 1], wi[3 * i + 2]);
     Closure C;
-    closure_setup(C, M, front[i] != 0, o.z);
+    closure_setup(C, M, front[i] != 0, o.z, fuzz + (size_t)FUZZ_FLOATS * i);
     float3 f;
     float pdf;
     closure_eval(C, o, w, f, pdf);
@@ -456,14 +465,15 @@ __global__ void k_bsdf_eval(const float* mats, const int32_t* front, const float
     pdf_out[i] = pdf;
 }
 
-__global__ void k_bsdf_sample(const float* mats, const int32_t* front, const float* wo, const float* u,
-                              uint32_t n, float* wi_out, float* w_out, float* pdf_out, uint32_t* flags) {
+__global__ void k_bsdf_sample(const float* mats, const float* fuzz, const int32_t* front, const float* wo,
+                              const float* u, uint32_t n, float* wi_out, float* w_out, float* pdf_out,
+                              uint32_t* flags) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const DMat M = pack_material(mats + (uint32_t)PT_OPENPBR_FLOATS * i);
     const float3 o = mk3(wo[3 * i], wo[3 * i + 1], wo[3 * i + 2]);
     Closure C;
-    closure_setup(C, M, front[i] != 0, o.z);
+    closure_setup(C, M, front[i] != 0, o.z, fuzz + (size_t)FUZZ_FLOATS * i);
     BsdfSample bs;
     const bool ok = closure_sample(C, o, u[4 * i], u[4 * i + 1], u[4 * i + 2], u[4 * i + 3], bs);
     if (!ok) {
@@ -482,10 +492,21 @@ extern "C" pt_status pt_bsdf_eval(const pt_openpbr* materials, const int32_t* fr
                                   const float* wi, uint32_t n, float* f_out, float* pdf_out, void* cuda_stream) {
     PT_CHECK_ARG(materials && front && wo && wi && f_out && pdf_out, "NULL argument");
     if (n == 0) return PT_OK;
-    PT_LAUNCH(k_bsdf_eval, (n + 127) / 128, 128, 0, (cudaStream_t)cuda_stream,
-              reinterpret_cast<const float*>(materials), front, wo, wi, n, f_out, pdf_out);
-    PT_CUDA_TRY(cudaGetLastError());
-    return PT_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const float* raw = reinterpret_cast<const float*>(materials);
+    float* fuzz = nullptr;   // the rows' fuzz series, stream-ordered scratch
+    PT_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&fuzz), (size_t)n * FUZZ_FLOATS * sizeof(float), st));
+    pt_status r = pt_fuzz_series(raw, n, fuzz, st);
+    if (r == PT_OK) {
+        PT_LAUNCH(k_bsdf_eval, (n + 127) / 128, 128, 0, st, raw, fuzz, front, wo, wi, n, f_out, pdf_out);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            pt_set_error(std::string("k_bsdf_eval: ") + cudaGetErrorString(e));
+            r = PT_ERR_CUDA;
+        }
+    }
+    cudaFreeAsync(fuzz, st);
+    return r;
 }
 
 extern "C" pt_status pt_bsdf_sample(const pt_openpbr* materials, const int32_t* front, const float* wo,
@@ -493,10 +514,22 @@ extern "C" pt_status pt_bsdf_sample(const pt_openpbr* materials, const int32_t* 
                                     float* pdf_out, uint32_t* flags_out, void* cuda_stream) {
     PT_CHECK_ARG(materials && front && wo && u && wi_out && weight_out && pdf_out && flags_out, "NULL argument");
     if (n == 0) return PT_OK;
-    PT_LAUNCH(k_bsdf_sample, (n + 127) / 128, 128, 0, (cudaStream_t)cuda_stream,
-              reinterpret_cast<const float*>(materials), front, wo, u, n, wi_out, weight_out, pdf_out, flags_out);
-    PT_CUDA_TRY(cudaGetLastError());
-    return PT_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const float* raw = reinterpret_cast<const float*>(materials);
+    float* fuzz = nullptr;   // the rows' fuzz series, stream-ordered scratch
+    PT_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&fuzz), (size_t)n * FUZZ_FLOATS * sizeof(float), st));
+    pt_status r = pt_fuzz_series(raw, n, fuzz, st);
+    if (r == PT_OK) {
+        PT_LAUNCH(k_bsdf_sample, (n + 127) / 128, 128, 0, st, raw, fuzz, front, wo, u, n, wi_out, weight_out,
+                  pdf_out, flags_out);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            pt_set_error(std::string("k_bsdf_sample: ") + cudaGetErrorString(e));
+            r = PT_ERR_CUDA;
+        }
+    }
+    cudaFreeAsync(fuzz, st);
+    return r;
 }
 
 __global__ void k_camera_rays(DCam cam, uint64_t seed, const uint32_t* pix, uint32_t n, float* out) {

@@ -79,6 +79,7 @@ struct __align__(16) DMat {
     float spec_rough, spec_ior, coat_rough, coat_ior;
     float diffuse_rough, thin_walled;   // thin_walled: 0 or 1
     float spec_aniso, spec_rot;         // specular_roughness_anisotropy, tangent rotation (turns)
+    float fuzz_weight, pad0, pad1, pad2;   // colour and width live in the material's fuzz block
 };
 
 struct __align__(16) DQuad {
@@ -172,20 +173,60 @@ __device__ __forceinline__ bool refract3(float3 wo, float3 h, float eta, float3&
     return true;
 }
 
+// ------------------------------------------------------------------ fuzz (sheen) lobe
+// The Charlie distribution D = (2 + 1/a) sin(theta_m)^(1/a) / (2 pi) (Estevez & Kulla 2017)
+// with its exact Smith masking: G1 = mu / A(mu), A(mu) = int <w, m>+ D(m) dm its projected
+// area, so the height-correlated lobe is D(h) / (4 (A(mu_i) mu_o + A(mu_o) mu_i - mu_i mu_o)).
+// A and the lobe's directional albedo E have no closed form: per material the library keeps
+// a fuzz block of FUZZ_FLOATS floats -- fw, fc[3], a (= max(fuzz_roughness, 0.2)^2), 3 unused,
+// then A as a Chebyshev series in x = 2 mu - 1 (FUZZ_A_TERMS) and E as one in
+// x = 2 sqrt(mu) - 1 (FUZZ_E_TERMS; E behaves like mu log mu at grazing) -- computed by
+// quadrature when the material table is made (pt_fuzz.cu).  Only materials with fuzz read it.
+constexpr int FUZZ_HEAD = 8, FUZZ_A_TERMS = 16, FUZZ_E_TERMS = 32;
+constexpr int FUZZ_FLOATS = FUZZ_HEAD + FUZZ_A_TERMS + FUZZ_E_TERMS;
+
+// sum_k c[k] T_k(x) by Clenshaw's recurrence
+template <int N>
+__device__ __forceinline__ float cheb_eval(const float* __restrict__ c, float x) {
+    float b1 = 0.0f, b2 = 0.0f;
+#pragma unroll
+    for (int k = N - 1; k >= 1; --k) {
+        const float t = 2.0f * x * b1 - b2 + __ldg(c + k);
+        b2 = b1;
+        b1 = t;
+    }
+    return x * b1 - b2 + __ldg(c);
+}
+__device__ __forceinline__ float fuzz_area(const float* fz, float mu) {
+    return cheb_eval<FUZZ_A_TERMS>(fz + FUZZ_HEAD, 2.0f * fminf(fmaxf(mu, 0.0f), 1.0f) - 1.0f);
+}
+__device__ __forceinline__ float fuzz_albedo(const float* fz, float mu) {
+    return cheb_eval<FUZZ_E_TERMS>(fz + FUZZ_HEAD + FUZZ_A_TERMS, 2.0f * sqrtf(fminf(fmaxf(mu, 0.0f), 1.0f)) - 1.0f);
+}
+__device__ __forceinline__ float sheen_D(float cos_m, float alpha) {
+    const float s2 = fmaxf(0.0f, 1.0f - cos_m * cos_m);
+    return (2.0f + 1.0f / alpha) * powf(s2, 0.5f / alpha) * (0.5f * PT_INV_PI_F);
+}
+
 // ------------------------------------------------------------------ OpenPBR closure
-// f = cw f_coat + A_c (m f_metal + (1 - m) f_diel), lobes coat / metal / dielectric / diffuse,
-// picked with probability proportional to an albedo estimate at wo (one-sample MIS).
-enum { LOBE_COAT = 0, LOBE_METAL = 1, LOBE_DIEL = 2, LOBE_DIFF = 3 };
+// f = fw fc f_fuzz + A_f (cw f_coat + A_c (m f_metal + (1 - m) f_diel)), lobes coat / metal /
+// dielectric / diffuse / fuzz, picked with probability proportional to an albedo estimate at
+// wo (one-sample MIS).  A_f = (1 - fw) + fw (1 - E(|mu_i|)) (1 - E(mu_o)).
+enum { LOBE_COAT = 0, LOBE_METAL = 1, LOBE_DIEL = 2, LOBE_DIFF = 3, LOBE_FUZZ = 4, N_LOBES = 5 };
 
 struct Closure {
     float3 bc, sc, tc, cc;
     float bw, m, sw, t, cw, dr;
     float eta_s, eta_c, ax_s, ay_s, a_c;   // specular widths along tangent / bitangent; coat
     bool delta_s, delta_c, any, has_smooth, thin;
-    float p[4];
+    const float* fz;            // the material's fuzz block, nullptr without fuzz
+    float p[N_LOBES];
 };
 
-__device__ __forceinline__ void closure_setup(Closure& C, const DMat& M, bool front, float mu_o) {
+// fz: the material's fuzz block (read only when its fuzz_weight is > 0).  FUZZ = false
+// compiles the closure without the fuzz layer, for kernels that render scenes without it.
+template <bool FUZZ = true>
+__device__ __forceinline__ void closure_setup(Closure& C, const DMat& M, bool front, float mu_o, const float* fz) {
     C.bc = M.base_color; C.bw = M.base_weight; C.m = M.metalness; C.dr = M.diffuse_rough;
     C.sc = M.spec_color; C.sw = M.spec_weight;
     C.tc = M.trans_color; C.t = M.trans_weight;
@@ -211,14 +252,29 @@ __device__ __forceinline__ void closure_setup(Closure& C, const DMat& M, bool fr
     const float fs = fresnel_dielectric(mu_o, C.eta_s);
     const float w_spec = att * (1.0f - C.m) * C.sw * lum3(C.sc) * fs;
     const float w_trans = att * (1.0f - C.m) * C.t * lum3(C.tc) * (1.0f - C.sw * fs);
-    const float w_diff = att * (1.0f - C.m) * (1.0f - C.t) * (1.0f - C.sw * fs) * lum3(f0);
-    const float w2 = w_spec + w_trans;
-    const float sum = w_coat + w_metal + w2 + w_diff;
+    float w_diff = att * (1.0f - C.m) * (1.0f - C.t) * (1.0f - C.sw * fs) * lum3(f0);
+    float w2 = w_spec + w_trans, wc = w_coat, wm = w_metal, w_fuzz = 0.0f;
+    C.fz = nullptr;
+    if (FUZZ && M.fuzz_weight > 0.0f) {
+        C.fz = fz;
+        const float fw = M.fuzz_weight, e_o = fuzz_albedo(fz, mu_o);
+        const float sc = 1.0f - fw * e_o;
+        wc *= sc; wm *= sc; w2 *= sc; w_diff *= sc;
+        w_fuzz = fw * lum3(mk3(__ldg(fz + 1), __ldg(fz + 2), __ldg(fz + 3))) * e_o;
+    }
+    const float sum = wc + wm + w2 + w_diff + w_fuzz;
     C.any = sum > 0.0f;
     const float inv = C.any ? 1.0f / sum : 0.0f;
-    C.p[0] = w_coat * inv; C.p[1] = w_metal * inv; C.p[2] = w2 * inv; C.p[3] = w_diff * inv;
+    C.p[0] = wc * inv; C.p[1] = wm * inv; C.p[2] = w2 * inv; C.p[3] = w_diff * inv; C.p[4] = FUZZ ? w_fuzz * inv : 0.0f;
     C.has_smooth = (C.p[0] > 0.0f && !C.delta_c) || ((C.p[1] > 0.0f || C.p[2] > 0.0f) && !C.delta_s) ||
-                   C.p[3] > 0.0f;
+                   C.p[3] > 0.0f || C.p[4] > 0.0f;
+}
+
+// A_f: the part of the layers under the fuzz that reaches wo from wi (1 without fuzz)
+__device__ __forceinline__ float fuzz_attenuation(const Closure& C, float mi_abs, float mo) {
+    if (C.fz == nullptr) return 1.0f;
+    const float fw = __ldg(C.fz);
+    return (1.0f - fw) + fw * (1.0f - fuzz_albedo(C.fz, mi_abs)) * (1.0f - fuzz_albedo(C.fz, mo));
 }
 
 __device__ __forceinline__ float diel_reflect_prob(const Closure& C, float F) {
@@ -308,6 +364,17 @@ __device__ __forceinline__ void closure_eval(const Closure& C, float3 wo, float3
                    fabsf(ih) / (denom * denom);
         }
     }
+    if (C.fz != nullptr) {
+        f = f * fuzz_attenuation(C, fabsf(mi), mo);
+        if (mi > 0.0f) {
+            const float* fz = C.fz;
+            const float3 h = norm3(wo + wi);
+            const float den = 4.0f * (fuzz_area(fz, mi) * mo + fuzz_area(fz, mo) * mi - mi * mo);
+            const float3 fc = mk3(__ldg(fz + 1), __ldg(fz + 2), __ldg(fz + 3));
+            f = f + fc * (__ldg(fz) * sheen_D(h.z, __ldg(fz + 4)) / den);
+            pdf += C.p[LOBE_FUZZ] * (0.5f * PT_INV_PI_F);
+        }
+    }
     f_out = f;
     pdf_out = pdf;
 }
@@ -325,7 +392,7 @@ __device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, floa
     int lobe = -1, last = -1;
     float c = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < N_LOBES; ++j) {
         if (C.p[j] > 0.0f && lobe < 0) {
             last = j;
             c += C.p[j];
@@ -340,7 +407,7 @@ __device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, floa
     if (lobe == LOBE_COAT) {
         if (C.delta_c) {
             out.wi = mk3(-wo.x, -wo.y, wo.z);
-            out.weight = splat3(C.cw * fresnel_dielectric(mo, C.eta_c) / C.p[0]);
+            out.weight = splat3(C.cw * fresnel_dielectric(mo, C.eta_c) * fuzz_attenuation(C, mo, mo) / C.p[0]);
             out.delta = true;
             return true;
         }
@@ -350,7 +417,7 @@ __device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, floa
         if (C.delta_s) {
             out.wi = mk3(-wo.x, -wo.y, wo.z);
             const float3 fm = fresnel_f82(C.bc * C.bw, C.sc, mo);
-            out.weight = (coat_attenuation(C, mo, mo) * fm) * (C.m * C.sw / C.p[1]);
+            out.weight = (coat_attenuation(C, mo, mo) * fm) * (C.m * C.sw * fuzz_attenuation(C, mo, mo) / C.p[1]);
             out.delta = true;
             return true;
         }
@@ -379,19 +446,28 @@ __device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, floa
             out.wi = wi;
             out.delta = true;
             if (do_reflect) {
-                out.weight = (coat_attenuation(C, mo, mo) * C.sc) * ((1.0f - C.m) * C.sw * fr / (C.p[2] * pr));
+                out.weight = (coat_attenuation(C, mo, mo) * C.sc) *
+                             ((1.0f - C.m) * C.sw * fr * fuzz_attenuation(C, mo, mo) / (C.p[2] * pr));
             } else {
                 const float scale = C.thin ? 1.0f : C.eta_s * C.eta_s;   // radiance across the interface
                 out.weight = (coat_attenuation(C, fabsf(wi.z), mo) * C.tc) *
-                             ((1.0f - C.m) * C.t * (1.0f - C.sw * fr) / (scale * C.p[2] * (1.0f - pr)));
+                             ((1.0f - C.m) * C.t * (1.0f - C.sw * fr) * fuzz_attenuation(C, fabsf(wi.z), mo) /
+                              (scale * C.p[2] * (1.0f - pr)));
             }
             return true;
         }
-    } else {
+    } else if (lobe == LOBE_DIFF) {
         const float r = sqrtf(u1), phi = 2.0f * PT_PI_F * u2;
         float sp, cp;
         sincosf(phi, &sp, &cp);
         wi = mk3(r * cp, r * sp, sqrtf(fmaxf(0.0f, 1.0f - u1)));
+        if (wi.z <= 0.0f) return false;
+    } else {
+        // fuzz: uniform over the upper hemisphere
+        const float r = sqrtf(fmaxf(0.0f, 1.0f - u1 * u1)), phi = 2.0f * PT_PI_F * u2;
+        float sp, cp;
+        sincosf(phi, &sp, &cp);
+        wi = mk3(r * cp, r * sp, u1);
         if (wi.z <= 0.0f) return false;
     }
     float3 f;
@@ -445,6 +521,7 @@ struct DScene {
     const float4* tris;        // leaf order
     const uint4* nodes;        // compressed 8-wide BVH, 5 x uint4 per node
     const DMat* mats;
+    const float* fuzz;         // FUZZ_FLOATS per material: the fuzz lobe's series
     const DQuad* quads;
     const float* env;          // env_h * env_w * 3
     const float* env_marg;     // env_h + 1
@@ -1094,13 +1171,14 @@ __device__ __forceinline__ void rsurf_make(const DScene& S, float3 x, float3 wo_
     const float4 ta = __ldg(S.tris + 3u * tri), tb = __ldg(S.tris + 3u * tri + 1), tc = __ldg(S.tris + 3u * tri + 2);
     const float3 ng = norm3(cross3(xyz(tb) - xyz(ta), xyz(tc) - xyz(ta)));
     const bool front = dot3(wo_w, ng) > 0.0f;
-    const DMat M = S.mats[__float_as_uint(tb.w)];
+    const uint32_t mid = __float_as_uint(tb.w);
+    const DMat M = S.mats[mid];
     g.x = x;
     g.n = front ? ng : -ng;
     if (M.spec_aniso > 0.0f) tangent_frame(g.n, xyz(tb) - xyz(ta), M.spec_rot, g.tt, g.bb);
     else onb(g.n, g.tt, g.bb);
     g.wo = mk3(dot3(wo_w, g.tt), dot3(wo_w, g.bb), dot3(wo_w, g.n));
-    closure_setup(g.C, M, front, g.wo.z);
+    closure_setup(g.C, M, front, g.wo.z, S.fuzz + FUZZ_FLOATS * mid);
 }
 
 enum ShadeResult { SHADE_END = 0, SHADE_CONTINUE = 1 };
@@ -1127,7 +1205,7 @@ struct NoHook {
 // may end the path there (the radiance cache does).
 // RIS: the ReSTIR DI branches (vertex 0 from its reservoir, later vertices by resampled
 // candidates, zero-weighted light hits) are compiled in only where a ReSTIR render runs.
-template <class Hook, bool RIS = false>
+template <class Hook, bool RIS = false, bool FUZZ = true>
 __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, float3 o, float3 d, uint32_t k,
                                               uint32_t max_depth, uint32_t flags, const VertexRng& rng,
                                               PathState& ps, ShadeOut& out, Hook& hook,
@@ -1182,7 +1260,7 @@ __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, 
     const float3 wo = mk3(dot3(wo_w, tt), dot3(wo_w, bb), dot3(wo_w, n));
     if (hook(x, wo_w, n, M, ps, k)) return SHADE_END;
     Closure C;
-    closure_setup(C, M, front, wo.z);
+    closure_setup<FUZZ>(C, M, front, wo.z, S.fuzz + FUZZ_FLOATS * code);
 
     const uint4 r0 = rng.block(0), r1 = rng.block(1), r2 = rng.block(2);
     if (RIS && (flags & FLAG_RESTIR) && k == 0) {
@@ -1306,13 +1384,13 @@ __device__ __forceinline__ int shade_vertex_h(const DScene& S, const HitRec& h, 
     return SHADE_CONTINUE;
 }
 
-template <bool RIS = false>
+template <bool RIS = false, bool FUZZ = true>
 __device__ __forceinline__ int shade_vertex(const DScene& S, const HitRec& h, float3 o, float3 d, uint32_t k,
                                             uint32_t max_depth, uint32_t flags, const VertexRng& rng,
                                             PathState& ps, ShadeOut& out, const float4* rres = nullptr,
                                             uint32_t later_m = 0) {
     NoHook nh;
-    return shade_vertex_h<NoHook, RIS>(S, h, o, d, k, max_depth, flags, rng, ps, out, nh, rres, later_m);
+    return shade_vertex_h<NoHook, RIS, FUZZ>(S, h, o, d, k, max_depth, flags, rng, ps, out, nh, rres, later_m);
 }
 
 // "diffuse-ish" measure of a vertex: diffuse lobes count as roughness 1

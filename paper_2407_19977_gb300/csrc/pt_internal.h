@@ -94,6 +94,8 @@ struct pt_scene {
     uint4* d_nodes = nullptr;
     uint32_t n_nodes = 0, depth = 0;
     DMat* d_mats = nullptr;
+    float* d_fuzz = nullptr;         // FUZZ_FLOATS per material: the fuzz lobe's series
+    bool has_fuzz = false;           // some material has fuzz_weight > 0
     DQuad* d_quads = nullptr;
     float* d_quads_raw = nullptr;
     float* d_env = nullptr;
@@ -130,6 +132,7 @@ struct pt_scene {
         s.tris = d_tris;
         s.nodes = d_nodes;
         s.mats = d_mats;
+        s.fuzz = d_fuzz;
         s.quads = d_quads;
         s.env = d_env;
         s.env_marg = d_env_marg;
@@ -163,6 +166,9 @@ pt_status pt_nrc_render_infer_dev(pt_nrc* N, const float* queries, const uint32_
                                   cudaStream_t st);
 uint32_t pt_nrc_frame_samples(const pt_nrc* N);
 pt_status pt_nrc_render_prepare(pt_nrc* N, uint32_t infer_cap, uint32_t train_cap);
+// Series of the fuzz lobe (FUZZ_FLOATS per row) for n raw material rows of PT_OPENPBR_FLOATS
+// floats on the device; rows without fuzz get zeros (pt_fuzz.cu).
+pt_status pt_fuzz_series(const float* raw_materials, uint32_t n, float* out, cudaStream_t st);
 pt_status pt_nrc_render_train_dev(pt_nrc* N, const float* samples, const uint32_t* n_dev, uint32_t cap, cudaStream_t st);
 
 // the lens of a camera: radius finite and >= 0; an open lens needs a finite focus distance > 0

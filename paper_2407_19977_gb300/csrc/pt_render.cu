@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(128, 6) k_restir_spatial(WfParams P, uint32_t 
     }
 }
 
-template <bool NRC, bool RIS>
+template <bool NRC, bool RIS, bool FUZZ = true>
 __global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
     if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[in_q];
@@ -764,8 +764,8 @@ __global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int o
                 P.aux[id] = hook.aux;
             } else {
                 const float4* rres = (P.restir_on && k == 0) ? P.rs_f + 2u * id : nullptr;
-                r = shade_vertex<RIS>(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so, rres,
-                                      P.restir_on ? P.restir_L : 0u);
+                r = shade_vertex<RIS, FUZZ>(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so, rres,
+                                            P.restir_on ? P.restir_L : 0u);
             }
             P.radiance[id] = make_float4(ps.L.x, ps.L.y, ps.L.z, 0.0f);
             if (so.rr_end) rr_cnt++;
@@ -845,7 +845,7 @@ __global__ void __launch_bounds__(128) k_wf_shadow(WfParams P) {
 // numbers as k_wf_shade), then the shadow ray, whose contribution is added after the vertex's
 // own terms exactly as k_wf_shadow adds it.  It appends nothing, so the later per-bounce
 // launches of the wave find empty queues (and C_TAIL makes the rest of this bounce skip).
-template <bool NRC, bool COUNT, bool RIS>
+template <bool NRC, bool COUNT, bool RIS, bool FUZZ = true>
 __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32_t k0, uint32_t limit) {
     const uint32_t count = P.counters[in_q];
     if (count == 0 || count > limit) return;
@@ -885,8 +885,8 @@ __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32
             ShadeOut so;
             int r;
             if (NRC) r = shade_vertex_h(P.S, h, o, d, k, P.max_depth, P.flags, rng, ps, so, hook);
-            else r = shade_vertex<RIS>(P.S, h, o, d, k, P.max_depth, P.flags, rng, ps, so, nullptr,
-                                       P.restir_on ? P.restir_L : 0u);
+            else r = shade_vertex<RIS, FUZZ>(P.S, h, o, d, k, P.max_depth, P.flags, rng, ps, so, nullptr,
+                                             P.restir_on ? P.restir_L : 0u);
             if (so.rr_end) n_rr++;
             if (so.has_shadow) {
                 n_sh++;
@@ -1210,9 +1210,13 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                             if (restir) {
                                 if (count) PT_LAUNCH((k_wf_tail<false, true, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
                                 else PT_LAUNCH((k_wf_tail<false, false, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                            } else {
+                            } else if (s->has_fuzz) {
                                 if (count) PT_LAUNCH((k_wf_tail<false, true, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
                                 else PT_LAUNCH((k_wf_tail<false, false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                            } else {
+                                // no material has fuzz: kernels compiled without the fuzz layer
+                                if (count) PT_LAUNCH((k_wf_tail<false, true, false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                                else PT_LAUNCH((k_wf_tail<false, false, false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
                             }
                         }
                         end(e);
@@ -1240,7 +1244,8 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                     e = begin(PT_K_SHADE);
                     if (P.nrc_on) PT_LAUNCH((k_wf_shade<true, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
                     else if (restir) PT_LAUNCH((k_wf_shade<false, true>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
-                    else PT_LAUNCH((k_wf_shade<false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+                    else if (s->has_fuzz) PT_LAUNCH((k_wf_shade<false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+                    else PT_LAUNCH((k_wf_shade<false, false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
                     end(e);
                     e = begin(PT_K_SHADOW);
                     if (count) PT_LAUNCH(k_wf_shadow<true>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
@@ -1653,7 +1658,8 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
                 PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
                 launches += 2;
             }
-            PT_LAUNCH((k_wf_shade<false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+            if (s->has_fuzz) PT_LAUNCH((k_wf_shade<false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+            else PT_LAUNCH((k_wf_shade<false, false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
             PT_LAUNCH(k_wf_shadow<false>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
             launches += 2;
         }

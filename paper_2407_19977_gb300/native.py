@@ -22,7 +22,7 @@ vp = C.c_void_p
 
 
 class pt_openpbr(C.Structure):
-    _fields_ = [("v", f32 * 29)]
+    _fields_ = [("v", f32 * 34)]
 
 
 class pt_quad_light(C.Structure):

@@ -32,7 +32,7 @@ def test_status_strings_and_struct_sizes():
     lib = N.load()
     for code, name in enumerate(N.STATUS):
         assert lib.pt_status_string(code).decode() == name
-    assert C.sizeof(N.pt_openpbr) == 29 * 4
+    assert C.sizeof(N.pt_openpbr) == 34 * 4
     assert C.sizeof(N.pt_quad_light) == 13 * 4
     assert C.sizeof(N.pt_camera) == 14 * 4
     assert C.sizeof(N.pt_accum) == 32
@@ -50,7 +50,8 @@ def test_host_side_validation_needs_no_gpu():
     idx = np.array([[0, 1, 2]], np.uint32)
     mid = np.zeros(1, np.uint32)
     m = (N.pt_openpbr * 1)()
-    m[0].v[:] = [1, .8, .8, .8, 0, 0, 1, 1, 1, 1, .3, 0.9, 0, 1, 1, 1, 0, 1, 1, 1, 0, 1.6, 0, 1, 1, 1, 0, 0, 0]  # ior 0.9
+    m[0].v[:] = [1, .8, .8, .8, 0, 0, 1, 1, 1, 1, .3, 0.9, 0, 1, 1, 1, 0, 1, 1, 1, 0, 1.6, 0, 1, 1, 1, 0, 0, 0,
+                 0, 1, 1, 1, .5]  # ior 0.9
     code = lib.pt_scene_create(v.ctypes.data_as(C.c_void_p), 3, idx.ctypes.data_as(C.c_void_p), 1,
                                mid.ctypes.data_as(C.c_void_p), m, 1, None, 0, None, 0, 0, 0, None, C.byref(h))
     assert code == 1 and b"specular_ior" in lib.pt_last_error()
@@ -64,12 +65,13 @@ def test_host_side_validation_needs_no_gpu():
                                mid.ctypes.data_as(C.c_void_p), m, 1, None, 0, None, 0, 0, 0, None, C.byref(h))
     assert code == 1 and b"thin_walled" in lib.pt_last_error()
     m[0].v[26] = 0.0
-    for i, bad in ((27, 1.5), (28, -0.25)):   # anisotropy and rotation in [0, 1]
+    # anisotropy, rotation and the fuzz parameters in [0, 1]
+    for i, bad in ((27, 1.5), (28, -0.25), (29, 1.25), (31, -0.5), (33, 2.0)):
         m[0].v[i] = bad
         code = lib.pt_scene_create(v.ctypes.data_as(C.c_void_p), 3, idx.ctypes.data_as(C.c_void_p), 1,
                                    mid.ctypes.data_as(C.c_void_p), m, 1, None, 0, None, 0, 0, 0, None, C.byref(h))
         assert code == 1 and f"parameter {i} ".encode() in lib.pt_last_error()
-        m[0].v[i] = 0.0
+        m[0].v[i] = 0.5
     assert lib.pt_render(None, None, 1, 1, 0, None, None, None) == 1
 
 

@@ -127,8 +127,20 @@ def _bsdf_materials():
                        specular_roughness_anisotropy=0.5),
         scenes.openpbr(base_color=(0.8, 0.8, 0.8), base_metalness=1.0, specular_roughness=0.7,
                        specular_roughness_anisotropy=1.0),
+        scenes.openpbr(base_color=(0.5, 0.1, 0.2), specular_roughness=0.5, fuzz_weight=1.0,
+                       fuzz_color=(0.9, 0.6, 0.7), fuzz_roughness=0.4),
+        scenes.openpbr(specular_roughness=0.45, transmission_weight=0.8, coat_weight=0.6, coat_roughness=0.3,
+                       fuzz_weight=0.5, fuzz_color=(0.7, 0.8, 0.9), fuzz_roughness=0.8),
+        scenes.openpbr(base_weight=0.0, specular_weight=0.0, fuzz_weight=1.0, fuzz_roughness=0.2),
     ]
     return np.stack(mats)
+
+
+# A fuzz material's layer factor (1 - fw) + fw (1 - E(mu_i)) (1 - E(mu_o)) carries the error of
+# the lobe's albedo E on both sides: the GPU's Chebyshev series of E is good to about 1e-5 and
+# the oracle's fixed 64 x 64 rule to 7e-5 below mu ~ 1e-3, so the factor's absolute error is up
+# to about 2e-4 (relative to the largest value of f, as the scale below measures it).
+FUZZ_REL = 3e-4
 
 
 def _dirs(rng, n, lower=False):
@@ -173,11 +185,12 @@ def test_bsdf_eval_parity(api, front):
             f_g = f_g.cpu().numpy().astype(np.float64)
             p_g = p_g.cpu().numpy().astype(np.float64)
             ill = _near_tir(m, front, wo, wi)
-            assert ill.mean() < 0.25
+            assert ill.mean() < 0.3     # most tuples keep the tight bound (seen from inside glass ~ 1/4 do not)
+            tight = FUZZ_REL if m[29] > 0 else 1e-5
             for g, o, what in ((f_g, f_o, "f"), (p_g, p_o, "pdf")):
                 scale = np.maximum(np.abs(o), 1e-3 * np.abs(o).max())
                 err = np.abs(g - o) - 1e-30
-                bad = err > np.where(ill[:, None] if g.ndim == 2 else ill, 1e-3, 1e-5) * scale
+                bad = err > np.where(ill[:, None] if g.ndim == 2 else ill, 1e-3, tight) * scale
                 assert not bad.any(), (m_i, lower, what, np.argwhere(bad)[:3].ravel(),
                                        g[bad][:3], o[bad][:3])
 
@@ -218,7 +231,7 @@ def test_bsdf_sample_parity(api):
             # (a few 1e-7) into wi.z, and the weight's Smith term (1 + Lambda(wi))^-1 grows
             # like wi.z there: the weight's relative error is about 3e-7 / |wi.z| on top
             mu_i = np.abs(wi_o[sel][same_dir][:, 2:3])
-            rel = 1e-4 + 3e-7 / np.maximum(mu_i, 1e-12)
+            rel = (FUZZ_REL if m[29] > 0 else 1e-4) + 3e-7 / np.maximum(mu_i, 1e-12)
             close = np.abs(w_g[same_dir] - ww) <= rel * np.maximum(np.abs(ww), 1e-3 * np.abs(ww).max()) + 1e-30
             assert close.mean() >= need, (m_i, front, close.mean(), mu_i[~close.all(1)][:5].ravel())
 
@@ -471,6 +484,37 @@ def test_image_parity_anisotropic(api, mode):
     sc2 = scenes.Scene(base.name, base.vertices, base.indices, mid, turned, base.lights, base.env,
                        base.camera, base.spp, base.max_depth)
     acc = A.Scene(sc2).render(sc.spp, mode=mode, seed=9)
+    torch.cuda.synchronize()
+    assert np.abs(acc.image().cpu().numpy() - gi).max() > 1e-3
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_image_parity_fuzz(api, mode):
+    """The Cornell box with velvet boxes (a red base under white fuzz of roughness 0.4) and a
+    fuzz-over-coat back wall, GPU vs oracle; without the fuzz the picture is darker at the
+    boxes' silhouettes and differs."""
+    from paper_2407_19977_gb300 import api as A
+    base = scenes.cornell_box(width=40, height=32, spp=8, max_depth=4)
+    mats = np.array(base.materials, dtype=np.float32).copy()
+    velvet = scenes.openpbr(base_color=(0.6, 0.05, 0.1), specular_roughness=0.6, fuzz_weight=1.0,
+                            fuzz_color=(1.0, 0.9, 0.9), fuzz_roughness=0.4)
+    wall = scenes.openpbr(base_color=(0.3, 0.5, 0.7), specular_roughness=0.4, coat_weight=0.7, coat_roughness=0.2,
+                          fuzz_weight=0.6, fuzz_color=(0.8, 0.8, 0.5), fuzz_roughness=0.9)
+    mats = np.concatenate([mats, velvet[None], wall[None]])
+    mid = np.asarray(base.material_ids, np.uint32).copy()
+    mid[10:] = len(mats) - 2                # the two boxes (triangles after the 10 wall triangles)
+    mid[:2] = len(mats) - 1                 # one wall
+    sc = scenes.Scene(base.name, base.vertices, base.indices, mid, mats, base.lights, base.env,
+                      base.camera, base.spp, base.max_depth)
+    g = A.Scene(sc)
+    osc = oracle.OracleScene(sc)
+    gi, oi, gs, os_, st = _render_pair(g, osc, sc, sc.spp, mode=mode, max_depth=sc.max_depth, seed=11)
+    _samples_check(gs, os_, f"fuzz mode {mode}")
+    plain = mats.copy()
+    plain[-2:, 29] = 0.0
+    sc2 = scenes.Scene(base.name, base.vertices, base.indices, mid, plain, base.lights, base.env,
+                       base.camera, base.spp, base.max_depth)
+    acc = A.Scene(sc2).render(sc.spp, mode=mode, seed=11)
     torch.cuda.synchronize()
     assert np.abs(acc.image().cpu().numpy() - gi).max() > 1e-3
 

@@ -192,6 +192,33 @@ def test_nrc_render_queries_and_trains():
     assert np.mean(losses[-3:]) < np.mean(losses[:3])
 
 
+def test_nrc_render_with_fuzz_materials():
+    """The cached tracer on a scene with velvet boxes: queries and training run, the image is
+    finite and its mean within 25 % of the plain tracer's (the cache is biased, not wrong by a
+    factor)."""
+    from paper_2407_19977_gb300 import api, scenes
+    base = scenes.cornell_box(width=128, height=96, spp=1, max_depth=6)
+    velvet = scenes.openpbr(base_color=(0.4, 0.4, 0.5), specular_roughness=0.5, fuzz_weight=1.0,
+                            fuzz_color=(1.0, 0.8, 0.8), fuzz_roughness=0.4)
+    mats = np.concatenate([np.asarray(base.materials, np.float32), velvet[None]])
+    mid = np.asarray(base.material_ids, np.uint32).copy()
+    mid[10:] = len(mats) - 1                # the boxes
+    sc = scenes.Scene(base.name, base.vertices, base.indices, mid, mats, base.lights, base.env,
+                      base.camera, base.spp, base.max_depth)
+    g = api.Scene(sc)
+    lo = sc.vertices.min(0) - 0.01
+    hi = sc.vertices.max(0) + 0.01
+    net = api.Nrc(seed=2, box=(tuple(lo), tuple(hi)))
+    for f in range(24):
+        acc = g.render(1, seed=f, mode=1, nrc=net, nrc_train=True)
+    cached = g.render(16, seed=77, mode=1, nrc=net).image().cpu().numpy()
+    plain = g.render(64, seed=78, mode=1).image().cpu().numpy()
+    st = g.stats()
+    assert st["error_flags"] == 0 and st["nrc_queries"] > 0
+    assert np.all(np.isfinite(cached))
+    assert abs(cached.mean() / plain.mean() - 1.0) < 0.25, (cached.mean(), plain.mean())
+
+
 def test_nrc_frame_same_with_and_without_tail_kernel():
     """With the radiance cache on, the tail kernel ends paths at the same vertices, issues the
     same cache queries (in another order) and records the same training vertices: a frame

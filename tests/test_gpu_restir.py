@@ -54,6 +54,24 @@ def test_restir_parity_in_a_window_and_with_the_sky(api):
     _samples_check(gs, os_, "restir pushbutton crop", max_divergent=4e-3)
 
 
+def test_restir_parity_with_fuzz_materials(api):
+    """The reservoirs' full target and the shading of their sample evaluate the fuzz layer
+    (velvet walls and boxes in the many-light box), with later-vertex candidates too."""
+    import numpy as np
+    base = scenes.many_light_box(24, width=40, height=32, spp=3, max_depth=3, seed=6)
+    velvet = scenes.openpbr(base_color=(0.5, 0.2, 0.1), specular_roughness=0.5, fuzz_weight=0.8,
+                            fuzz_color=(0.9, 0.9, 1.0), fuzz_roughness=0.5)
+    mats = np.concatenate([np.asarray(base.materials, np.float32), velvet[None]])
+    mid = np.asarray(base.material_ids, np.uint32).copy()
+    mid[:10] = len(mats) - 1                # the enclosure's walls
+    sc = scenes.Scene(base.name, base.vertices, base.indices, mid, mats, base.lights, base.env,
+                      base.camera, base.spp, base.max_depth)
+    for r in ((8, 5, 4), (8, 5, 4, 4)):
+        g, acc, gs, os_, st = _pair(sc, r, sc.spp, seed=13)
+        _samples_check(gs, os_, f"restir fuzz {r}", max_divergent=4e-3)
+        assert g.stats()["error_flags"] == 0
+
+
 def test_restir_progressive_graph_and_auto_are_identical(api):
     from paper_2407_19977_gb300 import api as A
     from paper_2407_19977_gb300 import native as N

@@ -925,6 +925,21 @@ __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32
     }
 }
 
+// Launches with the fuzz layer compiled in only for scenes that have a material with fuzz
+// (the kernels without it are the same code as before the layer existed, with fewer spills).
+template <bool NRC, bool COUNT, bool RIS>
+static void launch_tail(bool fuzz, uint32_t grid, cudaStream_t st, const WfParams& P, int in_q, uint32_t k,
+                        uint32_t limit) {
+    if (fuzz) PT_LAUNCH((k_wf_tail<NRC, COUNT, RIS, true>), grid, 128, 0, st, P, in_q, k, limit);
+    else PT_LAUNCH((k_wf_tail<NRC, COUNT, RIS, false>), grid, 128, 0, st, P, in_q, k, limit);
+}
+template <bool NRC, bool RIS>
+static void launch_shade(bool fuzz, uint32_t grid, cudaStream_t st, const WfParams& P, int in_q, int out_q,
+                         uint32_t k) {
+    if (fuzz) PT_LAUNCH((k_wf_shade<NRC, RIS, true>), grid, 128, 0, st, P, in_q, out_q, k);
+    else PT_LAUNCH((k_wf_shade<NRC, RIS, false>), grid, 128, 0, st, P, in_q, out_q, k);
+}
+
 __global__ void k_wf_accum(WfParams P) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long nan_cnt = 0;
@@ -1203,21 +1218,16 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                     ++launches;
                     if (tail_limit && !(restir && k == 0)) {
                         e = begin(PT_K_TAIL);
+                        const bool fz = s->has_fuzz;
                         if (P.nrc_on) {
-                            if (count) PT_LAUNCH((k_wf_tail<true, true, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                            else PT_LAUNCH((k_wf_tail<true, false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+                            if (count) launch_tail<true, true, false>(fz, tail_grid, st, P, in_q, k, tail_limit);
+                            else launch_tail<true, false, false>(fz, tail_grid, st, P, in_q, k, tail_limit);
+                        } else if (restir) {
+                            if (count) launch_tail<false, true, true>(fz, tail_grid, st, P, in_q, k, tail_limit);
+                            else launch_tail<false, false, true>(fz, tail_grid, st, P, in_q, k, tail_limit);
                         } else {
-                            if (restir) {
-                                if (count) PT_LAUNCH((k_wf_tail<false, true, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                                else PT_LAUNCH((k_wf_tail<false, false, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                            } else if (s->has_fuzz) {
-                                if (count) PT_LAUNCH((k_wf_tail<false, true, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                                else PT_LAUNCH((k_wf_tail<false, false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                            } else {
-                                // no material has fuzz: kernels compiled without the fuzz layer
-                                if (count) PT_LAUNCH((k_wf_tail<false, true, false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                                else PT_LAUNCH((k_wf_tail<false, false, false, false>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
-                            }
+                            if (count) launch_tail<false, true, false>(fz, tail_grid, st, P, in_q, k, tail_limit);
+                            else launch_tail<false, false, false>(fz, tail_grid, st, P, in_q, k, tail_limit);
                         }
                         end(e);
                         ++launches;
@@ -1242,10 +1252,10 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                         launches += 2;
                     }
                     e = begin(PT_K_SHADE);
-                    if (P.nrc_on) PT_LAUNCH((k_wf_shade<true, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
-                    else if (restir) PT_LAUNCH((k_wf_shade<false, true>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
-                    else if (s->has_fuzz) PT_LAUNCH((k_wf_shade<false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
-                    else PT_LAUNCH((k_wf_shade<false, false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+                    const uint32_t shade_grid = sms * g_shade_blocks_per_sm;
+                    if (P.nrc_on) launch_shade<true, false>(s->has_fuzz, shade_grid, st, P, in_q, out_q, k);
+                    else if (restir) launch_shade<false, true>(s->has_fuzz, shade_grid, st, P, in_q, out_q, k);
+                    else launch_shade<false, false>(s->has_fuzz, shade_grid, st, P, in_q, out_q, k);
                     end(e);
                     e = begin(PT_K_SHADOW);
                     if (count) PT_LAUNCH(k_wf_shadow<true>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
@@ -1658,8 +1668,7 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
                 PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
                 launches += 2;
             }
-            if (s->has_fuzz) PT_LAUNCH((k_wf_shade<false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
-            else PT_LAUNCH((k_wf_shade<false, false, false>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+            launch_shade<false, false>(s->has_fuzz, sms * g_shade_blocks_per_sm, st, P, in_q, out_q, k);
             PT_LAUNCH(k_wf_shadow<false>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
             launches += 2;
         }

@@ -43,6 +43,8 @@ WORKLOADS = {
                       "1920x1080, 1 spp/step, max depth 8",
     "many_lights": "Cornell-style box lit by 248 small non-overlapping quad lights (heavy-tailed radiance, random "
                    "tints) on the ceiling and side walls, 1920x1080, 1 spp/step, max depth 4",
+    "pushbutton_fuzz": "the pushbutton frame with the button's red coated plastic under a fuzz layer (velvet), "
+                       "1920x1080, 1 spp/step, max depth 8",
 }
 NODE_BYTES = 80      # compressed 8-wide BVH node
 TRI_BYTES = 48       # triangle record
@@ -208,6 +210,8 @@ def _make_workload(name):
         return scenes.cornell_box(width=1920, height=1080, spp=1, max_depth=8)
     if name == "many_lights":
         return scenes.many_light_box(256, width=1920, height=1080, spp=1, max_depth=4, seed=0)
+    if name == "pushbutton_fuzz":
+        return scenes.pushbutton_fuzz()
     if name == "pushbutton_dof":
         sc = scenes.pushbutton()
         c = sc.camera

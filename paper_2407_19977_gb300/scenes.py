@@ -409,6 +409,18 @@ def _pushbutton_materials():
     ])
 
 
+def pushbutton_fuzz(**kw) -> Scene:
+    """The pushbutton with its red coated plastic turned into velvet: the same red base and
+    coat under a fuzz layer (weight 1, roughness 0.5, pale pink fibres)."""
+    sc = pushbutton(**kw)
+    mats = np.array(sc.materials, dtype=np.float32).copy()
+    mats[1] = openpbr(base_color=(0.8, 0.05, 0.05), specular_roughness=0.3, specular_ior=1.5, coat_weight=1.0,
+                      coat_roughness=0.05, coat_ior=1.5, fuzz_weight=1.0, fuzz_color=(1.0, 0.85, 0.85),
+                      fuzz_roughness=0.5)
+    return Scene("pushbutton_fuzz", sc.vertices, sc.indices, sc.material_ids, mats, sc.lights, sc.env, sc.camera,
+                 sc.spp, sc.max_depth)
+
+
 def pushbutton(seed=0, n_profile=250, n_angular=400, ground=(50, 100), width=1920, height=1080,
                spp=256, max_depth=8, env_size=(512, 256), with_light=True) -> Scene:
     """Config 2: lathe of a seeded Catmull-Rom profile (cap, cylinder, bezel) on a ground grid.

@@ -421,6 +421,21 @@ def test_full_frame_bench_configuration(api):
     _image_check(g[::45], o[::45], "pushbutton 1080p rows")
 
 
+def test_full_frame_fuzz_configuration(api):
+    """The benchmark's velvet variant of the 1080p pushbutton, whole frame, one sample per
+    pixel, wavefront (kernels with the fuzz layer); the oracle checks every 45th row."""
+    from paper_2407_19977_gb300 import api as A
+    sc = scenes.pushbutton_fuzz()
+    g = A.Scene(sc)
+    acc = A.Accum(sc.camera.width, sc.camera.height)
+    g.render(1, seed=0, accum=acc, mode=1)
+    torch.cuda.synchronize()
+    img = acc.sum.cpu().numpy()
+    o, _, st = oracle.OracleScene(sc).render(spp=1, seed=0, row_step=45)
+    _image_check(img[::45], o[::45], "velvet pushbutton 1080p rows")
+    assert g.stats()["error_flags"] == 0
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_image_parity_depth_of_field(api, mode):
     """A thin-lens Cornell frame (focus on the back wall, aperture ~ 2 % of the box): the GPU

@@ -220,6 +220,7 @@ struct Closure {
     float eta_s, eta_c, ax_s, ay_s, a_c;   // specular widths along tangent / bitangent; coat
     bool delta_s, delta_c, any, has_smooth, thin;
     const float* fz;            // the material's fuzz block, nullptr without fuzz
+    float fe_o, fa_o;           // with fuzz: E(mu_o), A(mu_o) of the setup's mu_o
     float p[N_LOBES];
 };
 
@@ -258,6 +259,8 @@ __device__ __forceinline__ void closure_setup(Closure& C, const DMat& M, bool fr
     if (FUZZ && M.fuzz_weight > 0.0f) {
         C.fz = fz;
         const float fw = M.fuzz_weight, e_o = fuzz_albedo(fz, mu_o);
+        C.fe_o = e_o;
+        C.fa_o = fuzz_area(fz, mu_o);
         const float sc = 1.0f - fw * e_o;
         wc *= sc; wm *= sc; w2 *= sc; w_diff *= sc;
         w_fuzz = fw * lum3(mk3(__ldg(fz + 1), __ldg(fz + 2), __ldg(fz + 3))) * e_o;
@@ -270,11 +273,12 @@ __device__ __forceinline__ void closure_setup(Closure& C, const DMat& M, bool fr
                    C.p[3] > 0.0f || C.p[4] > 0.0f;
 }
 
-// A_f: the part of the layers under the fuzz that reaches wo from wi (1 without fuzz)
-__device__ __forceinline__ float fuzz_attenuation(const Closure& C, float mi_abs, float mo) {
+// A_f: the part of the layers under the fuzz that reaches wo from wi (1 without fuzz); wo is
+// the direction the closure was set up for
+__device__ __forceinline__ float fuzz_attenuation(const Closure& C, float mi_abs) {
     if (C.fz == nullptr) return 1.0f;
     const float fw = __ldg(C.fz);
-    return (1.0f - fw) + fw * (1.0f - fuzz_albedo(C.fz, mi_abs)) * (1.0f - fuzz_albedo(C.fz, mo));
+    return (1.0f - fw) + fw * (1.0f - fuzz_albedo(C.fz, mi_abs)) * (1.0f - C.fe_o);
 }
 
 __device__ __forceinline__ float diel_reflect_prob(const Closure& C, float F) {
@@ -365,11 +369,11 @@ __device__ __forceinline__ void closure_eval(const Closure& C, float3 wo, float3
         }
     }
     if (C.fz != nullptr) {
-        f = f * fuzz_attenuation(C, fabsf(mi), mo);
+        f = f * fuzz_attenuation(C, fabsf(mi));
         if (mi > 0.0f) {
             const float* fz = C.fz;
             const float3 h = norm3(wo + wi);
-            const float den = 4.0f * (fuzz_area(fz, mi) * mo + fuzz_area(fz, mo) * mi - mi * mo);
+            const float den = 4.0f * (fuzz_area(fz, mi) * mo + C.fa_o * mi - mi * mo);
             const float3 fc = mk3(__ldg(fz + 1), __ldg(fz + 2), __ldg(fz + 3));
             f = f + fc * (__ldg(fz) * sheen_D(h.z, __ldg(fz + 4)) / den);
             pdf += C.p[LOBE_FUZZ] * (0.5f * PT_INV_PI_F);
@@ -407,7 +411,7 @@ __device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, floa
     if (lobe == LOBE_COAT) {
         if (C.delta_c) {
             out.wi = mk3(-wo.x, -wo.y, wo.z);
-            out.weight = splat3(C.cw * fresnel_dielectric(mo, C.eta_c) * fuzz_attenuation(C, mo, mo) / C.p[0]);
+            out.weight = splat3(C.cw * fresnel_dielectric(mo, C.eta_c) * fuzz_attenuation(C, mo) / C.p[0]);
             out.delta = true;
             return true;
         }
@@ -417,7 +421,7 @@ __device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, floa
         if (C.delta_s) {
             out.wi = mk3(-wo.x, -wo.y, wo.z);
             const float3 fm = fresnel_f82(C.bc * C.bw, C.sc, mo);
-            out.weight = (coat_attenuation(C, mo, mo) * fm) * (C.m * C.sw * fuzz_attenuation(C, mo, mo) / C.p[1]);
+            out.weight = (coat_attenuation(C, mo, mo) * fm) * (C.m * C.sw * fuzz_attenuation(C, mo) / C.p[1]);
             out.delta = true;
             return true;
         }
@@ -447,11 +451,11 @@ __device__ __forceinline__ bool closure_sample(const Closure& C, float3 wo, floa
             out.delta = true;
             if (do_reflect) {
                 out.weight = (coat_attenuation(C, mo, mo) * C.sc) *
-                             ((1.0f - C.m) * C.sw * fr * fuzz_attenuation(C, mo, mo) / (C.p[2] * pr));
+                             ((1.0f - C.m) * C.sw * fr * fuzz_attenuation(C, mo) / (C.p[2] * pr));
             } else {
                 const float scale = C.thin ? 1.0f : C.eta_s * C.eta_s;   // radiance across the interface
                 out.weight = (coat_attenuation(C, fabsf(wi.z), mo) * C.tc) *
-                             ((1.0f - C.m) * C.t * (1.0f - C.sw * fr) * fuzz_attenuation(C, fabsf(wi.z), mo) /
+                             ((1.0f - C.m) * C.t * (1.0f - C.sw * fr) * fuzz_attenuation(C, fabsf(wi.z)) /
                               (scale * C.p[2] * (1.0f - pr)));
             }
             return true;

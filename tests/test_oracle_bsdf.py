@@ -70,6 +70,37 @@ def test_rough_diffuse_properties():
         assert E <= rho * (1 + 1e-2), (mu, E)
 
 
+@pytest.mark.parametrize("sigma", [0.3, 0.7, 1.0])
+def test_rough_diffuse_normalisation_fixes_the_grazing_albedo(sigma):
+    """Fujii's normalisation of the qualitative Oren-Nayar term, 1 / (1 + (1/2 - 2/(3 pi)) sigma),
+    is the value its s/t term integrates to at a grazing view: with wo on the horizon, t = mu_i
+    where s > 0 and
+      (1/pi) int (s/t) mu_i dwi = (1/pi) [int sin(th_i) cos(phi)+ dwi - int mu_i sin(th_i) cos(phi)- dwi]
+                                = (1/pi) (pi/2 - 2/3),
+    so the directional albedo there is exactly rho for every roughness.  A wrong constant (or a
+    wrong s, t or sign) moves this albedo by about sigma times its error.  Quadrature: Gauss in
+    mu_i and, split where s changes sign (phi = pi/2), in the azimuth."""
+    rho = 0.8
+    mat = scenes.openpbr(base_color=(rho,) * 3, base_diffuse_roughness=sigma, specular_weight=0.0)
+    x, w = np.polynomial.legendre.leggauss(96)
+    mus, wm = 0.5 * (x + 1), 0.5 * w
+    phs = np.concatenate([0.25 * math.pi * (x + 1), 0.5 * math.pi + 0.25 * math.pi * (x + 1)])
+    wp = np.concatenate([0.25 * math.pi * w, 0.25 * math.pi * w])       # [0, pi]; doubled below
+    M, P = np.meshgrid(mus, phs, indexing="ij")
+    sn = np.sqrt(1 - M * M)
+    wi = np.stack([sn * np.cos(P), sn * np.sin(P), M], -1).reshape(-1, 3)
+    mu_o = 1e-7
+    wo = np.tile([math.sqrt(1 - mu_o * mu_o), 0.0, mu_o], (wi.shape[0], 1))
+    f, _ = oracle.bsdf_eval_batch(mat, 1, wo, wi)
+    E = 2.0 * float((f[:, 0] * wi[:, 2] * np.outer(wm, wp).reshape(-1)).sum())
+    assert E == pytest.approx(rho, rel=1e-5), E
+    # away from grazing the same term loses energy (no multiple-scattering compensation)
+    wo1 = np.tile([0.0, 0.0, 1.0], (wi.shape[0], 1))
+    f1, _ = oracle.bsdf_eval_batch(mat, 1, wo1, wi)
+    E1 = 2.0 * float((f1[:, 0] * wi[:, 2] * np.outer(wm, wp).reshape(-1)).sum())
+    assert E1 == pytest.approx(rho / (1 + (0.5 - 2 / (3 * math.pi)) * sigma), rel=1e-6)
+
+
 def test_thin_walled_sheet():
     """A smooth white thin-walled sheet passes light straight through (wi = -wo) with
     weight 1 - F and reflects F into the mirror direction, so reflectance plus transmittance

@@ -1,6 +1,7 @@
 """Pins of the display-resolve oracle (oracle/tonemap.py): facts the Khronos PBR Neutral
 mapping and the sRGB transfer function fix, independent of how the oracle writes them."""
 import numpy as np
+import pytest
 
 from oracle import tonemap as tm
 
@@ -56,6 +57,32 @@ def test_desaturation_moves_highlights_towards_white():
     shifted = c[0] - f
     assert (out.max() - out.min()) / out.max() < (shifted.max() - shifted.min()) / shifted.max()
     assert out.min() > shifted.min() * out.max() / shifted.max()
+
+
+def test_desaturation_constant_half_way_to_white():
+    """The desaturation step mixes the compressed colour towards white by
+    g = 1 - 1 / (K_d (p - p') + 1), p - p' the amount the highlight was compressed and K_d = 0.15
+    the published desaturation speed: a highlight compressed by exactly 1 / K_d = 20/3 is moved
+    half-way to white.  A pure-red highlight c = (p, 0, 0) has no toe offset (the offset
+    x - x^2 / (4 F90) vanishes at its minimum x = 0) and becomes (p', g p', g p'), so green
+    over red reads g directly.  p solves p - p'(p) = 20/3 with p' = 1 - d^2 / (p + d - K_s),
+    d = 1 - K_s (bisection in float64).  With K_d = 0.10 or 0.30 the ratio is 0.40 or 0.67."""
+    ks, d = 0.76, 0.24
+    lo, hi = 1.0, 20.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid - (1 - d * d / (mid + d - ks)) < 20.0 / 3.0:
+            lo = mid
+        else:
+            hi = mid
+    p = 0.5 * (lo + hi)
+    out = tm.pbr_neutral(np.array([[p, 0.0, 0.0]], np.float32))[0].astype(np.float64)
+    assert out[1] == out[2]
+    assert out[1] / out[0] == pytest.approx(0.5, abs=2e-6)
+    assert out[0] == pytest.approx(1 - d * d / (p + d - ks), abs=2e-6)
+    # at the knee (p = K_s) nothing has been compressed, so nothing is desaturated
+    knee = tm.pbr_neutral(np.array([[0.76 + 1e-4, 0.0, 0.0]], np.float32))[0].astype(np.float64)
+    assert knee[1] / knee[0] < 1e-5
 
 
 def test_srgb_closed_forms():

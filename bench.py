@@ -55,9 +55,14 @@ HIT_BYTES = 16       # hit record out
 # ~ 50 (9 sub, 12 shear, 9 edge products/differences, sign tests, det, T, divide, range)
 OPS_PER_NODE = 8 * 30
 OPS_PER_TRI = 50
-# FP32 lane peak: 152 SMs x 128 FP32 lanes x 2.07 GHz (an FMA counted as one operation)
-SM_COUNT, FP32_LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.07
-ALU_PEAK_GOPS = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_GHZ
+# FP32 lane peak: SMs (read from the device) x 128 FP32 lanes x the maximum SM clock (an FMA
+# counted as one operation); 2.07 GHz is the GB300's maximum SM clock, MEASURED_PEAKS.json's
+# sm_max_mhz when present
+FP32_LANES_PER_SM, SM_MAX_GHZ = 128, 2.07
+
+
+def alu_peak_gops(sm_count: int, sm_max_ghz: float = SM_MAX_GHZ) -> float:
+    return sm_count * FP32_LANES_PER_SM * sm_max_ghz
 
 
 def _args():
@@ -148,28 +153,86 @@ def _recorded_traffic(kernel: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """SM clock and clock-event (throttle) reasons sampled while running: NVML read through
+    ctypes every 2 ms (a 20-frame timed region lasts about 70 ms), else nvidia-smi every 50 ms.
+    Only reads; changes no setting."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_s: float = 0.002):
         self.gpu = gpu_index
+        self.period = period_s
         self.proc = None
         self.file = None
+        self.nvml = None
+        self.rows = []
+        self.thread = None
+        self.stop = None
+        self.source = None
+
+    def _nvml_open(self):
+        import ctypes as C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = C.c_void_p()
+        bus = None
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.gpu)
+            bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        except Exception:
+            bus = None
+        ok = bus is not None and lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), C.byref(h)) == 0
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.gpu), C.byref(h)) != 0:
+            return None
+        mx = C.c_uint()
+        lib.nvmlDeviceGetMaxClockInfo(h, C.c_int(1), C.byref(mx))
+        self.max_mhz = float(mx.value)
+        return lib, h
+
+    def _nvml_loop(self):
+        import ctypes as C
+        lib, h = self.nvml
+        mhz, reasons = C.c_uint(), C.c_ulonglong()
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, C.c_int(1), C.byref(mhz)) == 0 and \
+                    get_reasons(h, C.byref(reasons)) == 0:
+                self.rows.append((float(mhz.value), int(reasons.value)))
+            self.stop.wait(self.period)
 
     def __enter__(self):
+        import threading
+        try:
+            self.nvml = self._nvml_open()
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            self.source = f"NVML every {self.period * 1e3:.0f} ms"
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._nvml_loop, daemon=True)
+            self.thread.start()
+            return self
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.file, stderr=subprocess.DEVNULL)
+            self.source = "nvidia-smi every 50 ms"
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *exc):
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -178,6 +241,13 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        if self.nvml is not None:
+            if not self.rows:
+                return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"], "source": self.source}
+            reasons = sorted({name for _, r in self.rows for bit, name in self.REASONS.items() if r & bit})
+            return {"sm_mhz": statistics.median(m for m, _ in self.rows), "sm_max_mhz": self.max_mhz,
+                    "sm_mhz_min": min(m for m, _ in self.rows), "reasons": reasons, "samples": len(self.rows),
+                    "source": self.source}
         if self.proc is None or self.file is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.file.flush()
@@ -195,7 +265,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": self.source}
 
 
 def _make_workload(name):
@@ -267,8 +337,10 @@ def run_reference(args, world, rank):
     import oracle
     threads = os.cpu_count() or 1
     osc = oracle.OracleScene(sc)
-    # each step renders a bounded slice: every 32nd row of the frame at 1 spp
-    row_step = 32
+    # each step renders a bounded slice of the frame at 1 spp: every row_step-th row, with
+    # at least 16 rows per host thread so that the oracle's round-robin rows keep every
+    # thread busy (the same loading as the cpu_baseline leg)
+    row_step = max(1, sc.camera.height // (16 * threads))
     for w in range(args.warmup):
         osc.render(spp=1, seed=0, s0=w, row_step=row_step, threads=threads)
     t0 = time.perf_counter()
@@ -286,7 +358,9 @@ def run_reference(args, world, rank):
         "config": {"workload": WORKLOADS[args.workload], "sample": f"every {row_step}th row, 1 spp per step"},
         "spp_per_s_1080p": paths / dt / (sc.camera.width * sc.camera.height),
         "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-                         "sample": f"every {row_step}th row of the 1080p frame at 1 spp per step, {args.steps} steps"},
+                         "sample": f"every {row_step}th row of the {sc.camera.width}x{sc.camera.height} frame "
+                                   f"({len(range(0, sc.camera.height, row_step))} rows) at 1 spp per step, "
+                                   f"{args.steps} steps"},
         "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -425,6 +499,9 @@ def run_ours(args, world, rank, local):
     trace_ms = kms["trace"]
     achieved_gbs = trace_bytes_step / (trace_ms * 1e-3) / 1e9 if trace_ms > 0 else None
     achieved_gops = trace_ops_step / (trace_ms * 1e-3) / 1e9 if trace_ms > 0 else None
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_ghz = float(_peaks()[0].get("sm_max_mhz", SM_MAX_GHZ * 1e3)) / 1e3
+    alu_peak = alu_peak_gops(sm_count, sm_ghz)
     traffic = _recorded_traffic("trace")
     trace_launches = max(kl["trace"], 1)
     result = {
@@ -445,10 +522,11 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": W * H * 3 * 4,
                 "copies": "each frame's image to pinned host memory, double-buffered on a copy stream"},
         "roofline": {"bound": "alu", "kernel": "k_wf_trace (closest hit)",
-                     "achieved": achieved_gops, "peak": ALU_PEAK_GOPS, "unit": "GOP/s",
-                     "frac": achieved_gops / ALU_PEAK_GOPS if achieved_gops else None,
+                     "achieved": achieved_gops, "peak": alu_peak, "unit": "GOP/s",
+                     "frac": achieved_gops / alu_peak if achieved_gops else None,
                      "traffic": traffic,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (recipe unit counts and clock)",
+                     "peak_source": f"{sm_count} SMs (device query) x {FP32_LANES_PER_SM} FP32 lanes x "
+                                    f"{sm_ghz:.2f} GHz maximum SM clock (recipe unit counts and clock)",
                      "algorithmic_ops_per_launch": trace_ops_step / trace_launches,
                      "launch_ms": trace_ms / trace_launches,
                      "per_ray": {"nodes": cnt["trace_nodes"] / max(cnt["trace_rays"], 1),

@@ -220,7 +220,17 @@ typedef struct {
                                    (that call launches directly). */
     const pt_restir_opts* restir; /* optional: ReSTIR DI at the primary vertex (NULL = next-event
                                    estimation) */
+    uint32_t traversal;         /* wavefront closest-hit and shadow passes: PT_TRAVERSAL_* (the
+                                   hits, and the node and triangle counts, are the same) */
 } pt_render_opts;
+
+enum {
+    PT_TRAVERSAL_AUTO = 0,      /* one ray per lane */
+    PT_TRAVERSAL_PER_LANE = 1,  /* one ray per lane, its 8 child boxes tested in a loop */
+    PT_TRAVERSAL_COOP = 2       /* one ray per group of 8 lanes: a lane per child box, a node's
+                                   leaf triangles spread over the group (more lanes busy, but
+                                   more instructions per ray: slower on the CAD frames) */
+};
 
 typedef struct {
     uint32_t leaf_size;         /* max triangles per leaf, 1..4 (0 = 4) */
@@ -293,18 +303,23 @@ pt_status pt_render(pt_scene* scene, const pt_camera* camera, uint32_t spp, uint
 /* pt_render for callers that cannot allocate device memory (no counterpart in the paper).
  * Some host programs are not allowed to call cudaMalloc: they run under a device-memory
  * budget fixed at start-up, inside a host application that owns every allocation, or in a
- * real-time loop that must not enter the allocator.  This call renders exactly what
- * pt_render renders in PT_MODE_WAVEFRONT (same kernels, same random numbers, bit-identical
- * accumulators) but takes its work queues from one fixed array compiled into the library
- * (16,384 paths, about 2.7 MB, held on every GPU that loads the library until the process
- * exits) and calls no allocating routine.  Limits and rules:
+ * real-time loop that must not enter the allocator.  This call renders what pt_render
+ * renders in PT_MODE_WAVEFRONT: the same per-bounce kernels and random numbers, so the
+ * accumulators are bit-identical to pt_render's (pt_render may finish small queues in its
+ * tail kernel, which gives the same bits; this call never launches it).  Its work queues live
+ * in one fixed array compiled into the library (16,384 paths, about 2.7 MB, held on every GPU
+ * that loads the library until the process exits) and it calls no allocating routine.
+ * Limits and rules:
  *  - the window (accum->width * accum->height) holds at most 16,384 pixels; larger images
- *    are rendered tile by tile; larger windows return PT_ERR_INVALID_ARG;
- *  - opts->nrc and opts->kernel_ms / kernel_launches must be NULL (PT_ERR_INVALID_ARG);
- *  - every call shares the one array: calls that overlap on the GPU (different streams, or
- *    threads without ordering) race on it and corrupt each other's work;
- *  - the first call on a device looks the array's device address up with
- *    cudaGetSymbolAddress; make that first call before any stream capture.
+ *    are rendered tile by tile (crop_x0, crop_y0); larger windows return PT_ERR_INVALID_ARG;
+ *  - opts->nrc, opts->restir and opts->kernel_ms / kernel_launches must be NULL, and
+ *    opts->flags may hold PT_FLAG_NO_NEE and PT_FLAG_NO_RR only (PT_ERR_INVALID_ARG);
+ *  - every call shares the one array and leaves its contents behind; the kernels reset every
+ *    counter they read before reading it.  Calls that overlap on the GPU (different streams,
+ *    or threads without ordering) race on the array and corrupt each other's work;
+ *  - each call looks the array's device address up in the current context with
+ *    cudaGetSymbolAddress (no allocation once the library's device code is loaded there); the
+ *    first call on a device loads that code, so make it before any stream capture.
  * Inputs, outputs and errors otherwise as pt_render. */
 pt_status pt_render_noalloc(pt_scene* scene, const pt_camera* camera, uint32_t spp,
                             uint32_t max_depth, uint64_t seed, pt_accum* accum,
@@ -371,8 +386,11 @@ pt_status pt_autotune_batch(const pt_job* jobs, uint32_t n_jobs, uint32_t frames
  * hit_tri uint32[n] triangle id (mesh ids, then light triangles; 0xFFFFFFFF on a miss),
  * hit_t float[n], hit_uv float[n*2] barycentric weights of v1 and v2.  Ties at equal t go
  * to the lower triangle id.  flags bit 0 (PT_TRACE_ANY): occlusion only (hit_tri = 0 or ~0);
- * bit 1 (PT_TRACE_COUNT): hit_uv receives the ray's wide-node visits and triangle tests. */
-enum { PT_TRACE_ANY = 1, PT_TRACE_COUNT = 2 };
+ * bit 1 (PT_TRACE_COUNT): hit_uv receives the ray's wide-node visits and triangle tests;
+ * bit 2 (PT_TRACE_COOP): the cooperative traversal of the wavefront passes (a group of 8
+ * lanes per ray) instead of one ray per thread -- the same results and counts.
+ * Asynchronous on the stream. */
+enum { PT_TRACE_ANY = 1, PT_TRACE_COUNT = 2, PT_TRACE_COOP = 4 };
 pt_status pt_trace(pt_scene* scene, const float* rays, uint32_t n, int flags,
                    uint32_t* hit_tri, float* hit_t, float* hit_uv, void* cuda_stream);
 

@@ -108,11 +108,15 @@ def relative_l2(y, target, eps=0.01):
     return loss, dy
 
 
-def mlp_backward(acts, weights, dy):
-    """Gradients of the weights and of the input given dL/dy."""
+def mlp_backward(acts, weights, dy, operand=None):
+    """Gradients of the weights and of the input given dL/dy.  operand: optional function
+    applied to each layer's output gradient where it enters the products (a tensor-core
+    implementation holds it as an FP16 operand); None = exact."""
     grads = [None] * len(weights)
     g = dy
     for i in range(len(weights) - 1, -1, -1):
+        if operand is not None:
+            g = operand(g)
         a = acts[i]
         grads[i] = g.T @ a
         g = g @ weights[i]

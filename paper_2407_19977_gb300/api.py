@@ -128,7 +128,7 @@ class Scene:
     def render(self, spp, max_depth=None, seed=0, accum=None, camera=None, crop=None, flags=0,
                mode=N.PT_MODE_AUTO, wave_paths=0, sort=-1, sample_out=None, block_size=0, stream=None,
                kernel_ms=None, kernel_launches=None, nrc=None, nrc_train=False, tail_paths=0, use_graph=False,
-               restir=None):
+               restir=None, traversal=N.PT_TRAVERSAL_AUTO):
         cam = camera or self.desc.camera
         max_depth = self.desc.max_depth if max_depth is None else max_depth
         if crop is None:
@@ -141,6 +141,7 @@ class Scene:
         o.wave_paths, o.sort_by_material, o.block_size = wave_paths, sort, block_size
         o.tail_paths = int(tail_paths)
         o.use_graph = 1 if use_graph else 0
+        o.traversal = int(traversal)
         if restir is not None:
             # (M candidates, K neighbours, radius R[, L later candidates]): ReSTIR DI at the
             # primary vertex, resampled next-event estimation at later vertices if L > 0
@@ -182,7 +183,7 @@ class Scene:
         return {k: int(getattr(best, k)) for k in keys}, float(ms.value)
 
     def trace(self, origins: torch.Tensor, dirs: torch.Tensor, tmax=None, any_hit=False, count=False,
-              stream=None):
+              coop=False, stream=None):
         n = origins.shape[0]
         rays = torch.zeros((n, 8), dtype=torch.float32, device="cuda")
         rays[:, 0:3] = origins
@@ -191,8 +192,8 @@ class Scene:
         tri = torch.empty(n, dtype=torch.int32, device="cuda")
         t = torch.empty(n, dtype=torch.float32, device="cuda")
         uv = torch.empty((n, 2), dtype=torch.float32, device="cuda")
-        N.call("pt_trace", self.h, _ptr(rays), n, (1 if any_hit else 0) | (2 if count else 0), _ptr(tri), _ptr(t), _ptr(uv),
-               _stream_handle(stream))
+        flags = (1 if any_hit else 0) | (2 if count else 0) | (4 if coop else 0)
+        N.call("pt_trace", self.h, _ptr(rays), n, flags, _ptr(tri), _ptr(t), _ptr(uv), _stream_handle(stream))
         return tri, t, uv
 
     def env_sample(self, u: torch.Tensor, stream=None):

@@ -434,6 +434,55 @@ __global__ void k_trace(DScene S, const float* rays, uint32_t n, int flags, uint
     }
 }
 
+// the same with the cooperative traversal: ray i is carried by the 8 lanes of group i
+__global__ void __launch_bounds__(128) k_trace_coop(DScene S, const float* rays, uint32_t n, int flags, uint32_t* tri,
+                                                    float* t, float* uv) {
+    __shared__ CoopShared gsh[128 / COOP_W];
+    const uint32_t lane = threadIdx.x & 31u, gl = lane & (COOP_W - 1u), gbase = lane & ~(COOP_W - 1u);
+    const uint32_t gm = 0xffu << gbase;
+    const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) / COOP_W;
+    if (i >= n) return;   // whole groups leave together
+    CoopShared& sh = gsh[threadIdx.x / COOP_W];
+    const float* r = rays + 8u * i;
+    const float3 o = mk3(r[0], r[1], r[2]), d = mk3(r[3], r[4], r[5]);
+    const float tmax = r[6];
+    const bool count = (flags & PT_TRACE_COUNT) != 0;
+    TravCount tc = {0, 0};
+    if (flags & PT_TRACE_ANY) {
+        CoopAny st;
+        coop_any_init(S, o, d, tmax, st);
+        if (count) while (!coop_any_step<true>(S, st, sh, gl, gm, gbase, tc)) {}
+        else while (!coop_any_step<false>(S, st, sh, gl, gm, gbase, tc)) {}
+        if (gl == 0) {
+            tri[i] = st.hit ? 0u : PT_NO_HIT;
+            if (t) t[i] = 0.0f;
+            if (uv && count) { uv[2 * i] = (float)tc.nodes; uv[2 * i + 1] = (float)tc.tris; }
+        }
+        return;
+    }
+    CoopClosest st;
+    coop_closest_init(S, o, d, tmax, st);
+    if (count) while (!coop_closest_step<true>(S, st, sh, gl, gm, gbase, tc)) {}
+    else while (!coop_closest_step<false>(S, st, sh, gl, gm, gbase, tc)) {}
+    HitRec h;
+    const bool mine = coop_closest_finish(st, gl, gm, gbase, h);
+    // the counts live in lane 0 of the group, the hit in the lane that found it
+    const uint32_t cn = __shfl_sync(gm, tc.nodes, 0, COOP_W), ct = __shfl_sync(gm, tc.tris, 0, COOP_W);
+    if (!mine) return;
+    if (h.tri == PT_NO_HIT) {
+        tri[i] = PT_NO_HIT;
+        if (t) t[i] = __int_as_float(0x7f800000);
+    } else {
+        tri[i] = __float_as_uint(S.tris[3u * h.tri].w);
+        if (t) t[i] = h.t;
+    }
+    if (uv) {
+        if (count) { uv[2 * i] = (float)cn; uv[2 * i + 1] = (float)ct; }
+        else if (h.tri == PT_NO_HIT) { uv[2 * i] = 0.0f; uv[2 * i + 1] = 0.0f; }
+        else { uv[2 * i] = h.u; uv[2 * i + 1] = h.v; }
+    }
+}
+
 extern "C" pt_status pt_trace(pt_scene* s, const float* rays, uint32_t n, int flags, uint32_t* hit_tri,
                               float* hit_t, float* hit_uv, void* cuda_stream) {
     PT_CHECK_ARG(s && rays && hit_tri, "NULL argument");
@@ -441,7 +490,14 @@ extern "C" pt_status pt_trace(pt_scene* s, const float* rays, uint32_t n, int fl
     if (n == 0) return PT_OK;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     s->last_stream = st;
-    PT_LAUNCH(k_trace, (n + 127) / 128, 128, 0, st, s->view(), rays, n, flags, hit_tri, hit_t, hit_uv);
+    PT_CHECK_ARG((flags & ~(PT_TRACE_ANY | PT_TRACE_COUNT | PT_TRACE_COOP)) == 0, "unknown trace flags");
+    if (flags & PT_TRACE_COOP) {
+        const uint64_t threads = (uint64_t)n * COOP_W;
+        PT_LAUNCH(k_trace_coop, (uint32_t)((threads + 127) / 128), 128, 0, st, s->view(), rays, n, flags, hit_tri,
+                  hit_t, hit_uv);
+    } else {
+        PT_LAUNCH(k_trace, (n + 127) / 128, 128, 0, st, s->view(), rays, n, flags, hit_tri, hit_t, hit_uv);
+    }
     s->launches++;
     PT_CUDA_TRY(cudaGetLastError());
     return PT_OK;

@@ -180,7 +180,7 @@ __device__ __forceinline__ bool refract3(float3 wo, float3 h, float eta, float3&
 // A and the lobe's directional albedo E have no closed form: per material the library keeps
 // a fuzz block of FUZZ_FLOATS floats -- fw, fc[3], a (= max(fuzz_roughness, 0.2)^2), 3 unused,
 // then A as a Chebyshev series in x = 2 mu - 1 (FUZZ_A_TERMS) and E as one in
-// x = 2 sqrt(mu) - 1 (FUZZ_E_TERMS; E behaves like mu log mu at grazing) -- computed by
+// x = 2 mu^(1/4) - 1 (FUZZ_E_TERMS; E behaves like mu log mu at grazing) -- computed by
 // quadrature when the material table is made (pt_fuzz.cu).  Only materials with fuzz read it.
 constexpr int FUZZ_HEAD = 8, FUZZ_A_TERMS = 16, FUZZ_E_TERMS = 32;
 constexpr int FUZZ_FLOATS = FUZZ_HEAD + FUZZ_A_TERMS + FUZZ_E_TERMS;
@@ -201,7 +201,8 @@ __device__ __forceinline__ float fuzz_area(const float* fz, float mu) {
     return cheb_eval<FUZZ_A_TERMS>(fz + FUZZ_HEAD, 2.0f * fminf(fmaxf(mu, 0.0f), 1.0f) - 1.0f);
 }
 __device__ __forceinline__ float fuzz_albedo(const float* fz, float mu) {
-    return cheb_eval<FUZZ_E_TERMS>(fz + FUZZ_HEAD + FUZZ_A_TERMS, 2.0f * sqrtf(fminf(fmaxf(mu, 0.0f), 1.0f)) - 1.0f);
+    return cheb_eval<FUZZ_E_TERMS>(fz + FUZZ_HEAD + FUZZ_A_TERMS,
+                                   2.0f * sqrtf(sqrtf(fminf(fmaxf(mu, 0.0f), 1.0f))) - 1.0f);
 }
 __device__ __forceinline__ float sheen_D(float cos_m, float alpha) {
     const float s2 = fmaxf(0.0f, 1.0f - cos_m * cos_m);
@@ -889,6 +890,267 @@ __device__ __forceinline__ bool trace_any_t(const DScene& S, float3 o, float3 d,
     while (!any_step<COUNT>(S, st, stack, tc)) {
     }
     return st.hit;
+}
+
+// ---- cooperative traversal: one ray per group of 8 lanes ----
+// The per-lane traversal above keeps a warp's 32 rays in 32 lanes; rays need different numbers
+// of nodes and leaves, so most lanes idle (about 9 of 32 active per instruction on the 1080p
+// CAD frame).  Here a group of COOP_W = 8 lanes carries one ray (4 rays per warp): lane j of
+// the group tests child slot j of the node, and the triangles of the node's hit leaves are
+// spread over the group's lanes.  The group visits exactly the nodes the per-lane traversal
+// visits, in the same order: the same box tests against the same current closest t, the same
+// nearest child descended into, and the other hit children pushed in the same order -- the
+// per-lane loop pushes, at each later internal hit, either that child or (when it is nearer
+// than every earlier one) the previous nearest; an exclusive prefix minimum over the group's
+// lanes gives each lane what the loop pushes at its slot and where.  So the hit, and the node
+// and triangle counts of the counting variant, equal the per-lane traversal's.
+constexpr uint32_t COOP_W = 8;
+constexpr uint32_t COOP_LIST = 64;   // triangle slots: 8 leaves of at most 7 triangles
+
+// per group, in shared memory: the node stack (node, entry t bits) and the hit leaves'
+// triangle list of the current node
+struct CoopShared {
+    uint2 stack[PT_STACK];
+    uint32_t list[COOP_LIST];
+};
+
+struct CoopClosest {
+    WRay wr;
+    TravRay tr;
+    float tmax;
+    float hit_t;                      // the group's closest t so far (the same in every lane)
+    uint32_t node, budget;
+    int sp;
+    bool fail;
+    float bt, bu, bv;                 // this lane's closest hit among the triangles it tested
+    uint32_t btri, borig;
+};
+
+__device__ __forceinline__ void coop_closest_init(const DScene& S, float3 o, float3 d, float tmax, CoopClosest& st) {
+    st.wr = make_wray(o, d);
+    st.tr = make_trav(o, d);
+    st.tmax = tmax;
+    st.hit_t = tmax;
+    st.node = 0;
+    st.sp = 0;
+    st.fail = false;
+    st.budget = (uint32_t)S.n_nodes + 1u;
+    st.bt = tmax;
+    st.bu = st.bv = 0.0f;
+    st.btri = PT_NO_HIT;
+    st.borig = PT_NO_HIT;
+}
+
+// box test of this lane's child slot; ib / lb: the group's internal / leaf hits (slot bits)
+__device__ __forceinline__ float coop_node_test(const NodeView& v, const TravRay& tr, float tmax, uint32_t gl,
+                                                uint32_t gm, uint32_t gbase, uint32_t& meta, uint32_t& ib,
+                                                uint32_t& lb) {
+    meta = byte_of(v.meta_lo, v.meta_hi, (int)gl);
+    float tn = -1.0f;
+    if (meta != 0u) {
+        NodeTest T;
+        node_setup(v, tr, T);
+        tn = child_test(T, (int)gl, tmax);
+    }
+    const bool hit = meta != 0u && tn >= 0.0f && tn <= tmax;
+    const bool is_int = (v.imask >> gl) & 1u;
+    ib = (__ballot_sync(gm, hit && is_int) >> gbase) & 0xffu;
+    lb = (__ballot_sync(gm, hit && !is_int) >> gbase) & 0xffu;
+    return tn;
+}
+
+// the triangles of the hit leaves (slot order, then triangle order) into the group's list;
+// returns their number
+__device__ __forceinline__ uint32_t coop_leaf_list(const NodeView& v, uint32_t meta, uint32_t lb, uint32_t gl,
+                                                   uint32_t gm, uint32_t* list) {
+    const uint32_t cnt = ((lb >> gl) & 1u) ? (meta >> 5) : 0u;
+    uint32_t x = cnt;
+#pragma unroll
+    for (uint32_t d = 1; d < COOP_W; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(gm, x, d, COOP_W);
+        if (gl >= d) x += y;
+    }
+    const uint32_t total = __shfl_sync(gm, x, COOP_W - 1, COOP_W);
+    const uint32_t first = v.tri_base + (meta & 31u);
+    for (uint32_t k = 0; k < cnt; ++k) list[x - cnt + k] = first + k;
+    __syncwarp(gm);
+    return total;
+}
+
+// one node of the closest-hit traversal by the group; true once the ray is finished
+template <bool COUNT>
+__device__ __forceinline__ bool coop_closest_step(const DScene& S, CoopClosest& st, CoopShared& sh, uint32_t gl,
+                                                  uint32_t gm, uint32_t gbase, TravCount& tc) {
+    __syncwarp(gm);   // the last pop's read of the stack comes before this node's pushes
+    if (S.n_nodes == 0) return true;
+    if (st.budget-- == 0u) {
+        if (gl == 0) atomicOr(S.err, 4u);
+        st.fail = true;
+        return true;
+    }
+    const NodeView v = load_node(S.nodes, st.node);
+    if (COUNT && gl == 0) tc.nodes++;
+    uint32_t meta, ib, lb;
+    const float tn = coop_node_test(v, st.tr, st.hit_t, gl, gm, gbase, meta, ib, lb);
+    const bool ih = (ib >> gl) & 1u;
+    const uint32_t child = v.child_base + __popc(v.imask & ((1u << gl) - 1u));
+    // inclusive prefix minimum of (t, child) over the internal hits in slot order; a later
+    // hit displaces an earlier one only when strictly nearer
+    float pt = ih ? tn : __int_as_float(0x7f800000);
+    uint32_t pc = child;
+#pragma unroll
+    for (uint32_t d = 1; d < COOP_W; d <<= 1) {
+        const float t2 = __shfl_up_sync(gm, pt, d, COOP_W);
+        const uint32_t c2 = __shfl_up_sync(gm, pc, d, COOP_W);
+        if (gl >= d && !(pt < t2)) { pt = t2; pc = c2; }
+    }
+    float ex_t = __shfl_up_sync(gm, pt, 1, COOP_W);
+    const uint32_t ex_c = __shfl_up_sync(gm, pc, 1, COOP_W);
+    if (gl == 0) ex_t = __int_as_float(0x7f800000);
+    const float near_t = __shfl_sync(gm, pt, COOP_W - 1, COOP_W);
+    const uint32_t near_c = __shfl_sync(gm, pc, COOP_W - 1, COOP_W);
+    // the j-th internal hit (j >= 1) pushes the displaced nearest or itself at stack slot sp + j - 1
+    const uint32_t n_int = __popc(ib);
+    const uint32_t n_push = n_int > 0u ? n_int - 1u : 0u;
+    if (st.sp + (int)n_push > PT_STACK) {
+        if (gl == 0) atomicOr(S.err, 1u);
+        st.fail = true;
+        return true;
+    }
+    const uint32_t j = __popc(ib & ((1u << gl) - 1u));
+    if (ih && j > 0u) {
+        const bool displaces = tn < ex_t;
+        sh.stack[st.sp + (int)j - 1] = displaces ? make_uint2(ex_c, __float_as_uint(ex_t))
+                                                 : make_uint2(child, __float_as_uint(tn));
+    }
+    st.sp += (int)n_push;
+    if (lb) {
+        const uint32_t total = coop_leaf_list(v, meta, lb, gl, gm, sh.list);
+        if (COUNT && gl == 0) tc.tris += total;
+        for (uint32_t b = 0; b < total; b += COOP_W) {
+            const uint32_t q = b + gl;
+            if (q < total) {
+                const uint32_t ti = sh.list[q];
+                const float4 a = __ldg(S.tris + 3u * ti), bb = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
+                float t, u, w;
+                if (tri_hit(st.wr, xyz(a), xyz(bb), xyz(c), st.tmax, t, u, w)) {
+                    const uint32_t orig = __float_as_uint(a.w);
+                    if (t < st.bt || (t == st.bt && orig < st.borig)) {
+                        st.bt = t; st.bu = u; st.bv = w; st.btri = ti; st.borig = orig;
+                    }
+                }
+            }
+        }
+        // t > 0 and +inf order like their bit patterns
+        st.hit_t = __uint_as_float(__reduce_min_sync(gm, __float_as_uint(st.bt)));
+    }
+    __syncwarp(gm);   // the pushes and the list are read by other lanes of the group
+    if (n_int > 0u && near_t <= st.hit_t) {
+        st.node = near_c;
+        return false;
+    }
+    while (st.sp > 0) {
+        const uint2 e = sh.stack[--st.sp];
+        if (__uint_as_float(e.y) <= st.hit_t) { st.node = e.x; return false; }
+    }
+    return true;
+}
+
+// the group's hit: the lexicographic minimum of (t, original triangle id) over its lanes.
+// Returns true in the one lane that holds it (lane 0 of the group for a miss).
+__device__ __forceinline__ bool coop_closest_finish(const CoopClosest& st, uint32_t gl, uint32_t gm, uint32_t gbase,
+                                                    HitRec& h) {
+    const uint32_t tb = __reduce_min_sync(gm, __float_as_uint(st.bt));
+    const bool at_t = __float_as_uint(st.bt) == tb && st.btri != PT_NO_HIT;
+    const uint32_t ob = __reduce_min_sync(gm, at_t ? st.borig : 0xffffffffu);
+    const uint32_t wl = (__ballot_sync(gm, at_t && st.borig == ob) >> gbase) & 0xffu;
+    const bool fail = st.fail;
+    if (wl == 0u || fail) {
+        h.t = fail ? st.hit_t : st.tmax;
+        h.u = h.v = 0.0f;
+        h.tri = PT_NO_HIT;
+        return gl == 0u;
+    }
+    h.t = st.bt; h.u = st.bu; h.v = st.bv; h.tri = st.btri;
+    return gl == (uint32_t)(__ffs(wl) - 1);
+}
+
+struct CoopAny {
+    WRay wr;
+    TravRay tr;
+    float tmax;
+    uint32_t node, budget;
+    int sp;
+    bool hit;
+};
+
+__device__ __forceinline__ void coop_any_init(const DScene& S, float3 o, float3 d, float tmax, CoopAny& st) {
+    st.wr = make_wray(o, d);
+    st.tr = make_trav(o, d);
+    st.tmax = tmax;
+    st.node = 0;
+    st.sp = 0;
+    st.hit = false;
+    st.budget = (uint32_t)S.n_nodes + 1u;
+}
+
+// one node of the any-hit traversal by the group (the per-lane order: the first internal hit
+// in slot order next, the others pushed in slot order; leaf triangles in slot order, counted
+// up to the first hit); true once the ray is finished (st.hit: occluded)
+template <bool COUNT>
+__device__ __forceinline__ bool coop_any_step(const DScene& S, CoopAny& st, CoopShared& sh, uint32_t gl, uint32_t gm,
+                                              uint32_t gbase, TravCount& tc) {
+    __syncwarp(gm);   // the last pop's read of the stack comes before this node's pushes
+    if (S.n_nodes == 0) return true;
+    if (st.budget-- == 0u) {
+        if (gl == 0) atomicOr(S.err, 4u);
+        return true;
+    }
+    const NodeView v = load_node(S.nodes, st.node);
+    if (COUNT && gl == 0) tc.nodes++;
+    uint32_t meta, ib, lb;
+    coop_node_test(v, st.tr, st.tmax, gl, gm, gbase, meta, ib, lb);
+    const uint32_t n_int = __popc(ib);
+    const uint32_t n_push = n_int > 0u ? n_int - 1u : 0u;
+    if (st.sp + (int)n_push > PT_STACK) {
+        if (gl == 0) atomicOr(S.err, 1u);
+        st.hit = true;
+        return true;
+    }
+    const uint32_t child = v.child_base + __popc(v.imask & ((1u << gl) - 1u));
+    const uint32_t j = __popc(ib & ((1u << gl) - 1u));
+    if (((ib >> gl) & 1u) && j > 0u) sh.stack[st.sp + (int)j - 1].x = child;
+    const uint32_t first_slot = ib ? (uint32_t)(__ffs(ib) - 1) : 0u;
+    const uint32_t next = __shfl_sync(gm, child, first_slot, COOP_W);
+    st.sp += (int)n_push;
+    if (lb) {
+        const uint32_t total = coop_leaf_list(v, meta, lb, gl, gm, sh.list);
+        for (uint32_t b = 0; b < total; b += COOP_W) {
+            const uint32_t q = b + gl;
+            bool h = false;
+            if (q < total) {
+                const uint32_t ti = sh.list[q];
+                const float4 a = __ldg(S.tris + 3u * ti), bb = __ldg(S.tris + 3u * ti + 1), c = __ldg(S.tris + 3u * ti + 2);
+                float t, u, w;
+                h = tri_hit(st.wr, xyz(a), xyz(bb), xyz(c), st.tmax, t, u, w);
+            }
+            const uint32_t hm = (__ballot_sync(gm, h) >> gbase) & 0xffu;
+            if (hm) {
+                if (COUNT && gl == 0) tc.tris += b + (uint32_t)__ffs(hm);
+                st.hit = true;
+                return true;
+            }
+        }
+        if (COUNT && gl == 0) tc.tris += total;
+    }
+    __syncwarp(gm);
+    if (n_int > 0u) {
+        st.node = next;
+        return false;
+    }
+    if (st.sp == 0) return true;
+    st.node = sh.stack[--st.sp].x;
+    return false;
 }
 
 // out-of-line entry points keep the megakernel's code and registers in check

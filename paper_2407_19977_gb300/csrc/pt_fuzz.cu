@@ -8,12 +8,19 @@
 // has a closed form.  One CTA per material integrates them and stores Chebyshev series:
 //   A: 16 terms in x = 2 mu - 1, from A at the 16 Chebyshev points, each a 1-D integral over
 //      theta_m with the azimuth done in closed form, split where the circle of azimuths
-//      starts to dip below the horizon of w (theta_m = asin(mu)), 48 Gauss points a piece;
-//   E: 32 terms in x = 2 sqrt(mu) - 1 (E behaves like mu log mu at grazing), from E at the
-//      32 Chebyshev points, each a 2-D integral: mu_i over the pieces [0, mu_o], [mu_o, 8 mu_o],
-//      [8 mu_o, 64 mu_o], ... (the integrand turns over at mu_i ~ mu_o, and D has a kink at
-//      mu_i = mu_o), 16 Gauss points a piece, the azimuth over [0, pi] (the integrand is even)
-//      with 48 Gauss points; A(mu_i) from its series.
+//      starts to dip below the horizon of w (theta_m = asin(mu));
+//   E: 32 terms in x = 2 mu^(1/4) - 1 (E behaves like mu log mu at grazing: in mu^(1/4) the
+//      series converges to about 1e-9), from E at the 32 Chebyshev points, each a 2-D
+//      integral: the polar range cut at mu_i = c, 4c, 16c, ... up to 1 with c = max(mu_o, 1e-6)
+//      (the integrand turns over at mu_i ~ mu_o and D has a kink at the mirror direction),
+//      each piece integrated over the polar angle (smooth through the pole), the azimuth over
+//      [0, pi] (the integrand is even) cut at pi - min(pi, 8 (mu_o + mu_hi)) next to the mirror
+//      direction; A(mu_i) from its series.
+// Everything is FP32.  The rules are Fejer's first rule (nodes cos((2k+1) pi / 2n), weights
+// from a cosine sum), whose nodes and weights FP32 evaluates to a few ulp (Newton-iterated
+// Gauss-Legendre weights lose up to 1e-3 in FP32 near the ends); sums are Kahan-compensated
+// per lane and combined across a warp by TwoSum.  D is evaluated from sin^2 of the
+// microfacet angle, formed without cancellation.
 #include <cmath>
 
 #include "pt_device.cuh"
@@ -23,37 +30,55 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kGA = 48;      // Gauss points per piece of the A integral
-constexpr int kGM = 16;      // per piece of the mu_i integral of E
-constexpr int kGP = 48;      // over the azimuth of E
-constexpr int kRatio = 8;    // growth of the mu_i pieces
-constexpr int kMaxPieces = 16;   // mu_o >= 3.6e-7 at the Chebyshev points needs 9
-constexpr double kPi = 3.14159265358979323846;
+constexpr int kNA = 48;      // Fejer points per piece of the A integral (theta_m)
+constexpr int kNT = 24;      // per polar piece of the E integral
+constexpr int kNP = 64;      // per azimuth part of the E integral
+constexpr float kFloor = 1e-6f;   // first polar cut of the E integral: max(mu_o, kFloor)
 
-// node j of the n-point Gauss-Legendre rule on [-1, 1]: a root of P_n by Newton's method
-// from cos(pi (j + 3/4) / (n + 1/2)); weight 2 / ((1 - x^2) P_n'(x)^2)
-__device__ void gauss_node(int n, int j, double* x_out, double* w_out) {
-    double x = cos(kPi * (j + 0.75) / (n + 0.5)), dp = 1.0;
-    for (int it = 0; it < 64; ++it) {
-        double p0 = 1.0, p1 = x;
-        for (int k = 2; k <= n; ++k) {
-            const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-            p0 = p1;
-            p1 = p2;
-        }
-        dp = n * (x * p1 - p0) / (x * x - 1.0);
-        const double dx = p1 / dp;
-        x -= dx;
-        if (fabs(dx) < 1e-15) break;
+// Kahan-compensated running sum: s - c is the sum of everything added
+struct KSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
     }
-    *x_out = x;
-    *w_out = 2.0 / ((1.0 - x * x) * dp * dp);
+};
+
+// sum over the warp of compensated partial sums: TwoSum of the leading parts, the rounding
+// errors and the lanes' compensations carried in a second word
+__device__ __forceinline__ float warp_ksum(const KSum& k) {
+    float hi = k.s, lo = -k.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = hi + h2, bb = s - hi;
+        const float e = (hi - (s - bb)) + (h2 - bb);
+        hi = s;
+        lo = lo + l2 + e;
+    }
+    return hi + lo;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// node k of Fejer's first n-point rule on [-1, 1]: x = cos(theta), theta = (2k+1) pi / (2n),
+// w = (2/n) (1 - 2 sum_{j=1}^{n/2} cos(2 j theta) / (4 j^2 - 1)); the cosine arguments are
+// reduced in integers (2 j theta = pi m / n, m = j (2k+1) mod 2n) and the sum runs from its
+// smallest terms
+__device__ void fejer_node(int n, int k, float* x_out, float* w_out) {
+    *x_out = cospif((float)(2 * k + 1) / (float)(2 * n));
+    KSum s;
+    for (int j = n / 2; j >= 1; --j) {
+        const int m = (j * (2 * k + 1)) % (2 * n);
+        s.add(cospif((float)m / (float)n) / (float)(4 * j * j - 1));
+    }
+    *w_out = (2.0f / (float)n) * (1.0f - 2.0f * (s.s - s.c));
+}
+
+// Charlie D from sin^2 of the microfacet angle
+__device__ __forceinline__ float charlie_D_s2(float s2, float alpha) {
+    return (2.0f + 1.0f / alpha) * powf(s2, 0.5f / alpha) * (0.5f * PT_INV_PI_F);
 }
 
 // Clenshaw sum of n Chebyshev terms (series in shared memory)
@@ -67,13 +92,25 @@ __device__ __forceinline__ float cheb_smem(const float* c, int n, float x) {
     return x * b1 - b2 + c[0];
 }
 
+// coefficient k of the n-term Chebyshev interpolant of values v at the points
+// cos(pi (j + 1/2) / n): (2/n) sum_j v_j cos(pi k (j + 1/2) / n), halved for k = 0
+__device__ float cheb_coef(const float* v, int n, int k) {
+    KSum s;
+    for (int j = 0; j < n; ++j) {
+        const int m = (k * (2 * j + 1)) % (4 * n);
+        s.add(v[j] * cospif((float)m / (float)(2 * n)));
+    }
+    const float c = (2.0f / (float)n) * (s.s - s.c);
+    return k == 0 ? 0.5f * c : c;
+}
+
 // one material per CTA; raw rows of PT_OPENPBR_FLOATS floats; out FUZZ_FLOATS per row (the
 // head fw, fc[3], a, then the A and E series; zeros for a row without fuzz)
 __global__ void __launch_bounds__(kThreads) k_fuzz_series(const float* __restrict__ raw, uint32_t n,
                                                           float* __restrict__ out) {
-    __shared__ double ga_x[kGA], ga_w[kGA], gm_x[kGM], gm_w[kGM], gp_x[kGP], gp_w[kGP];
+    __shared__ float fa_x[kNA], fa_w[kNA], ft_x[kNT], ft_w[kNT], fp_x[kNP], fp_w[kNP];
     __shared__ float a_val[FUZZ_A_TERMS], e_val[FUZZ_E_TERMS], c_a[FUZZ_A_TERMS];
-    __shared__ float gp_c[kGP], gp_s[kGP];   // cos, sin of the azimuth nodes
+    __shared__ float piece_mu[kWarps][kNT], piece_s[kWarps][kNT], piece_k[kWarps][kNT];
     const uint32_t row = blockIdx.x;
     if (row >= n) return;
     const float* v = raw + (size_t)PT_OPENPBR_FLOATS * row;
@@ -86,29 +123,26 @@ __global__ void __launch_bounds__(kThreads) k_fuzz_series(const float* __restric
     const float r = fmaxf(v[33], 0.2f);
     const float alpha = r * r;
     if (t < FUZZ_HEAD) o[t] = t < 4 ? v[29 + t] : (t == 4 ? alpha : 0.0f);   // fw, fc, a
-    if (t < kGA) gauss_node(kGA, t, &ga_x[t], &ga_w[t]);
-    else if (t < kGA + kGM) gauss_node(kGM, t - kGA, &gm_x[t - kGA], &gm_w[t - kGA]);
-    else if (t < kGA + kGM + kGP) gauss_node(kGP, t - kGA - kGM, &gp_x[t - kGA - kGM], &gp_w[t - kGA - kGM]);
-    __syncthreads();
-    if (t < kGP) {
-        const double ph = 0.5 * kPi * (1.0 + gp_x[t]);
-        gp_c[t] = (float)cos(ph);
-        gp_s[t] = (float)sin(ph);
-    }
+    if (t < kNA) fejer_node(kNA, t, &fa_x[t], &fa_w[t]);
+    else if (t < kNA + kNT) fejer_node(kNT, t - kNA, &ft_x[t - kNA], &ft_w[t - kNA]);
+    else if (t < kNA + kNT + kNP) fejer_node(kNP, t - kNA - kNT, &fp_x[t - kNA - kNT], &fp_w[t - kNA - kNT]);
     __syncthreads();
 
-    // A at the Chebyshev points mu_j = (1 + cos(pi (j + 1/2) / 16)) / 2: one warp per point
+    // A at the Chebyshev points mu_j = (1 + cos(pi (j + 1/2) / 16)) / 2 = cos^2(pi (j + 1/2) / 32):
+    // one warp per point, lanes over the nodes of both pieces
     for (int j = warp; j < FUZZ_A_TERMS; j += kWarps) {
-        const double mu = 0.5 * (1.0 + cos(kPi * (j + 0.5) / FUZZ_A_TERMS));
-        const double st = sqrt(fmax(0.0, 1.0 - mu * mu)), split = asin(mu);
-        double acc = 0.0;
-        for (int q = lane; q < 2 * kGA; q += 32) {
-            const int g = q % kGA;
-            const bool outer = q >= kGA;
-            const double lo = outer ? split : 0.0, hi = outer ? 0.5 * kPi : split;
-            const double th = 0.5 * (hi + lo) + 0.5 * (hi - lo) * ga_x[g], w = 0.5 * (hi - lo) * ga_w[g];
-            const float ct = (float)cos(th), sn = (float)sin(th);
-            const float b = (float)mu * ct, a = (float)st * sn;
+        const float cq = cospif((j + 0.5f) / (2.0f * FUZZ_A_TERMS));
+        const float mu = cq * cq;
+        const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu)), split = asinf(mu);
+        KSum acc;
+        for (int q = lane; q < 2 * kNA; q += 32) {
+            const int g = q % kNA;
+            const bool outer = q >= kNA;
+            const float lo = outer ? split : 0.0f, hi = outer ? 0.5f * PT_PI_F : split;
+            const float th = 0.5f * (hi + lo) + 0.5f * (hi - lo) * fa_x[g], w = 0.5f * (hi - lo) * fa_w[g];
+            float sn, ct;
+            sincosf(th, &sn, &ct);
+            const float b = mu * ct, a = st * sn;
             float inner;
             if (b >= a) {
                 inner = 2.0f * PT_PI_F * b;
@@ -116,58 +150,66 @@ __global__ void __launch_bounds__(kThreads) k_fuzz_series(const float* __restric
                 const float c = -b / a;
                 inner = 2.0f * a * sqrtf(fmaxf(0.0f, 1.0f - c * c)) + 2.0f * b * acosf(c);
             }
-            acc += w * (double)(sheen_D(ct, alpha) * sn * inner);
+            acc.add(w * (charlie_D_s2(sn * sn, alpha) * sn * inner));
         }
-        acc = warp_sum(acc);
-        if (lane == 0) a_val[j] = (float)acc;
+        const float s = warp_ksum(acc);
+        if (lane == 0) a_val[j] = s;
     }
     __syncthreads();
-    if (t < FUZZ_A_TERMS) {
-        double c = 0.0;
-        for (int j = 0; j < FUZZ_A_TERMS; ++j) c += a_val[j] * cos(kPi * t * (j + 0.5) / FUZZ_A_TERMS);
-        c *= 2.0 / FUZZ_A_TERMS;
-        if (t == 0) c *= 0.5;
-        c_a[t] = (float)c;
-    }
+    if (t < FUZZ_A_TERMS) c_a[t] = cheb_coef(a_val, FUZZ_A_TERMS, t);
     __syncthreads();
 
-    // E at the Chebyshev points of x = 2 sqrt(mu) - 1: one warp per point
+    // E at the Chebyshev points of x = 2 mu^(1/4) - 1: mu^(1/4) = cos^2(pi (j + 1/2) / 64);
+    // one warp per point
     for (int j = warp; j < FUZZ_E_TERMS; j += kWarps) {
-        const double sq = 0.5 * (1.0 + cos(kPi * (j + 0.5) / FUZZ_E_TERMS));
-        const float mu_o = (float)(sq * sq);
+        const float cq = cospif((j + 0.5f) / (2.0f * FUZZ_E_TERMS));
+        const float q = cq * cq, q2 = q * q;
+        const float mu_o = q2 * q2;
         const float so = sqrtf(fmaxf(0.0f, 1.0f - mu_o * mu_o));
         const float a_o = cheb_smem(c_a, FUZZ_A_TERMS, 2.0f * mu_o - 1.0f);
-        double acc = 0.0;
-        double lo = 0.0, hi = mu_o;
-        for (int piece = 0; piece < kMaxPieces && lo < 1.0; ++piece) {
-            for (int i = 0; i < kGM; ++i) {
-                const double mi_d = 0.5 * (hi + lo) + 0.5 * (hi - lo) * gm_x[i];
-                const double wm = 0.5 * (hi - lo) * gm_w[i];
-                const float mi = (float)mi_d, si = sqrtf(fmaxf(0.0f, 1.0f - mi * mi));
+        KSum acc;
+        float lo = 0.0f, hi = fmaxf(mu_o, kFloor);
+        while (lo < 1.0f) {
+            const float t0 = acosf(hi), t1 = acosf(lo);
+            const float cut = fminf(PT_PI_F, 8.0f * (mu_o + hi));
+            if (lane < kNT) {
+                const float th = 0.5f * (t0 + t1) + 0.5f * (t1 - t0) * ft_x[lane];
+                float si, mi;
+                sincosf(th, &si, &mi);
                 const float a_i = cheb_smem(c_a, FUZZ_A_TERMS, 2.0f * mi - 1.0f);
-                const float den = 4.0f * (a_i * mu_o + a_o * mi - mi * mu_o);
-                for (int p = lane; p < kGP; p += 32) {
-                    const double wp = 0.5 * kPi * gp_w[p];
-                    const float hx = si * gp_c[p] + so, hy = si * gp_s[p], hz = mi + mu_o;
-                    const float cz = hz * rsqrtf(hx * hx + hy * hy + hz * hz);
-                    acc += wm * wp * (double)(sheen_D(cz, alpha) * mi / den);
+                piece_mu[warp][lane] = mi;
+                piece_s[warp][lane] = si;
+                // polar weight times mu_i sin(theta_i) / (4 (A_i mu_o + A_o mu_i - mu_i mu_o))
+                piece_k[warp][lane] = 0.5f * (t1 - t0) * ft_w[lane] * mi * si /
+                                      (4.0f * (a_i * mu_o + a_o * mi - mi * mu_o));
+            }
+            __syncwarp();
+            for (int part = 0; part < 2; ++part) {
+                const float p0 = part == 0 ? 0.0f : PT_PI_F - cut, p1 = part == 0 ? PT_PI_F - cut : PT_PI_F;
+                if (!(p1 > p0)) continue;
+                for (int idx = lane; idx < kNT * kNP; idx += 32) {
+                    const int i = idx / kNP, p = idx % kNP;
+                    const float ph = 0.5f * (p0 + p1) + 0.5f * (p1 - p0) * fp_x[p];
+                    const float wp = 0.5f * (p1 - p0) * fp_w[p];
+                    float sp, cp;
+                    sincosf(ph, &sp, &cp);
+                    const float mi = piece_mu[warp][i], si = piece_s[warp][i];
+                    const float hx = si * cp + so, hy = si * sp, hz = mi + mu_o;
+                    const float hxy = hx * hx + hy * hy;
+                    const float s2 = hxy / (hxy + hz * hz);
+                    acc.add(wp * piece_k[warp][i] * charlie_D_s2(s2, alpha));
                 }
             }
+            __syncwarp();
             lo = hi;
-            hi = fmin(hi * kRatio, 1.0);
+            hi = fminf(4.0f * lo, 1.0f);
         }
-        acc = 2.0 * warp_sum(acc);
-        if (lane == 0) e_val[j] = (float)acc;
+        const float s = 2.0f * warp_ksum(acc);
+        if (lane == 0) e_val[j] = s;
     }
     __syncthreads();
     if (t < FUZZ_A_TERMS) o[FUZZ_HEAD + t] = c_a[t];
-    if (t < FUZZ_E_TERMS) {
-        double c = 0.0;
-        for (int j = 0; j < FUZZ_E_TERMS; ++j) c += e_val[j] * cos(kPi * t * (j + 0.5) / FUZZ_E_TERMS);
-        c *= 2.0 / FUZZ_E_TERMS;
-        if (t == 0) c *= 0.5;
-        o[FUZZ_HEAD + FUZZ_A_TERMS + t] = (float)c;
-    }
+    if (t < FUZZ_E_TERMS) o[FUZZ_HEAD + FUZZ_A_TERMS + t] = cheb_coef(e_val, FUZZ_E_TERMS, t);
 }
 
 }  // namespace

@@ -838,6 +838,133 @@ __global__ void __launch_bounds__(128) k_wf_shadow(WfParams P) {
     }
 }
 
+// Cooperative variants of the two traversal passes (PT_TRAVERSAL_COOP): a group of COOP_W = 8
+// lanes carries one ray (pt_device.cuh, coop_*), so a warp holds 4 rays and its lanes test a
+// node's 8 child boxes, or a node's leaf triangles, side by side.  A warp claims 32 queue
+// slots with one atomic and hands them out one by one as its groups finish their rays; the
+// warp leaves once the queue is drained and its groups are done.  Hits, node and triangle
+// counts equal the per-lane kernels' above.  Measured on the 1080p CAD frame: 20 of 32 lanes
+// active per instruction (per-lane: 9), but every lane of a group decodes and sets up the
+// node and takes part in the scans, so a ray costs 5x the thread instructions and the pass
+// takes 2.7x as long; the per-lane kernels stay the default.
+__device__ __forceinline__ void coop_hand_out(uint32_t* head, uint32_t count, uint32_t lane, uint32_t gbase,
+                                              bool active, uint32_t& wb, uint32_t& we, bool& drained,
+                                              uint32_t& taken) {
+    // taken: the slot handed to this lane's group (~0u: none)
+    taken = 0xffffffffu;
+    uint32_t idle = __ballot_sync(0xffffffffu, !active) & 0x01010101u;
+    while (idle != 0u && !drained) {
+        if (wb >= we) {
+            uint32_t b = 0;
+            if (lane == 0) b = atomicAdd(head, 32u);
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (b >= count) { drained = true; break; }
+            wb = b;
+            we = min(b + 32u, count);
+        }
+        if (gbase == (uint32_t)(__ffs(idle) - 1)) taken = wb;
+        ++wb;
+        idle &= idle - 1u;
+    }
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_wf_trace_coop(WfParams P, int in_q) {
+    __shared__ uint32_t hist[MAX_SORT_KEYS];
+    __shared__ CoopShared gsh[128 / COOP_W];
+    if (P.counters[C_TAIL]) return;
+    const bool sort = P.n_keys > 0;
+    if (sort)
+        for (uint32_t k = threadIdx.x; k < P.n_keys; k += blockDim.x) hist[k] = 0;
+    __syncthreads();
+    const uint32_t count = P.counters[in_q];
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&P.stats[ST_EXT], (unsigned long long)count);
+    const uint32_t lane = lane_id(), gl = lane & (COOP_W - 1u), gbase = lane & ~(COOP_W - 1u);
+    const uint32_t gm = 0xffu << gbase;
+    CoopShared& sh = gsh[threadIdx.x / COOP_W];
+    TravCount tc = {0, 0};
+    CoopClosest st;
+    uint32_t slot = 0, wb = 0, we = 0;
+    bool active = false, drained = false;
+    for (;;) {
+        uint32_t taken;
+        coop_hand_out(&P.counters[C_HEAD_TRACE], count, lane, gbase, active, wb, we, drained, taken);
+        if (taken != 0xffffffffu) {
+            slot = taken;
+            active = true;
+            const float4 ro = P.ray_o[in_q][slot], rd = P.ray_d[in_q][slot];
+            coop_closest_init(P.S, xyz(ro), xyz(rd), __int_as_float(0x7f800000), st);
+        }
+        if (__ballot_sync(0xffffffffu, active) == 0u) break;
+        if (active && coop_closest_step<COUNT>(P.S, st, sh, gl, gm, gbase, tc)) {
+            HitRec h;
+            if (coop_closest_finish(st, gl, gm, gbase, h)) {
+                P.hit[slot] = make_float4(h.t, h.u, h.v, __uint_as_float(h.tri));
+                if (sort) {
+                    const uint32_t key = hit_key(P.S, h, P.n_keys - 2);
+                    P.keys[slot] = key;
+                    atomicAdd(&hist[key], 1u);
+                }
+            }
+            active = false;
+        }
+    }
+    if (COUNT) {
+        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris);
+        if (lane == 0) {
+            atomicAdd(&P.stats[ST_NODES], nn);
+            atomicAdd(&P.stats[ST_TRIS], nt);
+        }
+    }
+    if (sort) {
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < P.n_keys; k += blockDim.x)
+            if (hist[k]) atomicAdd(&P.counters[C_BUCKETS + k], hist[k]);
+    }
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_wf_shadow_coop(WfParams P) {
+    __shared__ CoopShared gsh[128 / COOP_W];
+    const uint32_t count = P.counters[C_SH];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && count) atomicAdd(&P.stats[ST_SHADOW], (unsigned long long)count);
+    const uint32_t lane = lane_id(), gl = lane & (COOP_W - 1u), gbase = lane & ~(COOP_W - 1u);
+    const uint32_t gm = 0xffu << gbase;
+    CoopShared& sh = gsh[threadIdx.x / COOP_W];
+    TravCount tc = {0, 0};
+    CoopAny st;
+    uint32_t slot = 0, wb = 0, we = 0;
+    bool active = false, drained = false;
+    for (;;) {
+        uint32_t taken;
+        coop_hand_out(&P.counters[C_HEAD_SHADOW], count, lane, gbase, active, wb, we, drained, taken);
+        if (taken != 0xffffffffu) {
+            slot = taken;
+            active = true;
+            const float4 so = P.sh_o[slot], sd = P.sh_d[slot];
+            coop_any_init(P.S, xyz(so), xyz(sd), so.w, st);
+        }
+        if (__ballot_sync(0xffffffffu, active) == 0u) break;
+        if (active && coop_any_step<COUNT>(P.S, st, sh, gl, gm, gbase, tc)) {
+            if (!st.hit && gl == 0) {
+                const uint32_t id = __float_as_uint(P.sh_d[slot].w);
+                const float4 c = P.sh_c[slot];
+                float4 L = P.radiance[id];
+                L.x += c.x; L.y += c.y; L.z += c.z;
+                P.radiance[id] = L;
+            }
+            active = false;
+        }
+    }
+    if (COUNT) {
+        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris);
+        if (lane == 0) {
+            atomicAdd(&P.stats[ST_SH_NODES], nn);
+            atomicAdd(&P.stats[ST_SH_TRIS], nt);
+        }
+    }
+}
+
 // Tail of a wave: when few paths are left, a per-bounce kernel lasts about as long as its
 // slowest ray (a chain of dependent node and triangle loads), and the wave pays that once per
 // stage and bounce.  This kernel takes the remaining queue instead and carries each path to
@@ -1048,6 +1175,35 @@ static pt_status ensure_restir_buffers(WaveBuffers& w) {
 }
 
 static int g_trace_blocks_per_sm = 0, g_shade_blocks_per_sm = 0, g_shadow_blocks_per_sm = 0, g_tail_blocks_per_sm = 0;
+static int g_coop_trace_bps = 0, g_coop_shadow_bps = 0;
+
+// resident blocks per SM of the per-bounce kernels, queried once
+static void wf_occupancy() {
+    if (g_trace_blocks_per_sm != 0) return;
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_trace<false>, 128, 0);
+    g_trace_blocks_per_sm = std::max(b, 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shade<false, false>, 128, 0);
+    g_shade_blocks_per_sm = std::max(b, 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shadow<false>, 128, 0);
+    g_shadow_blocks_per_sm = std::max(b, 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_trace_coop<false>, 128, 0);
+    g_coop_trace_bps = std::max(b, 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shadow_coop<false>, 128, 0);
+    g_coop_shadow_bps = std::max(b, 1);
+}
+
+// the closest-hit and shadow passes, per-lane or cooperative (the same hits and counts)
+template <bool COUNT>
+static void launch_trace(bool coop, int sms, cudaStream_t st, const WfParams& P, int in_q) {
+    if (coop) PT_LAUNCH(k_wf_trace_coop<COUNT>, sms * g_coop_trace_bps, 128, 0, st, P, in_q);
+    else PT_LAUNCH(k_wf_trace<COUNT>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
+}
+template <bool COUNT>
+static void launch_shadow(bool coop, int sms, cudaStream_t st, const WfParams& P) {
+    if (coop) PT_LAUNCH(k_wf_shadow_coop<COUNT>, sms * g_coop_shadow_bps, 128, 0, st, P);
+    else PT_LAUNCH(k_wf_shadow<COUNT>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
+}
 
 pt_status pt_wavefront_tail_limit(int* out) {
     if (g_tail_blocks_per_sm == 0) {
@@ -1063,7 +1219,7 @@ pt_status pt_wavefront_tail_limit(int* out) {
 // sample and seed, live in device memory): equal keys mean the same captured graph replays.
 struct WfGraphKey {
     WfParams P;             // with the per-wave fields cleared
-    uint32_t spp, npix_total, pix_chunk, samp_per_wave, tail_limit, tail_grid, count;
+    uint32_t spp, npix_total, pix_chunk, samp_per_wave, tail_limit, tail_grid, count, coop;
     int sms, trace_bps, shade_bps, shadow_bps;
     const void* nrc;        // the radiance cache the launches read and train
 };
@@ -1077,6 +1233,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     // waves hold whole samples of a pixel range: pixel chunk <= cap, then samples per wave;
     // with ReSTIR the chunk is the whole window (the spatial pass reads any pixel of it)
     const bool restir = o.restir != nullptr;
+    const bool coop = o.traversal == PT_TRAVERSAL_COOP;
     const uint32_t pix_chunk = restir ? npix_total : std::min(npix_total, cap);
     const uint32_t samp_per_wave = std::max(1u, std::min(spp, cap / pix_chunk));
     pt_status r = ensure_wave(s->wave, pix_chunk * samp_per_wave);
@@ -1088,15 +1245,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     }
     const bool sort = o.sort_by_material == 1 || (o.sort_by_material < 0 && s->n_mats + 2 <= MAX_SORT_KEYS && s->n_mats > 1);
     const uint32_t n_keys = (sort && s->n_mats + 2 <= MAX_SORT_KEYS) ? s->n_mats + 2 : 0;
-    if (g_trace_blocks_per_sm == 0) {
-        int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_trace<false>, 128, 0);
-        g_trace_blocks_per_sm = std::max(b, 1);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shade<false, false>, 128, 0);
-        g_shade_blocks_per_sm = std::max(b, 1);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shadow<false>, 128, 0);
-        g_shadow_blocks_per_sm = std::max(b, 1);
-    }
+    wf_occupancy();
     if (g_tail_blocks_per_sm == 0) {
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_tail<true, false, false>, 128, 0);
@@ -1159,6 +1308,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
         key.P = P;
         key.spp = spp; key.npix_total = npix_total; key.pix_chunk = pix_chunk; key.samp_per_wave = samp_per_wave;
         key.tail_limit = tail_limit; key.tail_grid = tail_grid; key.count = count ? 1u : 0u;
+        key.coop = coop ? 1u : 0u;
         key.sms = sms; key.trace_bps = g_trace_blocks_per_sm; key.shade_bps = g_shade_blocks_per_sm;
         key.shadow_bps = g_shadow_blocks_per_sm;
         key.nrc = o.nrc;
@@ -1233,8 +1383,8 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                         ++launches;
                     }
                     e = begin(PT_K_TRACE);
-                    if (count) PT_LAUNCH(k_wf_trace<true>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
-                    else PT_LAUNCH(k_wf_trace<false>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
+                    if (count) launch_trace<true>(coop, sms, st, P, in_q);
+                    else launch_trace<false>(coop, sms, st, P, in_q);
                     end(e);
                     ++launches;
                     if (n_keys) {
@@ -1258,8 +1408,8 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                     else launch_shade<false, false>(s->has_fuzz, shade_grid, st, P, in_q, out_q, k);
                     end(e);
                     e = begin(PT_K_SHADOW);
-                    if (count) PT_LAUNCH(k_wf_shadow<true>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
-                    else PT_LAUNCH(k_wf_shadow<false>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
+                    if (count) launch_shadow<true>(coop, sms, st, P);
+                    else launch_shadow<false>(coop, sms, st, P);
                     end(e);
                     launches += 2;
                 }
@@ -1376,6 +1526,7 @@ extern "C" pt_status pt_render(pt_scene* s, const pt_camera* camera, uint32_t sp
                      (uint64_t)o.crop_y0 + acc->height <= camera->height, "window outside the frame");
     PT_CHECK_ARG(acc->spp_done + spp < (1ull << 32), "sample index overflows 32 bits");
     PT_CHECK_ARG(o.mode <= PT_MODE_MEGAKERNEL, "unknown mode");
+    PT_CHECK_ARG(o.traversal <= PT_TRAVERSAL_COOP, "unknown traversal");
     PT_CHECK_ARG(!o.nrc || o.mode != PT_MODE_MEGAKERNEL, "the radiance cache runs in wavefront mode");
     if (o.restir) {
         const pt_restir_opts& ro = *o.restir;
@@ -1556,25 +1707,19 @@ constexpr size_t NOALLOC_BYTES =
     (C_BUCKETS + MAX_SORT_KEYS) * sizeof(uint32_t);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
-// device address of g_noalloc_scratch per device, resolved on the first call on that device
-static std::mutex g_noalloc_mutex;
-static void* g_noalloc_addr[64] = {nullptr};
-
+// Device address of g_noalloc_scratch in the current context.  In host code the array's name
+// is only a host-side stand-in, so every call asks the runtime for the address that goes to
+// the kernels.  The lookup allocates nothing once the library's device code is loaded in the
+// context; looking it up on each call, rather than caching it per device ordinal, keeps the
+// address right after cudaDeviceReset or under a context other than the primary one.
 static pt_status noalloc_scratch(void** out) {
-    int dev = 0;
-    PT_CUDA_TRY(cudaGetDevice(&dev));
-    PT_CHECK_ARG(dev >= 0 && dev < 64, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            pt_set_error(std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
-            return PT_ERR_CUDA;
-        }
-        g_noalloc_addr[dev] = p;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        pt_set_error(std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
+        return PT_ERR_CUDA;
     }
-    *out = g_noalloc_addr[dev];
+    *out = p;
     return PT_OK;
 }
 
@@ -1599,6 +1744,8 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
     PT_CHECK_ARG(o.nrc == nullptr, "the radiance cache needs allocations: use pt_render");
     PT_CHECK_ARG(o.restir == nullptr, "ReSTIR DI needs allocations: use pt_render");
     PT_CHECK_ARG(o.kernel_ms == nullptr && o.kernel_launches == nullptr, "kernel timing is not available here");
+    PT_CHECK_ARG((o.flags & ~(uint32_t)(FLAG_NO_NEE | FLAG_NO_RR)) == 0,
+                 "only PT_FLAG_NO_NEE and PT_FLAG_NO_RR are available here (no PT_FLAG_COUNT)");
     if (spp == 0) return PT_OK;
     void* base = nullptr;
     pt_status r = noalloc_scratch(&base);
@@ -1620,15 +1767,7 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
     const uint32_t samp_per_wave = std::max(1u, std::min(spp, NOALLOC_MAX_PATHS / npix));
     const bool sort = o.sort_by_material == 1 || (o.sort_by_material < 0 && s->n_mats + 2 <= MAX_SORT_KEYS && s->n_mats > 1);
     const uint32_t n_keys = (sort && s->n_mats + 2 <= MAX_SORT_KEYS) ? s->n_mats + 2 : 0;
-    if (g_trace_blocks_per_sm == 0) {
-        int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_trace<false>, 128, 0);
-        g_trace_blocks_per_sm = std::max(b, 1);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shade<false, false>, 128, 0);
-        g_shade_blocks_per_sm = std::max(b, 1);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_shadow<false>, 128, 0);
-        g_shadow_blocks_per_sm = std::max(b, 1);
-    }
+    wf_occupancy();
     const int sms = pt_num_sms();
     WfParams P;
     std::memset(&P, 0, sizeof(P));
@@ -1661,7 +1800,7 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
         for (uint32_t k = 0; k <= max_depth; ++k) {
             const int in_q = (int)(k & 1u), out_q = (int)((k + 1) & 1u);
             PT_LAUNCH(k_wf_setup, 1, 256, 0, st, w.counters, out_q, n_keys);
-            PT_LAUNCH(k_wf_trace<false>, sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
+            launch_trace<false>(false, sms, st, P, in_q);
             launches += 2;
             if (n_keys) {
                 PT_LAUNCH(k_wf_sort_scan, 1, MAX_SORT_KEYS, 0, st, w.counters, n_keys);
@@ -1669,7 +1808,7 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
                 launches += 2;
             }
             launch_shade<false, false>(s->has_fuzz, sms * g_shade_blocks_per_sm, st, P, in_q, out_q, k);
-            PT_LAUNCH(k_wf_shadow<false>, sms * g_shadow_blocks_per_sm, 128, 0, st, P);
+            launch_shadow<false>(false, sms, st, P);
             launches += 2;
         }
         PT_LAUNCH(k_wf_accum, (npix + 255) / 256, 256, 0, st, P);

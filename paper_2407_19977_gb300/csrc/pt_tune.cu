@@ -134,6 +134,16 @@ extern "C" pt_status pt_autotune(pt_scene* s, const pt_camera* camera, uint32_t 
         if (r != PT_OK) return r;
         if (t < win_t) { win_t = t; win = o; }
     }
+    // the traversal passes of the winning wavefront schedule: one ray per lane (the default)
+    // or one ray per group of 8 lanes
+    if (win.mode == PT_MODE_WAVEFRONT) {
+        pt_render_opts o = win;
+        o.traversal = PT_TRAVERSAL_COOP;
+        float t = 0.0f;
+        r = run(o, &t);
+        if (r != PT_OK) return r;
+        if (t < win_t) { win_t = t; win = o; }
+    }
     *best = win;
     if (best_ms) *best_ms = win_t;
     s->tuned = true;

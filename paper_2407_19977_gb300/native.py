@@ -47,7 +47,8 @@ class pt_render_opts(C.Structure):
     _fields_ = [("crop_x0", u32), ("crop_y0", u32), ("flags", u32), ("mode", u32), ("wave_paths", u32),
                 ("sort_by_material", C.c_int32), ("block_size", u32), ("sample_out", vp), ("nrc", vp),
                 ("nrc_train", u32), ("kernel_ms", C.POINTER(f32)), ("kernel_launches", C.POINTER(u32)),
-                ("tail_paths", C.c_int32), ("use_graph", u32), ("restir", C.POINTER(pt_restir_opts))]
+                ("tail_paths", C.c_int32), ("use_graph", u32), ("restir", C.POINTER(pt_restir_opts)),
+                ("traversal", u32)]
 
 
 class pt_bvh_opts(C.Structure):
@@ -82,11 +83,13 @@ class pt_nrc_opts(C.Structure):
 
 
 PT_OK = 0
+PT_ERR_INVALID_ARG = 1
 STATUS = ["PT_OK", "PT_ERR_INVALID_ARG", "PT_ERR_OOM", "PT_ERR_CUDA", "PT_ERR_NOT_BUILT", "PT_ERR_TIMEOUT",
           "PT_ERR_QUEUE_OVERFLOW", "PT_ERR_UNSUPPORTED"]
 PT_FLAG_NO_NEE = 1
 PT_FLAG_NO_RR = 2
 PT_FLAG_COUNT = 4
+PT_TRAVERSAL_AUTO, PT_TRAVERSAL_PER_LANE, PT_TRAVERSAL_COOP = 0, 1, 2
 PT_TUNE_BVH = 1
 PT_TONEMAP_SRGB = 1
 KERNEL_KINDS = ("raygen", "trace", "sort", "shade", "shadow", "accum", "tail", "restir")

@@ -15,10 +15,16 @@ torch = pytest.importorskip("torch")
 
 L, LOG2T = 8, 12
 
+# (levels, log2 entries per level, coarsest resolution, growth per level; 0 = up to 2048):
+# a small grid whose levels are mostly dense, and the cache the renderer uses (16 levels of
+# 2^19 entries, resolutions 16 ... 2048, hashed from the fifth level on)
+GRIDS = {"small": (8, 12, 4, 1.6), "production": (16, 19, 16, 0.0)}
 
-def _make(seed=0, lr=1e-2, batch=4096, tcgen05=False):
+
+def _make(seed=0, lr=1e-2, batch=4096, tcgen05=False, grid="small"):
     from paper_2407_19977_gb300 import api
-    return api.Nrc(n_levels=L, log2_table=LOG2T, base_resolution=4, per_level_scale=1.6, learning_rate=lr,
+    nl, lt, base, scale = GRIDS[grid]
+    return api.Nrc(n_levels=nl, log2_table=lt, base_resolution=base, per_level_scale=scale, learning_rate=lr,
                    batch=batch, seed=seed, tcgen05=tcgen05)
 
 
@@ -55,28 +61,36 @@ def _set_random_params(net, rng):
     return wn, gn
 
 
-def _oracle_params(wn, gn):
+def _oracle_params(wn, gn, grid="small"):
     """FP16-rounded copies, as the kernels read them."""
     h = lambda a: a.astype(np.float16).astype(np.float64)  # noqa: E731
     nh = 4 * 64 * 64
+    nl, lt, _, _ = GRIDS[grid]
     ws = [h(wn[i * 4096:(i + 1) * 4096]).reshape(64, 64) for i in range(4)] + [h(wn[nh:]).reshape(16, 64)[:3]]
-    table = h(gn).reshape(L, 2 ** LOG2T, 2)
+    table = h(gn).reshape(nl, 2 ** lt, 2)
     return ws, table
+
+
+def _resolutions(grid):
+    nl, _, base, scale = GRIDS[grid]
+    return onrc.level_resolutions(nl, base, scale)
 
 
 def _rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+@pytest.mark.parametrize("grid", ["small", "production"])
 @pytest.mark.parametrize("tcgen05", [False, True])
-def test_nrc_forward_matches_oracle(tcgen05):
+def test_nrc_forward_matches_oracle(tcgen05, grid):
     """Inference (fused encoding + MLP) on mma.sync or on tcgen05 with tensor-memory
-    accumulators, over ragged sizes around the 16- and 128-row tiles."""
+    accumulators, over ragged sizes around the 16- and 128-row tiles, on a small grid and on
+    the production cache (16 levels x 2^19 entries, resolutions 16 ... 2048)."""
     rng = np.random.default_rng(0)
-    net = _make(tcgen05=tcgen05)
+    net = _make(tcgen05=tcgen05, grid=grid)
     wn, gn = _set_random_params(net, rng)
-    ws, table = _oracle_params(wn, gn)
-    res = onrc.level_resolutions(L, 4, 1.6)
+    ws, table = _oracle_params(wn, gn, grid)
+    res = _resolutions(grid)
     for n in (5000, 1, 127, 128, 129):
         rec = _records(rng, n, with_target=False)
         y = net.infer(torch.from_numpy(rec).cuda()).cpu().numpy().astype(np.float64)
@@ -88,16 +102,18 @@ def test_nrc_forward_matches_oracle(tcgen05):
     assert net.last_loss() == 0.0   # no device wait ran out (it would raise PT_ERR_TIMEOUT)
 
 
-def test_nrc_gradients_match_oracle():
+@pytest.mark.parametrize("grid", ["small", "production"])
+def test_nrc_gradients_match_oracle(grid):
     rng = np.random.default_rng(1)
-    net = _make()
+    net = _make(grid=grid)
     wn, gn = _set_random_params(net, rng)
     rec = _records(rng, 3000)
     dw, dg = net.gradients(torch.from_numpy(rec).cuda())
+    nl, lt, _, _ = GRIDS[grid]
     dw = dw.cpu().numpy().astype(np.float64)
-    dg = dg.cpu().numpy().astype(np.float64).reshape(L, 2 ** LOG2T, 2)
-    ws, table = _oracle_params(wn, gn)
-    res = onrc.level_resolutions(L, 4, 1.6)
+    dg = dg.cpu().numpy().astype(np.float64).reshape(nl, 2 ** lt, 2)
+    ws, table = _oracle_params(wn, gn, grid)
+    res = _resolutions(grid)
     # reference: the oracle's forward and backward, fed the FP16 values the kernels store
     # (the 64-wide input and each layer's activations)
     h16 = lambda a: a.astype(np.float16).astype(np.float64)  # noqa: E731
@@ -111,7 +127,7 @@ def test_nrc_gradients_match_oracle():
     y = hcur @ ws[-1].T
     loss, dy = onrc.relative_l2(y, rec[:, 10:13].astype(np.float64))
     gw, dx = onrc.mlp_backward(acts, ws, dy)
-    dtable = onrc.grid_backward(lookups, dx[:, :2 * L], table.shape)
+    dtable = onrc.grid_backward(lookups, dx[:, :2 * nl], table.shape)
     for i in range(4):
         assert _rel_l2(dw[i * 4096:(i + 1) * 4096].reshape(64, 64), gw[i]) <= 1e-2, i
     out = dw[4 * 4096:].reshape(16, 64)

@@ -126,14 +126,26 @@ def test_nrc_gradients_match_oracle(grid):
         acts.append(hcur)
     y = hcur @ ws[-1].T
     loss, dy = onrc.relative_l2(y, rec[:, 10:13].astype(np.float64))
-    gw, dx = onrc.mlp_backward(acts, ws, dy)
+    # the kernels hold each layer's output gradient as an FP16 tensor-core operand, in units of
+    # the loss sum (times 3n; the 1/(3n) of the mean is applied in FP32 at the end)
+    n_el = float(dy.size)
+    gw, dx = onrc.mlp_backward(acts, ws, dy, operand=lambda g: h16(g * n_el) / n_el)
     dtable = onrc.grid_backward(lookups, dx[:, :2 * nl], table.shape)
     for i in range(4):
-        assert _rel_l2(dw[i * 4096:(i + 1) * 4096].reshape(64, 64), gw[i]) <= 1e-2, i
+        assert _rel_l2(dw[i * 4096:(i + 1) * 4096].reshape(64, 64), gw[i]) <= 2e-3, i
     out = dw[4 * 4096:].reshape(16, 64)
-    assert _rel_l2(out[:3], gw[4]) <= 1e-2
+    assert _rel_l2(out[:3], gw[4]) <= 2e-3
     assert np.all(out[3:] == 0)
-    assert _rel_l2(dg, dtable) <= 1e-2
+    assert _rel_l2(dg, dtable) <= 2e-3
+    # against the exact backward (FP16 forward activations only): the FP16 output gradients
+    # cost about 1e-3 per layer, amplified by the cancellation in each 64-term product; on the
+    # production grid most table entries receive one sample's gradient (no averaging), so the
+    # table gradient sits near 2e-2 there
+    gw_x, dx_x = onrc.mlp_backward(acts, ws, dy)
+    dtable_x = onrc.grid_backward(lookups, dx_x[:, :2 * nl], table.shape)
+    for i in range(4):
+        assert _rel_l2(dw[i * 4096:(i + 1) * 4096].reshape(64, 64), gw_x[i]) <= 1e-2, i
+    assert _rel_l2(dg, dtable_x) <= (1e-2 if grid == "small" else 3e-2)
 
 
 def test_nrc_adam_step():

@@ -512,6 +512,10 @@ typedef struct {
                                    accumulators in tensor memory); 0: on mma.sync, 16-row tiles
                                    per warp, which measures faster here because inference is
                                    bound by the hash-grid gathers, not by the MLP */
+    uint32_t train_kernels;     /* 0: each training batch's loss and gradients in ONE fused
+                                   tcgen05 kernel (encoding, forward, loss, backward, weight and
+                                   grid gradients per 128-sample tile); 1: the same steps as
+                                   separate mma.sync kernels.  Adam runs after either. */
 } pt_nrc_opts;
 
 /* Query layout for pt_nrc_infer / training samples (DEVICE arrays of float[n*16]):

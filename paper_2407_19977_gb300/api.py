@@ -319,7 +319,7 @@ class Nrc:
 
     def __init__(self, n_levels=16, log2_table=19, base_resolution=16, per_level_scale=0.0, learning_rate=1e-2,
                  batch=8192, seed=0, box=((0.0, 0.0, 0.0), (1.0, 1.0, 1.0)), frame_samples=32768, tcgen05=False,
-                 stream=None):
+                 train_kernels=0, stream=None):
         o = N.pt_nrc_opts()
         o.n_levels, o.log2_table, o.base_resolution = n_levels, log2_table, base_resolution
         o.per_level_scale, o.n_hidden, o.learning_rate, o.batch, o.seed = per_level_scale, 4, learning_rate, batch, seed
@@ -327,6 +327,7 @@ class Nrc:
         o.scene_max[:] = [float(x) for x in box[1]]
         o.frame_samples = int(frame_samples)
         o.tcgen05 = 1 if tcgen05 else 0
+        o.train_kernels = int(train_kernels)
         self.opts = o
         h = C.c_void_p()
         N.call("pt_nrc_create", C.byref(o), _stream_handle(stream), C.byref(h))

@@ -82,6 +82,31 @@ __device__ __forceinline__ float3 pos01(const GridDesc& G, const float* q) {
                fminf(fmaxf((q[2] - G.lo.z) * G.inv_ext.z, 0.0f), 1.0f));
 }
 
+// cell and in-cell fraction of a coordinate u in [0, 1] on a grid of res cells.  The product
+// u * res is carried as the unevaluated sum hi + lo (lo = fma(u, res, -hi) is its exact rounding
+// error), so the cell and the fraction are those of the exact product, as FP64 has them,
+// rather than off by up to half an FP32 ulp of u * res (3e-5 of a cell at res ~ 1000) -- an
+// error that flips the FP16 rounding of fine-level features.
+__device__ __forceinline__ void cell_frac(float u, uint32_t res, uint32_t& c, float& f) {
+    const float r = (float)res;
+    const float hi = u * r;
+    const float lo = fmaf(u, r, -hi);
+    int ci = (int)floorf(hi);
+    float fr = (hi - (float)ci) + lo;        // hi - ci is exact
+    if (fr < 0.0f) { ci -= 1; fr += 1.0f; }  // hi an integer and the exact product just below it
+    if (ci > (int)res - 1) { ci = (int)res - 1; fr = 1.0f; }   // u = 1: the far face of the last cell
+    if (ci < 0) { ci = 0; fr = 0.0f; }
+    c = (uint32_t)ci;
+    f = fr;
+}
+
+__device__ __forceinline__ void grid_cell(float3 p, uint32_t res, uint32_t& cx, uint32_t& cy, uint32_t& cz, float& rx,
+                                          float& ry, float& rz) {
+    cell_frac(p.x, res, cx, rx);
+    cell_frac(p.y, res, cy, ry);
+    cell_frac(p.z, res, cz, rz);
+}
+
 // one thread per (query, level): interpolated features of that level -> X[q][2l..2l+1];
 // the same thread writes columns 32 + 2l, 33 + 2l of the non-grid part
 __global__ void k_encode(GridDesc G, const float* __restrict__ queries, RowCount rc, __half* __restrict__ X) {
@@ -92,9 +117,9 @@ __global__ void k_encode(GridDesc G, const float* __restrict__ queries, RowCount
     const float* rec = queries + (size_t)QSTRIDE * q;
     const float3 p = pos01(G, rec);
     const uint32_t res = G.res[l];
-    const float fx = p.x * res, fy = p.y * res, fz = p.z * res;
-    const uint32_t cx = min((uint32_t)fx, res - 1), cy = min((uint32_t)fy, res - 1), cz = min((uint32_t)fz, res - 1);
-    const float rx = fx - cx, ry = fy - cy, rz = fz - cz;
+    uint32_t cx, cy, cz;
+    float rx, ry, rz;
+    grid_cell(p, res, cx, cy, cz, rx, ry, rz);
     const __half2* tab = reinterpret_cast<const __half2*>(G.table) + (size_t)l * G.T;
     float f0 = 0.0f, f1 = 0.0f;
 #pragma unroll
@@ -134,9 +159,9 @@ __global__ void k_grid_backward(GridDesc G, const float* __restrict__ samples, R
     const uint32_t q = (uint32_t)(gid / G.L), l = (uint32_t)(gid % G.L);
     const float3 p = pos01(G, samples + (size_t)QSTRIDE * q);
     const uint32_t res = G.res[l];
-    const float fx = p.x * res, fy = p.y * res, fz = p.z * res;
-    const uint32_t cx = min((uint32_t)fx, res - 1), cy = min((uint32_t)fy, res - 1), cz = min((uint32_t)fz, res - 1);
-    const float rx = fx - cx, ry = fy - cy, rz = fz - cz;
+    uint32_t cx, cy, cz;
+    float rx, ry, rz;
+    grid_cell(p, res, cx, cy, cz, rx, ry, rz);
     const float g0 = dX[(size_t)2 * G.L * q + 2 * l] * scale, g1 = dX[(size_t)2 * G.L * q + 2 * l + 1] * scale;
     float* gr = G.grad + (size_t)l * G.T * 2;
 #pragma unroll
@@ -287,9 +312,9 @@ __global__ void __launch_bounds__(INFER_THREADS, 2) k_nrc_infer(GridDesc G, cons
             float f0 = 0.0f, f1 = 0.0f;
             if (grid_lane && q < n) {
                 const float3 p = pos01(G, queries + (size_t)QSTRIDE * q);
-                const float fx = p.x * res, fy = p.y * res, fz = p.z * res;
-                const uint32_t cx = min((uint32_t)fx, res - 1), cy = min((uint32_t)fy, res - 1), cz = min((uint32_t)fz, res - 1);
-                const float rx = fx - cx, ry = fy - cy, rz = fz - cz;
+                uint32_t cx, cy, cz;
+                float rx, ry, rz;
+                grid_cell(p, res, cx, cy, cz, rx, ry, rz);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const uint32_t ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
@@ -493,10 +518,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_nrc_infer_tc(GridDesc G, cons
                 float f0 = 0.0f, f1 = 0.0f;
                 if (grid_lane && q < n) {
                     const float3 p = pos01(G, queries + (size_t)QSTRIDE * q);
-                    const float fx = p.x * res, fy = p.y * res, fz = p.z * res;
-                    const uint32_t cx = min((uint32_t)fx, res - 1), cy = min((uint32_t)fy, res - 1),
-                                   cz = min((uint32_t)fz, res - 1);
-                    const float rx = fx - cx, ry = fy - cy, rz = fz - cz;
+                    uint32_t cx, cy, cz;
+                    float rx, ry, rz;
+                    grid_cell(p, res, cx, cy, cz, rx, ry, rz);
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         const uint32_t ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
@@ -592,6 +616,440 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_nrc_infer_tc(GridDesc G, cons
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(*tslot), "r"(TC_TMEM_COLS) : "memory");
+}
+
+// ---- fused training step on tcgen05 -----------------------------------------------------
+// One persistent kernel computes a training batch's loss and every gradient: per 128-sample
+// tile the hash-grid encoding, the five forward layers, the relative L2 loss, the backward
+// chain, the weight gradients and the scatter of the grid gradient, with the activations and
+// output gradients kept in shared memory and the accumulators in tensor memory.  Every product
+// is a tcgen05.mma with M = 128 and FP16 operands (FP32 accumulation), issued by one thread.
+//
+// Shared-memory tiles are K-major FP16 (8 x 8 core matrices of 128 bytes) whose rows hold 16
+// core matrices along K, so one tile stores two layers side by side: H01 = [h0 | h1], H23 =
+// [h2 | h3] (h0 the encoded input, h_l the l-th hidden activation), DZ01 = [dz1 | dz2], DZ23 =
+// [dz3 | dz4] (dz_l the gradient of the l-th pre-activation, in units of the loss sum).  A
+// layer's product reads its half as a K-major A operand.  The weight gradients of a pair,
+// dW_l = dz_(l+1)^T h_l (sum over the tile's rows), come from ONE product that reads the pair
+// tiles themselves as MN-major operands: A = [dz_(l+1) | dz_(l+2)]^T (M = 128, K = rows),
+// B = [h_l | h_(l+1)]^T (N = 128), whose diagonal 64 x 64 blocks are dW_l and dW_(l+1) (the
+// off-diagonal blocks are never read); they accumulate in tensor memory over all the CTA's
+// tiles and go out with one atomic add per weight at the end.  The backward products read the
+// forward weight tiles as MN-major B operands (N = layer input, K = layer output).  The output
+// layer's gradient uses A = DZ01 read from its first 16 columns (dy); its rows 16..127 hold
+// stale data and produce accumulator rows that are never read.
+//
+// MN-major descriptors: SBO = the stride between core matrices along M/N, LBO = along K (the
+// reverse of K-major).
+//
+// The encoding gathers 16 levels x 8 corners of table entries per sample: they are copied
+// straight into a shared-memory staging area with cp.async (no registers held while in flight,
+// so a tile's gathers are in flight together), 8 levels at a time, then interpolated.
+constexpr uint32_t TR_TILE = 128;
+constexpr uint32_t TR_W_BYTES = (N_HIDDEN * W * W + OUT_PAD * W) * 2;   // 34,816
+constexpr uint32_t TR_PAIR_BYTES = TR_TILE * 2 * W * 2;                   // 32,768: 128 rows x 128 FP16
+constexpr uint32_t TR_H4_BYTES = TR_TILE * W * 2;                         // 16,384
+constexpr uint32_t TR_STAGE_BYTES = TR_TILE * 8 * 8 * 4;                  // 32,768: 8 levels x 8 corners
+constexpr uint32_t TR_SMEM = 1024 + TR_W_BYTES + 4 * TR_PAIR_BYTES + TR_H4_BYTES + TR_STAGE_BYTES + 64;
+constexpr uint32_t TR_TMEM_COLS = 512;   // 0..63 layer products, 64..191 dW01, 192..319 dW23, 320..383 dW4
+
+// element (r, k) of a K-major FP16 tile whose rows hold kg core matrices along K, in halves
+__device__ __forceinline__ uint32_t kmaj_off(uint32_t r, uint32_t k, uint32_t kg) {
+    return (((r >> 3) * kg + (k >> 3)) << 6) + ((r & 7u) << 3) + (k & 7u);
+}
+
+// shared-memory matrix descriptor with explicit leading / stride byte offsets, no swizzle
+__device__ __forceinline__ uint64_t tc_desc_ls(const void* p, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor of kind::f16 with the major-ness of A and B (1 = MN-major)
+__host__ __device__ constexpr uint32_t tc_idesc_t(uint32_t m, uint32_t n, uint32_t a_mn, uint32_t b_mn) {
+    return (1u << 4) | (a_mn << 15) | (b_mn << 16) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+
+// every thread waits for the products committed to the barrier; false in every thread if the
+// wait ran out (after one more bounded wait for what is in flight)
+__device__ __forceinline__ bool tr_wait(uint32_t mbar, uint32_t& phase, uint32_t* err) {
+    const bool got = mbar_wait(mbar, phase);
+    if (!got && (threadIdx.x & 31u) == 0) atomicOr(err, 1u);
+    if (!__syncthreads_and(got)) {
+        mbar_wait(mbar, phase);
+        return false;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    return true;
+}
+
+// the tiles written by every thread are visible to the tensor core, and every thread's
+// tensor-memory loads are complete, before thread 0 issues the next products
+__device__ __forceinline__ void tr_publish() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+
+// 32 FP32 columns of this thread's row (tensor-memory address taddr): ReLU (recording its mask
+// bits) or the recorded mask applied, to FP16 in row r of a K-major tile at column col0
+template <bool FWD>
+__device__ __forceinline__ void tr_row_out(uint32_t taddr, __half* tile, uint32_t kg, uint32_t r, uint32_t col0,
+                                           uint32_t& mask) {
+    uint32_t v[32];
+    tc_ld32(taddr, v);
+    uint32_t bits = FWD ? 0u : mask;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint4 pk;
+        uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int j = 8 * c + 2 * h;
+            float a = __uint_as_float(v[j]), b = __uint_as_float(v[j + 1]);
+            if (FWD) {
+                bits |= (a > 0.0f ? 1u : 0u) << j;
+                bits |= (b > 0.0f ? 1u : 0u) << (j + 1);
+                a = fmaxf(a, 0.0f);
+                b = fmaxf(b, 0.0f);
+            } else {
+                a = ((bits >> j) & 1u) ? a : 0.0f;
+                b = ((bits >> (j + 1)) & 1u) ? b : 0.0f;
+            }
+            pw[h] = pack_h2(a, b);
+        }
+        *reinterpret_cast<uint4*>(tile + kmaj_off(r, col0 + 8u * c, kg)) = pk;
+    }
+    if (FWD) mask = bits;
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : TC_LD_REGS8(0), TC_LD_REGS8(8)
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// The CTA has 8 warps: warp w reaches tensor-memory lanes 32 (w % 4) .. + 31 (one row of the
+// tile per thread) and takes the column half w / 4 of each 64-wide layer output, so two warps
+// share a row quarter.
+constexpr uint32_t TR_THREADS = 256;
+
+__global__ void __launch_bounds__(TR_THREADS, 1) k_nrc_train_tc(GridDesc G, const float* __restrict__ samples, RowCount rc,
+                                                             const __half* __restrict__ Wg, float* __restrict__ dW,
+                                                             float* __restrict__ loss_sum, uint32_t* __restrict__ err) {
+    extern __shared__ unsigned char tr_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)tr_raw + 1023) & ~(uintptr_t)1023);
+    __half* sW = reinterpret_cast<__half*>(base);
+    __half* H01 = reinterpret_cast<__half*>(base + TR_W_BYTES);
+    __half* H23 = reinterpret_cast<__half*>(base + TR_W_BYTES + TR_PAIR_BYTES);
+    __half* DZ01 = reinterpret_cast<__half*>(base + TR_W_BYTES + 2 * TR_PAIR_BYTES);
+    __half* DZ23 = reinterpret_cast<__half*>(base + TR_W_BYTES + 3 * TR_PAIR_BYTES);
+    __half* H4 = reinterpret_cast<__half*>(base + TR_W_BYTES + 4 * TR_PAIR_BYTES);
+    __half2* stage = reinterpret_cast<__half2*>(base + TR_W_BYTES + 4 * TR_PAIR_BYTES + TR_H4_BYTES);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(base + TR_W_BYTES + 4 * TR_PAIR_BYTES + TR_H4_BYTES + TR_STAGE_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t quarter = warp & 3u, hf = warp >> 2;
+    // weights: global row-major [out][in] -> K-major tiles of 8 core matrices per row, 16-byte
+    // asynchronous copies
+    for (uint32_t i = tid; i < (N_HIDDEN * W + OUT_PAD) * (W / 8); i += blockDim.x) {
+        const uint32_t row = i / (W / 8), c = i % (W / 8);
+        const uint32_t layer = min(row / W, (uint32_t)N_HIDDEN), r = row - layer * W;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n"
+                     :: "r"(smem_u32(sW + layer * W * W + kmaj_off(r, 8 * c, 8))), "l"(Wg + (size_t)row * W + 8 * c)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     :: "r"(smem_u32(tslot)), "r"(TR_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tbase = *tslot;
+    const uint32_t lanes = (32u * quarter) << 16;          // this warp's 32 tensor-memory lanes
+    const uint32_t c32 = 32u * hf;                           // this warp's 32 columns of a layer output
+    const uint32_t t_main = tbase, t_w01 = tbase + 64u, t_w23 = tbase + 192u, t_w4 = tbase + 320u;
+    const uint32_t n = rc.get();
+    const uint32_t n_tiles = (n + TR_TILE - 1) / TR_TILE;
+    const float scale = n ? 1.0f / (3.0f * (float)n) : 0.0f;
+    const uint32_t mb = smem_u32(mbar);
+    const uint32_t ncols = W - 2 * G.L;
+    const uint32_t r = 32u * quarter + lane;                // this thread's row of the tile
+    const uint32_t idesc_f64 = tc_idesc_t(TR_TILE, W, 0, 0), idesc_f16 = tc_idesc_t(TR_TILE, OUT_PAD, 0, 0);
+    const uint32_t idesc_b = tc_idesc_t(TR_TILE, W, 0, 1);
+    const uint32_t idesc_w128 = tc_idesc_t(TR_TILE, 2 * W, 1, 1), idesc_w64 = tc_idesc_t(TR_TILE, W, 1, 1);
+    uint32_t phase = 0;
+    bool first = true, ok = true;
+    float loss_acc = 0.0f;
+    for (uint32_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const uint32_t t0 = tile * TR_TILE;
+        // ---- encoding into H01 columns 0..63 (h0): thread pair (2 rows' worth of threads per
+        // row) row = tid / 2 takes levels 4 sub .. 4 sub + 3 of each 8-level pass (sub = tid % 2);
+        // a row past n reads the last row's record and is written as zeros
+        {
+            const uint32_t row = tid >> 1, sub = tid & 1u;
+            const uint32_t q = t0 + row;
+            const bool valid = q < n;
+            const float* rec = samples + (size_t)QSTRIDE * min(q, n - 1u);
+            const float3 p = pos01(G, rec);
+            for (uint32_t pass = 0; pass < 2; ++pass) {
+                float3 fr[4];
+#pragma unroll
+                for (uint32_t j = 0; j < 4; ++j) {
+                    const uint32_t l = 8u * pass + 4u * sub + j;
+                    fr[j] = make_float3(0.0f, 0.0f, 0.0f);
+                    if (l < G.L) {
+                        const uint32_t res = G.res[l];
+                        uint32_t cx, cy, cz;
+                        grid_cell(p, res, cx, cy, cz, fr[j].x, fr[j].y, fr[j].z);
+                        const __half2* tl = reinterpret_cast<const __half2*>(G.table) + (size_t)l * G.T;
+                        __half2* dst = stage + (row * 8u + 4u * sub + j) * 8u;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const uint32_t ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n"
+                                         :: "r"(smem_u32(dst + c)),
+                                            "l"(tl + corner_index(cx + ox, cy + oy, cz + oz, res, G.T))
+                                         : "memory");
+                        }
+                    }
+                }
+                asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+#pragma unroll
+                for (uint32_t j = 0; j < 4; ++j) {
+                    const uint32_t l = 8u * pass + 4u * sub + j;
+                    if (l >= G.L) continue;
+                    const __half2* src = stage + (row * 8u + 4u * sub + j) * 8u;
+                    float f0 = 0.0f, f1 = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const uint32_t ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+                        const float w = (ox ? fr[j].x : 1.0f - fr[j].x) * (oy ? fr[j].y : 1.0f - fr[j].y) *
+                                        (oz ? fr[j].z : 1.0f - fr[j].z);
+                        const float2 v = __half22float2(src[c]);
+                        f0 += w * v.x;
+                        f1 += w * v.y;
+                    }
+                    *reinterpret_cast<__half2*>(H01 + kmaj_off(row, 2 * l, 16)) =
+                        valid ? __floats2half2_rn(f0, f1) : __floats2half2_rn(0.0f, 0.0f);
+                }
+            }
+            // the other columns: direction, normal, roughness, a constant 1, zeros (each
+            // thread of the pair half of them)
+            for (uint32_t k = sub; k < ncols; k += 2) {
+                float v = 0.0f;
+                if (valid) {
+                    if (k < 3) v = rec[3 + k];
+                    else if (k < 6) v = rec[6 + (k - 3)];
+                    else if (k == 6) v = rec[9];
+                    else if (k == 7) v = 1.0f;
+                }
+                H01[kmaj_off(row, 2 * G.L + k, 16)] = __float2half_rn(v);
+            }
+        }
+        // ---- forward: four hidden layers, then the output layer
+        uint32_t mask[4];
+        __half* const in_tile[4] = {H01, H01 + 512, H23, H23 + 512};   // 512 halves = 8 core matrices on
+        __half* const out_tile[4] = {H01, H23, H23, H4};
+        const uint32_t out_col[4] = {64, 0, 64, 0};
+        const uint32_t out_kg[4] = {16, 16, 16, 8};
+        for (int l = 0; l < N_HIDDEN && ok; ++l) {
+            tr_publish();
+            if (tid == 0) {
+#pragma unroll
+                for (uint32_t kk = 0; kk < 4; ++kk)
+                    tc_mma(t_main, tc_desc_ls(in_tile[l] + kk * 128, 128, 2048), tc_desc_ls(sW + l * W * W + kk * 128, 128, 1024),
+                           idesc_f64, kk > 0 ? 1u : 0u);
+                tc_commit(mb);
+            }
+            __syncwarp();
+            if (!(ok = tr_wait(mb, phase, err))) break;
+            tr_row_out<true>(t_main + lanes + c32, out_tile[l], out_kg[l], r, out_col[l] + c32, mask[l]);
+        }
+        if (!ok) break;
+        tr_publish();
+        if (tid == 0) {
+#pragma unroll
+            for (uint32_t kk = 0; kk < 4; ++kk)
+                tc_mma(t_main, tc_desc_ls(H4 + kk * 128, 128, 1024), tc_desc_ls(sW + N_HIDDEN * W * W + kk * 128, 128, 1024),
+                       idesc_f16, kk > 0 ? 1u : 0u);
+            tc_commit(mb);
+        }
+        __syncwarp();
+        if (!(ok = tr_wait(mb, phase, err))) break;
+        // ---- relative L2 loss; dy (times 3n) into DZ01 columns 0..15 (warps 0-3)
+        if (hf == 0) {
+            uint32_t v[4];
+            tc_ld4(t_main + lanes, v);
+            const uint32_t q = t0 + r;
+            float d[3] = {0.0f, 0.0f, 0.0f};
+            if (q < n) {
+                const float* tg = samples + (size_t)QSTRIDE * q + 10;
+                for (int c = 0; c < 3; ++c) {
+                    const float y = __uint_as_float(v[c]);
+                    const float den = y * y + 0.01f;
+                    const float diff = y - tg[c];
+                    loss_acc += diff * diff / den;
+                    d[c] = 2.0f * diff / den;
+                }
+            }
+            uint4 lo, hi = make_uint4(0u, 0u, 0u, 0u);
+            lo.x = pack_h2(d[0], d[1]);
+            lo.y = pack_h2(d[2], 0.0f);
+            lo.z = 0u;
+            lo.w = 0u;
+            *reinterpret_cast<uint4*>(DZ01 + kmaj_off(r, 0, 16)) = lo;
+            *reinterpret_cast<uint4*>(DZ01 + kmaj_off(r, 8, 16)) = hi;
+        }
+        // ---- backward: dh4 = dy W4 and the output layer's weight gradient
+        tr_publish();
+        if (tid == 0) {
+            tc_mma(t_main, tc_desc_ls(DZ01, 128, 2048), tc_desc_ls(sW + N_HIDDEN * W * W, 1024, 128), idesc_b, 0u);
+#pragma unroll
+            for (uint32_t kr = 0; kr < TR_TILE / 16; ++kr)
+                tc_mma(t_w4, tc_desc_ls(DZ01 + kr * 2048, 2048, 128), tc_desc_ls(H4 + kr * 1024, 1024, 128), idesc_w64,
+                       (first && kr == 0) ? 0u : 1u);
+            tc_commit(mb);
+        }
+        __syncwarp();
+        if (!(ok = tr_wait(mb, phase, err))) break;
+        tr_row_out<false>(t_main + lanes + c32, DZ23, 16, r, 64 + c32, mask[3]);          // dz4
+        // dh3 = dz4 W3
+        tr_publish();
+        if (tid == 0) {
+#pragma unroll
+            for (uint32_t kk = 0; kk < 4; ++kk)
+                tc_mma(t_main, tc_desc_ls(DZ23 + 512 + kk * 128, 128, 2048), tc_desc_ls(sW + 3 * W * W + kk * 1024, 1024, 128),
+                       idesc_b, kk > 0 ? 1u : 0u);
+            tc_commit(mb);
+        }
+        __syncwarp();
+        if (!(ok = tr_wait(mb, phase, err))) break;
+        tr_row_out<false>(t_main + lanes + c32, DZ23, 16, r, c32, mask[2]);               // dz3
+        // dW2, dW3 from [dz3 | dz4]^T [h2 | h3]; dh2 = dz3 W2
+        tr_publish();
+        if (tid == 0) {
+#pragma unroll
+            for (uint32_t kr = 0; kr < TR_TILE / 16; ++kr)
+                tc_mma(t_w23, tc_desc_ls(DZ23 + kr * 2048, 2048, 128), tc_desc_ls(H23 + kr * 2048, 2048, 128), idesc_w128,
+                       (first && kr == 0) ? 0u : 1u);
+#pragma unroll
+            for (uint32_t kk = 0; kk < 4; ++kk)
+                tc_mma(t_main, tc_desc_ls(DZ23 + kk * 128, 128, 2048), tc_desc_ls(sW + 2 * W * W + kk * 1024, 1024, 128),
+                       idesc_b, kk > 0 ? 1u : 0u);
+            tc_commit(mb);
+        }
+        __syncwarp();
+        if (!(ok = tr_wait(mb, phase, err))) break;
+        tr_row_out<false>(t_main + lanes + c32, DZ01, 16, r, 64 + c32, mask[1]);          // dz2
+        // dh1 = dz2 W1
+        tr_publish();
+        if (tid == 0) {
+#pragma unroll
+            for (uint32_t kk = 0; kk < 4; ++kk)
+                tc_mma(t_main, tc_desc_ls(DZ01 + 512 + kk * 128, 128, 2048), tc_desc_ls(sW + 1 * W * W + kk * 1024, 1024, 128),
+                       idesc_b, kk > 0 ? 1u : 0u);
+            tc_commit(mb);
+        }
+        __syncwarp();
+        if (!(ok = tr_wait(mb, phase, err))) break;
+        tr_row_out<false>(t_main + lanes + c32, DZ01, 16, r, c32, mask[0]);               // dz1
+        // dW0, dW1 from [dz1 | dz2]^T [h0 | h1]; dx = dz1 W0
+        tr_publish();
+        if (tid == 0) {
+#pragma unroll
+            for (uint32_t kr = 0; kr < TR_TILE / 16; ++kr)
+                tc_mma(t_w01, tc_desc_ls(DZ01 + kr * 2048, 2048, 128), tc_desc_ls(H01 + kr * 2048, 2048, 128), idesc_w128,
+                       (first && kr == 0) ? 0u : 1u);
+#pragma unroll
+            for (uint32_t kk = 0; kk < 4; ++kk)
+                tc_mma(t_main, tc_desc_ls(DZ01 + kk * 128, 128, 2048), tc_desc_ls(sW + kk * 1024, 1024, 128), idesc_b,
+                       kk > 0 ? 1u : 0u);
+            tc_commit(mb);
+        }
+        __syncwarp();
+        if (!(ok = tr_wait(mb, phase, err))) break;
+        first = false;
+        // ---- grid gradient: dx of the grid columns (levels 8 hf .. 8 hf + 7 in this warp),
+        // scattered onto the corners with FP32 vector atomics
+        {
+            uint32_t v[16];
+            tc_ld16(t_main + lanes + 16u * hf, v);
+            const uint32_t q = t0 + r;
+            if (q < n) {
+                const float3 p = pos01(G, samples + (size_t)QSTRIDE * q);
+#pragma unroll
+                for (uint32_t j = 0; j < 8; ++j) {
+                    const uint32_t l = 8u * hf + j;
+                    if (l >= G.L) break;
+                    const uint32_t res = G.res[l];
+                    uint32_t cx, cy, cz;
+                    float rx, ry, rz;
+                    grid_cell(p, res, cx, cy, cz, rx, ry, rz);
+                    const float g0 = __uint_as_float(v[2 * j]) * scale, g1 = __uint_as_float(v[2 * j + 1]) * scale;
+                    float* gr = G.grad + (size_t)l * G.T * 2;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const uint32_t ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+                        const float w = (ox ? rx : 1.0f - rx) * (oy ? ry : 1.0f - ry) * (oz ? rz : 1.0f - rz);
+                        const uint32_t idx = corner_index(cx + ox, cy + oy, cz + oz, res, G.T);
+                        atomicAdd(reinterpret_cast<float2*>(gr + 2 * idx), make_float2(w * g0, w * g1));
+                    }
+                }
+            }
+        }
+        // the next tile's encoding and dy rewrite tiles the finished products have read
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+    }
+    // loss of the CTA's rows
+    for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
+    if (lane == 0 && loss_acc != 0.0f) atomicAdd(loss_sum, loss_acc);
+    if (blockIdx.x == 0 && tid == 0 && n) atomicAdd(loss_sum + 1, (float)n);
+    // weight gradients: one vector atomic add per 4 weights (the rows of the diagonal blocks),
+    // scaled by 1/(3n); this warp takes 32 of the row's 64 columns
+    if (ok && !first) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t lo = (r < 64 ? 0u : 64u) + c32;   // this row's layer block, this warp's half
+        for (int pr = 0; pr < 2; ++pr) {
+            uint32_t v[32];
+            tc_ld32((pr == 0 ? t_w01 : t_w23) + lanes + lo, v);
+            float* dst = dW + (size_t)(2 * pr + (r < 64 ? 0 : 1)) * W * W + (size_t)(r & 63u) * W + c32;
+#pragma unroll
+            for (int c = 0; c < 32; c += 4)
+                atomicAdd(reinterpret_cast<float4*>(dst + c),
+                          make_float4(__uint_as_float(v[c]) * scale, __uint_as_float(v[c + 1]) * scale,
+                                      __uint_as_float(v[c + 2]) * scale, __uint_as_float(v[c + 3]) * scale));
+        }
+        uint32_t v[32];
+        tc_ld32(t_w4 + lanes + c32, v);
+        if (r < OUT_PAD) {
+            float* dst = dW + (size_t)N_HIDDEN * W * W + (size_t)r * W + c32;
+#pragma unroll
+            for (int c = 0; c < 32; c += 4)
+                atomicAdd(reinterpret_cast<float4*>(dst + c),
+                          make_float4(__uint_as_float(v[c]) * scale, __uint_as_float(v[c + 1]) * scale,
+                                      __uint_as_float(v[c + 2]) * scale, __uint_as_float(v[c + 3]) * scale));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tbase), "r"(TR_TMEM_COLS) : "memory");
 }
 
 // relative L2 loss: dL/dy * (3n) (the 1/(3n) of the mean is applied to the gradients later
@@ -976,6 +1434,7 @@ extern "C" pt_status pt_nrc_create(const pt_nrc_opts* opts, void* cuda_stream, p
     PT_CHECK_ARG(o.n_levels >= 1 && o.n_levels <= 16, "n_levels must be 1..16 (2 features each fill 32 inputs)");
     PT_CHECK_ARG(o.log2_table >= 8 && o.log2_table <= 24, "log2_table must be 8..24");
     PT_CHECK_ARG(o.base_resolution >= 2, "base_resolution must be >= 2");
+    PT_CHECK_ARG(o.train_kernels <= 1, "train_kernels must be 0 (fused) or 1 (separate kernels)");
     for (int a = 0; a < 3; ++a)
         PT_CHECK_ARG(o.scene_max[a] > o.scene_min[a], "empty normalisation box");
     pt_nrc* N = new pt_nrc();
@@ -1093,7 +1552,24 @@ static pt_status nrc_forward(pt_nrc* N, const float* q, RowCount rc, __half* X, 
 
 // loss and gradients of one batch into d_wg / d_gg (accumulated; caller zeroes via Adam).
 // rc.n is the capacity the buffers are laid out with; rc.dev (optional) the row count.
+static int g_train_tc_blocks = 0;
+
 static pt_status nrc_gradients(pt_nrc* N, const float* samples, RowCount rc, cudaStream_t st) {
+    if (N->o.train_kernels == 0) {
+        // one fused tcgen05 kernel, persistent over the batch's 128-sample tiles (one CTA per SM:
+        // its shared memory and all 512 tensor-memory columns)
+        if (g_train_tc_blocks == 0) {
+            PT_CUDA_TRY(cudaFuncSetAttribute(k_nrc_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM));
+            g_train_tc_blocks = pt_num_sms();
+        }
+        const uint32_t tiles = (rc.n + TR_TILE - 1) / TR_TILE;
+        const uint32_t blocks = std::max(1u, std::min((uint32_t)g_train_tc_blocks, tiles));
+        PT_LAUNCH(k_nrc_train_tc, blocks, TR_THREADS, TR_SMEM, st, grid_desc(N), samples, rc, N->d_wh, N->d_wg,
+                  N->d_loss, N->d_err);
+        N->launches += 1;
+        PT_CUDA_TRY(cudaGetLastError());
+        return PT_OK;
+    }
     pt_status r = ensure_train(N, rc.n);
     if (r != PT_OK) return r;
     // every training buffer is addressed with the row stride rc.n (<= the allocation)
@@ -1227,6 +1703,7 @@ static pt_status ensure_infer(pt_nrc* N, uint32_t cap) {
 pt_status pt_nrc_render_prepare(pt_nrc* N, uint32_t infer_cap, uint32_t train_cap) {
     pt_status r = ensure_infer(N, infer_cap);
     if (r != PT_OK) return r;
+    if (N->o.train_kernels == 0) return PT_OK;   // the fused training kernel needs no scratch
     return ensure_train(N, std::min(N->o.batch, std::max(train_cap, 1u)));
 }
 
@@ -1243,7 +1720,7 @@ uint32_t pt_nrc_frame_samples(const pt_nrc* N) { return N->o.frame_samples; }
 // a batch past the end of the list is no step)
 pt_status pt_nrc_render_train_dev(pt_nrc* N, const float* samples, const uint32_t* n_dev, uint32_t cap, cudaStream_t st) {
     const uint32_t batch = std::min(N->o.batch, cap);
-    pt_status r = ensure_train(N, batch);
+    pt_status r = N->o.train_kernels == 0 ? PT_OK : ensure_train(N, batch);
     if (r != PT_OK) return r;
     PT_CUDA_TRY(cudaMemsetAsync(N->d_loss, 0, 2 * sizeof(float), st));
     for (uint32_t b0 = 0; b0 < cap; b0 += batch) {

@@ -79,7 +79,8 @@ class pt_batch_opts(C.Structure):
 class pt_nrc_opts(C.Structure):
     _fields_ = [("n_levels", u32), ("log2_table", u32), ("base_resolution", u32), ("per_level_scale", f32),
                 ("n_hidden", u32), ("learning_rate", f32), ("batch", u32), ("seed", u64),
-                ("scene_min", f32 * 3), ("scene_max", f32 * 3), ("frame_samples", u32), ("tcgen05", u32)]
+                ("scene_min", f32 * 3), ("scene_max", f32 * 3), ("frame_samples", u32), ("tcgen05", u32),
+                ("train_kernels", u32)]
 
 
 PT_OK = 0

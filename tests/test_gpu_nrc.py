@@ -21,11 +21,11 @@ L, LOG2T = 8, 12
 GRIDS = {"small": (8, 12, 4, 1.6), "production": (16, 19, 16, 0.0)}
 
 
-def _make(seed=0, lr=1e-2, batch=4096, tcgen05=False, grid="small"):
+def _make(seed=0, lr=1e-2, batch=4096, tcgen05=False, grid="small", train_kernels=0):
     from paper_2407_19977_gb300 import api
     nl, lt, base, scale = GRIDS[grid]
     return api.Nrc(n_levels=nl, log2_table=lt, base_resolution=base, per_level_scale=scale, learning_rate=lr,
-                   batch=batch, seed=seed, tcgen05=tcgen05)
+                   batch=batch, seed=seed, tcgen05=tcgen05, train_kernels=train_kernels)
 
 
 def _records(rng, n, with_target=True):
@@ -102,29 +102,54 @@ def test_nrc_forward_matches_oracle(tcgen05, grid):
     assert net.last_loss() == 0.0   # no device wait ran out (it would raise PT_ERR_TIMEOUT)
 
 
-@pytest.mark.parametrize("grid", ["small", "production"])
-def test_nrc_gradients_match_oracle(grid):
-    rng = np.random.default_rng(1)
-    net = _make(grid=grid)
-    wn, gn = _set_random_params(net, rng)
-    rec = _records(rng, 3000)
-    dw, dg = net.gradients(torch.from_numpy(rec).cuda())
-    nl, lt, _, _ = GRIDS[grid]
-    dw = dw.cpu().numpy().astype(np.float64)
-    dg = dg.cpu().numpy().astype(np.float64).reshape(nl, 2 ** lt, 2)
-    ws, table = _oracle_params(wn, gn, grid)
-    res = _resolutions(grid)
-    # reference: the oracle's forward and backward, fed the FP16 values the kernels store
-    # (the 64-wide input and each layer's activations)
+def _reference_forward(rec, ws, table, res):
+    """The oracle's forward fed the FP16 values the kernels store (the 64-wide input and each
+    layer's activations), and per sample the conditioning of its ReLU decisions: the smallest
+    |z| / sum_k |h_k w_k| over the hidden units.  Below 2e-5 (five times the FP32 accumulation
+    bound of a 64-term product, which also covers one input whose FP16 rounding the two
+    precisions take differently) the kernel's FP32 sum and the oracle's FP64 sum may put the
+    pre-activation on different sides of zero, and the sample's whole gradient then takes
+    another path through the network."""
     h16 = lambda a: a.astype(np.float16).astype(np.float64)  # noqa: E731
     feats, lookups = onrc.encode(rec[:, 0:3].astype(np.float64), table, res)
     x = h16(onrc.build_input(feats, rec[:, 3:6], rec[:, 6:9], rec[:, 9]))
     acts = [x]
     hcur = x
+    margin = np.full(len(rec), np.inf)
     for Wl in ws[:-1]:
-        hcur = h16(np.maximum(hcur @ Wl.T, 0.0))
+        z = hcur @ Wl.T
+        mag = np.abs(hcur) @ np.abs(Wl).T
+        margin = np.minimum(margin, (np.abs(z) / np.maximum(mag, 1e-300)).min(1))
+        hcur = h16(np.maximum(z, 0.0))
         acts.append(hcur)
-    y = hcur @ ws[-1].T
+    return acts, lookups, margin
+
+
+@pytest.mark.parametrize("grid", ["small", "production"])
+@pytest.mark.parametrize("train_kernels", [0, 1])
+def test_nrc_gradients_match_oracle(grid, train_kernels):
+    """Loss gradients of the weights and of the grid table, from the fused tcgen05 training
+    kernel (0) and from the separate mma.sync kernels (1), against the oracle's backward, on
+    the samples whose ReLU decisions are well conditioned (the others, at most 2 %, counted:
+    a decision FP32 and FP64 may take differently, like a path's reflect/refract choice)."""
+    rng = np.random.default_rng(1)
+    net = _make(grid=grid, train_kernels=train_kernels)
+    wn, gn = _set_random_params(net, rng)
+    rec_all = _records(rng, 3000)
+    nl, lt, _, _ = GRIDS[grid]
+    ws, table = _oracle_params(wn, gn, grid)
+    res = _resolutions(grid)
+    _, _, margin = _reference_forward(rec_all, ws, table, res)
+    ill = margin < 2e-5
+    assert ill.mean() <= 2e-2, ill.mean()
+    rec = np.ascontiguousarray(rec_all[~ill])
+    print(f"{grid}: {int(ill.sum())} of {len(rec_all)} samples with an ill-conditioned ReLU decision left out")
+    dw, dg = net.gradients(torch.from_numpy(rec).cuda())
+    dw = dw.cpu().numpy().astype(np.float64)
+    dg = dg.cpu().numpy().astype(np.float64).reshape(nl, 2 ** lt, 2)
+    h16 = lambda a: a.astype(np.float16).astype(np.float64)  # noqa: E731
+    acts, lookups, _ = _reference_forward(rec, ws, table, res)
+    y = acts[-1] @ ws[-1].T
     loss, dy = onrc.relative_l2(y, rec[:, 10:13].astype(np.float64))
     # the kernels hold each layer's output gradient as an FP16 tensor-core operand, in units of
     # the loss sum (times 3n; the 1/(3n) of the mean is applied in FP32 at the end)
@@ -138,19 +163,18 @@ def test_nrc_gradients_match_oracle(grid):
     assert np.all(out[3:] == 0)
     assert _rel_l2(dg, dtable) <= 2e-3
     # against the exact backward (FP16 forward activations only): the FP16 output gradients
-    # cost about 1e-3 per layer, amplified by the cancellation in each 64-term product; on the
-    # production grid most table entries receive one sample's gradient (no averaging), so the
-    # table gradient sits near 2e-2 there
+    # cost about 1e-3 per layer, amplified by the cancellation in each 64-term product
     gw_x, dx_x = onrc.mlp_backward(acts, ws, dy)
     dtable_x = onrc.grid_backward(lookups, dx_x[:, :2 * nl], table.shape)
     for i in range(4):
         assert _rel_l2(dw[i * 4096:(i + 1) * 4096].reshape(64, 64), gw_x[i]) <= 1e-2, i
-    assert _rel_l2(dg, dtable_x) <= (1e-2 if grid == "small" else 3e-2)
+    assert _rel_l2(dg, dtable_x) <= 1e-2
 
 
-def test_nrc_adam_step():
+@pytest.mark.parametrize("train_kernels", [0, 1])
+def test_nrc_adam_step(train_kernels):
     rng = np.random.default_rng(2)
-    net = _make(lr=5e-3)
+    net = _make(lr=5e-3, train_kernels=train_kernels)
     wn, gn = _set_random_params(net, rng)
     rec = _records(rng, 2048)
     t = torch.from_numpy(rec).cuda()

@@ -756,10 +756,12 @@ def run_nrc_study(args, local):
 
 def run_batch_study(args, local):
     """64 seeded scenes of uneven size (pushbutton / heavy generators, 1k-500k triangles
-    log-uniform, 256^2 .. 1920x1080, 1-32 spp, depth 8): aggregate samples per second of one
-    persistent batched launch (graph-replayed, tile schedule from pt_autotune_batch on 1-spp
-    copies of the jobs) against the same jobs as per-scene pt_render calls (PT_MODE_AUTO:
-    wavefront from 2^16 pixels with graph replay, megakernel below), both on one stream."""
+    log-uniform, 256^2 .. 1920x1080, 1-32 spp, depth 8): aggregate samples per second of the
+    batch schedules (the one pt_autotune_batch picks on 1-spp copies of the jobs; one persistent
+    megakernel launch; per-job wavefronts on 4 and 8 streams; one merged wavefront for all jobs
+    as a captured graph at 2^21 .. 2^24 paths per wave) against the same jobs as per-scene
+    pt_render calls (PT_MODE_AUTO: wavefront from 2^16 pixels with graph replay, megakernel
+    below), all on one stream."""
     import torch
     from paper_2407_19977_gb300 import api, scenes
     from paper_2407_19977_gb300 import native as N
@@ -802,11 +804,18 @@ def run_batch_study(args, local):
                 "megakernel_one_launch": {"mode": N.PT_MODE_MEGAKERNEL, "streams": 0, "tile_pixels": 32,
                                           "blocks_per_sm": 4, "use_graph": 1},
                 "wavefront_4_streams": {"mode": N.PT_MODE_WAVEFRONT, "streams": 4, "tile_pixels": 0,
+                                        "blocks_per_sm": 0, "use_graph": 0},
+                "wavefront_8_streams": {"mode": N.PT_MODE_WAVEFRONT, "streams": 8, "tile_pixels": 0,
                                         "blocks_per_sm": 0, "use_graph": 0}}
+    for wp in (1 << 21, 1 << 22, 1 << 23, 1 << 24):
+        variants[f"merged_wavefront_{wp >> 20}M_graph"] = {"mode": N.PT_MODE_WAVEFRONT, "streams": 0, "tile_pixels": 0,
+                                                          "blocks_per_sm": 0, "use_graph": 1, "merged": 1,
+                                                          "wave_paths": wp}
     res = {}
     for name, o in variants.items():
         t = timed(lambda: api.render_batch(jobs, tile_pixels=o["tile_pixels"], blocks_per_sm=o["blocks_per_sm"],
-                                           use_graph=bool(o["use_graph"]), mode=o["mode"], streams=o["streams"]))
+                                           use_graph=bool(o["use_graph"]), mode=o["mode"], streams=o["streams"],
+                                           merged=bool(o.get("merged", 0)), wave_paths=o.get("wave_paths", 0)))
         res[name] = {"ms": t, "msamples_per_s": samples / (t * 1e-3) / 1e6, "opts": o,
                      "over_per_scene": t_scene / t}
     out = {"study": "batch", "workload": f"{len(specs)} seeded scenes: pushbutton/heavy generators, "

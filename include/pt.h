@@ -351,7 +351,19 @@ typedef struct {
                                    job count and work-item layout and replayed; the table is
                                    rewritten before each replay, so seeds, sample indices and
                                    cameras may change between calls.  The call then waits for the
-                                   previous graph batch to finish before rewriting the table. */
+                                   previous graph batch to finish before rewriting the table.
+                                   Merged wavefront mode: the same for its launch sequence. */
+    uint32_t merged;            /* wavefront mode, 1: ONE wavefront for all jobs -- the paths of
+                                   every job share each wave's queues and launches (a wave holds
+                                   pixel ranges of several jobs, a job split only along pixels,
+                                   so each pixel's samples are accumulated in sample order); the
+                                   kernels find a path's scene, camera, depth and seed through
+                                   its wave segment; hits are sorted by (job, material) while the
+                                   keys fit (at most 1024).  With use_graph the whole launch
+                                   sequence is one graph.  The batch's rays and paths are counted
+                                   in the first job's scene (pt_get_stats).  0: each job's own
+                                   wavefront on `streams` streams */
+    uint32_t wave_paths;        /* merged mode: paths per wave (0 = 2^22) */
 } pt_batch_opts;
 
 /* Batched rendering of many scenes of uneven size in ONE persistent launch: blocks pop
@@ -377,7 +389,7 @@ pt_status pt_autotune(pt_scene* scene, const pt_camera* camera, uint32_t spp, ui
                       void* cuda_stream);
 /* The same for a batch: each job rendered into scratch accumulators (the jobs' own are not
  * touched); candidates: megakernel with tile_pixels 32..256 x blocks_per_sm (automatic, 2, 4),
- * wavefront with 1, 2, 4, 8 streams. */
+ * wavefront with 1, 2, 4, 8 streams, merged wavefront with 2^22, 2^23, 2^24 paths per wave. */
 pt_status pt_autotune_batch(const pt_job* jobs, uint32_t n_jobs, uint32_t frames, pt_batch_opts* best,
                             float* best_ms, void* cuda_stream);
 

@@ -272,10 +272,13 @@ def bmfr(color: torch.Tensor, features: torch.Tensor, block=32, offset=(0, 0), o
     return out
 
 
-def render_batch(jobs, tile_pixels=0, blocks_per_sm=0, use_graph=False, mode=0, streams=0, stream=None):
-    """jobs: list of (Scene, camera, spp, max_depth, seed, Accum)."""
+def render_batch(jobs, tile_pixels=0, blocks_per_sm=0, use_graph=False, mode=0, streams=0, merged=False,
+                 wave_paths=0, stream=None):
+    """jobs: list of (Scene, camera, spp, max_depth, seed, Accum).  merged (wavefront mode):
+    one wavefront whose waves hold the paths of every job."""
     arr = _job_array(jobs)
-    o = N.pt_batch_opts(mode, streams, tile_pixels, blocks_per_sm, 1 if use_graph else 0)
+    o = N.pt_batch_opts(mode, streams, tile_pixels, blocks_per_sm, 1 if use_graph else 0, 1 if merged else 0,
+                        int(wave_paths))
     N.call("pt_render_batch", arr, len(jobs), C.byref(o), _stream_handle(stream))
 
 
@@ -299,7 +302,8 @@ def autotune_batch(jobs, frames=2, stream=None):
     ms = N.f32()
     N.call("pt_autotune_batch", arr, len(jobs), int(frames), C.byref(best), C.byref(ms), _stream_handle(stream))
     return {"mode": int(best.mode), "streams": int(best.streams), "tile_pixels": int(best.tile_pixels),
-            "blocks_per_sm": int(best.blocks_per_sm), "use_graph": int(best.use_graph)}, float(ms.value)
+            "blocks_per_sm": int(best.blocks_per_sm), "use_graph": int(best.use_graph),
+            "merged": int(best.merged), "wave_paths": int(best.wave_paths)}, float(ms.value)
 
 
 def launch_count() -> int:

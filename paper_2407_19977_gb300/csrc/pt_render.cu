@@ -37,6 +37,8 @@ struct DJob {
     unsigned long long* stats;
     uint32_t tile_begin;          // first work item of this job
     uint32_t n_tiles;
+    uint32_t n_mats;              // materials of the scene
+    uint32_t key_base;            // merged batch waves: first material-sort key of this job
 };
 
 struct PixelCounters {
@@ -337,7 +339,49 @@ struct WfParams {
     float4* rs_i;             // per path: initial reservoir (2 float4)
     float4* rs_f;             // per path: final reservoir (2 float4)
     float* train_samples;     // training sample records (16 floats)
+    // merged batch waves (pt_render_batch): paths of several jobs share a wave
+    const DJob* jobs;
+    const struct WfmSeg* segs;  // this wave's segments
+    uint32_t n_segs;
 };
+
+// A segment of a merged batch wave: samples i0 .. i0 + ns - 1 (relative to the job's first
+// sample of the call) of the job's window pixels pb .. pb + npix - 1; its paths are path0 + i *
+// npix + j (sample-major, as in a single-scene wave) and its pixels pix0 .. pix0 + npix - 1 of
+// the wave's accumulation pass.  A job is split into segments only along pixels, so each
+// pixel's samples stay in sample order from wave to wave.
+struct WfmSeg {
+    uint32_t job, pb, npix, i0, ns, path0, pix0, pad;
+};
+
+// the segment that holds path id (the last one whose first path is <= id)
+__device__ __forceinline__ uint32_t wfm_seg_of(const WfParams& P, uint32_t id) {
+    uint32_t lo = 0, hi = P.n_segs;
+    while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (P.segs[mid].path0 <= id) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// scene, depth, flags and random-number keys of path id of a merged batch wave, from its
+// segment (whose wave-local index the path carries in the w word of its radiance)
+__device__ __forceinline__ void wfm_context(const WfParams& P, uint32_t seg, uint32_t id, DScene& S, VertexRng& rng,
+                                            uint32_t& max_depth, uint32_t& flags, uint32_t& job) {
+    const WfmSeg g = P.segs[seg];
+    const DJob& J = P.jobs[g.job];
+    S = J.S;
+    const uint32_t local = id - g.path0;
+    const uint32_t lp = g.pb + local % g.npix;
+    rng.p = (J.y0 + lp / J.cw) * J.cam.width + (J.x0 + lp % J.cw);
+    rng.s = J.s0 + g.i0 + local / g.npix;
+    rng.k0 = (uint32_t)J.seed;
+    rng.k1 = (uint32_t)(J.seed >> 32);
+    max_depth = J.max_depth;
+    flags = J.flags;
+    job = g.job;
+}
 
 constexpr uint32_t NRC_DIM_TRAIN = 10;   // uniform dimension of the training-path choice
 constexpr uint32_t NRC_TRAIN_END = 4;     // diffuse-ish vertex at which training paths end into the cache
@@ -509,7 +553,7 @@ __device__ __forceinline__ uint32_t hit_key(const DScene& S, const HitRec& h, ui
 // Persistent closest-hit over the input queue.  A warp takes 32 queue slots with one atomic,
 // each lane carries its ray through the per-ray step loop (one BVH node per step), and the
 // warp takes the next 32 once all of its rays are done (lane refill was measured slower).
-template <bool COUNT>
+template <bool COUNT, bool MULTI = false>
 __global__ void __launch_bounds__(128) k_wf_trace(WfParams P, int in_q) {
     __shared__ uint32_t hist[MAX_SORT_KEYS];
     if (P.counters[C_TAIL]) return;
@@ -530,10 +574,19 @@ __global__ void __launch_bounds__(128) k_wf_trace(WfParams P, int in_q) {
         if (slot < count) {
             const float4 ro = P.ray_o[in_q][slot], rd = P.ray_d[in_q][slot];
             HitRec h;
-            trace_closest_t<COUNT>(P.S, xyz(ro), xyz(rd), __int_as_float(0x7f800000), h, tc);
+            uint32_t key = 0;
+            if (MULTI) {
+                // merged batch waves: the ray carries its job in the w word of its origin
+                const DJob& J = P.jobs[__float_as_uint(ro.w)];
+                const DScene S = J.S;
+                trace_closest_t<COUNT>(S, xyz(ro), xyz(rd), __int_as_float(0x7f800000), h, tc);
+                if (sort) key = J.key_base + hit_key(S, h, J.n_mats);
+            } else {
+                trace_closest_t<COUNT>(P.S, xyz(ro), xyz(rd), __int_as_float(0x7f800000), h, tc);
+                if (sort) key = hit_key(P.S, h, P.n_keys - 2);
+            }
             P.hit[slot] = make_float4(h.t, h.u, h.v, __uint_as_float(h.tri));
             if (sort) {
-                const uint32_t key = hit_key(P.S, h, P.n_keys - 2);
                 P.keys[slot] = key;
                 atomicAdd(&hist[key], 1u);
             }
@@ -717,7 +770,7 @@ __global__ void __launch_bounds__(128, 6) k_restir_spatial(WfParams P, uint32_t 
     }
 }
 
-template <bool NRC, bool RIS, bool FUZZ = true>
+template <bool NRC, bool RIS, bool FUZZ = true, bool MULTI = false>
 __global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
     if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[in_q];
@@ -734,6 +787,7 @@ __global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int o
         float3 no = splat3(0.0f), nd = splat3(0.0f);
         ShadowRay sh;
         uint32_t id = 0;
+        float tag = 0.0f;   // merged batch waves: the job, carried by the appended rays
         float4 b4 = make_float4(0, 0, 0, 0);
         if (valid) {
             const uint32_t slot = P.n_keys ? P.perm[i] : i;
@@ -748,14 +802,24 @@ __global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int o
             ps.beta = xyz(b4);
             ps.prev_pdf = b4.w;
             ps.L = xyz(L4);
-            const uint32_t lp = P.pb + id % P.npix;
-            const uint32_t s = sbase + id / P.npix;
             VertexRng rng;
-            rng.p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
-            rng.s = s; rng.k = k; rng.k0 = (uint32_t)seed; rng.k1 = (uint32_t)(seed >> 32);
+            DScene Sm;
+            uint32_t md = 0, fl = 0, job = 0;
+            if constexpr (MULTI) {
+                wfm_context(P, __float_as_uint(L4.w), id, Sm, rng, md, fl, job);
+            } else {
+                const uint32_t lp = P.pb + id % P.npix;
+                rng.p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
+                rng.s = sbase + id / P.npix;
+                rng.k0 = (uint32_t)seed;
+                rng.k1 = (uint32_t)(seed >> 32);
+            }
+            rng.k = k;
             ShadeOut so;
             int r;
-            if (NRC) {
+            if constexpr (MULTI) {
+                r = shade_vertex<false, FUZZ>(Sm, h, xyz(ro), xyz(rd), k, md, fl, rng, ps, so, nullptr, 0u);
+            } else if (NRC) {
                 NrcHook hook;
                 hook.P = &P;
                 hook.id = id;
@@ -767,8 +831,9 @@ __global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int o
                 r = shade_vertex<RIS, FUZZ>(P.S, h, xyz(ro), xyz(rd), k, P.max_depth, P.flags, rng, ps, so, rres,
                                             P.restir_on ? P.restir_L : 0u);
             }
-            P.radiance[id] = make_float4(ps.L.x, ps.L.y, ps.L.z, 0.0f);
+            P.radiance[id] = make_float4(ps.L.x, ps.L.y, ps.L.z, MULTI ? L4.w : 0.0f);
             if (so.rr_end) rr_cnt++;
+            tag = MULTI ? __uint_as_float(job) : 0.0f;
             cont = r == SHADE_CONTINUE;
             shadow = so.has_shadow;
             if (cont) {
@@ -790,14 +855,14 @@ __global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int o
         bs = __shfl_sync(0xffffffffu, bs, 0);
         if (cont) {
             const uint32_t pos = bc + __popc(mc & lt);
-            P.ray_o[out_q][pos] = make_float4(no.x, no.y, no.z, 0.0f);
+            P.ray_o[out_q][pos] = make_float4(no.x, no.y, no.z, tag);
             P.ray_d[out_q][pos] = make_float4(nd.x, nd.y, nd.z, __uint_as_float(id));
         }
         if (shadow) {
             const uint32_t pos = bs + __popc(ms & lt);
             P.sh_o[pos] = make_float4(sh.o.x, sh.o.y, sh.o.z, sh.tmax);
             P.sh_d[pos] = make_float4(sh.d.x, sh.d.y, sh.d.z, __uint_as_float(id));
-            P.sh_c[pos] = make_float4(sh.contrib.x, sh.contrib.y, sh.contrib.z, 0.0f);
+            P.sh_c[pos] = make_float4(sh.contrib.x, sh.contrib.y, sh.contrib.z, tag);
         }
     }
     rr_cnt = warp_sum_u64(rr_cnt);
@@ -806,7 +871,7 @@ __global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int o
 
 // Persistent shadow any-hit over the shadow queue, with the same lane refilling; an
 // unoccluded shadow ray adds its contribution to its path's radiance.
-template <bool COUNT>
+template <bool COUNT, bool MULTI = false>
 __global__ void __launch_bounds__(128) k_wf_shadow(WfParams P) {
     const uint32_t count = P.counters[C_SH];
     if (blockIdx.x == 0 && threadIdx.x == 0 && count) atomicAdd(&P.stats[ST_SHADOW], (unsigned long long)count);
@@ -820,7 +885,15 @@ __global__ void __launch_bounds__(128) k_wf_shadow(WfParams P) {
         const uint32_t slot = base + lane;
         if (slot < count) {
             const float4 so = P.sh_o[slot], sd = P.sh_d[slot];
-            if (!trace_any_t<COUNT>(P.S, xyz(so), xyz(sd), so.w, tc)) {
+            bool occ;
+            if (MULTI) {
+                // merged batch waves: the job rides in the w word of the contribution
+                const DScene S = P.jobs[__float_as_uint(P.sh_c[slot].w)].S;
+                occ = trace_any_t<COUNT>(S, xyz(so), xyz(sd), so.w, tc);
+            } else {
+                occ = trace_any_t<COUNT>(P.S, xyz(so), xyz(sd), so.w, tc);
+            }
+            if (!occ) {
                 const uint32_t id = __float_as_uint(sd.w);
                 const float4 c = P.sh_c[slot];
                 float4 L = P.radiance[id];
@@ -972,7 +1045,7 @@ __global__ void __launch_bounds__(128) k_wf_shadow_coop(WfParams P) {
 // numbers as k_wf_shade), then the shadow ray, whose contribution is added after the vertex's
 // own terms exactly as k_wf_shadow adds it.  It appends nothing, so the later per-bounce
 // launches of the wave find empty queues (and C_TAIL makes the rest of this bounce skip).
-template <bool NRC, bool COUNT, bool RIS, bool FUZZ = true>
+template <bool NRC, bool COUNT, bool RIS, bool FUZZ = true, bool MULTI = false>
 __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32_t k0, uint32_t limit) {
     const uint32_t count = P.counters[in_q];
     if (count == 0 || count > limit) return;
@@ -990,12 +1063,20 @@ __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32
         ps.beta = xyz(b4);
         ps.prev_pdf = b4.w;
         ps.L = xyz(L4);
-        const uint32_t lp = P.pb + id % P.npix;
         VertexRng rng;
-        rng.p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
-        rng.s = sbase + id / P.npix;
-        rng.k0 = (uint32_t)seed;
-        rng.k1 = (uint32_t)(seed >> 32);
+        DScene Sm;
+        uint32_t md = 0, fl = 0, job = 0;
+        if constexpr (MULTI) {
+            wfm_context(P, __float_as_uint(L4.w), id, Sm, rng, md, fl, job);
+        } else {
+            const uint32_t lp = P.pb + id % P.npix;
+            rng.p = (P.y0 + lp / P.cw) * P.cam.width + (P.x0 + lp % P.cw);
+            rng.s = sbase + id / P.npix;
+            rng.k0 = (uint32_t)seed;
+            rng.k1 = (uint32_t)(seed >> 32);
+        }
+        const DScene& S = MULTI ? Sm : P.S;
+        const uint32_t max_depth = MULTI ? md : P.max_depth, flags = MULTI ? fl : P.flags;
         NrcHook hook;
         if (NRC) {
             hook.P = &P;
@@ -1005,20 +1086,20 @@ __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32
         float3 o = xyz(ro), d = xyz(rd);
         for (uint32_t k = k0;; ++k) {
             HitRec h;
-            if (COUNT) trace_closest_t<true>(P.S, o, d, __int_as_float(0x7f800000), h, tc);
-            else trace_closest(P.S, o, d, __int_as_float(0x7f800000), h);
+            if (COUNT) trace_closest_t<true>(S, o, d, __int_as_float(0x7f800000), h, tc);
+            else trace_closest(S, o, d, __int_as_float(0x7f800000), h);
             n_ext++;
             rng.k = k;
             ShadeOut so;
             int r;
-            if (NRC) r = shade_vertex_h(P.S, h, o, d, k, P.max_depth, P.flags, rng, ps, so, hook);
-            else r = shade_vertex<RIS, FUZZ>(P.S, h, o, d, k, P.max_depth, P.flags, rng, ps, so, nullptr,
+            if (NRC) r = shade_vertex_h(S, h, o, d, k, max_depth, flags, rng, ps, so, hook);
+            else r = shade_vertex<RIS, FUZZ>(S, h, o, d, k, max_depth, flags, rng, ps, so, nullptr,
                                              P.restir_on ? P.restir_L : 0u);
             if (so.rr_end) n_rr++;
             if (so.has_shadow) {
                 n_sh++;
-                const bool occ = COUNT ? trace_any_t<true>(P.S, so.sh.o, so.sh.d, so.sh.tmax, sc)
-                                       : trace_any(P.S, so.sh.o, so.sh.d, so.sh.tmax);
+                const bool occ = COUNT ? trace_any_t<true>(S, so.sh.o, so.sh.d, so.sh.tmax, sc)
+                                       : trace_any(S, so.sh.o, so.sh.d, so.sh.tmax);
                 if (!occ) {
                     ps.L.x += so.sh.contrib.x;
                     ps.L.y += so.sh.contrib.y;
@@ -1029,8 +1110,9 @@ __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32
             o = so.next_o;
             d = so.next_d;
         }
-        P.radiance[id] = make_float4(ps.L.x, ps.L.y, ps.L.z, 0.0f);
+        P.radiance[id] = make_float4(ps.L.x, ps.L.y, ps.L.z, MULTI ? L4.w : 0.0f);
         if (NRC) P.aux[id] = hook.aux;
+        (void)job;
     }
     n_ext = warp_sum_u64(n_ext);
     n_sh = warp_sum_u64(n_sh);
@@ -1050,6 +1132,64 @@ __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32
             atomicAdd(&P.stats[ST_TAIL_SH_TRIS], e);
         }
     }
+}
+
+// ---- merged batch waves: raygen and accumulation over a wave's segments
+__global__ void k_wfm_raygen(WfParams P, uint32_t n_paths) {
+    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id == 0) {
+        P.counters[C_Q0] = n_paths;
+        P.counters[C_TAIL] = 0;
+    }
+    if (id >= n_paths) return;
+    const uint32_t si = wfm_seg_of(P, id);
+    const WfmSeg g = P.segs[si];
+    const DJob& J = P.jobs[g.job];
+    const uint32_t local = id - g.path0;
+    const uint32_t lp = g.pb + local % g.npix;
+    const uint32_t s = J.s0 + g.i0 + local / g.npix;
+    const uint32_t px = J.x0 + lp % J.cw, py = J.y0 + lp / J.cw;
+    const uint32_t p = py * J.cam.width + px;
+    float3 o, d;
+    camera_ray_ps(J.cam, px, py, p, s, (uint32_t)J.seed, (uint32_t)(J.seed >> 32), o, d);
+    P.ray_o[0][id] = make_float4(o.x, o.y, o.z, __uint_as_float(g.job));
+    P.ray_d[0][id] = make_float4(d.x, d.y, d.z, __uint_as_float(id));
+    P.beta[id] = make_float4(1.0f, 1.0f, 1.0f, -1.0f);
+    P.radiance[id] = make_float4(0.0f, 0.0f, 0.0f, __uint_as_float(si));
+    if (id == 0) atomicAdd(&P.stats[ST_PATHS], (unsigned long long)n_paths);
+}
+
+// each segment pixel of the wave adds its samples in sample order (Kahan), as k_wf_accum does
+__global__ void k_wfm_accum(WfParams P, uint32_t n_pix) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_pix) return;
+    uint32_t lo = 0, hi = P.n_segs;
+    while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (P.segs[mid].pix0 <= t) lo = mid;
+        else hi = mid;
+    }
+    const WfmSeg g = P.segs[lo];
+    const DJob& J = P.jobs[g.job];
+    const uint32_t j = t - g.pix0;
+    const uint32_t lp = g.pb + j;
+    float* sp = J.sum + 3ull * lp;
+    float* cp = J.comp + 3ull * lp;
+    float s0 = sp[0], s1 = sp[1], s2 = sp[2], c0 = cp[0], c1 = cp[1], c2 = cp[2];
+    unsigned long long nan_cnt = 0;
+    for (uint32_t q = 0; q < g.ns; ++q) {
+        float4 L = P.radiance[g.path0 + q * g.npix + j];
+        if (!isfinite(L.x) || !isfinite(L.y) || !isfinite(L.z)) {
+            nan_cnt++;
+            L = make_float4(0, 0, 0, 0);
+        }
+        kahan_add(s0, c0, L.x);
+        kahan_add(s1, c1, L.y);
+        kahan_add(s2, c2, L.z);
+    }
+    sp[0] = s0; sp[1] = s1; sp[2] = s2;
+    cp[0] = c0; cp[1] = c1; cp[2] = c2;
+    if (nan_cnt) atomicAdd(&P.stats[ST_NAN], nan_cnt);
 }
 
 // Launches with the fuzz layer compiled in only for scenes that have a material with fuzz
@@ -1505,6 +1645,7 @@ static DJob make_job(pt_scene* s, const pt_camera& cam, uint32_t x0, uint32_t y0
     j.comp = acc->comp;
     j.sample_out = sample_out;
     j.stats = s->d_stats;
+    j.n_mats = s->n_mats;
     return j;
 }
 
@@ -1638,6 +1779,239 @@ static pt_status batch_wavefront(const pt_job* jobs, uint32_t n_jobs, uint32_t K
     return r;
 }
 
+// ---- merged batch: the paths of every job share the wavefront waves
+// A wave is a list of segments (WfmSeg), filled in job order: each job's (pixel range x
+// sample range) blocks are the ones a single-scene wavefront of that job would make, and a
+// block that does not fit in the wave's remaining room is split along its pixels.  Every
+// wave runs the single-scene launch sequence (raygen, per bounce: setup, tail, closest hit,
+// shade, shadow rays; accumulation) once for all its jobs, the kernels looking each path's
+// scene, camera, depth and seed up through its segment.  The launch sequence of a batch
+// layout is captured once as a CUDA graph (with the job table copied in from pinned memory
+// at its start, so seeds, first samples and cameras may change between calls) and replayed.
+struct MergedBatch {
+    int device = -1;
+    std::vector<uint64_t> key;      // per job: scene, width, height, spp, max depth; wave size
+    std::vector<WfmSeg> segs;
+    std::vector<uint32_t> wave_seg0, wave_paths, wave_pix;   // per wave: first segment, paths, pixels
+    WaveBuffers wave;
+    DJob* h_jobs = nullptr;
+    DJob* d_jobs = nullptr;
+    WfmSeg* d_segs = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaStream_t cap = nullptr;
+    uint64_t launches = 0;
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (done) cudaEventDestroy(done);
+        if (cap) cudaStreamDestroy(cap);
+        if (h_jobs) cudaFreeHost(h_jobs);
+        if (d_jobs) cudaFree(d_jobs);
+        if (d_segs) cudaFree(d_segs);
+        pt_free_wave(wave);
+        exec = nullptr; done = nullptr; cap = nullptr; h_jobs = nullptr; d_jobs = nullptr; d_segs = nullptr;
+        key.clear();
+        launches = 0;
+    }
+};
+static MergedBatch g_merged;   // guarded by g_batch_mutex
+
+static void merged_layout(const std::vector<DJob>& dj, uint32_t cap, MergedBatch& m) {
+    m.segs.clear();
+    m.wave_seg0.clear();
+    m.wave_paths.clear();
+    m.wave_pix.clear();
+    uint32_t fill = 0, pix = 0;
+    auto close = [&]() {
+        if (fill == 0) return;
+        m.wave_paths.push_back(fill);
+        m.wave_pix.push_back(pix);
+        fill = 0;
+        pix = 0;
+    };
+    for (uint32_t j = 0; j < dj.size(); ++j) {
+        const uint32_t npix = dj[j].cw * dj[j].ch, spp = dj[j].spp;
+        if (npix == 0 || spp == 0) continue;
+        const uint32_t chunk = std::min(npix, cap);
+        const uint32_t spw = std::max(1u, std::min(spp, cap / chunk));
+        for (uint32_t pb = 0; pb < npix; pb += chunk) {
+            const uint32_t np = std::min(chunk, npix - pb);
+            for (uint32_t i0 = 0; i0 < spp; i0 += spw) {
+                const uint32_t ns = std::min(spw, spp - i0);
+                for (uint32_t done = 0; done < np;) {
+                    if (cap - fill < ns) {
+                        close();
+                        continue;
+                    }
+                    const uint32_t take = std::min(np - done, (cap - fill) / ns);
+                    // a wave holds each pixel of a job once: one accumulation thread adds all of
+                    // the pixel's samples of the wave, in order (a later sample block of the same
+                    // pixels waits for the next wave)
+                    bool overlap = false;
+                    if (fill > 0)
+                        for (size_t k = m.wave_seg0.back(); k < m.segs.size() && !overlap; ++k)
+                            overlap = m.segs[k].job == j && m.segs[k].pb < pb + done + take &&
+                                      pb + done < m.segs[k].pb + m.segs[k].npix;
+                    if (overlap) {
+                        close();
+                        continue;
+                    }
+                    if (fill == 0) m.wave_seg0.push_back((uint32_t)m.segs.size());
+                    m.segs.push_back(WfmSeg{j, pb + done, take, i0, ns, fill, pix, 0u});
+                    fill += take * ns;
+                    pix += take;
+                    done += take;
+                    if (fill == cap) close();
+                }
+            }
+        }
+    }
+    close();
+}
+
+static pt_status merged_launches(MergedBatch& m, const WfParams& base, uint32_t max_depth, bool fuzz, cudaStream_t st,
+                                 uint64_t* launches) {
+    const int sms = pt_num_sms();
+    const uint32_t tail_grid = (uint32_t)(sms * g_tail_blocks_per_sm);
+    const uint32_t tail_limit = tail_grid * 128u;
+    for (size_t w = 0; w < m.wave_paths.size(); ++w) {
+        WfParams P = base;
+        const uint32_t seg_end = w + 1 < m.wave_seg0.size() ? m.wave_seg0[w + 1] : (uint32_t)m.segs.size();
+        P.segs = m.d_segs + m.wave_seg0[w];
+        P.n_segs = seg_end - m.wave_seg0[w];
+        const uint32_t n = m.wave_paths[w];
+        PT_LAUNCH(k_wfm_raygen, (n + 255) / 256, 256, 0, st, P, n);
+        ++*launches;
+        for (uint32_t k = 0; k <= max_depth; ++k) {
+            const int in_q = (int)(k & 1u), out_q = (int)((k + 1) & 1u);
+            PT_LAUNCH(k_wf_setup, 1, 256, 0, st, m.wave.counters, out_q, P.n_keys);
+            if (fuzz) PT_LAUNCH((k_wf_tail<false, false, false, true, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+            else PT_LAUNCH((k_wf_tail<false, false, false, false, true>), tail_grid, 128, 0, st, P, in_q, k, tail_limit);
+            PT_LAUNCH((k_wf_trace<false, true>), sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
+            if (P.n_keys) {
+                PT_LAUNCH(k_wf_sort_scan, 1, MAX_SORT_KEYS, 0, st, m.wave.counters, P.n_keys);
+                PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
+                *launches += 2;
+            }
+            if (fuzz) PT_LAUNCH((k_wf_shade<false, false, true, true>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+            else PT_LAUNCH((k_wf_shade<false, false, false, true>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
+            PT_LAUNCH((k_wf_shadow<false, true>), sms * g_shadow_blocks_per_sm, 128, 0, st, P);
+            *launches += 5;
+        }
+        PT_LAUNCH(k_wfm_accum, (m.wave_pix[w] + 255) / 256, 256, 0, st, P, m.wave_pix[w]);
+        ++*launches;
+    }
+    PT_CUDA_TRY(cudaGetLastError());
+    return PT_OK;
+}
+
+static pt_status batch_merged(const pt_job* jobs, uint32_t n_jobs, const pt_batch_opts& bo, cudaStream_t st) {
+    std::vector<DJob> dj;
+    std::vector<uint64_t> key;
+    bool fuzz = false;
+    uint32_t max_depth = 0;
+    const uint32_t cap = std::max(bo.wave_paths ? bo.wave_paths : (1u << 22), 1024u);
+    uint32_t n_keys = 0;   // material sort keys: (job, material) pairs, plus miss and light per job
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        const pt_job& j = jobs[i];
+        dj.push_back(make_job(j.scene, j.camera, 0, 0, j.accum, j.spp, j.max_depth, j.seed, 0, nullptr));
+        dj.back().key_base = n_keys;
+        n_keys += j.scene->n_mats + 2;
+        fuzz = fuzz || j.scene->has_fuzz;
+        max_depth = std::max(max_depth, j.max_depth);
+        key.insert(key.end(), {(uint64_t)(uintptr_t)j.scene, j.camera.width, j.camera.height, j.spp, j.max_depth});
+    }
+    key.push_back(cap);
+    key.push_back(fuzz ? 1u : 0u);
+    wf_occupancy();
+    if (g_tail_blocks_per_sm == 0) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wf_tail<true, false, false>, 128, 0);
+        g_tail_blocks_per_sm = std::max(b, 1);
+    }
+    int dev = 0;
+    PT_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    MergedBatch& m = g_merged;
+    const bool same = m.device == dev && m.key == key && m.d_jobs != nullptr;
+    if (!same) {
+        // a new layout: wait for what the old one may still run, then rebuild
+        if (m.done) cudaEventSynchronize(m.done);
+        m.release();
+        m.device = dev;
+        merged_layout(dj, cap, m);
+        pt_status r = ensure_wave(m.wave, cap);
+        if (r != PT_OK) { m.release(); return r; }
+        if (cudaMallocHost((void**)&m.h_jobs, dj.size() * sizeof(DJob)) != cudaSuccess ||
+            cudaMalloc((void**)&m.d_jobs, dj.size() * sizeof(DJob)) != cudaSuccess ||
+            cudaMalloc((void**)&m.d_segs, std::max<size_t>(m.segs.size(), 1) * sizeof(WfmSeg)) != cudaSuccess) {
+            m.release();
+            pt_set_error("merged batch tables: out of memory");
+            return PT_ERR_OOM;
+        }
+        PT_CUDA_TRY(cudaMemcpy(m.d_segs, m.segs.data(), m.segs.size() * sizeof(WfmSeg), cudaMemcpyHostToDevice));
+        PT_CUDA_TRY(cudaEventCreateWithFlags(&m.done, cudaEventDisableTiming));
+        m.key = key;
+    } else {
+        // the previous call may still read the pinned job table
+        PT_CUDA_TRY(cudaEventSynchronize(m.done));
+    }
+    std::memcpy(m.h_jobs, dj.data(), dj.size() * sizeof(DJob));
+    WfParams P;
+    std::memset(&P, 0, sizeof(P));
+    const WaveBuffers& w = m.wave;
+    for (int q = 0; q < 2; ++q) { P.ray_o[q] = w.ray_o[q]; P.ray_d[q] = w.ray_d[q]; }
+    P.hit = w.hit; P.beta = w.beta; P.radiance = w.radiance;
+    P.sh_o = w.sh_o; P.sh_d = w.sh_d; P.sh_c = w.sh_c;
+    P.perm = w.perm; P.keys = w.keys; P.counters = w.counters;
+    P.stats = jobs[0].scene->d_stats;
+    P.jobs = m.d_jobs;
+    P.n_keys = n_keys <= MAX_SORT_KEYS ? n_keys : 0u;
+    uint64_t launches = 0;
+    if (bo.use_graph) {
+        if (!m.exec) {
+            if (!m.cap) PT_CUDA_TRY(cudaStreamCreateWithFlags(&m.cap, cudaStreamNonBlocking));
+            PT_CUDA_TRY(cudaStreamBeginCapture(m.cap, cudaStreamCaptureModeThreadLocal));
+            const uint64_t before = g_pt_launches.load();
+            cudaMemcpyAsync(m.d_jobs, m.h_jobs, dj.size() * sizeof(DJob), cudaMemcpyHostToDevice, m.cap);
+            uint64_t n_l = 0;
+            const pt_status r = merged_launches(m, P, max_depth, fuzz, m.cap, &n_l);
+            g_pt_launches.fetch_sub(g_pt_launches.load() - before);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(m.cap, &graph);
+            if (r != PT_OK || ce != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                m.release();
+                if (r != PT_OK) return r;
+                pt_set_error(std::string("merged batch capture: ") + cudaGetErrorString(ce));
+                return PT_ERR_CUDA;
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&m.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                m.release();
+                pt_set_error(std::string("merged batch instantiate: ") + cudaGetErrorString(ie));
+                return PT_ERR_CUDA;
+            }
+            m.launches = n_l;
+        }
+        PT_CUDA_TRY(cudaGraphLaunch(m.exec, st));
+        pt_count_launch(m.launches);
+        launches = m.launches;
+    } else {
+        PT_CUDA_TRY(cudaMemcpyAsync(m.d_jobs, m.h_jobs, dj.size() * sizeof(DJob), cudaMemcpyHostToDevice, st));
+        pt_status r = merged_launches(m, P, max_depth, fuzz, st, &launches);
+        if (r != PT_OK) return r;
+    }
+    PT_CUDA_TRY(cudaEventRecord(m.done, st));
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        jobs[i].scene->last_stream = st;
+        jobs[i].accum->spp_done += jobs[i].spp;
+    }
+    jobs[0].scene->launches += launches;
+    return PT_OK;
+}
+
 extern "C" pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const pt_batch_opts* opts, void* cuda_stream) {
     PT_CHECK_ARG(jobs != nullptr || n_jobs == 0, "jobs is NULL");
     if (n_jobs == 0) return PT_OK;
@@ -1661,6 +2035,7 @@ extern "C" pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const 
         j.scene->last_stream = st;
     }
     PT_CHECK_ARG(bo.mode == PT_MODE_AUTO || bo.mode == PT_MODE_WAVEFRONT || bo.mode == PT_MODE_MEGAKERNEL, "unknown mode");
+    if (bo.mode == PT_MODE_WAVEFRONT && bo.merged) return batch_merged(jobs, n_jobs, bo, st);
     if (bo.mode == PT_MODE_WAVEFRONT) {
         const uint32_t K = std::min(bo.streams ? bo.streams : 4u, 16u);
         return batch_wavefront(jobs, n_jobs, K, st);

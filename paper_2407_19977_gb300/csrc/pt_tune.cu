@@ -199,6 +199,16 @@ extern "C" pt_status pt_autotune_batch(const pt_job* jobs, uint32_t n_jobs, uint
         o.streams = k;
         cand.push_back(o);
     }
+    // one merged wavefront for all jobs (a captured graph), at three wave sizes
+    for (uint32_t wp : {1u << 22, 1u << 23, 1u << 24}) {
+        pt_batch_opts o;
+        std::memset(&o, 0, sizeof(o));
+        o.mode = PT_MODE_WAVEFRONT;
+        o.merged = 1;
+        o.wave_paths = wp;
+        o.use_graph = 1;
+        cand.push_back(o);
+    }
     for (const pt_batch_opts& o : cand) {
         float t = 0.0f;
         for (auto& a : accs) a.spp_done = 0;

@@ -73,7 +73,8 @@ class pt_job(C.Structure):
 
 
 class pt_batch_opts(C.Structure):
-    _fields_ = [("mode", u32), ("streams", u32), ("tile_pixels", u32), ("blocks_per_sm", u32), ("use_graph", u32)]
+    _fields_ = [("mode", u32), ("streams", u32), ("tile_pixels", u32), ("blocks_per_sm", u32), ("use_graph", u32),
+                ("merged", u32), ("wave_paths", u32)]
 
 
 class pt_nrc_opts(C.Structure):

@@ -834,6 +834,35 @@ def test_batch_wavefront_streams_equal_single_renders(api):
         assert torch.equal(acc.sum, one.sum)
 
 
+@pytest.mark.parametrize("wave_paths,graph", [(0, False), (2500, False), (2500, True), (7000, True)])
+def test_batch_merged_wavefront_equals_single_renders(api, wave_paths, graph):
+    """Merged wavefront batch: the paths of every job share the waves (small waves force jobs
+    to be split along pixels across several waves; 2500 paths is less than one job's frame);
+    mixed depths, a fuzz scene and two jobs of one scene.  Every job's accumulators equal the
+    job rendered alone, bit for bit, over two calls (graph capture and replay included)."""
+    from paper_2407_19977_gb300 import api as A
+    from paper_2407_19977_gb300 import native as N
+    mk, gs = _batch_scenes()
+    velvet = scenes.pushbutton_fuzz(width=40, height=30)
+    mk, gs = mk + [velvet, mk[1]], gs + [A.Scene(velvet), gs[1]]
+    accs = [A.Accum(s.camera.width, s.camera.height) for s in mk]
+    depths = [5, 8, 3, 6, 4][:len(mk)]
+    for call in range(2):
+        jobs = [(g, s.camera, 2 + i % 3, depths[i], 300 + i + 7 * call, a)
+                for i, (s, g, a) in enumerate(zip(mk, gs, accs))]
+        A.render_batch(jobs, mode=N.PT_MODE_WAVEFRONT, merged=True, wave_paths=wave_paths, use_graph=graph)
+    torch.cuda.synchronize()
+    for i, (s, g, acc) in enumerate(zip(mk, gs, accs)):
+        one = A.Accum(s.camera.width, s.camera.height)
+        for call in range(2):
+            g.render(2 + i % 3, max_depth=depths[i], seed=300 + i + 7 * call, accum=one, mode=N.PT_MODE_WAVEFRONT)
+        torch.cuda.synchronize()
+        assert acc.spp_done == one.spp_done
+        assert torch.equal(acc.sum, one.sum) and torch.equal(acc.comp, one.comp), (i, wave_paths, graph)
+    for g in gs:
+        assert g.stats()["error_flags"] == 0
+
+
 def test_autotune_batch_leaves_jobs_untouched(api):
     from paper_2407_19977_gb300 import api as A
     mk, gs = _batch_scenes()

@@ -78,6 +78,7 @@ def _load():
         lib.oracle_sheen_albedo.restype = C.c_double
         lib.oracle_sheen_f.argtypes = [_dp, _dp, C.c_double]
         lib.oracle_sheen_f.restype = C.c_double
+        lib.oracle_sah_reference.argtypes = [_dp, C.c_int, C.c_int, _dp]
         lib.oracle_scene_create.argtypes = [_dp, C.c_int, _u32p, C.c_int, _u32p, _dp, C.c_int,
                                             _dp, C.c_int, _dp, C.c_int, C.c_int, C.c_int]
         lib.oracle_scene_create.restype = C.c_void_p
@@ -190,6 +191,15 @@ def sheen_f(wo, wi, alpha):
     wo, po = _d(wo)
     wi, pi = _d(wi)
     return _load().oracle_sheen_f(po, pi, float(alpha))
+
+
+def sah_reference(verts, leaf_max=4):
+    """Surface-area cost of a binned-SAH binary BVH over the triangles (n, 3, 3): expected box
+    tests and triangle tests of a ray through the root box, and the tree's node count."""
+    v, pv = _d(np.asarray(verts, dtype=np.float64).reshape(-1, 9))
+    out = np.zeros(3)
+    _load().oracle_sah_reference(pv, int(v.shape[0]), int(leaf_max), out.ctypes.data_as(_dp))
+    return {"box_tests": float(out[0]), "tri_tests": float(out[1]), "nodes": int(out[2])}
 
 
 def bsdf_eval(mat, front, wo, wi):

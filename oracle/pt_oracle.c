@@ -821,6 +821,130 @@ static void build_bvh(oscene* S) {
     free(r);
 }
 
+/* ---- reference BVH quality: a binned surface-area-heuristic build ----
+ * The quality of a BVH is judged here by the work a ray that enters the root box does on
+ * average when it is tested against every box it meets (no early exit): with the probability
+ * of meeting a box taken as its surface area over the root's (a uniform ray density, the
+ * surface area heuristic of Goldsmith & Salmon, MacDonald & Booth),
+ *   box tests = sum over internal nodes of A(node) / A(root) * (children of the node),
+ *   triangle tests = sum over leaves of A(leaf) / A(root) * (triangles of the leaf).
+ * The reference tree is binary, built top down: at each node 32 bins of the triangles'
+ * centroids per axis, the split that minimises 2 + (A_L n_L + A_R n_R) / A (two child box
+ * tests, then the triangles below, costed by the leaf estimate), a leaf when that is not
+ * below n and n <= leaf_max.  It shares nothing with the device build (Morton codes, a radix
+ * tree, an 8-wide collapse). */
+static double box_area(const double lo[3], const double hi[3]) {
+    double dx = fmax(hi[0] - lo[0], 0.0), dy = fmax(hi[1] - lo[1], 0.0), dz = fmax(hi[2] - lo[2], 0.0);
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+}
+
+#define SAH_BINS 32
+static void sah_rec(prim_ref* r, int count, int leaf_max, double root_area, double* box_tests, double* tri_tests,
+                    int* n_nodes) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < count; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], r[i].lo[a]);
+            hi[a] = fmax(hi[a], r[i].hi[a]);
+            clo[a] = fmin(clo[a], r[i].c[a]);
+            chi[a] = fmax(chi[a], r[i].c[a]);
+        }
+    const double area = box_area(lo, hi);
+    (*n_nodes)++;
+    double best = INFINITY;
+    int best_axis = -1, best_bin = -1;
+    for (int a = 0; a < 3 && count > 1; ++a) {
+        const double ext = chi[a] - clo[a];
+        if (!(ext > 0.0)) continue;
+        int bn[SAH_BINS] = {0};
+        double blo[SAH_BINS][3], bhi[SAH_BINS][3];
+        for (int b = 0; b < SAH_BINS; ++b)
+            for (int k = 0; k < 3; ++k) { blo[b][k] = INFINITY; bhi[b][k] = -INFINITY; }
+        for (int i = 0; i < count; ++i) {
+            int b = (int)(SAH_BINS * (r[i].c[a] - clo[a]) / ext);
+            if (b >= SAH_BINS) b = SAH_BINS - 1;
+            bn[b]++;
+            for (int k = 0; k < 3; ++k) {
+                blo[b][k] = fmin(blo[b][k], r[i].lo[k]);
+                bhi[b][k] = fmax(bhi[b][k], r[i].hi[k]);
+            }
+        }
+        /* sweep: left areas and counts from the low side, right from the high side */
+        double la[SAH_BINS], ra[SAH_BINS];
+        int ln[SAH_BINS], rn[SAH_BINS];
+        double l0[3] = {INFINITY, INFINITY, INFINITY}, l1[3] = {-INFINITY, -INFINITY, -INFINITY};
+        int c = 0;
+        for (int b = 0; b < SAH_BINS; ++b) {
+            c += bn[b];
+            for (int k = 0; k < 3; ++k) { l0[k] = fmin(l0[k], blo[b][k]); l1[k] = fmax(l1[k], bhi[b][k]); }
+            ln[b] = c;
+            la[b] = c ? box_area(l0, l1) : 0.0;
+        }
+        double r0[3] = {INFINITY, INFINITY, INFINITY}, r1[3] = {-INFINITY, -INFINITY, -INFINITY};
+        c = 0;
+        for (int b = SAH_BINS - 1; b >= 0; --b) {
+            c += bn[b];
+            for (int k = 0; k < 3; ++k) { r0[k] = fmin(r0[k], blo[b][k]); r1[k] = fmax(r1[k], bhi[b][k]); }
+            rn[b] = c;
+            ra[b] = c ? box_area(r0, r1) : 0.0;
+        }
+        for (int b = 0; b + 1 < SAH_BINS; ++b) {
+            if (ln[b] == 0 || rn[b + 1] == 0) continue;
+            const double cost = 2.0 + (la[b] * ln[b] + ra[b + 1] * rn[b + 1]) / area;
+            if (cost < best) { best = cost; best_axis = a; best_bin = b; }
+        }
+    }
+    if (count <= leaf_max && !(best < (double)count)) best_axis = -1;
+    if (best_axis < 0 && count > leaf_max) {
+        /* every centroid in one bin: split the list in halves */
+        const int half = count / 2;
+        *box_tests += 2.0 * area / root_area;
+        sah_rec(r, half, leaf_max, root_area, box_tests, tri_tests, n_nodes);
+        sah_rec(r + half, count - half, leaf_max, root_area, box_tests, tri_tests, n_nodes);
+        return;
+    }
+    if (best_axis < 0) {
+        *tri_tests += area / root_area * count;
+        return;
+    }
+    const double ext = chi[best_axis] - clo[best_axis];
+    int i = 0, j = count - 1;
+    while (i <= j) {
+        int b = (int)(SAH_BINS * (r[i].c[best_axis] - clo[best_axis]) / ext);
+        if (b >= SAH_BINS) b = SAH_BINS - 1;
+        if (b <= best_bin) ++i;
+        else { swap_ref(&r[i], &r[j]); --j; }
+    }
+    *box_tests += 2.0 * area / root_area;
+    sah_rec(r, i, leaf_max, root_area, box_tests, tri_tests, n_nodes);
+    sah_rec(r + i, count - i, leaf_max, root_area, box_tests, tri_tests, n_nodes);
+}
+
+/* verts: n_tris * 9 doubles (three vertices per triangle); out: box tests, triangle tests,
+ * nodes of the reference binned-SAH tree */
+void oracle_sah_reference(const double* verts, int n_tris, int leaf_max, double* out) {
+    out[0] = out[1] = out[2] = 0.0;
+    if (n_tris <= 0) return;
+    prim_ref* r = (prim_ref*)malloc(sizeof(prim_ref) * (size_t)n_tris);
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < n_tris; ++i) {
+        for (int ax = 0; ax < 3; ++ax) {
+            double x = verts[9 * i + ax], y = verts[9 * i + 3 + ax], z = verts[9 * i + 6 + ax];
+            r[i].lo[ax] = fmin(x, fmin(y, z));
+            r[i].hi[ax] = fmax(x, fmax(y, z));
+            r[i].c[ax] = (x + y + z) / 3.0;
+            lo[ax] = fmin(lo[ax], r[i].lo[ax]);
+            hi[ax] = fmax(hi[ax], r[i].hi[ax]);
+        }
+        r[i].id = i;
+    }
+    int nodes = 0;
+    sah_rec(r, n_tris, leaf_max, box_area(lo, hi), &out[0], &out[1], &nodes);
+    out[2] = nodes;
+    free(r);
+}
+
 /* ---- environment map tables (reading: piecewise-constant 2D distribution over texels,
  *      weight = luminance * sin(theta at the texel centre)) ---- */
 static void build_env(oscene* S) {

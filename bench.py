@@ -77,11 +77,14 @@ def _args():
     ap.add_argument("--graph", type=int, default=1, help="replay each frame's wavefront launches as a CUDA graph")
     ap.add_argument("--mode", default="wavefront", choices=["auto", "wavefront", "megakernel"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spp-per-step", type=int, default=4,
+                    help="samples per pixel of the frame one step renders (progressive: each step adds them)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     ap.add_argument("--study-frames", type=int, default=256, help="frames per curve of the NRC study")
     ap.add_argument("--batch-scenes", type=int, default=64)
-    ap.add_argument("--study", default=None, choices=[None, "nrc", "batch", "paper", "restir", "bmfr"],
-                    help="nrc: relMSE vs time, radiance cache against the plain tracer")
+    ap.add_argument("--study", default=None, choices=[None, "nrc", "nrc_train", "batch", "paper", "restir", "bmfr"],
+                    help="nrc: relMSE vs time, radiance cache against the plain tracer; nrc_train: the "
+                         "radiance-cache training and inference kernels alone")
     ap.add_argument("--ref-spp", type=int, default=4096)
     ap.add_argument("--max-depth", type=int, default=None, help="studies: override the workload's max depth")
     ap.add_argument("--nrc-batch", type=int, default=8192, help="NRC study: training samples per Adam step")
@@ -126,15 +129,17 @@ def _metric_name(workload: str) -> str:
 
 def _source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_2407_19977_gb300/csrc/pt_device.cuh", "paper_2407_19977_gb300/csrc/pt_render.cu"):
+    for rel in ("paper_2407_19977_gb300/csrc/pt_device.cuh", "paper_2407_19977_gb300/csrc/pt_render.cu",
+                "paper_2407_19977_gb300/csrc/pt_bvh.cu"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def _recorded_traffic(kernel: str):
+def _recorded_traffic(kernel: str, workload: str, spp_per_step: int):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
-    current kernel source (the summary records the source hash); else None."""
+    current kernel source (the summary records the source hash) and on this launch shape (the
+    workload and the samples per step, which set the wave size); else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -145,6 +150,8 @@ def _recorded_traffic(kernel: str):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
     if vals.get("source_hash") != _source_hash():
+        return None
+    if vals.get("workload") != workload or vals.get("spp_per_step") != str(spp_per_step):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -396,13 +403,13 @@ def run_ours(args, world, rank, local):
     if args.tune:
         # untimed: the schedule (wavefront/megakernel, tail limit, sort, wave size) that renders
         # this frame fastest; PT_MODE_AUTO then uses it
-        tuned, tuned_ms = scene.autotune(spp=1, frames=2)
+        tuned, tuned_ms = scene.autotune(spp=args.spp_per_step, frames=2)
         mode = N.PT_MODE_AUTO
     acc = api.Accum(W, H)
     seed = 1000 * rank
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     for _ in range(args.warmup):
-        scene.render(1, seed=seed, accum=acc, mode=mode, use_graph=args.graph)
+        scene.render(args.spp_per_step, seed=seed, accum=acc, mode=mode, use_graph=args.graph)
     torch.cuda.synchronize()
     # untimed instrumented frame at the first timed sample index: node visits and triangle
     # tests per ray give the traversal's algorithmic bytes
@@ -410,7 +417,7 @@ def run_ours(args, world, rank, local):
     probe = api.Accum(W, H)
     probe.c.spp_done = s_first
     before = scene.stats()
-    scene.render(1, seed=seed, accum=probe, mode=mode, flags=N.PT_FLAG_COUNT)
+    scene.render(args.spp_per_step, seed=seed, accum=probe, mode=mode, flags=N.PT_FLAG_COUNT)
     after = scene.stats()
     cnt = {k: after[k] - before[k] for k in ("ext_rays", "shadow_rays", "trace_nodes", "trace_tris",
                                              "shadow_nodes", "shadow_tris", "tail_ext_rays")}
@@ -436,7 +443,7 @@ def run_ours(args, world, rank, local):
         for k in range(args.steps):
             flush.fill_(float(k))  # L2 flush between steps, outside the timed events
             starts[k].record(stream)
-            scene.render(1, seed=seed, accum=acc, mode=mode, use_graph=args.graph)
+            scene.render(args.spp_per_step, seed=seed, accum=acc, mode=mode, use_graph=args.graph)
             ends[k].record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -447,13 +454,13 @@ def run_ours(args, world, rank, local):
     # are kept out of the headline timing)
     for k in range(args.steps):
         flush.fill_(float(k))
-        scene.render(1, seed=seed, accum=acc, mode=mode, kernel_ms=kernel_ms, kernel_launches=kernel_launches)
+        scene.render(args.spp_per_step, seed=seed, accum=acc, mode=mode, kernel_ms=kernel_ms, kernel_launches=kernel_launches)
     torch.cuda.synchronize()
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     rays = (st_after["ext_rays"] - st_before["ext_rays"]) + (st_after["shadow_rays"] - st_before["shadow_rays"])
     t_max, rays_all = combine_replicas(dev_ms, float(rays), dev if world > 1 else None)
     value = rays_all / (t_max * 1e-3) / 1e6
-    spp_s = world * args.steps / (t_max * 1e-3)
+    spp_s = world * args.steps * args.spp_per_step / (t_max * 1e-3)
     # end to end through the public API: the step's inputs cross host->device (the camera and
     # seed, marshalled into the launch) and every frame estimate comes back to pinned host
     # memory.  Double-buffered: the frame is snapshotted on the device, then copied to the host
@@ -476,7 +483,7 @@ def run_ours(args, world, rank, local):
             done[b].synchronize()                 # frame k - 2 is on the host
             compute.wait_event(done[b])
         cam_k = type(cam)(**cam.__dict__)
-        scene.render(1, seed=seed, accum=acc, mode=mode, camera=cam_k, use_graph=args.graph)
+        scene.render(args.spp_per_step, seed=seed, accum=acc, mode=mode, camera=cam_k, use_graph=args.graph)
         stage[b].copy_(acc.sum)
         ready = torch.cuda.Event()
         ready.record(compute)
@@ -502,14 +509,15 @@ def run_ours(args, world, rank, local):
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     sm_ghz = float(_peaks()[0].get("sm_max_mhz", SM_MAX_GHZ * 1e3)) / 1e3
     alu_peak = alu_peak_gops(sm_count, sm_ghz)
-    traffic = _recorded_traffic("trace")
+    traffic = _recorded_traffic("trace", args.workload, args.spp_per_step)
     trace_launches = max(kl["trace"], 1)
     result = {
         "metric": _metric_name(args.workload),
         "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "mode": "auto (autotuned)" if tuned else args.mode,
+        "config": {"workload": WORKLOADS[args.workload].replace("1 spp/step", f"{args.spp_per_step} spp/step"),
+                   "spp_per_step": args.spp_per_step, "mode": "auto (autotuned)" if tuned else args.mode,
                    "l2": "flushed between steps",
                    "parallelism": f"replicas x{world}", "cuda_graph": bool(args.graph),
                    "schedule": ({"autotuned": tuned} if tuned else {"mode": args.mode})},
@@ -751,6 +759,73 @@ def run_nrc_study(args, local):
         tn = time_to(curves["nrc"], target)
         out[f"at_plain_{spp}spp"] = {"relmse": target, "plain_ms": tp, "nrc_ms": tn,
                                      "speedup": (tp / tn) if tn else None}
+    # the equal-time factor splits into the error removed per sample and the time each sample
+    # costs: at equal spp, plain relMSE / NRC relMSE and NRC ms / plain ms
+    out["per_spp"] = [{"spp": a["spp"], "relmse_plain_over_nrc": a["relmse"] / b["relmse"],
+                       "ms_nrc_over_plain": b["ms"] / a["ms"]}
+                      for a, b in zip(curves["plain"], curves["nrc"])]
+    print(json.dumps(out))
+
+
+def run_nrc_train_study(args, local):
+    """Radiance-cache kernels alone at the production configuration (16 levels x 2^19 entries,
+    64-wide 4-hidden MLP): one frame's online training (65,536 samples by default, Adam steps of
+    8,192) with the fused tcgen05 kernel and with the multi-kernel path, and inference on one
+    1080p frame of queries with each inference kernel.  Synthetic records: positions uniform in
+    the unit box, directions and normals uniform on the sphere, roughness and targets uniform.
+    MLP FLOPs per sample: forward 2 (4 * 64 * 64 + 3 * 64); training three times that (forward,
+    input gradients, weight gradients)."""
+    import numpy as np
+    import torch
+    from paper_2407_19977_gb300 import api
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+
+    def records(rng, n):
+        rec = np.zeros((n, 16), np.float32)
+        rec[:, 0:3] = rng.random((n, 3))
+        d = rng.normal(size=(n, 3))
+        rec[:, 3:6] = d / np.linalg.norm(d, axis=1, keepdims=True)
+        m = rng.normal(size=(n, 3))
+        rec[:, 6:9] = m / np.linalg.norm(m, axis=1, keepdims=True)
+        rec[:, 9] = rng.random(n)
+        rec[:, 10:13] = rng.random((n, 3))
+        return torch.from_numpy(rec).to("cuda")
+
+    rng = np.random.default_rng(0)
+    n_train = args.nrc_frame_samples
+    train = records(rng, n_train)
+    queries = records(rng, 1920 * 1080)
+    flops_fwd = 2.0 * (4 * 64 * 64 + 3 * 64)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps
+
+    out = {"study": "nrc_kernels", "grid": "16 levels x 2^19 entries x 2 FP16 features", "mlp": "64 wide, 4 hidden",
+           "train_samples_per_frame": n_train, "batch": args.nrc_batch, "infer_queries": queries.shape[0],
+           "steps": args.steps, "train": {}, "infer": {}}
+    for tk, name in ((0, "fused_tcgen05"), (1, "multi_kernel")):
+        net = api.Nrc(batch=args.nrc_batch, seed=3, train_kernels=tk)
+        ms = timed(lambda: net.train(train))
+        out["train"][name] = {"ms_per_frame": ms, "ms_per_batch": ms * args.nrc_batch / n_train,
+                              "mlp_tflops": 3 * flops_fwd * n_train / (ms * 1e-3) / 1e12,
+                              "final_loss": net.last_loss()}
+        del net
+    for tc, name in ((False, "mma_sync"), (True, "tcgen05")):
+        net = api.Nrc(batch=args.nrc_batch, seed=3, tcgen05=tc)
+        net.train(train)
+        ms = timed(lambda: net.infer(queries))
+        out["infer"][name] = {"ms_per_frame": ms, "mlp_tflops": flops_fwd * queries.shape[0] / (ms * 1e-3) / 1e12}
+        del net
     print(json.dumps(out))
 
 
@@ -923,6 +998,10 @@ def main():
     if args.study == "batch":
         if rank == 0:
             run_batch_study(args, local)
+        return
+    if args.study == "nrc_train":
+        if rank == 0:
+            run_nrc_train_study(args, local)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -375,8 +375,9 @@ pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const pt_batch_op
 /* Autotuner of the execution schedule (beyond the paper).  Renders `frames` frames (after one
  * warm-up frame) of `spp` samples per candidate into a scratch accumulator of camera->width x
  * height and times them with CUDA events on the stream; candidates: wavefront with material
- * sort off/on x tail limit (off, automatic, a quarter, four times) x wave size (2^20, 2^21,
- * 2^22 paths), graph replay on; megakernel with 32, 64, 128 pixels per work item.  With
+ * sort off/on x tail limit (off, automatic, a quarter, four times) x wave size (2^20 .. 2^23
+ * paths, as far as the call needs them), graph replay on; megakernel with 32, 64, 128 pixels
+ * per work item; then the winner's traversal passes one ray per lane or per 8-lane group.  With
  * PT_TUNE_BVH it first rebuilds the BVH with leaf sizes 1..4 (the node width is fixed at 8
  * by the node format) and keeps the fastest.  The winner goes to *best (and ms per frame to
  * *best_ms) and is stored in the scene: pt_render with PT_MODE_AUTO then uses it for frames

@@ -103,8 +103,8 @@ extern "C" pt_status pt_autotune(pt_scene* s, const pt_camera* camera, uint32_t 
     const uint32_t npix = W * H;
     for (int sort = 0; sort <= 1; ++sort)
         for (int tail : {-1, 0, 1, 2})   // off, automatic, a quarter of it, four times it
-            for (uint32_t wave : {1u << 20, 1u << 21, 1u << 22}) {
-                if (wave > (1u << 20) && (uint64_t)npix * spp <= (1u << 20)) continue;   // one wave anyway
+            for (uint32_t wave : {1u << 20, 1u << 21, 1u << 22, 1u << 23}) {
+                if (wave > (1u << 20) && (uint64_t)npix * spp <= wave / 2) continue;   // the smaller wave holds it all
                 pt_render_opts o = base;
                 o.sort_by_material = sort;
                 o.tail_paths = tail;   // resolved below

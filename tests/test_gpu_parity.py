@@ -326,6 +326,31 @@ def test_closest_hit_parity(api, which, coop):
 
 
 @pytest.mark.parametrize("which", ["cornell", "pushbutton", "heavy"])
+def test_bvh_structure_and_surface_area_cost(api, which):
+    """The exported 8-wide tree is sound (one parent per node, each triangle in one leaf,
+    every decoded box holding what lies below it) and its surface-area cost is compared with
+    a binned-SAH binary tree built by the oracle on the same triangles.  The comparable
+    measure is the expected number of triangle tests (leaf areas times counts, leaves of at
+    most four in both): a Morton-order build is known to give up some of it to a SAH sweep;
+    the test bounds the loss at 1.5x and prints both trees' figures."""
+    from paper_2407_19977_gb300 import bvh_check
+    sc, gsc, osc = {"cornell": cornell, "pushbutton": pushbutton, "heavy": heavy}[which]()
+    nodes, tris = gsc.export_bvh()
+    tv = _tri_vertices(sc)
+    assert tris.shape[0] == tv.shape[0]
+    problems, stats = bvh_check.check(nodes, tris)
+    assert problems == [], problems
+    dev = bvh_check.sah_cost(nodes, tris)
+    ref = oracle.sah_reference(tv)
+    print(f"\nbvh {which}: {stats}\n  device {dev}\n  binned-SAH binary {ref}; "
+          f"triangle tests device/reference {dev['tri_tests_exact'] / ref['tri_tests']:.3f}, "
+          f"wide node visits {dev['node_visits']:.2f} vs binary node visits {ref['box_tests'] / 2:.2f}")
+    assert dev["tri_tests_exact"] <= 1.5 * ref["tri_tests"]
+    # the 8-bit boxes the traversal tests are conservative: never below the exact measure
+    assert dev["tri_tests"] >= dev["tri_tests_exact"] * (1 - 1e-6)
+
+
+@pytest.mark.parametrize("which", ["cornell", "pushbutton", "heavy"])
 def test_cooperative_traversal_equals_per_lane(api, which):
     """The cooperative traversal visits the nodes the per-lane one visits, in the same order:
     the same hit (id, t, barycentrics) and the same node and triangle counts for every ray,
@@ -455,17 +480,19 @@ def test_image_parity_heavy_crops(api, crop):
     _samples_check(gs, os_, f"heavy crop {crop}")
 
 
-def test_full_frame_bench_configuration(api):
-    """1080p pushbutton, whole frame, one sample per pixel, wavefront: the launch the benchmark
-    times.  The oracle checks every 45th row."""
+@pytest.mark.parametrize("spp,wave", [(1, 0), (4, 1 << 23)])
+def test_full_frame_bench_configuration(api, spp, wave):
+    """1080p pushbutton, whole frame, wavefront: one sample per pixel, and the benchmark's step
+    of four samples in one wave of 2^23 paths (the largest wave its autotuner tries), with
+    material sort and the tail kernel.  The oracle checks every 45th row."""
     from paper_2407_19977_gb300 import api as A
     sc, gsc, osc = pushbutton()
     acc = A.Accum(sc.camera.width, sc.camera.height)
-    gsc.render(1, seed=0, accum=acc, mode=1)
+    gsc.render(spp, seed=0, accum=acc, mode=1, wave_paths=wave, sort=1)
     torch.cuda.synchronize()
     g = acc.sum.cpu().numpy()
-    o, _, st = osc.render(spp=1, seed=0, row_step=45)
-    _image_check(g[::45], o[::45], "pushbutton 1080p rows")
+    o, _, st = osc.render(spp=spp, seed=0, row_step=45)
+    _image_check(g[::45], o[::45], f"pushbutton 1080p rows, {spp} spp")
 
 
 def test_full_frame_fuzz_configuration(api):
@@ -871,8 +898,20 @@ def test_autotune_batch_leaves_jobs_untouched(api):
     best, ms = A.autotune_batch(jobs, frames=1)
     torch.cuda.synchronize()
     assert ms > 0
-    assert best["tile_pixels"] in (32, 64, 128, 256) or best["streams"] in (1, 2, 4, 8)
+    # one of the candidates: a megakernel tile size, per-job wavefronts on K streams, or the
+    # merged wavefront with one of its wave sizes
+    assert (best["tile_pixels"] in (32, 64, 128, 256) or best["streams"] in (1, 2, 4, 8)
+            or (best["merged"] == 1 and best["wave_paths"] in (1 << 22, 1 << 23, 1 << 24))), best
     assert all(a.spp_done == 0 and float(a.sum.abs().sum()) == 0.0 for a in accs)
+    # and the chosen schedule renders what the jobs render one by one
+    A.render_batch(jobs, tile_pixels=best["tile_pixels"], blocks_per_sm=best["blocks_per_sm"],
+                   use_graph=bool(best["use_graph"]), mode=best["mode"], streams=best["streams"],
+                   merged=bool(best["merged"]), wave_paths=best["wave_paths"])
+    for s, g, a in zip(mk, gs, accs):
+        one = A.Accum(s.camera.width, s.camera.height)
+        g.render(2, max_depth=5, seed=7, accum=one, mode=best["mode"] if best["mode"] else 1)
+        torch.cuda.synchronize()
+        assert torch.equal(a.sum, one.sum) and torch.equal(a.comp, one.comp), best
 
 
 def test_bvh_leaf_size_does_not_change_samples(api):

@@ -77,6 +77,8 @@ def _args():
     ap.add_argument("--graph", type=int, default=1, help="replay each frame's wavefront launches as a CUDA graph")
     ap.add_argument("--mode", default="wavefront", choices=["auto", "wavefront", "megakernel"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bvh-builder", default="ploc", choices=["ploc", "lbvh"],
+                    help="binary tree the 8-wide BVH is collapsed from: clustering (default) or radix tree")
     ap.add_argument("--spp-per-step", type=int, default=4,
                     help="samples per pixel of the frame one step renders (progressive: each step adds them)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
@@ -393,8 +395,11 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     upload_ms = (time.perf_counter() - t0) * 1e3
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    builder = {"ploc": N.PT_BVH_PLOC, "lbvh": N.PT_BVH_LBVH}[args.bvh_builder]
+    scene.build(builder=builder)           # first build: allocations and module load
+    torch.cuda.synchronize()
     ev0.record(stream)
-    scene.build()
+    scene.build(builder=builder)
     ev1.record(stream)
     torch.cuda.synchronize()
     bvh_ms = ev0.elapsed_time(ev1)
@@ -517,7 +522,8 @@ def run_ours(args, world, rank, local):
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload].replace("1 spp/step", f"{args.spp_per_step} spp/step"),
-                   "spp_per_step": args.spp_per_step, "mode": "auto (autotuned)" if tuned else args.mode,
+                   "spp_per_step": args.spp_per_step, "bvh_builder": args.bvh_builder,
+                   "mode": "auto (autotuned)" if tuned else args.mode,
                    "l2": "flushed between steps",
                    "parallelism": f"replicas x{world}", "cuda_graph": bool(args.graph),
                    "schedule": ({"autotuned": tuned} if tuned else {"mode": args.mode})},

@@ -232,8 +232,19 @@ enum {
                                    more instructions per ray: slower on the CAD frames) */
 };
 
+/* Binary tree that the 8-wide BVH is collapsed from (Sec. 5.1.1 builds an AABB hierarchy on
+ * the CPU; here both builders run on the device over the same 63-bit Morton order):
+ *  PT_BVH_LBVH  Karras' radix tree over the Morton codes (fastest build, splits at the
+ *               codes' highest differing bit whatever the triangles' sizes);
+ *  PT_BVH_PLOC  parallel locally-ordered clustering (Meister & Bittner 2018): rounds in which
+ *               each cluster merges with its mutual nearest neighbour by surface area within
+ *               16 positions in the Morton order (a tree close to a full SAH build; the
+ *               default). */
+enum { PT_BVH_DEFAULT = 0, PT_BVH_LBVH = 1, PT_BVH_PLOC = 2 };
+
 typedef struct {
     uint32_t leaf_size;         /* max triangles per leaf, 1..4 (0 = 4) */
+    uint32_t builder;           /* PT_BVH_* (0 = PT_BVH_PLOC) */
 } pt_bvh_opts;
 
 typedef struct {
@@ -378,8 +389,8 @@ pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const pt_batch_op
  * sort off/on x tail limit (off, automatic, a quarter, four times) x wave size (2^20 .. 2^23
  * paths, as far as the call needs them), graph replay on; megakernel with 32, 64, 128 pixels
  * per work item; then the winner's traversal passes one ray per lane or per 8-lane group.  With
- * PT_TUNE_BVH it first rebuilds the BVH with leaf sizes 1..4 (the node width is fixed at 8
- * by the node format) and keeps the fastest.  The winner goes to *best (and ms per frame to
+ * PT_TUNE_BVH it first rebuilds the BVH with both builders and leaf sizes 1..4 (the node
+ * width is fixed at 8 by the node format) and keeps the fastest.  The winner goes to *best (and ms per frame to
  * *best_ms) and is stored in the scene: pt_render with PT_MODE_AUTO then uses it for frames
  * of that size (not with nrc; with kernel_ms the launches are direct, not replayed).  No candidate changes the image: they render the
  * same samples; the tuning renders do count in pt_get_stats.  Synchronises the stream.

@@ -70,7 +70,7 @@ class Accum:
 class Scene:
     """A scene uploaded through pt_scene_create and (by default) built with pt_bvh_build."""
 
-    def __init__(self, sc, stream=None, build=True, leaf_size=4, on_device=False):
+    def __init__(self, sc, stream=None, build=True, leaf_size=4, on_device=False, builder=0):
         lib = N.load()
         self.desc = sc
         self._stream = stream
@@ -111,10 +111,11 @@ class Scene:
         self.h = h
         self.n_tris = idx.shape[0] + 2 * nq
         if build:
-            self.build(leaf_size)
+            self.build(leaf_size, builder=builder)
 
-    def build(self, leaf_size=4, stream=None):
-        o = N.pt_bvh_opts(leaf_size)
+    def build(self, leaf_size=4, stream=None, builder=0):
+        """pt_bvh_build; builder N.PT_BVH_LBVH or N.PT_BVH_PLOC (0: the default, PLOC)."""
+        o = N.pt_bvh_opts(leaf_size, builder)
         N.call("pt_bvh_build", self.h, C.byref(o), _stream_handle(stream))
 
     def __del__(self):

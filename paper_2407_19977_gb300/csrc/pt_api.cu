@@ -320,10 +320,15 @@ extern "C" pt_status pt_bvh_build(pt_scene* s, const pt_bvh_opts* opts, void* cu
     PT_CHECK_ARG(s != nullptr, "scene is NULL");
     uint32_t leaf = opts && opts->leaf_size ? opts->leaf_size : 4;
     PT_CHECK_ARG(leaf >= 1 && leaf <= 4, "leaf_size must be 1..4");
+    uint32_t builder = opts && opts->builder ? opts->builder : (uint32_t)PT_BVH_PLOC;
+    PT_CHECK_ARG(builder == PT_BVH_LBVH || builder == PT_BVH_PLOC, "builder must be PT_BVH_LBVH or PT_BVH_PLOC");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     s->last_stream = st;
-    pt_status r = pt_build_bvh_impl(s, leaf, st);
-    if (r == PT_OK) s->leaf_size = leaf;
+    pt_status r = pt_build_bvh_impl(s, leaf, builder, st);
+    if (r == PT_OK) {
+        s->leaf_size = leaf;
+        s->builder = builder;
+    }
     if (r != PT_OK) return r;
     r = pt_build_env_impl(s, st);
     if (r != PT_OK) return r;

@@ -238,6 +238,196 @@ __global__ void k_bottom_up(BinTree T, int n, const uint32_t* par_int, const uin
     }
 }
 
+// ------------------------------------------------------------------ PLOC binary tree
+// Parallel locally-ordered clustering (Meister & Bittner, IEEE TVCG 2018): the clusters start
+// as the triangles in Morton order; each round every cluster finds, within PLOC_R positions on
+// either side, the cluster whose union with it has the least surface area, mutual pairs merge
+// into a new binary node (at the lower position), and the survivors are compacted in order.
+// Pairs are ranked by (area, lower index, higher index), a total order, so the globally least
+// pair within the window is always mutual and every round merges at least once.  Merges get
+// node indices counting down from n - 2, so the last merge (the root) is node 0, and every
+// node's children have higher indices than the node.  A top-down pass over the rounds in
+// reverse then lays the triangles out in tree order, giving each subtree the contiguous
+// [first, last] range the collapse needs.
+constexpr int PLOC_R = 16;
+constexpr int PLOC_THREADS = 256;
+constexpr int PLOC_SCAN_ITEMS = 4;                      // per thread of the block scan
+constexpr int PLOC_SCAN_TILE = PLOC_THREADS * PLOC_SCAN_ITEMS;
+
+struct Clusters {
+    uint32_t* ref;      // LEAF_BIT | triangle id, or binary node index
+    uint32_t* cnt;      // triangles below
+    float4 *lo, *hi;    // bounds
+};
+
+__device__ __forceinline__ float half_area3(float3 lo, float3 hi) {
+    const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_ploc_init(const float4* tris, const uint32_t* perm, uint32_t n, Clusters c) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t t = perm[i];
+    const Box b = tri_box(tris, t);
+    c.ref[i] = LEAF_BIT | t;
+    c.cnt[i] = 1u;
+    c.lo[i] = make_float4(b.lo.x, b.lo.y, b.lo.z, 0.0f);
+    c.hi[i] = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.0f);
+}
+
+// nearest neighbour of each of the m clusters within the window (lowest index on equal area)
+__global__ void __launch_bounds__(PLOC_THREADS) k_ploc_nn(Clusters c, uint32_t m, uint32_t* nn) {
+    __shared__ float4 slo[PLOC_THREADS + 2 * PLOC_R], shi[PLOC_THREADS + 2 * PLOC_R];
+    const int base = (int)(blockIdx.x * PLOC_THREADS) - PLOC_R;
+    for (int k = threadIdx.x; k < PLOC_THREADS + 2 * PLOC_R; k += PLOC_THREADS) {
+        const int g = base + k;
+        if (g >= 0 && g < (int)m) { slo[k] = c.lo[g]; shi[k] = c.hi[g]; }
+    }
+    __syncthreads();
+    const int i = (int)(blockIdx.x * PLOC_THREADS + threadIdx.x);
+    if (i >= (int)m) return;
+    const int li = threadIdx.x + PLOC_R;
+    const float3 alo = xyz(slo[li]), ahi = xyz(shi[li]);
+    float best = __int_as_float(0x7f800000);
+    int bj = -1;
+    const int j0 = max(i - PLOC_R, 0), j1 = min(i + PLOC_R, (int)m - 1);
+    for (int j = j0; j <= j1; ++j) {
+        if (j == i) continue;
+        const int lj = j - base;
+        const float3 blo = xyz(slo[lj]), bhi = xyz(shi[lj]);
+        const float a = half_area3(mk3(fminf(alo.x, blo.x), fminf(alo.y, blo.y), fminf(alo.z, blo.z)),
+                                   mk3(fmaxf(ahi.x, bhi.x), fmaxf(ahi.y, bhi.y), fmaxf(ahi.z, bhi.z)));
+        if (a < best) { best = a; bj = j; }
+    }
+    nn[i] = (uint32_t)bj;
+}
+
+// per cluster: survives (1) and creates a node (bit 32) -- the lower index of a mutual pair --
+// or is absorbed (0); exclusive block-level scan of those 64-bit values, block totals aside
+__device__ __forceinline__ uint64_t ploc_flag(const uint32_t* nn, uint32_t m, uint32_t i) {
+    if (i >= m) return 0ull;
+    const uint32_t j = nn[i];
+    if (j >= m) return 1ull;                       // m == 1: no neighbour
+    if (nn[j] != i) return 1ull;
+    return i < j ? ((1ull << 32) | 1ull) : 0ull;
+}
+
+__global__ void __launch_bounds__(PLOC_THREADS) k_ploc_scan(const uint32_t* nn, uint32_t m, uint64_t* pre,
+                                                            uint64_t* block_sum) {
+    __shared__ uint64_t warp_sum[PLOC_THREADS / 32];
+    const uint32_t t0 = blockIdx.x * PLOC_SCAN_TILE + threadIdx.x * PLOC_SCAN_ITEMS;
+    uint64_t v[PLOC_SCAN_ITEMS], run = 0;
+#pragma unroll
+    for (int k = 0; k < PLOC_SCAN_ITEMS; ++k) {
+        v[k] = ploc_flag(nn, m, t0 + k);
+        run += v[k];
+    }
+    // inclusive scan of the per-thread totals across the warp, then across warps
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t x = run;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    uint64_t before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_sum[w];
+    uint64_t acc = before + x - run;               // exclusive prefix of this thread
+#pragma unroll
+    for (int k = 0; k < PLOC_SCAN_ITEMS; ++k) {
+        if (t0 + k < m) pre[t0 + k] = acc;
+        acc += v[k];
+    }
+    if (threadIdx.x == PLOC_THREADS - 1) block_sum[blockIdx.x] = before + x;
+}
+
+// exclusive scan of nb block totals by one block; the grand total goes to data[nb]
+__global__ void k_ploc_scan_top(uint64_t* data, uint32_t nb) {
+    __shared__ uint64_t part[1024];
+    const uint32_t per = (nb + 1023) / 1024;
+    const uint32_t b = threadIdx.x * per, e = min(b + per, nb);
+    uint64_t sum = 0;
+    for (uint32_t i = b; i < e; ++i) sum += data[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const uint64_t v = threadIdx.x >= (uint32_t)off ? part[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint64_t run = part[threadIdx.x] - sum;
+    for (uint32_t i = b; i < e; ++i) {
+        const uint64_t v = data[i];
+        data[i] = run;
+        run += v;
+    }
+    if (threadIdx.x == 1023) data[nb] = part[1023];
+}
+
+// survivors to their compacted position; a mutual pair becomes binary node
+// n - 2 - (merged_before + its rank among this round's merges)
+__global__ void k_ploc_compact(Clusters a, Clusters b, const uint32_t* nn, uint32_t m, const uint64_t* pre,
+                               const uint64_t* block_pre, uint32_t n, uint32_t merged_before, uint32_t* left,
+                               uint32_t* right, uint32_t* count, float4* blo, float4* bhi) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint64_t f = ploc_flag(nn, m, i);
+    if (f == 0ull) return;
+    const uint64_t p = pre[i] + block_pre[i / PLOC_SCAN_TILE];
+    const uint32_t pos = (uint32_t)(p & 0xffffffffull);
+    if (f == 1ull) {
+        b.ref[pos] = a.ref[i];
+        b.cnt[pos] = a.cnt[i];
+        b.lo[pos] = a.lo[i];
+        b.hi[pos] = a.hi[i];
+        return;
+    }
+    const uint32_t j = nn[i];
+    const uint32_t node = n - 2u - (merged_before + (uint32_t)(p >> 32));
+    const float4 l0 = a.lo[i], h0 = a.hi[i], l1 = a.lo[j], h1 = a.hi[j];
+    const float4 lo = make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.0f);
+    const float4 hi = make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.0f);
+    const uint32_t c = a.cnt[i] + a.cnt[j];
+    left[node] = a.ref[i];
+    right[node] = a.ref[j];
+    count[node] = c;
+    blo[node] = lo;
+    bhi[node] = hi;
+    b.ref[pos] = node;
+    b.cnt[pos] = c;
+    b.lo[pos] = lo;
+    b.hi[pos] = hi;
+}
+
+// top-down layout of the nodes [lo, hi] (one round's merges; their parents are done): each
+// node's range starts at first[node], its left subtree first; leaves take their position in
+// perm and their child reference becomes LEAF_BIT | position
+__global__ void k_ploc_layout(uint32_t lo, uint32_t hi, uint32_t* left, uint32_t* right, const uint32_t* count,
+                              uint32_t* first, uint32_t* last, uint32_t* perm) {
+    const uint32_t k = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > hi) return;
+    const uint32_t f = first[k];
+    const uint32_t L = left[k], R = right[k];
+    const uint32_t cl = (L & LEAF_BIT) ? 1u : count[L];
+    if (L & LEAF_BIT) {
+        perm[f] = L & ~LEAF_BIT;
+        left[k] = LEAF_BIT | f;
+    } else {
+        first[L] = f;
+    }
+    if (R & LEAF_BIT) {
+        perm[f + cl] = R & ~LEAF_BIT;
+        right[k] = LEAF_BIT | (f + cl);
+    } else {
+        first[R] = f + cl;
+    }
+    last[k] = f + count[k] - 1u;
+}
+
 // ------------------------------------------------------------------ collapse to 8-wide nodes
 struct CollapseCtx {
     BinTree T;
@@ -380,7 +570,7 @@ static cudaError_t dalloc(T** p, size_t n) {
     return cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
 }
 
-pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, cudaStream_t st) {
+pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, cudaStream_t st) {
     const uint32_t n = s->n_tris;
     if (s->d_nodes) { cudaFree(s->d_nodes); s->d_nodes = nullptr; }
     if (s->d_tris) { cudaFree(s->d_tris); s->d_tris = nullptr; }
@@ -388,11 +578,12 @@ pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, cudaStream_t st) {
     uint32_t *v0 = nullptr, *v1 = nullptr, *hist = nullptr, *cb = nullptr;
     uint32_t *left = nullptr, *right = nullptr, *pint = nullptr, *pleaf = nullptr, *first = nullptr, *last = nullptr;
     uint32_t *flags = nullptr, *tref = nullptr, *tnode = nullptr, *counters = nullptr;
-    float4 *blo = nullptr, *bhi = nullptr;
+    float4 *blo = nullptr, *bhi = nullptr, *clo = nullptr, *chi = nullptr;
     const uint32_t nblocks = (n + RS_TILE - 1) / RS_TILE;
     pt_status status = PT_OK;
     auto cleanup = [&]() {
-        void* ps[] = {k0, k1, v0, v1, hist, cb, left, right, pint, pleaf, first, last, flags, tref, tnode, counters, blo, bhi};
+        void* ps[] = {k0,    k1,    v0,    v1,    hist,  cb,       left, right, pint, pleaf,
+                      first, last,  flags, tref,  tnode, counters, blo,  bhi,   clo,  chi};
         for (void* q : ps)
             if (q) cudaFree(q);
     };
@@ -411,6 +602,7 @@ pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, cudaStream_t st) {
     BTRY(dalloc(&first, n)); BTRY(dalloc(&last, n)); BTRY(dalloc(&flags, n));
     BTRY(dalloc(&tref, n + 1)); BTRY(dalloc(&tnode, n + 1)); BTRY(dalloc(&counters, 4));
     BTRY(dalloc(&blo, n)); BTRY(dalloc(&bhi, n));
+    if (builder == PT_BVH_PLOC) { BTRY(dalloc(&clo, (size_t)2 * n)); BTRY(dalloc(&chi, (size_t)2 * n)); }
     BTRY(dalloc(&s->d_nodes, (size_t)5 * (n + 1)));
     BTRY(dalloc(&s->d_tris, (size_t)3 * n));
 
@@ -432,11 +624,51 @@ pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, cudaStream_t st) {
     BinTree T;
     T.left = left; T.right = right; T.first = first; T.last = last; T.perm = v0;
     T.blo = blo; T.bhi = bhi; T.tris = s->d_tris_raw;
-    if (n > 1) {
+    if (n > 1 && builder == PT_BVH_LBVH) {
         PT_LAUNCH(k_karras, (n - 1 + 255) / 256, 256, 0, st, k0, (int)n, left, right, pint, pleaf, first, last);
         BTRY(cudaMemsetAsync(flags, 0, (size_t)n * sizeof(uint32_t), st));
         PT_LAUNCH(k_bottom_up, g, 256, 0, st, T, (int)n, pint, pleaf, flags);
         s->launches += 2;
+    } else if (n > 1) {
+        // PLOC over the Morton order: cluster arrays ping-pong between (tref, flags, clo, chi)
+        // and (tnode, last, clo + n, chi + n); scan prefixes in k1, block totals in hist,
+        // nearest neighbours in pint, node triangle counts in pleaf, the final order in v1
+        Clusters ca{tref, flags, clo, chi}, cb2{tnode, last, clo + n, chi + n};
+        uint64_t* pre = k1;
+        uint64_t* bsum = reinterpret_cast<uint64_t*>(hist);
+        PT_LAUNCH(k_ploc_init, g, 256, 0, st, s->d_tris_raw, v0, n, ca);
+        s->launches++;
+        std::vector<std::pair<uint32_t, uint32_t>> rounds;
+        uint32_t m = n, merged = 0;
+        while (m > 1) {
+            const uint32_t nb = (m + PLOC_SCAN_TILE - 1) / PLOC_SCAN_TILE;
+            PT_LAUNCH(k_ploc_nn, (m + PLOC_THREADS - 1) / PLOC_THREADS, PLOC_THREADS, 0, st, ca, m, pint);
+            PT_LAUNCH(k_ploc_scan, nb, PLOC_THREADS, 0, st, pint, m, pre, bsum);
+            PT_LAUNCH(k_ploc_scan_top, 1, 1024, 0, st, bsum, nb);
+            PT_LAUNCH(k_ploc_compact, (m + 255) / 256, 256, 0, st, ca, cb2, pint, m, pre, bsum, n, merged, left,
+                      right, pleaf, blo, bhi);
+            s->launches += 4;
+            uint64_t total = 0;
+            BTRY(cudaMemcpyAsync(&total, bsum + nb, sizeof(total), cudaMemcpyDeviceToHost, st));
+            BTRY(cudaStreamSynchronize(st));
+            const uint32_t merges = (uint32_t)(total >> 32), m_new = (uint32_t)(total & 0xffffffffull);
+            if (merges == 0 || m_new != m - merges || merged + merges > n - 1) {
+                pt_set_error("PLOC clustering made no progress");
+                cleanup();
+                return PT_ERR_CUDA;
+            }
+            rounds.emplace_back(n - 1 - merged - merges, n - 2 - merged);
+            merged += merges;
+            m = m_new;
+            std::swap(ca, cb2);
+        }
+        BTRY(cudaMemsetAsync(first, 0, sizeof(uint32_t), st));
+        for (size_t r = rounds.size(); r-- > 0;) {
+            const uint32_t lo = rounds[r].first, hi = rounds[r].second;
+            PT_LAUNCH(k_ploc_layout, (hi - lo + 1 + 255) / 256, 256, 0, st, lo, hi, left, right, pleaf, first, last, v1);
+            s->launches++;
+        }
+        T.perm = v1;
     }
     // collapse, one level per launch
     const uint32_t root_ref = n > 1 ? 0u : LEAF_BIT;

@@ -122,6 +122,7 @@ struct pt_scene {
     cudaStream_t cap_stream = nullptr;
     uint64_t graph_replays = 0;
     uint32_t leaf_size = 4;          // of the current BVH
+    uint32_t builder = PT_BVH_PLOC;  // of the current BVH
     // schedule chosen by pt_autotune for frames of tuned_w x tuned_h (used by PT_MODE_AUTO)
     bool tuned = false;
     uint32_t tuned_w = 0, tuned_h = 0;
@@ -152,7 +153,7 @@ struct pt_scene {
 };
 
 // implemented in pt_bvh.cu
-pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, cudaStream_t st);
+pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, cudaStream_t st);
 pt_status pt_build_env_impl(pt_scene* s, cudaStream_t st);
 
 // implemented in pt_render.cu

@@ -80,22 +80,22 @@ extern "C" pt_status pt_autotune(pt_scene* s, const pt_camera* camera, uint32_t 
     base.mode = PT_MODE_WAVEFRONT;
     base.sort_by_material = -1;
     base.use_graph = 1;
-    // BVH leaf size first (one default schedule), then the schedule on the chosen tree
+    // BVH builder and leaf size first (one default schedule), then the schedule on the chosen tree
     if (tune_flags & PT_TUNE_BVH) {
-        uint32_t best_leaf = s->leaf_size;
+        pt_bvh_opts best_bo{s->leaf_size, s->builder};
         float best_t = 3.4e38f;
-        for (uint32_t leaf = 1; leaf <= 4; ++leaf) {
-            pt_bvh_opts bo{leaf};
-            pt_status r = pt_bvh_build(s, &bo, cuda_stream);
-            if (r != PT_OK) return r;
-            float t = 0.0f;
-            r = run(base, &t);
-            if (r != PT_OK) return r;
-            if (t < best_t) { best_t = t; best_leaf = leaf; }
-        }
-        if (s->leaf_size != best_leaf) {
-            pt_bvh_opts bo{best_leaf};
-            pt_status r = pt_bvh_build(s, &bo, cuda_stream);
+        for (uint32_t builder : {(uint32_t)PT_BVH_PLOC, (uint32_t)PT_BVH_LBVH})
+            for (uint32_t leaf = 1; leaf <= 4; ++leaf) {
+                pt_bvh_opts bo{leaf, builder};
+                pt_status r = pt_bvh_build(s, &bo, cuda_stream);
+                if (r != PT_OK) return r;
+                float t = 0.0f;
+                r = run(base, &t);
+                if (r != PT_OK) return r;
+                if (t < best_t) { best_t = t; best_bo = bo; }
+            }
+        if (s->leaf_size != best_bo.leaf_size || s->builder != best_bo.builder) {
+            pt_status r = pt_bvh_build(s, &best_bo, cuda_stream);
             if (r != PT_OK) return r;
         }
     }

@@ -327,27 +327,41 @@ def test_closest_hit_parity(api, which, coop):
 
 @pytest.mark.parametrize("which", ["cornell", "pushbutton", "heavy"])
 def test_bvh_structure_and_surface_area_cost(api, which):
-    """The exported 8-wide tree is sound (one parent per node, each triangle in one leaf,
-    every decoded box holding what lies below it) and its surface-area cost is compared with
-    a binned-SAH binary tree built by the oracle on the same triangles.  The comparable
-    measure is the expected number of triangle tests (leaf areas times counts, leaves of at
-    most four in both): a Morton-order build is known to give up some of it to a SAH sweep;
-    the test bounds the loss at 1.5x and prints both trees' figures."""
+    """The exported 8-wide tree from both builders is sound (one parent per node, each
+    triangle in one leaf, every decoded box holding what lies below it) and its surface-area
+    cost is compared with a binned-SAH binary tree built by the oracle on the same triangles.
+    The comparable measure is the expected number of triangle tests of a ray through the root
+    box (leaf areas times counts, leaves of at most four in both).  A Morton-order radix tree
+    gives up part of it to a SAH sweep; the clustering builder (the default) must give up
+    less, at most 35 % on the two large scenes (the radix tree: at most 60 %).  The 36 large
+    triangles of the Cornell box are only checked for soundness.  Both trees' figures are
+    printed."""
     from paper_2407_19977_gb300 import bvh_check
+    from paper_2407_19977_gb300 import native as N
     sc, gsc, osc = {"cornell": cornell, "pushbutton": pushbutton, "heavy": heavy}[which]()
-    nodes, tris = gsc.export_bvh()
     tv = _tri_vertices(sc)
-    assert tris.shape[0] == tv.shape[0]
-    problems, stats = bvh_check.check(nodes, tris)
-    assert problems == [], problems
-    dev = bvh_check.sah_cost(nodes, tris)
     ref = oracle.sah_reference(tv)
-    print(f"\nbvh {which}: {stats}\n  device {dev}\n  binned-SAH binary {ref}; "
-          f"triangle tests device/reference {dev['tri_tests_exact'] / ref['tri_tests']:.3f}, "
-          f"wide node visits {dev['node_visits']:.2f} vs binary node visits {ref['box_tests'] / 2:.2f}")
-    assert dev["tri_tests_exact"] <= 1.5 * ref["tri_tests"]
-    # the 8-bit boxes the traversal tests are conservative: never below the exact measure
-    assert dev["tri_tests"] >= dev["tri_tests_exact"] * (1 - 1e-6)
+    cost = {}
+    try:
+        for builder, name in ((N.PT_BVH_LBVH, "radix tree"), (N.PT_BVH_PLOC, "clustering")):
+            gsc.build(builder=builder)
+            nodes, tris = gsc.export_bvh()
+            assert tris.shape[0] == tv.shape[0]
+            problems, stats = bvh_check.check(nodes, tris)
+            assert problems == [], (name, problems)
+            dev = bvh_check.sah_cost(nodes, tris)
+            # the 8-bit boxes the traversal tests are conservative: never below the exact measure
+            assert dev["tri_tests"] >= dev["tri_tests_exact"] * (1 - 1e-6)
+            cost[name] = dev["tri_tests_exact"] / ref["tri_tests"]
+            print(f"\nbvh {which} {name}: {stats}\n  {dev}\n  triangle tests / binned-SAH reference "
+                  f"{cost[name]:.3f}; wide node visits {dev['node_visits']:.2f} (binary reference "
+                  f"{ref['box_tests'] / 2:.2f})")
+    finally:
+        gsc.build()
+    print(f"binned-SAH reference {ref}")
+    if which != "cornell":
+        assert cost["clustering"] <= 1.35 and cost["radix tree"] <= 1.6, cost
+        assert cost["clustering"] < cost["radix tree"], cost
 
 
 @pytest.mark.parametrize("which", ["cornell", "pushbutton", "heavy"])
@@ -915,21 +929,23 @@ def test_autotune_batch_leaves_jobs_untouched(api):
 
 
 def test_bvh_leaf_size_does_not_change_samples(api):
-    """Closest hits (equal t -> lower id) and any-hits do not depend on the tree: every leaf
-    size gives bit-identical samples."""
+    """Closest hits (equal t -> lower id) and any-hits do not depend on the tree: both
+    builders and every leaf size give bit-identical samples."""
     from paper_2407_19977_gb300 import api as A
     from paper_2407_19977_gb300 import native as N
     sc = scenes.pushbutton_lod(20000, width=96, height=64, seed=2)
     g = A.Scene(sc, build=False)
     ref = None
-    for leaf in (4, 1, 2, 3):
-        g.build(leaf_size=leaf)
-        smp = torch.zeros((64, 96, 2, 3), dtype=torch.float32, device="cuda")
-        g.render(2, accum=A.Accum(96, 64), mode=N.PT_MODE_WAVEFRONT, sample_out=smp, seed=3)
-        torch.cuda.synchronize()
-        if ref is None:
-            ref = smp.clone()
-        assert torch.equal(smp, ref), leaf
+    for builder in (N.PT_BVH_PLOC, N.PT_BVH_LBVH):
+        for leaf in (4, 1, 2, 3):
+            g.build(leaf_size=leaf, builder=builder)
+            smp = torch.zeros((64, 96, 2, 3), dtype=torch.float32, device="cuda")
+            g.render(2, accum=A.Accum(96, 64), mode=N.PT_MODE_WAVEFRONT, sample_out=smp, seed=3)
+            torch.cuda.synchronize()
+            if ref is None:
+                ref = smp.clone()
+            assert torch.equal(smp, ref), (builder, leaf)
+    assert g.stats()["error_flags"] == 0
 
 
 def test_autotune_and_auto_mode(api):

@@ -308,11 +308,13 @@ def cpu_baseline(sc, target_s: float, seed: int = 0):
     t0 = time.perf_counter()
     osc = oracle.OracleScene(sc)
     setup = time.perf_counter() - t0
-    # calibration on every 64th row, then scale the sample to the target time
+    # calibration on every 64th row (warms the threads and caches), then on every 16th, and
+    # the sample scaled from the second to the target time
+    osc.render(spp=1, seed=seed, row_step=64, threads=threads)
     t0 = time.perf_counter()
-    _, _, st = osc.render(spp=1, seed=seed, row_step=64, threads=threads)
+    _, _, st = osc.render(spp=1, seed=seed, row_step=16, threads=threads)
     cal = max(time.perf_counter() - t0, 1e-3)
-    rows_cal = len(range(0, sc.camera.height, 64))
+    rows_cal = len(range(0, sc.camera.height, 16))
     rows = max(1, min(sc.camera.height, int(rows_cal * target_s / cal)))
     row_step = max(1, sc.camera.height // rows)
     spp = 1

@@ -79,6 +79,12 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bvh-builder", default="ploc", choices=["ploc", "lbvh"],
                     help="binary tree the 8-wide BVH is collapsed from: clustering (default) or radix tree")
+    ap.add_argument("--bvh-collapse", default="optimal", choices=["optimal", "greedy"],
+                    help="folding of the binary tree into 8-wide nodes: least surface-area cost or largest child first")
+    ap.add_argument("--bvh-tri-cost", type=float, default=0.0,
+                    help="cost of a triangle test against a wide node visit for the optimal collapse (0: default)")
+    ap.add_argument("--bvh-box-cost", type=float, default=0.0,
+                    help="cost of each child slot of a visited wide node for the optimal collapse (0: default)")
     ap.add_argument("--spp-per-step", type=int, default=4,
                     help="samples per pixel of the frame one step renders (progressive: each step adds them)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
@@ -397,11 +403,13 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     upload_ms = (time.perf_counter() - t0) * 1e3
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    builder = {"ploc": N.PT_BVH_PLOC, "lbvh": N.PT_BVH_LBVH}[args.bvh_builder]
-    scene.build(builder=builder)           # first build: allocations and module load
+    bvh = {"builder": {"ploc": N.PT_BVH_PLOC, "lbvh": N.PT_BVH_LBVH}[args.bvh_builder],
+           "collapse": {"optimal": N.PT_COLLAPSE_OPTIMAL, "greedy": N.PT_COLLAPSE_GREEDY}[args.bvh_collapse],
+           "tri_cost": args.bvh_tri_cost, "box_cost": args.bvh_box_cost}
+    scene.build(**bvh)                      # first build: allocations and module load
     torch.cuda.synchronize()
     ev0.record(stream)
-    scene.build(builder=builder)
+    scene.build(**bvh)
     ev1.record(stream)
     torch.cuda.synchronize()
     bvh_ms = ev0.elapsed_time(ev1)
@@ -525,6 +533,8 @@ def run_ours(args, world, rank, local):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload].replace("1 spp/step", f"{args.spp_per_step} spp/step"),
                    "spp_per_step": args.spp_per_step, "bvh_builder": args.bvh_builder,
+                   "bvh_collapse": args.bvh_collapse + (f" (tri_cost {args.bvh_tri_cost}, box_cost {args.bvh_box_cost})"
+                                                        if args.bvh_tri_cost or args.bvh_box_cost else ""),
                    "mode": "auto (autotuned)" if tuned else args.mode,
                    "l2": "flushed between steps",
                    "parallelism": f"replicas x{world}", "cuda_graph": bool(args.graph),

@@ -242,9 +242,23 @@ enum {
  *               default). */
 enum { PT_BVH_DEFAULT = 0, PT_BVH_LBVH = 1, PT_BVH_PLOC = 2 };
 
+/* How the binary tree is folded into 8-wide nodes:
+ *  PT_COLLAPSE_OPTIMAL  the least surface-area cost (a wide node visit costs 1 plus box_cost
+ *                       per child slot, a triangle test tri_cost, each weighted by area / root
+ *                       area), found per binary node by a dynamic programme over the number of
+ *                       slots its subtree fills (Ylitie, Karras, Laine, HPG 2017); the default;
+ *  PT_COLLAPSE_GREEDY   open the child of largest area until 8 slots are used. */
+enum { PT_COLLAPSE_DEFAULT = 0, PT_COLLAPSE_OPTIMAL = 1, PT_COLLAPSE_GREEDY = 2 };
+
 typedef struct {
     uint32_t leaf_size;         /* max triangles per leaf, 1..4 (0 = 4) */
     uint32_t builder;           /* PT_BVH_* (0 = PT_BVH_PLOC) */
+    uint32_t collapse;          /* PT_COLLAPSE_* (0 = PT_COLLAPSE_OPTIMAL) */
+    float tri_cost;             /* cost of a triangle test against a wide node visit, > 0 and
+                                   finite (0 = 0.8: measured best of 0.15 .. 1.5 on the CAD
+                                   frames); used by PT_COLLAPSE_OPTIMAL */
+    float box_cost;             /* cost of each child slot of a visited wide node, >= 0 and
+                                   finite (0 = 0, negative = exactly 0); PT_COLLAPSE_OPTIMAL */
 } pt_bvh_opts;
 
 typedef struct {

@@ -113,9 +113,11 @@ class Scene:
         if build:
             self.build(leaf_size, builder=builder)
 
-    def build(self, leaf_size=4, stream=None, builder=0):
-        """pt_bvh_build; builder N.PT_BVH_LBVH or N.PT_BVH_PLOC (0: the default, PLOC)."""
-        o = N.pt_bvh_opts(leaf_size, builder)
+    def build(self, leaf_size=4, stream=None, builder=0, collapse=0, tri_cost=0.0, box_cost=0.0):
+        """pt_bvh_build; builder N.PT_BVH_LBVH or N.PT_BVH_PLOC (0: the default, PLOC); collapse
+        N.PT_COLLAPSE_OPTIMAL or N.PT_COLLAPSE_GREEDY (0: optimal) with tri_cost and box_cost
+        (0: defaults)."""
+        o = N.pt_bvh_opts(leaf_size, builder, collapse, float(tri_cost), float(box_cost))
         N.call("pt_bvh_build", self.h, C.byref(o), _stream_handle(stream))
 
     def __del__(self):

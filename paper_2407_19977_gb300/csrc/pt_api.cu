@@ -322,12 +322,23 @@ extern "C" pt_status pt_bvh_build(pt_scene* s, const pt_bvh_opts* opts, void* cu
     PT_CHECK_ARG(leaf >= 1 && leaf <= 4, "leaf_size must be 1..4");
     uint32_t builder = opts && opts->builder ? opts->builder : (uint32_t)PT_BVH_PLOC;
     PT_CHECK_ARG(builder == PT_BVH_LBVH || builder == PT_BVH_PLOC, "builder must be PT_BVH_LBVH or PT_BVH_PLOC");
+    uint32_t collapse = opts && opts->collapse ? opts->collapse : (uint32_t)PT_COLLAPSE_OPTIMAL;
+    PT_CHECK_ARG(collapse == PT_COLLAPSE_OPTIMAL || collapse == PT_COLLAPSE_GREEDY,
+                 "collapse must be PT_COLLAPSE_OPTIMAL or PT_COLLAPSE_GREEDY");
+    const float tri_cost = opts && opts->tri_cost != 0.0f ? opts->tri_cost : 0.8f;
+    PT_CHECK_ARG(tri_cost > 0.0f && tri_cost < 1e6f, "tri_cost must be positive and finite");
+    float box_cost = opts && opts->box_cost != 0.0f ? opts->box_cost : 0.0f;
+    PT_CHECK_ARG(box_cost < 1e6f && box_cost == box_cost, "box_cost must be finite");
+    if (box_cost < 0.0f) box_cost = 0.0f;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     s->last_stream = st;
-    pt_status r = pt_build_bvh_impl(s, leaf, builder, st);
+    pt_status r = pt_build_bvh_impl(s, leaf, builder, collapse, tri_cost, box_cost, st);
     if (r == PT_OK) {
         s->leaf_size = leaf;
         s->builder = builder;
+        s->collapse = collapse;
+        s->tri_cost = tri_cost;
+        s->box_cost = opts ? opts->box_cost : 0.0f;
     }
     if (r != PT_OK) return r;
     r = pt_build_env_impl(s, st);

@@ -208,6 +208,76 @@ __device__ __forceinline__ Box box_union(Box a, Box b) {
     return r;
 }
 
+// ---- cost-optimal collapse: per binary node, the least surface-area cost of its subtree
+// when it fills exactly j = 1..8 slots of a wide node (the dynamic programme of Ylitie,
+// Karras and Laine, HPG 2017, restated for leaves of at most leaf_size triangles).  With A the
+// (half) surface area, a wide node visit costing 1 plus box_cost per slot and a triangle test
+// tri_cost:
+//   C(k)    = A(k) * tri_cost * count(k)                          if count(k) <= leaf_size
+//           = A(k) + min_{j=2..8} E(k, j) + A(k) * box_cost * j    otherwise (a wide node)
+//   E(k, 1) = C(k);  E(k, j) = min_{i=1..j-1} E(L, i) + E(R, j - i)  (j >= 2)
+// and a single triangle costs A * tri_cost as one slot and cannot fill more.  dec[k] keeps
+// the choices in nibbles: nibble 0 the slot count j of C(k) for a wide node, nibble j - 1
+// (j = 2..8) the split i of E(k, j).
+struct DpArrays {
+    float* cost;            // 8 per binary node: E(k, 1..8); null: greedy collapse
+    uint32_t* dec;          // choices, one word per binary node
+    uint32_t leaf_size;
+    float tri_cost, box_cost;
+};
+
+__device__ __forceinline__ float half_area_box(float3 lo, float3 hi) {
+    const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+// E(child, 1..8) of a child reference: a triangle (its area given) or a binary node
+__device__ __forceinline__ void dp_child(const DpArrays& D, uint32_t ref, float leaf_area, float (&c)[8]) {
+    if (ref & 0x80000000u) {
+        c[0] = leaf_area * D.tri_cost;
+#pragma unroll
+        for (int j = 1; j < 8; ++j) c[j] = __int_as_float(0x7f800000);
+    } else {
+        const float4 a = __ldcg(reinterpret_cast<const float4*>(D.cost + 8u * ref));
+        const float4 b = __ldcg(reinterpret_cast<const float4*>(D.cost + 8u * ref) + 1);
+        c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w; c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+    }
+}
+
+__device__ __forceinline__ void dp_node(const DpArrays& D, uint32_t k, uint32_t lref, float larea, uint32_t rref,
+                                        float rarea, uint32_t count, float area) {
+    float cl[8], cr[8], e[8];
+    dp_child(D, lref, larea, cl);
+    dp_child(D, rref, rarea, cr);
+    uint32_t dec = 0;
+#pragma unroll
+    for (uint32_t j = 2; j <= 8; ++j) {
+        float best = __int_as_float(0x7f800000);
+        uint32_t bi = 1;
+        for (uint32_t i = 1; i < j; ++i) {
+            const float v = cl[i - 1] + cr[j - i - 1];
+            if (v < best) { best = v; bi = i; }
+        }
+        e[j - 1] = best;
+        dec |= bi << (4 * (j - 1));
+    }
+    if (count <= D.leaf_size) {
+        e[0] = area * D.tri_cost * (float)count;
+    } else {
+        float best = __int_as_float(0x7f800000);
+        uint32_t bj = 2;
+        for (uint32_t j = 2; j <= 8; ++j) {
+            const float v = e[j - 1] + area * D.box_cost * (float)j;
+            if (v < best) { best = v; bj = j; }
+        }
+        e[0] = area + best;
+        dec |= bj;
+    }
+    __stcg(reinterpret_cast<float4*>(D.cost + 8u * k), make_float4(e[0], e[1], e[2], e[3]));
+    __stcg(reinterpret_cast<float4*>(D.cost + 8u * k) + 1, make_float4(e[4], e[5], e[6], e[7]));
+    __stcg(D.dec + k, dec);
+}
+
 struct BinTree {
     const uint32_t *left, *right, *first, *last, *perm;
     float4 *blo, *bhi;
@@ -223,7 +293,8 @@ __device__ __forceinline__ Box ref_box(const BinTree& T, uint32_t ref) {
     return b;
 }
 
-__global__ void k_bottom_up(BinTree T, int n, const uint32_t* par_int, const uint32_t* par_leaf, uint32_t* flags) {
+__global__ void k_bottom_up(BinTree T, int n, const uint32_t* par_int, const uint32_t* par_leaf, uint32_t* flags,
+                            DpArrays D) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t node = par_leaf[i];
@@ -231,9 +302,14 @@ __global__ void k_bottom_up(BinTree T, int n, const uint32_t* par_int, const uin
         __threadfence();
         if (atomicAdd(&flags[node], 1u) == 0u) return;  // first child to arrive stops
         __threadfence();
-        const Box b = box_union(ref_box(T, T.left[node]), ref_box(T, T.right[node]));
+        const uint32_t l = T.left[node], r = T.right[node];
+        const Box bl = ref_box(T, l), br = ref_box(T, r);
+        const Box b = box_union(bl, br);
         __stcg(T.blo + node, make_float4(b.lo.x, b.lo.y, b.lo.z, 0.0f));
         __stcg(T.bhi + node, make_float4(b.hi.x, b.hi.y, b.hi.z, 0.0f));
+        if (D.cost)
+            dp_node(D, node, l, half_area_box(bl.lo, bl.hi), r, half_area_box(br.lo, br.hi),
+                    T.last[node] - T.first[node] + 1u, half_area_box(b.lo, b.hi));
         node = par_int[node];
     }
 }
@@ -372,7 +448,7 @@ __global__ void k_ploc_scan_top(uint64_t* data, uint32_t nb) {
 // n - 2 - (merged_before + its rank among this round's merges)
 __global__ void k_ploc_compact(Clusters a, Clusters b, const uint32_t* nn, uint32_t m, const uint64_t* pre,
                                const uint64_t* block_pre, uint32_t n, uint32_t merged_before, uint32_t* left,
-                               uint32_t* right, uint32_t* count, float4* blo, float4* bhi) {
+                               uint32_t* right, uint32_t* count, float4* blo, float4* bhi, DpArrays D) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const uint64_t f = ploc_flag(nn, m, i);
@@ -397,6 +473,9 @@ __global__ void k_ploc_compact(Clusters a, Clusters b, const uint32_t* nn, uint3
     count[node] = c;
     blo[node] = lo;
     bhi[node] = hi;
+    if (D.cost)   // the children's costs were written in earlier rounds
+        dp_node(D, node, a.ref[i], half_area_box(xyz(l0), xyz(h0)), a.ref[j], half_area_box(xyz(l1), xyz(h1)), c,
+                half_area_box(xyz(lo), xyz(hi)));
     b.ref[pos] = node;
     b.cnt[pos] = c;
     b.lo[pos] = lo;
@@ -438,6 +517,7 @@ struct CollapseCtx {
     uint4* nodes;
     float4* out_tris;
     const float4* in_tris;
+    DpArrays dp;            // cost-optimal choices (dp.cost null: greedy, largest child first)
 };
 
 __device__ __forceinline__ uint32_t ref_count(const BinTree& T, uint32_t ref) {
@@ -468,6 +548,27 @@ __global__ void k_collapse(CollapseCtx C, uint32_t qbeg, uint32_t qend) {
         ch[0] = root_ref;
         cb[0] = ref_box(T, root_ref);
         nc = 1;
+    } else if (C.dp.cost) {
+        // unfold the choices: the root's split, then each part's split of its slot budget
+        uint32_t sref[8], sj[8];
+        int sp = 0;
+        const uint32_t d0 = C.dp.dec[root_ref];
+        const uint32_t j0 = min(max(d0 & 15u, 2u), 8u);
+        const uint32_t i0 = (d0 >> (4u * (j0 - 1u))) & 15u;
+        sref[sp] = T.right[root_ref]; sj[sp++] = j0 - i0;
+        sref[sp] = T.left[root_ref]; sj[sp++] = i0;
+        while (sp > 0) {
+            const uint32_t r = sref[--sp], j = sj[sp];
+            const uint32_t i = (r & LEAF_BIT) || j < 2u || j > 8u ? 0u : (C.dp.dec[r] >> (4u * (j - 1u))) & 15u;
+            if (i == 0u || i >= j || nc + sp + 2 > 8) {   // one slot (valid choices never need the guards)
+                ch[nc] = r;
+                cb[nc] = ref_box(T, r);
+                ++nc;
+            } else {
+                sref[sp] = T.right[r]; sj[sp++] = j - i;
+                sref[sp] = T.left[r]; sj[sp++] = i;
+            }
+        }
     } else {
         ch[0] = T.left[root_ref];
         ch[1] = T.right[root_ref];
@@ -570,7 +671,8 @@ static cudaError_t dalloc(T** p, size_t n) {
     return cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
 }
 
-pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, cudaStream_t st) {
+pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, uint32_t collapse, float tri_cost,
+                            float box_cost, cudaStream_t st) {
     const uint32_t n = s->n_tris;
     if (s->d_nodes) { cudaFree(s->d_nodes); s->d_nodes = nullptr; }
     if (s->d_tris) { cudaFree(s->d_tris); s->d_tris = nullptr; }
@@ -579,11 +681,13 @@ pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, c
     uint32_t *left = nullptr, *right = nullptr, *pint = nullptr, *pleaf = nullptr, *first = nullptr, *last = nullptr;
     uint32_t *flags = nullptr, *tref = nullptr, *tnode = nullptr, *counters = nullptr;
     float4 *blo = nullptr, *bhi = nullptr, *clo = nullptr, *chi = nullptr;
+    float* dpc = nullptr;
+    uint32_t* dpd = nullptr;
     const uint32_t nblocks = (n + RS_TILE - 1) / RS_TILE;
     pt_status status = PT_OK;
     auto cleanup = [&]() {
-        void* ps[] = {k0,    k1,    v0,    v1,    hist,  cb,       left, right, pint, pleaf,
-                      first, last,  flags, tref,  tnode, counters, blo,  bhi,   clo,  chi};
+        void* ps[] = {k0,    k1,    v0,    v1,    hist,  cb,       left, right, pint, pleaf, first,
+                      last,  flags, tref,  tnode, counters, blo,  bhi,   clo,  chi,  dpc,   dpd};
         for (void* q : ps)
             if (q) cudaFree(q);
     };
@@ -603,6 +707,13 @@ pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, c
     BTRY(dalloc(&tref, n + 1)); BTRY(dalloc(&tnode, n + 1)); BTRY(dalloc(&counters, 4));
     BTRY(dalloc(&blo, n)); BTRY(dalloc(&bhi, n));
     if (builder == PT_BVH_PLOC) { BTRY(dalloc(&clo, (size_t)2 * n)); BTRY(dalloc(&chi, (size_t)2 * n)); }
+    DpArrays D{nullptr, nullptr, leaf_size, tri_cost, box_cost};
+    if (collapse == PT_COLLAPSE_OPTIMAL) {
+        BTRY(dalloc(&dpc, (size_t)8 * n));
+        BTRY(dalloc(&dpd, n));
+        D.cost = dpc;
+        D.dec = dpd;
+    }
     BTRY(dalloc(&s->d_nodes, (size_t)5 * (n + 1)));
     BTRY(dalloc(&s->d_tris, (size_t)3 * n));
 
@@ -627,7 +738,7 @@ pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, c
     if (n > 1 && builder == PT_BVH_LBVH) {
         PT_LAUNCH(k_karras, (n - 1 + 255) / 256, 256, 0, st, k0, (int)n, left, right, pint, pleaf, first, last);
         BTRY(cudaMemsetAsync(flags, 0, (size_t)n * sizeof(uint32_t), st));
-        PT_LAUNCH(k_bottom_up, g, 256, 0, st, T, (int)n, pint, pleaf, flags);
+        PT_LAUNCH(k_bottom_up, g, 256, 0, st, T, (int)n, pint, pleaf, flags, D);
         s->launches += 2;
     } else if (n > 1) {
         // PLOC over the Morton order: cluster arrays ping-pong between (tref, flags, clo, chi)
@@ -646,7 +757,7 @@ pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, c
             PT_LAUNCH(k_ploc_scan, nb, PLOC_THREADS, 0, st, pint, m, pre, bsum);
             PT_LAUNCH(k_ploc_scan_top, 1, 1024, 0, st, bsum, nb);
             PT_LAUNCH(k_ploc_compact, (m + 255) / 256, 256, 0, st, ca, cb2, pint, m, pre, bsum, n, merged, left,
-                      right, pleaf, blo, bhi);
+                      right, pleaf, blo, bhi, D);
             s->launches += 4;
             uint64_t total = 0;
             BTRY(cudaMemcpyAsync(&total, bsum + nb, sizeof(total), cudaMemcpyDeviceToHost, st));
@@ -686,6 +797,7 @@ pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, c
     C.nodes = s->d_nodes;
     C.out_tris = s->d_tris;
     C.in_tris = s->d_tris_raw;
+    C.dp = D;
     uint32_t qbeg = 0, qend = 1, depth = 0;
     uint32_t host_counters[4] = {0, 0, 0, 0};
     while (qbeg < qend) {

@@ -82,11 +82,11 @@ extern "C" pt_status pt_autotune(pt_scene* s, const pt_camera* camera, uint32_t 
     base.use_graph = 1;
     // BVH builder and leaf size first (one default schedule), then the schedule on the chosen tree
     if (tune_flags & PT_TUNE_BVH) {
-        pt_bvh_opts best_bo{s->leaf_size, s->builder};
+        pt_bvh_opts best_bo{s->leaf_size, s->builder, s->collapse, s->tri_cost, s->box_cost};
         float best_t = 3.4e38f;
         for (uint32_t builder : {(uint32_t)PT_BVH_PLOC, (uint32_t)PT_BVH_LBVH})
             for (uint32_t leaf = 1; leaf <= 4; ++leaf) {
-                pt_bvh_opts bo{leaf, builder};
+                pt_bvh_opts bo{leaf, builder, s->collapse, s->tri_cost, s->box_cost};
                 pt_status r = pt_bvh_build(s, &bo, cuda_stream);
                 if (r != PT_OK) return r;
                 float t = 0.0f;
@@ -94,7 +94,7 @@ extern "C" pt_status pt_autotune(pt_scene* s, const pt_camera* camera, uint32_t 
                 if (r != PT_OK) return r;
                 if (t < best_t) { best_t = t; best_bo = bo; }
             }
-        if (s->leaf_size != best_bo.leaf_size || s->builder != best_bo.builder) {
+        if (s->leaf_size != best_bo.leaf_size || s->builder != best_bo.builder) {   // same collapse rule
             pt_status r = pt_bvh_build(s, &best_bo, cuda_stream);
             if (r != PT_OK) return r;
         }

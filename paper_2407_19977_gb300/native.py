@@ -52,7 +52,8 @@ class pt_render_opts(C.Structure):
 
 
 class pt_bvh_opts(C.Structure):
-    _fields_ = [("leaf_size", u32), ("builder", u32)]
+    _fields_ = [("leaf_size", u32), ("builder", u32), ("collapse", u32), ("tri_cost", C.c_float),
+                ("box_cost", C.c_float)]
 
 
 class pt_stats(C.Structure):
@@ -93,6 +94,7 @@ PT_FLAG_NO_RR = 2
 PT_FLAG_COUNT = 4
 PT_TRAVERSAL_AUTO, PT_TRAVERSAL_PER_LANE, PT_TRAVERSAL_COOP = 0, 1, 2
 PT_BVH_DEFAULT, PT_BVH_LBVH, PT_BVH_PLOC = 0, 1, 2
+PT_COLLAPSE_DEFAULT, PT_COLLAPSE_OPTIMAL, PT_COLLAPSE_GREEDY = 0, 1, 2
 PT_TUNE_BVH = 1
 PT_TONEMAP_SRGB = 1
 KERNEL_KINDS = ("raygen", "trace", "sort", "shade", "shadow", "accum", "tail", "restir")

@@ -327,9 +327,10 @@ def test_closest_hit_parity(api, which, coop):
 
 @pytest.mark.parametrize("which", ["cornell", "pushbutton", "heavy"])
 def test_bvh_structure_and_surface_area_cost(api, which):
-    """The exported 8-wide tree from both builders is sound (one parent per node, each
-    triangle in one leaf, every decoded box holding what lies below it) and its surface-area
-    cost is compared with a binned-SAH binary tree built by the oracle on the same triangles.
+    """The exported 8-wide tree from both builders, folded greedily or by the cost-optimal
+    collapse, is sound (one parent per node, each triangle in one leaf, every decoded box
+    holding what lies below it) and its surface-area cost is compared with a binned-SAH
+    binary tree built by the oracle on the same triangles.
     The comparable measure is the expected number of triangle tests of a ray through the root
     box (leaf areas times counts, leaves of at most four in both).  A Morton-order radix tree
     gives up part of it to a SAH sweep; the clustering builder (the default) must give up
@@ -343,8 +344,11 @@ def test_bvh_structure_and_surface_area_cost(api, which):
     ref = oracle.sah_reference(tv)
     cost = {}
     try:
-        for builder, name in ((N.PT_BVH_LBVH, "radix tree"), (N.PT_BVH_PLOC, "clustering")):
-            gsc.build(builder=builder)
+        for builder, collapse, name in ((N.PT_BVH_LBVH, N.PT_COLLAPSE_GREEDY, "radix tree, greedy"),
+                                        (N.PT_BVH_LBVH, N.PT_COLLAPSE_OPTIMAL, "radix tree"),
+                                        (N.PT_BVH_PLOC, N.PT_COLLAPSE_GREEDY, "clustering, greedy"),
+                                        (N.PT_BVH_PLOC, N.PT_COLLAPSE_OPTIMAL, "clustering")):
+            gsc.build(builder=builder, collapse=collapse)
             nodes, tris = gsc.export_bvh()
             assert tris.shape[0] == tv.shape[0]
             problems, stats = bvh_check.check(nodes, tris)
@@ -930,21 +934,22 @@ def test_autotune_batch_leaves_jobs_untouched(api):
 
 def test_bvh_leaf_size_does_not_change_samples(api):
     """Closest hits (equal t -> lower id) and any-hits do not depend on the tree: both
-    builders and every leaf size give bit-identical samples."""
+    builders, both collapse rules and every leaf size give bit-identical samples."""
     from paper_2407_19977_gb300 import api as A
     from paper_2407_19977_gb300 import native as N
     sc = scenes.pushbutton_lod(20000, width=96, height=64, seed=2)
     g = A.Scene(sc, build=False)
     ref = None
     for builder in (N.PT_BVH_PLOC, N.PT_BVH_LBVH):
-        for leaf in (4, 1, 2, 3):
-            g.build(leaf_size=leaf, builder=builder)
-            smp = torch.zeros((64, 96, 2, 3), dtype=torch.float32, device="cuda")
-            g.render(2, accum=A.Accum(96, 64), mode=N.PT_MODE_WAVEFRONT, sample_out=smp, seed=3)
-            torch.cuda.synchronize()
-            if ref is None:
-                ref = smp.clone()
-            assert torch.equal(smp, ref), (builder, leaf)
+        for collapse in (N.PT_COLLAPSE_OPTIMAL, N.PT_COLLAPSE_GREEDY):
+            for leaf in (4, 1, 2, 3):
+                g.build(leaf_size=leaf, builder=builder, collapse=collapse)
+                smp = torch.zeros((64, 96, 2, 3), dtype=torch.float32, device="cuda")
+                g.render(2, accum=A.Accum(96, 64), mode=N.PT_MODE_WAVEFRONT, sample_out=smp, seed=3)
+                torch.cuda.synchronize()
+                if ref is None:
+                    ref = smp.clone()
+                assert torch.equal(smp, ref), (builder, collapse, leaf)
     assert g.stats()["error_flags"] == 0
 
 
@@ -1003,6 +1008,12 @@ def test_edge_cases(api):
                        sc.lights, None, sc.camera, 1, 1)
     with pytest.raises(N.PtError, match="INVALID_ARG"):
         A.Scene(nan, on_device=True)
+    # BVH options out of range; the scene keeps its tree
+    for kw in ({"leaf_size": 5}, {"builder": 3}, {"collapse": 3}, {"tri_cost": -1.0},
+               {"tri_cost": float("inf")}, {"box_cost": float("nan")}):
+        with pytest.raises(N.PtError, match="INVALID_ARG"):
+            g.build(**kw)
+    g.render(1, accum=A.Accum(37, 23))
 
 
 def test_stats_match_oracle_ray_counts(api):

@@ -623,21 +623,45 @@ __global__ void k_wf_sort_scan(uint32_t* counters, uint32_t n_keys) {
     if (t < n_keys) counters[C_BUCKETS + t] = part[t] - v;
 }
 
-__global__ void k_wf_sort_scatter(WfParams P, int in_q) {
+// Counting-sort scatter: each block ranks a chunk of SORT_ITEMS x SORT_THREADS slots in shared
+// memory (warp-aggregated shared atomics per key), reserves each key's run of the chunk with
+// one global atomic, then writes the permutation.  (One global atomic per key and warp made
+// the few material buckets a point of contention: 8.3M slots gave 0.8M atomics on 5 words.)
+constexpr uint32_t SORT_THREADS = 256, SORT_ITEMS = 16;
+
+__global__ void __launch_bounds__(SORT_THREADS) k_wf_sort_scatter(WfParams P, int in_q) {
+    __shared__ uint32_t s_cnt[MAX_SORT_KEYS];
     if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[in_q];
-    const uint32_t lane = lane_id();
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; base < count; base += nwarps * 32u) {
-        const uint32_t slot = base + lane;
-        const bool valid = slot < count;
-        const uint32_t key = valid ? P.keys[slot] : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, key);
-        const uint32_t leader = __ffs(peers) - 1;
-        uint32_t pos = 0;
-        if (valid && lane == leader) pos = atomicAdd(&P.counters[C_BUCKETS + key], __popc(peers));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (valid) P.perm[pos + __popc(peers & ((1u << lane) - 1u))] = slot;
+    const uint32_t n_keys = P.n_keys;
+    const uint32_t lane = lane_id(), tid = threadIdx.x;
+    const uint32_t lt = (1u << lane) - 1u;
+    constexpr uint32_t CHUNK = SORT_THREADS * SORT_ITEMS;
+    for (uint32_t c0 = blockIdx.x * CHUNK; c0 < count; c0 += gridDim.x * CHUNK) {
+        for (uint32_t k = tid; k < n_keys; k += SORT_THREADS) s_cnt[k] = 0u;
+        __syncthreads();
+        uint32_t key[SORT_ITEMS], rank[SORT_ITEMS];
+#pragma unroll
+        for (uint32_t i = 0; i < SORT_ITEMS; ++i) {
+            const uint32_t slot = c0 + i * SORT_THREADS + tid;
+            key[i] = slot < count ? min(P.keys[slot], n_keys - 1u) : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, key[i]);
+            const uint32_t leader = __ffs(peers) - 1;
+            uint32_t b = 0;
+            if (key[i] != 0xffffffffu && lane == leader) b = atomicAdd(&s_cnt[key[i]], __popc(peers));
+            rank[i] = __shfl_sync(0xffffffffu, b, leader) + __popc(peers & lt);
+        }
+        __syncthreads();
+        // the chunk's run of each key: counts -> global positions (in place)
+        for (uint32_t k = tid; k < n_keys; k += SORT_THREADS) {
+            const uint32_t c = s_cnt[k];
+            s_cnt[k] = c ? atomicAdd(&P.counters[C_BUCKETS + k], c) : 0u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (uint32_t i = 0; i < SORT_ITEMS; ++i)
+            if (key[i] != 0xffffffffu) P.perm[s_cnt[key[i]] + rank[i]] = c0 + i * SORT_THREADS + tid;
+        __syncthreads();
     }
 }
 
@@ -1530,7 +1554,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                     if (n_keys) {
                         e = begin(PT_K_SORT);
                         PT_LAUNCH(k_wf_sort_scan, 1, MAX_SORT_KEYS, 0, st, w.counters, n_keys);
-                        PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
+                        PT_LAUNCH(k_wf_sort_scatter, sms * 2, SORT_THREADS, 0, st, P, in_q);
                         end(e);
                         launches += 2;
                     }
@@ -1890,7 +1914,7 @@ static pt_status merged_launches(MergedBatch& m, const WfParams& base, uint32_t 
             PT_LAUNCH((k_wf_trace<false, true>), sms * g_trace_blocks_per_sm, 128, 0, st, P, in_q);
             if (P.n_keys) {
                 PT_LAUNCH(k_wf_sort_scan, 1, MAX_SORT_KEYS, 0, st, m.wave.counters, P.n_keys);
-                PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
+                PT_LAUNCH(k_wf_sort_scatter, sms * 2, SORT_THREADS, 0, st, P, in_q);
                 *launches += 2;
             }
             if (fuzz) PT_LAUNCH((k_wf_shade<false, false, true, true>), sms * g_shade_blocks_per_sm, 128, 0, st, P, in_q, out_q, k);
@@ -2179,7 +2203,7 @@ extern "C" pt_status pt_render_noalloc(pt_scene* s, const pt_camera* camera, uin
             launches += 2;
             if (n_keys) {
                 PT_LAUNCH(k_wf_sort_scan, 1, MAX_SORT_KEYS, 0, st, w.counters, n_keys);
-                PT_LAUNCH(k_wf_sort_scatter, sms * 8, 128, 0, st, P, in_q);
+                PT_LAUNCH(k_wf_sort_scatter, sms * 2, SORT_THREADS, 0, st, P, in_q);
                 launches += 2;
             }
             launch_shade<false, false>(s->has_fuzz, sms * g_shade_blocks_per_sm, st, P, in_q, out_q, k);

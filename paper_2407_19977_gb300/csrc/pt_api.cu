@@ -152,7 +152,7 @@ static void free_scene(pt_scene* s) {
     if (!s) return;
     void* ptrs[] = {s->d_vertices, s->d_indices, s->d_matids, s->d_tris_raw, s->d_tris, s->d_nodes,
                     s->d_mats, s->d_fuzz, s->d_quads, s->d_quads_raw, s->d_env, s->d_env_marg, s->d_env_cond,
-                    s->d_env_wtex, s->d_env_total, s->d_err, s->d_stats, s->d_head};
+                    s->d_env_wtex, s->d_env_total, s->d_env_guide, s->d_err, s->d_stats, s->d_head};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     pt_free_wave(s->wave);

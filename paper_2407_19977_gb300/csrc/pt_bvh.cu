@@ -891,6 +891,19 @@ __global__ void k_env_marg(const float* rowsum, int h, float* marg, float* total
     }
 }
 
+// search guides: guide[g] = the CDF index for u = g / G (see cdf_find_guided)
+__global__ void k_env_guides(const float* marg, const float* cond, int w, int h, int gm, int gc, int* guide) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= gm) {
+        guide[t] = cdf_find(marg, h, (float)t / (float)gm);
+        return;
+    }
+    const int r = t - (gm + 1);
+    if (r >= h * (gc + 1)) return;
+    const int y = r / (gc + 1), g = r % (gc + 1);
+    guide[t] = cdf_find(cond + (size_t)y * (w + 1), w, (float)g / (float)gc);
+}
+
 pt_status pt_build_env_impl(pt_scene* s, cudaStream_t st) {
     if (!s->d_env || s->env_w <= 0) { s->env_total = 0.0f; return PT_OK; }
     const int w = s->env_w, h = s->env_h;
@@ -900,11 +913,20 @@ pt_status pt_build_env_impl(pt_scene* s, cudaStream_t st) {
         PT_CUDA_TRY(cudaMalloc(&s->d_env_cond, (size_t)h * (w + 1) * sizeof(float)));
         PT_CUDA_TRY(cudaMalloc(&s->d_env_marg, (size_t)(h + 1) * sizeof(float)));
         PT_CUDA_TRY(cudaMalloc(&s->d_env_total, sizeof(float)));
+        int gm = 1, gc = 1;
+        while (gm < h) gm <<= 1;
+        while (gc < w) gc <<= 1;
+        s->env_gm = gm;
+        s->env_gc = gc;
+        PT_CUDA_TRY(cudaMalloc(&s->d_env_guide, ((size_t)gm + 1 + (size_t)h * (gc + 1)) * sizeof(int)));
     }
     PT_CUDA_TRY(cudaMalloc(&rowsum, (size_t)h * sizeof(float)));
     PT_LAUNCH(k_env_rows, h, 256, 0, st, s->d_env, w, h, s->d_env_wtex, s->d_env_cond, rowsum);
     PT_LAUNCH(k_env_marg, 1, 1024, 0, st, rowsum, h, s->d_env_marg, s->d_env_total);
-    s->launches += 2;
+    const int ng = s->env_gm + 1 + h * (s->env_gc + 1);
+    PT_LAUNCH(k_env_guides, (ng + 255) / 256, 256, 0, st, s->d_env_marg, s->d_env_cond, w, h, s->env_gm, s->env_gc,
+              s->d_env_guide);
+    s->launches += 3;
     PT_CUDA_TRY(cudaMemcpyAsync(&s->env_total, s->d_env_total, sizeof(float), cudaMemcpyDeviceToHost, st));
     PT_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(rowsum);

@@ -532,6 +532,7 @@ struct DScene {
     const float* env_marg;     // env_h + 1
     const float* env_cond;     // env_h * (env_w + 1)
     const float* env_wtex;     // env_h * env_w (unnormalised weights)
+    const int* env_guide;      // search guides: env_gm + 1 for the marginal, then env_gc + 1 per row
     uint32_t* err;             // sticky error bits
     float env_total;
     float eps;
@@ -539,6 +540,7 @@ struct DScene {
     int n_quads;
     int n_nodes;
     int n_tris;
+    int env_gm, env_gc;        // guide sizes (powers of two)
     int pad;
 };
 
@@ -1190,8 +1192,8 @@ __device__ __forceinline__ float env_pdf(const DScene& S, float3 d) {
     return pdf_uv / (2.0f * PT_PI_F * PT_PI_F * s);
 }
 // largest i in [0, n-1] with cdf[i] <= u
-__device__ __forceinline__ int cdf_find(const float* cdf, int n, float u) {
-    int lo = 0, hi = n - 1;
+// the largest i in [lo, hi] with cdf[i] <= u, given cdf[lo] <= u (cdf non-decreasing)
+__device__ __forceinline__ int cdf_find_in(const float* cdf, int lo, int hi, float u) {
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (__ldg(cdf + mid) <= u) lo = mid;
@@ -1199,14 +1201,24 @@ __device__ __forceinline__ int cdf_find(const float* cdf, int n, float u) {
     }
     return lo;
 }
+__device__ __forceinline__ int cdf_find(const float* cdf, int n, float u) { return cdf_find_in(cdf, 0, n - 1, u); }
+
+// The same index through a guide table (the cutpoint method of Chen and Asau 1974): guide[g] is
+// the answer for u = g / G, G a power of two, so g = floor(u G) is exact and the answer for u
+// lies in [guide[g], guide[g + 1]]: the search there returns what the search over [0, n - 1]
+// returns, in about one step instead of log2 n dependent loads.
+__device__ __forceinline__ int cdf_find_guided(const float* cdf, const int* guide, int G, float u) {
+    const int g = min(max((int)(u * (float)G), 0), G - 1);
+    return cdf_find_in(cdf, __ldg(guide + g), __ldg(guide + g + 1), u);
+}
 __device__ __forceinline__ bool env_sample(const DScene& S, float u3, float u4, float3& d, float& pdf, float3& L) {
     if (S.env_total <= 0.0f) return false;
     const int w = S.env_w, h = S.env_h;
-    const int y = cdf_find(S.env_marg, h, u3);
+    const int y = cdf_find_guided(S.env_marg, S.env_guide, S.env_gm, u3);
     const float m0 = S.env_marg[y], m1 = S.env_marg[y + 1];
     const float dv = m1 > m0 ? (u3 - m0) / (m1 - m0) : 0.5f;
     const float* cd = S.env_cond + (size_t)y * (w + 1);
-    const int x = cdf_find(cd, w, u4);
+    const int x = cdf_find_guided(cd, S.env_guide + (S.env_gm + 1) + (size_t)y * (S.env_gc + 1), S.env_gc, u4);
     const float c0 = cd[x], c1 = cd[x + 1];
     const float du = c1 > c0 ? (u4 - c0) / (c1 - c0) : 0.5f;
     const float u = ((float)x + du) / (float)w, v = ((float)y + dv) / (float)h;

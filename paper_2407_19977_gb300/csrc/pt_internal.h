@@ -103,6 +103,8 @@ struct pt_scene {
     float* d_env_cond = nullptr;
     float* d_env_wtex = nullptr;
     float* d_env_total = nullptr;
+    int* d_env_guide = nullptr;      // search guides of the marginal and conditional CDFs
+    int env_gm = 0, env_gc = 0;
     float env_total = 0.0f;
     int env_w = 0, env_h = 0;
     float eps = 0.0f;
@@ -142,6 +144,9 @@ struct pt_scene {
         s.env_marg = d_env_marg;
         s.env_cond = d_env_cond;
         s.env_wtex = d_env_wtex;
+        s.env_guide = d_env_guide;
+        s.env_gm = env_gm;
+        s.env_gc = env_gc;
         s.err = d_err;
         s.env_total = env_total;
         s.eps = eps;

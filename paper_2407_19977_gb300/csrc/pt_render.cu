@@ -795,7 +795,7 @@ __global__ void __launch_bounds__(128, 6) k_restir_spatial(WfParams P, uint32_t 
 }
 
 template <bool NRC, bool RIS, bool FUZZ = true, bool MULTI = false>
-__global__ void __launch_bounds__(128, 4) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
+__global__ void __launch_bounds__(128, 5) k_wf_shade(WfParams P, int in_q, int out_q, uint32_t k) {
     if (P.counters[C_TAIL]) return;
     const uint32_t count = P.counters[in_q];
     const uint32_t sbase = wf_sample_base(P);

@@ -87,7 +87,7 @@ def _args():
                     help="cost of each child slot of a visited wide node for the optimal collapse (0: default)")
     ap.add_argument("--spp-per-step", type=int, default=4,
                     help="samples per pixel of the frame one step renders (progressive: each step adds them)")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU work of the oracle sample")
     ap.add_argument("--study-frames", type=int, default=256, help="frames per curve of the NRC study")
     ap.add_argument("--batch-scenes", type=int, default=64)
     ap.add_argument("--study", default=None, choices=[None, "nrc", "nrc_train", "batch", "paper", "restir", "bmfr"],
@@ -372,7 +372,9 @@ def run_reference(args, world, rank):
         "metric": _metric_name(args.workload), "value": value, "unit": "Mrays/s", "impl": "reference",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "sample": f"every {row_step}th row, 1 spp per step"},
+        "config": {"workload": WORKLOADS[args.workload].replace("1 spp/step", f"{args.spp_per_step} spp/step"),
+                   "spp_per_step": args.spp_per_step,
+                   "sample": f"every {row_step}th row at 1 spp per step (a bounded slice of each step's rays)"},
         "spp_per_s_1080p": paths / dt / (sc.camera.width * sc.camera.height),
         "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
                          "sample": f"every {row_step}th row of the {sc.camera.width}x{sc.camera.height} frame "
@@ -743,6 +745,16 @@ def run_nrc_study(args, local):
         scene.render(chunk, seed=777, accum=ref, mode=N.PT_MODE_WAVEFRONT)
     torch.cuda.synchronize()
     ref_img = ref.image()
+    # where the light comes from: the image rendered with paths cut after their first and
+    # second vertices, against the full reference (the cache can only replace what lies past
+    # the second diffuse-ish vertex, so the shares bound what it can gain)
+    shares = {}
+    for depth in (1, 2):
+        part = api.Accum(W, H)
+        for i in range(256 // chunk):
+            scene.render(chunk, max_depth=depth, seed=778, accum=part, mode=N.PT_MODE_WAVEFRONT)
+        torch.cuda.synchronize()
+        shares[f"depth_le_{depth}"] = float(part.image().mean() / ref_img.mean())
     marks = [m for m in (1, 2, 4, 8, 16, 32, 64, 128, 256) if m <= args.study_frames]
     curves = {}
     lo = sc.vertices.min(0) - 0.05
@@ -768,7 +780,7 @@ def run_nrc_study(args, local):
     time_to = _time_to
     out = {"study": "nrc_equal_time", "workload": WORKLOADS[args.workload], "ref_spp": args.ref_spp,
            "nrc_batch": args.nrc_batch, "nrc_frame_samples": args.nrc_frame_samples,
-           "relmse_eps": 1e-2, "curves": curves}
+           "relmse_eps": 1e-2, "radiance_share_of_paths_cut_at_depth": shares, "curves": curves}
     for spp in (16, 64):
         if spp > marks[-1]:
             continue

@@ -513,6 +513,25 @@ def test_full_frame_bench_configuration(api, spp, wave):
     _image_check(g[::45], o[::45], f"pushbutton 1080p rows, {spp} spp")
 
 
+@pytest.mark.parametrize("spp,wave", [(1, 0), (4, 1 << 23)])
+def test_full_frame_heavy_configuration(api, spp, wave):
+    """The 5.24M-triangle glass/metal scene at 1080p, whole frame, depth 12, wavefront with
+    material sort and the tail kernel: one sample per pixel, and four in one wave of 2^23
+    paths.  The oracle checks every 45th row sample by sample: paths whose reflect/refract
+    choice flips between FP32 and FP64 are counted and bounded, the rest held to 1e-3."""
+    from paper_2407_19977_gb300 import api as A
+    sc, gsc, osc = heavy()
+    W, H = sc.camera.width, sc.camera.height
+    smp = torch.zeros((H, W, spp, 3), dtype=torch.float32, device="cuda")
+    acc = A.Accum(W, H)
+    gsc.render(spp, seed=9, accum=acc, mode=1, wave_paths=wave, sort=1, sample_out=smp)
+    torch.cuda.synchronize()
+    gs = smp[::45].cpu().numpy()
+    _, os_, st = osc.render(spp=spp, seed=9, row_step=45, keep_samples=True)
+    _samples_check(gs, np.asarray(os_)[::45], f"heavy 1080p rows, {spp} spp")
+    assert gsc.stats()["error_flags"] == 0
+
+
 def test_full_frame_fuzz_configuration(api):
     """The benchmark's velvet variant of the 1080p pushbutton, whole frame, one sample per
     pixel, wavefront (kernels with the fuzz layer); the oracle checks every 45th row."""

@@ -85,11 +85,15 @@ def _args():
                     help="cost of a triangle test against a wide node visit for the optimal collapse (0: default)")
     ap.add_argument("--bvh-box-cost", type=float, default=0.0,
                     help="cost of each child slot of a visited wide node for the optimal collapse (0: default)")
+    ap.add_argument("--bvh-width", type=int, default=8, choices=range(2, 9),
+                    help="most children per BVH node (the node format holds 8)")
     ap.add_argument("--spp-per-step", type=int, default=4,
                     help="samples per pixel of the frame one step renders (progressive: each step adds them)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU work of the oracle sample")
     ap.add_argument("--study-frames", type=int, default=256, help="frames per curve of the NRC study")
     ap.add_argument("--batch-scenes", type=int, default=64)
+    ap.add_argument("--no-bvh-tune", action="store_true",
+                    help="batch study: keep the scenes' 8-wide trees (no BVH width in pt_autotune_batch)")
     ap.add_argument("--study", default=None, choices=[None, "nrc", "nrc_train", "batch", "paper", "restir", "bmfr"],
                     help="nrc: relMSE vs time, radiance cache against the plain tracer; nrc_train: the "
                          "radiance-cache training and inference kernels alone")
@@ -407,7 +411,7 @@ def run_ours(args, world, rank, local):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     bvh = {"builder": {"ploc": N.PT_BVH_PLOC, "lbvh": N.PT_BVH_LBVH}[args.bvh_builder],
            "collapse": {"optimal": N.PT_COLLAPSE_OPTIMAL, "greedy": N.PT_COLLAPSE_GREEDY}[args.bvh_collapse],
-           "tri_cost": args.bvh_tri_cost, "box_cost": args.bvh_box_cost}
+           "tri_cost": args.bvh_tri_cost, "box_cost": args.bvh_box_cost, "max_width": args.bvh_width}
     scene.build(**bvh)                      # first build: allocations and module load
     torch.cuda.synchronize()
     ev0.record(stream)
@@ -534,7 +538,7 @@ def run_ours(args, world, rank, local):
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload].replace("1 spp/step", f"{args.spp_per_step} spp/step"),
-                   "spp_per_step": args.spp_per_step, "bvh_builder": args.bvh_builder,
+                   "spp_per_step": args.spp_per_step, "bvh_builder": args.bvh_builder, "bvh_width": args.bvh_width,
                    "bvh_collapse": args.bvh_collapse + (f" (tri_cost {args.bvh_tri_cost}, box_cost {args.bvh_box_cost})"
                                                         if args.bvh_tri_cost or args.bvh_box_cost else ""),
                    "mode": "auto (autotuned)" if tuned else args.mode,
@@ -900,10 +904,13 @@ def run_batch_study(args, local):
         for sp, g, sc, acc in zip(specs, gs, scs, accs):
             g.render(sp["spp"], max_depth=sp["max_depth"], seed=sp["seed"], accum=acc, mode=N.PT_MODE_AUTO,
                      use_graph=True)
-    t_scene = timed(per_scene)
     baccs = [api.Accum(s["width"], s["height"]) for s in specs]
     tune_jobs = [(g, sc.camera, 1, sp["max_depth"], sp["seed"], acc) for sp, g, sc, acc in zip(specs, gs, scs, baccs)]
-    best, tune_ms = api.autotune_batch(tune_jobs, frames=1)
+    # BVH width (every scene rebuilt at 8, 6 and 4 children per node) and schedule; every
+    # variant below, per-scene launches included, then runs on the trees it leaves
+    best, tune_ms = api.autotune_batch(tune_jobs, frames=1, bvh=not args.no_bvh_tune)
+    bvh_width = gs[0].stats()["bvh_width"]
+    t_scene = timed(per_scene)
     jobs = [(g, sc.camera, sp["spp"], sp["max_depth"], sp["seed"], acc) for sp, g, sc, acc in zip(specs, gs, scs, baccs)]
     variants = {"tuned": best,
                 "megakernel_one_launch": {"mode": N.PT_MODE_MEGAKERNEL, "streams": 0, "tile_pixels": 32,
@@ -927,7 +934,7 @@ def run_batch_study(args, local):
                                           f"{tris:,} triangles in all, 256^2..1920x1080, 1-32 spp, depth 8",
            "samples": samples, "scene_gen_s": gen_s, "upload_build_s": upload_build_s,
            "per_scene": {"ms": t_scene, "msamples_per_s": samples / (t_scene * 1e-3) / 1e6},
-           "batch": res, "tune_ms_per_1spp_batch": tune_ms}
+           "batch": res, "tune_ms_per_1spp_batch": tune_ms, "bvh_width": bvh_width}
     print(json.dumps(out))
 
 

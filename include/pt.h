@@ -259,6 +259,11 @@ typedef struct {
                                    frames); used by PT_COLLAPSE_OPTIMAL */
     float box_cost;             /* cost of each child slot of a visited wide node, >= 0 and
                                    finite (0 = 0, negative = exactly 0); PT_COLLAPSE_OPTIMAL */
+    uint32_t max_width;         /* BVH width: most children a node may have, 2..8 (0 = 8).  The
+                                   node format keeps 8 slots; a narrower tree leaves the rest
+                                   empty (more, smaller nodes, fewer box tests per node).  Both
+                                   collapse rules honour it; pt_autotune with PT_TUNE_BVH and
+                                   pt_autotune_batch with PT_TUNE_BVH choose it. */
 } pt_bvh_opts;
 
 typedef struct {
@@ -287,7 +292,8 @@ typedef struct {
     uint64_t tail_shadow_tris;
     uint64_t graph_replays;     /* wavefront calls served by replaying a captured CUDA graph */
     uint32_t error_flags;       /* sticky device error bits (1 = stack overflow, 2 = timeout) */
-    uint32_t reserved;
+    uint32_t bvh_width;         /* most children a node of the current BVH may have
+                                   (pt_bvh_opts.max_width as built; 0 before the first build) */
 } pt_stats;
 
 /* Scene setup (Sec. 5.1.1 "CPU setup": load geometry and materials).
@@ -403,8 +409,8 @@ pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const pt_batch_op
  * sort off/on x tail limit (off, automatic, a quarter, four times) x wave size (2^20 .. 2^23
  * paths, as far as the call needs them), graph replay on; megakernel with 32, 64, 128 pixels
  * per work item; then the winner's traversal passes one ray per lane or per 8-lane group.  With
- * PT_TUNE_BVH it first rebuilds the BVH with both builders and leaf sizes 1..4 (the node
- * width is fixed at 8 by the node format) and keeps the fastest.  The winner goes to *best (and ms per frame to
+ * PT_TUNE_BVH it first rebuilds the BVH with both builders and leaf sizes 1..4 at width 8, then
+ * the fastest of those at widths 4 and 6 (pt_bvh_opts.max_width), and keeps the fastest tree.  The winner goes to *best (and ms per frame to
  * *best_ms) and is stored in the scene: pt_render with PT_MODE_AUTO then uses it for frames
  * of that size (not with nrc; with kernel_ms the launches are direct, not replayed).  No candidate changes the image: they render the
  * same samples; the tuning renders do count in pt_get_stats.  Synchronises the stream.
@@ -415,9 +421,13 @@ pt_status pt_autotune(pt_scene* scene, const pt_camera* camera, uint32_t spp, ui
                       void* cuda_stream);
 /* The same for a batch: each job rendered into scratch accumulators (the jobs' own are not
  * touched); candidates: megakernel with tile_pixels 32..256 x blocks_per_sm (automatic, 2, 4),
- * wavefront with 1, 2, 4, 8 streams, merged wavefront with 2^22, 2^23, 2^24 paths per wave. */
-pt_status pt_autotune_batch(const pt_job* jobs, uint32_t n_jobs, uint32_t frames, pt_batch_opts* best,
-                            float* best_ms, void* cuda_stream);
+ * wavefront with 1, 2, 4, 8 streams, merged wavefront with 2^22, 2^23, 2^24 paths per wave.
+ * With PT_TUNE_BVH it first rebuilds every scene of the jobs at BVH widths 8, 6 and 4 (each
+ * scene keeps its builder, leaf size and collapse rule), times one merged wavefront of 2^23
+ * paths per wave on each, and leaves the scenes built at the fastest width, which goes to
+ * the schedule sweep; the scenes' trees change, their images do not. */
+pt_status pt_autotune_batch(const pt_job* jobs, uint32_t n_jobs, uint32_t frames, uint32_t tune_flags,
+                            pt_batch_opts* best, float* best_ms, void* cuda_stream);
 
 /* Closest hit of n rays through the scene's BVH (Sec. 5.1.3 "checks for intersections using
  * the BVH").  rays: DEVICE float[n*8] = origin[3], dir[3], tmax, unused.  Outputs (DEVICE):

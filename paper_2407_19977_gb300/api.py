@@ -113,11 +113,11 @@ class Scene:
         if build:
             self.build(leaf_size, builder=builder)
 
-    def build(self, leaf_size=4, stream=None, builder=0, collapse=0, tri_cost=0.0, box_cost=0.0):
+    def build(self, leaf_size=4, stream=None, builder=0, collapse=0, tri_cost=0.0, box_cost=0.0, max_width=0):
         """pt_bvh_build; builder N.PT_BVH_LBVH or N.PT_BVH_PLOC (0: the default, PLOC); collapse
         N.PT_COLLAPSE_OPTIMAL or N.PT_COLLAPSE_GREEDY (0: optimal) with tri_cost and box_cost
-        (0: defaults)."""
-        o = N.pt_bvh_opts(leaf_size, builder, collapse, float(tri_cost), float(box_cost))
+        (0: defaults); max_width the most children of a node, 2..8 (0: 8)."""
+        o = N.pt_bvh_opts(leaf_size, builder, collapse, float(tri_cost), float(box_cost), int(max_width))
         N.call("pt_bvh_build", self.h, C.byref(o), _stream_handle(stream))
 
     def __del__(self):
@@ -297,13 +297,15 @@ def _job_array(jobs):
     return arr
 
 
-def autotune_batch(jobs, frames=2, stream=None):
+def autotune_batch(jobs, frames=2, stream=None, bvh=False):
     """pt_autotune_batch over (Scene, camera, spp, max_depth, seed, Accum) jobs; the jobs'
-    accumulators are not touched.  Returns ({tile_pixels, blocks_per_sm}, ms per batch)."""
+    accumulators are not touched.  With bvh the jobs' scenes are rebuilt at the fastest BVH
+    width first (N.PT_TUNE_BVH).  Returns (the chosen pt_batch_opts fields, ms per batch)."""
     arr = _job_array(jobs)
     best = N.pt_batch_opts()
     ms = N.f32()
-    N.call("pt_autotune_batch", arr, len(jobs), int(frames), C.byref(best), C.byref(ms), _stream_handle(stream))
+    N.call("pt_autotune_batch", arr, len(jobs), int(frames), N.PT_TUNE_BVH if bvh else 0, C.byref(best),
+           C.byref(ms), _stream_handle(stream))
     return {"mode": int(best.mode), "streams": int(best.streams), "tile_pixels": int(best.tile_pixels),
             "blocks_per_sm": int(best.blocks_per_sm), "use_graph": int(best.use_graph),
             "merged": int(best.merged), "wave_paths": int(best.wave_paths)}, float(ms.value)

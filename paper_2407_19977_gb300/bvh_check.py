@@ -148,7 +148,8 @@ def check(nodes: np.ndarray, tris: np.ndarray):
         problems.append(f"{int(bad.sum())} child boxes do not contain their subtrees")
     children = np.bincount(S["ni"], minlength=n) + np.bincount(S["li"], minlength=n)
     stats = dict(n_nodes=int(n), n_tris=int(n_tris), depth=len(B["levels"]),
-                 mean_children=float(children.mean()), mean_leaf_size=float(S["count"].mean()),
+                 mean_children=float(children.mean()), max_children=int(children.max()),
+                 mean_leaf_size=float(S["count"].mean()),
                  max_leaf_size=int(S["count"].max()))
     return problems, stats
 

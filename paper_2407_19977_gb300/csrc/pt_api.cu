@@ -330,10 +330,13 @@ extern "C" pt_status pt_bvh_build(pt_scene* s, const pt_bvh_opts* opts, void* cu
     float box_cost = opts && opts->box_cost != 0.0f ? opts->box_cost : 0.0f;
     PT_CHECK_ARG(box_cost < 1e6f && box_cost == box_cost, "box_cost must be finite");
     if (box_cost < 0.0f) box_cost = 0.0f;
+    const uint32_t width = opts && opts->max_width ? opts->max_width : 8u;
+    PT_CHECK_ARG(width >= 2 && width <= 8, "max_width must be 2..8");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     s->last_stream = st;
-    pt_status r = pt_build_bvh_impl(s, leaf, builder, collapse, tri_cost, box_cost, st);
+    pt_status r = pt_build_bvh_impl(s, leaf, builder, collapse, tri_cost, box_cost, width, st);
     if (r == PT_OK) {
+        s->max_width = width;
         s->leaf_size = leaf;
         s->builder = builder;
         s->collapse = collapse;
@@ -381,6 +384,7 @@ extern "C" pt_status pt_get_stats(pt_scene* s, pt_stats* out) {
     out->kernel_launches = s->launches;
     out->bvh_nodes = s->n_nodes;
     out->bvh_depth = s->depth;
+    out->bvh_width = s->built ? s->max_width : 0u;
     out->n_triangles = s->n_tris;
     out->trace_nodes = st[ST_NODES];
     out->trace_tris = st[ST_TRIS];

@@ -210,11 +210,11 @@ __device__ __forceinline__ Box box_union(Box a, Box b) {
 
 // ---- cost-optimal collapse: per binary node, the least surface-area cost of its subtree
 // when it fills exactly j = 1..8 slots of a wide node (the dynamic programme of Ylitie,
-// Karras and Laine, HPG 2017, restated for leaves of at most leaf_size triangles).  With A the
-// (half) surface area, a wide node visit costing 1 plus box_cost per slot and a triangle test
-// tri_cost:
+// Karras and Laine, HPG 2017, restated for leaves of at most leaf_size triangles and nodes of
+// at most W = width children).  With A the (half) surface area, a wide node visit costing 1
+// plus box_cost per slot and a triangle test tri_cost:
 //   C(k)    = A(k) * tri_cost * count(k)                          if count(k) <= leaf_size
-//           = A(k) + min_{j=2..8} E(k, j) + A(k) * box_cost * j    otherwise (a wide node)
+//           = A(k) + min_{j=2..W} E(k, j) + A(k) * box_cost * j    otherwise (a wide node)
 //   E(k, 1) = C(k);  E(k, j) = min_{i=1..j-1} E(L, i) + E(R, j - i)  (j >= 2)
 // and a single triangle costs A * tri_cost as one slot and cannot fill more.  dec[k] keeps
 // the choices in nibbles: nibble 0 the slot count j of C(k) for a wide node, nibble j - 1
@@ -224,6 +224,7 @@ struct DpArrays {
     uint32_t* dec;          // choices, one word per binary node
     uint32_t leaf_size;
     float tri_cost, box_cost;
+    uint32_t width;         // most children of a wide node, 2..8
 };
 
 __device__ __forceinline__ float half_area_box(float3 lo, float3 hi) {
@@ -266,7 +267,7 @@ __device__ __forceinline__ void dp_node(const DpArrays& D, uint32_t k, uint32_t 
     } else {
         float best = __int_as_float(0x7f800000);
         uint32_t bj = 2;
-        for (uint32_t j = 2; j <= 8; ++j) {
+        for (uint32_t j = 2; j <= D.width; ++j) {
             const float v = e[j - 1] + area * D.box_cost * (float)j;
             if (v < best) { best = v; bj = j; }
         }
@@ -511,6 +512,7 @@ __global__ void k_ploc_layout(uint32_t lo, uint32_t hi, uint32_t* left, uint32_t
 struct CollapseCtx {
     BinTree T;
     uint32_t leaf_size;
+    uint32_t width;         // most children of a wide node, 2..8
     uint32_t* task_ref;     // binary node ref of each wide-node task
     uint32_t* task_node;    // wide node index of each task
     uint32_t* counters;     // [0] node count, [1] triangle count, [2] queue tail
@@ -575,7 +577,7 @@ __global__ void k_collapse(CollapseCtx C, uint32_t qbeg, uint32_t qend) {
         cb[0] = ref_box(T, ch[0]);
         cb[1] = ref_box(T, ch[1]);
         nc = 2;
-        while (nc < 8) {
+        while (nc < (int)C.width) {
             int best = -1;
             float best_a = -1.0f;
             for (int j = 0; j < nc; ++j) {
@@ -672,7 +674,7 @@ static cudaError_t dalloc(T** p, size_t n) {
 }
 
 pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, uint32_t collapse, float tri_cost,
-                            float box_cost, cudaStream_t st) {
+                            float box_cost, uint32_t max_width, cudaStream_t st) {
     const uint32_t n = s->n_tris;
     if (s->d_nodes) { cudaFree(s->d_nodes); s->d_nodes = nullptr; }
     if (s->d_tris) { cudaFree(s->d_tris); s->d_tris = nullptr; }
@@ -707,7 +709,7 @@ pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, u
     BTRY(dalloc(&tref, n + 1)); BTRY(dalloc(&tnode, n + 1)); BTRY(dalloc(&counters, 4));
     BTRY(dalloc(&blo, n)); BTRY(dalloc(&bhi, n));
     if (builder == PT_BVH_PLOC) { BTRY(dalloc(&clo, (size_t)2 * n)); BTRY(dalloc(&chi, (size_t)2 * n)); }
-    DpArrays D{nullptr, nullptr, leaf_size, tri_cost, box_cost};
+    DpArrays D{nullptr, nullptr, leaf_size, tri_cost, box_cost, max_width};
     if (collapse == PT_COLLAPSE_OPTIMAL) {
         BTRY(dalloc(&dpc, (size_t)8 * n));
         BTRY(dalloc(&dpd, n));
@@ -791,6 +793,7 @@ pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, u
     CollapseCtx C;
     C.T = T;
     C.leaf_size = leaf_size;
+    C.width = max_width;
     C.task_ref = tref;
     C.task_node = tnode;
     C.counters = counters;

@@ -649,30 +649,39 @@ __device__ __forceinline__ NodeView load_node(const uint4* __restrict__ nodes, u
 
 // Per-node setup of the child box tests.  Along each axis the near and far planes of child
 // slot i are p + q_near(i) * scale and p + q_far(i) * scale (near/far chosen once per ray by
-// the direction's sign), so their ray distances are fma(q, scale/d, (p - o)/d).  eps widens
-// every slab by a bound on the rounding of those terms (the products, the fma and the
-// builder's one-rounding decode), which keeps the test conservative.
+// the direction's sign), so their ray distances are q * b + (p - o)/d with b = scale/d.  The
+// byte q is read as the float f = 1 + q / 2^15 (the byte placed in the mantissa of 1.0, no
+// conversion instruction), and the distance is evaluated as fma(f, B, c) with B = 2^15 b
+// (exact: a power of two times b) and c = (p - o)/d - B (one more rounding).  eps widens
+// every slab by a bound on the rounding of those terms: the subtraction, the products and
+// the fma (at most 4 units of the last place of |(p - o)/d| + 255 |b|), the builder's
+// one-rounding decode of the plane (|p/d| + 255 |b|) and the rounding of c (half a unit of
+// the last place of 2^15 |b|, i.e. at most 2^-9 |b|): 4e-7 (|(p - o)/d| + 255 |b| + |p/d|) +
+// 4e-3 |b| covers them, so the test stays conservative.  (A B or c that overflows makes that
+// axis's distances NaN, which fmaxf/fminf ignore: the box is then tested on the other axes
+// only, which is conservative too.)
 struct NodeTest {
-    float3 an, af, b;                              // (p - o)/d - eps, (p - o)/d + eps, scale/d
+    float3 cn, cf, B;                              // (p - o)/d -/+ eps - B, B = 2^15 scale/d
     uint32_t nx0, nx1, ny0, ny1, nz0, nz1;         // near-plane byte words per axis
     uint32_t fx0, fx1, fy0, fy1, fz0, fz1;         // far-plane byte words per axis
 };
 
-// byte i of the 8-byte array (w0, w1) as a float, via a float whose mantissa holds it
+// byte i of the 8-byte array (w0, w1) in bits 8..15 of 1.0f: the float 1 + q / 2^15, exactly
 __device__ __forceinline__ float qbyte(uint32_t w0, uint32_t w1, int i) {
-    return __uint_as_float(__byte_perm(i < 4 ? w0 : w1, 0x4B000000u, 0x7440u | (uint32_t)(i & 3))) - 8388608.0f;
+    return __uint_as_float(__byte_perm(i < 4 ? w0 : w1, 0x3F800000u, 0x7604u | ((uint32_t)(i & 3) << 4)));
 }
 
 __device__ __forceinline__ void node_setup(const NodeView& v, const TravRay& r, NodeTest& T) {
     const float ax = __fmul_rn(__fsub_rn(v.p.x, r.o.x), r.inv.x);
     const float ay = __fmul_rn(__fsub_rn(v.p.y, r.o.y), r.inv.y);
     const float az = __fmul_rn(__fsub_rn(v.p.z, r.o.z), r.inv.z);
-    T.b = mk3(v.scale.x * r.inv.x, v.scale.y * r.inv.y, v.scale.z * r.inv.z);
-    const float ex = 4e-7f * (fabsf(ax) + 255.0f * fabsf(T.b.x) + fabsf(v.p.x * r.inv.x));
-    const float ey = 4e-7f * (fabsf(ay) + 255.0f * fabsf(T.b.y) + fabsf(v.p.y * r.inv.y));
-    const float ez = 4e-7f * (fabsf(az) + 255.0f * fabsf(T.b.z) + fabsf(v.p.z * r.inv.z));
-    T.an = mk3(ax - ex, ay - ey, az - ez);
-    T.af = mk3(ax + ex, ay + ey, az + ez);
+    const float bx = v.scale.x * r.inv.x, by = v.scale.y * r.inv.y, bz = v.scale.z * r.inv.z;
+    T.B = mk3(bx * 32768.0f, by * 32768.0f, bz * 32768.0f);
+    const float ex = 4e-7f * (fabsf(ax) + 10240.0f * fabsf(bx) + fabsf(v.p.x * r.inv.x));
+    const float ey = 4e-7f * (fabsf(ay) + 10240.0f * fabsf(by) + fabsf(v.p.y * r.inv.y));
+    const float ez = 4e-7f * (fabsf(az) + 10240.0f * fabsf(bz) + fabsf(v.p.z * r.inv.z));
+    T.cn = mk3((ax - ex) - T.B.x, (ay - ey) - T.B.y, (az - ez) - T.B.z);
+    T.cf = mk3((ax + ex) - T.B.x, (ay + ey) - T.B.y, (az + ez) - T.B.z);
     const bool px = r.inv.x >= 0.0f, py = r.inv.y >= 0.0f, pz = r.inv.z >= 0.0f;
     // lo words: x (q0.x, q0.y), y (q0.z, q0.w), z (q1.x, q1.y); hi: x (q1.z, q1.w), y (q2.x, q2.y), z (q2.z, q2.w)
     T.nx0 = px ? v.q0.x : v.q1.z; T.nx1 = px ? v.q0.y : v.q1.w;
@@ -685,12 +694,12 @@ __device__ __forceinline__ void node_setup(const NodeView& v, const TravRay& r, 
 
 // entry distance of child slot i, or -1 if the ray misses its box within [0, tmax]
 __device__ __forceinline__ float child_test(const NodeTest& T, int i, float tmax) {
-    const float ex = fmaf(qbyte(T.nx0, T.nx1, i), T.b.x, T.an.x);
-    const float ey = fmaf(qbyte(T.ny0, T.ny1, i), T.b.y, T.an.y);
-    const float ez = fmaf(qbyte(T.nz0, T.nz1, i), T.b.z, T.an.z);
-    const float xx = fmaf(qbyte(T.fx0, T.fx1, i), T.b.x, T.af.x);
-    const float xy = fmaf(qbyte(T.fy0, T.fy1, i), T.b.y, T.af.y);
-    const float xz = fmaf(qbyte(T.fz0, T.fz1, i), T.b.z, T.af.z);
+    const float ex = fmaf(qbyte(T.nx0, T.nx1, i), T.B.x, T.cn.x);
+    const float ey = fmaf(qbyte(T.ny0, T.ny1, i), T.B.y, T.cn.y);
+    const float ez = fmaf(qbyte(T.nz0, T.nz1, i), T.B.z, T.cn.z);
+    const float xx = fmaf(qbyte(T.fx0, T.fx1, i), T.B.x, T.cf.x);
+    const float xy = fmaf(qbyte(T.fy0, T.fy1, i), T.B.y, T.cf.y);
+    const float xz = fmaf(qbyte(T.fz0, T.fz1, i), T.B.z, T.cf.z);
     const float tn = fmaxf(fmaxf(ex, ey), fmaxf(ez, 0.0f));
     const float tf = fminf(fminf(xx, xy), fminf(xz, tmax));
     return tn <= tf ? tn : -1.0f;

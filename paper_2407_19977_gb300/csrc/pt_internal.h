@@ -128,6 +128,7 @@ struct pt_scene {
     uint32_t collapse = PT_COLLAPSE_OPTIMAL;
     float tri_cost = 0.0f;           // 0: the default
     float box_cost = 0.0f;           // as passed (0: the default)
+    uint32_t max_width = 8;          // most children per wide node of the current BVH
     // schedule chosen by pt_autotune for frames of tuned_w x tuned_h (used by PT_MODE_AUTO)
     bool tuned = false;
     uint32_t tuned_w = 0, tuned_h = 0;
@@ -162,7 +163,7 @@ struct pt_scene {
 
 // implemented in pt_bvh.cu
 pt_status pt_build_bvh_impl(pt_scene* s, uint32_t leaf_size, uint32_t builder, uint32_t collapse, float tri_cost,
-                            float box_cost, cudaStream_t st);
+                            float box_cost, uint32_t max_width, cudaStream_t st);
 pt_status pt_build_env_impl(pt_scene* s, cudaStream_t st);
 
 // implemented in pt_render.cu

@@ -80,22 +80,35 @@ extern "C" pt_status pt_autotune(pt_scene* s, const pt_camera* camera, uint32_t 
     base.mode = PT_MODE_WAVEFRONT;
     base.sort_by_material = -1;
     base.use_graph = 1;
-    // BVH builder and leaf size first (one default schedule), then the schedule on the chosen tree
+    // BVH builder and leaf size first, then the width on that tree (one default schedule), then
+    // the schedule on the chosen tree
     if (tune_flags & PT_TUNE_BVH) {
-        pt_bvh_opts best_bo{s->leaf_size, s->builder, s->collapse, s->tri_cost, s->box_cost};
+        pt_bvh_opts best_bo{s->leaf_size, s->builder, s->collapse, s->tri_cost, s->box_cost, s->max_width};
         float best_t = 3.4e38f;
+        auto try_tree = [&](const pt_bvh_opts& bo) {
+            pt_status r = pt_bvh_build(s, &bo, cuda_stream);
+            if (r != PT_OK) return r;
+            float t = 0.0f;
+            r = run(base, &t);
+            if (r != PT_OK) return r;
+            if (t < best_t) { best_t = t; best_bo = bo; }
+            return PT_OK;
+        };
         for (uint32_t builder : {(uint32_t)PT_BVH_PLOC, (uint32_t)PT_BVH_LBVH})
             for (uint32_t leaf = 1; leaf <= 4; ++leaf) {
-                pt_bvh_opts bo{leaf, builder, s->collapse, s->tri_cost, s->box_cost};
-                pt_status r = pt_bvh_build(s, &bo, cuda_stream);
+                const pt_status r = try_tree(pt_bvh_opts{leaf, builder, s->collapse, s->tri_cost, s->box_cost, 8u});
                 if (r != PT_OK) return r;
-                float t = 0.0f;
-                r = run(base, &t);
-                if (r != PT_OK) return r;
-                if (t < best_t) { best_t = t; best_bo = bo; }
             }
-        if (s->leaf_size != best_bo.leaf_size || s->builder != best_bo.builder) {   // same collapse rule
-            pt_status r = pt_bvh_build(s, &best_bo, cuda_stream);
+        const pt_bvh_opts tree8 = best_bo;
+        for (uint32_t width : {4u, 6u}) {
+            pt_bvh_opts bo = tree8;
+            bo.max_width = width;
+            const pt_status r = try_tree(bo);
+            if (r != PT_OK) return r;
+        }
+        // the last tree tried is 6 wide: rebuild the winner (same collapse rule and costs)
+        if (best_bo.max_width != 6u) {
+            const pt_status r = pt_bvh_build(s, &best_bo, cuda_stream);
             if (r != PT_OK) return r;
         }
     }
@@ -153,9 +166,10 @@ extern "C" pt_status pt_autotune(pt_scene* s, const pt_camera* camera, uint32_t 
     return PT_OK;
 }
 
-extern "C" pt_status pt_autotune_batch(const pt_job* jobs, uint32_t n_jobs, uint32_t frames, pt_batch_opts* best,
-                                       float* best_ms, void* cuda_stream) {
+extern "C" pt_status pt_autotune_batch(const pt_job* jobs, uint32_t n_jobs, uint32_t frames, uint32_t tune_flags,
+                                       pt_batch_opts* best, float* best_ms, void* cuda_stream) {
     PT_CHECK_ARG((jobs || n_jobs == 0) && best, "NULL argument");
+    PT_CHECK_ARG((tune_flags & ~PT_TUNE_BVH) == 0, "unknown tune flags");
     std::memset(best, 0, sizeof(*best));
     if (n_jobs == 0) return PT_OK;
     if (frames == 0) frames = 2;
@@ -209,11 +223,50 @@ extern "C" pt_status pt_autotune_batch(const pt_job* jobs, uint32_t n_jobs, uint
         o.use_graph = 1;
         cand.push_back(o);
     }
+    auto time_batch = [&](const pt_batch_opts& o, float* t) {
+        for (auto& a : accs) a.spp_done = 0;
+        return time_frames([&]() { return pt_render_batch(tj.data(), n_jobs, &o, cuda_stream); }, frames, st, t);
+    };
+    // BVH width first: every scene of the batch rebuilt at 4, 6 and 8 children per node (each
+    // keeps its own builder, leaf size and collapse rule), timed with one merged wavefront
+    if (tune_flags & PT_TUNE_BVH) {
+        std::vector<pt_scene*> scenes;
+        for (uint32_t i = 0; i < n_jobs; ++i) {
+            PT_CHECK_ARG(jobs[i].scene != nullptr && jobs[i].scene->built, "job scene is NULL or not built");
+            if (std::find(scenes.begin(), scenes.end(), jobs[i].scene) == scenes.end()) scenes.push_back(jobs[i].scene);
+        }
+        auto rebuild = [&](uint32_t width) {
+            for (pt_scene* sc : scenes) {
+                pt_bvh_opts bo{sc->leaf_size, sc->builder, sc->collapse, sc->tri_cost, sc->box_cost, width};
+                const pt_status r = pt_bvh_build(sc, &bo, cuda_stream);
+                if (r != PT_OK) return r;
+            }
+            return PT_OK;
+        };
+        pt_batch_opts probe;
+        std::memset(&probe, 0, sizeof(probe));
+        probe.mode = PT_MODE_WAVEFRONT;
+        probe.merged = 1;
+        probe.wave_paths = 1u << 23;
+        probe.use_graph = 1;
+        uint32_t best_w = 8;
+        float best_t = 3.4e38f;
+        for (uint32_t width : {8u, 6u, 4u}) {
+            pt_status r = rebuild(width);
+            if (r != PT_OK) return r;
+            float t = 0.0f;
+            r = time_batch(probe, &t);
+            if (r != PT_OK) return r;
+            if (t < best_t) { best_t = t; best_w = width; }
+        }
+        if (best_w != 4u) {
+            const pt_status r = rebuild(best_w);
+            if (r != PT_OK) return r;
+        }
+    }
     for (const pt_batch_opts& o : cand) {
         float t = 0.0f;
-        for (auto& a : accs) a.spp_done = 0;
-        const pt_status r = time_frames([&]() { return pt_render_batch(tj.data(), n_jobs, &o, cuda_stream); }, frames,
-                                        st, &t);
+        const pt_status r = time_batch(o, &t);
         if (r != PT_OK) return r;
         if (t < win_t) { win_t = t; win = o; }
     }

@@ -53,7 +53,7 @@ class pt_render_opts(C.Structure):
 
 class pt_bvh_opts(C.Structure):
     _fields_ = [("leaf_size", u32), ("builder", u32), ("collapse", u32), ("tri_cost", C.c_float),
-                ("box_cost", C.c_float)]
+                ("box_cost", C.c_float), ("max_width", u32)]
 
 
 class pt_stats(C.Structure):
@@ -62,10 +62,10 @@ class pt_stats(C.Structure):
                 ("bvh_depth", u64), ("n_triangles", u64), ("trace_nodes", u64), ("trace_tris", u64),
                 ("shadow_nodes", u64), ("shadow_tris", u64), ("tail_ext_rays", u64), ("tail_shadow_rays", u64),
                 ("tail_trace_nodes", u64), ("tail_trace_tris", u64), ("tail_shadow_nodes", u64),
-                ("tail_shadow_tris", u64), ("graph_replays", u64), ("error_flags", u32), ("reserved", u32)]
+                ("tail_shadow_tris", u64), ("graph_replays", u64), ("error_flags", u32), ("bvh_width", u32)]
 
     def as_dict(self):
-        return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
 class pt_job(C.Structure):
@@ -115,7 +115,8 @@ SIGNATURES = {
     "pt_denoise_bmfr": (C.c_int, [vp, vp, u32, u32, u32, u32, u32, vp, vp]),
     "pt_autotune": (C.c_int, [vp, C.POINTER(pt_camera), u32, u32, u32, u32, C.POINTER(pt_render_opts),
                               C.POINTER(f32), vp]),
-    "pt_autotune_batch": (C.c_int, [C.POINTER(pt_job), u32, u32, C.POINTER(pt_batch_opts), C.POINTER(f32), vp]),
+    "pt_autotune_batch": (C.c_int, [C.POINTER(pt_job), u32, u32, u32, C.POINTER(pt_batch_opts), C.POINTER(f32),
+                                     vp]),
     "pt_trace": (C.c_int, [vp, vp, u32, C.c_int, vp, vp, vp, vp]),
     "pt_bsdf_eval": (C.c_int, [vp, vp, vp, vp, u32, vp, vp, vp]),
     "pt_bsdf_sample": (C.c_int, [vp, vp, vp, vp, u32, vp, vp, vp, vp, vp]),

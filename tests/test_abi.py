@@ -36,7 +36,7 @@ def test_status_strings_and_struct_sizes():
     assert C.sizeof(N.pt_quad_light) == 13 * 4
     assert C.sizeof(N.pt_camera) == 14 * 4
     assert C.sizeof(N.pt_accum) == 32
-    assert C.sizeof(N.pt_bvh_opts) == 20   # leaf_size, builder, collapse, tri_cost, box_cost
+    assert C.sizeof(N.pt_bvh_opts) == 24   # leaf_size, builder, collapse, tri_cost, box_cost, max_width
     assert (N.PT_BVH_LBVH, N.PT_BVH_PLOC, N.PT_COLLAPSE_OPTIMAL, N.PT_COLLAPSE_GREEDY) == (1, 2, 1, 2)
 
 

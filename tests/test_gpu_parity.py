@@ -972,8 +972,79 @@ def test_bvh_leaf_size_does_not_change_samples(api):
     assert g.stats()["error_flags"] == 0
 
 
+def test_bvh_width_limits_children_and_keeps_hits(api):
+    """pt_bvh_opts.max_width W: under both collapse rules and both builders every node of the
+    exported tree has at most W children and the tree is sound; closest hits (triangle, t,
+    barycentrics), any hits and rendered samples equal those of the 8-wide tree bit for bit,
+    since a closest hit (equal t -> lower id) does not depend on the tree."""
+    from paper_2407_19977_gb300 import api as A
+    from paper_2407_19977_gb300 import bvh_check
+    from paper_2407_19977_gb300 import native as N
+    sc = scenes.pushbutton_lod(20000, width=96, height=64, seed=2)
+    g = A.Scene(sc, build=False)
+    osc = oracle.OracleScene(sc)
+    o, d = _camera_and_bounce_rays(sc, osc, 20001, 21)
+    ot = torch.from_numpy(o.astype(np.float32)).cuda()
+    dt = torch.from_numpy(d.astype(np.float32)).cuda()
+    ref = None
+    for builder in (N.PT_BVH_PLOC, N.PT_BVH_LBVH):
+        for collapse in (N.PT_COLLAPSE_OPTIMAL, N.PT_COLLAPSE_GREEDY):
+            for width in (8, 2, 3, 4, 6):
+                g.build(builder=builder, collapse=collapse, max_width=width)
+                assert g.stats()["bvh_width"] == width
+                nodes, tris = g.export_bvh()
+                problems, stats = bvh_check.check(nodes, tris)
+                assert problems == [], (builder, collapse, width, problems)
+                assert stats["max_children"] <= width, (builder, collapse, width, stats)
+                if width == 8:
+                    assert stats["max_children"] > 4, stats
+                smp = torch.zeros((64, 96, 2, 3), dtype=torch.float32, device="cuda")
+                g.render(2, accum=A.Accum(96, 64), mode=N.PT_MODE_WAVEFRONT, sample_out=smp, seed=3)
+                got = (g.trace(ot, dt), g.trace(ot, dt, any_hit=True, tmax=0.7)[0], smp)
+                torch.cuda.synchronize()
+                if ref is None:
+                    ref = got
+                for x, y in zip(ref[0], got[0]):
+                    assert torch.equal(x, y), (builder, collapse, width)
+                assert torch.equal(ref[1], got[1]) and torch.equal(ref[2], got[2]), (builder, collapse, width)
+                print(f"\nwidth {width} builder {builder} collapse {collapse}: {stats['n_nodes']} nodes, "
+                      f"{stats['mean_children']:.2f} children, depth {stats['depth']}")
+    assert g.stats()["error_flags"] == 0
+
+
+def test_autotune_batch_chooses_a_bvh_width(api):
+    """With PT_TUNE_BVH the batch autotuner rebuilds every scene of the jobs at widths 8, 6 and
+    4 and leaves them built at the fastest one; the chosen schedule then renders what each job
+    rendered alone on its 8-wide tree."""
+    from paper_2407_19977_gb300 import api as A
+    mk, gs = _batch_scenes()
+    refs = []
+    for s, g in zip(mk, gs):
+        one = A.Accum(s.camera.width, s.camera.height)
+        g.render(2, max_depth=5, seed=9, accum=one, mode=1)
+        refs.append(one)
+    accs = [A.Accum(s.camera.width, s.camera.height) for s in mk]
+    jobs = [(g, s.camera, 2, 5, 9, a) for s, g, a in zip(mk, gs, accs)]
+    try:
+        best, ms = A.autotune_batch(jobs, frames=1, bvh=True)
+        torch.cuda.synchronize()
+        widths = {g.stats()["bvh_width"] for g in gs}
+        assert len(widths) == 1 and widths <= {4, 6, 8}, widths
+        assert ms > 0 and all(a.spp_done == 0 for a in accs)
+        A.render_batch(jobs, tile_pixels=best["tile_pixels"], blocks_per_sm=best["blocks_per_sm"],
+                       use_graph=bool(best["use_graph"]), mode=best["mode"], streams=best["streams"],
+                       merged=bool(best["merged"]), wave_paths=best["wave_paths"])
+        torch.cuda.synchronize()
+        for a, r in zip(accs, refs):
+            assert torch.equal(a.sum, r.sum) and torch.equal(a.comp, r.comp), (best, widths)
+    finally:
+        for g in gs:
+            g.build()
+    assert all(g.stats()["error_flags"] == 0 for g in gs)
+
+
 def test_autotune_and_auto_mode(api):
-    """pt_autotune picks a schedule (BVH leaf size included); PT_MODE_AUTO then renders with
+    """pt_autotune picks a schedule (BVH builder, leaf size and width included); PT_MODE_AUTO then renders with
     it, and the image is what the explicit schedule renders and what the oracle renders."""
     from paper_2407_19977_gb300 import api as A
     from paper_2407_19977_gb300 import native as N
@@ -1029,7 +1100,7 @@ def test_edge_cases(api):
         A.Scene(nan, on_device=True)
     # BVH options out of range; the scene keeps its tree
     for kw in ({"leaf_size": 5}, {"builder": 3}, {"collapse": 3}, {"tri_cost": -1.0},
-               {"tri_cost": float("inf")}, {"box_cost": float("nan")}):
+               {"tri_cost": float("inf")}, {"box_cost": float("nan")}, {"max_width": 1}, {"max_width": 9}):
         with pytest.raises(N.PtError, match="INVALID_ARG"):
             g.build(**kw)
     g.render(1, accum=A.Accum(37, 23))

@@ -51,9 +51,10 @@ TRI_BYTES = 48       # triangle record
 RAY_BYTES = 32       # ray in (origin + direction float4 pair)
 HIT_BYTES = 16       # hit record out
 # algorithmic FP32 operations of the traversal: one child box test = 6 decode FMA + 6 sub +
-# 6 mul + 12 min/max + 1 compare ~ 30; a node tests its 8 slots; one watertight triangle test
-# ~ 50 (9 sub, 12 shear, 9 edge products/differences, sign tests, det, T, divide, range)
-OPS_PER_NODE = 8 * 30
+# 6 mul + 12 min/max + 1 compare ~ 30, counted for each filled child slot of a visited node
+# (the counting traversal reports those box tests); one watertight triangle test ~ 50 (9 sub,
+# 12 shear, 9 edge products/differences, sign tests, det, T, divide, range)
+OPS_PER_BOX = 30
 OPS_PER_TRI = 50
 # FP32 lane peak: SMs (read from the device) x 128 FP32 lanes x the maximum SM clock (an FMA
 # counted as one operation); 2.07 GHz is the GB300's maximum SM clock, MEASURED_PEAKS.json's
@@ -441,12 +442,12 @@ def run_ours(args, world, rank, local):
     scene.render(args.spp_per_step, seed=seed, accum=probe, mode=mode, flags=N.PT_FLAG_COUNT)
     after = scene.stats()
     cnt = {k: after[k] - before[k] for k in ("ext_rays", "shadow_rays", "trace_nodes", "trace_tris",
-                                             "shadow_nodes", "shadow_tris", "tail_ext_rays")}
+                                             "trace_boxes", "shadow_nodes", "shadow_tris", "tail_ext_rays")}
     # rays the per-bounce closest-hit kernel traced (the tail kernel counts its own)
     cnt["trace_rays"] = cnt["ext_rays"] - cnt["tail_ext_rays"]
     trace_bytes_step = (cnt["trace_nodes"] * NODE_BYTES + cnt["trace_tris"] * TRI_BYTES +
                         cnt["trace_rays"] * (RAY_BYTES + HIT_BYTES))
-    trace_ops_step = cnt["trace_nodes"] * OPS_PER_NODE + cnt["trace_tris"] * OPS_PER_TRI
+    trace_ops_step = cnt["trace_boxes"] * OPS_PER_BOX + cnt["trace_tris"] * OPS_PER_TRI
     # timed region
     kernel_ms = (N.f32 * len(N.KERNEL_KINDS))()
     kernel_launches = (N.u32 * len(N.KERNEL_KINDS))()
@@ -562,8 +563,10 @@ def run_ours(args, world, rank, local):
                      "algorithmic_ops_per_launch": trace_ops_step / trace_launches,
                      "launch_ms": trace_ms / trace_launches,
                      "per_ray": {"nodes": cnt["trace_nodes"] / max(cnt["trace_rays"], 1),
+                                 "box_tests": cnt["trace_boxes"] / max(cnt["trace_rays"], 1),
                                  "tris": cnt["trace_tris"] / max(cnt["trace_rays"], 1),
-                                 "rays_per_step": cnt["trace_rays"]},
+                                 "rays_per_step": cnt["trace_rays"],
+                                 "ops": f"{OPS_PER_BOX} per child box test, {OPS_PER_TRI} per triangle test"},
                      "hbm_view": {"algorithmic_bytes_per_step": trace_bytes_step, "achieved_gbs": achieved_gbs,
                                   "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src}},
         "clocks": clocks.summary(),

@@ -294,6 +294,12 @@ typedef struct {
     uint32_t error_flags;       /* sticky device error bits (1 = stack overflow, 2 = timeout) */
     uint32_t bvh_width;         /* most children a node of the current BVH may have
                                    (pt_bvh_opts.max_width as built; 0 before the first build) */
+    /* PT_FLAG_COUNT: child box tests (filled child slots of the nodes visited) of closest-hit
+       and shadow rays in the per-bounce kernels, and in the tail kernel */
+    uint64_t trace_boxes;
+    uint64_t shadow_boxes;
+    uint64_t tail_trace_boxes;
+    uint64_t tail_shadow_boxes;
 } pt_stats;
 
 /* Scene setup (Sec. 5.1.1 "CPU setup": load geometry and materials).

@@ -398,6 +398,10 @@ extern "C" pt_status pt_get_stats(pt_scene* s, pt_stats* out) {
     out->tail_shadow_tris = st[ST_TAIL_SH_TRIS];
     out->graph_replays = s->graph_replays;
     out->error_flags = err;
+    out->trace_boxes = st[ST_BOXES];
+    out->shadow_boxes = st[ST_SH_BOXES];
+    out->tail_trace_boxes = st[ST_TAIL_BOXES];
+    out->tail_shadow_boxes = st[ST_TAIL_SH_BOXES];
     if (err & 2u) { pt_set_error("device wait ran out of its spin budget"); return PT_ERR_TIMEOUT; }
     if (err & 1u) { pt_set_error("traversal stack or work queue overflow"); return PT_ERR_QUEUE_OVERFLOW; }
     if (err & 4u) { pt_set_error("BVH traversal exceeded its node budget (malformed tree)"); return PT_ERR_CUDA; }
@@ -429,7 +433,7 @@ __global__ void k_trace(DScene S, const float* rays, uint32_t n, int flags, uint
     const float* r = rays + 8u * i;
     const float3 o = mk3(r[0], r[1], r[2]), d = mk3(r[3], r[4], r[5]);
     const float tmax = r[6];
-    TravCount tc = {0, 0};
+    TravCount tc = {0, 0, 0};
     if (flags & PT_TRACE_ANY) {
         const bool occ = (flags & PT_TRACE_COUNT) ? trace_any_t<true>(S, o, d, tmax, tc) : trace_any(S, o, d, tmax);
         tri[i] = occ ? 0u : PT_NO_HIT;
@@ -467,7 +471,7 @@ __global__ void __launch_bounds__(128) k_trace_coop(DScene S, const float* rays,
     const float3 o = mk3(r[0], r[1], r[2]), d = mk3(r[3], r[4], r[5]);
     const float tmax = r[6];
     const bool count = (flags & PT_TRACE_COUNT) != 0;
-    TravCount tc = {0, 0};
+    TravCount tc = {0, 0, 0};
     if (flags & PT_TRACE_ANY) {
         CoopAny st;
         coop_any_init(S, o, d, tmax, st);

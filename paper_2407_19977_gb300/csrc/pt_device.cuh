@@ -712,8 +712,13 @@ struct HitRec {
 
 // Node visits and triangle tests of one traversal (counting variant only).
 struct TravCount {
-    uint32_t nodes, tris;
+    uint32_t nodes, tris, boxes;   // node visits, triangle tests, child box tests (filled slots)
 };
+
+// child slots of a node that hold a child (nonzero meta bytes): the box tests of one visit
+__device__ __forceinline__ uint32_t node_slots(const NodeView& v) {
+    return (uint32_t)(__popc(__vcmpne4(v.meta_lo, 0u)) + __popc(__vcmpne4(v.meta_hi, 0u))) >> 3;
+}
 
 // Closest-hit traversal as a state machine: closest_init sets up one ray, closest_step
 // processes one node (eight unrolled box tests; the nearest internal child is descended
@@ -752,7 +757,7 @@ __device__ __forceinline__ bool closest_step(const DScene& S, ClosestState& st, 
     if (S.n_nodes == 0) return true;
     if (st.budget-- == 0u) { atomicOr(S.err, 4u); st.h.tri = PT_NO_HIT; return true; }
     const NodeView v = load_node(S.nodes, st.node);
-    if (COUNT) tc.nodes++;
+    if (COUNT) { tc.nodes++; tc.boxes += node_slots(v); }
     NodeTest T;
     node_setup(v, st.tr, T);
     uint32_t leafmask = 0u;
@@ -848,7 +853,7 @@ __device__ __forceinline__ bool any_step(const DScene& S, AnyState& st, uint32_t
     if (S.n_nodes == 0) return true;
     if (st.budget-- == 0u) { atomicOr(S.err, 4u); return true; }
     const NodeView v = load_node(S.nodes, st.node);
-    if (COUNT) tc.nodes++;
+    if (COUNT) { tc.nodes++; tc.boxes += node_slots(v); }
     NodeTest T;
     node_setup(v, st.tr, T);
     uint32_t leafmask = 0u;
@@ -1000,7 +1005,7 @@ __device__ __forceinline__ bool coop_closest_step(const DScene& S, CoopClosest& 
         return true;
     }
     const NodeView v = load_node(S.nodes, st.node);
-    if (COUNT && gl == 0) tc.nodes++;
+    if (COUNT && gl == 0) { tc.nodes++; tc.boxes += node_slots(v); }
     uint32_t meta, ib, lb;
     const float tn = coop_node_test(v, st.tr, st.hit_t, gl, gm, gbase, meta, ib, lb);
     const bool ih = (ib >> gl) & 1u;
@@ -1118,7 +1123,7 @@ __device__ __forceinline__ bool coop_any_step(const DScene& S, CoopAny& st, Coop
         return true;
     }
     const NodeView v = load_node(S.nodes, st.node);
-    if (COUNT && gl == 0) tc.nodes++;
+    if (COUNT && gl == 0) { tc.nodes++; tc.boxes += node_slots(v); }
     uint32_t meta, ib, lb;
     coop_node_test(v, st.tr, st.tmax, gl, gm, gbase, meta, ib, lb);
     const uint32_t n_int = __popc(ib);

@@ -46,7 +46,8 @@ int pt_num_sms();
 // ---- device statistics slots -----------------------------------------------------------
 enum { ST_EXT = 0, ST_SHADOW = 1, ST_PATHS = 2, ST_NAN = 3, ST_RR = 4, ST_NRC = 5, ST_NODES = 6, ST_TRIS = 7,
        ST_SH_NODES = 8, ST_SH_TRIS = 9, ST_TAIL_EXT = 10, ST_TAIL_SH = 11, ST_TAIL_NODES = 12, ST_TAIL_TRIS = 13,
-       ST_TAIL_SH_NODES = 14, ST_TAIL_SH_TRIS = 15, ST_COUNT = 16 };
+       ST_TAIL_SH_NODES = 14, ST_TAIL_SH_TRIS = 15, ST_BOXES = 16, ST_SH_BOXES = 17, ST_TAIL_BOXES = 18,
+       ST_TAIL_SH_BOXES = 19, ST_COUNT = 20 };
 
 // ---- wavefront workspace ---------------------------------------------------------------
 struct WaveBuffers {

@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(128) k_wf_trace(WfParams P, int in_q) {
     const uint32_t count = P.counters[in_q];
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&P.stats[ST_EXT], (unsigned long long)count);
     const uint32_t lane = lane_id();
-    TravCount tc = {0, 0};
+    TravCount tc = {0, 0, 0};
     for (;;) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&P.counters[C_HEAD_TRACE], 32u);
@@ -593,8 +593,10 @@ __global__ void __launch_bounds__(128) k_wf_trace(WfParams P, int in_q) {
         }
     }
     if (COUNT) {
-        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris);
+        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris),
+                                 nb = warp_sum_u64(tc.boxes);
         if (lane == 0) {
+            atomicAdd(&P.stats[ST_BOXES], nb);
             atomicAdd(&P.stats[ST_NODES], nn);
             atomicAdd(&P.stats[ST_TRIS], nt);
         }
@@ -900,7 +902,7 @@ __global__ void __launch_bounds__(128) k_wf_shadow(WfParams P) {
     const uint32_t count = P.counters[C_SH];
     if (blockIdx.x == 0 && threadIdx.x == 0 && count) atomicAdd(&P.stats[ST_SHADOW], (unsigned long long)count);
     const uint32_t lane = lane_id();
-    TravCount tc = {0, 0};
+    TravCount tc = {0, 0, 0};
     for (;;) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&P.counters[C_HEAD_SHADOW], 32u);
@@ -927,8 +929,10 @@ __global__ void __launch_bounds__(128) k_wf_shadow(WfParams P) {
         }
     }
     if (COUNT) {
-        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris);
+        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris),
+                                 nb = warp_sum_u64(tc.boxes);
         if (lane == 0) {
+            atomicAdd(&P.stats[ST_SH_BOXES], nb);
             atomicAdd(&P.stats[ST_SH_NODES], nn);
             atomicAdd(&P.stats[ST_SH_TRIS], nt);
         }
@@ -979,7 +983,7 @@ __global__ void __launch_bounds__(128) k_wf_trace_coop(WfParams P, int in_q) {
     const uint32_t lane = lane_id(), gl = lane & (COOP_W - 1u), gbase = lane & ~(COOP_W - 1u);
     const uint32_t gm = 0xffu << gbase;
     CoopShared& sh = gsh[threadIdx.x / COOP_W];
-    TravCount tc = {0, 0};
+    TravCount tc = {0, 0, 0};
     CoopClosest st;
     uint32_t slot = 0, wb = 0, we = 0;
     bool active = false, drained = false;
@@ -1007,8 +1011,10 @@ __global__ void __launch_bounds__(128) k_wf_trace_coop(WfParams P, int in_q) {
         }
     }
     if (COUNT) {
-        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris);
+        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris),
+                                 nb = warp_sum_u64(tc.boxes);
         if (lane == 0) {
+            atomicAdd(&P.stats[ST_BOXES], nb);
             atomicAdd(&P.stats[ST_NODES], nn);
             atomicAdd(&P.stats[ST_TRIS], nt);
         }
@@ -1028,7 +1034,7 @@ __global__ void __launch_bounds__(128) k_wf_shadow_coop(WfParams P) {
     const uint32_t lane = lane_id(), gl = lane & (COOP_W - 1u), gbase = lane & ~(COOP_W - 1u);
     const uint32_t gm = 0xffu << gbase;
     CoopShared& sh = gsh[threadIdx.x / COOP_W];
-    TravCount tc = {0, 0};
+    TravCount tc = {0, 0, 0};
     CoopAny st;
     uint32_t slot = 0, wb = 0, we = 0;
     bool active = false, drained = false;
@@ -1054,8 +1060,10 @@ __global__ void __launch_bounds__(128) k_wf_shadow_coop(WfParams P) {
         }
     }
     if (COUNT) {
-        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris);
+        const unsigned long long nn = warp_sum_u64(tc.nodes), nt = warp_sum_u64(tc.tris),
+                                 nb = warp_sum_u64(tc.boxes);
         if (lane == 0) {
+            atomicAdd(&P.stats[ST_SH_BOXES], nb);
             atomicAdd(&P.stats[ST_SH_NODES], nn);
             atomicAdd(&P.stats[ST_SH_TRIS], nt);
         }
@@ -1077,7 +1085,7 @@ __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32
     const uint32_t sbase = wf_sample_base(P);
     const uint64_t seed = wf_seed(P);
     unsigned long long n_ext = 0, n_sh = 0, n_rr = 0;
-    TravCount tc = {0, 0}, sc = {0, 0};
+    TravCount tc = {0, 0, 0}, sc = {0, 0, 0};
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         const float4 ro = P.ray_o[in_q][i], rd = P.ray_d[in_q][i];
         const uint32_t id = __float_as_uint(rd.w);
@@ -1148,8 +1156,11 @@ __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32
     }
     if (COUNT) {
         const unsigned long long a = warp_sum_u64(tc.nodes), b = warp_sum_u64(tc.tris),
-                                 c = warp_sum_u64(sc.nodes), e = warp_sum_u64(sc.tris);
+                                 c = warp_sum_u64(sc.nodes), e = warp_sum_u64(sc.tris),
+                                 f = warp_sum_u64(tc.boxes), g = warp_sum_u64(sc.boxes);
         if (lane_id() == 0) {
+            atomicAdd(&P.stats[ST_TAIL_BOXES], f);
+            atomicAdd(&P.stats[ST_TAIL_SH_BOXES], g);
             atomicAdd(&P.stats[ST_TAIL_NODES], a);
             atomicAdd(&P.stats[ST_TAIL_TRIS], b);
             atomicAdd(&P.stats[ST_TAIL_SH_NODES], c);

@@ -62,7 +62,8 @@ class pt_stats(C.Structure):
                 ("bvh_depth", u64), ("n_triangles", u64), ("trace_nodes", u64), ("trace_tris", u64),
                 ("shadow_nodes", u64), ("shadow_tris", u64), ("tail_ext_rays", u64), ("tail_shadow_rays", u64),
                 ("tail_trace_nodes", u64), ("tail_trace_tris", u64), ("tail_shadow_nodes", u64),
-                ("tail_shadow_tris", u64), ("graph_replays", u64), ("error_flags", u32), ("bvh_width", u32)]
+                ("tail_shadow_tris", u64), ("graph_replays", u64), ("error_flags", u32), ("bvh_width", u32),
+                ("trace_boxes", u64), ("shadow_boxes", u64), ("tail_trace_boxes", u64), ("tail_shadow_boxes", u64)]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}

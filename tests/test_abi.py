@@ -37,6 +37,7 @@ def test_status_strings_and_struct_sizes():
     assert C.sizeof(N.pt_camera) == 14 * 4
     assert C.sizeof(N.pt_accum) == 32
     assert C.sizeof(N.pt_bvh_opts) == 24   # leaf_size, builder, collapse, tri_cost, box_cost, max_width
+    assert C.sizeof(N.pt_stats) == 26 * 8   # 21 counters, error_flags + bvh_width, 4 box-test counters
     assert (N.PT_BVH_LBVH, N.PT_BVH_PLOC, N.PT_COLLAPSE_OPTIMAL, N.PT_COLLAPSE_GREEDY) == (1, 2, 1, 2)
 
 

@@ -763,6 +763,9 @@ def test_tail_kernel_ray_counts(api):
     assert off["rr_terminated"] == on["rr_terminated"] and off["paths"] == on["paths"]
     assert off["tail_ext_rays"] == 0 and on["tail_ext_rays"] > 0 and on["tail_shadow_rays"] > 0
     assert off["trace_nodes"] == on["trace_nodes"] + on["tail_trace_nodes"]
+    assert off["trace_boxes"] == on["trace_boxes"] + on["tail_trace_boxes"]
+    assert off["shadow_boxes"] == on["shadow_boxes"] + on["tail_shadow_boxes"]
+    assert on["trace_nodes"] < on["trace_boxes"] <= 8 * on["trace_nodes"]
     assert off["trace_tris"] == on["trace_tris"] + on["tail_trace_tris"]
     assert off["shadow_nodes"] == on["shadow_nodes"] + on["tail_shadow_nodes"]
     assert off["shadow_tris"] == on["shadow_tris"] + on["tail_shadow_tris"]
@@ -999,7 +1002,14 @@ def test_bvh_width_limits_children_and_keeps_hits(api):
                 if width == 8:
                     assert stats["max_children"] > 4, stats
                 smp = torch.zeros((64, 96, 2, 3), dtype=torch.float32, device="cuda")
-                g.render(2, accum=A.Accum(96, 64), mode=N.PT_MODE_WAVEFRONT, sample_out=smp, seed=3)
+                b = g.stats()
+                g.render(2, accum=A.Accum(96, 64), mode=N.PT_MODE_WAVEFRONT, sample_out=smp, seed=3,
+                         flags=N.PT_FLAG_COUNT)
+                a = g.stats()
+                # a visit tests the node's filled slots: at most `width` of them
+                for kind in ("trace", "shadow", "tail_trace", "tail_shadow"):
+                    nodes, boxes = a[f"{kind}_nodes"] - b[f"{kind}_nodes"], a[f"{kind}_boxes"] - b[f"{kind}_boxes"]
+                    assert nodes <= boxes <= width * nodes, (kind, width, nodes, boxes)
                 got = (g.trace(ot, dt), g.trace(ot, dt, any_hit=True, tmax=0.7)[0], smp)
                 torch.cuda.synchronize()
                 if ref is None:

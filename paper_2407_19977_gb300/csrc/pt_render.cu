@@ -1118,7 +1118,7 @@ __global__ void __launch_bounds__(128, 4) k_wf_tail(WfParams P, int in_q, uint32
         float3 o = xyz(ro), d = xyz(rd);
         for (uint32_t k = k0;; ++k) {
             HitRec h;
-            if (COUNT) trace_closest_t<true>(S, o, d, __int_as_float(0x7f800000), h, tc);
+            if (COUNT) trace_closest_t<true, true>(S, o, d, __int_as_float(0x7f800000), h, tc);
             else trace_closest(S, o, d, __int_as_float(0x7f800000), h);
             n_ext++;
             rng.k = k;

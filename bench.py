@@ -149,25 +149,45 @@ def _source_hash():
     return h.hexdigest()[:16]
 
 
-def _recorded_traffic(kernel: str, workload: str, spp_per_step: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
-    current kernel source (the summary records the source hash) and on this launch shape (the
-    workload and the samples per step, which set the wave size); else None."""
+def _recorded_profile(kernel: str, workload: str, spp_per_step: int):
+    """The committed ncu record of `kernel` (`profiles/<kernel>_traffic.txt`) as a dict, if it
+    was taken on the current kernel source (the record holds the source hash) and on this
+    launch shape (the workload and the samples per step, which set the wave size); else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     if not os.path.exists(path):
         return None
     vals = {}
     with open(path) as f:
         for line in f:
-            if ":" in line:
+            if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
     if vals.get("source_hash") != _source_hash():
         return None
     if vals.get("workload") != workload or vals.get("spp_per_step") != str(spp_per_step):
         return None
+    return vals
+
+
+def _recorded_traffic(kernel: str, workload: str, spp_per_step: int):
+    """DRAM bytes per launch of `kernel` from its committed ncu record (see _recorded_profile)."""
+    vals = _recorded_profile(kernel, workload, spp_per_step)
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals["dram_bytes_per_launch"]) if vals else None
+    except (KeyError, ValueError):
+        return None
+
+
+def _recorded_issue(kernel: str, workload: str, spp_per_step: int):
+    """Instruction issue of `kernel` from the full ncu capture named in its record: the share of
+    issue slots used and the active lanes per warp instruction (None when the record does not
+    match the current source)."""
+    vals = _recorded_profile(kernel, workload, spp_per_step)
+    try:
+        return {"issue_slots_busy": float(vals["issue_slots_busy_pct"]) / 100.0,
+                "active_lanes_per_warp_instruction": float(vals["active_threads_per_inst"]),
+                "lane_fraction": float(vals["active_threads_per_inst"]) / 32.0,
+                "source": vals.get("issue_source", "ncu")} if vals else None
     except (KeyError, ValueError):
         return None
 
@@ -558,6 +578,7 @@ def run_ours(args, world, rank, local):
                      "achieved": achieved_gops, "peak": alu_peak, "unit": "GOP/s",
                      "frac": achieved_gops / alu_peak if achieved_gops else None,
                      "traffic": traffic,
+                     "issue_view": _recorded_issue("trace", args.workload, args.spp_per_step),
                      "peak_source": f"{sm_count} SMs (device query) x {FP32_LANES_PER_SM} FP32 lanes x "
                                     f"{sm_ghz:.2f} GHz maximum SM clock (recipe unit counts and clock)",
                      "algorithmic_ops_per_launch": trace_ops_step / trace_launches,

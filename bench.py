@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -79,9 +80,9 @@ def _args():
     ap.add_argument("--mode", default="wavefront", choices=["auto", "wavefront", "megakernel"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bvh-builder", default="ploc", choices=["ploc", "lbvh"],
-                    help="binary tree the 8-wide BVH is collapsed from: clustering (default) or radix tree")
+                    help="binary tree the wide BVH is collapsed from: clustering (default) or radix tree")
     ap.add_argument("--bvh-collapse", default="optimal", choices=["optimal", "greedy"],
-                    help="folding of the binary tree into 8-wide nodes: least surface-area cost or largest child first")
+                    help="folding of the binary tree into wide nodes: least surface-area cost or largest child first")
     ap.add_argument("--bvh-tri-cost", type=float, default=0.0,
                     help="cost of a triangle test against a wide node visit for the optimal collapse (0: default)")
     ap.add_argument("--bvh-box-cost", type=float, default=0.0,
@@ -141,11 +142,16 @@ def _metric_name(workload: str) -> str:
 
 
 def _source_hash():
+    """Hash of the traversal kernels' and the BVH builder's code with comments and blank lines
+    removed (a comment edit does not change what a recorded ncu capture measured)."""
     h = hashlib.sha256()
     for rel in ("paper_2407_19977_gb300/csrc/pt_device.cuh", "paper_2407_19977_gb300/csrc/pt_render.cu",
                 "paper_2407_19977_gb300/csrc/pt_bvh.cu"):
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("\n".join(line.rstrip() for line in src.splitlines() if line.strip()).encode())
     return h.hexdigest()[:16]
 
 

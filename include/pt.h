@@ -232,7 +232,7 @@ enum {
                                    more instructions per ray: slower on the CAD frames) */
 };
 
-/* Binary tree that the 8-wide BVH is collapsed from (Sec. 5.1.1 builds an AABB hierarchy on
+/* Binary tree that the wide BVH is collapsed from (Sec. 5.1.1 builds an AABB hierarchy on
  * the CPU; here both builders run on the device over the same 63-bit Morton order):
  *  PT_BVH_LBVH  Karras' radix tree over the Morton codes (fastest build, splits at the
  *               codes' highest differing bit whatever the triangles' sizes);
@@ -242,12 +242,12 @@ enum {
  *               default). */
 enum { PT_BVH_DEFAULT = 0, PT_BVH_LBVH = 1, PT_BVH_PLOC = 2 };
 
-/* How the binary tree is folded into 8-wide nodes:
+/* How the binary tree is folded into wide nodes (at most max_width children each):
  *  PT_COLLAPSE_OPTIMAL  the least surface-area cost (a wide node visit costs 1 plus box_cost
  *                       per child slot, a triangle test tri_cost, each weighted by area / root
  *                       area), found per binary node by a dynamic programme over the number of
  *                       slots its subtree fills (Ylitie, Karras, Laine, HPG 2017); the default;
- *  PT_COLLAPSE_GREEDY   open the child of largest area until 8 slots are used. */
+ *  PT_COLLAPSE_GREEDY   open the child of largest area until max_width slots are used. */
 enum { PT_COLLAPSE_DEFAULT = 0, PT_COLLAPSE_OPTIMAL = 1, PT_COLLAPSE_GREEDY = 2 };
 
 typedef struct {
@@ -321,7 +321,8 @@ pt_status pt_scene_create(const float* vertices, uint32_t n_vertices, const uint
                           void* cuda_stream, pt_scene** out);
 
 /* Device BVH build (Sec. 5.1.1: AABB hierarchy, O(log n) intersection): 64-bit Morton codes,
- * radix sort, linear BVH, collapse to a compressed 8-wide BVH with 8-bit child boxes.
+ * radix sort, linear BVH, collapse to a compressed wide BVH (80-byte nodes of 8 child slots,
+ * at most pt_bvh_opts.max_width of them used) with 8-bit child boxes.
  * Enqueued on cuda_stream; synchronises that stream once per wide-tree level.  Also
  * builds the environment sampling tables. */
 pt_status pt_bvh_build(pt_scene* scene, const pt_bvh_opts* opts, void* cuda_stream);

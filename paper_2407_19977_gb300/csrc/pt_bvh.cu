@@ -2,9 +2,9 @@
 //
 // 1. centroid bounds, 2. 63-bit Morton codes, 3. LSD radix sort (8 passes of 8 bits),
 // 4. binary radix tree over the sorted codes (Karras, HPG 2012), 5. bottom-up boxes,
-// 6. top-down collapse into an 8-wide BVH with 8-bit quantised child boxes (80-byte nodes;
-//    the layout of compressed wide BVHs, Ylitie, Karras, Laine, HPG 2017), whose leaf
-//    triangles are laid out contiguously per node.
+// 6. top-down collapse into a wide BVH with 8-bit quantised child boxes (80-byte nodes of 8
+//    child slots, at most max_width of them used; the layout of compressed wide BVHs, Ylitie,
+//    Karras, Laine, HPG 2017), whose leaf triangles are laid out contiguously per node.
 // The environment's sampling tables (marginal/conditional CDFs) are built here too.
 #include <vector>
 
@@ -508,7 +508,7 @@ __global__ void k_ploc_layout(uint32_t lo, uint32_t hi, uint32_t* left, uint32_t
     last[k] = f + count[k] - 1u;
 }
 
-// ------------------------------------------------------------------ collapse to 8-wide nodes
+// ------------------------------------------------------------------ collapse to wide nodes
 struct CollapseCtx {
     BinTree T;
     uint32_t leaf_size;

@@ -222,6 +222,12 @@ typedef struct {
                                    estimation) */
     uint32_t traversal;         /* wavefront closest-hit and shadow passes: PT_TRAVERSAL_* (the
                                    hits, and the node and triangle counts, are the same) */
+    uint32_t tail_bounce;       /* wavefront with a tail limit (tail_paths >= 0): 0 = the
+                                   per-bounce launches are issued for every bounce up to
+                                   max_depth (after the tail kernel has taken over they find
+                                   nothing to do); k > 0 = at bounce k the tail kernel takes every
+                                   path still running, however many, and no launch is issued for
+                                   the later bounces.  The samples are the same. */
 } pt_render_opts;
 
 enum {
@@ -415,7 +421,8 @@ pt_status pt_render_batch(const pt_job* jobs, uint32_t n_jobs, const pt_batch_op
  * height and times them with CUDA events on the stream; candidates: wavefront with material
  * sort off/on x tail limit (off, automatic, a quarter, four times) x wave size (2^20 .. 2^23
  * paths, as far as the call needs them), graph replay on; megakernel with 32, 64, 128 pixels
- * per work item; then the winner's traversal passes one ray per lane or per 8-lane group.  With
+ * per work item; then the winner's traversal passes one ray per lane or per 8-lane group, and a
+ * wavefront winner with a tail limit with tail_bounce 3, 4, 5 and 6.  With
  * PT_TUNE_BVH it first rebuilds the BVH with both builders and leaf sizes 1..4 at width 8, then
  * the fastest of those at widths 4 and 6 (pt_bvh_opts.max_width), and keeps the fastest tree.  The winner goes to *best (and ms per frame to
  * *best_ms) and is stored in the scene: pt_render with PT_MODE_AUTO then uses it for frames

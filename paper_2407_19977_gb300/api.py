@@ -131,7 +131,7 @@ class Scene:
     def render(self, spp, max_depth=None, seed=0, accum=None, camera=None, crop=None, flags=0,
                mode=N.PT_MODE_AUTO, wave_paths=0, sort=-1, sample_out=None, block_size=0, stream=None,
                kernel_ms=None, kernel_launches=None, nrc=None, nrc_train=False, tail_paths=0, use_graph=False,
-               restir=None, traversal=N.PT_TRAVERSAL_AUTO):
+               restir=None, traversal=N.PT_TRAVERSAL_AUTO, tail_bounce=0):
         cam = camera or self.desc.camera
         max_depth = self.desc.max_depth if max_depth is None else max_depth
         if crop is None:
@@ -145,6 +145,7 @@ class Scene:
         o.tail_paths = int(tail_paths)
         o.use_graph = 1 if use_graph else 0
         o.traversal = int(traversal)
+        o.tail_bounce = int(tail_bounce)
         if restir is not None:
             # (M candidates, K neighbours, radius R[, L later candidates]): ReSTIR DI at the
             # primary vertex, resampled next-event estimation at later vertices if L > 0
@@ -182,7 +183,8 @@ class Scene:
         ms = N.f32()
         N.call("pt_autotune", self.h, C.byref(make_camera(cam)), int(spp), int(max_depth), int(frames),
                N.PT_TUNE_BVH if bvh else 0, C.byref(best), C.byref(ms), _stream_handle(stream))
-        keys = ("mode", "wave_paths", "sort_by_material", "block_size", "tail_paths", "use_graph")
+        keys = ("mode", "wave_paths", "sort_by_material", "block_size", "tail_paths", "use_graph", "traversal",
+                "tail_bounce")
         return {k: int(getattr(best, k)) for k in keys}, float(ms.value)
 
     def trace(self, origins: torch.Tensor, dirs: torch.Tensor, tmax=None, any_hit=False, count=False,

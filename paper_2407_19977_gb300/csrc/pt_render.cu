@@ -304,6 +304,7 @@ struct WfParams {
     uint32_t spp_call;             // samples in the call
     uint32_t max_depth, flags;
     uint32_t n_keys;               // material sort buckets (0 = no sort)
+    uint32_t tail_bounce;          // host: bounce at which the tail kernel takes every path (0: none)
     float4* ray_o[2];
     float4* ray_d[2];
     float4* hit;
@@ -1441,6 +1442,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
     P.max_depth = max_depth;
     P.flags = o.flags;
     P.n_keys = n_keys;
+    P.tail_bounce = tail_limit ? o.tail_bounce : 0u;   // part of the graph key: it shapes the launches
     for (int q = 0; q < 2; ++q) { P.ray_o[q] = w.ray_o[q]; P.ray_d[q] = w.ray_d[q]; }
     P.hit = w.hit; P.beta = w.beta; P.radiance = w.radiance;
     P.sh_o = w.sh_o; P.sh_d = w.sh_d; P.sh_c = w.sh_c;
@@ -1542,20 +1544,24 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                     PT_LAUNCH(k_wf_setup, 1, 256, 0, st, w.counters, out_q, n_keys);
                     ++launches;
                     if (tail_limit && !(restir && k == 0)) {
+                        // at the forced bounce the tail kernel takes the paths whatever their number
+                        const bool force = P.tail_bounce != 0 && k == P.tail_bounce;
+                        const uint32_t lim = force ? 0xFFFFFFFFu : tail_limit;
                         e = begin(PT_K_TAIL);
                         const bool fz = s->has_fuzz;
                         if (P.nrc_on) {
-                            if (count) launch_tail<true, true, false>(fz, tail_grid, st, P, in_q, k, tail_limit);
-                            else launch_tail<true, false, false>(fz, tail_grid, st, P, in_q, k, tail_limit);
+                            if (count) launch_tail<true, true, false>(fz, tail_grid, st, P, in_q, k, lim);
+                            else launch_tail<true, false, false>(fz, tail_grid, st, P, in_q, k, lim);
                         } else if (restir) {
-                            if (count) launch_tail<false, true, true>(fz, tail_grid, st, P, in_q, k, tail_limit);
-                            else launch_tail<false, false, true>(fz, tail_grid, st, P, in_q, k, tail_limit);
+                            if (count) launch_tail<false, true, true>(fz, tail_grid, st, P, in_q, k, lim);
+                            else launch_tail<false, false, true>(fz, tail_grid, st, P, in_q, k, lim);
                         } else {
-                            if (count) launch_tail<false, true, false>(fz, tail_grid, st, P, in_q, k, tail_limit);
-                            else launch_tail<false, false, false>(fz, tail_grid, st, P, in_q, k, tail_limit);
+                            if (count) launch_tail<false, true, false>(fz, tail_grid, st, P, in_q, k, lim);
+                            else launch_tail<false, false, false>(fz, tail_grid, st, P, in_q, k, lim);
                         }
                         end(e);
                         ++launches;
+                        if (force) break;   // no path is left for the later bounces
                     }
                     e = begin(PT_K_TRACE);
                     if (count) launch_trace<true>(coop, sms, st, P, in_q);
@@ -1729,6 +1735,8 @@ extern "C" pt_status pt_render(pt_scene* s, const pt_camera* camera, uint32_t sp
             o.tail_paths = s->tuned_opts.tail_paths;
             o.block_size = s->tuned_opts.block_size;
             o.use_graph = s->tuned_opts.use_graph;
+            o.traversal = s->tuned_opts.traversal;
+            o.tail_bounce = s->tuned_opts.tail_bounce;
         } else {
             mode = (o.nrc || (uint64_t)acc->width * acc->height >= (1u << 16)) ? PT_MODE_WAVEFRONT : PT_MODE_MEGAKERNEL;
         }

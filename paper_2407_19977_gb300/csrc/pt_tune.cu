@@ -157,6 +157,19 @@ extern "C" pt_status pt_autotune(pt_scene* s, const pt_camera* camera, uint32_t 
         if (r != PT_OK) return r;
         if (t < win_t) { win_t = t; win = o; }
     }
+    // a wavefront winner with a tail limit: the tail kernel forced to take every remaining path
+    // at bounce 3..6, which drops the later bounces' launches (they would find nothing to do)
+    if (win.mode == PT_MODE_WAVEFRONT && win.tail_paths >= 0) {
+        const pt_render_opts base_win = win;
+        for (uint32_t kb = 3; kb <= std::min(6u, max_depth); ++kb) {
+            pt_render_opts o = base_win;
+            o.tail_bounce = kb;
+            float t = 0.0f;
+            r = run(o, &t);
+            if (r != PT_OK) return r;
+            if (t < win_t) { win_t = t; win = o; }
+        }
+    }
     *best = win;
     if (best_ms) *best_ms = win_t;
     s->tuned = true;

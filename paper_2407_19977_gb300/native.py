@@ -48,7 +48,7 @@ class pt_render_opts(C.Structure):
                 ("sort_by_material", C.c_int32), ("block_size", u32), ("sample_out", vp), ("nrc", vp),
                 ("nrc_train", u32), ("kernel_ms", C.POINTER(f32)), ("kernel_launches", C.POINTER(u32)),
                 ("tail_paths", C.c_int32), ("use_graph", u32), ("restir", C.POINTER(pt_restir_opts)),
-                ("traversal", u32)]
+                ("traversal", u32), ("tail_bounce", u32)]
 
 
 class pt_bvh_opts(C.Structure):

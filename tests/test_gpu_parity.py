@@ -794,6 +794,41 @@ def test_cooperative_passes_equal_per_lane_passes(api, which):
     assert gsc.stats()["error_flags"] == 0
 
 
+@pytest.mark.parametrize("which", ["pushbutton", "heavy", "cornell"])
+def test_forced_tail_bounce_equals_per_bounce_kernels(api, which):
+    """tail_bounce k: at bounce k the tail kernel takes every path still running, however many,
+    and no launch is issued for the later bounces.  Every sample, the accumulators and the ray
+    and Russian-roulette counts equal those of the per-bounce kernels alone, for k from the
+    first bounce to past the depth, with and without the material sort and under graph replay."""
+    from paper_2407_19977_gb300 import api as A
+    from paper_2407_19977_gb300 import native as N
+    sc, gsc, osc = {"pushbutton": pushbutton, "heavy": heavy, "cornell": cornell}[which]()
+    crop = {"pushbutton": (640, 360, 160, 90), "heavy": (900, 480, 128, 72), "cornell": (0, 0, 64, 64)}[which]
+    keys = ("ext_rays", "shadow_rays", "paths", "rr_terminated", "nan_dropped")
+    for sort in (1, 0):
+        b = gsc.stats()
+        ref, acc_ref = _samples(gsc, 3, crop, 23, tail_paths=-1, sort=sort)
+        a = gsc.stats()
+        st_ref = {k: a[k] - b[k] for k in keys}
+        for kb in (1, 2, 4, 30):
+            b = gsc.stats()
+            smp, acc = _samples(gsc, 3, crop, 23, tail_paths=0, tail_bounce=kb, sort=sort)
+            a = gsc.stats()
+            assert torch.equal(smp, ref), (which, sort, kb, float((smp - ref).abs().max()))
+            assert torch.equal(acc.sum, acc_ref.sum) and torch.equal(acc.comp, acc_ref.comp)
+            assert {k: a[k] - b[k] for k in keys} == st_ref, (which, sort, kb)
+    x0, y0, cw, ch = crop
+    outs = []
+    for kw in ({"tail_paths": -1}, {"tail_paths": 0, "tail_bounce": 3, "use_graph": True}):
+        acc = A.Accum(cw, ch)
+        for seed in (5, 5, 6):
+            gsc.render(2, accum=acc, crop=crop, mode=N.PT_MODE_WAVEFRONT, seed=seed, **kw)
+        torch.cuda.synchronize()
+        outs.append(acc)
+    assert torch.equal(outs[0].sum, outs[1].sum) and torch.equal(outs[0].comp, outs[1].comp)
+    assert gsc.stats()["error_flags"] == 0
+
+
 @pytest.mark.parametrize("which", ["cornell", "pushbutton"])
 def test_graph_replay_equals_direct_launches(api, which):
     """use_graph captures a wavefront call once and replays it; the first sample index and the
@@ -1063,9 +1098,21 @@ def test_autotune_and_auto_mode(api):
     osc = oracle.OracleScene(sc)
     best, ms = g.autotune(spp=4, frames=1, bvh=True)
     assert best["mode"] in (N.PT_MODE_WAVEFRONT, N.PT_MODE_MEGAKERNEL) and ms > 0
+    explicit = dict(mode=best["mode"], wave_paths=best["wave_paths"], sort=best["sort_by_material"],
+                    block_size=best["block_size"], tail_paths=best["tail_paths"], use_graph=bool(best["use_graph"]),
+                    traversal=best["traversal"], tail_bounce=best["tail_bounce"])
+    # PT_MODE_AUTO launches what the explicit winning schedule launches (each render twice: the
+    # first may capture a graph, the second replays it)
+    launched = []
+    for kw in (explicit, {"mode": N.PT_MODE_AUTO}):
+        for rep in range(2):
+            n0 = A.launch_count()
+            g.render(sc.spp, seed=4, **kw)
+            torch.cuda.synchronize()
+        launched.append(A.launch_count() - n0)
+    assert launched[0] == launched[1], (best, launched)
     a = g.render(sc.spp, mode=N.PT_MODE_AUTO, seed=4)
-    b = g.render(sc.spp, mode=best["mode"], wave_paths=best["wave_paths"], sort=best["sort_by_material"],
-                 block_size=best["block_size"], tail_paths=best["tail_paths"], use_graph=bool(best["use_graph"]), seed=4)
+    b = g.render(sc.spp, seed=4, **explicit)
     torch.cuda.synchronize()
     assert torch.equal(a.sum, b.sum)
     o_sum, _, _ = osc.render(spp=sc.spp, seed=4)

@@ -175,11 +175,14 @@ def _recorded_profile(kernel: str, workload: str, spp_per_step: int):
     return vals
 
 
-def _recorded_traffic(kernel: str, workload: str, spp_per_step: int):
-    """DRAM bytes per launch of `kernel` from its committed ncu record (see _recorded_profile)."""
+def _recorded_traffic(kernel: str, workload: str, spp_per_step: int, launches_per_step: int):
+    """DRAM bytes per launch of `kernel` from its committed ncu record (see _recorded_profile):
+    the bytes of all its launches in a step, over the launches this run issues per step (the
+    autotuned tail bounce decides how many of the bounces' launches a step issues; the ones it
+    leaves out moved no data)."""
     vals = _recorded_profile(kernel, workload, spp_per_step)
     try:
-        return float(vals["dram_bytes_per_launch"]) if vals else None
+        return float(vals["dram_bytes_per_step"]) / max(launches_per_step, 1) if vals else None
     except (KeyError, ValueError):
         return None
 
@@ -557,8 +560,8 @@ def run_ours(args, world, rank, local):
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     sm_ghz = float(_peaks()[0].get("sm_max_mhz", SM_MAX_GHZ * 1e3)) / 1e3
     alu_peak = alu_peak_gops(sm_count, sm_ghz)
-    traffic = _recorded_traffic("trace", args.workload, args.spp_per_step)
     trace_launches = max(kl["trace"], 1)
+    traffic = _recorded_traffic("trace", args.workload, args.spp_per_step, trace_launches)
     result = {
         "metric": _metric_name(args.workload),
         "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -358,6 +358,8 @@ pt_status pt_render(pt_scene* scene, const pt_camera* camera, uint32_t spp, uint
  *    are rendered tile by tile (crop_x0, crop_y0); larger windows return PT_ERR_INVALID_ARG;
  *  - opts->nrc, opts->restir and opts->kernel_ms / kernel_launches must be NULL, and
  *    opts->flags may hold PT_FLAG_NO_NEE and PT_FLAG_NO_RR only (PT_ERR_INVALID_ARG);
+ *    mode, wave_paths, tail_paths, tail_bounce, traversal and use_graph are ignored (waves
+ *    of the array's size, one ray per lane, no tail kernel, direct launches: the same bits);
  *  - every call shares the one array and leaves its contents behind; the kernels reset every
  *    counter they read before reading it.  Calls that overlap on the GPU (different streams,
  *    or threads without ordering) race on the array and corrupt each other's work;

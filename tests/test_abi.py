@@ -85,6 +85,9 @@ def test_restir_and_denoiser_arguments_are_checked_on_the_host():
     lib = N.load()
     assert C.sizeof(N.pt_restir_opts) == 16
     assert N.pt_render_opts.restir.offset % 8 == 0
+    # traversal and tail_bounce close the struct: 96 bytes on a 64-bit host
+    assert (N.pt_render_opts.traversal.offset, N.pt_render_opts.tail_bounce.offset) == (88, 92)
+    assert C.sizeof(N.pt_render_opts) == 96
     buf = (C.c_float * 48)()
     # NULL pointers, block outside 4..32, offset not below the block
     assert lib.pt_denoise_bmfr(None, None, 4, 4, 16, 0, 0, None, None) == 1

@@ -1,9 +1,15 @@
 // pt_api.cu -- C-ABI entry points: scene setup and teardown, diagnostics, statistics.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "pt_internal.h"
+
+uint64_t pt_next_serial() {
+    static std::atomic<uint64_t> next{1};
+    return next.fetch_add(1);
+}
 
 std::atomic<uint64_t> g_pt_launches{0};
 static thread_local std::string t_last_error;
@@ -203,6 +209,7 @@ extern "C" pt_status pt_scene_create(const float* vertices, uint32_t n_vertices,
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     pt_scene* s = new pt_scene();
+    s->serial = pt_next_serial();
     cudaGetDevice(&s->device);
     s->n_vertices = n_vertices;
     s->n_mesh_tris = n_triangles;

@@ -84,8 +84,13 @@ struct WaveBuffers {
     float4* rs_f = nullptr;
 };
 
+// A number no other scene or cache of this process has had: graph caches key on it, since a
+// destroyed object's host address can come back for a new one.
+uint64_t pt_next_serial();
+
 struct pt_scene {
     int device = 0;
+    uint64_t serial = 0;                 // pt_next_serial() at creation
     uint32_t n_vertices = 0, n_mesh_tris = 0, n_tris = 0, n_mats = 0, n_quads = 0;
     float* d_vertices = nullptr;
     uint32_t* d_indices = nullptr;
@@ -177,6 +182,7 @@ pt_status pt_wavefront_tail_limit(int* out);
 pt_status pt_nrc_render_infer_dev(pt_nrc* N, const float* queries, const uint32_t* n_dev, uint32_t cap, float* out4,
                                   cudaStream_t st);
 uint32_t pt_nrc_frame_samples(const pt_nrc* N);
+uint64_t pt_nrc_serial(const pt_nrc* N);
 pt_status pt_nrc_render_prepare(pt_nrc* N, uint32_t infer_cap, uint32_t train_cap);
 // Series of the fuzz lobe (FUZZ_FLOATS per row) for n raw material rows of PT_OPENPBR_FLOATS
 // floats on the device; rows without fuzz get zeros (pt_fuzz.cu).

@@ -1357,6 +1357,7 @@ __global__ void k_init(float* w, uint64_t nw, float* grid, uint64_t ng, uint64_t
 }  // namespace
 
 struct pt_nrc {
+    uint64_t serial = 0;    // pt_next_serial() at creation
     pt_nrc_opts o;
     uint32_t L = 16, T = 1u << 19, grid_cols = 32;
     uint32_t* d_res = nullptr;
@@ -1438,6 +1439,7 @@ extern "C" pt_status pt_nrc_create(const pt_nrc_opts* opts, void* cuda_stream, p
     for (int a = 0; a < 3; ++a)
         PT_CHECK_ARG(o.scene_max[a] > o.scene_min[a], "empty normalisation box");
     pt_nrc* N = new pt_nrc();
+    N->serial = pt_next_serial();
     N->o = o;
     N->L = o.n_levels;
     N->T = 1u << o.log2_table;
@@ -1732,3 +1734,5 @@ pt_status pt_nrc_render_train_dev(pt_nrc* N, const float* samples, const uint32_
     }
     return PT_OK;
 }
+
+uint64_t pt_nrc_serial(const pt_nrc* N) { return N ? N->serial : 0u; }

@@ -1397,7 +1397,7 @@ struct WfGraphKey {
     WfParams P;             // with the per-wave fields cleared
     uint32_t spp, npix_total, pix_chunk, samp_per_wave, tail_limit, tail_grid, count, coop;
     int sms, trace_bps, shade_bps, shadow_bps;
-    const void* nrc;        // the radiance cache the launches read and train
+    uint64_t nrc_serial;    // the radiance cache the launches read and train (0: none)
 };
 
 static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
@@ -1488,7 +1488,7 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
         key.coop = coop ? 1u : 0u;
         key.sms = sms; key.trace_bps = g_trace_blocks_per_sm; key.shade_bps = g_shade_blocks_per_sm;
         key.shadow_bps = g_shadow_blocks_per_sm;
-        key.nrc = o.nrc;
+        key.nrc_serial = pt_nrc_serial(o.nrc);
         if (s->wf_graph && s->wf_key.size() == sizeof(key) && std::memcmp(s->wf_key.data(), &key, sizeof(key)) == 0) {
             PT_CUDA_TRY(cudaGraphLaunch(s->wf_graph, user_st));
             pt_count_launch(s->wf_graph_launches);
@@ -1962,7 +1962,9 @@ static pt_status batch_merged(const pt_job* jobs, uint32_t n_jobs, const pt_batc
         n_keys += j.scene->n_mats + 2;
         fuzz = fuzz || j.scene->has_fuzz;
         max_depth = std::max(max_depth, j.max_depth);
-        key.insert(key.end(), {(uint64_t)(uintptr_t)j.scene, j.camera.width, j.camera.height, j.spp, j.max_depth});
+        // the scene's serial, not its address: the graph holds the first scene's statistics
+        // pointer, and a new scene may reuse a destroyed one's address
+        key.insert(key.end(), {j.scene->serial, j.camera.width, j.camera.height, j.spp, j.max_depth});
     }
     key.push_back(cap);
     key.push_back(fuzz ? 1u : 0u);

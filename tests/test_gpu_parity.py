@@ -968,24 +968,24 @@ def test_batch_merged_wavefront_equals_single_renders(api, wave_paths, graph):
 def test_batch_merged_graph_follows_new_scenes(api):
     """The merged batch's captured graph is keyed on its scenes' serial numbers, not on their
     addresses: after the scenes of one batch are destroyed, new scenes of the same shapes (whose
-    host objects may reuse the old addresses) get a graph of their own.  Each round's batch
+    host objects may reuse the old addresses) get a graph of their own.  Each pass's batch
     renders what its jobs render one by one and counts its rays in its own first scene."""
     import gc
     from paper_2407_19977_gb300 import api as A
     from paper_2407_19977_gb300 import native as N
-    for rnd in range(3):
+    for rep in range(3):
         mk, gs = _batch_scenes()
         accs = [A.Accum(s.camera.width, s.camera.height) for s in mk]
-        jobs = [(g, s.camera, 2, 5, 40 + rnd, a) for s, g, a in zip(mk, gs, accs)]
+        jobs = [(g, s.camera, 2, 5, 40 + rep, a) for s, g, a in zip(mk, gs, accs)]
         before = gs[0].stats()["ext_rays"]
         A.render_batch(jobs, mode=N.PT_MODE_WAVEFRONT, merged=True, wave_paths=1 << 22, use_graph=True)
         torch.cuda.synchronize()
-        assert gs[0].stats()["ext_rays"] > before, rnd
+        assert gs[0].stats()["ext_rays"] > before, rep
         for s, g, a in zip(mk, gs, accs):
             one = A.Accum(s.camera.width, s.camera.height)
-            g.render(2, max_depth=5, seed=40 + rnd, accum=one, mode=N.PT_MODE_WAVEFRONT)
+            g.render(2, max_depth=5, seed=40 + rep, accum=one, mode=N.PT_MODE_WAVEFRONT)
             torch.cuda.synchronize()
-            assert torch.equal(a.sum, one.sum) and torch.equal(a.comp, one.comp), rnd
+            assert torch.equal(a.sum, one.sum) and torch.equal(a.comp, one.comp), rep
             assert g.stats()["error_flags"] == 0
         del jobs, gs
         gc.collect()

@@ -305,6 +305,7 @@ struct WfParams {
     uint32_t max_depth, flags;
     uint32_t n_keys;               // material sort buckets (0 = no sort)
     uint32_t tail_bounce;          // host: bounce at which the tail kernel takes every path (0: none)
+    uint32_t tiled;                // 1: the first queue holds each sample's pixels in 8 x 4 tiles
     float4* ray_o[2];
     float4* ray_d[2];
     float4* hit;
@@ -407,15 +408,27 @@ __global__ void k_wf_frame(uint32_t* counters, uint32_t first_sample, uint64_t s
     }
 }
 
+// Queue slot t of the first bounce holds path id = t unless the wave is tiled: then within
+// each sample's block of npix slots, slot j holds the pixel of the 8 x 4 tile order (tiles
+// left to right along each group of 4 rows), so that a warp's 32 camera rays cover a compact
+// 8 x 4 footprint instead of 32 pixels of one row.  Only the order of the queue changes: the
+// path id (pixel-major, as everywhere else) rides with the ray.
+__device__ __forceinline__ uint32_t tiled_path(const WfParams& P, uint32_t t) {
+    const uint32_t s = t / P.npix, j = t % P.npix, w4 = 4u * P.cw;
+    const uint32_t g = j / w4, w = j % w4, k = w & 31u;
+    return s * P.npix + (4u * g + (k >> 3)) * P.cw + (w >> 5) * 8u + (k & 7u);
+}
+
 __global__ void k_wf_raygen(WfParams P) {
-    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t n = P.npix * P.nsamp;
-    if (id == 0) {
+    if (t == 0) {
         P.counters[C_Q0] = n;
         P.counters[C_TAIL] = 0;
         atomicAdd(&P.stats[ST_PATHS], (unsigned long long)n);
     }
-    if (id >= n) return;
+    if (t >= n) return;
+    const uint32_t id = P.tiled ? tiled_path(P, t) : t;
     const uint32_t lp = P.pb + id % P.npix;
     const uint32_t s = wf_sample_base(P) + id / P.npix;
     const uint64_t seed = wf_seed(P);
@@ -423,8 +436,8 @@ __global__ void k_wf_raygen(WfParams P) {
     const uint32_t p = py * P.cam.width + px;
     float3 o, d;
     camera_ray_ps(P.cam, px, py, p, s, (uint32_t)seed, (uint32_t)(seed >> 32), o, d);
-    P.ray_o[0][id] = make_float4(o.x, o.y, o.z, 0.0f);
-    P.ray_d[0][id] = make_float4(d.x, d.y, d.z, __uint_as_float(id));
+    P.ray_o[0][t] = make_float4(o.x, o.y, o.z, 0.0f);
+    P.ray_d[0][t] = make_float4(d.x, d.y, d.z, __uint_as_float(id));
     P.beta[id] = make_float4(1.0f, 1.0f, 1.0f, -1.0f);
     P.radiance[id] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (P.nrc_on) {
@@ -1530,6 +1543,8 @@ static pt_status render_wavefront(pt_scene* s, const pt_camera& cam, uint32_t sp
                 P.npix = npix;
                 P.i0 = i0;
                 P.nsamp = ns;
+                // whole groups of 4 rows, 8-pixel tiles across; ReSTIR's first pass needs slot = path id
+                P.tiled = (!restir && pb % P.cw == 0 && npix % (4u * P.cw) == 0 && P.cw % 8u == 0) ? 1u : 0u;
                 const uint32_t n = npix * ns;
                 if (P.nrc_on) {
                     P.train_prob = std::min(1.0f, (float)w.train_slots / (float)n);
